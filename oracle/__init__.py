@@ -1,0 +1,168 @@
+"""The oracle: plain single-threaded C statement of the Chapter 5 method
+(LeGall 5/3 integer lifting, Eq. 5.1/5.2; dyadic 2-D decomposition, Sec. 5.1.1;
+AES-128-CTR on the final LL band, Sec. 5.2.1), wrapped with ctypes.
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` are its only users.  The CUDA library never loads
+it, and the two share no code.  Parity unpinned: none (every function is pinned
+by tests/test_oracle_*.py against the thesis's printed matrix A and F(4,4)
+weights, its magnitude bounds, hand-worked examples, closed forms, invariants
+and the FIPS-197 / SP 800-38A vectors).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "frag_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_lib = None
+
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, -O2, no vectorisation flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-Wall", "-Wextra",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        lib.oracle_lift53_fwd_1d.argtypes = [_i32p, ctypes.c_int64, _i32p]
+        lib.oracle_lift53_inv_1d.argtypes = [_i32p, ctypes.c_int64, _i32p]
+        lib.oracle_dwt53_fwd_2d.argtypes = [_i32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
+        lib.oracle_dwt53_inv_2d.argtypes = [_i32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
+        lib.oracle_aes128_expand_key.argtypes = [_u8p, _u8p]
+        lib.oracle_aes128_encrypt_block.argtypes = [_u8p, _u8p, _u8p]
+        lib.oracle_aes128_ctr_xor.argtypes = [_u8p, ctypes.c_uint64, ctypes.c_uint64, _u8p,
+                                              ctypes.c_uint64]
+        lib.oracle_sizes.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _u64p,
+                                     _u64p, _u64p]
+        lib.oracle_protect.argtypes = [_u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                       _u8p, ctypes.c_uint64, _u8p, _u8p]
+        lib.oracle_recover.argtypes = [_u8p, _u8p, ctypes.c_uint64, ctypes.c_uint32,
+                                       ctypes.c_uint32, _u8p, ctypes.c_uint64, _u8p]
+        for f in ("oracle_dwt53_fwd_2d", "oracle_dwt53_inv_2d", "oracle_sizes", "oracle_protect",
+                  "oracle_recover"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _key(key) -> np.ndarray:
+    k = np.frombuffer(bytes(key), dtype=np.uint8).copy()
+    if k.size != 16:
+        raise ValueError("AES-128 key must be 16 bytes")
+    return k
+
+
+def lift53_fwd_1d(x) -> np.ndarray:
+    """Eq. 5.1/5.2 on one even-length signal; returns [s | d]."""
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    out = np.empty_like(x)
+    _load().oracle_lift53_fwd_1d(_p(x, _i32p), x.size, _p(out, _i32p))
+    return out
+
+
+def lift53_inv_1d(sd) -> np.ndarray:
+    sd = np.ascontiguousarray(sd, dtype=np.int32)
+    out = np.empty_like(sd)
+    _load().oracle_lift53_inv_1d(_p(sd, _i32p), sd.size, _p(out, _i32p))
+    return out
+
+
+def dwt53_fwd_2d(img, levels: int) -> np.ndarray:
+    """L-level dyadic 2-D transform (rows first); Mallat layout, int32."""
+    a = np.array(img, dtype=np.int32, order="C", copy=True)
+    st = _load().oracle_dwt53_fwd_2d(_p(a, _i32p), a.shape[0], a.shape[1], levels)
+    if st:
+        raise RuntimeError("oracle_dwt53_fwd_2d failed: %d" % st)
+    return a
+
+
+def dwt53_inv_2d(coef, levels: int) -> np.ndarray:
+    a = np.array(coef, dtype=np.int32, order="C", copy=True)
+    st = _load().oracle_dwt53_inv_2d(_p(a, _i32p), a.shape[0], a.shape[1], levels)
+    if st:
+        raise RuntimeError("oracle_dwt53_inv_2d failed: %d" % st)
+    return a
+
+
+def aes128_expand_key(key) -> np.ndarray:
+    k = _key(key)
+    rk = np.empty(176, dtype=np.uint8)
+    _load().oracle_aes128_expand_key(_p(k, _u8p), _p(rk, _u8p))
+    return rk
+
+
+def aes128_encrypt_block(key, block) -> bytes:
+    rk = aes128_expand_key(key)
+    b = np.frombuffer(bytes(block), dtype=np.uint8).copy()
+    out = np.empty(16, dtype=np.uint8)
+    _load().oracle_aes128_encrypt_block(_p(rk, _u8p), _p(b, _u8p), _p(out, _u8p))
+    return out.tobytes()
+
+
+def aes128_ctr_xor(key, nonce: int, first_block: int, data) -> bytes:
+    k = _key(key)
+    d = np.frombuffer(bytes(data), dtype=np.uint8).copy()
+    _load().oracle_aes128_ctr_xor(_p(k, _u8p), nonce, first_block, _p(d, _u8p), d.size)
+    return d.tobytes()
+
+
+def sizes(n: int, width: int, levels: int):
+    """(H, private_bytes, public_bytes) for n input bytes."""
+    H, pb, ub = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    st = _load().oracle_sizes(n, width, levels, ctypes.byref(H), ctypes.byref(pb),
+                              ctypes.byref(ub))
+    if st:
+        raise ValueError("invalid plan: width=%d levels=%d" % (width, levels))
+    return H.value, pb.value, ub.value
+
+
+def protect(data, width: int, levels: int, key, nonce: int):
+    """Bytes -> (private fragment, public fragment), both uint8 arrays."""
+    buf = np.ascontiguousarray(np.frombuffer(data, dtype=np.uint8) if isinstance(data, (bytes, bytearray)) else data, dtype=np.uint8).reshape(-1)
+    n = buf.size
+    _, pb, ub = sizes(n, width, levels)
+    priv = np.zeros(pb, dtype=np.uint8)
+    pub = np.zeros(ub, dtype=np.uint8)
+    k = _key(key)
+    st = _load().oracle_protect(_p(buf, _u8p), n, width, levels, _p(k, _u8p), nonce,
+                                _p(priv, _u8p), _p(pub, _u8p))
+    if st:
+        raise RuntimeError("oracle_protect failed: %d" % st)
+    return priv, pub
+
+
+def recover(priv, pub, n: int, width: int, levels: int, key, nonce: int) -> np.ndarray:
+    _, pb, ub = sizes(n, width, levels)
+    priv = np.ascontiguousarray(priv, dtype=np.uint8).reshape(-1)
+    pub = np.ascontiguousarray(pub, dtype=np.uint8).reshape(-1)
+    if priv.size != pb or pub.size != ub:
+        raise ValueError("fragment sizes do not match the plan")
+    out = np.zeros(n, dtype=np.uint8)
+    k = _key(key)
+    st = _load().oracle_recover(_p(priv, _u8p), _p(pub, _u8p), n, width, levels, _p(k, _u8p),
+                                nonce, _p(out, _u8p))
+    if st:
+        raise RuntimeError("oracle_recover failed: %d" % st)
+    return out
