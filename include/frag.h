@@ -1,0 +1,186 @@
+/*
+ * frag.h -- C ABI of the B300 library for agnostic data fragmentation with a
+ * reversible integer wavelet (Chapter 5 of "An Efficient Data Protection
+ * Architecture Based on Fragmentation and Encryption", arXiv 1803.04880).
+ *
+ * The method (Sec. 5.2.1-5.2.3): any bytes are read as the pixels of a gray
+ * image of a chosen width; a reversible integer LeGall 5/3 2-D wavelet
+ * transform (lifting steps Eq. 5.1 / 5.2, rows before columns, dyadic levels
+ * on the LL band, Sec. 5.1.1) splits them into a small private fragment, the
+ * final-level LL band, protected with AES-128 (here in CTR mode), and a public
+ * fragment made of the detail bands.  The transform maps integers to integers,
+ * so recovery is exact.
+ *
+ * Conventions shared by every call:
+ *   - Status codes: every function returns frag_status; FRAG_OK is 0.  On an
+ *     error a thread-local message is available from frag_get_error().  No C++
+ *     exception crosses this boundary.
+ *   - Memory: the caller owns every data buffer.  Pointers named d_* are CUDA
+ *     DEVICE pointers of the current device; pointers named h_* are HOST
+ *     pointers.  The library owns plans, keys, batches and its own small
+ *     device tables.
+ *   - Streams: work is enqueued on the caller's stream (frag_stream, a
+ *     cudaStream_t; NULL is the legacy default stream) and the call returns
+ *     without waiting, except the h_* entry points, which wait for their own
+ *     copies.  Launch errors are returned; errors raised while the kernels run
+ *     surface through frag_sync_status().
+ *   - Matrix: for n input bytes and a plan (W, L), the image has W columns and
+ *     H = ceil(n / W) rows rounded up to a multiple of 2^L; bytes past n are
+ *     zeros that are never materialised.  Level l has H_l = H >> l rows and
+ *     W_l = W >> l columns.
+ *   - Level shift: bytes b are transformed as b - 128 (Sec. 5.2.3 treats
+ *     0..255 as -128..127).
+ *   - Private fragment: LL_L as int16 little-endian, row-major, H_L * W_L
+ *     values (2 * H_L * W_L bytes), XORed with the AES-128-CTR keystream whose
+ *     counter block for 16-byte block b is nonce (8 bytes, big-endian) || b
+ *     (8 bytes, big-endian), b counted from 0 at the fragment's first byte.
+ *   - Public fragment: the detail bands as int16 little-endian, coarsest level
+ *     first, HL_L, LH_L, HH_L, HL_{L-1}, ..., HH_1, each band H_l x W_l
+ *     row-major (2 * (H * W - H_L * W_L) bytes in all).  HL is the top-right
+ *     quadrant (high horizontal frequency), LH bottom-left, HH bottom-right.
+ *   - nbytes, (W, L) and the nonce are caller metadata: the fragments do not
+ *     record them.  Use one nonce per buffer under one key.
+ *   - Buffers may have any byte alignment.
+ */
+#ifndef FRAG_H
+#define FRAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FRAG_ABI_VERSION 1
+
+typedef enum {
+    FRAG_OK = 0,
+    FRAG_EINVAL = 1,       /* a bad argument: null pointer, bad size or plan */
+    FRAG_EUNSUPPORTED = 2, /* a filter or shape the library does not implement */
+    FRAG_ENOMEM = 3,       /* a host or device allocation of the library failed */
+    FRAG_ECUDA = 4,        /* a CUDA runtime call failed (message has the text) */
+    FRAG_ETIMEOUT = 5,     /* a bounded device-side wait ran out */
+    FRAG_EDEVICE = 6       /* a kernel recorded an error in the device error word */
+} frag_status;
+
+/* The only filter the thesis uses (Sec. 5.1.1: "Le Gall 5/3", lifting form
+ * Eq. 5.1 / 5.2, update step with a plus sign as in JPEG 2000). */
+typedef enum { FRAG_FILTER_LEGALL53 = 0 } frag_filter;
+
+typedef struct frag_plan_s *frag_plan;
+typedef struct frag_key_s *frag_key;
+typedef struct frag_batch_s *frag_batch;
+typedef struct CUstream_st *frag_stream; /* same type as cudaStream_t */
+
+/* Version of this ABI (FRAG_ABI_VERSION). */
+int frag_abi_version(void);
+
+/* Plan = matrix width W and number of levels L (Sec. 5.2.1: the chunk is a
+ * matrix of configurable size; Sec. 5.1.1: two levels in the thesis, L here).
+ * FRAG_EINVAL if out is NULL, levels == 0, levels > 8, width == 0 or width is
+ * not a multiple of 2^levels; FRAG_EUNSUPPORTED for any other filter. */
+frag_status frag_plan_create(frag_plan *out, uint32_t width, uint32_t levels, frag_filter filter);
+frag_status frag_plan_destroy(frag_plan plan);
+
+/* Sizes for nbytes of input: rows H, private and public fragment bytes.
+ * Any of the output pointers may be NULL.  nbytes == 0 gives all zeros.
+ * FRAG_EINVAL if H would not fit in 32 bits. */
+frag_status frag_plan_sizes(frag_plan plan, uint64_t nbytes, uint32_t *height,
+                            uint64_t *private_bytes, uint64_t *public_bytes);
+
+/* Launch tuning of the tiled kernels for this plan (the autotuner sets it;
+ * 0 keeps the default).  tile_w / tile_h: owned tile size in pixels,
+ * multiples of 16 and of 2^L, at most 256; ctas_per_sm: resident CTAs per SM
+ * of the persistent grid (0 = as many as fit). */
+frag_status frag_plan_set_tiling(frag_plan plan, uint32_t tile_w, uint32_t tile_h,
+                                 uint32_t ctas_per_sm);
+frag_status frag_plan_get_tiling(frag_plan plan, uint32_t *tile_w, uint32_t *tile_h,
+                                 uint32_t *ctas_per_sm);
+
+/* AES-128 key (Sec. 5.2.1 protects the private fragment with AES-128): the
+ * round keys are expanded on the host (FIPS-197 Sec. 5.2) and kept resident on
+ * each device that uses the key.  The 16 bytes are copied. */
+frag_status frag_key_create(frag_key *out, const uint8_t key[16]);
+frag_status frag_key_destroy(frag_key key);
+
+/* Protect one buffer (Sec. 5.2.1, Fig. "SE process for the single block"):
+ * d_in holds nbytes bytes; d_private receives private_bytes, d_public
+ * public_bytes (see frag_plan_sizes).  Output buffers must not overlap the
+ * input or each other.  nbytes == 0 is a no-op.  Asynchronous on stream. */
+frag_status frag_protect(frag_plan plan, frag_key key, uint64_t nonce, const void *d_in,
+                         uint64_t nbytes, void *d_private, void *d_public, frag_stream stream);
+
+/* Recover one buffer (Sec. 5.2.3: the transform is lossless): the exact
+ * inverse of frag_protect with the same plan, key, nonce and nbytes.  Writes
+ * exactly nbytes bytes to d_out.  Fragments that were not produced with these
+ * parameters give other bytes, never an out-of-bounds access. */
+frag_status frag_recover(frag_plan plan, frag_key key, uint64_t nonce, const void *d_private,
+                         const void *d_public, uint64_t nbytes, void *d_out, frag_stream stream);
+
+/* Host-buffer forms of the two calls: copy the host input into stream-ordered
+ * device memory (cudaMallocAsync), run the same kernels, copy the results
+ * back, and return once they are in host memory.  Pinned (cudaHostAlloc) host
+ * buffers give full copy bandwidth. */
+frag_status frag_protect_host(frag_plan plan, frag_key key, uint64_t nonce, const void *h_in,
+                              uint64_t nbytes, void *h_private, void *h_public,
+                              frag_stream stream);
+frag_status frag_recover_host(frag_plan plan, frag_key key, uint64_t nonce, const void *h_private,
+                              const void *h_public, uint64_t nbytes, void *h_out,
+                              frag_stream stream);
+
+/* Batched forms: many independent buffers, each with its own plan, nonce and
+ * size, under one key, processed by ONE persistent kernel launch whose CTAs
+ * pull tiles from a device work queue ordered from the most to the least
+ * costly buffer.  Each item's output is byte-identical to what the
+ * single-buffer call gives for it.  The descriptors are copied into
+ * library-owned memory before the call returns, so the caller may reuse the
+ * array; that memory is released lazily once the launch has completed.
+ * count == 0 is a no-op.  Items must not share output memory. */
+typedef struct {
+    frag_plan plan;
+    uint64_t nonce;
+    uint64_t nbytes;
+    const void *d_in;
+    void *d_private;
+    void *d_public;
+} frag_item;
+
+typedef struct {
+    frag_plan plan;
+    uint64_t nonce;
+    uint64_t nbytes;
+    const void *d_private;
+    const void *d_public;
+    void *d_out;
+} frag_ritem;
+
+frag_status frag_protect_batch(const frag_item *items, uint32_t count, frag_key key,
+                               frag_stream stream);
+frag_status frag_recover_batch(const frag_ritem *items, uint32_t count, frag_key key,
+                               frag_stream stream);
+
+/* Batch objects for CUDA-graph capture: *_create builds the work queue and
+ * uploads it (synchronously) to the current device; frag_batch_run enqueues
+ * only a memset of the queue head and the persistent kernel, so a capture of
+ * frag_batch_run replays with no host work.  Buffers named in the items must
+ * stay valid while the batch exists. */
+frag_status frag_batch_create_protect(frag_batch *out, const frag_item *items, uint32_t count);
+frag_status frag_batch_create_recover(frag_batch *out, const frag_ritem *items, uint32_t count);
+frag_status frag_batch_run(frag_batch batch, frag_key key, frag_stream stream);
+frag_status frag_batch_destroy(frag_batch batch);
+
+/* Thread-local text of the last error (always NUL-terminated).  Returns
+ * FRAG_OK, or FRAG_EINVAL if buf is NULL or len is 0. */
+frag_status frag_get_error(char *buf, size_t len);
+
+/* Waits for stream, then reads and clears the device error word of the
+ * current device: FRAG_OK, FRAG_EDEVICE (a kernel found an inconsistent
+ * descriptor), FRAG_ETIMEOUT (a bounded wait ran out) or FRAG_ECUDA. */
+frag_status frag_sync_status(frag_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRAG_H */

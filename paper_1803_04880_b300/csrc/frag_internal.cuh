@@ -1,0 +1,77 @@
+// frag_internal.cuh -- shared definitions of the CUDA library (kernels + C ABI).
+//
+// Nothing here is shared with the oracle: the AES tables are derived by this
+// library's own host code (log/antilog tables over GF(2^8)), and the lifting
+// is written for the in-place tile layout the kernels use.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace frag {
+
+// One buffer of a launch.  For protect, `in` is read and priv/pub are
+// written; for recover, priv_in/pub_in are read and `out` is written.
+struct Job {
+    const uint8_t *in;
+    const uint8_t *priv_in;
+    const uint8_t *pub_in;
+    uint8_t *out;
+    uint8_t *priv;
+    uint8_t *pub;
+    uint64_t n;       // bytes of the original buffer
+    uint64_t nonce;   // AES-CTR nonce (high 64 bits of the counter block)
+    uint32_t W;       // matrix width
+    uint32_t H;       // padded rows (multiple of 2^L)
+    uint32_t L;       // levels
+    uint32_t tile_w;  // owned tile width  (multiple of 2^L)
+    uint32_t tile_h;  // owned tile height (multiple of 2^L)
+    uint32_t tiles_x;
+    uint32_t tiles_y;
+    uint32_t pad_;
+};
+
+// Launch-wide description of where jobs and tiles come from.
+struct Work {
+    Job single;                 // used when jobs == nullptr
+    const Job *jobs;            // device array of jobs (batched launch)
+    const uint64_t *tile_start; // exclusive prefix of tiles per job (njobs + 1 entries)
+    uint32_t njobs;
+    uint64_t total_tiles;
+    unsigned long long *queue;  // device work-queue head (nullptr: static striding)
+    const uint32_t *aes_tables; // 4 x 256 T-table words + 256 S-box words, device
+    const uint32_t *round_keys; // 44 big-endian round-key words, device
+    int *err;                   // device error word
+};
+
+constexpr int kThreads = 256;
+constexpr int kAesWords = 4 * 256 + 256;
+
+// Byte offset of band b (0 = HL, 1 = LH, 2 = HH) of level l (1..L) inside the
+// public fragment: levels are stored coarsest first, three bands each.
+__host__ __device__ inline uint64_t band_offset(uint32_t H, uint32_t W, uint32_t L, uint32_t l,
+                                                uint32_t b)
+{
+    uint64_t off = 0;
+    for (uint32_t k = L; k > l; --k)
+        off += 6ull * (uint64_t)(H >> k) * (uint64_t)(W >> k);
+    return off + 2ull * b * (uint64_t)(H >> l) * (uint64_t)(W >> l);
+}
+
+// Halo of the tile window in level-0 pixels.  Forward: the level-L output at
+// index k depends on level-0 samples 2^L k - 2(2^L - 1) .. 2^L k + 2^L - 1
+// (each level needs two samples left and one right of its pair), so 2^(L+1)
+// to the left and 2^L to the right cover it.  Inverse: level-0 sample x needs
+// level-l coefficients from about x/2^l - 2 to x/2^l + 1 plus the detail
+// half-step, so 2^(L+1) on both sides.
+__host__ __device__ inline uint32_t halo_lo(uint32_t L) { return 2u << L; }
+__host__ __device__ inline uint32_t halo_hi_fwd(uint32_t L) { return 1u << L; }
+__host__ __device__ inline uint32_t halo_hi_inv(uint32_t L) { return 2u << L; }
+
+// kernels (tile_kernels.cu)
+size_t tile_smem_bytes(uint32_t tile_w, uint32_t tile_h, uint32_t L, bool fwd);
+cudaError_t launch_tiles(bool fwd, const Work &w, uint32_t grid, size_t smem, cudaStream_t stream);
+cudaError_t tile_occupancy(bool fwd, size_t smem, int *blocks_per_sm);
+
+} // namespace frag

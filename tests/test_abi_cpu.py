@@ -1,0 +1,76 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, it exports
+every entry point include/frag.h declares, and its plan logic (validation,
+fragment sizes) agrees with the oracle's size arithmetic."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+import paper_1803_04880_b300 as fr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    fr.build()
+    return fr.lib()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "frag.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:frag_status|int)\s+(frag_\w+)\s*\(", src, re.M)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_symbols()
+    assert len(names) >= 20
+    assert sorted(fr.EXPORTS) == names or set(fr.EXPORTS) <= set(names)
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_abi_version(L):
+    assert L.frag_abi_version() == 1
+
+
+@pytest.mark.parametrize("w,l,status", [(0, 1, fr.FRAG_EINVAL), (12, 3, fr.FRAG_EINVAL),
+                                        (64, 0, fr.FRAG_EINVAL), (1024, 9, fr.FRAG_EINVAL),
+                                        (1024, 6, fr.FRAG_EUNSUPPORTED)])
+def test_plan_validation(L, w, l, status):
+    h = ctypes.c_void_p()
+    assert L.frag_plan_create(ctypes.byref(h), w, l, 0) == status
+    assert "width" in fr.last_error() or "levels" in fr.last_error()
+
+
+def test_unknown_filter(L):
+    h = ctypes.c_void_p()
+    assert L.frag_plan_create(ctypes.byref(h), 64, 2, 7) == fr.FRAG_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("n,w,l", [(0, 64, 2), (1, 2, 1), (1000, 64, 3), (65536, 256, 1),
+                                   (3 * 4096 * 4096 // 3, 4096, 3), (77777, 256, 5),
+                                   (268435456, 8192, 4)])
+def test_sizes_match_oracle(L, n, w, l):
+    p = fr.Plan(w, l)
+    H, pb, ub = p.sizes(n)
+    assert (H, pb, ub) == oracle.sizes(n, w, l)
+
+
+def test_tiling_validation(L):
+    p = fr.Plan(256, 3)
+    assert p.tiling()[:2] == (64, 64)
+    p.set_tiling(128, 32, 2)
+    assert p.tiling() == (128, 32, 2)
+    for bad in ((40, 64), (64, 300), (8, 64)):
+        with pytest.raises(fr.FragError):
+            p.set_tiling(*bad)
+
+
+def test_null_arguments_are_rejected(L):
+    p = fr.Plan(64, 2)
+    assert L.frag_protect(p.handle, None, 0, None, 16, None, None, None) == fr.FRAG_EINVAL
+    assert L.frag_recover(None, None, 0, None, None, 16, None, None) == fr.FRAG_EINVAL
+    assert L.frag_get_error(None, 0) == fr.FRAG_EINVAL

@@ -1,0 +1,211 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle, bit-exact
+on every private, public and recovered byte.
+
+Integer work, so the bar is exact equality.  Sizes run from single tiles with
+ragged tails up to the full workloads (the 256 x 256 matrix, the 3-plane
+4096 x 4096 bitmap and the 256 MiB buffer at 2 and 4 levels).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_04880_b300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KEY = wl.KEY
+
+
+@pytest.fixture(scope="module")
+def fr():
+    import paper_1803_04880_b300 as m
+    m.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return m
+
+
+@pytest.fixture(scope="module")
+def key(fr):
+    return fr.Key(KEY)
+
+
+def gpu_round_trip(fr, key, data, W, L, nonce, tiling=None, offset=0):
+    plan = fr.Plan(W, L)
+    if tiling:
+        plan.set_tiling(*tiling)
+    n = data.size
+    _, pb, ub = plan.sizes(n)
+    # offset > 0 places every buffer at an odd address
+    dev_in = torch.zeros(n + offset, dtype=torch.uint8, device="cuda")
+    dev_in[offset:] = torch.from_numpy(np.ascontiguousarray(data).reshape(-1)).cuda()
+    priv = torch.full((pb + offset,), 0xAA, dtype=torch.uint8, device="cuda")
+    pub = torch.full((ub + offset,), 0xAA, dtype=torch.uint8, device="cuda")
+    out = torch.full((n + offset + 64,), 0x55, dtype=torch.uint8, device="cuda")
+    fr.protect(plan, key, nonce, dev_in[offset:], n, priv[offset:], pub[offset:])
+    fr.recover(plan, key, nonce, priv[offset:], pub[offset:], n, out[offset:offset + n])
+    fr.sync_status()
+    o = out.cpu().numpy()
+    assert (o[offset + n:] == 0x55).all(), "recover wrote past n"
+    return priv[offset:].cpu().numpy(), pub[offset:].cpu().numpy(), o[offset:offset + n]
+
+
+def check_against_oracle(fr, key, data, W, L, nonce=0, tiling=None, offset=0):
+    data = np.ascontiguousarray(data).reshape(-1)
+    p_ref, u_ref = oracle.protect(data, W, L, KEY, nonce)
+    p, u, r = gpu_round_trip(fr, key, data, W, L, nonce, tiling, offset)
+    assert np.array_equal(p, p_ref), "private fragment differs"
+    if not np.array_equal(u, u_ref):
+        bad = np.flatnonzero(u != u_ref)
+        raise AssertionError("public fragment differs at %d bytes, first %s" % (bad.size, bad[:8]))
+    assert np.array_equal(r, data), "recovered bytes differ"
+
+
+def test_c1_full(fr, key):
+    check_against_oracle(fr, key, wl.c1(), 256, 1, 0)
+
+
+SWEEP = [
+    # (n, W, L, tiling)
+    (1, 2, 1, None), (2, 2, 1, None), (5, 4, 2, None), (64, 8, 2, None), (1000, 64, 3, None),
+    (4096, 64, 1, None), (4097, 64, 1, None), (5000, 16, 4, None), (12345, 128, 2, None),
+    (65536 + 17, 256, 3, None), (77777, 256, 5, None), (100000, 1024, 4, None),
+    (200000, 96, 2, None), (300000, 160, 5, None), (131072, 512, 3, (32, 16, 0)),
+    (131072, 512, 3, (128, 32, 1)), (250000, 1000, 3, (16, 16, 0)), (262144, 256, 4, (256, 16, 0)),
+    (99999, 32, 5, (32, 32, 0)), (1 << 20, 2048, 2, (64, 128, 0)),
+]
+
+
+@pytest.mark.parametrize("n,W,L,tiling", SWEEP)
+def test_sweep_random(fr, key, n, W, L, tiling):
+    data = wl.random_bytes(n, seed=n + W + L)
+    check_against_oracle(fr, key, data, W, L, nonce=n % 7, tiling=tiling)
+
+
+@pytest.mark.parametrize("n,W,L", [(12345, 128, 2), (4096, 64, 3), (77777, 256, 5)])
+def test_unaligned_buffers(fr, key, n, W, L):
+    check_against_oracle(fr, key, wl.random_bytes(n, 5), W, L, nonce=3, offset=1)
+
+
+@pytest.mark.parametrize("kind", ["zeros", "ones", "checker", "ramp", "c3mix"])
+def test_structured_inputs(fr, key, kind):
+    W, L, H = 512, 4, 300
+    if kind == "zeros":
+        d = np.zeros(W * H, np.uint8)
+    elif kind == "ones":
+        d = np.full(W * H, 255, np.uint8)
+    elif kind == "checker":
+        d = (np.add.outer(np.arange(H), np.arange(W)) % 2 * 255).astype(np.uint8).ravel()
+    elif kind == "ramp":
+        d = (np.add.outer(np.arange(H), np.arange(W)) % 256).astype(np.uint8).ravel()
+    else:
+        d = wl.c3(total=W * H)
+    check_against_oracle(fr, key, d, W, L, nonce=9)
+
+
+def test_c2_full(fr, key):
+    planes = wl.c2()
+    for i in range(planes.shape[0]):
+        check_against_oracle(fr, key, planes[i], 4096, 3, nonce=i)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_c3_full(fr, key, L):
+    data = wl.c3()
+    check_against_oracle(fr, key, data, wl.C3_WIDTH, L, nonce=0)
+
+
+def test_zero_bytes_is_noop(fr, key):
+    plan = fr.Plan(64, 2)
+    t = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    fr.protect(plan, key, 0, t, 0, t, t)
+    fr.recover(plan, key, 0, t, t, 0, t)
+    fr.sync_status()
+    assert not t.any()
+
+
+def test_wrong_key_gives_other_bytes_without_error(fr, key):
+    data = wl.random_bytes(50000, 1)
+    plan = fr.Plan(256, 2)
+    d = torch.from_numpy(data).cuda()
+    priv, pub = fr.protect(plan, key, 4, d)
+    other = fr.Key(bytes([1]) + KEY[1:])
+    out = fr.recover(plan, other, 4, priv, pub, data.size)
+    out2 = fr.recover(plan, key, 5, priv, pub, data.size)
+    fr.sync_status()
+    assert not np.array_equal(out.cpu().numpy(), data)
+    assert not np.array_equal(out2.cpu().numpy(), data)
+
+
+def test_host_buffer_forms(fr, key):
+    data = wl.random_bytes(300000, 2)
+    plan = fr.Plan(512, 3)
+    p, u = fr.protect_host(plan, key, 11, data)
+    p_ref, u_ref = oracle.protect(data, 512, 3, KEY, 11)
+    assert np.array_equal(p.numpy(), p_ref) and np.array_equal(u.numpy(), u_ref)
+    r = fr.recover_host(plan, key, 11, p, u, data.size)
+    assert np.array_equal(r.numpy(), data)
+
+
+def _mixed_items(count, seed, hi=1 << 18):
+    items = wl.c4_items(count=count, lo=64, hi=hi, seed=seed)
+    datas = [wl.random_bytes(n, seed=i) for i, (n, _, _, _) in enumerate(items)]
+    return items, datas
+
+
+def test_batch_matches_single_calls_and_oracle(fr, key):
+    items, datas = _mixed_items(60, seed=31)
+    plans = {}
+    ins, privs, pubs, outs, entries, rentries = [], [], [], [], [], []
+    for (n, W, L, nonce), d in zip(items, datas):
+        plan = plans.setdefault((W, L), fr.Plan(W, L))
+        _, pb, ub = plan.sizes(n)
+        t = torch.from_numpy(d).cuda()
+        p = torch.empty(pb, dtype=torch.uint8, device="cuda")
+        u = torch.empty(ub, dtype=torch.uint8, device="cuda")
+        o = torch.empty(n, dtype=torch.uint8, device="cuda")
+        ins.append(t), privs.append(p), pubs.append(u), outs.append(o)
+        entries.append((plan, nonce, n, t, p, u))
+        rentries.append((plan, nonce, n, p, u, o))
+    fr.protect_batch(entries, key)
+    fr.recover_batch(rentries, key)
+    fr.sync_status()
+    for (n, W, L, nonce), d, p, u, o in zip(items, datas, privs, pubs, outs):
+        p_ref, u_ref = oracle.protect(d, W, L, KEY, nonce)
+        assert np.array_equal(p.cpu().numpy(), p_ref)
+        assert np.array_equal(u.cpu().numpy(), u_ref)
+        assert np.array_equal(o.cpu().numpy(), d)
+
+
+def test_batch_object_in_cuda_graph(fr, key):
+    items, datas = _mixed_items(40, seed=32)
+    plans = {}
+    entries, rentries, outs, refs = [], [], [], []
+    for (n, W, L, nonce), d in zip(items, datas):
+        plan = plans.setdefault((W, L), fr.Plan(W, L))
+        _, pb, ub = plan.sizes(n)
+        t = torch.from_numpy(d).cuda()
+        p = torch.empty(pb, dtype=torch.uint8, device="cuda")
+        u = torch.empty(ub, dtype=torch.uint8, device="cuda")
+        o = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        entries.append((plan, nonce, n, t, p, u))
+        rentries.append((plan, nonce, n, p, u, o))
+        outs.append(o)
+        refs.append(d)
+    bp = fr.Batch(entries, protect=True)
+    br = fr.Batch(rentries, protect=False)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        bp.run(key)
+        br.run(key)
+    for _ in range(3):
+        for o in outs:
+            o.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for o, d in zip(outs, refs):
+            assert np.array_equal(o.cpu().numpy(), d)
+    fr.sync_status()
