@@ -170,6 +170,32 @@ frag_status frag_batch_create_recover(frag_batch *out, const frag_ritem *items, 
 frag_status frag_batch_run(frag_batch batch, frag_key key, frag_stream stream);
 frag_status frag_batch_destroy(frag_batch batch);
 
+/* Batched protect that allocates nothing.  The thesis has no counterpart:
+ * this is a deployment aid.  Some callers may not call cudaMalloc at all --
+ * a plug-in whose host process owns every byte of device memory through its
+ * own pool, or a latency-critical path that cannot accept the implicit
+ * synchronisation of a driver allocation.  This call runs the same kernel as
+ * frag_protect_batch and gives byte-identical fragments, but keeps its work
+ * queue, job descriptors, round keys, AES tables and error word in one static
+ * device array of about 110 KiB that every GPU loading this library holds
+ * until the process exits; it calls no cudaMalloc, cudaFree or other
+ * allocating routine, and takes the raw 16-byte key instead of a frag_key.
+ * Limits and rules:
+ *   - at most FRAG_NOALLOC_MAX_ITEMS items per call; more is FRAG_EINVAL with
+ *     a message saying so;
+ *   - the first call on a device sets that device up synchronously (it looks
+ *     up the array's device address and copies the AES tables into it), so
+ *     make that first call before any stream capture;
+ *   - every call shares the one array and the array keeps the last call's
+ *     contents; the call clears what must start at zero (the queue head) on
+ *     the stream.  Calls whose work overlaps on the GPU (other streams, or no
+ *     ordering between them) race on the array and give wrong results: order
+ *     them on one stream.
+ * The caller still owns and passes every input and output buffer. */
+#define FRAG_NOALLOC_MAX_ITEMS 1024
+frag_status frag_protect_batch_noalloc(const frag_item *items, uint32_t count,
+                                       const uint8_t key[16], frag_stream stream);
+
 /* Thread-local text of the last error (always NUL-terminated).  Returns
  * FRAG_OK, or FRAG_EINVAL if buf is NULL or len is 0. */
 frag_status frag_get_error(char *buf, size_t len);

@@ -477,6 +477,18 @@ frag_status create_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, ui
 
 } // namespace
 
+// Accessors for other translation units of this library (no new behaviour).
+namespace frag {
+const uint32_t *host_aes_words() { return aes_host().words; }
+void host_expand_key(const uint8_t key[16], uint32_t rk[44]) { expand_key(key, rk); }
+frag_status plan_job(frag_plan plan, uint64_t nonce, uint64_t n, Job &j)
+{
+    return fill_job(plan, nonce, n, j);
+}
+frag_status report(frag_status st, const char *msg) { return fail(st, "%s", msg); }
+frag_status report_cuda(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+} // namespace frag
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

@@ -69,6 +69,10 @@ __host__ __device__ inline uint32_t halo_lo(uint32_t L) { return 2u << L; }
 __host__ __device__ inline uint32_t halo_hi_fwd(uint32_t L) { return 1u << L; }
 __host__ __device__ inline uint32_t halo_hi_inv(uint32_t L) { return 2u << L; }
 
+// host helpers (frag_api.cu)
+const uint32_t *host_aes_words();                             // kAesWords words
+void host_expand_key(const uint8_t key[16], uint32_t rk[44]); // FIPS-197 key schedule
+
 // kernels (tile_kernels.cu)
 size_t tile_smem_bytes(uint32_t tile_w, uint32_t tile_h, uint32_t L, bool fwd);
 cudaError_t launch_tiles(bool fwd, const Work &w, uint32_t grid, size_t smem, cudaStream_t stream);

@@ -1,0 +1,203 @@
+// noalloc.cu -- batched protect that allocates no memory.
+//
+// Some callers cannot call cudaMalloc: a plug-in whose host process owns all
+// device memory through its own pool (a framework's caching allocator, or a
+// reservation made once at start-up), or a latency-critical path that must not
+// take the implicit synchronisation and unbounded latency of a driver
+// allocation.  For them frag_protect_batch_noalloc runs the same persistent
+// work-queue kernel as frag_protect_batch, but everything that call keeps in
+// library-allocated device memory (AES tables, round keys, the error word, the
+// tile prefix, the job descriptors and the queue head) lives instead in one
+// file-scope static device array of fixed size, and the host-side staging
+// lives in static host arrays.  Neither this file nor the calls it makes
+// allocate host heap or device memory.
+#include "frag.h"
+#include "frag_internal.cuh"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+namespace frag {
+frag_status plan_job(frag_plan plan, uint64_t nonce, uint64_t n, Job &j);
+frag_status report(frag_status st, const char *msg);
+frag_status report_cuda(cudaError_t e, const char *what);
+} // namespace frag
+
+namespace {
+
+using frag::Job;
+using frag::Work;
+
+constexpr uint32_t kMaxItems = FRAG_NOALLOC_MAX_ITEMS;
+constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+// layout of the static scratch, in bytes
+constexpr size_t kOffHead = 0;                                   // queue head (8 B), error word (4 B)
+constexpr size_t kOffTables = 256;                               // AES T-tables + S-box words
+constexpr size_t kOffKeys = kOffTables + align256(sizeof(uint32_t) * frag::kAesWords);
+constexpr size_t kOffStart = kOffKeys + 256;                     // 44 round-key words
+constexpr size_t kOffJobs = kOffStart + align256(sizeof(uint64_t) * (kMaxItems + 1));
+constexpr size_t kScratchBytes = kOffJobs + align256(sizeof(Job) * kMaxItems);
+static_assert(kScratchBytes <= 160 * 1024, "scratch must stay modest");
+
+// The scratch.  Every GPU that loads the library holds it until the process
+// exits.  In host code its name is only a host-side stand-in for the symbol:
+// the device address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+struct DeviceSetup {
+    bool ready;
+    unsigned char *base; // device address of g_noalloc_scratch on this device
+    int sms;
+};
+DeviceSetup g_setup[kMaxDevices];
+std::mutex g_mu; // guards g_setup and the host staging below
+
+// host staging (static: filled under g_mu, copied to the device per call)
+Job h_jobs[kMaxItems];
+uint64_t h_start[kMaxItems + 1];
+uint64_t h_cost[kMaxItems];
+uint32_t h_order[kMaxItems];
+Job h_sorted[kMaxItems];
+uint32_t h_rk[44];
+
+// Once per device, with that device current: look up the scratch's device
+// address, copy the AES tables into it and zero the queue head and error
+// word.  This is synchronous, so the first call on a device must not be made
+// while its stream is being captured.
+frag_status setup_device(int dev, DeviceSetup **out)
+{
+    DeviceSetup &d = g_setup[dev];
+    if (!d.ready) {
+        unsigned char *base = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void **)&base, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return frag::report_cuda(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) !=
+            cudaSuccess)
+            return frag::report_cuda(e, "cudaDeviceGetAttribute");
+        if ((e = cudaMemcpy(base + kOffTables, frag::host_aes_words(),
+                            sizeof(uint32_t) * frag::kAesWords, cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return frag::report_cuda(e, "copy of AES tables into the no-alloc scratch");
+        if ((e = cudaMemset(base + kOffHead, 0, 256)) != cudaSuccess)
+            return frag::report_cuda(e, "clearing the no-alloc scratch");
+        d.base = base;
+        d.ready = true;
+    }
+    *out = &d;
+    return FRAG_OK;
+}
+
+} // namespace
+
+extern "C" frag_status frag_protect_batch_noalloc(const frag_item *items, uint32_t count,
+                                                  const uint8_t key[16], frag_stream stream)
+{
+    if (key == nullptr)
+        return frag::report(FRAG_EINVAL, "frag_protect_batch_noalloc: key is NULL");
+    if (count > kMaxItems) {
+        char msg[160];
+        std::snprintf(msg, sizeof(msg),
+                      "frag_protect_batch_noalloc: %u items exceed the static scratch limit of "
+                      "%u items per call",
+                      count, kMaxItems);
+        return frag::report(FRAG_EINVAL, msg);
+    }
+    if (count == 0)
+        return FRAG_OK;
+    if (items == nullptr)
+        return frag::report(FRAG_EINVAL, "frag_protect_batch_noalloc: items is NULL");
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return frag::report_cuda(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices)
+        return frag::report(FRAG_EUNSUPPORTED, "frag_protect_batch_noalloc: device index too high");
+
+    std::lock_guard<std::mutex> lock(g_mu);
+    DeviceSetup *d = nullptr;
+    frag_status st = setup_device(dev, &d);
+    if (st != FRAG_OK)
+        return st;
+
+    // descriptors, most costly first (same order rule as frag_protect_batch)
+    uint32_t nj = 0, max_tw = 0, max_th = 0, max_L = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        if (items[i].plan == nullptr)
+            return frag::report(FRAG_EINVAL, "frag_protect_batch_noalloc: an item has no plan");
+        if (items[i].nbytes == 0)
+            continue;
+        if (!items[i].d_in || !items[i].d_private || !items[i].d_public)
+            return frag::report(FRAG_EINVAL, "frag_protect_batch_noalloc: NULL buffer");
+        Job &j = h_jobs[nj];
+        if ((st = frag::plan_job(items[i].plan, items[i].nonce, items[i].nbytes, j)) != FRAG_OK)
+            return st;
+        j.in = (const uint8_t *)items[i].d_in;
+        j.priv = (uint8_t *)items[i].d_private;
+        j.pub = (uint8_t *)items[i].d_public;
+        h_cost[nj] = (uint64_t)j.tiles_x * j.tiles_y *
+                     frag::tile_smem_bytes(j.tile_w, j.tile_h, j.L, true);
+        h_order[nj] = nj;
+        max_tw = std::max(max_tw, j.tile_w);
+        max_th = std::max(max_th, j.tile_h);
+        max_L = std::max(max_L, j.L);
+        ++nj;
+    }
+    if (nj == 0)
+        return FRAG_OK;
+    // in-place sort (no temporary buffer); ties keep the caller's order
+    std::sort(h_order, h_order + nj, [](uint32_t a, uint32_t b) {
+        return h_cost[a] != h_cost[b] ? h_cost[a] > h_cost[b] : a < b;
+    });
+    h_start[0] = 0;
+    for (uint32_t k = 0; k < nj; ++k) {
+        h_sorted[k] = h_jobs[h_order[k]];
+        h_start[k + 1] = h_start[k] + (uint64_t)h_sorted[k].tiles_x * h_sorted[k].tiles_y;
+    }
+    frag::host_expand_key(key, h_rk);
+
+    // The scratch keeps whatever the previous call left there; what must
+    // start at zero (the queue head) is cleared on the stream.  Copies from
+    // these pageable host arrays return once the source has been staged.
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char *base = d->base;
+    e = cudaMemcpyAsync(base + kOffKeys, h_rk, sizeof(h_rk), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + kOffStart, h_start, sizeof(uint64_t) * (nj + 1),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + kOffJobs, h_sorted, sizeof(Job) * nj, cudaMemcpyHostToDevice,
+                            s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(base + kOffHead, 0, 16, s);
+    if (e != cudaSuccess)
+        return frag::report_cuda(e, "frag_protect_batch_noalloc: staging descriptors");
+
+    Work w;
+    std::memset(&w, 0, sizeof(w));
+    w.jobs = (const Job *)(base + kOffJobs);
+    w.tile_start = (const uint64_t *)(base + kOffStart);
+    w.njobs = nj;
+    w.total_tiles = h_start[nj];
+    w.queue = (unsigned long long *)(base + kOffHead);
+    w.err = (int *)(base + kOffHead + 8);
+    w.aes_tables = (const uint32_t *)(base + kOffTables);
+    w.round_keys = (const uint32_t *)(base + kOffKeys);
+
+    const size_t smem = frag::tile_smem_bytes(max_tw, max_th, max_L, true);
+    int occ = 0;
+    if ((e = frag::tile_occupancy(true, smem, &occ)) != cudaSuccess)
+        return frag::report_cuda(e, "frag_protect_batch_noalloc: occupancy query");
+    if (occ <= 0)
+        return frag::report(FRAG_EUNSUPPORTED, "frag_protect_batch_noalloc: tile too large");
+    const uint32_t grid =
+        (uint32_t)std::min<uint64_t>((uint64_t)d->sms * (uint64_t)occ, w.total_tiles);
+    if ((e = frag::launch_tiles(true, w, grid, smem, s)) != cudaSuccess)
+        return frag::report_cuda(e, "frag_protect_batch_noalloc: launch");
+    return FRAG_OK;
+}

@@ -1,0 +1,76 @@
+"""The allocation-free batched protect (frag_protect_batch_noalloc).
+
+It exists for callers that may not allocate device memory themselves or have
+the library do it: code whose process hands all device memory to one pool it
+does not control, or a latency-critical path that cannot take a driver
+allocation's implicit synchronisation.  Its fragments must be byte-identical
+to those of frag_protect_batch (integer work, so the tolerance is zero), on
+two calls in a row that share the static scratch.  This file is collected
+last so a failure here cannot hide the other tests' results.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1803_04880_b300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fr():
+    import paper_1803_04880_b300 as m
+    m.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    f = m.lib().frag_protect_batch_noalloc
+    f.argtypes = [ctypes.POINTER(m.frag_item), ctypes.c_uint32, ctypes.c_char_p,
+                  ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    return m
+
+
+def _buffers(fr, count, seed):
+    items = wl.c4_items(count=count, lo=100, hi=1 << 19, seed=seed)
+    plans, ins, ref, got = {}, [], [], []
+    for (n, W, L, nonce) in items:
+        plan = plans.setdefault((W, L), fr.Plan(W, L))
+        _, pb, ub = plan.sizes(n)
+        t = torch.from_numpy(wl.random_bytes(n, seed=seed * 7919 + nonce)).cuda()
+        mk = lambda k: torch.full((k,), 0x5A, dtype=torch.uint8, device="cuda")
+        ref.append((plan, nonce, n, t, mk(pb), mk(ub)))
+        got.append((plan, nonce, n, t, mk(pb), mk(ub)))
+    return plans, ref, got
+
+
+def _noalloc(fr, entries, key=wl.KEY):
+    arr = (fr.frag_item * len(entries))()
+    for i, (plan, nonce, n, t, p, u) in enumerate(entries):
+        arr[i] = fr.frag_item(plan.handle, nonce, n, t.data_ptr(), p.data_ptr(), u.data_ptr())
+    st = fr.lib().frag_protect_batch_noalloc(arr, len(entries), key,
+                                             torch.cuda.current_stream().cuda_stream)
+    return st
+
+
+def test_matches_allocating_batch_on_two_calls(fr):
+    key = fr.Key(wl.KEY)
+    for call, (count, seed) in enumerate(((40, 101), (25, 202))):
+        plans, ref, got = _buffers(fr, count, seed)
+        fr.protect_batch(ref, key)
+        st = _noalloc(fr, got)
+        assert st == fr.FRAG_OK, fr.last_error()
+        torch.cuda.synchronize()
+        fr.sync_status()
+        for (_, _, _, _, p0, u0), (_, _, _, _, p1, u1) in zip(ref, got):
+            assert torch.equal(p0, p1), "private fragment differs on call %d" % call
+            assert torch.equal(u0, u1), "public fragment differs on call %d" % call
+
+
+def test_rejects_more_items_than_the_scratch_holds(fr):
+    limit = 1024
+    arr = (fr.frag_item * (limit + 1))()
+    st = fr.lib().frag_protect_batch_noalloc(arr, limit + 1, wl.KEY, None)
+    assert st == fr.FRAG_EINVAL
+    assert "limit" in fr.last_error()
