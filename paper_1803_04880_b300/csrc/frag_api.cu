@@ -249,12 +249,21 @@ frag_status fill_job(frag_plan plan, uint64_t nonce, uint64_t n, Job &j)
     j.W = plan->width;
     j.H = (uint32_t)H;
     j.L = plan->levels;
-    j.tile_w = plan->tile_w;
-    j.tile_h = plan->tile_h;
+    if (plan->levels <= frag::kFastMaxLevels) {
+        j.path = 1;
+        j.tile_w = frag::kFastTile;
+        j.tile_h = frag::kFastTile;
+    } else {
+        j.path = 0;
+        j.tile_w = plan->tile_w;
+        j.tile_h = plan->tile_h;
+    }
     j.tiles_x = (j.W + j.tile_w - 1) / j.tile_w;
     j.tiles_y = (j.H + j.tile_h - 1) / j.tile_h;
     return FRAG_OK;
 }
+
+size_t job_smem(const Job &j, bool fwd) { return frag::job_smem_bytes(j, fwd); }
 
 void base_work(Work &w, DeviceState &d, const uint32_t *rk)
 {
@@ -278,7 +287,7 @@ frag_status launch_single(bool fwd, frag_plan plan, frag_key key, const Job &j, 
     base_work(w, *d, rk);
     w.single = j;
     w.total_tiles = (uint64_t)j.tiles_x * j.tiles_y;
-    const size_t smem = frag::tile_smem_bytes(j.tile_w, j.tile_h, j.L, fwd);
+    const size_t smem = job_smem(j, fwd);
     uint32_t grid = 0;
     if ((st = launch_shape(*d, fwd, smem, plan->ctas_per_sm, w.total_tiles, &grid)) != FRAG_OK)
         return st;
@@ -294,7 +303,8 @@ frag_status launch_single(bool fwd, frag_plan plan, frag_key key, const Job &j, 
 struct BatchHost {
     std::vector<Job> jobs;
     std::vector<uint64_t> tile_start;
-    uint32_t max_tw = 0, max_th = 0, max_L = 0, min_ctas = 0;
+    size_t smem = 0;
+    uint32_t min_ctas = 0;
 };
 
 // Order items from the most to the least costly (tiles x window area), so the
@@ -329,11 +339,9 @@ frag_status build_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uin
                 return fail(FRAG_EINVAL, "item %u has a NULL buffer", i);
         }
         const uint64_t tiles = (uint64_t)j.tiles_x * j.tiles_y;
-        const uint64_t cost = tiles * frag::tile_smem_bytes(j.tile_w, j.tile_h, j.L, fwd);
+        const uint64_t cost = tiles * (uint64_t)j.tile_w * j.tile_h;
         v.emplace_back(cost, j);
-        b.max_tw = std::max(b.max_tw, j.tile_w);
-        b.max_th = std::max(b.max_th, j.tile_h);
-        b.max_L = std::max(b.max_L, j.L);
+        b.smem = std::max(b.smem, job_smem(j, fwd));
         const uint32_t c = plan->ctas_per_sm;
         if (c != 0)
             b.min_ctas = b.min_ctas == 0 ? c : std::min(b.min_ctas, c);
@@ -406,7 +414,7 @@ frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, 
     w.njobs = (uint32_t)b.jobs.size();
     w.total_tiles = b.tile_start.back();
     w.queue = (unsigned long long *)(mem + off_queue);
-    const size_t smem = frag::tile_smem_bytes(b.max_tw, b.max_th, b.max_L, fwd);
+    const size_t smem = b.smem;
     uint32_t grid = 0;
     st = launch_shape(*d, fwd, smem, b.min_ctas, w.total_tiles, &grid);
     if (st == FRAG_OK) {
@@ -463,7 +471,7 @@ frag_status create_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, ui
         bt->work.njobs = (uint32_t)b.jobs.size();
         bt->work.total_tiles = b.tile_start.back();
         bt->work.queue = (unsigned long long *)(mem + off_queue);
-        bt->smem = frag::tile_smem_bytes(b.max_tw, b.max_th, b.max_L, fwd);
+        bt->smem = b.smem;
         if ((st = launch_shape(*d, fwd, bt->smem, b.min_ctas, bt->work.total_tiles, &bt->grid)) !=
             FRAG_OK) {
             cudaFree(bt->d_mem);

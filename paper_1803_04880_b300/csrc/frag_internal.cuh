@@ -29,7 +29,7 @@ struct Job {
     uint32_t tile_h;  // owned tile height (multiple of 2^L)
     uint32_t tiles_x;
     uint32_t tiles_y;
-    uint32_t pad_;
+    uint32_t path;    // 0: generic tile body, 1: register-streaming body (L <= 3)
 };
 
 // Launch-wide description of where jobs and tiles come from.
@@ -74,7 +74,11 @@ const uint32_t *host_aes_words();                             // kAesWords words
 void host_expand_key(const uint8_t key[16], uint32_t rk[44]); // FIPS-197 key schedule
 
 // kernels (tile_kernels.cu)
+constexpr uint32_t kFastTile = 224;   // owned tile side of the register-streaming body
+constexpr uint32_t kFastMaxLevels = 3;
 size_t tile_smem_bytes(uint32_t tile_w, uint32_t tile_h, uint32_t L, bool fwd);
+size_t fast_smem_bytes(bool fwd);
+size_t job_smem_bytes(const Job &j, bool fwd); // dynamic shared memory one job's tiles need
 cudaError_t launch_tiles(bool fwd, const Work &w, uint32_t grid, size_t smem, cudaStream_t stream);
 cudaError_t tile_occupancy(bool fwd, size_t smem, int *blocks_per_sm);
 

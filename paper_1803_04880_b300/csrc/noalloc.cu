@@ -126,7 +126,8 @@ extern "C" frag_status frag_protect_batch_noalloc(const frag_item *items, uint32
         return st;
 
     // descriptors, most costly first (same order rule as frag_protect_batch)
-    uint32_t nj = 0, max_tw = 0, max_th = 0, max_L = 0;
+    uint32_t nj = 0;
+    size_t smem = 0;
     for (uint32_t i = 0; i < count; ++i) {
         if (items[i].plan == nullptr)
             return frag::report(FRAG_EINVAL, "frag_protect_batch_noalloc: an item has no plan");
@@ -140,12 +141,9 @@ extern "C" frag_status frag_protect_batch_noalloc(const frag_item *items, uint32
         j.in = (const uint8_t *)items[i].d_in;
         j.priv = (uint8_t *)items[i].d_private;
         j.pub = (uint8_t *)items[i].d_public;
-        h_cost[nj] = (uint64_t)j.tiles_x * j.tiles_y *
-                     frag::tile_smem_bytes(j.tile_w, j.tile_h, j.L, true);
+        h_cost[nj] = (uint64_t)j.tiles_x * j.tiles_y * (uint64_t)j.tile_w * j.tile_h;
         h_order[nj] = nj;
-        max_tw = std::max(max_tw, j.tile_w);
-        max_th = std::max(max_th, j.tile_h);
-        max_L = std::max(max_L, j.L);
+        smem = std::max(smem, frag::job_smem_bytes(j, true));
         ++nj;
     }
     if (nj == 0)
@@ -189,7 +187,6 @@ extern "C" frag_status frag_protect_batch_noalloc(const frag_item *items, uint32
     w.aes_tables = (const uint32_t *)(base + kOffTables);
     w.round_keys = (const uint32_t *)(base + kOffKeys);
 
-    const size_t smem = frag::tile_smem_bytes(max_tw, max_th, max_L, true);
     int occ = 0;
     if ((e = frag::tile_occupancy(true, smem, &occ)) != cudaSuccess)
         return frag::report_cuda(e, "frag_protect_batch_noalloc: occupancy query");

@@ -66,6 +66,12 @@ __device__ __forceinline__ uint32_t ks_byte(const uint32_t ks[4], int k)
     return (ks[k >> 2] >> (24 - 8 * (k & 3))) & 255u;
 }
 
+} // namespace frag
+
+#include "fast_tiles.cuh"
+
+namespace frag {
+
 // Geometry of one tile window.  Lattice index i of level l-1 sits at level-0
 // coordinate i << (l-1); the window origin is a multiple of 2^L (or 0), so
 // every lattice starts on an even index.
@@ -385,10 +391,29 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(Work w)
             break;
         }
         const uint32_t tx = (uint32_t)(local % j.tiles_x), ty = (uint32_t)(local / j.tiles_x);
-        if (FWD)
+        if (j.path == 1) {
+            if (FWD) {
+                fast::FwdSmem &fs = *reinterpret_cast<fast::FwdSmem *>(S);
+                if (j.L == 1)
+                    fast::fwd_tile_fast<1>(j, tx, ty, fs, aes);
+                else if (j.L == 2)
+                    fast::fwd_tile_fast<2>(j, tx, ty, fs, aes);
+                else
+                    fast::fwd_tile_fast<3>(j, tx, ty, fs, aes);
+            } else {
+                fast::InvSmem &is = *reinterpret_cast<fast::InvSmem *>(S);
+                if (j.L == 1)
+                    fast::inv_tile_fast<1>(j, tx, ty, is, aes);
+                else if (j.L == 2)
+                    fast::inv_tile_fast<2>(j, tx, ty, is, aes);
+                else
+                    fast::inv_tile_fast<3>(j, tx, ty, is, aes);
+            }
+        } else if (FWD) {
             fwd_tile(j, tx, ty, S, aes, w.err);
-        else
+        } else {
             inv_tile(j, tx, ty, S, aes, w.err);
+        }
         __syncthreads();
         if (w.queue == nullptr)
             t += gridDim.x;
@@ -400,6 +425,16 @@ size_t tile_smem_bytes(uint32_t tile_w, uint32_t tile_h, uint32_t L, bool fwd)
     const uint32_t hh = fwd ? halo_hi_fwd(L) : halo_hi_inv(L);
     const size_t ew = tile_w + halo_lo(L) + hh, eh = tile_h + halo_lo(L) + hh;
     return sizeof(AesSmem) + ew * eh * sizeof(int32_t);
+}
+
+size_t fast_smem_bytes(bool fwd)
+{
+    return sizeof(AesSmem) + (fwd ? sizeof(fast::FwdSmem) : sizeof(fast::InvSmem));
+}
+
+size_t job_smem_bytes(const Job &j, bool fwd)
+{
+    return j.path == 1 ? fast_smem_bytes(fwd) : tile_smem_bytes(j.tile_w, j.tile_h, j.L, fwd);
 }
 
 static const void *kernel_fn(bool fwd)

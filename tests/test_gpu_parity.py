@@ -74,6 +74,10 @@ SWEEP = [
     (200000, 96, 2, None), (300000, 160, 5, None), (131072, 512, 3, (32, 16, 0)),
     (131072, 512, 3, (128, 32, 1)), (250000, 1000, 3, (16, 16, 0)), (262144, 256, 4, (256, 16, 0)),
     (99999, 32, 5, (32, 32, 0)), (1 << 20, 2048, 2, (64, 128, 0)),
+    # around the 224-pixel tile of the register-streaming path
+    (224 * 230, 224, 3, None), (448 * 449 + 3, 448, 2, None), (240 * 500, 240, 3, None),
+    (672 * 225 + 100, 672, 1, None), (16 * 1000, 16, 3, None), (8 * 7, 8, 3, None),
+    (232 * 232, 232, 3, None), (456 * 456 - 1, 456, 3, None), (904 * 220, 904, 2, None),
 ]
 
 
