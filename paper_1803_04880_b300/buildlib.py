@@ -29,7 +29,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, s) for s in SOURCES] + HEADERS + [__file__]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + HEADERS + [__file__]
     return any(os.path.getmtime(p) > t for p in deps)
 
 

@@ -1,269 +1,409 @@
-// fast_tiles.cuh -- register-streaming tile bodies for buffers of up to three
-// levels (included by tile_kernels.cu).
+// fast_tiles.cuh -- tile bodies for buffers of up to three levels, built from
+// a row pass and a packed-pair column pass (included by tile_kernels.cu).
 //
-// Forward: a CTA stages a 248 x 248 byte window (the 224 x 224 owned tile
-// plus 16 pixels of lifting halo above / left and 8 below / right) in shared
-// memory.  For each level, each of 248 work items owns G column pairs and S
-// row pairs of that level's input window: it lifts every row it needs on the
-// fly (Eq. 5.1 then Eq. 5.2 along the row, rows before columns as in
-// Sec. 5.2.2) and streams the column lifting down its rows in registers.
-// Detail coefficients of owned positions go straight from registers to HBM;
-// only the compact LL_l goes back to shared memory as the next level's input.
+// A CTA of 512 threads owns a 256 x 256 tile; its window adds 16 pixels of
+// lifting halo on every side (288 x 288).  Per level:
 //
-// Inverse: the mirror image.  A CTA owns a 224 x 224 output tile with a
-// 16-pixel halo on each side (256 x 256 window).  For each level from the
-// coarsest down, each of 256 work items streams the column inverse (undo
-// Eq. 5.2, then Eq. 5.1) down G + 1 low and G + 2 high columns, reading LL_l
-// from shared memory and the detail bands from HBM, then undoes the row
-// lifting of the two rows it just produced in registers and writes LL_{l-1}
-// (shared memory) or the recovered bytes (HBM).
+//   row pass     every row of the level's input window is lifted once along
+//                the row (Eq. 5.1 predict, Eq. 5.2 update; rows come first,
+//                Sec. 5.2.2) by scalar code; the low-pass and high-pass
+//                results go to shared memory as two halves of the row,
+//                packed two columns per 32-bit word;
+//   column pass  each work item streams down a strip of packed words and
+//                lifts the columns two at a time with 32-bit integer ops;
+//                detail bands go straight to HBM, LL_l stays in shared
+//                memory as the next level's input.
 //
-// Window positions outside the image hold garbage that is never part of the
-// dependency cone of an owned output; the symmetric extension is applied
-// exactly at the image borders.  Every shared-memory array is padded so that
-// neighbour reads at the window edge stay inside it.
+// Packed pairs: each 16-bit half holds v + 0x4000 with |v| < 2^14.  Sums of
+// two halves stay below 2^16, so floor((a + b) / 2) of both halves is
+// ((A + B) >> 1) & 0x7fff7fff and floor((a + b + 2) / 4) is
+// ((A + B + 0x00020002) >> 2) & 0x3fff3fff, each exact per half.  Every value
+// the transform produces from bytes (or from valid fragments) is far inside
+// that range; window halo positions are lifted from bounded data as well.
+//
+// The inverse mirrors this: a column-inverse pass (undo Eq. 5.2, then
+// Eq. 5.1, two columns per op, details read from HBM) writes the row-lifted
+// rows, and a scalar row-inverse pass writes LL_{l-1} or the output bytes.
+//
+// Window positions outside the image or outside the dependency cone of the
+// owned tile compute values that are never stored; the symmetric extension is
+// applied exactly at the image borders (Eq. 5.1's x_ext).
 #pragma once
 
 namespace frag {
 namespace fast {
 
-constexpr int kT = 224;                // owned tile side (pixels), multiple of 32
-constexpr int kFH = 16;                // forward halo above / left
-constexpr int kFW = kT + kFH + 8;      // forward window side: 248
-constexpr int kBP = 256;               // byte window pitch
-constexpr int kIH = 16;                // inverse halo on every side
-constexpr int kIW = kT + 2 * kIH;      // inverse window side: 256
-constexpr int kItemsF = 31 * 8;        // forward work items per level
-constexpr int kItemsI = 32 * 8;        // inverse work items per level
+constexpr int kT = 256;        // owned tile side (pixels)
+constexpr int kH = 16;         // halo on every side
+constexpr int kW = kT + 2 * kH; // window side at level 0: 288
+__host__ __device__ constexpr int side(int l) { return kW >> l; } // 288, 144, 72, 36
 
-// padded compact int16 arrays: pitch = side + 4, element (r, c) at
-// [(r + 1) * pitch + c + 2], one spare row above and below
-__host__ __device__ constexpr int pitch_of(int side) { return side + 4; }
-__host__ __device__ constexpr int words_of(int side) { return pitch_of(side) * (side + 2); }
+constexpr uint32_t kB2 = 0x40004000u; // bias of both halves of a packed pair
 
-struct FwdSmem {
-    uint8_t front[16];               // absorbs the (garbage) reads left of column 0
-    uint8_t bytes[(kFW + 1) * kBP];  // the byte window (+1 spare row)
-    int16_t a1[words_of(kFW / 2)];
-    int16_t a2[words_of(kFW / 4)];
-    int16_t a3[words_of(kFW / 8)];
+// shared memory (words): region X holds R_l (row-lifted rows of level l:
+// side(l-1) rows x side(l) words, low half then high half) and A2 / A3; A1
+// (LL_1, side(1) rows x side(1)/2 words) has its own array
+constexpr int kXWords = side(1) * side(0);                    // 41472 (= R_1)
+constexpr int kA1Words = side(1) * side(1) / 2;               // 10368
+constexpr int kA2Off = side(1) * side(2);                     // after R_2: 10368
+constexpr int kA3Off = kA2Off + side(2) * side(2) / 2;        // 12960
+static_assert(kA3Off + side(3) * side(3) / 2 <= kXWords, "A2/A3 must fit in region X");
+static_assert(side(2) * side(3) <= kA2Off, "R_3 must not reach A2");
+
+struct Smem {
+    uint32_t x[kXWords];
+    uint32_t a1[kA1Words];
 };
 
-struct InvSmem {
-    int16_t a0[words_of(kIW / 2)]; // LL_1 window (reconstructed from level 2)
-    int16_t a1[words_of(kIW / 4)]; // LL_2 window
-    int16_t a2[words_of(kIW / 8)]; // LL_3 window (decrypted private fragment)
-};
-
-template <typename T> __device__ __forceinline__ int ld_val(const T *p, int i) { return (int)p[i]; }
-
-__device__ __forceinline__ int16_t *cell(int16_t *a, int side, int r, int c)
+__device__ __forceinline__ uint32_t *a_arr(Smem &sm, int l)
 {
-    return a + (r + 1) * pitch_of(side) + c + 2;
+    return l == 1 ? sm.a1 : (l == 2 ? sm.x + kA2Off : sm.x + kA3Off);
 }
 
-// store G int16 values at dst (any alignment), vectorised when aligned
-template <int G> __device__ __forceinline__ void store_i16(uint8_t *dst, const int (&v)[G])
+__device__ __forceinline__ uint32_t pack2(int lo, int hi)
 {
-    const uintptr_t a = (uintptr_t)dst;
-    if (G == 4 && (a & 7) == 0) {
-        uint2 w;
-        w.x = ((uint32_t)v[0] & 0xffffu) | ((uint32_t)v[1] << 16);
-        w.y = ((uint32_t)v[2 % G] & 0xffffu) | ((uint32_t)v[3 % G] << 16);
-        *reinterpret_cast<uint2 *>(dst) = w;
-    } else if (G == 2 && (a & 3) == 0) {
-        *reinterpret_cast<uint32_t *>(dst) = ((uint32_t)v[0] & 0xffffu) | ((uint32_t)v[1 % G] << 16);
-    } else if (G == 1 && (a & 1) == 0) {
-        *reinterpret_cast<int16_t *>(dst) = (int16_t)v[0];
+    return __byte_perm((uint32_t)lo, (uint32_t)hi, 0x5410);
+}
+
+// floor((a + b) / 2) of both halves (biased in, biased out)
+__device__ __forceinline__ uint32_t pavg(uint32_t a, uint32_t b)
+{
+    return ((a + b) >> 1) & 0x7fff7fffu;
+}
+
+// floor((a + b + 2) / 4) + 0x2000 of both halves (biased in)
+__device__ __forceinline__ uint32_t pq4(uint32_t a, uint32_t b)
+{
+    return ((a + b + 0x00020002u) >> 2) & 0x3fff3fffu;
+}
+
+// packed pair (biased) -> two int16 little-endian values
+__device__ __forceinline__ uint32_t to_i16x2(uint32_t w) { return (w + kB2) ^ 0x80008000u; }
+// two int16 -> packed pair (biased)
+__device__ __forceinline__ uint32_t from_i16x2(uint32_t w) { return (w ^ 0x80008000u) - kB2; }
+
+struct Geo {
+    int W, H;     // level-0 image
+    int C0, R0;   // owned tile origin
+    int wc0, wr0; // window origin = C0 - 16, R0 - 16 (multiples of 16, may be < 0)
+    uint32_t L;   // levels of the buffer (band order)
+};
+
+__device__ __forceinline__ Geo make_geo(const Job &j, uint32_t tx, uint32_t ty)
+{
+    Geo g;
+    g.W = (int)j.W;
+    g.H = (int)j.H;
+    g.C0 = (int)tx * kT;
+    g.R0 = (int)ty * kT;
+    g.wc0 = g.C0 - kH;
+    g.wr0 = g.R0 - kH;
+    g.L = j.L;
+    return g;
+}
+
+// Store N int16 values (given as N/2 packed biased pairs) to dst, vectorised
+// when the whole run is owned and aligned.
+template <int NW>
+__device__ __forceinline__ void store_pairs(uint8_t *band, int Wl, int y, int x0, int ox0, int ox1,
+                                            const uint32_t (&w)[NW])
+{
+    uint8_t *dst = band + 2ull * ((uint64_t)y * (uint64_t)Wl + (uint64_t)x0);
+    uint32_t v[NW];
+#pragma unroll
+    for (int i = 0; i < NW; ++i)
+        v[i] = to_i16x2(w[i]);
+    const bool all = x0 >= ox0 && x0 + 2 * NW <= ox1;
+    if (all && NW == 4 && ((uintptr_t)dst & 15u) == 0) {
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(v[0], v[1 % NW], v[2 % NW], v[3 % NW]);
+    } else if (all && NW == 2 && ((uintptr_t)dst & 7u) == 0) {
+        *reinterpret_cast<uint2 *>(dst) = make_uint2(v[0], v[1 % NW]);
     } else {
 #pragma unroll
-        for (int i = 0; i < G; ++i) {
-            dst[2 * i] = (uint8_t)(v[i] & 255);
-            dst[2 * i + 1] = (uint8_t)((v[i] >> 8) & 255);
+        for (int i = 0; i < 2 * NW; ++i) {
+            const int x = x0 + i;
+            if (x < ox0 || x >= ox1)
+                continue;
+            const uint32_t h = (v[i >> 1] >> (16 * (i & 1))) & 0xffffu;
+            dst[2 * i] = (uint8_t)(h & 255u);
+            dst[2 * i + 1] = (uint8_t)(h >> 8);
+        }
+    }
+}
+
+// Load N = 2 * NW int16 values of a band row (0 outside the band) as packed
+// biased pairs.
+template <int NW>
+__device__ __forceinline__ void load_pairs(const uint8_t *band, int Hl, int Wl, int y, int x0,
+                                           uint32_t (&w)[NW])
+{
+    if (y < 0 || y >= Hl) {
+#pragma unroll
+        for (int i = 0; i < NW; ++i)
+            w[i] = kB2;
+        return;
+    }
+    const uint8_t *src = band + 2ull * ((uint64_t)y * (uint64_t)Wl + (uint64_t)x0);
+    const bool inside = x0 >= 0 && x0 + 2 * NW <= Wl;
+    if (inside && NW == 4 && ((uintptr_t)src & 15u) == 0) {
+        const uint4 t = __ldg(reinterpret_cast<const uint4 *>(src));
+        const uint32_t a[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int i = 0; i < NW; ++i)
+            w[i] = from_i16x2(a[i]);
+    } else if (inside && NW == 2 && ((uintptr_t)src & 7u) == 0) {
+        const uint2 t = __ldg(reinterpret_cast<const uint2 *>(src));
+        const uint32_t a[2] = {t.x, t.y};
+#pragma unroll
+        for (int i = 0; i < NW; ++i)
+            w[i] = from_i16x2(a[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+            uint32_t h[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int x = x0 + 2 * i + k;
+                h[k] = (x >= 0 && x < Wl)
+                           ? ((uint32_t)__ldg(src + 4 * i + 2 * k) |
+                              ((uint32_t)__ldg(src + 4 * i + 2 * k + 1) << 8))
+                           : 0u;
+            }
+            w[i] = from_i16x2(h[0] | (h[1] << 16));
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// forward
+// row passes (scalar): CV input values per item
 // ---------------------------------------------------------------------------
 
-// Row lifting of G pairs starting at pair p0 of one window row (Eq. 5.1, 5.2).
-// ic = image column of the row's sample 2 * p0; Wm = image row length.
-template <int G, typename T>
-__device__ __forceinline__ void row_lift(const T *row, int p0, int ic, int Wm, int (&s)[G],
-                                         int (&d)[G])
+// Lift one run: x[0..CV+2] are the samples at window columns c-2 .. c+CV,
+// ic the image column of sample c (even).  Returns CV/2 s and d values.
+template <int CV>
+__device__ __forceinline__ void lift_run(const int (&x)[CV + 3], int ic, int Wm, int (&s)[CV / 2],
+                                         int (&d)[CV / 2])
 {
-    int x[2 * G + 3];
-#pragma unroll
-    for (int t = 0; t < 2 * G + 3; ++t)
-        x[t] = ld_val(row, 2 * p0 - 2 + t);
     int dm1 = x[1] - ((x[0] + x[2]) >> 1);
 #pragma unroll
-    for (int i = 0; i < G; ++i) {
+    for (int i = 0; i < CV / 2; ++i) {
         const int xr = (ic + 2 * i + 2 == Wm) ? x[2 * i + 2] : x[2 * i + 4]; // x[m] = x[m-2]
         d[i] = x[2 * i + 3] - ((x[2 * i + 2] + xr) >> 1);
     }
-    if (ic == 0)
-        dm1 = d[0]; // d[-1] = d[0]
 #pragma unroll
-    for (int i = 0; i < G; ++i)
-        s[i] = x[2 * i + 2] + (((i == 0 ? dm1 : d[i - 1]) + d[i] + 2) >> 2);
+    for (int i = 0; i < CV / 2; ++i) {
+        // the image's first column may fall anywhere in the run: d[-1] = d[0]
+        const int dl = (ic + 2 * i == 0) ? d[i] : (i == 0 ? dm1 : d[i - 1]);
+        s[i] = x[2 * i + 2] + ((dl + d[i] + 2) >> 2);
+    }
 }
 
-struct FwdGeo {
-    int W, H;        // level-0 image
-    int C0, R0;      // owned tile origin (level 0)
-    int wc0, wr0;    // window origin (level 0), multiples of 16, may be negative
-    uint8_t *pub;
-    uint32_t L;      // total levels of the buffer (band order)
-};
-
-// One forward level l (1..3) over the window.  `in` is the level-(l-1)
-// window (bytes at l = 1), `out` the compact LL_l window.
-template <int l, typename T>
-__device__ void fwd_level(const T *in, int in_pitch, int16_t *out, const FwdGeo &g)
+// level-1 row pass: bytes from HBM -> R_1 (low words then high words per row)
+__device__ void fwd_row_pass_bytes(const Job &j, const Geo &g, uint32_t *R)
 {
-    constexpr int G = 4 >> (l - 1);
-    constexpr int S = 16 >> (l - 1);
-    constexpr int EIN = kFW >> (l - 1); // input window side
-    constexpr int PAIRS = EIN / 2;      // = output window side
-    constexpr int GROUPS = PAIRS / G;   // 31
-    constexpr int SEGS = (PAIRS + S - 1) / S;
-    const int wc = g.wc0 >> (l - 1), wr = g.wr0 >> (l - 1); // level l-1 window origin
-    const int Wm = g.W >> (l - 1), Hm = g.H >> (l - 1);
+    constexpr int CV = 16, CH = kW / CV; // 18 chunks per window row
+    constexpr int RW = side(1);          // words per R_1 row (72 low + 72 high)
+    const bool vec = ((j.W & 15u) == 0) && (((uintptr_t)j.in & 15u) == 0);
+    for (int it = threadIdx.x; it < kW * CH; it += blockDim.x) {
+        const int r = it / CH, k = it - r * CH;
+        const int Rr = g.wr0 + r, c = g.wc0 + CV * k;
+        int x[CV + 3];
+        if (Rr >= 0 && Rr < g.H) {
+            const uint64_t base = (uint64_t)Rr * (uint64_t)g.W;
+            if (vec && c >= 4 && c + CV + 4 <= g.W && base + (uint64_t)c + CV + 4 <= j.n) {
+                const uint8_t *p = j.in + base + c;
+                const uint4 m = __ldg(reinterpret_cast<const uint4 *>(p));
+                const uint32_t lw = __ldg(reinterpret_cast<const uint32_t *>(p - 4));
+                const uint32_t rw = __ldg(reinterpret_cast<const uint32_t *>(p + CV));
+                x[0] = (int)((lw >> 16) & 255u);
+                x[1] = (int)(lw >> 24);
+                const uint32_t mm[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+                for (int t = 0; t < CV; ++t)
+                    x[2 + t] = (int)((mm[t >> 2] >> (8 * (t & 3))) & 255u);
+                x[CV + 2] = (int)(rw & 255u);
+            } else {
+#pragma unroll
+                for (int t = 0; t < CV + 3; ++t) {
+                    const int cc = c - 2 + t;
+                    x[t] = (cc >= 0 && cc < g.W && base + (uint64_t)cc < j.n)
+                               ? (int)__ldg(j.in + base + (uint64_t)cc)
+                               : 0;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < CV + 3; ++t)
+                x[t] = 0;
+        }
+        int s[CV / 2], d[CV / 2];
+        lift_run<CV>(x, c, g.W, s, d);
+        uint32_t *row = R + r * RW;
+        uint4 lo, hi;
+        // unbiased values: pack as int16 pairs, then move to the biased form
+        lo.x = from_i16x2(pack2(s[0], s[1]));
+        lo.y = from_i16x2(pack2(s[2], s[3]));
+        lo.z = from_i16x2(pack2(s[4], s[5]));
+        lo.w = from_i16x2(pack2(s[6], s[7]));
+        hi.x = from_i16x2(pack2(d[0], d[1]));
+        hi.y = from_i16x2(pack2(d[2], d[3]));
+        hi.z = from_i16x2(pack2(d[4], d[5]));
+        hi.w = from_i16x2(pack2(d[6], d[7]));
+        *reinterpret_cast<uint4 *>(row + 4 * k) = lo;
+        *reinterpret_cast<uint4 *>(row + RW / 2 + 4 * k) = hi;
+    }
+}
+
+// level-l row pass (l >= 2): A_{l-1} (packed, biased) -> R_l
+template <int l>
+__device__ void fwd_row_pass_packed(const Geo &g, const uint32_t *A, uint32_t *R)
+{
+    constexpr int CV = l == 2 ? 16 : 8;  // values per item
+    constexpr int NW = CV / 2;           // input words per item
+    constexpr int IN = side(l - 1);      // values per input row (= rows)
+    constexpr int AW = IN / 2;           // words per input row
+    constexpr int CH = IN / CV;          // 9
+    constexpr int RW = side(l);          // words per R_l row
+    const int wc = g.wc0 >> (l - 1), Wm = g.W >> (l - 1);
+    for (int it = threadIdx.x; it < IN * CH; it += blockDim.x) {
+        const int r = it / CH, k = it - r * CH;
+        const uint32_t *arow = A + r * AW;
+        const int w0 = k * NW;
+        uint32_t m[NW];
+#pragma unroll
+        for (int i = 0; i < NW; i += 4) {
+            if (NW - i >= 4) {
+                const uint4 t = *reinterpret_cast<const uint4 *>(arow + w0 + i);
+                m[i] = t.x;
+                m[(i + 1) % NW] = t.y;
+                m[(i + 2) % NW] = t.z;
+                m[(i + 3) % NW] = t.w;
+            }
+        }
+        const uint32_t lw = arow[max(w0 - 1, 0)];
+        const uint32_t rw = arow[min(w0 + NW, AW - 1)];
+        int x[CV + 3];
+        x[0] = (int)(lw & 0xffffu);
+        x[1] = (int)(lw >> 16);
+#pragma unroll
+        for (int t = 0; t < NW; ++t) {
+            x[2 + 2 * t] = (int)(m[t] & 0xffffu);
+            x[3 + 2 * t] = (int)(m[t] >> 16);
+        }
+        x[CV + 2] = (int)(rw & 0xffffu);
+        int s[CV / 2], d[CV / 2];
+        lift_run<CV>(x, wc + CV * k, Wm, s, d); // s stays biased, d comes out unbiased
+        uint32_t *row = R + r * RW;
+#pragma unroll
+        for (int i = 0; i < CV / 4; ++i) {
+            row[(CV / 4) * k + i] = pack2(s[2 * i], s[2 * i + 1]);
+            row[RW / 2 + (CV / 4) * k + i] = from_i16x2(pack2(d[2 * i], d[2 * i + 1]));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// forward column pass (packed pairs)
+// ---------------------------------------------------------------------------
+template <int l>
+__device__ void fwd_col_pass(const Geo &g, const uint32_t *R, uint32_t *A, uint8_t *pub)
+{
+    constexpr int CW = l == 3 ? 2 : 4;          // words per item
+    constexpr int S = l == 1 ? 12 : (l == 2 ? 4 : 2);
+    constexpr int RW = side(l);                 // words per R_l row
+    constexpr int ROWS = side(l - 1);           // R_l rows
+    constexpr int PAIRS = side(l);              // row pairs
+    constexpr int CH = RW / CW;
+    constexpr int SEGS = PAIRS / S;
+    static_assert(PAIRS % S == 0 && RW % CW == 0, "partition");
+    const int wr = g.wr0 >> (l - 1), Hm = g.H >> (l - 1);
+    const int wcl = g.wc0 >> l, wrl = g.wr0 >> l;
     const int Wl = g.W >> l;
     const int ox0 = g.C0 >> l, ox1 = min(g.C0 + kT, g.W) >> l;
     const int oy0 = g.R0 >> l, oy1 = min(g.R0 + kT, g.H) >> l;
-    uint8_t *band_hl = g.pub + band_offset(g.H, g.W, g.L, l, 0);
-    uint8_t *band_lh = g.pub + band_offset(g.H, g.W, g.L, l, 1);
-    uint8_t *band_hh = g.pub + band_offset(g.H, g.W, g.L, l, 2);
+    uint8_t *band_hl = pub + band_offset(g.H, g.W, g.L, l, 0);
+    uint8_t *band_lh = pub + band_offset(g.H, g.W, g.L, l, 1);
+    uint8_t *band_hh = pub + band_offset(g.H, g.W, g.L, l, 2);
 
-    for (int it = threadIdx.x; it < GROUPS * SEGS; it += blockDim.x) {
-        const int gx = it % GROUPS, sy = it / GROUPS;
-        const int p0 = gx * G, q0 = sy * S, q1 = min(q0 + S, PAIRS);
-        const int ic = wc + 2 * p0;
-        auto lift = [&](int row, int (&s)[G], int (&d)[G]) {
-            row = min(max(row, 0), EIN - 1);
-            row_lift<G>(in + row * in_pitch, p0, ic, Wm, s, d);
+    for (int it = threadIdx.x; it < CH * SEGS; it += blockDim.x) {
+        const int c = it % CH, sy = it / CH;
+        const int w0 = c * CW;
+        const bool high = w0 >= RW / 2;
+        const int x0 = wcl + 2 * (w0 - (high ? RW / 2 : 0)); // level-l image column
+        const int q0 = sy * S;
+        auto rowv = [&](int r, uint32_t (&v)[CW]) {
+            r = min(max(r, 0), ROWS - 1);
+            const uint32_t *p = R + r * RW + w0;
+            if (CW == 4) {
+                const uint4 t = *reinterpret_cast<const uint4 *>(p);
+                v[0] = t.x;
+                v[1 % CW] = t.y;
+                v[2 % CW] = t.z;
+                v[3 % CW] = t.w;
+            } else {
+                const uint2 t = *reinterpret_cast<const uint2 *>(p);
+                v[0] = t.x;
+                v[1 % CW] = t.y;
+            }
         };
-        int e0s[G], e0d[G], os[G], od[G], e1s[G], e1d[G], dps[G], dpd[G];
-        lift(2 * q0, e0s, e0d);
+        uint32_t e0[CW], o[CW], e1[CW], dp[CW], dv[CW], sv[CW];
+        rowv(2 * q0, e0);
         {
-            int as[G], ad[G], bs[G], bd[G];
-            lift(2 * q0 - 2, as, ad);
-            lift(2 * q0 - 1, bs, bd);
+            uint32_t a[CW];
+            rowv(2 * q0 - 2, a);
+            rowv(2 * q0 - 1, o);
 #pragma unroll
-            for (int i = 0; i < G; ++i) {
-                dps[i] = bs[i] - ((as[i] + e0s[i]) >> 1);
-                dpd[i] = bd[i] - ((ad[i] + e0d[i]) >> 1);
-            }
+            for (int i = 0; i < CW; ++i)
+                dp[i] = o[i] - pavg(a[i], e0[i]) + kB2;
         }
-        const int x0 = (wc >> 1) + p0; // level-l image column of pair p0
-        const bool cols_owned = x0 >= ox0 && x0 + G <= ox1;
-        for (int q = q0; q < q1; ++q) {
-            lift(2 * q + 1, os, od);
-            if (wr + 2 * q + 2 == Hm) { // x[m] = x[m-2] at the bottom border
+        for (int q = q0; q < q0 + S; ++q) {
+            rowv(2 * q + 1, o);
+            if (wr + 2 * q + 2 == Hm) { // x[m] = x[m-2]
 #pragma unroll
-                for (int i = 0; i < G; ++i) {
-                    e1s[i] = e0s[i];
-                    e1d[i] = e0d[i];
-                }
+                for (int i = 0; i < CW; ++i)
+                    e1[i] = e0[i];
             } else {
-                lift(2 * q + 2, e1s, e1d);
-            }
-            int dvs[G], dvd[G], svs[G], svd[G];
-#pragma unroll
-            for (int i = 0; i < G; ++i) {
-                dvs[i] = os[i] - ((e0s[i] + e1s[i]) >> 1);
-                dvd[i] = od[i] - ((e0d[i] + e1d[i]) >> 1);
-            }
-            if (wr + 2 * q == 0) { // d[-1] = d[0] at the top border
-#pragma unroll
-                for (int i = 0; i < G; ++i) {
-                    dps[i] = dvs[i];
-                    dpd[i] = dvd[i];
-                }
+                rowv(2 * q + 2, e1);
             }
 #pragma unroll
-            for (int i = 0; i < G; ++i) {
-                svs[i] = e0s[i] + ((dps[i] + dvs[i] + 2) >> 2);
-                svd[i] = e0d[i] + ((dpd[i] + dvd[i] + 2) >> 2);
-            }
-            // LL_l into the next level's window
-            int16_t *o = cell(out, PAIRS, q, p0);
+            for (int i = 0; i < CW; ++i)
+                dv[i] = o[i] - pavg(e0[i], e1[i]) + kB2; // Eq. 5.1
+            if (wr + 2 * q == 0) {                       // d[-1] = d[0]
 #pragma unroll
-            for (int i = 0; i < G; ++i)
-                o[i] = (int16_t)svs[i];
-            // HL_l (low rows, high cols), LH_l (high rows, low cols), HH_l
-            const int y = (wr >> 1) + q;
-            if (y >= oy0 && y < oy1) {
-                const uint64_t off = 2ull * ((uint64_t)y * (uint64_t)Wl + (uint64_t)x0);
-                if (cols_owned) {
-                    store_i16<G>(band_hl + off, svd);
-                    store_i16<G>(band_lh + off, dvs);
-                    store_i16<G>(band_hh + off, dvd);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < G; ++i) {
-                        if (x0 + i < ox0 || x0 + i >= ox1)
-                            continue;
-                        const int a[1] = {svd[i]}, b[1] = {dvs[i]}, c[1] = {dvd[i]};
-                        store_i16<1>(band_hl + off + 2 * i, a);
-                        store_i16<1>(band_lh + off + 2 * i, b);
-                        store_i16<1>(band_hh + off + 2 * i, c);
-                    }
-                }
+                for (int i = 0; i < CW; ++i)
+                    dp[i] = dv[i];
             }
 #pragma unroll
-            for (int i = 0; i < G; ++i) {
-                e0s[i] = e1s[i];
-                e0d[i] = e1d[i];
-                dps[i] = dvs[i];
-                dpd[i] = dvd[i];
+            for (int i = 0; i < CW; ++i)
+                sv[i] = e0[i] + pq4(dp[i], dv[i]) - 0x20002000u; // Eq. 5.2
+            const int y = wrl + q;
+            const bool yown = y >= oy0 && y < oy1;
+            if (!high) {
+                uint32_t *dst = A + q * (RW / 2) + w0;
+                if (CW == 4)
+                    *reinterpret_cast<uint4 *>(dst) = make_uint4(sv[0], sv[1 % CW], sv[2 % CW], sv[3 % CW]);
+                else
+                    *reinterpret_cast<uint2 *>(dst) = make_uint2(sv[0], sv[1 % CW]);
+                if (yown)
+                    store_pairs<CW>(band_lh, Wl, y, x0, ox0, ox1, dv);
+            } else if (yown) {
+                store_pairs<CW>(band_hl, Wl, y, x0, ox0, ox1, sv);
+                store_pairs<CW>(band_hh, Wl, y, x0, ox0, ox1, dv);
+            }
+#pragma unroll
+            for (int i = 0; i < CW; ++i) {
+                e0[i] = e1[i];
+                dp[i] = dv[i];
             }
         }
     }
 }
 
-// Load the byte window: rows wr0 .. wr0 + kFW - 1, columns wc0 .. wc0 + 255.
-// Bytes past n (and outside the image) read as 0.
-__device__ __forceinline__ void fwd_load(const Job &j, const FwdGeo &g, FwdSmem &sm)
-{
-    const bool vec = ((j.W & 15u) == 0) && (((uintptr_t)j.in & 15u) == 0);
-    constexpr int CH = kBP / 16;
-    for (int idx = threadIdx.x; idx < kFW * CH; idx += blockDim.x) {
-        const int r = idx / CH, k = idx - r * CH;
-        const int R = g.wr0 + r, c = g.wc0 + 16 * k;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (R >= 0 && R < g.H && c < g.W && c + 16 > 0) {
-            const uint64_t base = (uint64_t)R * (uint64_t)g.W;
-            if (vec && c >= 0 && c + 16 <= g.W && base + (uint64_t)c + 16 <= j.n) {
-                v = __ldg(reinterpret_cast<const uint4 *>(j.in + base + c));
-            } else {
-                uint8_t b[16];
-#pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    const int cc = c + t;
-                    b[t] = (cc >= 0 && cc < g.W && base + (uint64_t)cc < j.n)
-                               ? __ldg(j.in + base + (uint64_t)cc)
-                               : 0;
-                }
-                v.x = b[0] | (b[1] << 8) | (b[2] << 16) | ((uint32_t)b[3] << 24);
-                v.y = b[4] | (b[5] << 8) | (b[6] << 16) | ((uint32_t)b[7] << 24);
-                v.z = b[8] | (b[9] << 8) | (b[10] << 16) | ((uint32_t)b[11] << 24);
-                v.w = b[12] | (b[13] << 8) | (b[14] << 16) | ((uint32_t)b[15] << 24);
-            }
-        }
-        *reinterpret_cast<uint4 *>(sm.bytes + r * kBP + 16 * k) = v;
-    }
-}
-
-// Encrypt and store the owned part of LL_L (window array a, side `side`).
+// owned part of LL_L (packed in A) -> private fragment, AES-CTR
 template <int L>
-__device__ void fwd_store_private(const Job &j, const FwdGeo &g, int16_t *a, const AesSmem &aes)
+__device__ void fwd_store_private(const Job &j, const Geo &g, const uint32_t *A, const AesSmem &aes)
 {
-    constexpr int side = kFW >> L;
+    constexpr int AW = side(L) / 2;
     const int WL = g.W >> L;
     const int X0 = g.C0 >> L, X1 = min(g.C0 + kT, g.W) >> L;
     const int Y0 = g.R0 >> L, Y1 = min(g.R0 + kT, g.H) >> L;
@@ -290,8 +430,9 @@ __device__ void fwd_store_private(const Job &j, const FwdGeo &g, int16_t *a, con
                 c[k] = c[k + 1] = 0;
                 continue;
             }
-            const int x = (int)((o - rowo) / 2);
-            const int v = (int)*cell(a, side, y - wrL, x - wcL) - 128;
+            const int x = (int)((o - rowo) / 2) - wcL;
+            const uint32_t w = A[(y - wrL) * AW + (x >> 1)];
+            const int v = (int)((w >> (16 * (x & 1))) & 0xffffu) - 0x4000 - 128;
             c[k] = (uint8_t)(((uint32_t)v & 255u) ^ ks_byte(ks, k));
             c[k + 1] = (uint8_t)((((uint32_t)v >> 8) & 255u) ^ ks_byte(ks, k + 1));
         }
@@ -315,208 +456,212 @@ __device__ void fwd_store_private(const Job &j, const FwdGeo &g, int16_t *a, con
 }
 
 template <int L>
-__device__ void fwd_tile_fast(const Job &j, uint32_t tx, uint32_t ty, FwdSmem &sm,
-                              const AesSmem &aes)
+__device__ void fwd_tile_fast(const Job &j, uint32_t tx, uint32_t ty, Smem &sm, const AesSmem &aes)
 {
-    FwdGeo g;
-    g.W = (int)j.W;
-    g.H = (int)j.H;
-    g.C0 = (int)tx * kT;
-    g.R0 = (int)ty * kT;
-    g.wc0 = g.C0 - kFH;
-    g.wr0 = g.R0 - kFH;
-    g.pub = j.pub;
-    g.L = j.L;
-    fwd_load(j, g, sm);
+    const Geo g = make_geo(j, tx, ty);
+    fwd_row_pass_bytes(j, g, sm.x);
     __syncthreads();
-    fwd_level<1>(sm.bytes, kBP, sm.a1, g);
+    fwd_col_pass<1>(g, sm.x, sm.a1, j.pub);
     __syncthreads();
     if (L >= 2) {
-        fwd_level<2>(cell(sm.a1, kFW / 2, 0, 0), pitch_of(kFW / 2), sm.a2, g);
+        fwd_row_pass_packed<2>(g, sm.a1, sm.x);
+        __syncthreads();
+        fwd_col_pass<2>(g, sm.x, sm.x + kA2Off, j.pub);
         __syncthreads();
     }
     if (L >= 3) {
-        fwd_level<3>(cell(sm.a2, kFW / 4, 0, 0), pitch_of(kFW / 4), sm.a3, g);
+        fwd_row_pass_packed<3>(g, sm.x + kA2Off, sm.x);
+        __syncthreads();
+        fwd_col_pass<3>(g, sm.x, sm.x + kA3Off, j.pub);
         __syncthreads();
     }
-    int16_t *ll = L == 1 ? sm.a1 : (L == 2 ? sm.a2 : sm.a3);
-    fwd_store_private<L>(j, g, ll, aes);
+    fwd_store_private<L>(j, g, a_arr(sm, L), aes);
 }
 
 // ---------------------------------------------------------------------------
 // inverse
 // ---------------------------------------------------------------------------
 
-struct InvGeo {
-    int W, H;
-    int C0, R0;   // owned output tile origin (level 0)
-    int wc0, wr0; // window origin (level 0) = C0 - 16, R0 - 16
-    const uint8_t *pub;
-    uint32_t L;
-};
-
-// a detail coefficient of band base `b` (level-l dims Hl x Wl) or 0 outside
-__device__ __forceinline__ int coef(const uint8_t *b, int y, int x, int Hl, int Wl)
-{
-    if (y < 0 || y >= Hl || x < 0 || x >= Wl)
-        return 0;
-    const uint8_t *p = b + 2ull * ((uint64_t)y * (uint64_t)Wl + (uint64_t)x);
-    if (((uintptr_t)p & 1u) == 0)
-        return (int)__ldg(reinterpret_cast<const int16_t *>(p));
-    return (int)(int16_t)(uint16_t)((uint32_t)__ldg(p) | ((uint32_t)__ldg(p + 1) << 8));
-}
-
-// One inverse level l: LL_l window `ll` (side 256 >> l) + detail bands ->
-// LL_{l-1} window `out` (side 256 >> (l-1)), or bytes to HBM when l == 1.
+// Column inverse of level l: A_l + detail bands -> R_l (row-lifted rows).
 template <int l>
-__device__ void inv_level(const int16_t *ll, int16_t *out, const Job &j, const InvGeo &g)
+__device__ void inv_col_pass(const Geo &g, const uint32_t *A, uint32_t *R, const uint8_t *pub)
 {
-    constexpr int G = 4 >> (l - 1);
-    constexpr int S = 16 >> (l - 1);
-    constexpr int PAIRS = kIW >> l;   // level-l window side: 128, 64, 32
-    constexpr int GROUPS = PAIRS / G; // 32
-    constexpr int SEGS = PAIRS / S;   // 8
-    constexpr int NL = G + 1, NH = G + 2;
-    const int wcl = g.wc0 >> l, wrl = g.wr0 >> l;             // level-l window origin
-    const int Wm = g.W >> (l - 1), Hm = g.H >> (l - 1);       // level l-1 image
-    const int Wl = g.W >> l, Hl = g.H >> l;
-    const uint8_t *band_hl = g.pub + band_offset(g.H, g.W, g.L, l, 0);
-    const uint8_t *band_lh = g.pub + band_offset(g.H, g.W, g.L, l, 1);
-    const uint8_t *band_hh = g.pub + band_offset(g.H, g.W, g.L, l, 2);
+    constexpr int CW = l == 3 ? 2 : 4;
+    constexpr int S = l == 1 ? 12 : (l == 2 ? 4 : 2);
+    constexpr int RW = side(l);
+    constexpr int PAIRS = side(l);
+    constexpr int CH = RW / CW;
+    constexpr int SEGS = PAIRS / S;
+    const int wrl = g.wr0 >> l, wcl = g.wc0 >> l;
+    const int Hm = g.H >> (l - 1);
+    const int Hl = g.H >> l, Wl = g.W >> l;
+    const uint8_t *band_hl = pub + band_offset(g.H, g.W, g.L, l, 0);
+    const uint8_t *band_lh = pub + band_offset(g.H, g.W, g.L, l, 1);
+    const uint8_t *band_hh = pub + band_offset(g.H, g.W, g.L, l, 2);
 
-    for (int it = threadIdx.x; it < GROUPS * SEGS; it += blockDim.x) {
-        const int gx = it % GROUPS, sy = it / GROUPS;
-        const int p0 = gx * G, q0 = sy * S;
-        // low columns p0 .. p0+G (s from LL_l, d from LH_l); high columns
-        // p0-1 .. p0+G (s from HL_l, d from HH_l)
-        auto load_row = [&](int k, int (&ls)[NL], int (&ld)[NL], int (&hs)[NH], int (&hd)[NH]) {
-            const int kk = min(max(k, -1), PAIRS); // padded rows of `ll`
+    for (int it = threadIdx.x; it < CH * SEGS; it += blockDim.x) {
+        const int c = it % CH, sy = it / CH;
+        const int w0 = c * CW;
+        const bool high = w0 >= RW / 2;
+        const int wl = w0 - (high ? RW / 2 : 0); // word within the half
+        const int x0 = wcl + 2 * wl;
+        const int q0 = sy * S;
+        // coefficients of row pair k: s (even row) and d (odd row)
+        auto coeffs = [&](int k, uint32_t (&s)[CW], uint32_t (&d)[CW]) {
             const int y = wrl + k;
+            if (!high) {
+                const int kk = min(max(k, 0), PAIRS - 1);
+                const uint32_t *p = A + kk * (RW / 2) + wl;
 #pragma unroll
-            for (int i = 0; i < NL; ++i) {
-                ls[i] = (int)*cell(const_cast<int16_t *>(ll), PAIRS, kk, p0 + i);
-                ld[i] = coef(band_lh, y, wcl + p0 + i, Hl, Wl);
-            }
-#pragma unroll
-            for (int i = 0; i < NH; ++i) {
-                hs[i] = coef(band_hl, y, wcl + p0 - 1 + i, Hl, Wl);
-                hd[i] = coef(band_hh, y, wcl + p0 - 1 + i, Hl, Wl);
+                for (int i = 0; i < CW; ++i)
+                    s[i] = p[i];
+                load_pairs<CW>(band_lh, Hl, Wl, y, x0, d);
+            } else {
+                load_pairs<CW>(band_hl, Hl, Wl, y, x0, s);
+                load_pairs<CW>(band_hh, Hl, Wl, y, x0, d);
             }
         };
-        int ls[NL], ld[NL], hs[NH], hd[NH];     // coefficients of row pair q (then q+1)
-        int lxe[NL], hxe[NH];                   // reconstructed even rows x[2q]
-        int ldp[NL], hdp[NH];                   // d[q-1]
-        load_row(q0 - 1, ls, ld, hs, hd);
-#pragma unroll
-        for (int i = 0; i < NL; ++i)
-            ldp[i] = ld[i];
-#pragma unroll
-        for (int i = 0; i < NH; ++i)
-            hdp[i] = hd[i];
-        load_row(q0, ls, ld, hs, hd);
+        uint32_t s0[CW], d0[CW], s1[CW], d1[CW], xe[CW], xe1[CW];
+        coeffs(q0 - 1, s1, d1); // d[q0-1] in d1
+        coeffs(q0, s0, d0);
         if (wrl + q0 == 0) { // d[-1] = d[0]
 #pragma unroll
-            for (int i = 0; i < NL; ++i)
-                ldp[i] = ld[i];
-#pragma unroll
-            for (int i = 0; i < NH; ++i)
-                hdp[i] = hd[i];
+            for (int i = 0; i < CW; ++i)
+                d1[i] = d0[i];
         }
 #pragma unroll
-        for (int i = 0; i < NL; ++i)
-            lxe[i] = ls[i] - ((ldp[i] + ld[i] + 2) >> 2);
-#pragma unroll
-        for (int i = 0; i < NH; ++i)
-            hxe[i] = hs[i] - ((hdp[i] + hd[i] + 2) >> 2);
-
+        for (int i = 0; i < CW; ++i)
+            xe[i] = s0[i] - pq4(d1[i], d0[i]) + 0x20002000u; // undo Eq. 5.2
         for (int q = q0; q < q0 + S; ++q) {
-            int ns[NL], nd[NL], nhs[NH], nhd[NH];
-            load_row(q + 1, ns, nd, nhs, nhd);
-            int lxn[NL], hxn[NH], lxo[NL], hxo[NH];
+            coeffs(q + 1, s1, d1);
+            const bool first = (wrl + q + 1 == 0);
+#pragma unroll
+            for (int i = 0; i < CW; ++i)
+                xe1[i] = s1[i] - pq4(first ? d1[i] : d0[i], d1[i]) + 0x20002000u;
             const bool bottom = (2 * (wrl + q) + 2 == Hm); // x[m] = x[m-2]
-            const bool first = (wrl + q + 1 == 0);         // d[-1] = d[0] for the next pair
+            uint32_t xo[CW];
 #pragma unroll
-            for (int i = 0; i < NL; ++i) {
-                lxn[i] = ns[i] - (((first ? nd[i] : ld[i]) + nd[i] + 2) >> 2);
-                lxo[i] = ld[i] + ((lxe[i] + (bottom ? lxe[i] : lxn[i])) >> 1);
+            for (int i = 0; i < CW; ++i)
+                xo[i] = d0[i] + pavg(xe[i], bottom ? xe[i] : xe1[i]) - kB2; // undo Eq. 5.1
+            uint32_t *re = R + (2 * q) * RW + w0;
+            uint32_t *ro = re + RW;
+            if (CW == 4) {
+                *reinterpret_cast<uint4 *>(re) = make_uint4(xe[0], xe[1 % CW], xe[2 % CW], xe[3 % CW]);
+                *reinterpret_cast<uint4 *>(ro) = make_uint4(xo[0], xo[1 % CW], xo[2 % CW], xo[3 % CW]);
+            } else {
+                *reinterpret_cast<uint2 *>(re) = make_uint2(xe[0], xe[1 % CW]);
+                *reinterpret_cast<uint2 *>(ro) = make_uint2(xo[0], xo[1 % CW]);
             }
 #pragma unroll
-            for (int i = 0; i < NH; ++i) {
-                hxn[i] = nhs[i] - (((first ? nhd[i] : hd[i]) + nhd[i] + 2) >> 2);
-                hxo[i] = hd[i] + ((hxe[i] + (bottom ? hxe[i] : hxn[i])) >> 1);
-            }
-            // undo the row lifting of rows 2q (lxe / hxe) and 2q+1 (lxo / hxo)
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int *Lv = half ? lxo : lxe;
-                const int *Hv = half ? hxo : hxe;
-                int ev[NL], xo[2 * G];
-#pragma unroll
-                for (int i = 0; i < NL; ++i) {
-                    const int hl = (wcl + p0 + i == 0) ? Hv[i + 1] : Hv[i]; // d[-1] = d[0]
-                    ev[i] = Lv[i] - ((hl + Hv[i + 1] + 2) >> 2);
-                }
-#pragma unroll
-                for (int i = 0; i < G; ++i) {
-                    const int xr = (2 * (wcl + p0 + i) + 2 == Wm) ? ev[i] : ev[i + 1];
-                    xo[2 * i] = ev[i];
-                    xo[2 * i + 1] = Hv[i + 1] + ((ev[i] + xr) >> 1);
-                }
-                const int r = 2 * q + half; // window row at level l-1
-                if (l > 1) {
-                    int16_t *o = cell(out, 2 * PAIRS, r, 2 * p0);
-#pragma unroll
-                    for (int i = 0; i < 2 * G; ++i)
-                        o[i] = (int16_t)xo[i];
-                } else {
-                    const int R = g.wr0 + r, C = g.wc0 + 2 * p0;
-                    if (R >= g.R0 && R < min(g.R0 + kT, g.H) && C >= g.C0 &&
-                        C + 2 * G <= g.C0 + kT && C < g.W) {
-                        const uint64_t go = (uint64_t)R * (uint64_t)g.W + (uint64_t)C;
-                        uint8_t *dst = j.out + go;
-                        if (C + 2 * G <= g.W && go + 2 * G <= j.n && ((uintptr_t)dst & 7u) == 0) {
-                            uint2 w;
-                            w.x = (xo[0] & 255) | ((xo[1] & 255) << 8) | ((xo[2] & 255) << 16) |
-                                  ((uint32_t)(xo[3] & 255) << 24);
-                            w.y = (xo[4] & 255) | ((xo[5] & 255) << 8) | ((xo[6] & 255) << 16) |
-                                  ((uint32_t)(xo[7] & 255) << 24);
-                            *reinterpret_cast<uint2 *>(dst) = w;
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < 2 * G; ++i)
-                                if (C + i < g.W && go + i < j.n)
-                                    dst[i] = (uint8_t)xo[i];
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < NL; ++i) {
-                lxe[i] = lxn[i];
-                ld[i] = nd[i];
-            }
-#pragma unroll
-            for (int i = 0; i < NH; ++i) {
-                hxe[i] = hxn[i];
-                hd[i] = nhd[i];
+            for (int i = 0; i < CW; ++i) {
+                xe[i] = xe1[i];
+                d0[i] = d1[i];
             }
         }
     }
 }
 
-// Decrypt the window's part of LL_L into `a` (side 256 >> L), adding back 128.
-template <int L>
-__device__ void inv_load_private(const Job &j, const InvGeo &g, int16_t *a, const AesSmem &aes)
+// Row inverse of level l: R_l -> A_{l-1} (l >= 2) or the output bytes (l = 1).
+template <int l>
+__device__ void inv_row_pass(const Job &j, const Geo &g, const uint32_t *R, uint32_t *Aout)
 {
-    constexpr int side = kIW >> L;
+    constexpr int P = l == 3 ? 4 : 8;  // pairs per item
+    constexpr int RW = side(l);        // words per R_l row
+    constexpr int HW = RW / 2;         // words per half
+    constexpr int ROWS = side(l - 1);
+    constexpr int CH = side(l) / P;    // items per row
+    const int wcl = g.wc0 >> l;
+    const int Wm = g.W >> (l - 1);
+    for (int it = threadIdx.x; it < ROWS * CH; it += blockDim.x) {
+        const int r = it / CH, k = it - r * CH;
+        const int p0 = k * P; // first pair (level-l window column)
+        const uint32_t *row = R + r * RW;
+        // low values L[p0 .. p0+P], high values H[p0-1 .. p0+P]
+        int Lv[P + 2], Hv[P + 4];
+        {
+            const int lw = p0 / 2;
+#pragma unroll
+            for (int t = 0; t < P / 2; ++t) {
+                const uint32_t w = row[lw + t];
+                Lv[2 * t] = (int)(w & 0xffffu);
+                Lv[2 * t + 1] = (int)(w >> 16);
+                const uint32_t h = row[HW + lw + t];
+                Hv[2 + 2 * t] = (int)(h & 0xffffu);
+                Hv[3 + 2 * t] = (int)(h >> 16);
+            }
+            const uint32_t ln = row[min(lw + P / 2, HW - 1)];
+            Lv[P] = (int)(ln & 0xffffu);
+            Lv[P + 1] = (int)(ln >> 16);
+            const uint32_t hp = row[HW + max(lw - 1, 0)];
+            Hv[0] = (int)(hp & 0xffffu);
+            Hv[1] = (int)(hp >> 16);
+            const uint32_t hn = row[HW + min(lw + P / 2, HW - 1)];
+            Hv[P + 2] = (int)(hn & 0xffffu);
+            Hv[P + 3] = (int)(hn >> 16);
+        }
+        // Hv[1 + i] is H[p0 + i - 1]
+        int ev[P + 1], out[2 * P];
+#pragma unroll
+        for (int i = 0; i <= P; ++i) {
+            const int hl = (wcl + p0 + i == 0) ? Hv[2 + i] : Hv[1 + i]; // d[-1] = d[0]
+            ev[i] = Lv[i] - ((hl + Hv[2 + i] + 2) >> 2) + 0x2000;     // undo Eq. 5.2 (biased)
+        }
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const int xr = (2 * (wcl + p0 + i) + 2 == Wm) ? ev[i] : ev[i + 1]; // x[m] = x[m-2]
+            out[2 * i] = ev[i];
+            out[2 * i + 1] = Hv[2 + i] + ((ev[i] + xr) >> 1) - 0x4000; // undo Eq. 5.1 (biased)
+        }
+        if (l > 1) {
+            uint32_t *dst = Aout + r * (ROWS / 2) + p0;
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                dst[i] = pack2(out[2 * i], out[2 * i + 1]);
+        } else {
+            const int Rr = g.wr0 + r, C = g.wc0 + 2 * p0;
+            if (Rr < g.R0 || Rr >= min(g.R0 + kT, g.H) || C < g.C0 || C >= g.C0 + kT || C >= g.W)
+                continue;
+            const uint64_t go = (uint64_t)Rr * (uint64_t)g.W + (uint64_t)C;
+            uint8_t *dst = j.out + go;
+            // biased values 0x4000 + b: the low byte is the recovered byte
+            if (C + 2 * P <= g.W && go + 2 * P <= j.n && ((uintptr_t)dst & 15u) == 0) {
+                uint32_t wv[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const uint32_t a = __byte_perm((uint32_t)out[4 * t], (uint32_t)out[4 * t + 1], 0x0040);
+                    const uint32_t b = __byte_perm((uint32_t)out[4 * t + 2], (uint32_t)out[4 * t + 3], 0x0040);
+                    wv[t] = __byte_perm(a, b, 0x5410);
+                }
+                *reinterpret_cast<uint4 *>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 2 * P; ++i)
+                    if (C + i < g.W && go + i < j.n)
+                        dst[i] = (uint8_t)out[i];
+            }
+        }
+    }
+}
+
+// LL_L window from the private fragment: decrypt, add back 128, pack biased.
+template <int L>
+__device__ void inv_load_private(const Job &j, const Geo &g, uint32_t *A, const AesSmem &aes)
+{
+    constexpr int SD = side(L), AW = SD / 2;
+    for (int i = threadIdx.x; i < SD * AW; i += blockDim.x)
+        A[i] = kB2; // positions outside the image: value 0
+    __syncthreads();
     const int WL = g.W >> L, HL = g.H >> L;
     const int wcL = g.wc0 >> L, wrL = g.wr0 >> L;
-    const int xa = max(wcL, 0), xb = min(wcL + side, WL); // columns [xa, xb)
+    const int xa = max(wcL, 0), xb = min(wcL + SD, WL);
+    if (xb <= xa)
+        return;
     const int bpr = (2 * (xb - xa) + 15) / 16 + 1;
-    for (int idx = threadIdx.x; idx < side * bpr; idx += blockDim.x) {
+    uint16_t *A16 = reinterpret_cast<uint16_t *>(A);
+    for (int idx = threadIdx.x; idx < SD * bpr; idx += blockDim.x) {
         const int k = idx / bpr, jb = idx - k * bpr;
         const int y = wrL + k;
-        if (y < 0 || y >= HL || xb <= xa)
+        if (y < 0 || y >= HL)
             continue;
         const uint64_t rowo = 2ull * (uint64_t)y * (uint64_t)WL;
         const uint64_t start = rowo + 2ull * xa, end = rowo + 2ull * xb;
@@ -532,38 +677,34 @@ __device__ void inv_load_private(const Job &j, const InvGeo &g, int16_t *a, cons
                 continue;
             const uint32_t lo8 = __ldg(j.priv_in + o) ^ ks_byte(ks, kk);
             const uint32_t hi8 = __ldg(j.priv_in + o + 1) ^ ks_byte(ks, kk + 1);
-            const int v = (int)(int16_t)(uint16_t)(lo8 | (hi8 << 8)) + 128;
-            const int x = (int)((o - rowo) / 2);
-            *cell(a, side, k, x - wcL) = (int16_t)v;
+            const int v = (int)(int16_t)(uint16_t)(lo8 | (hi8 << 8)) + 128 + 0x4000;
+            const int x = (int)((o - rowo) / 2) - wcL;
+            A16[k * SD + x] = (uint16_t)v;
         }
     }
 }
 
 template <int L>
-__device__ void inv_tile_fast(const Job &j, uint32_t tx, uint32_t ty, InvSmem &sm,
-                              const AesSmem &aes)
+__device__ void inv_tile_fast(const Job &j, uint32_t tx, uint32_t ty, Smem &sm, const AesSmem &aes)
 {
-    InvGeo g;
-    g.W = (int)j.W;
-    g.H = (int)j.H;
-    g.C0 = (int)tx * kT;
-    g.R0 = (int)ty * kT;
-    g.wc0 = g.C0 - kIH;
-    g.wr0 = g.R0 - kIH;
-    g.pub = j.pub_in;
-    g.L = j.L;
-    int16_t *top = L == 1 ? sm.a0 : (L == 2 ? sm.a1 : sm.a2);
-    inv_load_private<L>(j, g, top, aes);
+    const Geo g = make_geo(j, tx, ty);
+    inv_load_private<L>(j, g, a_arr(sm, L), aes);
     __syncthreads();
     if (L >= 3) {
-        inv_level<3>(sm.a2, sm.a1, j, g);
+        inv_col_pass<3>(g, sm.x + kA3Off, sm.x, j.pub_in);
+        __syncthreads();
+        inv_row_pass<3>(j, g, sm.x, sm.x + kA2Off);
         __syncthreads();
     }
     if (L >= 2) {
-        inv_level<2>(sm.a1, sm.a0, j, g);
+        inv_col_pass<2>(g, sm.x + kA2Off, sm.x, j.pub_in);
+        __syncthreads();
+        inv_row_pass<2>(j, g, sm.x, sm.a1);
         __syncthreads();
     }
-    inv_level<1>(sm.a0, nullptr, j, g);
+    inv_col_pass<1>(g, sm.a1, sm.x, j.pub_in);
+    __syncthreads();
+    inv_row_pass<1>(j, g, sm.x, nullptr);
 }
 
 } // namespace fast

@@ -29,7 +29,7 @@ struct Job {
     uint32_t tile_h;  // owned tile height (multiple of 2^L)
     uint32_t tiles_x;
     uint32_t tiles_y;
-    uint32_t path;    // 0: generic tile body, 1: register-streaming body (L <= 3)
+    uint32_t path;    // 0: generic tile body, 1: row/column-pass body (L <= 3)
 };
 
 // Launch-wide description of where jobs and tiles come from.
@@ -45,7 +45,7 @@ struct Work {
     int *err;                   // device error word
 };
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kAesWords = 4 * 256 + 256;
 
 // Byte offset of band b (0 = HL, 1 = LH, 2 = HH) of level l (1..L) inside the
@@ -74,7 +74,7 @@ const uint32_t *host_aes_words();                             // kAesWords words
 void host_expand_key(const uint8_t key[16], uint32_t rk[44]); // FIPS-197 key schedule
 
 // kernels (tile_kernels.cu)
-constexpr uint32_t kFastTile = 224;   // owned tile side of the register-streaming body
+constexpr uint32_t kFastTile = 256;   // owned tile side of the row/column-pass body
 constexpr uint32_t kFastMaxLevels = 3;
 size_t tile_smem_bytes(uint32_t tile_w, uint32_t tile_h, uint32_t L, bool fwd);
 size_t fast_smem_bytes(bool fwd);

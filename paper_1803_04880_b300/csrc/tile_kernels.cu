@@ -364,7 +364,7 @@ __device__ __forceinline__ const Job *find_job(const Work &w, uint64_t t, uint64
 }
 
 template <bool FWD>
-__global__ void __launch_bounds__(kThreads) tile_kernel(Work w)
+__global__ void __launch_bounds__(kThreads, 1) tile_kernel(Work w)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     AesSmem &aes = *reinterpret_cast<AesSmem *>(smem);
@@ -392,8 +392,8 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(Work w)
         }
         const uint32_t tx = (uint32_t)(local % j.tiles_x), ty = (uint32_t)(local / j.tiles_x);
         if (j.path == 1) {
+            fast::Smem &fs = *reinterpret_cast<fast::Smem *>(S);
             if (FWD) {
-                fast::FwdSmem &fs = *reinterpret_cast<fast::FwdSmem *>(S);
                 if (j.L == 1)
                     fast::fwd_tile_fast<1>(j, tx, ty, fs, aes);
                 else if (j.L == 2)
@@ -401,13 +401,12 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(Work w)
                 else
                     fast::fwd_tile_fast<3>(j, tx, ty, fs, aes);
             } else {
-                fast::InvSmem &is = *reinterpret_cast<fast::InvSmem *>(S);
                 if (j.L == 1)
-                    fast::inv_tile_fast<1>(j, tx, ty, is, aes);
+                    fast::inv_tile_fast<1>(j, tx, ty, fs, aes);
                 else if (j.L == 2)
-                    fast::inv_tile_fast<2>(j, tx, ty, is, aes);
+                    fast::inv_tile_fast<2>(j, tx, ty, fs, aes);
                 else
-                    fast::inv_tile_fast<3>(j, tx, ty, is, aes);
+                    fast::inv_tile_fast<3>(j, tx, ty, fs, aes);
             }
         } else if (FWD) {
             fwd_tile(j, tx, ty, S, aes, w.err);
@@ -429,7 +428,8 @@ size_t tile_smem_bytes(uint32_t tile_w, uint32_t tile_h, uint32_t L, bool fwd)
 
 size_t fast_smem_bytes(bool fwd)
 {
-    return sizeof(AesSmem) + (fwd ? sizeof(fast::FwdSmem) : sizeof(fast::InvSmem));
+    (void)fwd;
+    return sizeof(AesSmem) + sizeof(fast::Smem);
 }
 
 size_t job_smem_bytes(const Job &j, bool fwd)
