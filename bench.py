@@ -161,7 +161,7 @@ def run_reference(args, rank):
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for name in ("tile_kernels.cu", "frag_internal.cuh"):
+    for name in ("stream_kernels.cu", "frag_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1803_04880_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -310,8 +310,8 @@ def run_ours(args, rank, world, local_rank):
     achieved = alg_bytes / (t_dom / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": _traffic(args.workload, dominant),
-                "kernel": "tile_kernel<%s> (%s)" % ("true" if dominant == "protect" else "false",
-                                                   dominant),
+                "kernel": "level_kernel<%s> (%s, all levels of one direction)"
+                          % ("true" if dominant == "protect" else "false", dominant),
                 "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": alg_bytes}
 
@@ -353,9 +353,9 @@ def run_ours(args, rank, world, local_rank):
                 "dtype": "int32", "data": "synthetic",
                 "config": dict(desc, l2="flushed (512 MiB write) before each direction",
                                parallelism="replicas" if world > 1 else "single GPU",
-                               path="frag_batch_run (one persistent launch per direction)"),
+                               path="frag_batch_run (one launch per level and direction)"),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 2 * K,
+                "gpu_launches": 2 * K * max(L for (_, L, _, _) in items),
                 "protect_gbps": round(n_total / (t_prot / 1e3) / 1e9, 2),
                 "recover_gbps": round(n_total / (t_rec / 1e3) / 1e9, 2),
                 "hbm_frac_protect_recover": round(2 * alg_bytes / (ms_per_step / 1e3) / 1e9 / peak, 4),

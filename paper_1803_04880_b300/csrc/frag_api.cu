@@ -33,14 +33,6 @@ struct frag_key_s {
     std::map<int, uint32_t *> on_device;
 };
 
-struct frag_batch_s {
-    int device;
-    bool fwd;
-    Work work;
-    uint32_t grid;
-    size_t smem;
-    void *d_mem; // jobs | tile_start | queue head
-};
 
 namespace {
 
@@ -273,7 +265,118 @@ void base_work(Work &w, DeviceState &d, const uint32_t *rk)
     w.err = d.err;
 }
 
-frag_status launch_single(bool fwd, frag_plan plan, frag_key key, const Job &j, cudaStream_t s)
+// ---------------------------------------------------------------------------
+// Streaming path: one launch per level; LL between levels in scratch
+// ---------------------------------------------------------------------------
+using frag::LevelJob;
+using frag::LevelWork;
+
+constexpr uint32_t kSegPairs = 16;         // row pairs per work unit in batches
+constexpr uint64_t kScratchBudget = 8ull << 30; // per wave of a batch
+
+uint64_t align256(uint64_t v) { return (v + 255) / 256 * 256; }
+
+uint64_t ll_bytes(uint32_t H, uint32_t W, uint32_t l) { return 2ull * (H >> l) * (uint64_t)(W >> l); }
+
+// scratch of one buffer: LL_1 (and later LL_3, ...) in part 0, LL_2 (LL_4, ...) in part 1
+uint64_t scratch_bytes(uint32_t H, uint32_t W, uint32_t L, uint64_t *off1)
+{
+    *off1 = 0;
+    if (L < 2)
+        return 0;
+    const uint64_t a = align256(ll_bytes(H, W, 1));
+    *off1 = a;
+    return a + (L >= 3 ? align256(ll_bytes(H, W, 2)) : 0);
+}
+
+struct Buf {
+    uint32_t W, L, H;
+    uint64_t n, nonce;
+    const uint8_t *in;
+    uint8_t *priv, *pub;
+    const uint8_t *priv_in, *pub_in;
+    uint8_t *out;
+    uint8_t *scr[2];
+};
+
+void decompose(LevelJob &j, uint32_t seg_pairs)
+{
+    j.strips = (j.Ws + frag::kStripCols - 1) / frag::kStripCols;
+    j.seg_pairs = seg_pairs;
+    j.segs = ((j.Hs / 2) + seg_pairs - 1) / seg_pairs;
+}
+
+LevelJob protect_level(const Buf &b, uint32_t l, uint32_t seg_pairs)
+{
+    LevelJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.Ws = b.W >> (l - 1);
+    j.Hs = b.H >> (l - 1);
+    j.src = l == 1 ? b.in : b.scr[(l - 2) % 2];
+    j.src_bytes = l == 1;
+    j.hl = b.pub + frag::band_offset(b.H, b.W, b.L, l, 0);
+    j.lh = b.pub + frag::band_offset(b.H, b.W, b.L, l, 1);
+    j.hh = b.pub + frag::band_offset(b.H, b.W, b.L, l, 2);
+    j.final_level = l == b.L;
+    j.ll = l == b.L ? b.priv : b.scr[(l - 1) % 2];
+    j.n = b.n;
+    j.nonce = b.nonce;
+    decompose(j, seg_pairs);
+    return j;
+}
+
+LevelJob recover_level(const Buf &b, uint32_t l, uint32_t seg_pairs)
+{
+    LevelJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.Ws = b.W >> (l - 1);
+    j.Hs = b.H >> (l - 1);
+    j.hl = const_cast<uint8_t *>(b.pub_in) + frag::band_offset(b.H, b.W, b.L, l, 0);
+    j.lh = const_cast<uint8_t *>(b.pub_in) + frag::band_offset(b.H, b.W, b.L, l, 1);
+    j.hh = const_cast<uint8_t *>(b.pub_in) + frag::band_offset(b.H, b.W, b.L, l, 2);
+    j.top_level = l == b.L;
+    j.ll_in = l == b.L ? b.priv_in : b.scr[(l - 1) % 2];
+    j.out_bytes = l == 1;
+    j.out = l == 1 ? b.out : b.scr[(l - 2) % 2];
+    j.n = b.n;
+    j.nonce = b.nonce;
+    decompose(j, seg_pairs);
+    return j;
+}
+
+frag_status level_grid(DeviceState &d, bool fwd, uint64_t units, uint32_t *grid)
+{
+    int occ = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        auto it = d.occ[fwd].find(0);
+        if (it != d.occ[fwd].end())
+            occ = it->second;
+    }
+    if (occ == 0) {
+        cudaError_t e = frag::level_occupancy(fwd, &occ);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "occupancy query");
+        if (occ <= 0)
+            occ = 1;
+        std::lock_guard<std::mutex> lock(g_mu);
+        d.occ[fwd][0] = occ;
+    }
+    const uint64_t warps_per_block = 8;
+    const uint64_t blocks = (units + warps_per_block - 1) / warps_per_block;
+    *grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)d.sms * occ, blocks));
+    return FRAG_OK;
+}
+
+// row pairs per unit for a lone buffer: about two units per resident warp
+uint32_t single_seg_pairs(DeviceState &d, uint32_t strips, uint32_t pairs)
+{
+    const uint64_t slots = (uint64_t)d.sms * 64;
+    const uint64_t want = std::max<uint64_t>(1, (uint64_t)strips * pairs / (2 * slots));
+    return (uint32_t)std::min<uint64_t>(64, std::max<uint64_t>(8, want));
+}
+
+frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream_t s)
 {
     DeviceState *d = nullptr;
     int dev = 0;
@@ -283,37 +386,81 @@ frag_status launch_single(bool fwd, frag_plan plan, frag_key key, const Job &j, 
     const uint32_t *rk = nullptr;
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
-    Work w;
-    base_work(w, *d, rk);
-    w.single = j;
-    w.total_tiles = (uint64_t)j.tiles_x * j.tiles_y;
-    const size_t smem = job_smem(j, fwd);
-    uint32_t grid = 0;
-    if ((st = launch_shape(*d, fwd, smem, plan->ctas_per_sm, w.total_tiles, &grid)) != FRAG_OK)
-        return st;
-    cudaError_t e = frag::launch_tiles(fwd, w, grid, smem, s);
-    if (e != cudaSuccess)
-        return cuda_fail(e, fwd ? "protect launch" : "recover launch");
-    return FRAG_OK;
+    uint64_t off1 = 0;
+    const uint64_t sb = scratch_bytes(b.H, b.W, b.L, &off1);
+    uint8_t *scr = nullptr;
+    cudaError_t e;
+    if (sb) {
+        if ((e = cudaMallocAsync((void **)&scr, sb, s)) != cudaSuccess)
+            return cuda_fail(e, "cudaMallocAsync(level scratch)");
+        b.scr[0] = scr;
+        b.scr[1] = scr + off1;
+    }
+    for (uint32_t k = 0; k < b.L && st == FRAG_OK; ++k) {
+        const uint32_t l = fwd ? k + 1 : b.L - k;
+        LevelWork w;
+        std::memset(&w, 0, sizeof(w));
+        w.aes_tables = d->tables;
+        w.round_keys = rk;
+        w.err = d->err;
+        const uint32_t Ws = b.W >> (l - 1), Hs = b.H >> (l - 1);
+        const uint32_t strips = (Ws + frag::kStripCols - 1) / frag::kStripCols;
+        const uint32_t seg = single_seg_pairs(*d, strips, Hs / 2);
+        w.single = fwd ? protect_level(b, l, seg) : recover_level(b, l, seg);
+        w.total_units = (uint64_t)w.single.strips * w.single.segs;
+        uint32_t grid = 0;
+        if ((st = level_grid(*d, fwd, w.total_units, &grid)) != FRAG_OK)
+            break;
+        if ((e = frag::launch_level(fwd, w, grid, s)) != cudaSuccess)
+            st = cuda_fail(e, fwd ? "protect launch" : "recover launch");
+    }
+    (void)plan;
+    if (scr)
+        cudaFreeAsync(scr, s);
+    return st;
 }
 
 // ---------------------------------------------------------------------------
-// Batches
+// Batches: waves of buffers whose scratch fits a budget; per wave one launch
+// per level over all its buffers, units handed out by a device queue
 // ---------------------------------------------------------------------------
-struct BatchHost {
-    std::vector<Job> jobs;
-    std::vector<uint64_t> tile_start;
-    size_t smem = 0;
-    uint32_t min_ctas = 0;
+struct LevelList {
+    std::vector<LevelJob> jobs;
+    std::vector<uint64_t> start; // exclusive prefix of units
+    size_t job_off = 0, start_off = 0;
+    uint32_t queue_index = 0;
 };
 
-// Order items from the most to the least costly (tiles x window area), so the
-// queue hands out the long jobs first and the short ones fill the tail.
-frag_status build_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint32_t count,
-                        BatchHost &b)
+struct Wave {
+    std::vector<LevelList> levels; // forward: l = 1..maxL; inverse: l = maxL..1
+    bool fwd = true;
+};
+
+struct BatchPlan {
+    std::vector<Buf> bufs;
+    std::vector<uint64_t> scr_off;   // scratch offset of each buffer (within its wave)
+    std::vector<uint32_t> wave_of;
+    std::vector<Wave> waves;
+    uint64_t scratch = 0;            // bytes (largest wave)
+    size_t desc_bytes = 0;
+    uint32_t queues = 0;
+};
+
+} // namespace
+
+struct frag_batch_s {
+    int device = 0;
+    BatchPlan bp;
+    uint8_t *mem = nullptr; // [scratch][descriptors][queue heads]
+};
+
+namespace {
+
+frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint32_t count,
+                       BatchPlan &bp)
 {
-    std::vector<std::pair<uint64_t, Job>> v;
-    v.reserve(count);
+    // buffers, most work first (so long buffers start early)
+    std::vector<std::pair<uint64_t, Buf>> v;
     for (uint32_t i = 0; i < count; ++i) {
         frag_plan plan = fwd ? pi[i].plan : ri[i].plan;
         if (plan == nullptr)
@@ -321,52 +468,147 @@ frag_status build_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uin
         const uint64_t n = fwd ? pi[i].nbytes : ri[i].nbytes;
         if (n == 0)
             continue;
-        Job j;
-        frag_status st = fill_job(plan, fwd ? pi[i].nonce : ri[i].nonce, n, j);
-        if (st != FRAG_OK)
-            return st;
+        Buf b;
+        std::memset(&b, 0, sizeof(b));
+        b.W = plan->width;
+        b.L = plan->levels;
+        const uint64_t H = rows_for(n, b.W, b.L);
+        if (H > 0xFFFFFFFFull)
+            return fail(FRAG_EINVAL, "item %u is too tall for width %u", i, b.W);
+        b.H = (uint32_t)H;
+        b.n = n;
         if (fwd) {
-            j.in = (const uint8_t *)pi[i].d_in;
-            j.priv = (uint8_t *)pi[i].d_private;
-            j.pub = (uint8_t *)pi[i].d_public;
-            if (!j.in || !j.priv || !j.pub)
+            b.nonce = pi[i].nonce;
+            b.in = (const uint8_t *)pi[i].d_in;
+            b.priv = (uint8_t *)pi[i].d_private;
+            b.pub = (uint8_t *)pi[i].d_public;
+            if (!b.in || !b.priv || !b.pub)
                 return fail(FRAG_EINVAL, "item %u has a NULL buffer", i);
         } else {
-            j.priv_in = (const uint8_t *)ri[i].d_private;
-            j.pub_in = (const uint8_t *)ri[i].d_public;
-            j.out = (uint8_t *)ri[i].d_out;
-            if (!j.priv_in || !j.pub_in || !j.out)
+            b.nonce = ri[i].nonce;
+            b.priv_in = (const uint8_t *)ri[i].d_private;
+            b.pub_in = (const uint8_t *)ri[i].d_public;
+            b.out = (uint8_t *)ri[i].d_out;
+            if (!b.priv_in || !b.pub_in || !b.out)
                 return fail(FRAG_EINVAL, "item %u has a NULL buffer", i);
         }
-        const uint64_t tiles = (uint64_t)j.tiles_x * j.tiles_y;
-        const uint64_t cost = tiles * (uint64_t)j.tile_w * j.tile_h;
-        v.emplace_back(cost, j);
-        b.smem = std::max(b.smem, job_smem(j, fwd));
-        const uint32_t c = plan->ctas_per_sm;
-        if (c != 0)
-            b.min_ctas = b.min_ctas == 0 ? c : std::min(b.min_ctas, c);
+        v.emplace_back(H * (uint64_t)b.W, b);
     }
-    std::stable_sort(v.begin(), v.end(),
-                     [](const std::pair<uint64_t, Job> &a, const std::pair<uint64_t, Job> &c) {
-                         return a.first > c.first;
-                     });
-    b.jobs.clear();
-    b.tile_start.assign(1, 0);
+    std::stable_sort(v.begin(), v.end(), [](const std::pair<uint64_t, Buf> &a,
+                                            const std::pair<uint64_t, Buf> &c) {
+        return a.first > c.first;
+    });
+    // waves by scratch budget
+    uint64_t used = 0;
+    uint32_t wave = 0;
     for (auto &p : v) {
-        b.jobs.push_back(p.second);
-        b.tile_start.push_back(b.tile_start.back() + (uint64_t)p.second.tiles_x * p.second.tiles_y);
+        uint64_t off1 = 0;
+        const uint64_t sb = scratch_bytes(p.second.H, p.second.W, p.second.L, &off1);
+        if (used > 0 && used + sb > kScratchBudget) {
+            ++wave;
+            used = 0;
+        }
+        bp.bufs.push_back(p.second);
+        bp.scr_off.push_back(used);
+        bp.wave_of.push_back(wave);
+        used += sb;
+        bp.scratch = std::max(bp.scratch, used);
+    }
+    bp.waves.assign(bp.bufs.empty() ? 0 : wave + 1, Wave());
+    uint32_t maxL = 0;
+    for (auto &b : bp.bufs)
+        maxL = std::max(maxL, b.L);
+    for (auto &wv : bp.waves) {
+        wv.fwd = fwd;
+        wv.levels.assign(maxL, LevelList());
     }
     return FRAG_OK;
 }
 
-size_t batch_bytes(const BatchHost &b, size_t *off_start, size_t *off_queue)
+// fill the level lists once the scratch base is known; lay out descriptors
+void fill_batch(BatchPlan &bp, uint8_t *scratch_base, size_t desc_base_off)
 {
-    const size_t jb = (b.jobs.size() * sizeof(Job) + 255) / 256 * 256;
-    const size_t sb = (b.tile_start.size() * sizeof(uint64_t) + 255) / 256 * 256;
-    *off_start = jb;
-    *off_queue = jb + sb;
-    return jb + sb + 256;
+    for (size_t i = 0; i < bp.bufs.size(); ++i) {
+        Buf &b = bp.bufs[i];
+        uint64_t off1 = 0;
+        scratch_bytes(b.H, b.W, b.L, &off1);
+        b.scr[0] = scratch_base + bp.scr_off[i];
+        b.scr[1] = scratch_base + bp.scr_off[i] + off1;
+        Wave &wv = bp.waves[bp.wave_of[i]];
+        for (uint32_t l = 1; l <= b.L; ++l) {
+            const uint32_t slot = wv.fwd ? l - 1 : (uint32_t)wv.levels.size() - l;
+            LevelList &ll = wv.levels[slot];
+            ll.jobs.push_back(wv.fwd ? protect_level(b, l, kSegPairs) : recover_level(b, l, kSegPairs));
+        }
+    }
+    size_t off = desc_base_off;
+    uint32_t q = 0;
+    for (auto &wv : bp.waves)
+        for (auto &ll : wv.levels) {
+            ll.start.assign(1, 0);
+            for (auto &j : ll.jobs)
+                ll.start.push_back(ll.start.back() + (uint64_t)j.strips * j.segs);
+            ll.job_off = off;
+            off += align256(ll.jobs.size() * sizeof(LevelJob));
+            ll.start_off = off;
+            off += align256(ll.start.size() * sizeof(uint64_t));
+            ll.queue_index = q++;
+        }
+    bp.queues = q;
+    bp.desc_bytes = off - desc_base_off + align256(sizeof(unsigned long long) * std::max(q, 1u));
 }
+
+// device memory: [scratch][descriptors][queue heads]
+frag_status upload_batch(BatchPlan &bp, uint8_t *mem, cudaStream_t s, bool async)
+{
+    const size_t desc0 = align256(bp.scratch);
+    std::vector<uint8_t> host(bp.desc_bytes, 0);
+    for (auto &wv : bp.waves)
+        for (auto &ll : wv.levels) {
+            if (!ll.jobs.empty())
+                std::memcpy(host.data() + (ll.job_off - desc0), ll.jobs.data(), ll.jobs.size() * sizeof(LevelJob));
+            std::memcpy(host.data() + (ll.start_off - desc0), ll.start.data(), ll.start.size() * sizeof(uint64_t));
+        }
+    cudaError_t e = async ? cudaMemcpyAsync(mem + desc0, host.data(), host.size(), cudaMemcpyHostToDevice, s)
+                          : cudaMemcpy(mem + desc0, host.data(), host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "batch descriptor upload");
+    return FRAG_OK;
+}
+
+size_t queue_off(const BatchPlan &bp) { return align256(bp.scratch) + bp.desc_bytes - align256(sizeof(unsigned long long) * std::max(bp.queues, 1u)); }
+
+frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, const uint32_t *rk,
+                         cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(mem + queue_off(bp), 0, sizeof(unsigned long long) * std::max(bp.queues, 1u), s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "queue reset");
+    for (const auto &wv : bp.waves)
+        for (const auto &ll : wv.levels) {
+            if (ll.jobs.empty())
+                continue;
+            LevelWork w;
+            std::memset(&w, 0, sizeof(w));
+            w.jobs = (const LevelJob *)(mem + ll.job_off);
+            w.unit_start = (const uint64_t *)(mem + ll.start_off);
+            w.njobs = (uint32_t)ll.jobs.size();
+            w.total_units = ll.start.back();
+            w.queue = (unsigned long long *)(mem + queue_off(bp)) + ll.queue_index;
+            w.aes_tables = d.tables;
+            w.round_keys = rk;
+            w.err = d.err;
+            uint32_t grid = 0;
+            frag_status st = level_grid(d, wv.fwd, w.total_units, &grid);
+            if (st != FRAG_OK)
+                return st;
+            if ((e = frag::launch_level(wv.fwd, w, grid, s)) != cudaSuccess)
+                return cuda_fail(e, "batch launch");
+        }
+    return FRAG_OK;
+}
+
+size_t batch_mem_bytes(const BatchPlan &bp) { return align256(bp.scratch) + bp.desc_bytes; }
 
 frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, uint32_t count,
                            frag_key key, cudaStream_t s)
@@ -377,12 +619,10 @@ frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, 
         return FRAG_OK;
     if ((fwd ? (const void *)pi : (const void *)ri) == nullptr)
         return fail(FRAG_EINVAL, "items is NULL");
-    BatchHost b;
-    frag_status st = build_batch(fwd, pi, ri, count, b);
-    if (st != FRAG_OK)
+    BatchPlan bp;
+    frag_status st = plan_batch(fwd, pi, ri, count, bp);
+    if (st != FRAG_OK || bp.bufs.empty())
         return st;
-    if (b.jobs.empty())
-        return FRAG_OK;
     DeviceState *d = nullptr;
     int dev = 0;
     if ((st = device_state(&d, &dev)) != FRAG_OK)
@@ -390,39 +630,18 @@ frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, 
     const uint32_t *rk = nullptr;
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
-    size_t off_start = 0, off_queue = 0;
-    const size_t bytes = batch_bytes(b, &off_start, &off_queue);
+    // descriptor offsets do not depend on the scratch base: size on a copy
+    BatchPlan sizing = bp;
+    fill_batch(sizing, nullptr, align256(bp.scratch));
     uint8_t *mem = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&mem, bytes, s);
+    cudaError_t e = cudaMallocAsync((void **)&mem, batch_mem_bytes(sizing), s);
     if (e != cudaSuccess)
-        return cuda_fail(e, "cudaMallocAsync(batch queue)");
-    // pageable sources: each copy returns once its source has been staged
-    e = cudaMemcpyAsync(mem, b.jobs.data(), b.jobs.size() * sizeof(Job), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(mem + off_start, b.tile_start.data(),
-                            b.tile_start.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(mem + off_queue, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(mem, s);
-        return cuda_fail(e, "batch queue upload");
-    }
-    Work w;
-    base_work(w, *d, rk);
-    w.jobs = (const Job *)mem;
-    w.tile_start = (const uint64_t *)(mem + off_start);
-    w.njobs = (uint32_t)b.jobs.size();
-    w.total_tiles = b.tile_start.back();
-    w.queue = (unsigned long long *)(mem + off_queue);
-    const size_t smem = b.smem;
-    uint32_t grid = 0;
-    st = launch_shape(*d, fwd, smem, b.min_ctas, w.total_tiles, &grid);
-    if (st == FRAG_OK) {
-        e = frag::launch_tiles(fwd, w, grid, smem, s);
-        if (e != cudaSuccess)
-            st = cuda_fail(e, "batch launch");
-    }
-    cudaFreeAsync(mem, s); // released once the launch has completed
+        return cuda_fail(e, "cudaMallocAsync(batch)");
+    fill_batch(bp, mem, align256(bp.scratch));
+    st = upload_batch(bp, mem, s, true);
+    if (st == FRAG_OK)
+        st = launch_batch(bp, mem, *d, rk, s);
+    cudaFreeAsync(mem, s); // released once the launches have completed
     return st;
 }
 
@@ -434,50 +653,30 @@ frag_status create_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, ui
     *out = nullptr;
     if ((fwd ? (const void *)pi : (const void *)ri) == nullptr && count != 0)
         return fail(FRAG_EINVAL, "items is NULL");
-    BatchHost b;
-    frag_status st = build_batch(fwd, pi, ri, count, b);
-    if (st != FRAG_OK)
-        return st;
-    DeviceState *d = nullptr;
-    int dev = 0;
-    if ((st = device_state(&d, &dev)) != FRAG_OK)
-        return st;
     frag_batch bt = new (std::nothrow) frag_batch_s();
     if (bt == nullptr)
         return fail(FRAG_ENOMEM, "out of host memory");
-    bt->device = dev;
-    bt->fwd = fwd;
-    base_work(bt->work, *d, nullptr);
-    if (!b.jobs.empty()) {
-        size_t off_start = 0, off_queue = 0;
-        const size_t bytes = batch_bytes(b, &off_start, &off_queue);
-        cudaError_t e = cudaMalloc(&bt->d_mem, bytes);
+    frag_status st = plan_batch(fwd, pi, ri, count, bt->bp);
+    DeviceState *d = nullptr;
+    if (st == FRAG_OK)
+        st = device_state(&d, &bt->device);
+    if (st == FRAG_OK && !bt->bp.bufs.empty()) {
+        BatchPlan sizing = bt->bp;
+        fill_batch(sizing, nullptr, align256(sizing.scratch));
+        cudaError_t e = cudaMalloc((void **)&bt->mem, batch_mem_bytes(sizing));
         if (e != cudaSuccess) {
-            delete bt;
-            return cuda_fail(e, "cudaMalloc(batch queue)");
+            bt->mem = nullptr;
+            st = cuda_fail(e, "cudaMalloc(batch)");
+        } else {
+            fill_batch(bt->bp, bt->mem, align256(bt->bp.scratch));
+            st = upload_batch(bt->bp, bt->mem, nullptr, false);
         }
-        uint8_t *mem = (uint8_t *)bt->d_mem;
-        e = cudaMemcpy(mem, b.jobs.data(), b.jobs.size() * sizeof(Job), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(mem + off_start, b.tile_start.data(),
-                           b.tile_start.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            cudaFree(bt->d_mem);
-            delete bt;
-            return cuda_fail(e, "batch queue upload");
-        }
-        bt->work.jobs = (const Job *)mem;
-        bt->work.tile_start = (const uint64_t *)(mem + off_start);
-        bt->work.njobs = (uint32_t)b.jobs.size();
-        bt->work.total_tiles = b.tile_start.back();
-        bt->work.queue = (unsigned long long *)(mem + off_queue);
-        bt->smem = b.smem;
-        if ((st = launch_shape(*d, fwd, bt->smem, b.min_ctas, bt->work.total_tiles, &bt->grid)) !=
-            FRAG_OK) {
-            cudaFree(bt->d_mem);
-            delete bt;
-            return st;
-        }
+    }
+    if (st != FRAG_OK) {
+        if (bt->mem)
+            cudaFree(bt->mem);
+        delete bt;
+        return st;
     }
     *out = bt;
     return FRAG_OK;
@@ -650,13 +849,20 @@ frag_status frag_protect(frag_plan plan, frag_key key, uint64_t nonce, const voi
         return FRAG_OK;
     if (d_in == nullptr || d_private == nullptr || d_public == nullptr)
         return fail(FRAG_EINVAL, "NULL buffer");
-    Job j;
-    if ((st = fill_job(plan, nonce, nbytes, j)) != FRAG_OK)
-        return st;
-    j.in = (const uint8_t *)d_in;
-    j.priv = (uint8_t *)d_private;
-    j.pub = (uint8_t *)d_public;
-    return launch_single(true, plan, key, j, (cudaStream_t)stream);
+    const uint64_t H = rows_for(nbytes, plan->width, plan->levels);
+    if (H > 0xFFFFFFFFull)
+        return fail(FRAG_EINVAL, "buffer too tall for width %u", plan->width);
+    Buf b;
+    std::memset(&b, 0, sizeof(b));
+    b.W = plan->width;
+    b.L = plan->levels;
+    b.H = (uint32_t)H;
+    b.n = nbytes;
+    b.nonce = nonce;
+    b.in = (const uint8_t *)d_in;
+    b.priv = (uint8_t *)d_private;
+    b.pub = (uint8_t *)d_public;
+    return run_single(true, plan, key, b, (cudaStream_t)stream);
 }
 
 frag_status frag_recover(frag_plan plan, frag_key key, uint64_t nonce, const void *d_private,
@@ -671,13 +877,20 @@ frag_status frag_recover(frag_plan plan, frag_key key, uint64_t nonce, const voi
         return FRAG_OK;
     if (d_private == nullptr || d_public == nullptr || d_out == nullptr)
         return fail(FRAG_EINVAL, "NULL buffer");
-    Job j;
-    if ((st = fill_job(plan, nonce, nbytes, j)) != FRAG_OK)
-        return st;
-    j.priv_in = (const uint8_t *)d_private;
-    j.pub_in = (const uint8_t *)d_public;
-    j.out = (uint8_t *)d_out;
-    return launch_single(false, plan, key, j, (cudaStream_t)stream);
+    const uint64_t H = rows_for(nbytes, plan->width, plan->levels);
+    if (H > 0xFFFFFFFFull)
+        return fail(FRAG_EINVAL, "buffer too tall for width %u", plan->width);
+    Buf b;
+    std::memset(&b, 0, sizeof(b));
+    b.W = plan->width;
+    b.L = plan->levels;
+    b.H = (uint32_t)H;
+    b.n = nbytes;
+    b.nonce = nonce;
+    b.priv_in = (const uint8_t *)d_private;
+    b.pub_in = (const uint8_t *)d_public;
+    b.out = (uint8_t *)d_out;
+    return run_single(false, plan, key, b, (cudaStream_t)stream);
 }
 
 frag_status frag_protect_host(frag_plan plan, frag_key key, uint64_t nonce, const void *h_in,
@@ -779,7 +992,7 @@ frag_status frag_batch_run(frag_batch batch, frag_key key, frag_stream stream)
 {
     if (batch == nullptr || key == nullptr)
         return fail(FRAG_EINVAL, "NULL argument");
-    if (batch->work.total_tiles == 0)
+    if (batch->bp.bufs.empty())
         return FRAG_OK;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -788,26 +1001,22 @@ frag_status frag_batch_run(frag_batch batch, frag_key key, frag_stream stream)
     if (dev != batch->device)
         return fail(FRAG_EINVAL, "batch was created on device %d, current is %d", batch->device,
                     dev);
-    const uint32_t *rk = nullptr;
-    frag_status st = key_on_device(key, dev, &rk);
+    DeviceState *d = nullptr;
+    frag_status st = device_state(&d, nullptr);
     if (st != FRAG_OK)
         return st;
-    Work w = batch->work;
-    w.round_keys = rk;
-    cudaStream_t s = (cudaStream_t)stream;
-    if ((e = cudaMemsetAsync(w.queue, 0, sizeof(unsigned long long), s)) != cudaSuccess)
-        return cuda_fail(e, "queue reset");
-    if ((e = frag::launch_tiles(batch->fwd, w, batch->grid, batch->smem, s)) != cudaSuccess)
-        return cuda_fail(e, "batch launch");
-    return FRAG_OK;
+    const uint32_t *rk = nullptr;
+    if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
+        return st;
+    return launch_batch(batch->bp, batch->mem, *d, rk, (cudaStream_t)stream);
 }
 
 frag_status frag_batch_destroy(frag_batch batch)
 {
     if (batch == nullptr)
         return FRAG_OK;
-    if (batch->d_mem)
-        cudaFree(batch->d_mem);
+    if (batch->mem)
+        cudaFree(batch->mem);
     delete batch;
     return FRAG_OK;
 }

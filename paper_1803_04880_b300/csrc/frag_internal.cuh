@@ -32,6 +32,37 @@ struct Job {
     uint32_t path;    // 0: generic tile body, 1: row/column-pass body (L <= 3)
 };
 
+// One level of one buffer for the streaming level kernels.  Forward: the
+// level-(l-1) image `src` (bytes at l = 1, else packed LL pairs) gives the
+// level-l bands and LL_l (packed pairs in scratch, or the private fragment at
+// the last level).  Inverse: LL_l (`ll_in`: packed pairs, or the private
+// fragment at the top level) and the bands give LL_{l-1} (packed pairs) or
+// the bytes (`out`, l = 1).
+struct LevelJob {
+    const uint8_t *src;
+    uint8_t *hl, *lh, *hh; // band bases of level l
+    uint8_t *ll;           // forward output
+    const uint8_t *ll_in;  // inverse input
+    uint8_t *out;          // inverse output
+    uint64_t n;            // bytes of the buffer (level-1 source / output)
+    uint64_t nonce;
+    uint32_t Ws, Hs;       // level-(l-1) image
+    uint32_t strips, segs, seg_pairs;
+    uint8_t src_bytes, final_level, top_level, out_bytes;
+};
+
+struct LevelWork {
+    LevelJob single;
+    const LevelJob *jobs;
+    const uint64_t *unit_start; // exclusive prefix of units per job (njobs + 1)
+    uint32_t njobs;
+    uint64_t total_units;
+    unsigned long long *queue;
+    const uint32_t *aes_tables;
+    const uint32_t *round_keys;
+    int *err;
+};
+
 // Launch-wide description of where jobs and tiles come from.
 struct Work {
     Job single;                 // used when jobs == nullptr
@@ -72,6 +103,11 @@ __host__ __device__ inline uint32_t halo_hi_inv(uint32_t L) { return 2u << L; }
 // host helpers (frag_api.cu)
 const uint32_t *host_aes_words();                             // kAesWords words
 void host_expand_key(const uint8_t key[16], uint32_t rk[44]); // FIPS-197 key schedule
+
+// streaming level kernels (stream_kernels.cu)
+cudaError_t launch_level(bool fwd, const LevelWork &w, uint32_t grid, cudaStream_t stream);
+cudaError_t level_occupancy(bool fwd, int *blocks_per_sm);
+constexpr int kStripCols = 240; // level-(l-1) columns owned by one warp strip
 
 // kernels (tile_kernels.cu)
 constexpr uint32_t kFastTile = 256;   // owned tile side of the row/column-pass body

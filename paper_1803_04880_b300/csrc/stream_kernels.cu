@@ -1,0 +1,634 @@
+// stream_kernels.cu -- one LeGall 5/3 level per launch, streamed by warps.
+//
+// A launch runs level l of one or many buffers.  Its work units are
+// (buffer, strip, segment): a warp takes a strip of 256 columns of the
+// level-(l-1) image and a segment of rows, and streams down the rows:
+//
+//   forward  lane t loads 8 consecutive samples of a row, lifts the row
+//            (Eq. 5.1 predict, then Eq. 5.2 update; rows before columns,
+//            Sec. 5.2.2) with its neighbours' samples taken by warp shuffles,
+//            and packs its 4 low and 4 high results two per 32-bit word; the
+//            column lifting then runs on those packed pairs in registers,
+//            two row pairs of state per lane.  HL_l / LH_l / HH_l go straight
+//            to the public fragment, LL_l to a scratch array (packed pairs)
+//            or, at the last level, through AES-128-CTR to the private
+//            fragment.
+//   inverse  the exact reverse: the column inverse (undo Eq. 5.2, then Eq. 5.1)
+//            on packed pairs read from LL_l (scratch, or the decrypted
+//            private fragment at the top level) and the detail bands, then
+//            the row inverse with shuffles; the result is LL_{l-1} (scratch)
+//            or the recovered bytes.
+//
+// Lanes 0 and 31 of a warp only supply neighbours: lanes 1..30 own the
+// strip's 240 columns, so strips advance by 240 and no value ever needs a
+// lane outside the warp.  Rows above a segment are re-lifted (two rows) to
+// restart the column stream.  The symmetric extension (x[-1] = x[1],
+// x[m] = x[m-2], hence d[-1] = d[0]) applies only at the image borders.
+//
+// Packed pairs: each 16-bit half holds v + 0x4000 (|v| < 2^14); the halves of
+// (A + B) never carry into each other, so both floors of a lifting step take
+// one add, one shift and one mask for two columns.
+#include "frag_internal.cuh"
+
+namespace frag {
+
+struct AesTab {
+    uint32_t T[4][256];
+    uint32_t S[256];
+    uint32_t rk[44];
+};
+
+// AES-128 encryption of the counter block nonce || blk (FIPS-197 cipher,
+// 32-bit table form), big-endian words.
+__device__ __forceinline__ void aes_block(const AesTab &a, uint64_t nonce, uint64_t blk,
+                                          uint32_t ks[4])
+{
+    uint32_t s0 = (uint32_t)(nonce >> 32) ^ a.rk[0];
+    uint32_t s1 = (uint32_t)nonce ^ a.rk[1];
+    uint32_t s2 = (uint32_t)(blk >> 32) ^ a.rk[2];
+    uint32_t s3 = (uint32_t)blk ^ a.rk[3];
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        const uint32_t t0 = a.T[0][s0 >> 24] ^ a.T[1][(s1 >> 16) & 255] ^
+                            a.T[2][(s2 >> 8) & 255] ^ a.T[3][s3 & 255] ^ a.rk[4 * r];
+        const uint32_t t1 = a.T[0][s1 >> 24] ^ a.T[1][(s2 >> 16) & 255] ^
+                            a.T[2][(s3 >> 8) & 255] ^ a.T[3][s0 & 255] ^ a.rk[4 * r + 1];
+        const uint32_t t2 = a.T[0][s2 >> 24] ^ a.T[1][(s3 >> 16) & 255] ^
+                            a.T[2][(s0 >> 8) & 255] ^ a.T[3][s1 & 255] ^ a.rk[4 * r + 2];
+        const uint32_t t3 = a.T[0][s3 >> 24] ^ a.T[1][(s0 >> 16) & 255] ^
+                            a.T[2][(s1 >> 8) & 255] ^ a.T[3][s2 & 255] ^ a.rk[4 * r + 3];
+        s0 = t0;
+        s1 = t1;
+        s2 = t2;
+        s3 = t3;
+    }
+    ks[0] = ((a.S[s0 >> 24] << 24) | (a.S[(s1 >> 16) & 255] << 16) |
+             (a.S[(s2 >> 8) & 255] << 8) | a.S[s3 & 255]) ^ a.rk[40];
+    ks[1] = ((a.S[s1 >> 24] << 24) | (a.S[(s2 >> 16) & 255] << 16) |
+             (a.S[(s3 >> 8) & 255] << 8) | a.S[s0 & 255]) ^ a.rk[41];
+    ks[2] = ((a.S[s2 >> 24] << 24) | (a.S[(s3 >> 16) & 255] << 16) |
+             (a.S[(s0 >> 8) & 255] << 8) | a.S[s1 & 255]) ^ a.rk[42];
+    ks[3] = ((a.S[s3 >> 24] << 24) | (a.S[(s0 >> 16) & 255] << 16) |
+             (a.S[(s1 >> 8) & 255] << 8) | a.S[s2 & 255]) ^ a.rk[43];
+}
+
+// Keystream bytes [o, o + 8) (o even), as two little-endian words.  The
+// bytes come from the 32-byte stream block(o / 16) || block(o / 16 + 1).
+__device__ __forceinline__ void keystream8(const AesTab &a, uint64_t nonce, uint64_t o,
+                                           uint32_t &k0, uint32_t &k1)
+{
+    uint32_t ks[4], kb[4] = {0u, 0u, 0u, 0u};
+    const uint64_t b0 = o >> 4;
+    const int m = (int)(o & 15);
+    aes_block(a, nonce, b0, ks);
+    if (m > 8)
+        aes_block(a, nonce, b0 + 1, kb);
+    // little-endian words of the 32-byte stream
+    const uint32_t w0 = __byte_perm(ks[0], 0, 0x0123), w1 = __byte_perm(ks[1], 0, 0x0123);
+    const uint32_t w2 = __byte_perm(ks[2], 0, 0x0123), w3 = __byte_perm(ks[3], 0, 0x0123);
+    const uint32_t w4 = __byte_perm(kb[0], 0, 0x0123), w5 = __byte_perm(kb[1], 0, 0x0123);
+    const int wi = m >> 2, sh = 8 * (m & 3);
+    const uint32_t p0 = wi == 0 ? w0 : (wi == 1 ? w1 : (wi == 2 ? w2 : w3));
+    const uint32_t p1 = wi == 0 ? w1 : (wi == 1 ? w2 : (wi == 2 ? w3 : w4));
+    const uint32_t p2 = wi == 0 ? w2 : (wi == 1 ? w3 : (wi == 2 ? w4 : w5));
+    k0 = __funnelshift_r(p0, p1, sh);
+    k1 = __funnelshift_r(p1, p2, sh);
+}
+
+namespace strm {
+
+constexpr uint32_t kB2 = 0x40004000u;
+
+__device__ __forceinline__ uint32_t pack2(int lo, int hi)
+{
+    return __byte_perm((uint32_t)lo, (uint32_t)hi, 0x5410);
+}
+__device__ __forceinline__ uint32_t pavg(uint32_t a, uint32_t b) { return ((a + b) >> 1) & 0x7fff7fffu; }
+__device__ __forceinline__ uint32_t pq4(uint32_t a, uint32_t b)
+{
+    return ((a + b + 0x00020002u) >> 2) & 0x3fff3fffu;
+}
+__device__ __forceinline__ uint32_t to_i16x2(uint32_t w) { return (w + kB2) ^ 0x80008000u; }
+__device__ __forceinline__ uint32_t from_i16x2(uint32_t w) { return (w ^ 0x80008000u) - kB2; }
+__device__ __forceinline__ int lo16(uint32_t w) { return (int)(w & 0xffffu); }
+__device__ __forceinline__ int hi16(uint32_t w) { return (int)(w >> 16); }
+
+// ---------------------------------------------------------------------------
+// raw row loads (issued ahead of use)
+// ---------------------------------------------------------------------------
+struct Raw {
+    uint32_t w[4];
+};
+
+// 8 source samples of row r at columns c .. c+7 of the level-(l-1) image.
+// Byte sources: samples past n (or outside the image) are 0; packed sources:
+// outside the image they are the biased 0 (0x4000).
+template <bool BYTES>
+__device__ __forceinline__ Raw load_row(const LevelJob &j, int r, int c, bool vec)
+{
+    Raw raw;
+    if (BYTES) {
+        raw.w[2] = raw.w[3] = 0;
+        const uint64_t base = (uint64_t)r * (uint64_t)j.Ws;
+        if (r < (int)j.Hs && vec && c >= 0 && c + 8 <= (int)j.Ws && base + (uint64_t)c + 8 <= j.n) {
+            const uint2 t = __ldg(reinterpret_cast<const uint2 *>(j.src + base + c));
+            raw.w[0] = t.x;
+            raw.w[1] = t.y;
+        } else {
+            uint32_t b[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int cc = c + i;
+                b[i] = (r < (int)j.Hs && cc >= 0 && cc < (int)j.Ws && base + (uint64_t)cc < j.n)
+                           ? (uint32_t)__ldg(j.src + base + (uint64_t)cc)
+                           : 0u;
+            }
+            raw.w[0] = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+            raw.w[1] = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+        }
+    } else {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(j.src);
+        const int wpr = (int)j.Ws / 2, w0 = c >> 1;
+        const uint64_t base = (uint64_t)r * (uint64_t)wpr;
+        if (r < (int)j.Hs && vec && c >= 0 && c + 8 <= (int)j.Ws) {
+            const uint4 t = __ldg(reinterpret_cast<const uint4 *>(src + base + w0));
+            raw.w[0] = t.x;
+            raw.w[1] = t.y;
+            raw.w[2] = t.z;
+            raw.w[3] = t.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int ww = w0 + i;
+                raw.w[i] = (r < (int)j.Hs && ww >= 0 && ww < wpr) ? __ldg(src + base + ww) : kB2;
+            }
+        }
+    }
+    return raw;
+}
+
+// Lift one row along its length (Eq. 5.1 then Eq. 5.2) for the lane's four
+// pairs at image columns c .. c+7.  Returns the packed biased pairs:
+// P[0], P[1] = low (s) values, P[2], P[3] = high (d) values.
+template <bool BYTES>
+__device__ __forceinline__ void lift_row(const Raw &raw, int c, int Ws, bool edge, uint32_t (&P)[4])
+{
+    int x[8];
+    if (BYTES) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            x[i] = (int)((raw.w[i >> 2] >> (8 * (i & 3))) & 255u);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            x[2 * i] = lo16(raw.w[i]);
+            x[2 * i + 1] = hi16(raw.w[i]);
+        }
+    }
+    const int xn = __shfl_down_sync(0xffffffffu, x[0], 1); // next lane's first sample
+    int d[4], s[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int xr = i < 3 ? x[2 * i + 2] : xn;
+        if (edge && c + 2 * i + 2 == Ws) // x[m] = x[m-2]
+            xr = x[2 * i];
+        d[i] = x[2 * i + 1] - ((x[2 * i] + xr) >> 1);
+    }
+    int dm = __shfl_up_sync(0xffffffffu, d[3], 1); // previous lane's last d
+    if (c == 0)
+        dm = d[0]; // d[-1] = d[0]
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        s[i] = x[2 * i] + (((i ? d[i - 1] : dm) + d[i] + 2) >> 2);
+    // bytes give unbiased s; packed sources give biased s; d is unbiased
+    if (BYTES) {
+        P[0] = from_i16x2(pack2(s[0], s[1]));
+        P[1] = from_i16x2(pack2(s[2], s[3]));
+    } else {
+        P[0] = pack2(s[0], s[1]);
+        P[1] = pack2(s[2], s[3]);
+    }
+    P[2] = from_i16x2(pack2(d[0], d[1]));
+    P[3] = from_i16x2(pack2(d[2], d[3]));
+}
+
+// store 4 int16 values (2 packed biased pairs) to a band at (y, x .. x+3)
+__device__ __forceinline__ void store4(uint8_t *band, int Wl, int y, int x, uint32_t a, uint32_t b,
+                                       int nval)
+{
+    uint8_t *dst = band + 2ull * ((uint64_t)y * (uint64_t)Wl + (uint64_t)x);
+    const uint32_t u = to_i16x2(a), v = to_i16x2(b);
+    if (nval == 4 && ((uintptr_t)dst & 7u) == 0) {
+        *reinterpret_cast<uint2 *>(dst) = make_uint2(u, v);
+    } else {
+        const uint32_t h[4] = {u & 0xffffu, u >> 16, v & 0xffffu, v >> 16};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (i < nval) {
+                dst[2 * i] = (uint8_t)h[i];
+                dst[2 * i + 1] = (uint8_t)(h[i] >> 8);
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// forward unit: one strip x one segment of level l
+// ---------------------------------------------------------------------------
+template <bool BYTES, bool FINAL>
+__device__ void fwd_unit(const LevelJob &j, int sx, int sy, const AesTab &aes, int lane)
+{
+    const int Ws = (int)j.Ws, Hs = (int)j.Hs;
+    const int c = 240 * sx - 8 + 8 * lane;        // first column of this lane
+    const int q0 = sy * (int)j.seg_pairs;
+    const int q1 = min(q0 + (int)j.seg_pairs, Hs / 2);
+    const bool edge = (240 * sx + 248 >= Ws);      // strip reaches the right border
+    const bool vec = BYTES ? (((j.Ws & 7u) == 0) && (((uintptr_t)j.src & 7u) == 0))
+                           : (((j.Ws & 7u) == 0) && (((uintptr_t)j.src & 15u) == 0));
+    const int Wl = Ws / 2;
+    const int x = c / 2;                            // level-l column of the lane's first value
+    const bool own = lane >= 1 && lane <= 30 && x < Wl;
+    const int nval = min(4, Wl - x);
+
+    uint32_t e0[4], dp[4];
+    {
+        uint32_t a[4], o[4];
+        const Raw r0 = load_row<BYTES>(j, 2 * q0, c, vec);
+        const Raw rm2 = load_row<BYTES>(j, max(2 * q0 - 2, 0), c, vec);
+        const Raw rm1 = load_row<BYTES>(j, max(2 * q0 - 1, 0), c, vec);
+        lift_row<BYTES>(r0, c, Ws, edge, e0);
+        lift_row<BYTES>(rm2, c, Ws, edge, a);
+        lift_row<BYTES>(rm1, c, Ws, edge, o);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            dp[i] = o[i] - pavg(a[i], e0[i]) + kB2;
+    }
+    Raw n1 = load_row<BYTES>(j, 2 * q0 + 1, c, vec);
+    Raw n2 = load_row<BYTES>(j, 2 * q0 + 2, c, vec);
+    for (int q = q0; q < q1; ++q) {
+        const Raw c1 = n1, c2 = n2;
+        if (q + 1 < q1) {
+            n1 = load_row<BYTES>(j, 2 * q + 3, c, vec);
+            n2 = load_row<BYTES>(j, 2 * q + 4, c, vec);
+        }
+        uint32_t o[4], e1[4], dv[4], sv[4];
+        lift_row<BYTES>(c1, c, Ws, edge, o);
+        if (2 * q + 2 == Hs) { // x[m] = x[m-2] at the bottom border
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                e1[i] = e0[i];
+        } else {
+            lift_row<BYTES>(c2, c, Ws, edge, e1);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            dv[i] = o[i] - pavg(e0[i], e1[i]) + kB2; // Eq. 5.1 down the columns
+        if (q == 0) {                                // d[-1] = d[0] at the top border
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                dp[i] = dv[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            sv[i] = e0[i] + pq4(dp[i], dv[i]) - 0x20002000u; // Eq. 5.2 down the columns
+        if (own) {
+            // sv[0..1] = LL, sv[2..3] = HL, dv[0..1] = LH, dv[2..3] = HH
+            store4(j.hl, Wl, q, x, sv[2], sv[3], nval);
+            store4(j.lh, Wl, q, x, dv[0], dv[1], nval);
+            store4(j.hh, Wl, q, x, dv[2], dv[3], nval);
+            if (!FINAL) {
+                uint32_t *ll = reinterpret_cast<uint32_t *>(j.ll) + (uint64_t)q * (uint64_t)(Wl / 2) + x / 2;
+                if (nval == 4 && ((uintptr_t)ll & 7u) == 0) {
+                    *reinterpret_cast<uint2 *>(ll) = make_uint2(sv[0], sv[1]);
+                } else {
+                    ll[0] = sv[0];
+                    if (nval > 2)
+                        ll[1] = sv[1];
+                }
+            }
+        }
+        if (FINAL) {
+            // private fragment: LL - 128 as int16 LE, XOR AES-CTR keystream
+            const uint64_t o8 = 2ull * ((uint64_t)q * (uint64_t)Wl + (uint64_t)x);
+            uint32_t k0 = 0, k1 = 0;
+            if (own)
+                keystream8(aes, j.nonce, o8, k0, k1);
+            if (own) {
+                const uint32_t u = to_i16x2(sv[0] - 0x00800080u) ^ k0;
+                const uint32_t v = to_i16x2(sv[1] - 0x00800080u) ^ k1;
+                uint8_t *dst = j.ll + o8;
+                if (nval == 4 && ((uintptr_t)dst & 7u) == 0) {
+                    *reinterpret_cast<uint2 *>(dst) = make_uint2(u, v);
+                } else {
+                    const uint32_t bytes[2] = {u, v};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (i < 2 * nval)
+                            dst[i] = (uint8_t)(bytes[i >> 2] >> (8 * (i & 3)));
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            e0[i] = e1[i];
+            dp[i] = dv[i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// inverse unit
+// ---------------------------------------------------------------------------
+struct Coef {
+    uint32_t sl[2], dl[2], sh[2], dh[2]; // low s (LL), low d (LH), high s (HL), high d (HH)
+};
+
+__device__ __forceinline__ void load4(const uint8_t *band, int Hl, int Wl, int y, int x, bool vec,
+                                      uint32_t &a, uint32_t &b)
+{
+    if (y >= Hl || x < 0 || x >= Wl) {
+        a = b = kB2;
+        return;
+    }
+    const uint8_t *p = band + 2ull * ((uint64_t)y * (uint64_t)Wl + (uint64_t)x);
+    if (vec && x + 4 <= Wl && ((uintptr_t)p & 7u) == 0) {
+        const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+        a = from_i16x2(t.x);
+        b = from_i16x2(t.y);
+    } else {
+        uint32_t h[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            h[i] = (x + i < Wl) ? ((uint32_t)__ldg(p + 2 * i) | ((uint32_t)__ldg(p + 2 * i + 1) << 8))
+                                : 0u;
+        a = from_i16x2(h[0] | (h[1] << 16));
+        b = from_i16x2(h[2] | (h[3] << 16));
+    }
+}
+
+template <bool TOP>
+__device__ __forceinline__ Coef load_coef(const LevelJob &j, int k, int x, bool vec, const AesTab &aes)
+{
+    const int Hl = (int)j.Hs / 2, Wl = (int)j.Ws / 2;
+    Coef cf;
+    load4(j.lh, Hl, Wl, k, x, vec, cf.dl[0], cf.dl[1]);
+    load4(j.hl, Hl, Wl, k, x, vec, cf.sh[0], cf.sh[1]);
+    load4(j.hh, Hl, Wl, k, x, vec, cf.dh[0], cf.dh[1]);
+    if (TOP) {
+        // decrypt LL_L from the private fragment, add back 128
+        cf.sl[0] = cf.sl[1] = kB2;
+        if (k < Hl && x >= 0 && x < Wl) {
+            const uint64_t o8 = 2ull * ((uint64_t)k * (uint64_t)Wl + (uint64_t)x);
+            uint32_t k0, k1;
+            keystream8(aes, j.nonce, o8, k0, k1);
+            const uint8_t *p = j.ll_in + o8;
+            uint32_t c0, c1;
+            if (vec && x + 4 <= Wl && ((uintptr_t)p & 7u) == 0) {
+                const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+                c0 = t.x;
+                c1 = t.y;
+            } else {
+                uint32_t b[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    b[i] = (x + (i >> 1) < Wl) ? (uint32_t)__ldg(p + i) : 0u;
+                c0 = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+                c1 = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+            }
+            cf.sl[0] = from_i16x2(c0 ^ k0) + 0x00800080u;
+            cf.sl[1] = from_i16x2(c1 ^ k1) + 0x00800080u;
+        }
+    } else {
+        const uint32_t *ll = reinterpret_cast<const uint32_t *>(j.ll_in);
+        const int wpr = Wl / 2;
+        if (k >= Hl || x < 0 || x >= Wl) {
+            cf.sl[0] = cf.sl[1] = kB2;
+        } else {
+            const uint32_t *p = ll + (uint64_t)k * (uint64_t)wpr + x / 2;
+            if (vec && x + 4 <= Wl && ((uintptr_t)p & 7u) == 0) {
+                const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+                cf.sl[0] = t.x;
+                cf.sl[1] = t.y;
+            } else {
+                cf.sl[0] = __ldg(p);
+                cf.sl[1] = (x + 2 < Wl) ? __ldg(p + 1) : kB2;
+            }
+        }
+    }
+    return cf;
+}
+
+// Row inverse of one row (packed biased L[0..3] in w[0..1], H in w[2..3]):
+// returns 8 biased samples for image columns c .. c+7.
+__device__ __forceinline__ void unlift_row(const uint32_t (&w)[4], int c, int Ws, bool edge,
+                                           int (&out)[8])
+{
+    const int L[4] = {lo16(w[0]), hi16(w[0]), lo16(w[1]), hi16(w[1])};
+    const int Hv[4] = {lo16(w[2]), hi16(w[2]), lo16(w[3]), hi16(w[3])};
+    int hm = __shfl_up_sync(0xffffffffu, Hv[3], 1);
+    if (c == 0)
+        hm = Hv[0]; // d[-1] = d[0]
+    int ev[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        ev[i] = L[i] - (((i ? Hv[i - 1] : hm) + Hv[i] + 2) >> 2) + 0x2000; // undo Eq. 5.2
+    const int e4 = __shfl_down_sync(0xffffffffu, ev[0], 1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int en = i < 3 ? ev[i + 1] : e4;
+        if (edge && c + 2 * i + 2 == Ws) // x[m] = x[m-2]
+            en = ev[i];
+        out[2 * i] = ev[i];
+        out[2 * i + 1] = Hv[i] + ((ev[i] + en) >> 1) - 0x4000; // undo Eq. 5.1
+    }
+}
+
+template <bool BYTES_OUT>
+__device__ __forceinline__ void store_row(const LevelJob &j, int r, int c, bool own, int nv,
+                                          const int (&v)[8])
+{
+    if (!own)
+        return;
+    const int Ws = (int)j.Ws;
+    if (BYTES_OUT) {
+        // biased 0x4000 + b: the low byte is the recovered byte
+        const uint64_t g = (uint64_t)r * (uint64_t)Ws + (uint64_t)c;
+        if (g >= j.n)
+            return;
+        uint8_t *dst = j.out + g;
+        const uint32_t w0 = __byte_perm(__byte_perm((uint32_t)v[0], (uint32_t)v[1], 0x0040),
+                                        __byte_perm((uint32_t)v[2], (uint32_t)v[3], 0x0040), 0x5410);
+        const uint32_t w1 = __byte_perm(__byte_perm((uint32_t)v[4], (uint32_t)v[5], 0x0040),
+                                        __byte_perm((uint32_t)v[6], (uint32_t)v[7], 0x0040), 0x5410);
+        if (nv == 8 && g + 8 <= j.n && ((uintptr_t)dst & 7u) == 0) {
+            *reinterpret_cast<uint2 *>(dst) = make_uint2(w0, w1);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i < nv && g + i < j.n)
+                    dst[i] = (uint8_t)v[i];
+        }
+    } else {
+        uint32_t *dst = reinterpret_cast<uint32_t *>(j.out) + (uint64_t)r * (uint64_t)(Ws / 2) + c / 2;
+        const uint32_t p[4] = {pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]),
+                               pack2(v[6], v[7])};
+        if (nv == 8 && ((uintptr_t)dst & 15u) == 0) {
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(p[0], p[1], p[2], p[3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (2 * i < nv)
+                    dst[i] = p[i];
+        }
+    }
+}
+
+template <bool TOP, bool BYTES_OUT>
+__device__ void inv_unit(const LevelJob &j, int sx, int sy, const AesTab &aes, int lane)
+{
+    const int Ws = (int)j.Ws, Hs = (int)j.Hs;
+    const int c = 240 * sx - 8 + 8 * lane; // first output column of this lane
+    const int x = c >> 1;                  // first coefficient column
+    const int k0 = sy * (int)j.seg_pairs;
+    const int k1 = min(k0 + (int)j.seg_pairs, Hs / 2);
+    const bool edge = (240 * sx + 248 >= Ws);
+    const bool vec = ((j.Ws & 7u) == 0);
+    const bool own = lane >= 1 && lane <= 30 && c < Ws;
+    const int nv = min(8, Ws - c);
+
+    Coef cur = load_coef<TOP>(j, k0, x, vec, aes);
+    uint32_t xe[4], d0[4];
+    {
+        const Coef prev = load_coef<TOP>(j, max(k0 - 1, 0), x, vec, aes);
+        const uint32_t dm[4] = {k0 == 0 ? cur.dl[0] : prev.dl[0], k0 == 0 ? cur.dl[1] : prev.dl[1],
+                                k0 == 0 ? cur.dh[0] : prev.dh[0], k0 == 0 ? cur.dh[1] : prev.dh[1]};
+        const uint32_t s[4] = {cur.sl[0], cur.sl[1], cur.sh[0], cur.sh[1]};
+        d0[0] = cur.dl[0];
+        d0[1] = cur.dl[1];
+        d0[2] = cur.dh[0];
+        d0[3] = cur.dh[1];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            xe[i] = s[i] - pq4(dm[i], d0[i]) + 0x20002000u; // undo Eq. 5.2 down the columns
+    }
+    Coef nxt = load_coef<TOP>(j, k0 + 1, x, vec, aes);
+    for (int k = k0; k < k1; ++k) {
+        const Coef c1 = nxt;
+        if (k + 1 < k1)
+            nxt = load_coef<TOP>(j, k + 2, x, vec, aes);
+        const uint32_t s1[4] = {c1.sl[0], c1.sl[1], c1.sh[0], c1.sh[1]};
+        const uint32_t d1[4] = {c1.dl[0], c1.dl[1], c1.dh[0], c1.dh[1]};
+        uint32_t xe1[4], xo[4];
+        const bool bottom = (2 * k + 2 == Hs); // x[m] = x[m-2]
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            xe1[i] = s1[i] - pq4(d0[i], d1[i]) + 0x20002000u;
+            xo[i] = d0[i] + pavg(xe[i], bottom ? xe[i] : xe1[i]) - kB2; // undo Eq. 5.1
+        }
+        int ve[8], vo[8];
+        unlift_row(xe, c, Ws, edge, ve);
+        unlift_row(xo, c, Ws, edge, vo);
+        store_row<BYTES_OUT>(j, 2 * k, c, own, nv, ve);
+        store_row<BYTES_OUT>(j, 2 * k + 1, c, own, nv, vo);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            xe[i] = xe1[i];
+            d0[i] = d1[i];
+        }
+    }
+}
+
+} // namespace strm
+
+// ---------------------------------------------------------------------------
+// kernel: persistent warps over (job, strip, segment) units
+// ---------------------------------------------------------------------------
+constexpr int kStreamThreads = 256;
+
+__device__ __forceinline__ const LevelJob *level_job(const LevelWork &w, uint64_t u, uint64_t &local)
+{
+    if (w.jobs == nullptr) {
+        local = u;
+        return &w.single;
+    }
+    uint32_t lo = 0, hi = w.njobs;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (w.unit_start[mid] <= u)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    local = u - w.unit_start[lo];
+    return &w.jobs[lo];
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(kStreamThreads) level_kernel(LevelWork w)
+{
+    __shared__ AesTab aes;
+    for (int i = threadIdx.x; i < kAesWords; i += blockDim.x)
+        (&aes.T[0][0])[i] = w.aes_tables[i];
+    for (int i = threadIdx.x; i < 44; i += blockDim.x)
+        aes.rk[i] = w.round_keys[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    uint64_t u = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (;;) {
+        if (w.queue != nullptr) {
+            unsigned long long t = 0;
+            if (lane == 0)
+                t = atomicAdd(w.queue, 1ull);
+            u = __shfl_sync(0xffffffffu, t, 0);
+        }
+        if (u >= w.total_units)
+            break;
+        uint64_t local;
+        const LevelJob j = *level_job(w, u, local);
+        const int sx = (int)(local % j.strips), sy = (int)(local / j.strips);
+        if (FWD) {
+            if (j.src_bytes) {
+                if (j.final_level)
+                    strm::fwd_unit<true, true>(j, sx, sy, aes, lane);
+                else
+                    strm::fwd_unit<true, false>(j, sx, sy, aes, lane);
+            } else {
+                if (j.final_level)
+                    strm::fwd_unit<false, true>(j, sx, sy, aes, lane);
+                else
+                    strm::fwd_unit<false, false>(j, sx, sy, aes, lane);
+            }
+        } else {
+            if (j.top_level) {
+                if (j.out_bytes)
+                    strm::inv_unit<true, true>(j, sx, sy, aes, lane);
+                else
+                    strm::inv_unit<true, false>(j, sx, sy, aes, lane);
+            } else {
+                if (j.out_bytes)
+                    strm::inv_unit<false, true>(j, sx, sy, aes, lane);
+                else
+                    strm::inv_unit<false, false>(j, sx, sy, aes, lane);
+            }
+        }
+        if (w.queue == nullptr)
+            u += warps;
+    }
+}
+
+cudaError_t launch_level(bool fwd, const LevelWork &w, uint32_t grid, cudaStream_t stream)
+{
+    if (fwd)
+        level_kernel<true><<<grid, kStreamThreads, 0, stream>>>(w);
+    else
+        level_kernel<false><<<grid, kStreamThreads, 0, stream>>>(w);
+    return cudaGetLastError();
+}
+
+cudaError_t level_occupancy(bool fwd, int *blocks_per_sm)
+{
+    const void *fn = fwd ? (const void *)level_kernel<true> : (const void *)level_kernel<false>;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kStreamThreads, 0);
+}
+
+} // namespace frag
