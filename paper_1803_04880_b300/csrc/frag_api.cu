@@ -8,6 +8,7 @@
 #include "frag_internal.cuh"
 
 #include <algorithm>
+#include <array>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -344,23 +345,24 @@ LevelJob recover_level(const Buf &b, uint32_t l, uint32_t seg_pairs)
     return j;
 }
 
-frag_status level_grid(DeviceState &d, bool fwd, uint64_t units, uint32_t *grid)
+frag_status level_grid(DeviceState &d, bool fwd, int variant, uint64_t units, uint32_t *grid)
 {
     int occ = 0;
+    const size_t key = 1000 + (size_t)variant;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        auto it = d.occ[fwd].find(0);
+        auto it = d.occ[fwd].find(key);
         if (it != d.occ[fwd].end())
             occ = it->second;
     }
     if (occ == 0) {
-        cudaError_t e = frag::level_occupancy(fwd, &occ);
+        cudaError_t e = frag::level_occupancy(fwd, variant, &occ);
         if (e != cudaSuccess)
             return cuda_fail(e, "occupancy query");
         if (occ <= 0)
             occ = 1;
         std::lock_guard<std::mutex> lock(g_mu);
-        d.occ[fwd][0] = occ;
+        d.occ[fwd][key] = occ;
     }
     const uint64_t warps_per_block = 8;
     const uint64_t blocks = (units + warps_per_block - 1) / warps_per_block;
@@ -368,12 +370,13 @@ frag_status level_grid(DeviceState &d, bool fwd, uint64_t units, uint32_t *grid)
     return FRAG_OK;
 }
 
-// row pairs per unit for a lone buffer: about two units per resident warp
-uint32_t single_seg_pairs(DeviceState &d, uint32_t strips, uint32_t pairs)
+// Row pairs per work unit: about four units per resident warp, so every
+// level (the deep ones are small) keeps enough warps streaming.
+uint32_t seg_pairs_for(const DeviceState &d, uint64_t pair_strips)
 {
-    const uint64_t slots = (uint64_t)d.sms * 64;
-    const uint64_t want = std::max<uint64_t>(1, (uint64_t)strips * pairs / (2 * slots));
-    return (uint32_t)std::min<uint64_t>(64, std::max<uint64_t>(8, want));
+    const uint64_t slots = (uint64_t)d.sms * 24; // resident warps of the level kernels
+    const uint64_t want = pair_strips / (4 * slots);
+    return (uint32_t)std::min<uint64_t>(32, std::max<uint64_t>(4, want));
 }
 
 frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream_t s)
@@ -405,13 +408,14 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
         w.err = d->err;
         const uint32_t Ws = b.W >> (l - 1), Hs = b.H >> (l - 1);
         const uint32_t strips = (Ws + frag::kStripCols - 1) / frag::kStripCols;
-        const uint32_t seg = single_seg_pairs(*d, strips, Hs / 2);
+        const uint32_t seg = seg_pairs_for(*d, (uint64_t)strips * (Hs / 2));
         w.single = fwd ? protect_level(b, l, seg) : recover_level(b, l, seg);
         w.total_units = (uint64_t)w.single.strips * w.single.segs;
+        const int variant = frag::level_variant(w.single, fwd);
         uint32_t grid = 0;
-        if ((st = level_grid(*d, fwd, w.total_units, &grid)) != FRAG_OK)
+        if ((st = level_grid(*d, fwd, variant, w.total_units, &grid)) != FRAG_OK)
             break;
-        if ((e = frag::launch_level(fwd, w, grid, s)) != cudaSuccess)
+        if ((e = frag::launch_level(fwd, variant, w, grid, s)) != cudaSuccess)
             st = cuda_fail(e, fwd ? "protect launch" : "recover launch");
     }
     (void)plan;
@@ -429,10 +433,12 @@ struct LevelList {
     std::vector<uint64_t> start; // exclusive prefix of units
     size_t job_off = 0, start_off = 0;
     uint32_t queue_index = 0;
+    int variant = 0;
 };
 
 struct Wave {
-    std::vector<LevelList> levels; // forward: l = 1..maxL; inverse: l = maxL..1
+    // forward: l = 1..maxL; inverse: l = maxL..1; one list per kernel variant
+    std::vector<std::array<LevelList, 4>> levels;
     bool fwd = true;
 };
 
@@ -520,40 +526,53 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
         maxL = std::max(maxL, b.L);
     for (auto &wv : bp.waves) {
         wv.fwd = fwd;
-        wv.levels.assign(maxL, LevelList());
+        wv.levels.assign(maxL, std::array<LevelList, 4>());
     }
     return FRAG_OK;
 }
 
 // fill the level lists once the scratch base is known; lay out descriptors
-void fill_batch(BatchPlan &bp, uint8_t *scratch_base, size_t desc_base_off)
+void fill_batch(BatchPlan &bp, uint8_t *scratch_base, size_t desc_base_off, const DeviceState &d)
 {
+    for (auto &wv : bp.waves)
+        for (auto &slot : wv.levels)
+            for (auto &ll : slot)
+                ll.jobs.clear();
     for (size_t i = 0; i < bp.bufs.size(); ++i) {
         Buf &b = bp.bufs[i];
         uint64_t off1 = 0;
         scratch_bytes(b.H, b.W, b.L, &off1);
-        b.scr[0] = scratch_base + bp.scr_off[i];
-        b.scr[1] = scratch_base + bp.scr_off[i] + off1;
+        b.scr[0] = scratch_base ? scratch_base + bp.scr_off[i] : nullptr;
+        b.scr[1] = scratch_base ? scratch_base + bp.scr_off[i] + off1 : nullptr;
         Wave &wv = bp.waves[bp.wave_of[i]];
         for (uint32_t l = 1; l <= b.L; ++l) {
             const uint32_t slot = wv.fwd ? l - 1 : (uint32_t)wv.levels.size() - l;
-            LevelList &ll = wv.levels[slot];
-            ll.jobs.push_back(wv.fwd ? protect_level(b, l, kSegPairs) : recover_level(b, l, kSegPairs));
+            const LevelJob j = wv.fwd ? protect_level(b, l, kSegPairs) : recover_level(b, l, kSegPairs);
+            const int v = frag::level_variant(j, wv.fwd);
+            wv.levels[slot][v].variant = v;
+            wv.levels[slot][v].jobs.push_back(j);
         }
     }
     size_t off = desc_base_off;
     uint32_t q = 0;
     for (auto &wv : bp.waves)
-        for (auto &ll : wv.levels) {
-            ll.start.assign(1, 0);
-            for (auto &j : ll.jobs)
-                ll.start.push_back(ll.start.back() + (uint64_t)j.strips * j.segs);
-            ll.job_off = off;
-            off += align256(ll.jobs.size() * sizeof(LevelJob));
-            ll.start_off = off;
-            off += align256(ll.start.size() * sizeof(uint64_t));
-            ll.queue_index = q++;
-        }
+        for (auto &slot : wv.levels)
+            for (auto &ll : slot) {
+                uint64_t pair_strips = 0;
+                for (auto &j : ll.jobs)
+                    pair_strips += (uint64_t)j.strips * (j.Hs / 2);
+                const uint32_t seg = seg_pairs_for(d, pair_strips);
+                ll.start.assign(1, 0);
+                for (auto &j : ll.jobs) {
+                    decompose(j, seg);
+                    ll.start.push_back(ll.start.back() + (uint64_t)j.strips * j.segs);
+                }
+                ll.job_off = off;
+                off += align256(std::max<size_t>(1, ll.jobs.size()) * sizeof(LevelJob));
+                ll.start_off = off;
+                off += align256(ll.start.size() * sizeof(uint64_t));
+                ll.queue_index = q++;
+            }
     bp.queues = q;
     bp.desc_bytes = off - desc_base_off + align256(sizeof(unsigned long long) * std::max(q, 1u));
 }
@@ -564,11 +583,14 @@ frag_status upload_batch(BatchPlan &bp, uint8_t *mem, cudaStream_t s, bool async
     const size_t desc0 = align256(bp.scratch);
     std::vector<uint8_t> host(bp.desc_bytes, 0);
     for (auto &wv : bp.waves)
-        for (auto &ll : wv.levels) {
-            if (!ll.jobs.empty())
-                std::memcpy(host.data() + (ll.job_off - desc0), ll.jobs.data(), ll.jobs.size() * sizeof(LevelJob));
-            std::memcpy(host.data() + (ll.start_off - desc0), ll.start.data(), ll.start.size() * sizeof(uint64_t));
-        }
+        for (auto &slot : wv.levels)
+            for (auto &ll : slot) {
+                if (!ll.jobs.empty())
+                    std::memcpy(host.data() + (ll.job_off - desc0), ll.jobs.data(),
+                                ll.jobs.size() * sizeof(LevelJob));
+                std::memcpy(host.data() + (ll.start_off - desc0), ll.start.data(),
+                            ll.start.size() * sizeof(uint64_t));
+            }
     cudaError_t e = async ? cudaMemcpyAsync(mem + desc0, host.data(), host.size(), cudaMemcpyHostToDevice, s)
                           : cudaMemcpy(mem + desc0, host.data(), host.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess)
@@ -585,26 +607,27 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
     if (e != cudaSuccess)
         return cuda_fail(e, "queue reset");
     for (const auto &wv : bp.waves)
-        for (const auto &ll : wv.levels) {
-            if (ll.jobs.empty())
-                continue;
-            LevelWork w;
-            std::memset(&w, 0, sizeof(w));
-            w.jobs = (const LevelJob *)(mem + ll.job_off);
-            w.unit_start = (const uint64_t *)(mem + ll.start_off);
-            w.njobs = (uint32_t)ll.jobs.size();
-            w.total_units = ll.start.back();
-            w.queue = (unsigned long long *)(mem + queue_off(bp)) + ll.queue_index;
-            w.aes_tables = d.tables;
-            w.round_keys = rk;
-            w.err = d.err;
-            uint32_t grid = 0;
-            frag_status st = level_grid(d, wv.fwd, w.total_units, &grid);
-            if (st != FRAG_OK)
-                return st;
-            if ((e = frag::launch_level(wv.fwd, w, grid, s)) != cudaSuccess)
-                return cuda_fail(e, "batch launch");
-        }
+        for (const auto &slot : wv.levels)
+            for (const auto &ll : slot) {
+                if (ll.jobs.empty())
+                    continue;
+                LevelWork w;
+                std::memset(&w, 0, sizeof(w));
+                w.jobs = (const LevelJob *)(mem + ll.job_off);
+                w.unit_start = (const uint64_t *)(mem + ll.start_off);
+                w.njobs = (uint32_t)ll.jobs.size();
+                w.total_units = ll.start.back();
+                w.queue = (unsigned long long *)(mem + queue_off(bp)) + ll.queue_index;
+                w.aes_tables = d.tables;
+                w.round_keys = rk;
+                w.err = d.err;
+                uint32_t grid = 0;
+                frag_status st = level_grid(d, wv.fwd, ll.variant, w.total_units, &grid);
+                if (st != FRAG_OK)
+                    return st;
+                if ((e = frag::launch_level(wv.fwd, ll.variant, w, grid, s)) != cudaSuccess)
+                    return cuda_fail(e, "batch launch");
+            }
     return FRAG_OK;
 }
 
@@ -632,12 +655,12 @@ frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, 
         return st;
     // descriptor offsets do not depend on the scratch base: size on a copy
     BatchPlan sizing = bp;
-    fill_batch(sizing, nullptr, align256(bp.scratch));
+    fill_batch(sizing, nullptr, align256(bp.scratch), *d);
     uint8_t *mem = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&mem, batch_mem_bytes(sizing), s);
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaMallocAsync(batch)");
-    fill_batch(bp, mem, align256(bp.scratch));
+    fill_batch(bp, mem, align256(bp.scratch), *d);
     st = upload_batch(bp, mem, s, true);
     if (st == FRAG_OK)
         st = launch_batch(bp, mem, *d, rk, s);
@@ -662,13 +685,13 @@ frag_status create_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, ui
         st = device_state(&d, &bt->device);
     if (st == FRAG_OK && !bt->bp.bufs.empty()) {
         BatchPlan sizing = bt->bp;
-        fill_batch(sizing, nullptr, align256(sizing.scratch));
+        fill_batch(sizing, nullptr, align256(sizing.scratch), *d);
         cudaError_t e = cudaMalloc((void **)&bt->mem, batch_mem_bytes(sizing));
         if (e != cudaSuccess) {
             bt->mem = nullptr;
             st = cuda_fail(e, "cudaMalloc(batch)");
         } else {
-            fill_batch(bt->bp, bt->mem, align256(bt->bp.scratch));
+            fill_batch(bt->bp, bt->mem, align256(bt->bp.scratch), *d);
             st = upload_batch(bt->bp, bt->mem, nullptr, false);
         }
     }

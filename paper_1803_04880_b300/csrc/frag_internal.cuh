@@ -105,8 +105,10 @@ const uint32_t *host_aes_words();                             // kAesWords words
 void host_expand_key(const uint8_t key[16], uint32_t rk[44]); // FIPS-197 key schedule
 
 // streaming level kernels (stream_kernels.cu)
-cudaError_t launch_level(bool fwd, const LevelWork &w, uint32_t grid, cudaStream_t stream);
-cudaError_t level_occupancy(bool fwd, int *blocks_per_sm);
+int level_variant(const LevelJob &j, bool fwd); // 0..3: which kernel instantiation serves j
+cudaError_t launch_level(bool fwd, int variant, const LevelWork &w, uint32_t grid,
+                         cudaStream_t stream);
+cudaError_t level_occupancy(bool fwd, int variant, int *blocks_per_sm);
 constexpr int kStripCols = 240; // level-(l-1) columns owned by one warp strip
 
 // kernels (tile_kernels.cu)

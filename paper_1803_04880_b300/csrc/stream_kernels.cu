@@ -562,8 +562,10 @@ __device__ __forceinline__ const LevelJob *level_job(const LevelWork &w, uint64_
     return &w.jobs[lo];
 }
 
-template <bool FWD>
-__global__ void __launch_bounds__(kStreamThreads) level_kernel(LevelWork w)
+// V1: forward = byte source, inverse = top level (private fragment in);
+// V2: forward = final level (private fragment out), inverse = byte output.
+template <bool FWD, bool V1, bool V2>
+__global__ void __launch_bounds__(kStreamThreads, 3) level_kernel(LevelWork w)
 {
     __shared__ AesTab aes;
     for (int i = threadIdx.x; i < kAesWords; i += blockDim.x)
@@ -586,49 +588,47 @@ __global__ void __launch_bounds__(kStreamThreads) level_kernel(LevelWork w)
         uint64_t local;
         const LevelJob j = *level_job(w, u, local);
         const int sx = (int)(local % j.strips), sy = (int)(local / j.strips);
-        if (FWD) {
-            if (j.src_bytes) {
-                if (j.final_level)
-                    strm::fwd_unit<true, true>(j, sx, sy, aes, lane);
-                else
-                    strm::fwd_unit<true, false>(j, sx, sy, aes, lane);
-            } else {
-                if (j.final_level)
-                    strm::fwd_unit<false, true>(j, sx, sy, aes, lane);
-                else
-                    strm::fwd_unit<false, false>(j, sx, sy, aes, lane);
-            }
-        } else {
-            if (j.top_level) {
-                if (j.out_bytes)
-                    strm::inv_unit<true, true>(j, sx, sy, aes, lane);
-                else
-                    strm::inv_unit<true, false>(j, sx, sy, aes, lane);
-            } else {
-                if (j.out_bytes)
-                    strm::inv_unit<false, true>(j, sx, sy, aes, lane);
-                else
-                    strm::inv_unit<false, false>(j, sx, sy, aes, lane);
-            }
-        }
+        if (FWD)
+            strm::fwd_unit<V1, V2>(j, sx, sy, aes, lane);
+        else
+            strm::inv_unit<V1, V2>(j, sx, sy, aes, lane);
         if (w.queue == nullptr)
             u += warps;
     }
 }
 
-cudaError_t launch_level(bool fwd, const LevelWork &w, uint32_t grid, cudaStream_t stream)
+int level_variant(const LevelJob &j, bool fwd)
 {
-    if (fwd)
-        level_kernel<true><<<grid, kStreamThreads, 0, stream>>>(w);
-    else
-        level_kernel<false><<<grid, kStreamThreads, 0, stream>>>(w);
-    return cudaGetLastError();
+    return fwd ? (j.src_bytes ? 1 : 0) + (j.final_level ? 2 : 0)
+               : (j.top_level ? 1 : 0) + (j.out_bytes ? 2 : 0);
 }
 
-cudaError_t level_occupancy(bool fwd, int *blocks_per_sm)
+static const void *level_fn(bool fwd, int variant)
 {
-    const void *fn = fwd ? (const void *)level_kernel<true> : (const void *)level_kernel<false>;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kStreamThreads, 0);
+    switch ((fwd ? 4 : 0) + variant) {
+    case 0: return (const void *)level_kernel<false, false, false>;
+    case 1: return (const void *)level_kernel<false, true, false>;
+    case 2: return (const void *)level_kernel<false, false, true>;
+    case 3: return (const void *)level_kernel<false, true, true>;
+    case 4: return (const void *)level_kernel<true, false, false>;
+    case 5: return (const void *)level_kernel<true, true, false>;
+    case 6: return (const void *)level_kernel<true, false, true>;
+    default: return (const void *)level_kernel<true, true, true>;
+    }
+}
+
+cudaError_t launch_level(bool fwd, int variant, const LevelWork &w, uint32_t grid,
+                         cudaStream_t stream)
+{
+    void *args[] = {const_cast<LevelWork *>(&w)};
+    return cudaLaunchKernel(level_fn(fwd, variant), dim3(grid), dim3(kStreamThreads), args, 0,
+                            stream);
+}
+
+cudaError_t level_occupancy(bool fwd, int variant, int *blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, level_fn(fwd, variant),
+                                                         kStreamThreads, 0);
 }
 
 } // namespace frag
