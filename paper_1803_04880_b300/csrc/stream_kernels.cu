@@ -168,48 +168,49 @@ __device__ __forceinline__ Raw load_row(const LevelJob &j, int r, int c, bool ve
 }
 
 // Lift one row along its length (Eq. 5.1 then Eq. 5.2) for the lane's four
-// pairs at image columns c .. c+7.  Returns the packed biased pairs:
-// P[0], P[1] = low (s) values, P[2], P[3] = high (d) values.
+// pairs at image columns c .. c+7, on packed pairs: (x0, x2), (x1, x3),
+// (x4, x6), (x5, x7) are formed with byte permutes, the neighbours x8 and
+// d[-1] come from the adjacent lanes.  Returns P[0] = (s0, s1),
+// P[1] = (s2, s3), P[2] = (d0, d1), P[3] = (d2, d3), all biased.
 template <bool BYTES>
 __device__ __forceinline__ void lift_row(const Raw &raw, int c, int Ws, bool edge, uint32_t (&P)[4])
 {
-    int x[8];
+    uint32_t e01, o01, e23, o23;
     if (BYTES) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-            x[i] = (int)((raw.w[i >> 2] >> (8 * (i & 3))) & 255u);
+        e01 = __byte_perm(raw.w[0], 0, 0x4240) + kB2;
+        o01 = __byte_perm(raw.w[0], 0, 0x4341) + kB2;
+        e23 = __byte_perm(raw.w[1], 0, 0x4240) + kB2;
+        o23 = __byte_perm(raw.w[1], 0, 0x4341) + kB2;
     } else {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            x[2 * i] = lo16(raw.w[i]);
-            x[2 * i + 1] = hi16(raw.w[i]);
-        }
+        e01 = __byte_perm(raw.w[0], raw.w[1], 0x5410);
+        o01 = __byte_perm(raw.w[0], raw.w[1], 0x7632);
+        e23 = __byte_perm(raw.w[2], raw.w[3], 0x5410);
+        o23 = __byte_perm(raw.w[2], raw.w[3], 0x7632);
     }
-    const int xn = __shfl_down_sync(0xffffffffu, x[0], 1); // next lane's first sample
-    int d[4], s[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int xr = i < 3 ? x[2 * i + 2] : xn;
-        if (edge && c + 2 * i + 2 == Ws) // x[m] = x[m-2]
-            xr = x[2 * i];
-        d[i] = x[2 * i + 1] - ((x[2 * i] + xr) >> 1);
+    const uint32_t e01n = __shfl_down_sync(0xffffffffu, e01, 1); // (x8, x10) of the next lane
+    uint32_t e12 = __byte_perm(e01, e23, 0x5432);                // (x2, x4)
+    uint32_t e34 = __byte_perm(e23, e01n, 0x5432);               // (x6, x8)
+    if (edge) { // x[m] = x[m-2] for the pair that ends the row
+        if (c + 2 == Ws)
+            e12 = __byte_perm(e12, e01, 0x3254);
+        if (c + 4 == Ws)
+            e12 = __byte_perm(e12, e01, 0x7610);
+        if (c + 6 == Ws)
+            e34 = __byte_perm(e34, e23, 0x3254);
+        if (c + 8 == Ws)
+            e34 = __byte_perm(e34, e23, 0x7610);
     }
-    int dm = __shfl_up_sync(0xffffffffu, d[3], 1); // previous lane's last d
+    const uint32_t d01 = o01 - pavg(e01, e12) + kB2; // Eq. 5.1
+    const uint32_t d23 = o23 - pavg(e23, e34) + kB2;
+    const uint32_t d23p = __shfl_up_sync(0xffffffffu, d23, 1); // (d2, d3) of the previous lane
+    uint32_t dm0 = __byte_perm(d23p, d01, 0x5432);               // (d[-1], d0)
     if (c == 0)
-        dm = d[0]; // d[-1] = d[0]
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        s[i] = x[2 * i] + (((i ? d[i - 1] : dm) + d[i] + 2) >> 2);
-    // bytes give unbiased s; packed sources give biased s; d is unbiased
-    if (BYTES) {
-        P[0] = from_i16x2(pack2(s[0], s[1]));
-        P[1] = from_i16x2(pack2(s[2], s[3]));
-    } else {
-        P[0] = pack2(s[0], s[1]);
-        P[1] = pack2(s[2], s[3]);
-    }
-    P[2] = from_i16x2(pack2(d[0], d[1]));
-    P[3] = from_i16x2(pack2(d[2], d[3]));
+        dm0 = __byte_perm(d01, d01, 0x1010); // d[-1] = d[0]
+    const uint32_t d12 = __byte_perm(d01, d23, 0x5432); // (d1, d2)
+    P[0] = e01 + pq4(dm0, d01) - 0x20002000u; // Eq. 5.2
+    P[1] = e23 + pq4(d12, d23) - 0x20002000u;
+    P[2] = d01;
+    P[3] = d23;
 }
 
 // store 4 int16 values (2 packed biased pairs) to a band at (y, x .. x+3)
@@ -417,60 +418,65 @@ __device__ __forceinline__ Coef load_coef(const LevelJob &j, int k, int x, bool 
     return cf;
 }
 
-// Row inverse of one row (packed biased L[0..3] in w[0..1], H in w[2..3]):
-// returns 8 biased samples for image columns c .. c+7.
+// Row inverse of one row on packed pairs: w[0] = (L0, L1), w[1] = (L2, L3),
+// w[2] = (H0, H1), w[3] = (H2, H3); returns the 8 samples of image columns
+// c .. c+7 as packed pairs (x0, x1), (x2, x3), (x4, x5), (x6, x7).
 __device__ __forceinline__ void unlift_row(const uint32_t (&w)[4], int c, int Ws, bool edge,
-                                           int (&out)[8])
+                                           uint32_t (&out)[4])
 {
-    const int L[4] = {lo16(w[0]), hi16(w[0]), lo16(w[1]), hi16(w[1])};
-    const int Hv[4] = {lo16(w[2]), hi16(w[2]), lo16(w[3]), hi16(w[3])};
-    int hm = __shfl_up_sync(0xffffffffu, Hv[3], 1);
+    const uint32_t h23p = __shfl_up_sync(0xffffffffu, w[3], 1);
+    uint32_t hm0 = __byte_perm(h23p, w[2], 0x5432); // (H[-1], H0)
     if (c == 0)
-        hm = Hv[0]; // d[-1] = d[0]
-    int ev[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        ev[i] = L[i] - (((i ? Hv[i - 1] : hm) + Hv[i] + 2) >> 2) + 0x2000; // undo Eq. 5.2
-    const int e4 = __shfl_down_sync(0xffffffffu, ev[0], 1);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int en = i < 3 ? ev[i + 1] : e4;
-        if (edge && c + 2 * i + 2 == Ws) // x[m] = x[m-2]
-            en = ev[i];
-        out[2 * i] = ev[i];
-        out[2 * i + 1] = Hv[i] + ((ev[i] + en) >> 1) - 0x4000; // undo Eq. 5.1
+        hm0 = __byte_perm(w[2], w[2], 0x1010); // d[-1] = d[0]
+    const uint32_t h12 = __byte_perm(w[2], w[3], 0x5432);
+    const uint32_t e01 = w[0] - pq4(hm0, w[2]) + 0x20002000u; // undo Eq. 5.2
+    const uint32_t e23 = w[1] - pq4(h12, w[3]) + 0x20002000u;
+    const uint32_t e01n = __shfl_down_sync(0xffffffffu, e01, 1);
+    uint32_t e12 = __byte_perm(e01, e23, 0x5432);
+    uint32_t e34 = __byte_perm(e23, e01n, 0x5432);
+    if (edge) { // x[m] = x[m-2]
+        if (c + 2 == Ws)
+            e12 = __byte_perm(e12, e01, 0x3254);
+        if (c + 4 == Ws)
+            e12 = __byte_perm(e12, e01, 0x7610);
+        if (c + 6 == Ws)
+            e34 = __byte_perm(e34, e23, 0x3254);
+        if (c + 8 == Ws)
+            e34 = __byte_perm(e34, e23, 0x7610);
     }
+    const uint32_t o01 = w[2] + pavg(e01, e12) - kB2; // undo Eq. 5.1
+    const uint32_t o23 = w[3] + pavg(e23, e34) - kB2;
+    out[0] = __byte_perm(e01, o01, 0x5410);
+    out[1] = __byte_perm(e01, o01, 0x7632);
+    out[2] = __byte_perm(e23, o23, 0x5410);
+    out[3] = __byte_perm(e23, o23, 0x7632);
 }
 
 template <bool BYTES_OUT>
 __device__ __forceinline__ void store_row(const LevelJob &j, int r, int c, bool own, int nv,
-                                          const int (&v)[8])
+                                          const uint32_t (&p)[4])
 {
     if (!own)
         return;
     const int Ws = (int)j.Ws;
     if (BYTES_OUT) {
-        // biased 0x4000 + b: the low byte is the recovered byte
+        // biased 0x4000 + b: the low byte of each half is the recovered byte
         const uint64_t g = (uint64_t)r * (uint64_t)Ws + (uint64_t)c;
         if (g >= j.n)
             return;
         uint8_t *dst = j.out + g;
-        const uint32_t w0 = __byte_perm(__byte_perm((uint32_t)v[0], (uint32_t)v[1], 0x0040),
-                                        __byte_perm((uint32_t)v[2], (uint32_t)v[3], 0x0040), 0x5410);
-        const uint32_t w1 = __byte_perm(__byte_perm((uint32_t)v[4], (uint32_t)v[5], 0x0040),
-                                        __byte_perm((uint32_t)v[6], (uint32_t)v[7], 0x0040), 0x5410);
+        const uint32_t w0 = __byte_perm(p[0], p[1], 0x6420);
+        const uint32_t w1 = __byte_perm(p[2], p[3], 0x6420);
         if (nv == 8 && g + 8 <= j.n && ((uintptr_t)dst & 7u) == 0) {
             *reinterpret_cast<uint2 *>(dst) = make_uint2(w0, w1);
         } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 if (i < nv && g + i < j.n)
-                    dst[i] = (uint8_t)v[i];
+                    dst[i] = (uint8_t)((i < 4 ? w0 : w1) >> (8 * (i & 3)));
         }
     } else {
         uint32_t *dst = reinterpret_cast<uint32_t *>(j.out) + (uint64_t)r * (uint64_t)(Ws / 2) + c / 2;
-        const uint32_t p[4] = {pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]),
-                               pack2(v[6], v[7])};
         if (nv == 8 && ((uintptr_t)dst & 15u) == 0) {
             *reinterpret_cast<uint4 *>(dst) = make_uint4(p[0], p[1], p[2], p[3]);
         } else {
@@ -524,7 +530,7 @@ __device__ void inv_unit(const LevelJob &j, int sx, int sy, const AesTab &aes, i
             xe1[i] = s1[i] - pq4(d0[i], d1[i]) + 0x20002000u;
             xo[i] = d0[i] + pavg(xe[i], bottom ? xe[i] : xe1[i]) - kB2; // undo Eq. 5.1
         }
-        int ve[8], vo[8];
+        uint32_t ve[4], vo[4];
         unlift_row(xe, c, Ws, edge, ve);
         unlift_row(xo, c, Ws, edge, vo);
         store_row<BYTES_OUT>(j, 2 * k, c, own, nv, ve);
