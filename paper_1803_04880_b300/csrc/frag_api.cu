@@ -267,27 +267,33 @@ void base_work(Work &w, DeviceState &d, const uint32_t *rk)
 }
 
 // ---------------------------------------------------------------------------
-// Streaming path: one launch per level; LL between levels in scratch
+// Streaming path: all levels of all buffers of a call in one launch of the
+// dependency-ordered kernel; LL between levels in scratch
 // ---------------------------------------------------------------------------
+using frag::DagUnit;
+using frag::DagWork;
 using frag::LevelJob;
-using frag::LevelWork;
 
-constexpr uint32_t kSegPairs = 16;         // row pairs per work unit in batches
-constexpr uint64_t kScratchBudget = 8ull << 30; // per wave of a batch
+constexpr uint64_t kScratchBudget = 8ull << 30; // scratch of one wave of a batch
+constexpr uint32_t kMinLag = 3;                 // rounds between consecutive levels, at least
+constexpr uint32_t kSpinLimit = 1u << 22;       // polls of a dependency before giving up
 
 uint64_t align256(uint64_t v) { return (v + 255) / 256 * 256; }
 
 uint64_t ll_bytes(uint32_t H, uint32_t W, uint32_t l) { return 2ull * (H >> l) * (uint64_t)(W >> l); }
 
-// scratch of one buffer: LL_1 (and later LL_3, ...) in part 0, LL_2 (LL_4, ...) in part 1
-uint64_t scratch_bytes(uint32_t H, uint32_t W, uint32_t L, uint64_t *off1)
+// scratch of one buffer: LL_1 .. LL_{L-1}, each in its own region (the levels
+// of one buffer run concurrently, so no region can be reused); off[l] is the
+// offset of LL_l
+uint64_t scratch_bytes(uint32_t H, uint32_t W, uint32_t L, uint64_t *off)
 {
-    *off1 = 0;
-    if (L < 2)
-        return 0;
-    const uint64_t a = align256(ll_bytes(H, W, 1));
-    *off1 = a;
-    return a + (L >= 3 ? align256(ll_bytes(H, W, 2)) : 0);
+    uint64_t total = 0;
+    for (uint32_t l = 1; l < L; ++l) {
+        if (off)
+            off[l] = total;
+        total += align256(ll_bytes(H, W, l));
+    }
+    return total;
 }
 
 struct Buf {
@@ -297,90 +303,123 @@ struct Buf {
     uint8_t *priv, *pub;
     const uint8_t *priv_in, *pub_in;
     uint8_t *out;
-    uint8_t *scr[2];
+    uint8_t *scr[frag::kMaxInlineJobs]; // scr[l]: LL_l (1 <= l < L)
 };
 
-void decompose(LevelJob &j, uint32_t seg_pairs)
+// level-0 rows per work segment, the same at every level: a power of two
+// >= 2^L, so every level has the same number of segments
+uint32_t seg_rows0(uint32_t L)
 {
+    uint32_t r = 64;
+    while (r < (1u << L))
+        r <<= 1;
+    return r;
+}
+
+LevelJob level_job(bool fwd, const Buf &b, uint32_t l, uint32_t R0)
+{
+    LevelJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.Ws = b.W >> (l - 1);
+    j.Hs = b.H >> (l - 1);
+    uint8_t *pub = fwd ? b.pub : const_cast<uint8_t *>(b.pub_in);
+    j.hl = pub + frag::band_offset(b.H, b.W, b.L, l, 0);
+    j.lh = pub + frag::band_offset(b.H, b.W, b.L, l, 1);
+    j.hh = pub + frag::band_offset(b.H, b.W, b.L, l, 2);
+    if (fwd) {
+        j.src = l == 1 ? b.in : b.scr[l - 1];
+        j.src_bytes = l == 1;
+        j.final_level = l == b.L;
+        j.ll = l == b.L ? b.priv : b.scr[l];
+    } else {
+        j.top_level = l == b.L;
+        j.ll_in = l == b.L ? b.priv_in : b.scr[l];
+        j.out_bytes = l == 1;
+        j.out = l == 1 ? b.out : b.scr[l - 1];
+    }
+    j.n = b.n;
+    j.nonce = b.nonce;
     j.strips = (j.Ws + frag::kStripCols - 1) / frag::kStripCols;
-    j.seg_pairs = seg_pairs;
-    j.segs = ((j.Hs / 2) + seg_pairs - 1) / seg_pairs;
-}
-
-LevelJob protect_level(const Buf &b, uint32_t l, uint32_t seg_pairs)
-{
-    LevelJob j;
-    std::memset(&j, 0, sizeof(j));
-    j.Ws = b.W >> (l - 1);
-    j.Hs = b.H >> (l - 1);
-    j.src = l == 1 ? b.in : b.scr[(l - 2) % 2];
-    j.src_bytes = l == 1;
-    j.hl = b.pub + frag::band_offset(b.H, b.W, b.L, l, 0);
-    j.lh = b.pub + frag::band_offset(b.H, b.W, b.L, l, 1);
-    j.hh = b.pub + frag::band_offset(b.H, b.W, b.L, l, 2);
-    j.final_level = l == b.L;
-    j.ll = l == b.L ? b.priv : b.scr[(l - 1) % 2];
-    j.n = b.n;
-    j.nonce = b.nonce;
-    decompose(j, seg_pairs);
+    j.seg_pairs = R0 >> l;
+    j.segs = ((j.Hs / 2) + j.seg_pairs - 1) / j.seg_pairs;
+    j.dep = -1;
     return j;
 }
 
-LevelJob recover_level(const Buf &b, uint32_t l, uint32_t seg_pairs)
+// the jobs of one buffer in processing order (forward l = 1..L, inverse
+// l = L..1); each depends on the previous one
+void buffer_jobs(bool fwd, const Buf &b, uint32_t first_job, uint32_t *counters,
+                 std::vector<LevelJob> &jobs)
 {
-    LevelJob j;
-    std::memset(&j, 0, sizeof(j));
-    j.Ws = b.W >> (l - 1);
-    j.Hs = b.H >> (l - 1);
-    j.hl = const_cast<uint8_t *>(b.pub_in) + frag::band_offset(b.H, b.W, b.L, l, 0);
-    j.lh = const_cast<uint8_t *>(b.pub_in) + frag::band_offset(b.H, b.W, b.L, l, 1);
-    j.hh = const_cast<uint8_t *>(b.pub_in) + frag::band_offset(b.H, b.W, b.L, l, 2);
-    j.top_level = l == b.L;
-    j.ll_in = l == b.L ? b.priv_in : b.scr[(l - 1) % 2];
-    j.out_bytes = l == 1;
-    j.out = l == 1 ? b.out : b.scr[(l - 2) % 2];
-    j.n = b.n;
-    j.nonce = b.nonce;
-    decompose(j, seg_pairs);
-    return j;
+    const uint32_t R0 = seg_rows0(b.L);
+    for (uint32_t m = 0; m < b.L; ++m) {
+        LevelJob j = level_job(fwd, b, fwd ? m + 1 : b.L - m, R0);
+        j.dep = m ? (int32_t)(first_job + m - 1) : -1;
+        j.done_off = *counters;
+        *counters += j.segs;
+        jobs.push_back(j);
+    }
 }
 
-frag_status level_grid(DeviceState &d, bool fwd, int variant, uint64_t units, uint32_t *grid)
+// Rounds between consecutive levels of a lone buffer: a level's segment is
+// queued only after about 1.5 times the resident warps' worth of earlier
+// units, so it rarely waits for its producers (small images end up level by
+// level; tall ones stream with the coarse levels behind the fine ones).
+uint32_t buffer_lag(const std::vector<LevelJob> &jobs, uint32_t first_job, uint32_t L,
+                    uint64_t resident_warps)
+{
+    uint64_t per_round = 0;
+    for (uint32_t m = 0; m < L; ++m)
+        per_round += jobs[first_job + m].strips;
+    const uint64_t lag = (3 * resident_warps / 2 + per_round - 1) / std::max<uint64_t>(1, per_round);
+    return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(kMinLag, lag), 1u << 24);
+}
+
+// units of a wave of buffers, level by level (level m of every buffer before
+// level m + 1 of any), each level's units in row-segment order
+void wave_units(const std::vector<LevelJob> &jobs, const std::vector<uint32_t> &first,
+                const std::vector<uint32_t> &levels, std::vector<DagUnit> &units)
+{
+    uint32_t maxL = 0;
+    for (uint32_t L : levels)
+        maxL = std::max(maxL, L);
+    for (uint32_t m = 0; m < maxL; ++m)
+        for (size_t b = 0; b < first.size(); ++b) {
+            if (m >= levels[b])
+                continue;
+            const LevelJob &j = jobs[first[b] + m];
+            for (uint32_t sy = 0; sy < j.segs; ++sy)
+                for (uint32_t sx = 0; sx < j.strips; ++sx)
+                    units.push_back(DagUnit{first[b] + m, sx, sy});
+        }
+}
+
+frag_status dag_grid(DeviceState &d, bool fwd, uint64_t units, uint32_t *grid)
 {
     int occ = 0;
-    const size_t key = 1000 + (size_t)variant;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        auto it = d.occ[fwd].find(key);
+        auto it = d.occ[fwd].find(7777);
         if (it != d.occ[fwd].end())
             occ = it->second;
     }
     if (occ == 0) {
-        cudaError_t e = frag::level_occupancy(fwd, variant, &occ);
+        cudaError_t e = frag::dag_occupancy(fwd, &occ);
         if (e != cudaSuccess)
             return cuda_fail(e, "occupancy query");
         if (occ <= 0)
             occ = 1;
         std::lock_guard<std::mutex> lock(g_mu);
-        d.occ[fwd][key] = occ;
+        d.occ[fwd][7777] = occ;
     }
-    const uint64_t warps_per_block = 8;
-    const uint64_t blocks = (units + warps_per_block - 1) / warps_per_block;
+    const uint64_t blocks = (units + 7) / 8; // 8 warps per block
     *grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)d.sms * occ, blocks));
     return FRAG_OK;
 }
 
-// Row pairs per work unit: about four units per resident warp, so every
-// level (the deep ones are small) keeps enough warps streaming.
-uint32_t seg_pairs_for(const DeviceState &d, uint64_t pair_strips)
-{
-    const uint64_t slots = (uint64_t)d.sms * 24; // resident warps of the level kernels
-    const uint64_t want = pair_strips / (4 * slots);
-    return (uint32_t)std::min<uint64_t>(32, std::max<uint64_t>(4, want));
-}
-
 frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream_t s)
 {
+    (void)plan;
     DeviceState *d = nullptr;
     int dev = 0;
     frag_status st = device_state(&d, &dev);
@@ -389,83 +428,75 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     const uint32_t *rk = nullptr;
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
-    uint64_t off1 = 0;
-    const uint64_t sb = scratch_bytes(b.H, b.W, b.L, &off1);
-    uint8_t *scr = nullptr;
-    cudaError_t e;
-    if (sb) {
-        if ((e = cudaMallocAsync((void **)&scr, sb, s)) != cudaSuccess)
-            return cuda_fail(e, "cudaMallocAsync(level scratch)");
-        b.scr[0] = scr;
-        b.scr[1] = scr + off1;
+    if (b.L > (uint32_t)frag::kMaxInlineJobs)
+        return fail(FRAG_EUNSUPPORTED, "more than %d levels", frag::kMaxInlineJobs);
+    // one stream-ordered allocation: [scratch][counters][queue head]
+    uint64_t off[frag::kMaxInlineJobs] = {0};
+    const uint64_t sb = align256(scratch_bytes(b.H, b.W, b.L, off));
+    const uint32_t NS = ((b.H >> 1) + (seg_rows0(b.L) >> 1) - 1) / (seg_rows0(b.L) >> 1);
+    const uint64_t cb = align256(4ull * NS * b.L);
+    uint8_t *mem = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&mem, sb + cb + 256, s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMallocAsync(level scratch)");
+    for (uint32_t l = 1; l < b.L; ++l)
+        b.scr[l] = mem + off[l];
+    std::vector<LevelJob> jobs;
+    uint32_t counters = 0;
+    buffer_jobs(fwd, b, 0, &counters, jobs);
+    DagWork w;
+    std::memset(&w, 0, sizeof(w));
+    uint64_t units = 0;
+    for (uint32_t m = 0; m < b.L; ++m) {
+        w.inline_jobs[m] = jobs[m];
+        units += (uint64_t)jobs[m].strips * jobs[m].segs;
     }
-    for (uint32_t k = 0; k < b.L && st == FRAG_OK; ++k) {
-        const uint32_t l = fwd ? k + 1 : b.L - k;
-        LevelWork w;
-        std::memset(&w, 0, sizeof(w));
-        w.aes_tables = d->tables;
-        w.round_keys = rk;
-        w.err = d->err;
-        const uint32_t Ws = b.W >> (l - 1), Hs = b.H >> (l - 1);
-        const uint32_t strips = (Ws + frag::kStripCols - 1) / frag::kStripCols;
-        const uint32_t seg = seg_pairs_for(*d, (uint64_t)strips * (Hs / 2));
-        w.single = fwd ? protect_level(b, l, seg) : recover_level(b, l, seg);
-        w.total_units = (uint64_t)w.single.strips * w.single.segs;
-        const int variant = frag::level_variant(w.single, fwd);
-        uint32_t grid = 0;
-        if ((st = level_grid(*d, fwd, variant, w.total_units, &grid)) != FRAG_OK)
-            break;
-        if ((e = frag::launch_level(fwd, variant, w, grid, s)) != cudaSuccess)
-            st = cuda_fail(e, fwd ? "protect launch" : "recover launch");
-    }
-    (void)plan;
-    if (scr)
-        cudaFreeAsync(scr, s);
+    w.n_inline = b.L;
+    w.lag = buffer_lag(jobs, 0, b.L, (uint64_t)d->sms * 16);
+    w.total_units = units;
+    w.done = (unsigned *)(mem + sb);
+    w.queue = (unsigned long long *)(mem + sb + cb);
+    w.aes_tables = d->tables;
+    w.round_keys = rk;
+    w.err = d->err;
+    w.spin_limit = kSpinLimit;
+    e = cudaMemsetAsync(mem + sb, 0, cb + 256, s);
+    uint32_t grid = 0;
+    if (e != cudaSuccess)
+        st = cuda_fail(e, "counter reset");
+    else if ((st = dag_grid(*d, fwd, units, &grid)) == FRAG_OK &&
+             (e = frag::launch_dag(fwd, w, grid, s)) != cudaSuccess)
+        st = cuda_fail(e, fwd ? "protect launch" : "recover launch");
+    cudaFreeAsync(mem, s);
     return st;
 }
 
 // ---------------------------------------------------------------------------
-// Batches: waves of buffers whose scratch fits a budget; per wave one launch
-// per level over all its buffers, units handed out by a device queue
+// Batches: buffers, most work first, cut into waves whose scratch fits a
+// budget; one launch per wave over an explicit dependency-ordered unit list
 // ---------------------------------------------------------------------------
-struct LevelList {
+struct DagWave {
     std::vector<LevelJob> jobs;
-    std::vector<uint64_t> start; // exclusive prefix of units
-    size_t job_off = 0, start_off = 0;
-    uint32_t queue_index = 0;
-    int variant = 0;
-};
-
-struct Wave {
-    // forward: l = 1..maxL; inverse: l = maxL..1; one list per kernel variant
-    std::vector<std::array<LevelList, 4>> levels;
-    bool fwd = true;
+    std::vector<uint32_t> first, levels; // per buffer: first job, levels
+    std::vector<DagUnit> units;
+    uint32_t counters = 0;
+    size_t jobs_off = 0, units_off = 0, done_off = 0, queue_off = 0;
 };
 
 struct BatchPlan {
+    bool fwd = true;
     std::vector<Buf> bufs;
-    std::vector<uint64_t> scr_off;   // scratch offset of each buffer (within its wave)
+    std::vector<uint64_t> scr_off;
     std::vector<uint32_t> wave_of;
-    std::vector<Wave> waves;
-    uint64_t scratch = 0;            // bytes (largest wave)
+    std::vector<DagWave> waves;
+    uint64_t scratch = 0;
     size_t desc_bytes = 0;
-    uint32_t queues = 0;
 };
-
-} // namespace
-
-struct frag_batch_s {
-    int device = 0;
-    BatchPlan bp;
-    uint8_t *mem = nullptr; // [scratch][descriptors][queue heads]
-};
-
-namespace {
 
 frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint32_t count,
                        BatchPlan &bp)
 {
-    // buffers, most work first (so long buffers start early)
+    bp.fwd = fwd;
     std::vector<std::pair<uint64_t, Buf>> v;
     for (uint32_t i = 0; i < count; ++i) {
         frag_plan plan = fwd ? pi[i].plan : ri[i].plan;
@@ -500,16 +531,14 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
         }
         v.emplace_back(H * (uint64_t)b.W, b);
     }
-    std::stable_sort(v.begin(), v.end(), [](const std::pair<uint64_t, Buf> &a,
-                                            const std::pair<uint64_t, Buf> &c) {
-        return a.first > c.first;
-    });
-    // waves by scratch budget
+    std::stable_sort(v.begin(), v.end(),
+                     [](const std::pair<uint64_t, Buf> &a, const std::pair<uint64_t, Buf> &c) {
+                         return a.first > c.first;
+                     });
     uint64_t used = 0;
     uint32_t wave = 0;
     for (auto &p : v) {
-        uint64_t off1 = 0;
-        const uint64_t sb = scratch_bytes(p.second.H, p.second.W, p.second.L, &off1);
+        const uint64_t sb = align256(scratch_bytes(p.second.H, p.second.W, p.second.L, nullptr));
         if (used > 0 && used + sb > kScratchBudget) {
             ++wave;
             used = 0;
@@ -520,118 +549,95 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
         used += sb;
         bp.scratch = std::max(bp.scratch, used);
     }
-    bp.waves.assign(bp.bufs.empty() ? 0 : wave + 1, Wave());
-    uint32_t maxL = 0;
-    for (auto &b : bp.bufs)
-        maxL = std::max(maxL, b.L);
-    for (auto &wv : bp.waves) {
-        wv.fwd = fwd;
-        wv.levels.assign(maxL, std::array<LevelList, 4>());
-    }
+    bp.waves.assign(bp.bufs.empty() ? 0 : wave + 1, DagWave());
     return FRAG_OK;
 }
 
-// fill the level lists once the scratch base is known; lay out descriptors
-void fill_batch(BatchPlan &bp, uint8_t *scratch_base, size_t desc_base_off, const DeviceState &d)
+// jobs and units of every wave, with scratch pointers from `scratch_base`;
+// then the layout of the descriptors after the scratch
+void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
 {
-    for (auto &wv : bp.waves)
-        for (auto &slot : wv.levels)
-            for (auto &ll : slot)
-                ll.jobs.clear();
+    for (auto &wv : bp.waves) {
+        wv.jobs.clear();
+        wv.first.clear();
+        wv.levels.clear();
+        wv.units.clear();
+        wv.counters = 0;
+    }
     for (size_t i = 0; i < bp.bufs.size(); ++i) {
         Buf &b = bp.bufs[i];
-        uint64_t off1 = 0;
-        scratch_bytes(b.H, b.W, b.L, &off1);
-        b.scr[0] = scratch_base ? scratch_base + bp.scr_off[i] : nullptr;
-        b.scr[1] = scratch_base ? scratch_base + bp.scr_off[i] + off1 : nullptr;
-        Wave &wv = bp.waves[bp.wave_of[i]];
-        for (uint32_t l = 1; l <= b.L; ++l) {
-            const uint32_t slot = wv.fwd ? l - 1 : (uint32_t)wv.levels.size() - l;
-            const LevelJob j = wv.fwd ? protect_level(b, l, kSegPairs) : recover_level(b, l, kSegPairs);
-            const int v = frag::level_variant(j, wv.fwd);
-            wv.levels[slot][v].variant = v;
-            wv.levels[slot][v].jobs.push_back(j);
-        }
+        uint64_t off[frag::kMaxInlineJobs] = {0};
+        scratch_bytes(b.H, b.W, b.L, off);
+        for (uint32_t l = 1; l < b.L; ++l)
+            b.scr[l] = scratch_base + bp.scr_off[i] + off[l];
+        DagWave &wv = bp.waves[bp.wave_of[i]];
+        const uint32_t first = (uint32_t)wv.jobs.size();
+        buffer_jobs(bp.fwd, b, first, &wv.counters, wv.jobs);
+        wv.first.push_back(first);
+        wv.levels.push_back(b.L);
     }
-    size_t off = desc_base_off;
-    uint32_t q = 0;
     for (auto &wv : bp.waves)
-        for (auto &slot : wv.levels)
-            for (auto &ll : slot) {
-                uint64_t pair_strips = 0;
-                for (auto &j : ll.jobs)
-                    pair_strips += (uint64_t)j.strips * (j.Hs / 2);
-                const uint32_t seg = seg_pairs_for(d, pair_strips);
-                ll.start.assign(1, 0);
-                for (auto &j : ll.jobs) {
-                    decompose(j, seg);
-                    ll.start.push_back(ll.start.back() + (uint64_t)j.strips * j.segs);
-                }
-                ll.job_off = off;
-                off += align256(std::max<size_t>(1, ll.jobs.size()) * sizeof(LevelJob));
-                ll.start_off = off;
-                off += align256(ll.start.size() * sizeof(uint64_t));
-                ll.queue_index = q++;
-            }
-    bp.queues = q;
-    bp.desc_bytes = off - desc_base_off + align256(sizeof(unsigned long long) * std::max(q, 1u));
+        wave_units(wv.jobs, wv.first, wv.levels, wv.units);
+    size_t off = align256(bp.scratch);
+    for (auto &wv : bp.waves) {
+        wv.jobs_off = off;
+        off += align256(std::max<size_t>(1, wv.jobs.size()) * sizeof(LevelJob));
+        wv.units_off = off;
+        off += align256(std::max<size_t>(1, wv.units.size()) * sizeof(DagUnit));
+        wv.done_off = off;
+        off += align256(4ull * std::max(1u, wv.counters));
+        wv.queue_off = off;
+        off += 256;
+    }
+    bp.desc_bytes = off - align256(bp.scratch);
 }
 
-// device memory: [scratch][descriptors][queue heads]
-frag_status upload_batch(BatchPlan &bp, uint8_t *mem, cudaStream_t s, bool async)
+size_t batch_mem_bytes(const BatchPlan &bp) { return align256(bp.scratch) + bp.desc_bytes; }
+
+frag_status upload_batch(const BatchPlan &bp, uint8_t *mem, cudaStream_t s, bool async)
 {
-    const size_t desc0 = align256(bp.scratch);
+    const size_t base = align256(bp.scratch);
     std::vector<uint8_t> host(bp.desc_bytes, 0);
-    for (auto &wv : bp.waves)
-        for (auto &slot : wv.levels)
-            for (auto &ll : slot) {
-                if (!ll.jobs.empty())
-                    std::memcpy(host.data() + (ll.job_off - desc0), ll.jobs.data(),
-                                ll.jobs.size() * sizeof(LevelJob));
-                std::memcpy(host.data() + (ll.start_off - desc0), ll.start.data(),
-                            ll.start.size() * sizeof(uint64_t));
-            }
-    cudaError_t e = async ? cudaMemcpyAsync(mem + desc0, host.data(), host.size(), cudaMemcpyHostToDevice, s)
-                          : cudaMemcpy(mem + desc0, host.data(), host.size(), cudaMemcpyHostToDevice);
+    for (const auto &wv : bp.waves) {
+        std::memcpy(host.data() + (wv.jobs_off - base), wv.jobs.data(), wv.jobs.size() * sizeof(LevelJob));
+        std::memcpy(host.data() + (wv.units_off - base), wv.units.data(), wv.units.size() * sizeof(DagUnit));
+    }
+    cudaError_t e = async ? cudaMemcpyAsync(mem + base, host.data(), host.size(), cudaMemcpyHostToDevice, s)
+                          : cudaMemcpy(mem + base, host.data(), host.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess)
         return cuda_fail(e, "batch descriptor upload");
     return FRAG_OK;
 }
 
-size_t queue_off(const BatchPlan &bp) { return align256(bp.scratch) + bp.desc_bytes - align256(sizeof(unsigned long long) * std::max(bp.queues, 1u)); }
-
 frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, const uint32_t *rk,
                          cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(mem + queue_off(bp), 0, sizeof(unsigned long long) * std::max(bp.queues, 1u), s);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "queue reset");
-    for (const auto &wv : bp.waves)
-        for (const auto &slot : wv.levels)
-            for (const auto &ll : slot) {
-                if (ll.jobs.empty())
-                    continue;
-                LevelWork w;
-                std::memset(&w, 0, sizeof(w));
-                w.jobs = (const LevelJob *)(mem + ll.job_off);
-                w.unit_start = (const uint64_t *)(mem + ll.start_off);
-                w.njobs = (uint32_t)ll.jobs.size();
-                w.total_units = ll.start.back();
-                w.queue = (unsigned long long *)(mem + queue_off(bp)) + ll.queue_index;
-                w.aes_tables = d.tables;
-                w.round_keys = rk;
-                w.err = d.err;
-                uint32_t grid = 0;
-                frag_status st = level_grid(d, wv.fwd, ll.variant, w.total_units, &grid);
-                if (st != FRAG_OK)
-                    return st;
-                if ((e = frag::launch_level(wv.fwd, ll.variant, w, grid, s)) != cudaSuccess)
-                    return cuda_fail(e, "batch launch");
-            }
+    for (const auto &wv : bp.waves) {
+        if (wv.units.empty())
+            continue;
+        cudaError_t e = cudaMemsetAsync(mem + wv.done_off, 0, wv.queue_off + 256 - wv.done_off, s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "counter reset");
+        DagWork w;
+        std::memset(&w, 0, sizeof(w));
+        w.jobs = (const LevelJob *)(mem + wv.jobs_off);
+        w.units = (const DagUnit *)(mem + wv.units_off);
+        w.total_units = wv.units.size();
+        w.done = (unsigned *)(mem + wv.done_off);
+        w.queue = (unsigned long long *)(mem + wv.queue_off);
+        w.aes_tables = d.tables;
+        w.round_keys = rk;
+        w.err = d.err;
+        w.spin_limit = kSpinLimit;
+        uint32_t grid = 0;
+        frag_status st = dag_grid(d, bp.fwd, w.total_units, &grid);
+        if (st != FRAG_OK)
+            return st;
+        if ((e = frag::launch_dag(bp.fwd, w, grid, s)) != cudaSuccess)
+            return cuda_fail(e, "batch launch");
+    }
     return FRAG_OK;
 }
-
-size_t batch_mem_bytes(const BatchPlan &bp) { return align256(bp.scratch) + bp.desc_bytes; }
 
 frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, uint32_t count,
                            frag_key key, cudaStream_t s)
@@ -653,20 +659,29 @@ frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, 
     const uint32_t *rk = nullptr;
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
-    // descriptor offsets do not depend on the scratch base: size on a copy
-    BatchPlan sizing = bp;
-    fill_batch(sizing, nullptr, align256(bp.scratch), *d);
+    BatchPlan sizing = bp; // the layout does not depend on the scratch base
+    fill_batch(sizing, nullptr);
     uint8_t *mem = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&mem, batch_mem_bytes(sizing), s);
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaMallocAsync(batch)");
-    fill_batch(bp, mem, align256(bp.scratch), *d);
+    fill_batch(bp, mem);
     st = upload_batch(bp, mem, s, true);
     if (st == FRAG_OK)
         st = launch_batch(bp, mem, *d, rk, s);
     cudaFreeAsync(mem, s); // released once the launches have completed
     return st;
 }
+
+} // namespace
+
+struct frag_batch_s {
+    int device = 0;
+    BatchPlan bp;
+    uint8_t *mem = nullptr; // [scratch][descriptors, counters, queue heads]
+};
+
+namespace {
 
 frag_status create_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint32_t count,
                          frag_batch *out)
@@ -685,13 +700,13 @@ frag_status create_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, ui
         st = device_state(&d, &bt->device);
     if (st == FRAG_OK && !bt->bp.bufs.empty()) {
         BatchPlan sizing = bt->bp;
-        fill_batch(sizing, nullptr, align256(sizing.scratch), *d);
+        fill_batch(sizing, nullptr);
         cudaError_t e = cudaMalloc((void **)&bt->mem, batch_mem_bytes(sizing));
         if (e != cudaSuccess) {
             bt->mem = nullptr;
             st = cuda_fail(e, "cudaMalloc(batch)");
         } else {
-            fill_batch(bt->bp, bt->mem, align256(bt->bp.scratch), *d);
+            fill_batch(bt->bp, bt->mem);
             st = upload_batch(bt->bp, bt->mem, nullptr, false);
         }
     }

@@ -48,7 +48,32 @@ struct LevelJob {
     uint64_t nonce;
     uint32_t Ws, Hs;       // level-(l-1) image
     uint32_t strips, segs, seg_pairs;
+    uint32_t done_off; // first completion counter of this job's segments
+    int32_t dep;       // job whose LL output this job reads (-1: none)
     uint8_t src_bytes, final_level, top_level, out_bytes;
+};
+
+struct DagUnit {
+    uint32_t job, sx, sy;
+};
+
+constexpr int kMaxInlineJobs = 8;
+
+struct DagWork {
+    // one buffer: its levels inline, units implied (wavefront rounds); many
+    // buffers: a job array and an explicit dependency-ordered unit list
+    LevelJob inline_jobs[kMaxInlineJobs];
+    uint32_t n_inline;    // > 0: implicit units over inline_jobs
+    uint32_t lag;         // rounds between consecutive levels (implicit mode)
+    const LevelJob *jobs;
+    const DagUnit *units; // dependency-ordered
+    uint64_t total_units;
+    unsigned long long *queue;
+    unsigned *done;       // completed strips per (job, segment)
+    const uint32_t *aes_tables;
+    const uint32_t *round_keys;
+    int *err;
+    uint32_t spin_limit;
 };
 
 struct LevelWork {
@@ -105,10 +130,10 @@ const uint32_t *host_aes_words();                             // kAesWords words
 void host_expand_key(const uint8_t key[16], uint32_t rk[44]); // FIPS-197 key schedule
 
 // streaming level kernels (stream_kernels.cu)
-int level_variant(const LevelJob &j, bool fwd); // 0..3: which kernel instantiation serves j
-cudaError_t launch_level(bool fwd, int variant, const LevelWork &w, uint32_t grid,
-                         cudaStream_t stream);
-cudaError_t level_occupancy(bool fwd, int variant, int *blocks_per_sm);
+cudaError_t launch_dag(bool fwd, const DagWork &w, uint32_t grid, cudaStream_t stream);
+cudaError_t dag_occupancy(bool fwd, int *blocks_per_sm);
+cudaError_t launch_stall_probe(const unsigned *ctr, uint32_t spin_limit, int *err,
+                               cudaStream_t stream);
 constexpr int kStripCols = 240; // level-(l-1) columns owned by one warp strip
 
 // kernels (tile_kernels.cu)

@@ -151,7 +151,7 @@ __device__ __forceinline__ Raw load_row(const LevelJob &j, int r, int c, bool ve
         const int wpr = (int)j.Ws / 2, w0 = c >> 1;
         const uint64_t base = (uint64_t)r * (uint64_t)wpr;
         if (r < (int)j.Hs && vec && c >= 0 && c + 8 <= (int)j.Ws) {
-            const uint4 t = __ldg(reinterpret_cast<const uint4 *>(src + base + w0));
+            const uint4 t = __ldcg(reinterpret_cast<const uint4 *>(src + base + w0));
             raw.w[0] = t.x;
             raw.w[1] = t.y;
             raw.w[2] = t.z;
@@ -160,7 +160,7 @@ __device__ __forceinline__ Raw load_row(const LevelJob &j, int r, int c, bool ve
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int ww = w0 + i;
-                raw.w[i] = (r < (int)j.Hs && ww >= 0 && ww < wpr) ? __ldg(src + base + ww) : kB2;
+                raw.w[i] = (r < (int)j.Hs && ww >= 0 && ww < wpr) ? __ldcg(src + base + ww) : kB2;
             }
         }
     }
@@ -406,12 +406,12 @@ __device__ __forceinline__ Coef load_coef(const LevelJob &j, int k, int x, bool 
         } else {
             const uint32_t *p = ll + (uint64_t)k * (uint64_t)wpr + x / 2;
             if (vec && x + 4 <= Wl && ((uintptr_t)p & 7u) == 0) {
-                const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+                const uint2 t = __ldcg(reinterpret_cast<const uint2 *>(p));
                 cf.sl[0] = t.x;
                 cf.sl[1] = t.y;
             } else {
-                cf.sl[0] = __ldg(p);
-                cf.sl[1] = (x + 2 < Wl) ? __ldg(p + 1) : kB2;
+                cf.sl[0] = __ldcg(p);
+                cf.sl[1] = (x + 2 < Wl) ? __ldcg(p + 1) : kB2;
             }
         }
     }
@@ -546,32 +546,122 @@ __device__ void inv_unit(const LevelJob &j, int sx, int sy, const AesTab &aes, i
 } // namespace strm
 
 // ---------------------------------------------------------------------------
-// kernel: persistent warps over (job, strip, segment) units
+// kernel: persistent warps over a dependency-ordered queue of units
 // ---------------------------------------------------------------------------
+// All levels of all buffers of a call run in one launch.  The queue lists
+// units so that every unit's producers come before it; a unit whose input is
+// another level's LL waits (lane 0, bounded spin) until the producer row
+// segments it reads are complete, so the coarse levels stream right behind
+// the fine ones.  A wait that runs out sets the error word to 3
+// (FRAG_ETIMEOUT) and the unit is skipped but still reported complete, so no
+// consumer can wait forever.
 constexpr int kStreamThreads = 256;
 
-__device__ __forceinline__ const LevelJob *level_job(const LevelWork &w, uint64_t u, uint64_t &local)
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 {
-    if (w.jobs == nullptr) {
-        local = u;
-        return &w.single;
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// lane 0: wait until done[lo .. hi] all reach `target`
+__device__ __forceinline__ bool wait_segments(const unsigned *done, uint32_t lo, uint32_t hi,
+                                              unsigned target, uint32_t spin_limit, int *err)
+{
+    for (uint32_t s = lo; s <= hi; ++s) {
+        uint32_t it = 0;
+        while (ld_acquire(done + s) < target) {
+            if (++it > spin_limit) {
+                atomicCAS(err, 0, 3);
+                return false;
+            }
+            __nanosleep(100);
+        }
     }
-    uint32_t lo = 0, hi = w.njobs;
+    return true;
+}
+
+__device__ __forceinline__ const LevelJob &dag_job(const DagWork &w, uint32_t i)
+{
+    return w.n_inline ? w.inline_jobs[i] : w.jobs[i];
+}
+
+// Implicit order for one buffer: job m (m-th level in processing order) runs
+// its segment sy in round sy + m * lag; rounds are listed in order, levels in
+// order within a round, strips within a level.  All jobs have the same
+// segment count.
+__device__ __forceinline__ void implicit_unit(const DagWork &w, uint64_t t, uint32_t &job,
+                                              uint32_t &sx, uint32_t &sy)
+{
+    const int n = (int)w.n_inline;
+    const int NS = (int)w.inline_jobs[0].segs;
+    const int lag = (int)w.lag;
+    auto before = [&](int r) -> uint64_t { // units in rounds < r
+        uint64_t c = 0;
+        for (int m = 0; m < n; ++m)
+            c += (uint64_t)w.inline_jobs[m].strips * (uint64_t)min(max(r - lag * m, 0), NS);
+        return c;
+    };
+    int lo = 0, hi = NS + lag * (n - 1); // before(lo) <= t < before(hi)
     while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) / 2;
-        if (w.unit_start[mid] <= u)
+        const int mid = (lo + hi) / 2;
+        if (before(mid) <= t)
             lo = mid;
         else
             hi = mid;
     }
-    local = u - w.unit_start[lo];
-    return &w.jobs[lo];
+    uint64_t off = t - before(lo);
+    job = 0;
+    sx = sy = 0;
+    for (int m = 0; m < n; ++m) {
+        const int seg = lo - lag * m;
+        if (seg < 0 || seg >= NS)
+            continue;
+        const uint64_t st = w.inline_jobs[m].strips;
+        if (off < st) {
+            job = (uint32_t)m;
+            sx = (uint32_t)off;
+            sy = (uint32_t)seg;
+            return;
+        }
+        off -= st;
+    }
 }
 
-// V1: forward = byte source, inverse = top level (private fragment in);
-// V2: forward = final level (private fragment out), inverse = byte output.
-template <bool FWD, bool V1, bool V2>
-__global__ void __launch_bounds__(kStreamThreads, 3) level_kernel(LevelWork w)
+// true if the unit may run (its producers are complete)
+template <bool FWD>
+__device__ __forceinline__ bool wait_producers(const DagWork &w, const LevelJob &j, int sy, int lane)
+{
+    int ok = 1;
+    if (j.dep >= 0) {
+        if (lane == 0) {
+            const LevelJob &p = dag_job(w, (uint32_t)j.dep);
+            int rlo, rhi; // producer segments covering the LL rows this unit reads
+            if (FWD) {
+                const int q0 = sy * (int)j.seg_pairs;
+                const int q1 = min(q0 + (int)j.seg_pairs, (int)j.Hs / 2);
+                rlo = max(2 * q0 - 2, 0) / (int)p.seg_pairs;
+                rhi = min(2 * q1, (int)j.Hs - 1) / (int)p.seg_pairs;
+            } else {
+                const int k0 = sy * (int)j.seg_pairs;
+                const int k1 = min(k0 + (int)j.seg_pairs, (int)j.Hs / 2);
+                const int Hl = (int)j.Hs / 2;
+                rlo = (max(k0 - 1, 0) / 2) / (int)p.seg_pairs;
+                rhi = (min(k1 + 1, Hl - 1) / 2) / (int)p.seg_pairs;
+            }
+            ok = wait_segments(w.done + p.done_off, (uint32_t)rlo, (uint32_t)rhi, p.strips,
+                               w.spin_limit, w.err)
+                     ? 1
+                     : 0;
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        __syncwarp();
+    }
+    return ok != 0;
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(kStreamThreads, 2) dag_kernel(DagWork w)
 {
     __shared__ AesTab aes;
     for (int i = threadIdx.x; i < kAesWords; i += blockDim.x)
@@ -580,61 +670,87 @@ __global__ void __launch_bounds__(kStreamThreads, 3) level_kernel(LevelWork w)
         aes.rk[i] = w.round_keys[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    uint64_t u = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     for (;;) {
-        if (w.queue != nullptr) {
-            unsigned long long t = 0;
-            if (lane == 0)
-                t = atomicAdd(w.queue, 1ull);
-            u = __shfl_sync(0xffffffffu, t, 0);
-        }
-        if (u >= w.total_units)
+        unsigned long long t = 0;
+        if (lane == 0)
+            t = atomicAdd(w.queue, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= w.total_units)
             break;
-        uint64_t local;
-        const LevelJob j = *level_job(w, u, local);
-        const int sx = (int)(local % j.strips), sy = (int)(local / j.strips);
-        if (FWD)
-            strm::fwd_unit<V1, V2>(j, sx, sy, aes, lane);
-        else
-            strm::inv_unit<V1, V2>(j, sx, sy, aes, lane);
-        if (w.queue == nullptr)
-            u += warps;
+        uint32_t ji, ux, uy;
+        if (w.n_inline) {
+            implicit_unit(w, t, ji, ux, uy);
+        } else {
+            const DagUnit un = w.units[t];
+            ji = un.job;
+            ux = un.sx;
+            uy = un.sy;
+        }
+        const LevelJob j = dag_job(w, ji);
+        const int sx = (int)ux, sy = (int)uy;
+        if (wait_producers<FWD>(w, j, sy, lane)) {
+            if (FWD) {
+                if (j.src_bytes) {
+                    if (j.final_level)
+                        strm::fwd_unit<true, true>(j, sx, sy, aes, lane);
+                    else
+                        strm::fwd_unit<true, false>(j, sx, sy, aes, lane);
+                } else {
+                    if (j.final_level)
+                        strm::fwd_unit<false, true>(j, sx, sy, aes, lane);
+                    else
+                        strm::fwd_unit<false, false>(j, sx, sy, aes, lane);
+                }
+            } else {
+                if (j.top_level) {
+                    if (j.out_bytes)
+                        strm::inv_unit<true, true>(j, sx, sy, aes, lane);
+                    else
+                        strm::inv_unit<true, false>(j, sx, sy, aes, lane);
+                } else {
+                    if (j.out_bytes)
+                        strm::inv_unit<false, true>(j, sx, sy, aes, lane);
+                    else
+                        strm::inv_unit<false, false>(j, sx, sy, aes, lane);
+                }
+            }
+        }
+        // publish: every lane's stores before the count
+        __threadfence();
+        __syncwarp();
+        if (lane == 0)
+            atomicAdd(w.done + j.done_off + sy, 1u);
     }
 }
 
-int level_variant(const LevelJob &j, bool fwd)
+cudaError_t launch_dag(bool fwd, const DagWork &w, uint32_t grid, cudaStream_t stream)
 {
-    return fwd ? (j.src_bytes ? 1 : 0) + (j.final_level ? 2 : 0)
-               : (j.top_level ? 1 : 0) + (j.out_bytes ? 2 : 0);
+    if (fwd)
+        dag_kernel<true><<<grid, kStreamThreads, 0, stream>>>(w);
+    else
+        dag_kernel<false><<<grid, kStreamThreads, 0, stream>>>(w);
+    return cudaGetLastError();
 }
 
-static const void *level_fn(bool fwd, int variant)
+cudaError_t dag_occupancy(bool fwd, int *blocks_per_sm)
 {
-    switch ((fwd ? 4 : 0) + variant) {
-    case 0: return (const void *)level_kernel<false, false, false>;
-    case 1: return (const void *)level_kernel<false, true, false>;
-    case 2: return (const void *)level_kernel<false, false, true>;
-    case 3: return (const void *)level_kernel<false, true, true>;
-    case 4: return (const void *)level_kernel<true, false, false>;
-    case 5: return (const void *)level_kernel<true, true, false>;
-    case 6: return (const void *)level_kernel<true, false, true>;
-    default: return (const void *)level_kernel<true, true, true>;
-    }
+    const void *fn = fwd ? (const void *)dag_kernel<true> : (const void *)dag_kernel<false>;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kStreamThreads, 0);
 }
 
-cudaError_t launch_level(bool fwd, int variant, const LevelWork &w, uint32_t grid,
-                         cudaStream_t stream)
+// A lone wait on a counter nothing increments: lets a test check that a wait
+// that runs out reports FRAG_ETIMEOUT and returns.
+__global__ void stall_probe_kernel(const unsigned *ctr, uint32_t spin_limit, int *err)
 {
-    void *args[] = {const_cast<LevelWork *>(&w)};
-    return cudaLaunchKernel(level_fn(fwd, variant), dim3(grid), dim3(kStreamThreads), args, 0,
-                            stream);
+    if (threadIdx.x == 0)
+        wait_segments(ctr, 0, 0, 1u, spin_limit, err);
 }
 
-cudaError_t level_occupancy(bool fwd, int variant, int *blocks_per_sm)
+cudaError_t launch_stall_probe(const unsigned *ctr, uint32_t spin_limit, int *err,
+                               cudaStream_t stream)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, level_fn(fwd, variant),
-                                                         kStreamThreads, 0);
+    stall_probe_kernel<<<1, 32, 0, stream>>>(ctr, spin_limit, err);
+    return cudaGetLastError();
 }
 
 } // namespace frag
