@@ -13,7 +13,8 @@ import os
 from typing import Iterable, List, Optional, Sequence, Tuple
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfrag.so")
+# FRAG_LIBRARY selects another build of the same library (e.g. a tuning variant)
+LIB_PATH = os.environ.get("FRAG_LIBRARY") or os.path.join(_HERE, "libfrag.so")
 
 FRAG_OK, FRAG_EINVAL, FRAG_EUNSUPPORTED, FRAG_ENOMEM, FRAG_ECUDA, FRAG_ETIMEOUT, FRAG_EDEVICE = range(7)
 STATUS_NAMES = {0: "FRAG_OK", 1: "FRAG_EINVAL", 2: "FRAG_EUNSUPPORTED", 3: "FRAG_ENOMEM",

@@ -33,11 +33,13 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, out: str = LIB, defines=()) -> str:
+    """Compile libfrag.so (or `out`, with extra -D `defines`) for sm_103a."""
+    if out == LIB and not defines and not force and not _stale():
         return LIB
-    tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [NVCC] + FLAGS + ["-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
+    tmp = out + ".tmp.%d" % os.getpid()
+    cmd = [NVCC] + FLAGS + ["-D" + d for d in defines] + ["-o", tmp] + \
+        [os.path.join(CSRC, s) for s in SOURCES]
     res = subprocess.run(cmd, capture_output=True, text=True)
     log = os.path.join(HERE, "build.log")
     with open(log, "w") as f:
@@ -47,8 +49,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError("nvcc failed (see %s)" % log)
     if verbose:
         sys.stdout.write(res.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

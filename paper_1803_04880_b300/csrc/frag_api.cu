@@ -282,13 +282,13 @@ uint64_t align256(uint64_t v) { return (v + 255) / 256 * 256; }
 
 uint64_t ll_bytes(uint32_t H, uint32_t W, uint32_t l) { return 2ull * (H >> l) * (uint64_t)(W >> l); }
 
-// scratch of one buffer: LL_1 .. LL_{L-1}, each in its own region (the levels
-// of one buffer run concurrently, so no region can be reused); off[l] is the
-// offset of LL_l
-uint64_t scratch_bytes(uint32_t H, uint32_t W, uint32_t L, uint64_t *off)
+// scratch of one buffer: LL_1 .. LL_{L-1}, each in its own region (the jobs
+// of one buffer run concurrently, so no region can be reused), and for the
+// inverse the deciphered LL_L; off[l] is the offset of LL_l
+uint64_t scratch_bytes(bool fwd, uint32_t H, uint32_t W, uint32_t L, uint64_t *off)
 {
     uint64_t total = 0;
-    for (uint32_t l = 1; l < L; ++l) {
+    for (uint32_t l = 1; l < (fwd ? L : L + 1); ++l) {
         if (off)
             off[l] = total;
         total += align256(ll_bytes(H, W, l));
@@ -298,22 +298,35 @@ uint64_t scratch_bytes(uint32_t H, uint32_t W, uint32_t L, uint64_t *off)
 
 struct Buf {
     uint32_t W, L, H;
+    uint32_t R0; // level-0 rows per work segment
     uint64_t n, nonce;
     const uint8_t *in;
     uint8_t *priv, *pub;
     const uint8_t *priv_in, *pub_in;
     uint8_t *out;
-    uint8_t *scr[frag::kMaxInlineJobs]; // scr[l]: LL_l (1 <= l < L)
+    uint8_t *scr[frag::kMaxInlineJobs + 1]; // scr[l]: LL_l (1 <= l < L; l = L: deciphered LL_L)
 };
 
-// level-0 rows per work segment, the same at every level: a power of two
-// >= 2^L, so every level has the same number of segments
-uint32_t seg_rows0(uint32_t L)
+// Level-0 rows per work segment, the same at every level: a power of two
+// >= 2^L, so every level has the same number of segments.  64 rows unless the
+// first level would then have fewer than two units per resident warp; then
+// down to 16 (each segment re-reads three rows above it).
+uint32_t seg_rows0(uint32_t L, uint64_t l1_units_at_64, uint64_t resident_warps)
 {
     uint32_t r = 64;
+    uint64_t u = l1_units_at_64;
+    while (r > 16 && u < 2 * resident_warps) {
+        r >>= 1;
+        u <<= 1;
+    }
     while (r < (1u << L))
         r <<= 1;
     return r;
+}
+
+uint64_t l1_units_at_64(const Buf &b)
+{
+    return (uint64_t)((b.W + frag::kStripCols - 1) / frag::kStripCols) * ((b.H + 63) / 64);
 }
 
 LevelJob level_job(bool fwd, const Buf &b, uint32_t l, uint32_t R0)
@@ -333,7 +346,7 @@ LevelJob level_job(bool fwd, const Buf &b, uint32_t l, uint32_t R0)
         j.ll = l == b.L ? b.priv : b.scr[l];
     } else {
         j.top_level = l == b.L;
-        j.ll_in = l == b.L ? b.priv_in : b.scr[l];
+        j.ll_in = b.scr[l];
         j.out_bytes = l == 1;
         j.out = l == 1 ? b.out : b.scr[l - 1];
     }
@@ -343,17 +356,49 @@ LevelJob level_job(bool fwd, const Buf &b, uint32_t l, uint32_t R0)
     j.seg_pairs = R0 >> l;
     j.segs = ((j.Hs / 2) + j.seg_pairs - 1) / j.seg_pairs;
     j.dep = -1;
+    j.kind = frag::kJobLevel;
     return j;
 }
 
-// the jobs of one buffer in processing order (forward l = 1..L, inverse
-// l = L..1); each depends on the previous one
+// AES-128-CTR over the private fragment (LL_L): forward in place, inverse into
+// the plaintext scratch; segments of R0 >> L rows of LL_L, as at the last level
+LevelJob cipher_job(bool fwd, const Buf &b, uint32_t R0)
+{
+    LevelJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.kind = frag::kJobCipher;
+    j.Ws = b.W >> b.L;
+    j.Hs = b.H >> b.L;
+    if (fwd) {
+        j.ll = b.priv;
+    } else {
+        j.ll_in = b.priv_in;
+        j.out = b.scr[b.L];
+    }
+    j.n = b.n;
+    j.nonce = b.nonce;
+    j.seg_pairs = R0 >> b.L;
+    j.segs = (j.Hs + j.seg_pairs - 1) / j.seg_pairs;
+    // blocks starting in one segment's rows, at most
+    const uint64_t blocks = (uint64_t)j.seg_pairs * 2ull * j.Ws / 16 + 2;
+    j.strips = (uint32_t)((blocks + frag::kCipherBlocks - 1) / frag::kCipherBlocks);
+    j.dep = -1;
+    return j;
+}
+
+// the L + 1 jobs of one buffer in processing order (forward: levels 1..L, then
+// the cipher; inverse: the cipher, then levels L..1); each reads what the
+// previous one writes
 void buffer_jobs(bool fwd, const Buf &b, uint32_t first_job, uint32_t *counters,
                  std::vector<LevelJob> &jobs)
 {
-    const uint32_t R0 = seg_rows0(b.L);
-    for (uint32_t m = 0; m < b.L; ++m) {
-        LevelJob j = level_job(fwd, b, fwd ? m + 1 : b.L - m, R0);
+    const uint32_t R0 = b.R0;
+    for (uint32_t m = 0; m <= b.L; ++m) {
+        LevelJob j;
+        if (fwd)
+            j = m < b.L ? level_job(true, b, m + 1, R0) : cipher_job(true, b, R0);
+        else
+            j = m == 0 ? cipher_job(false, b, R0) : level_job(false, b, b.L + 1 - m, R0);
         j.dep = m ? (int32_t)(first_job + m - 1) : -1;
         j.done_off = *counters;
         *counters += j.segs;
@@ -365,27 +410,27 @@ void buffer_jobs(bool fwd, const Buf &b, uint32_t first_job, uint32_t *counters,
 // queued only after about 1.5 times the resident warps' worth of earlier
 // units, so it rarely waits for its producers (small images end up level by
 // level; tall ones stream with the coarse levels behind the fine ones).
-uint32_t buffer_lag(const std::vector<LevelJob> &jobs, uint32_t first_job, uint32_t L,
+uint32_t buffer_lag(const std::vector<LevelJob> &jobs, uint32_t first_job, uint32_t njobs,
                     uint64_t resident_warps)
 {
     uint64_t per_round = 0;
-    for (uint32_t m = 0; m < L; ++m)
+    for (uint32_t m = 0; m < njobs; ++m)
         per_round += jobs[first_job + m].strips;
     const uint64_t lag = (3 * resident_warps / 2 + per_round - 1) / std::max<uint64_t>(1, per_round);
     return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(kMinLag, lag), 1u << 24);
 }
 
-// units of a wave of buffers, level by level (level m of every buffer before
-// level m + 1 of any), each level's units in row-segment order
+// units of a wave of buffers, job by job (job m of every buffer before job
+// m + 1 of any), each job's units in row-segment order
 void wave_units(const std::vector<LevelJob> &jobs, const std::vector<uint32_t> &first,
-                const std::vector<uint32_t> &levels, std::vector<DagUnit> &units)
+                const std::vector<uint32_t> &njobs, std::vector<DagUnit> &units)
 {
-    uint32_t maxL = 0;
-    for (uint32_t L : levels)
-        maxL = std::max(maxL, L);
-    for (uint32_t m = 0; m < maxL; ++m)
+    uint32_t maxj = 0;
+    for (uint32_t k : njobs)
+        maxj = std::max(maxj, k);
+    for (uint32_t m = 0; m < maxj; ++m)
         for (size_t b = 0; b < first.size(); ++b) {
-            if (m >= levels[b])
+            if (m >= njobs[b])
                 continue;
             const LevelJob &j = jobs[first[b] + m];
             for (uint32_t sy = 0; sy < j.segs; ++sy)
@@ -412,7 +457,7 @@ frag_status dag_grid(DeviceState &d, bool fwd, uint64_t units, uint32_t *grid)
         std::lock_guard<std::mutex> lock(g_mu);
         d.occ[fwd][7777] = occ;
     }
-    const uint64_t blocks = (units + 7) / 8; // 8 warps per block
+    const uint64_t blocks = units / 8 + (units % 8 != 0); // 8 warps per block
     *grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)d.sms * occ, blocks));
     return FRAG_OK;
 }
@@ -428,18 +473,23 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     const uint32_t *rk = nullptr;
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
-    if (b.L > (uint32_t)frag::kMaxInlineJobs)
-        return fail(FRAG_EUNSUPPORTED, "more than %d levels", frag::kMaxInlineJobs);
+    const uint32_t njobs = b.L + 1;
+    if (njobs > (uint32_t)frag::kMaxInlineJobs)
+        return fail(FRAG_EUNSUPPORTED, "more than %d levels", frag::kMaxInlineJobs - 1);
     // one stream-ordered allocation: [scratch][counters][queue head]
-    uint64_t off[frag::kMaxInlineJobs] = {0};
-    const uint64_t sb = align256(scratch_bytes(b.H, b.W, b.L, off));
-    const uint32_t NS = ((b.H >> 1) + (seg_rows0(b.L) >> 1) - 1) / (seg_rows0(b.L) >> 1);
-    const uint64_t cb = align256(4ull * NS * b.L);
+    uint64_t off[frag::kMaxInlineJobs + 1] = {0};
+    const uint64_t sb = align256(scratch_bytes(fwd, b.H, b.W, b.L, off));
+    uint32_t grid = 0;
+    if ((st = dag_grid(*d, fwd, ~0ull, &grid)) != FRAG_OK)
+        return st;
+    b.R0 = seg_rows0(b.L, l1_units_at_64(b), (uint64_t)grid * 8);
+    const uint32_t NS = (b.H + b.R0 - 1) / b.R0;
+    const uint64_t cb = align256(4ull * NS * njobs);
     uint8_t *mem = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&mem, sb + cb + 256, s);
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaMallocAsync(level scratch)");
-    for (uint32_t l = 1; l < b.L; ++l)
+    for (uint32_t l = 1; l < (fwd ? b.L : b.L + 1); ++l)
         b.scr[l] = mem + off[l];
     std::vector<LevelJob> jobs;
     uint32_t counters = 0;
@@ -447,12 +497,12 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     DagWork w;
     std::memset(&w, 0, sizeof(w));
     uint64_t units = 0;
-    for (uint32_t m = 0; m < b.L; ++m) {
+    for (uint32_t m = 0; m < njobs; ++m) {
         w.inline_jobs[m] = jobs[m];
         units += (uint64_t)jobs[m].strips * jobs[m].segs;
     }
-    w.n_inline = b.L;
-    w.lag = buffer_lag(jobs, 0, b.L, (uint64_t)d->sms * 16);
+    w.n_inline = njobs;
+    w.lag = buffer_lag(jobs, 0, njobs, (uint64_t)grid * 8);
     w.total_units = units;
     w.done = (unsigned *)(mem + sb);
     w.queue = (unsigned long long *)(mem + sb + cb);
@@ -461,7 +511,6 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     w.err = d->err;
     w.spin_limit = kSpinLimit;
     e = cudaMemsetAsync(mem + sb, 0, cb + 256, s);
-    uint32_t grid = 0;
     if (e != cudaSuccess)
         st = cuda_fail(e, "counter reset");
     else if ((st = dag_grid(*d, fwd, units, &grid)) == FRAG_OK &&
@@ -477,7 +526,7 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
 // ---------------------------------------------------------------------------
 struct DagWave {
     std::vector<LevelJob> jobs;
-    std::vector<uint32_t> first, levels; // per buffer: first job, levels
+    std::vector<uint32_t> first, levels; // per buffer: first job, number of jobs
     std::vector<DagUnit> units;
     uint32_t counters = 0;
     size_t jobs_off = 0, units_off = 0, done_off = 0, queue_off = 0;
@@ -485,6 +534,7 @@ struct DagWave {
 
 struct BatchPlan {
     bool fwd = true;
+    uint64_t resident_warps = 0; // warps one launch keeps resident
     std::vector<Buf> bufs;
     std::vector<uint64_t> scr_off;
     std::vector<uint32_t> wave_of;
@@ -538,7 +588,7 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
     uint64_t used = 0;
     uint32_t wave = 0;
     for (auto &p : v) {
-        const uint64_t sb = align256(scratch_bytes(p.second.H, p.second.W, p.second.L, nullptr));
+        const uint64_t sb = align256(scratch_bytes(fwd, p.second.H, p.second.W, p.second.L, nullptr));
         if (used > 0 && used + sb > kScratchBudget) {
             ++wave;
             used = 0;
@@ -557,6 +607,10 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
 // then the layout of the descriptors after the scratch
 void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
 {
+    // one segment height for the whole batch, from its first-level units
+    uint64_t u64 = 0;
+    for (const Buf &b : bp.bufs)
+        u64 += l1_units_at_64(b);
     for (auto &wv : bp.waves) {
         wv.jobs.clear();
         wv.first.clear();
@@ -566,15 +620,16 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
     }
     for (size_t i = 0; i < bp.bufs.size(); ++i) {
         Buf &b = bp.bufs[i];
-        uint64_t off[frag::kMaxInlineJobs] = {0};
-        scratch_bytes(b.H, b.W, b.L, off);
-        for (uint32_t l = 1; l < b.L; ++l)
+        uint64_t off[frag::kMaxInlineJobs + 1] = {0};
+        b.R0 = seg_rows0(b.L, u64, bp.resident_warps);
+        scratch_bytes(bp.fwd, b.H, b.W, b.L, off);
+        for (uint32_t l = 1; l < (bp.fwd ? b.L : b.L + 1); ++l)
             b.scr[l] = scratch_base + bp.scr_off[i] + off[l];
         DagWave &wv = bp.waves[bp.wave_of[i]];
         const uint32_t first = (uint32_t)wv.jobs.size();
         buffer_jobs(bp.fwd, b, first, &wv.counters, wv.jobs);
         wv.first.push_back(first);
-        wv.levels.push_back(b.L);
+        wv.levels.push_back(b.L + 1);
     }
     for (auto &wv : bp.waves)
         wave_units(wv.jobs, wv.first, wv.levels, wv.units);
@@ -659,6 +714,10 @@ frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, 
     const uint32_t *rk = nullptr;
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
+    uint32_t grid = 0;
+    if ((st = dag_grid(*d, fwd, ~0ull, &grid)) != FRAG_OK)
+        return st;
+    bp.resident_warps = (uint64_t)grid * 8;
     BatchPlan sizing = bp; // the layout does not depend on the scratch base
     fill_batch(sizing, nullptr);
     uint8_t *mem = nullptr;
@@ -698,6 +757,9 @@ frag_status create_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, ui
     DeviceState *d = nullptr;
     if (st == FRAG_OK)
         st = device_state(&d, &bt->device);
+    uint32_t grid = 0;
+    if (st == FRAG_OK && (st = dag_grid(*d, fwd, ~0ull, &grid)) == FRAG_OK)
+        bt->bp.resident_warps = (uint64_t)grid * 8;
     if (st == FRAG_OK && !bt->bp.bufs.empty()) {
         BatchPlan sizing = bt->bp;
         fill_batch(sizing, nullptr);

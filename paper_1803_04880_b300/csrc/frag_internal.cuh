@@ -32,12 +32,20 @@ struct Job {
     uint32_t path;    // 0: generic tile body, 1: row/column-pass body (L <= 3)
 };
 
-// One level of one buffer for the streaming level kernels.  Forward: the
-// level-(l-1) image `src` (bytes at l = 1, else packed LL pairs) gives the
-// level-l bands and LL_l (packed pairs in scratch, or the private fragment at
-// the last level).  Inverse: LL_l (`ll_in`: packed pairs, or the private
-// fragment at the top level) and the bands give LL_{l-1} (packed pairs) or
-// the bytes (`out`, l = 1).
+// Job kinds of the dependency-ordered launch.
+constexpr uint8_t kJobLevel = 0;  // one LeGall 5/3 level of one buffer
+constexpr uint8_t kJobCipher = 1; // AES-128-CTR over the private fragment (LL_L)
+
+// One job of one buffer in the dependency-ordered launch.
+// Level job, forward: the level-(l-1) image `src` (bytes at l = 1, else packed
+// LL pairs) gives the level-l bands and LL_l (packed pairs in scratch, or
+// LL_L - 128 as int16 in the private fragment at the last level).  Inverse:
+// LL_l (`ll_in`: packed pairs, or LL_L - 128 as int16 at the top level) and
+// the bands give LL_{l-1} (packed pairs) or the bytes (`out`, l = 1).
+// Cipher job: Ws x Hs is LL_L; forward XORs the keystream into `ll` in place,
+// inverse writes `ll_in` XOR keystream to `out` (the plaintext scratch).
+// Segment sy covers rows [sy * seg_pairs, (sy + 1) * seg_pairs) of the job's
+// output (LL_l pair rows for a level job, LL_L rows for a cipher job).
 struct LevelJob {
     const uint8_t *src;
     uint8_t *hl, *lh, *hh; // band bases of level l
@@ -46,11 +54,11 @@ struct LevelJob {
     uint8_t *out;          // inverse output
     uint64_t n;            // bytes of the buffer (level-1 source / output)
     uint64_t nonce;
-    uint32_t Ws, Hs;       // level-(l-1) image
+    uint32_t Ws, Hs;       // level-(l-1) image (cipher job: LL_L)
     uint32_t strips, segs, seg_pairs;
     uint32_t done_off; // first completion counter of this job's segments
-    int32_t dep;       // job whose LL output this job reads (-1: none)
-    uint8_t src_bytes, final_level, top_level, out_bytes;
+    int32_t dep;       // job whose output this job reads (-1: none)
+    uint8_t kind, src_bytes, final_level, top_level, out_bytes;
 };
 
 struct DagUnit {
@@ -60,7 +68,7 @@ struct DagUnit {
 constexpr int kMaxInlineJobs = 8;
 
 struct DagWork {
-    // one buffer: its levels inline, units implied (wavefront rounds); many
+    // one buffer: its jobs inline, units implied (wavefront rounds); many
     // buffers: a job array and an explicit dependency-ordered unit list
     LevelJob inline_jobs[kMaxInlineJobs];
     uint32_t n_inline;    // > 0: implicit units over inline_jobs
@@ -74,18 +82,6 @@ struct DagWork {
     const uint32_t *round_keys;
     int *err;
     uint32_t spin_limit;
-};
-
-struct LevelWork {
-    LevelJob single;
-    const LevelJob *jobs;
-    const uint64_t *unit_start; // exclusive prefix of units per job (njobs + 1)
-    uint32_t njobs;
-    uint64_t total_units;
-    unsigned long long *queue;
-    const uint32_t *aes_tables;
-    const uint32_t *round_keys;
-    int *err;
 };
 
 // Launch-wide description of where jobs and tiles come from.
@@ -134,7 +130,8 @@ cudaError_t launch_dag(bool fwd, const DagWork &w, uint32_t grid, cudaStream_t s
 cudaError_t dag_occupancy(bool fwd, int *blocks_per_sm);
 cudaError_t launch_stall_probe(const unsigned *ctr, uint32_t spin_limit, int *err,
                                cudaStream_t stream);
-constexpr int kStripCols = 240; // level-(l-1) columns owned by one warp strip
+constexpr int kStripCols = 240;          // level-(l-1) columns owned by one warp strip
+constexpr uint32_t kCipherBlocks = 128;  // AES blocks of one cipher unit
 
 // kernels (tile_kernels.cu)
 constexpr uint32_t kFastTile = 256;   // owned tile side of the row/column-pass body
