@@ -162,20 +162,29 @@ frag_status frag_recover_batch(const frag_ritem *items, uint32_t count, frag_key
 
 /* Batch objects for CUDA-graph capture: *_create builds the work queue and
  * uploads it (synchronously) to the current device; frag_batch_run enqueues
- * only a memset of the queue head and the persistent kernel, so a capture of
- * frag_batch_run replays with no host work.  Buffers named in the items must
- * stay valid while the batch exists. */
+ * per wave only a memset of the completion counters and queue head and one
+ * launch of the dependency-ordered kernel, so a capture of frag_batch_run
+ * replays with no host work.  Buffers named in the items must stay valid
+ * while the batch exists. */
 frag_status frag_batch_create_protect(frag_batch *out, const frag_item *items, uint32_t count);
 frag_status frag_batch_create_recover(frag_batch *out, const frag_ritem *items, uint32_t count);
 frag_status frag_batch_run(frag_batch batch, frag_key key, frag_stream stream);
 frag_status frag_batch_destroy(frag_batch batch);
 
+/* What one frag_batch_run issues: *launches = kernel launches (one per wave
+ * of buffers whose scratch fits the library's budget), *scratch_bytes =
+ * device memory the batch holds for level scratch and descriptors.  Either
+ * pointer may be NULL.  FRAG_EINVAL if batch is NULL. */
+frag_status frag_batch_info(frag_batch batch, uint32_t *launches, uint64_t *scratch_bytes);
+
 /* Batched protect that allocates nothing.  The thesis has no counterpart:
  * this is a deployment aid.  Some callers may not call cudaMalloc at all --
  * a plug-in whose host process owns every byte of device memory through its
  * own pool, or a latency-critical path that cannot accept the implicit
- * synchronisation of a driver allocation.  This call runs the same kernel as
- * frag_protect_batch and gives byte-identical fragments, but keeps its work
+ * synchronisation of a driver allocation.  This call gives fragments
+ * byte-identical to frag_protect_batch (it runs the tile kernel that keeps
+ * every level of a tile in shared memory, so it needs no level scratch; up to
+ * 5 levels), but keeps its work
  * queue, job descriptors, round keys, AES tables and error word in one static
  * device array of about 110 KiB that every GPU loading this library holds
  * until the process exits; it calls no cudaMalloc, cudaFree or other

@@ -26,7 +26,8 @@ EXPORTS = [
     "frag_plan_set_tiling", "frag_plan_get_tiling", "frag_key_create", "frag_key_destroy",
     "frag_protect", "frag_recover", "frag_protect_host", "frag_recover_host",
     "frag_protect_batch", "frag_recover_batch", "frag_batch_create_protect",
-    "frag_batch_create_recover", "frag_batch_run", "frag_batch_destroy", "frag_get_error",
+    "frag_batch_create_recover", "frag_batch_run", "frag_batch_destroy", "frag_batch_info",
+    "frag_get_error",
     "frag_sync_status",
 ]
 
@@ -90,6 +91,7 @@ def lib():
                                       ctypes.c_int),
         "frag_batch_run": ([vp, vp, vp], ctypes.c_int),
         "frag_batch_destroy": ([vp], ctypes.c_int),
+        "frag_batch_info": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u64)], ctypes.c_int),
         "frag_get_error": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
         "frag_sync_status": ([vp], ctypes.c_int),
     }
@@ -276,6 +278,16 @@ class Batch:
 
     def run(self, key: Key, stream=None) -> None:
         check(lib().frag_batch_run(self._h, key.handle, _stream(stream)))
+
+    def info(self) -> Tuple[int, int]:
+        """(kernel launches per run, device bytes the batch holds)."""
+        n, b = ctypes.c_uint32(), ctypes.c_uint64()
+        check(lib().frag_batch_info(self._h, ctypes.byref(n), ctypes.byref(b)))
+        return n.value, b.value
+
+    @property
+    def launches(self) -> int:
+        return self.info()[0]
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

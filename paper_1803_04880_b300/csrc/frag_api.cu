@@ -400,6 +400,7 @@ void buffer_jobs(bool fwd, const Buf &b, uint32_t first_job, uint32_t *counters,
         else
             j = m == 0 ? cipher_job(false, b, R0) : level_job(false, b, b.L + 1 - m, R0);
         j.dep = m ? (int32_t)(first_job + m - 1) : -1;
+        j.publish = m < b.L; // the last job's output is read by nothing in the launch
         j.done_off = *counters;
         *counters += j.segs;
         jobs.push_back(j);
@@ -1109,6 +1110,20 @@ frag_status frag_batch_run(frag_batch batch, frag_key key, frag_stream stream)
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
     return launch_batch(batch->bp, batch->mem, *d, rk, (cudaStream_t)stream);
+}
+
+frag_status frag_batch_info(frag_batch batch, uint32_t *launches, uint64_t *scratch_bytes)
+{
+    if (batch == nullptr)
+        return fail(FRAG_EINVAL, "batch is NULL");
+    uint32_t n = 0;
+    for (const auto &wv : batch->bp.waves)
+        n += wv.units.empty() ? 0 : 1;
+    if (launches)
+        *launches = n;
+    if (scratch_bytes)
+        *scratch_bytes = batch->mem ? batch_mem_bytes(batch->bp) : 0;
+    return FRAG_OK;
 }
 
 frag_status frag_batch_destroy(frag_batch batch)

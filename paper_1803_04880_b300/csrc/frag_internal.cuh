@@ -59,6 +59,7 @@ struct LevelJob {
     uint32_t done_off; // first completion counter of this job's segments
     int32_t dep;       // job whose output this job reads (-1: none)
     uint8_t kind, src_bytes, final_level, top_level, out_bytes;
+    uint8_t publish; // another job of the launch reads this one's output
 };
 
 struct DagUnit {

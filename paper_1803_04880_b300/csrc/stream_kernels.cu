@@ -85,6 +85,24 @@ __device__ __forceinline__ void aes_block(const AesTab &a, uint64_t nonce, uint6
 
 namespace strm {
 
+// row pairs of loads kept in flight by an interior unit, and resident blocks
+// of 256 threads per SM the kernel is compiled for (tuning knobs)
+#ifndef FRAG_PREFETCH_BYTES
+#define FRAG_PREFETCH_BYTES 4
+#endif
+#ifndef FRAG_PREFETCH_PACKED
+#define FRAG_PREFETCH_PACKED 2
+#endif
+#ifndef FRAG_PREFETCH_INV
+#define FRAG_PREFETCH_INV 2
+#endif
+#ifndef FRAG_PREFETCH_GENERAL
+#define FRAG_PREFETCH_GENERAL 1
+#endif
+#ifndef FRAG_BLOCKS_PER_SM
+#define FRAG_BLOCKS_PER_SM 3
+#endif
+
 constexpr uint32_t kB2 = 0x40004000u;
 
 __device__ __forceinline__ uint32_t pavg(uint32_t a, uint32_t b) { return ((a + b) >> 1) & 0x7fff7fffu; }
@@ -311,7 +329,7 @@ __device__ void fwd_unit(const LevelJob &j, int sx, int sy, int lane)
         // every row of the segment and its halo exists and holds data, no
         // border rule applies, and every lane's addresses lie inside the
         // buffers (lanes 0 and 31 only skip their stores)
-        constexpr int D = BYTES ? 4 : 2; // row pairs of loads in flight
+        constexpr int D = BYTES ? FRAG_PREFETCH_BYTES : FRAG_PREFETCH_PACKED;
         const uint64_t pitch = BYTES ? (uint64_t)Ws : 2ull * (uint64_t)Ws;
         const uint8_t *rp = j.src + (uint64_t)(2 * q0 - 2) * pitch + (BYTES ? c : 2 * c);
         auto ld = [&](const uint8_t *p) -> Raw {
@@ -356,47 +374,68 @@ __device__ void fwd_unit(const LevelJob &j, int sx, int sy, int lane)
         const uint64_t ostep = 2ull * (uint64_t)Wl; // bytes per band row
         const uint64_t o0 = 2ull * ((uint64_t)q0 * (uint64_t)Wl + (uint64_t)x);
         uint8_t *phl = j.hl + o0, *plh = j.lh + o0, *phh = j.hh + o0, *pll = j.ll + o0;
-        for (int i = 0; i < n_it; i += D) {
+        auto step = [&](const Raw &c1, const Raw &c2) {
+            uint32_t o[4], e1[4], sv[4], dv[4];
+            lift_row<BYTES, false>(c1, c, Ws, false, o);
+            lift_row<BYTES, false>(c2, c, Ws, false, e1);
+            col_step(o, e1, e0, dp, false, sv, dv);
+            // sv[0..1] = LL, sv[2..3] = HL, dv[0..1] = LH, dv[2..3] = HH
+            if (own) {
+                *reinterpret_cast<uint2 *>(phl) = make_uint2(to_i16x2(sv[2]), to_i16x2(sv[3]));
+                *reinterpret_cast<uint2 *>(plh) = make_uint2(to_i16x2(dv[0]), to_i16x2(dv[1]));
+                *reinterpret_cast<uint2 *>(phh) = make_uint2(to_i16x2(dv[2]), to_i16x2(dv[3]));
+                *reinterpret_cast<uint2 *>(pll) = ll_out<FINAL>(sv);
+            }
+            phl += ostep;
+            plh += ostep;
+            phh += ostep;
+            pll += ostep;
+        };
+        // whole groups of D row pairs: slot s is consumed, then refilled D
+        // row pairs ahead (predicated loads, straight-line code)
+        int i = 0;
+        for (; i + D <= n_it; i += D) {
 #pragma unroll
             for (int s = 0; s < D; ++s) {
-                if (i + s < n_it) {
-                    const Raw c1 = ra[s], c2 = rb[s];
-                    if (i + s + D < n_it) {
-                        ra[s] = ld(rp);
-                        rb[s] = ld(rp + pitch);
-                    }
-                    rp += 2 * pitch;
-                    uint32_t o[4], e1[4], sv[4], dv[4];
-                    lift_row<BYTES, false>(c1, c, Ws, false, o);
-                    lift_row<BYTES, false>(c2, c, Ws, false, e1);
-                    col_step(o, e1, e0, dp, false, sv, dv);
-                    // sv[0..1] = LL, sv[2..3] = HL, dv[0..1] = LH, dv[2..3] = HH
-                    if (own) {
-                        *reinterpret_cast<uint2 *>(phl) = make_uint2(to_i16x2(sv[2]), to_i16x2(sv[3]));
-                        *reinterpret_cast<uint2 *>(plh) = make_uint2(to_i16x2(dv[0]), to_i16x2(dv[1]));
-                        *reinterpret_cast<uint2 *>(phh) = make_uint2(to_i16x2(dv[2]), to_i16x2(dv[3]));
-                        *reinterpret_cast<uint2 *>(pll) = ll_out<FINAL>(sv);
-                    }
-                    phl += ostep;
-                    plh += ostep;
-                    phh += ostep;
-                    pll += ostep;
+                const Raw c1 = ra[s], c2 = rb[s];
+                if (i + s + D < n_it) {
+                    ra[s] = ld(rp);
+                    rb[s] = ld(rp + pitch);
                 }
+                rp += 2 * pitch;
+                step(c1, c2);
             }
         }
+        // the last n_it mod D row pairs are already loaded
+#pragma unroll
+        for (int s = 0; s < D - 1; ++s)
+            if (i + s < n_it)
+                step(ra[s], rb[s]);
         return;
     }
 
-    // general path: bounds checks and the border rules
+    // general path: bounds checks and the border rules, a shorter ring of
+    // loads in flight (its checked loads need more registers)
+    constexpr int D = FRAG_PREFETCH_GENERAL;
     const bool vec = BYTES ? (((j.Ws & 7u) == 0) && (((uintptr_t)j.src & 7u) == 0))
                            : (((j.Ws & 7u) == 0) && (((uintptr_t)j.src & 15u) == 0));
     const bool own = lane >= 1 && lane <= 30 && x < Wl;
     const int nval = min(4, Wl - x);
+    Raw ra[D], rb[D];
     {
         uint32_t a[4], o[4];
         const Raw r0 = load_row<BYTES>(j, 2 * q0, c, vec);
         const Raw rm2 = load_row<BYTES>(j, max(2 * q0 - 2, 0), c, vec);
         const Raw rm1 = load_row<BYTES>(j, max(2 * q0 - 1, 0), c, vec);
+#pragma unroll
+        for (int s = 0; s < D; ++s) {
+            if (s < n_it) {
+                ra[s] = load_row<BYTES>(j, 2 * (q0 + s) + 1, c, vec);
+                rb[s] = load_row<BYTES>(j, 2 * (q0 + s) + 2, c, vec);
+            } else {
+                ra[s] = rb[s] = Raw{{0u, 0u, 0u, 0u}};
+            }
+        }
         lift_row<BYTES, true>(r0, c, Ws, edge, e0);
         lift_row<BYTES, true>(rm2, c, Ws, edge, a);
         lift_row<BYTES, true>(rm1, c, Ws, edge, o);
@@ -404,14 +443,7 @@ __device__ void fwd_unit(const LevelJob &j, int sx, int sy, int lane)
         for (int i = 0; i < 4; ++i)
             dp[i] = o[i] - pavg(a[i], e0[i]) + kB2;
     }
-    Raw n1 = load_row<BYTES>(j, 2 * q0 + 1, c, vec);
-    Raw n2 = load_row<BYTES>(j, 2 * q0 + 2, c, vec);
-    for (int q = q0; q < q1; ++q) {
-        const Raw c1 = n1, c2 = n2;
-        if (q + 1 < q1) {
-            n1 = load_row<BYTES>(j, 2 * q + 3, c, vec);
-            n2 = load_row<BYTES>(j, 2 * q + 4, c, vec);
-        }
+    auto gstep = [&](int q, const Raw &c1, const Raw &c2) {
         uint32_t o[4], e1[4], dv[4], sv[4];
         lift_row<BYTES, true>(c1, c, Ws, edge, o);
         if (2 * q + 2 == Hs) { // x[m] = x[m-2] at the bottom border
@@ -441,7 +473,23 @@ __device__ void fwd_unit(const LevelJob &j, int sx, int sy, int lane)
                 }
             }
         }
+    };
+    int i = 0;
+    for (; i + D <= n_it; i += D) {
+#pragma unroll
+        for (int s = 0; s < D; ++s) {
+            const Raw c1 = ra[s], c2 = rb[s];
+            if (i + s + D < n_it) {
+                ra[s] = load_row<BYTES>(j, 2 * (q0 + i + s + D) + 1, c, vec);
+                rb[s] = load_row<BYTES>(j, 2 * (q0 + i + s + D) + 2, c, vec);
+            }
+            gstep(q0 + i + s, c1, c2);
+        }
     }
+#pragma unroll
+    for (int s = 0; s < D - 1; ++s)
+        if (i + s < n_it)
+            gstep(q0 + i + s, ra[s], rb[s]);
 }
 
 // ---------------------------------------------------------------------------
@@ -596,7 +644,7 @@ __device__ void inv_unit(const LevelJob &j, int sx, int sy, int lane)
                       (uint64_t)(2 * k1 - 1) * (uint64_t)Ws + (uint64_t)(240 * sx + 248) <= j.n)
                    : (((uintptr_t)j.out & 15u) == 0));
     if (interior) {
-        constexpr int D = 2; // coefficient rows of loads in flight
+        constexpr int D = FRAG_PREFETCH_INV; // coefficient rows of loads in flight
         const uint64_t cstep = 2ull * (uint64_t)Wl; // bytes per coefficient row
         const uint64_t cb = 2ull * ((uint64_t)(k0 - 1) * (uint64_t)Wl + (uint64_t)x);
         const uint8_t *pll = j.ll_in + cb, *plh = j.lh + cb, *phl = j.hl + cb, *phh = j.hh + cb;
@@ -644,39 +692,48 @@ __device__ void inv_unit(const LevelJob &j, int sx, int sy, int lane)
         const bool own = lane >= 1 && lane <= 30;
         const uint64_t rstep = BYTES_OUT ? (uint64_t)Ws : 2ull * (uint64_t)Ws; // bytes per output row
         uint8_t *po = j.out + (uint64_t)(2 * k0) * rstep + (BYTES_OUT ? c : 2 * c);
-        for (int i = 0; i < n_it; i += D) {
-#pragma unroll
-            for (int s = 0; s < D; ++s) {
-                if (i + s < n_it) {
-                    const Coef c1 = ring[s];
-                    if (i + s + D < n_it)
-                        ring[s] = ld();
-                    uint32_t ev[4], xo[4], ve[4], vo[4];
-                    col_unstep(c1, false, xe, d0, ev, xo);
-                    unlift_row<false>(ev, c, Ws, false, ve);
-                    unlift_row<false>(xo, c, Ws, false, vo);
-                    if (own) {
-                        if (BYTES_OUT) {
-                            *reinterpret_cast<uint2 *>(po) = make_uint2(
-                                __byte_perm(ve[0], ve[1], 0x6420), __byte_perm(ve[2], ve[3], 0x6420));
-                            *reinterpret_cast<uint2 *>(po + rstep) = make_uint2(
-                                __byte_perm(vo[0], vo[1], 0x6420), __byte_perm(vo[2], vo[3], 0x6420));
-                        } else {
-                            *reinterpret_cast<uint4 *>(po) = make_uint4(ve[0], ve[1], ve[2], ve[3]);
-                            *reinterpret_cast<uint4 *>(po + rstep) = make_uint4(vo[0], vo[1], vo[2], vo[3]);
-                        }
-                    }
-                    po += 2 * rstep;
+        auto step = [&](const Coef &c1) {
+            uint32_t ev[4], xo[4], ve[4], vo[4];
+            col_unstep(c1, false, xe, d0, ev, xo);
+            unlift_row<false>(ev, c, Ws, false, ve);
+            unlift_row<false>(xo, c, Ws, false, vo);
+            if (own) {
+                if (BYTES_OUT) {
+                    *reinterpret_cast<uint2 *>(po) = make_uint2(__byte_perm(ve[0], ve[1], 0x6420),
+                                                                __byte_perm(ve[2], ve[3], 0x6420));
+                    *reinterpret_cast<uint2 *>(po + rstep) = make_uint2(
+                        __byte_perm(vo[0], vo[1], 0x6420), __byte_perm(vo[2], vo[3], 0x6420));
+                } else {
+                    *reinterpret_cast<uint4 *>(po) = make_uint4(ve[0], ve[1], ve[2], ve[3]);
+                    *reinterpret_cast<uint4 *>(po + rstep) = make_uint4(vo[0], vo[1], vo[2], vo[3]);
                 }
             }
+            po += 2 * rstep;
+        };
+        int i = 0;
+        for (; i + D <= n_it; i += D) {
+#pragma unroll
+            for (int s = 0; s < D; ++s) {
+                const Coef c1 = ring[s];
+                if (i + s + D < n_it)
+                    ring[s] = ld();
+                step(c1);
+            }
         }
+#pragma unroll
+        for (int s = 0; s < D - 1; ++s)
+            if (i + s < n_it)
+                step(ring[s]);
         return;
     }
 
-    // general path
+    // general path: bounds checks and the border rules, a shorter ring of
+    // loads in flight
+    constexpr int D = FRAG_PREFETCH_GENERAL;
     const bool vec = ((j.Ws & 7u) == 0);
     const bool own = lane >= 1 && lane <= 30 && c < Ws;
     const int nv = min(8, Ws - c);
+    Coef ring[D];
     {
         const Coef cur = load_coef<TOP>(j, k0, x, vec);
         const Coef prev = load_coef<TOP>(j, max(k0 - 1, 0), x, vec);
@@ -690,19 +747,32 @@ __device__ void inv_unit(const LevelJob &j, int sx, int sy, int lane)
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             xe[i] = s[i] - pq4(dm[i], d0[i]) + 0x20002000u; // undo Eq. 5.2 down the columns
+#pragma unroll
+        for (int t = 0; t < D; ++t)
+            ring[t] = t < n_it ? load_coef<TOP>(j, k0 + 1 + t, x, vec) : cur;
     }
-    Coef nxt = load_coef<TOP>(j, k0 + 1, x, vec);
-    for (int k = k0; k < k1; ++k) {
-        const Coef c1 = nxt;
-        if (k + 1 < k1)
-            nxt = load_coef<TOP>(j, k + 2, x, vec);
+    auto gstep = [&](int k, const Coef &c1) {
         uint32_t ev[4], xo[4], ve[4], vo[4];
         col_unstep(c1, 2 * k + 2 == Hs, xe, d0, ev, xo); // x[m] = x[m-2] at the bottom
         unlift_row<true>(ev, c, Ws, edge, ve);
         unlift_row<true>(xo, c, Ws, edge, vo);
         store_row<BYTES_OUT>(j, 2 * k, c, own, nv, ve);
         store_row<BYTES_OUT>(j, 2 * k + 1, c, own, nv, vo);
+    };
+    int i = 0;
+    for (; i + D <= n_it; i += D) {
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+            const Coef c1 = ring[t];
+            if (i + t + D < n_it)
+                ring[t] = load_coef<TOP>(j, k0 + 1 + i + t + D, x, vec);
+            gstep(k0 + i + t, c1);
+        }
     }
+#pragma unroll
+    for (int t = 0; t < D - 1; ++t)
+        if (i + t < n_it)
+            gstep(k0 + i + t, ring[t]);
 }
 
 // ---------------------------------------------------------------------------
@@ -771,7 +841,7 @@ __device__ __forceinline__ unsigned ld_relaxed(const unsigned *p)
 __device__ __forceinline__ bool wait_segments(const unsigned *done, uint32_t lo, uint32_t hi,
                                               unsigned target, uint32_t spin_limit, int *err)
 {
-    uint32_t it = 0, ns = 32;
+    uint32_t it = 0, ns = 128;
     for (uint32_t s = lo; s <= hi; ++s) {
         while (ld_relaxed(done + s) < target) {
             if (++it > spin_limit) {
@@ -779,7 +849,7 @@ __device__ __forceinline__ bool wait_segments(const unsigned *done, uint32_t lo,
                 return false;
             }
             __nanosleep(ns);
-            ns = min(2 * ns, 1024u);
+            ns = min(2 * ns, 2048u);
         }
     }
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
@@ -905,7 +975,7 @@ __device__ __forceinline__ bool wait_producers(const DagWork &w, const LevelJob 
 }
 
 template <bool FWD>
-__global__ void __launch_bounds__(kStreamThreads, 3) dag_kernel(DagWork w)
+__global__ void __launch_bounds__(kStreamThreads, FRAG_BLOCKS_PER_SM) dag_kernel(DagWork w)
 {
     __shared__ AesTab aes;
     const int lane = threadIdx.x & 31;
@@ -964,11 +1034,14 @@ __global__ void __launch_bounds__(kStreamThreads, 3) dag_kernel(DagWork w)
                 }
             }
         }
-        // publish: every lane's stores before the count
-        __threadfence();
-        __syncwarp();
-        if (lane == 0)
-            atomicAdd(w.done + j.done_off + sy, 1u);
+        // publish: every lane's stores before the count (jobs that nothing
+        // in the launch reads skip it)
+        if (j.publish) {
+            __threadfence();
+            __syncwarp();
+            if (lane == 0)
+                atomicAdd(w.done + j.done_off + sy, 1u);
+        }
     }
 }
 
