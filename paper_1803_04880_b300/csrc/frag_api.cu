@@ -309,13 +309,13 @@ struct Buf {
 
 // Level-0 rows per work segment, the same at every level: a power of two
 // >= 2^L, so every level has the same number of segments.  64 rows unless the
-// first level would then have fewer than two units per resident warp; then
+// first level would then have fewer than two units per resident CTA; then
 // down to 16 (each segment re-reads three rows above it).
-uint32_t seg_rows0(uint32_t L, uint64_t l1_units_at_64, uint64_t resident_warps)
+uint32_t seg_rows0(uint32_t L, uint64_t l1_units_at_64, uint64_t resident_ctas)
 {
     uint32_t r = 64;
     uint64_t u = l1_units_at_64;
-    while (r > 16 && u < 2 * resident_warps) {
+    while (r > 16 && u < 2 * resident_ctas) {
         r >>= 1;
         u <<= 1;
     }
@@ -324,10 +324,12 @@ uint32_t seg_rows0(uint32_t L, uint64_t l1_units_at_64, uint64_t resident_warps)
     return r;
 }
 
-uint64_t l1_units_at_64(const Buf &b)
-{
-    return (uint64_t)((b.W + frag::kStripCols - 1) / frag::kStripCols) * ((b.H + 63) / 64);
-}
+uint32_t warp_strips(uint32_t Ws) { return (Ws + frag::kStripCols - 1) / frag::kStripCols; }
+uint32_t tiles(uint32_t Ws) { return (warp_strips(Ws) + frag::kTileStrips - 1) / frag::kTileStrips; }
+
+uint64_t l1_units_at_64(const Buf &b) { return (uint64_t)tiles(b.W) * ((b.H + 63) / 64); }
+
+bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
 
 LevelJob level_job(bool fwd, const Buf &b, uint32_t l, uint32_t R0)
 {
@@ -352,7 +354,18 @@ LevelJob level_job(bool fwd, const Buf &b, uint32_t l, uint32_t R0)
     }
     j.n = b.n;
     j.nonce = b.nonce;
-    j.strips = (j.Ws + frag::kStripCols - 1) / frag::kStripCols;
+    j.wstrips = warp_strips(j.Ws);
+    j.strips = tiles(j.Ws);
+    // whole rows move by 16-byte bulk copies and results leave as 8- or
+    // 16-byte vector stores when every base and pitch allows it
+    const uint32_t Wl = j.Ws / 2;
+    if (fwd)
+        j.bulk = aligned(j.src, 16) && (j.src_bytes ? j.Ws % 16 == 0 : j.Ws % 8 == 0) &&
+                 Wl % 4 == 0 && aligned(j.hl, 8) && aligned(j.lh, 8) && aligned(j.hh, 8) &&
+                 aligned(j.ll, 8);
+    else
+        j.bulk = Wl % 8 == 0 && aligned(j.ll_in, 16) && aligned(j.lh, 16) && aligned(j.hl, 16) &&
+                 aligned(j.hh, 16) && aligned(j.out, j.out_bytes ? 8 : 16);
     j.seg_pairs = R0 >> l;
     j.segs = ((j.Hs / 2) + j.seg_pairs - 1) / j.seg_pairs;
     j.dep = -1;
@@ -403,6 +416,15 @@ void buffer_jobs(bool fwd, const Buf &b, uint32_t first_job, uint32_t *counters,
         j.publish = m < b.L; // the last job's output is read by nothing in the launch
         j.done_off = *counters;
         *counters += j.segs;
+        if (m) {
+            const LevelJob &p = jobs.back();
+            j.dep_done_off = p.done_off;
+            j.dep_segs = p.segs;
+            j.dep_units = p.strips;
+            j.dep_seg_pairs = p.seg_pairs;
+            j.dep_Ws = p.Ws;
+            j.dep_kind = p.kind;
+        }
         jobs.push_back(j);
     }
 }
@@ -412,12 +434,12 @@ void buffer_jobs(bool fwd, const Buf &b, uint32_t first_job, uint32_t *counters,
 // units, so it rarely waits for its producers (small images end up level by
 // level; tall ones stream with the coarse levels behind the fine ones).
 uint32_t buffer_lag(const std::vector<LevelJob> &jobs, uint32_t first_job, uint32_t njobs,
-                    uint64_t resident_warps)
+                    uint64_t resident_ctas)
 {
     uint64_t per_round = 0;
     for (uint32_t m = 0; m < njobs; ++m)
         per_round += jobs[first_job + m].strips;
-    const uint64_t lag = (3 * resident_warps / 2 + per_round - 1) / std::max<uint64_t>(1, per_round);
+    const uint64_t lag = (3 * resident_ctas / 2 + per_round - 1) / std::max<uint64_t>(1, per_round);
     return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(kMinLag, lag), 1u << 24);
 }
 
@@ -436,7 +458,7 @@ void wave_units(const std::vector<LevelJob> &jobs, const std::vector<uint32_t> &
             const LevelJob &j = jobs[first[b] + m];
             for (uint32_t sy = 0; sy < j.segs; ++sy)
                 for (uint32_t sx = 0; sx < j.strips; ++sx)
-                    units.push_back(DagUnit{first[b] + m, sx, sy});
+                    units.push_back(DagUnit{first[b] + m, sx, sy, 0});
         }
 }
 
@@ -458,8 +480,8 @@ frag_status dag_grid(DeviceState &d, bool fwd, uint64_t units, uint32_t *grid)
         std::lock_guard<std::mutex> lock(g_mu);
         d.occ[fwd][7777] = occ;
     }
-    const uint64_t blocks = units / 8 + (units % 8 != 0); // 8 warps per block
-    *grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)d.sms * occ, blocks));
+    // one unit at a time per CTA
+    *grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)d.sms * occ, units));
     return FRAG_OK;
 }
 
@@ -483,7 +505,7 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     uint32_t grid = 0;
     if ((st = dag_grid(*d, fwd, ~0ull, &grid)) != FRAG_OK)
         return st;
-    b.R0 = seg_rows0(b.L, l1_units_at_64(b), (uint64_t)grid * 8);
+    b.R0 = seg_rows0(b.L, l1_units_at_64(b), grid);
     const uint32_t NS = (b.H + b.R0 - 1) / b.R0;
     const uint64_t cb = align256(4ull * NS * njobs);
     uint8_t *mem = nullptr;
@@ -503,7 +525,7 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
         units += (uint64_t)jobs[m].strips * jobs[m].segs;
     }
     w.n_inline = njobs;
-    w.lag = buffer_lag(jobs, 0, njobs, (uint64_t)grid * 8);
+    w.lag = buffer_lag(jobs, 0, njobs, grid);
     w.total_units = units;
     w.done = (unsigned *)(mem + sb);
     w.queue = (unsigned long long *)(mem + sb + cb);
@@ -535,7 +557,7 @@ struct DagWave {
 
 struct BatchPlan {
     bool fwd = true;
-    uint64_t resident_warps = 0; // warps one launch keeps resident
+    uint64_t resident_ctas = 0; // CTAs one launch keeps resident
     std::vector<Buf> bufs;
     std::vector<uint64_t> scr_off;
     std::vector<uint32_t> wave_of;
@@ -622,7 +644,7 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
     for (size_t i = 0; i < bp.bufs.size(); ++i) {
         Buf &b = bp.bufs[i];
         uint64_t off[frag::kMaxInlineJobs + 1] = {0};
-        b.R0 = seg_rows0(b.L, u64, bp.resident_warps);
+        b.R0 = seg_rows0(b.L, u64, bp.resident_ctas);
         scratch_bytes(bp.fwd, b.H, b.W, b.L, off);
         for (uint32_t l = 1; l < (bp.fwd ? b.L : b.L + 1); ++l)
             b.scr[l] = scratch_base + bp.scr_off[i] + off[l];
@@ -718,7 +740,7 @@ frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, 
     uint32_t grid = 0;
     if ((st = dag_grid(*d, fwd, ~0ull, &grid)) != FRAG_OK)
         return st;
-    bp.resident_warps = (uint64_t)grid * 8;
+    bp.resident_ctas = grid;
     BatchPlan sizing = bp; // the layout does not depend on the scratch base
     fill_batch(sizing, nullptr);
     uint8_t *mem = nullptr;
@@ -760,7 +782,7 @@ frag_status create_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, ui
         st = device_state(&d, &bt->device);
     uint32_t grid = 0;
     if (st == FRAG_OK && (st = dag_grid(*d, fwd, ~0ull, &grid)) == FRAG_OK)
-        bt->bp.resident_warps = (uint64_t)grid * 8;
+        bt->bp.resident_ctas = grid;
     if (st == FRAG_OK && !bt->bp.bufs.empty()) {
         BatchPlan sizing = bt->bp;
         fill_batch(sizing, nullptr);

@@ -45,8 +45,10 @@ constexpr uint8_t kJobCipher = 1; // AES-128-CTR over the private fragment (LL_L
 // Cipher job: Ws x Hs is LL_L; forward XORs the keystream into `ll` in place,
 // inverse writes `ll_in` XOR keystream to `out` (the plaintext scratch).
 // Segment sy covers rows [sy * seg_pairs, (sy + 1) * seg_pairs) of the job's
-// output (LL_l pair rows for a level job, LL_L rows for a cipher job).
-struct LevelJob {
+// output (LL_l pair rows for a level job, LL_L rows for a cipher job); each
+// segment has `strips` units (tiles of kTileStrips warp strips for a level
+// job, kCipherBlocks AES blocks for a cipher job).
+struct __align__(16) LevelJob {
     const uint8_t *src;
     uint8_t *hl, *lh, *hh; // band bases of level l
     uint8_t *ll;           // forward output
@@ -55,15 +57,23 @@ struct LevelJob {
     uint64_t n;            // bytes of the buffer (level-1 source / output)
     uint64_t nonce;
     uint32_t Ws, Hs;       // level-(l-1) image (cipher job: LL_L)
-    uint32_t strips, segs, seg_pairs;
+    uint32_t strips;       // units per segment
+    uint32_t wstrips;      // 240-column warp strips of the image (level job)
+    uint32_t segs, seg_pairs;
     uint32_t done_off; // first completion counter of this job's segments
     int32_t dep;       // job whose output this job reads (-1: none)
+    // the fields of job `dep` a unit's dependency check needs, copied here so
+    // that the check reads one descriptor
+    uint32_t dep_done_off, dep_segs, dep_units, dep_seg_pairs, dep_Ws;
+    uint8_t dep_kind;
     uint8_t kind, src_bytes, final_level, top_level, out_bytes;
     uint8_t publish; // another job of the launch reads this one's output
+    uint8_t bulk;    // bases and pitches allow whole-row bulk copies and vector stores
 };
+static_assert(sizeof(LevelJob) % 16 == 0, "job descriptors are copied in 16-byte pieces");
 
 struct DagUnit {
-    uint32_t job, sx, sy;
+    uint32_t job, sx, sy, pad; // 16 bytes: one vector load
 };
 
 constexpr int kMaxInlineJobs = 8;
@@ -132,7 +142,8 @@ cudaError_t dag_occupancy(bool fwd, int *blocks_per_sm);
 cudaError_t launch_stall_probe(const unsigned *ctr, uint32_t spin_limit, int *err,
                                cudaStream_t stream);
 constexpr int kStripCols = 240;          // level-(l-1) columns owned by one warp strip
-constexpr uint32_t kCipherBlocks = 128;  // AES blocks of one cipher unit
+constexpr uint32_t kTileStrips = 4;      // warp strips (consumer warps) of one tile unit
+constexpr uint32_t kCipherBlocks = 512;  // AES blocks of one cipher unit
 
 // kernels (tile_kernels.cu)
 constexpr uint32_t kFastTile = 256;   // owned tile side of the row/column-pass body

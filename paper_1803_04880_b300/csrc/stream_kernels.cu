@@ -1,11 +1,14 @@
 // stream_kernels.cu -- every LeGall 5/3 level of one or many buffers, and the
 // AES-128-CTR pass over their private fragments, in one launch.
 //
-// Work units (the host lists them so that every unit's producers come first):
-//   level unit   (buffer, level l, strip, row segment): a warp takes a strip of
-//                256 columns of the level-(l-1) image and streams down the
-//                rows of its segment.
-//                forward: lane t loads 8 consecutive samples of a row; the row
+// A CTA is four consumer warps and one producer warp.  Work units (the host
+// lists them so that every unit's producers come first):
+//   level unit   (buffer, level l, tile, row segment): the tile is 960
+//                columns of the level-(l-1) image, one 256-column strip per
+//                consumer warp (lanes 1..30 own 240 columns, lanes 0 and 31
+//                supply neighbours), and the unit streams down the rows of its
+//                segment.
+//                forward: a lane takes 8 consecutive samples of a row; the row
 //                lifting (Eq. 5.1 predict, then Eq. 5.2 update; rows before
 //                columns, Sec. 5.2.2) runs on packed pairs, the neighbours x8
 //                and d[-1] taken from the adjacent lanes by warp shuffles; the
@@ -16,29 +19,39 @@
 //                inverse: the exact reverse (undo Eq. 5.2, then Eq. 5.1, down
 //                the columns, then along the rows) gives LL_{l-1} (scratch) or
 //                the recovered bytes.
-//   cipher unit  the 16-byte blocks of the private fragment that start in one
-//                row segment of LL_L, XORed with the AES-128 keystream of the
-//                counter block nonce || block index, one block per lane.
-//                forward: in place, after the last level wrote those rows;
-//                inverse: into a plaintext copy that the top level reads.
+//   cipher unit  512 of the 16-byte blocks of the private fragment, XORed with
+//                the AES-128 keystream of the counter block nonce || block
+//                index, one block per lane at a time.  forward: in place, after
+//                the last level wrote those rows; inverse: into a plaintext copy
+//                that the top level reads.
 //
-// Lanes 0 and 31 of a warp only supply neighbours: lanes 1..30 own the
-// strip's 240 columns.  Rows above a segment are re-lifted to restart the
-// column stream.  The symmetric extension (x[-1] = x[1], x[m] = x[m-2], hence
-// d[-1] = d[0]) applies only at the image borders.  A unit away from every
-// border runs a branch-free loop that keeps several row pairs of loads in
-// flight; the others run the general loop with bounds checks and the border
-// rules.
+// Data movement: the producer warp (one elected lane) dequeues units, waits
+// for their producers, and streams each unit's rows (forward: image rows,
+// inverse: one row of each of LL, LH, HL, HH) into a ring of shared-memory
+// stages with bulk asynchronous copies (cp.async.bulk, completion counted in
+// bytes on the stage's mbarrier), so many kilobytes per CTA are in flight
+// without registers.  Consumers wait on a stage's "full" barrier, take their
+// samples into registers and release the stage on its "empty" barrier.  A
+// tile reads rows about 1 KB wide, which the DRAM serves far better than the
+// 256-byte pieces of a single warp strip.  Units whose rows are not whole
+// aligned runs (unaligned buffers or pitches, rows past the end of the data)
+// run the general path instead: each consumer warp loads its own strip with
+// bounds checks.
+//
+// The symmetric extension (x[-1] = x[1], x[m] = x[m-2], hence d[-1] = d[0])
+// applies only at the image borders; rows above a segment are re-lifted to
+// restart the column stream.
 //
 // Packed pairs: each 16-bit half holds v + 0x4000 (|v| < 2^14); the halves of
 // (A + B) never carry into each other, so both floors of a lifting step take
 // one add, one shift and one mask for two columns.
 //
-// A unit whose input another unit of the launch writes waits (lane 0, bounded
-// spin) until the producer row segments are complete and then reads that data
-// with L2-coherent loads.  A wait that runs out sets the error word to 3
-// (FRAG_ETIMEOUT) and skips the unit, which is still reported complete so that
-// no consumer waits forever.
+// Each consumer warp reports its share of a unit complete on the segment's
+// counter (fence, then atomic add); there is no barrier across warps.  Every
+// wait is bounded.  A dependency wait that runs out sets the error word to 3
+// (FRAG_ETIMEOUT) and the unit is skipped but still reported complete, so no
+// consumer waits forever; a stage wait that runs out sets the error word to 4
+// and the CTA stops (the producer first waits, bounded, for its copies).
 #include "frag_internal.cuh"
 
 namespace frag {
@@ -83,25 +96,45 @@ __device__ __forceinline__ void aes_block(const AesTab &a, uint64_t nonce, uint6
              (a.S[(s1 >> 8) & 255] << 8) | a.S[s2 & 255]) ^ a.rk[43];
 }
 
-namespace strm {
+// tuning knobs: ring stages per CTA, KiB per stage, resident CTAs per SM the
+// kernel is compiled for
+#ifndef FRAG_STAGES
+#define FRAG_STAGES 3
+#endif
+#ifndef FRAG_STAGE_KB
+#define FRAG_STAGE_KB 16
+#endif
+#ifndef FRAG_CTAS_PER_SM
+#define FRAG_CTAS_PER_SM 4
+#endif
 
-// row pairs of loads kept in flight by an interior unit, and resident blocks
-// of 256 threads per SM the kernel is compiled for (tuning knobs)
-#ifndef FRAG_PREFETCH_BYTES
-#define FRAG_PREFETCH_BYTES 4
-#endif
-#ifndef FRAG_PREFETCH_PACKED
-#define FRAG_PREFETCH_PACKED 2
-#endif
-#ifndef FRAG_PREFETCH_INV
-#define FRAG_PREFETCH_INV 2
-#endif
-#ifndef FRAG_PREFETCH_GENERAL
-#define FRAG_PREFETCH_GENERAL 1
-#endif
-#ifndef FRAG_BLOCKS_PER_SM
-#define FRAG_BLOCKS_PER_SM 3
-#endif
+constexpr int kConsumerWarps = (int)kTileStrips;
+constexpr int kCtaThreads = 32 * (kConsumerWarps + 1);
+constexpr int kStages = FRAG_STAGES;
+// A stage is a run of row slots: forward 1 KB (byte rows) or 2 KB (packed
+// rows) per image row, inverse 4 KB per coefficient row (LL, LH, HL, HH in
+// 1 KB slots).  Few large stages keep the handshakes per byte low.
+constexpr int kStageBytes = FRAG_STAGE_KB * 1024;
+constexpr int kCoefSlot = 1024;
+constexpr int kCoefRow = 4 * kCoefSlot;
+constexpr int kTileCols = kConsumerWarps * kStripCols; // 960
+constexpr uint32_t kStageSpin = 1u << 23;              // tests of a stage barrier before giving up
+
+// stage kinds
+constexpr uint32_t kModeEnd = 0;      // no more units
+constexpr uint32_t kModeBulk = 1;     // rows streamed into the ring, away from column borders
+constexpr uint32_t kModeBulkEdge = 2; // rows streamed into the ring, tile touches a border
+constexpr uint32_t kModeGeneral = 3;  // consumers load their own strips (bounds checked)
+constexpr uint32_t kModeCipher = 4;   // AES-CTR blocks
+constexpr uint32_t kModeSkip = 5;     // a dependency wait ran out: report complete, do nothing
+
+// written by the producer into the first stage of every unit
+struct StageHdr {
+    LevelJob job;
+    uint32_t x, y, mode, pad;
+};
+
+namespace strm {
 
 constexpr uint32_t kB2 = 0x40004000u;
 
@@ -226,16 +259,15 @@ __device__ __forceinline__ void col_step(const uint32_t (&o)[4], const uint32_t 
 
 // LL words of a pair for the output: scratch keeps packed pairs; the last
 // level writes LL_L - 128 as int16 (the level shift moves only LL_L)
-template <bool FINAL>
-__device__ __forceinline__ uint2 ll_out(const uint32_t (&sv)[4])
+__device__ __forceinline__ uint2 ll_out(bool final_level, const uint32_t (&sv)[4])
 {
-    if (FINAL)
+    if (final_level)
         return make_uint2(to_i16x2(sv[0] - 0x00800080u), to_i16x2(sv[1] - 0x00800080u));
     return make_uint2(sv[0], sv[1]);
 }
 
 // ---------------------------------------------------------------------------
-// general-path memory helpers (bounds checked)
+// bounds-checked global memory helpers (general path)
 // ---------------------------------------------------------------------------
 
 // 8 source samples of row r at columns c .. c+7 of the level-(l-1) image.
@@ -303,139 +335,53 @@ __device__ __forceinline__ void store4(uint8_t *band, int Wl, int y, int x, uint
     }
 }
 
+// the four outputs of one row pair of one lane (checked stores)
+__device__ __forceinline__ void fwd_store(const LevelJob &j, int Wl, int q, int x, int nval,
+                                          const uint32_t (&sv)[4], const uint32_t (&dv)[4])
+{
+    // sv[0..1] = LL, sv[2..3] = HL, dv[0..1] = LH, dv[2..3] = HH
+    store4(j.hl, Wl, q, x, to_i16x2(sv[2]), to_i16x2(sv[3]), nval);
+    store4(j.lh, Wl, q, x, to_i16x2(dv[0]), to_i16x2(dv[1]), nval);
+    store4(j.hh, Wl, q, x, to_i16x2(dv[2]), to_i16x2(dv[3]), nval);
+    const uint2 ll = ll_out(j.final_level, sv);
+    if (j.final_level) {
+        store4(j.ll, Wl, q, x, ll.x, ll.y, nval);
+    } else {
+        // packed scratch rows have Wl / 2 words (Wl is even below the last level)
+        uint32_t *p = reinterpret_cast<uint32_t *>(j.ll) + (uint64_t)q * (uint64_t)(Wl / 2) + x / 2;
+        if (nval == 4 && ((uintptr_t)p & 7u) == 0) {
+            *reinterpret_cast<uint2 *>(p) = ll;
+        } else {
+            p[0] = ll.x;
+            if (nval > 2)
+                p[1] = ll.y;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
-// forward level unit
+// forward level: general path (one warp, one 256-column strip)
 // ---------------------------------------------------------------------------
-template <bool BYTES, bool FINAL>
-__device__ void fwd_unit(const LevelJob &j, int sx, int sy, int lane)
+template <bool BYTES>
+__device__ void fwd_general(const LevelJob &j, int sx, int sy, int lane)
 {
     const int Ws = (int)j.Ws, Hs = (int)j.Hs;
-    const int c = 240 * sx - 8 + 8 * lane; // first column of this lane
+    const int c = kStripCols * sx - 8 + 8 * lane; // first column of this lane
     const int q0 = sy * (int)j.seg_pairs;
     const int q1 = min(q0 + (int)j.seg_pairs, Hs / 2);
     const int Wl = Ws / 2;
     const int x = c / 2; // level-l column of the lane's first value
-    const bool edge = (240 * sx + 248 >= Ws);
-    const int n_it = q1 - q0;
-
-    uint32_t e0[4], dp[4];
-    const bool interior =
-        sx >= 1 && !edge && q0 >= 1 && 2 * q1 < Hs && (Wl & 3) == 0 && (j.Ws & 7u) == 0 &&
-        ((((uintptr_t)j.hl | (uintptr_t)j.lh | (uintptr_t)j.hh | (uintptr_t)j.ll) & 7u) == 0) &&
-        (BYTES ? (((uintptr_t)j.src & 7u) == 0 &&
-                  (uint64_t)(2 * q1) * (uint64_t)Ws + (uint64_t)(240 * sx + 248) <= j.n)
-               : (((uintptr_t)j.src & 15u) == 0));
-    if (interior) {
-        // every row of the segment and its halo exists and holds data, no
-        // border rule applies, and every lane's addresses lie inside the
-        // buffers (lanes 0 and 31 only skip their stores)
-        constexpr int D = BYTES ? FRAG_PREFETCH_BYTES : FRAG_PREFETCH_PACKED;
-        const uint64_t pitch = BYTES ? (uint64_t)Ws : 2ull * (uint64_t)Ws;
-        const uint8_t *rp = j.src + (uint64_t)(2 * q0 - 2) * pitch + (BYTES ? c : 2 * c);
-        auto ld = [&](const uint8_t *p) -> Raw {
-            Raw r;
-            if (BYTES) {
-                const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
-                r.w[0] = t.x;
-                r.w[1] = t.y;
-                r.w[2] = r.w[3] = 0;
-            } else {
-                const uint4 t = __ldcg(reinterpret_cast<const uint4 *>(p));
-                r.w[0] = t.x;
-                r.w[1] = t.y;
-                r.w[2] = t.z;
-                r.w[3] = t.w;
-            }
-            return r;
-        };
-        Raw ra[D], rb[D];
-        {
-            const Raw rm2 = ld(rp), rm1 = ld(rp + pitch), r0 = ld(rp + 2 * pitch);
-            rp += 3 * pitch; // row 2 q0 + 1
-#pragma unroll
-            for (int s = 0; s < D; ++s) {
-                if (s < n_it) {
-                    ra[s] = ld(rp);
-                    rb[s] = ld(rp + pitch);
-                } else {
-                    ra[s] = rb[s] = Raw{{0u, 0u, 0u, 0u}};
-                }
-                rp += 2 * pitch;
-            }
-            uint32_t a[4], o[4];
-            lift_row<BYTES, false>(r0, c, Ws, false, e0);
-            lift_row<BYTES, false>(rm2, c, Ws, false, a);
-            lift_row<BYTES, false>(rm1, c, Ws, false, o);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                dp[i] = o[i] - pavg(a[i], e0[i]) + kB2;
-        }
-        const bool own = lane >= 1 && lane <= 30;
-        const uint64_t ostep = 2ull * (uint64_t)Wl; // bytes per band row
-        const uint64_t o0 = 2ull * ((uint64_t)q0 * (uint64_t)Wl + (uint64_t)x);
-        uint8_t *phl = j.hl + o0, *plh = j.lh + o0, *phh = j.hh + o0, *pll = j.ll + o0;
-        auto step = [&](const Raw &c1, const Raw &c2) {
-            uint32_t o[4], e1[4], sv[4], dv[4];
-            lift_row<BYTES, false>(c1, c, Ws, false, o);
-            lift_row<BYTES, false>(c2, c, Ws, false, e1);
-            col_step(o, e1, e0, dp, false, sv, dv);
-            // sv[0..1] = LL, sv[2..3] = HL, dv[0..1] = LH, dv[2..3] = HH
-            if (own) {
-                *reinterpret_cast<uint2 *>(phl) = make_uint2(to_i16x2(sv[2]), to_i16x2(sv[3]));
-                *reinterpret_cast<uint2 *>(plh) = make_uint2(to_i16x2(dv[0]), to_i16x2(dv[1]));
-                *reinterpret_cast<uint2 *>(phh) = make_uint2(to_i16x2(dv[2]), to_i16x2(dv[3]));
-                *reinterpret_cast<uint2 *>(pll) = ll_out<FINAL>(sv);
-            }
-            phl += ostep;
-            plh += ostep;
-            phh += ostep;
-            pll += ostep;
-        };
-        // whole groups of D row pairs: slot s is consumed, then refilled D
-        // row pairs ahead (predicated loads, straight-line code)
-        int i = 0;
-        for (; i + D <= n_it; i += D) {
-#pragma unroll
-            for (int s = 0; s < D; ++s) {
-                const Raw c1 = ra[s], c2 = rb[s];
-                if (i + s + D < n_it) {
-                    ra[s] = ld(rp);
-                    rb[s] = ld(rp + pitch);
-                }
-                rp += 2 * pitch;
-                step(c1, c2);
-            }
-        }
-        // the last n_it mod D row pairs are already loaded
-#pragma unroll
-        for (int s = 0; s < D - 1; ++s)
-            if (i + s < n_it)
-                step(ra[s], rb[s]);
-        return;
-    }
-
-    // general path: bounds checks and the border rules, a shorter ring of
-    // loads in flight (its checked loads need more registers)
-    constexpr int D = FRAG_PREFETCH_GENERAL;
+    const bool edge = (kStripCols * sx + 248 >= Ws);
     const bool vec = BYTES ? (((j.Ws & 7u) == 0) && (((uintptr_t)j.src & 7u) == 0))
                            : (((j.Ws & 7u) == 0) && (((uintptr_t)j.src & 15u) == 0));
     const bool own = lane >= 1 && lane <= 30 && x < Wl;
     const int nval = min(4, Wl - x);
-    Raw ra[D], rb[D];
+    uint32_t e0[4], dp[4];
     {
         uint32_t a[4], o[4];
         const Raw r0 = load_row<BYTES>(j, 2 * q0, c, vec);
         const Raw rm2 = load_row<BYTES>(j, max(2 * q0 - 2, 0), c, vec);
         const Raw rm1 = load_row<BYTES>(j, max(2 * q0 - 1, 0), c, vec);
-#pragma unroll
-        for (int s = 0; s < D; ++s) {
-            if (s < n_it) {
-                ra[s] = load_row<BYTES>(j, 2 * (q0 + s) + 1, c, vec);
-                rb[s] = load_row<BYTES>(j, 2 * (q0 + s) + 2, c, vec);
-            } else {
-                ra[s] = rb[s] = Raw{{0u, 0u, 0u, 0u}};
-            }
-        }
         lift_row<BYTES, true>(r0, c, Ws, edge, e0);
         lift_row<BYTES, true>(rm2, c, Ws, edge, a);
         lift_row<BYTES, true>(rm1, c, Ws, edge, o);
@@ -443,7 +389,14 @@ __device__ void fwd_unit(const LevelJob &j, int sx, int sy, int lane)
         for (int i = 0; i < 4; ++i)
             dp[i] = o[i] - pavg(a[i], e0[i]) + kB2;
     }
-    auto gstep = [&](int q, const Raw &c1, const Raw &c2) {
+    Raw n1 = load_row<BYTES>(j, 2 * q0 + 1, c, vec);
+    Raw n2 = load_row<BYTES>(j, 2 * q0 + 2, c, vec);
+    for (int q = q0; q < q1; ++q) {
+        const Raw c1 = n1, c2 = n2;
+        if (q + 1 < q1) {
+            n1 = load_row<BYTES>(j, 2 * q + 3, c, vec);
+            n2 = load_row<BYTES>(j, 2 * q + 4, c, vec);
+        }
         uint32_t o[4], e1[4], dv[4], sv[4];
         lift_row<BYTES, true>(c1, c, Ws, edge, o);
         if (2 * q + 2 == Hs) { // x[m] = x[m-2] at the bottom border
@@ -454,46 +407,13 @@ __device__ void fwd_unit(const LevelJob &j, int sx, int sy, int lane)
             lift_row<BYTES, true>(c2, c, Ws, edge, e1);
         }
         col_step(o, e1, e0, dp, q == 0, sv, dv);
-        if (own) {
-            store4(j.hl, Wl, q, x, to_i16x2(sv[2]), to_i16x2(sv[3]), nval);
-            store4(j.lh, Wl, q, x, to_i16x2(dv[0]), to_i16x2(dv[1]), nval);
-            store4(j.hh, Wl, q, x, to_i16x2(dv[2]), to_i16x2(dv[3]), nval);
-            const uint2 ll = ll_out<FINAL>(sv);
-            if (FINAL) {
-                store4(j.ll, Wl, q, x, ll.x, ll.y, nval);
-            } else {
-                // packed scratch rows have Wl / 2 words (Wl is even below the last level)
-                uint32_t *p = reinterpret_cast<uint32_t *>(j.ll) + (uint64_t)q * (uint64_t)(Wl / 2) + x / 2;
-                if (nval == 4 && ((uintptr_t)p & 7u) == 0) {
-                    *reinterpret_cast<uint2 *>(p) = ll;
-                } else {
-                    p[0] = ll.x;
-                    if (nval > 2)
-                        p[1] = ll.y;
-                }
-            }
-        }
-    };
-    int i = 0;
-    for (; i + D <= n_it; i += D) {
-#pragma unroll
-        for (int s = 0; s < D; ++s) {
-            const Raw c1 = ra[s], c2 = rb[s];
-            if (i + s + D < n_it) {
-                ra[s] = load_row<BYTES>(j, 2 * (q0 + i + s + D) + 1, c, vec);
-                rb[s] = load_row<BYTES>(j, 2 * (q0 + i + s + D) + 2, c, vec);
-            }
-            gstep(q0 + i + s, c1, c2);
-        }
+        if (own)
+            fwd_store(j, Wl, q, x, nval, sv, dv);
     }
-#pragma unroll
-    for (int s = 0; s < D - 1; ++s)
-        if (i + s < n_it)
-            gstep(q0 + i + s, ra[s], rb[s]);
 }
 
 // ---------------------------------------------------------------------------
-// inverse level unit
+// inverse level: general path
 // ---------------------------------------------------------------------------
 struct Coef {
     uint32_t sl[2], dl[2], sh[2], dh[2]; // low s (LL), low d (LH), high s (HL), high d (HH)
@@ -531,7 +451,6 @@ __device__ __forceinline__ void load4(const uint8_t *band, int Hl, int Wl, int y
 
 // coefficients of row k: the detail bands, and LL_l from the packed scratch
 // or, at the top level, LL_L - 128 as int16 (the deciphered private fragment)
-template <bool TOP>
 __device__ __forceinline__ Coef load_coef(const LevelJob &j, int k, int x, bool vec)
 {
     const int Hl = (int)j.Hs / 2, Wl = (int)j.Ws / 2;
@@ -546,7 +465,7 @@ __device__ __forceinline__ Coef load_coef(const LevelJob &j, int k, int x, bool 
     load4(j.hh, Hl, Wl, k, x, vec, false, a, b);
     cf.dh[0] = from_i16x2(a);
     cf.dh[1] = from_i16x2(b);
-    if (TOP) {
+    if (j.top_level) {
         load4(j.ll_in, Hl, Wl, k, x, vec, true, a, b);
         cf.sl[0] = from_i16x2(a) + 0x00800080u;
         cf.sl[1] = from_i16x2(b) + 0x00800080u;
@@ -624,162 +543,60 @@ __device__ __forceinline__ void col_unstep(const Coef &c1, bool bottom, uint32_t
     }
 }
 
-template <bool TOP, bool BYTES_OUT>
-__device__ void inv_unit(const LevelJob &j, int sx, int sy, int lane)
+// start of the column inverse at pair k0: xe = even row of pair k0, d0 = d of
+// pair k0 (prev = coefficients of pair k0 - 1, ignored at the top border)
+__device__ __forceinline__ void col_unstart(const Coef &prev, const Coef &cur, bool top,
+                                            uint32_t (&xe)[4], uint32_t (&d0)[4])
+{
+    const uint32_t dm[4] = {top ? cur.dl[0] : prev.dl[0], top ? cur.dl[1] : prev.dl[1],
+                            top ? cur.dh[0] : prev.dh[0], top ? cur.dh[1] : prev.dh[1]};
+    const uint32_t s[4] = {cur.sl[0], cur.sl[1], cur.sh[0], cur.sh[1]};
+    d0[0] = cur.dl[0];
+    d0[1] = cur.dl[1];
+    d0[2] = cur.dh[0];
+    d0[3] = cur.dh[1];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        xe[i] = s[i] - pq4(dm[i], d0[i]) + 0x20002000u; // undo Eq. 5.2 down the columns
+}
+
+template <bool BYTES_OUT>
+__device__ void inv_general(const LevelJob &j, int sx, int sy, int lane)
 {
     const int Ws = (int)j.Ws, Hs = (int)j.Hs;
-    const int c = 240 * sx - 8 + 8 * lane; // first output column of this lane
-    const int x = c >> 1;                  // first coefficient column
+    const int c = kStripCols * sx - 8 + 8 * lane; // first output column of this lane
+    const int x = c >> 1;                         // first coefficient column
     const int k0 = sy * (int)j.seg_pairs;
     const int k1 = min(k0 + (int)j.seg_pairs, Hs / 2);
-    const int Wl = Ws / 2, Hl = Hs / 2;
-    const bool edge = (240 * sx + 248 >= Ws);
-    const int n_it = k1 - k0;
-
-    uint32_t xe[4], d0[4];
-    const bool interior =
-        sx >= 1 && !edge && k0 >= 1 && k1 <= Hl - 1 && (Wl & 3) == 0 && (j.Ws & 7u) == 0 &&
-        ((((uintptr_t)j.hl | (uintptr_t)j.lh | (uintptr_t)j.hh | (uintptr_t)j.ll_in) & 7u) == 0) &&
-        (BYTES_OUT ? (((uintptr_t)j.out & 7u) == 0 &&
-                      (uint64_t)(2 * k1 - 1) * (uint64_t)Ws + (uint64_t)(240 * sx + 248) <= j.n)
-                   : (((uintptr_t)j.out & 15u) == 0));
-    if (interior) {
-        constexpr int D = FRAG_PREFETCH_INV; // coefficient rows of loads in flight
-        const uint64_t cstep = 2ull * (uint64_t)Wl; // bytes per coefficient row
-        const uint64_t cb = 2ull * ((uint64_t)(k0 - 1) * (uint64_t)Wl + (uint64_t)x);
-        const uint8_t *pll = j.ll_in + cb, *plh = j.lh + cb, *phl = j.hl + cb, *phh = j.hh + cb;
-        auto ld = [&]() -> Coef {
-            Coef cf;
-            const uint2 a = __ldcg(reinterpret_cast<const uint2 *>(pll));
-            const uint2 b = __ldg(reinterpret_cast<const uint2 *>(plh));
-            const uint2 h = __ldg(reinterpret_cast<const uint2 *>(phl));
-            const uint2 d = __ldg(reinterpret_cast<const uint2 *>(phh));
-            cf.sl[0] = TOP ? from_i16x2(a.x) + 0x00800080u : a.x;
-            cf.sl[1] = TOP ? from_i16x2(a.y) + 0x00800080u : a.y;
-            cf.dl[0] = from_i16x2(b.x);
-            cf.dl[1] = from_i16x2(b.y);
-            cf.sh[0] = from_i16x2(h.x);
-            cf.sh[1] = from_i16x2(h.y);
-            cf.dh[0] = from_i16x2(d.x);
-            cf.dh[1] = from_i16x2(d.y);
-            pll += cstep;
-            plh += cstep;
-            phl += cstep;
-            phh += cstep;
-            return cf;
-        };
-        Coef ring[D];
-        {
-            const Coef prev = ld(); // row k0 - 1
-            const Coef cur = ld();  // row k0
-#pragma unroll
-            for (int s = 0; s < D; ++s) {
-                if (s < n_it)
-                    ring[s] = ld(); // rows k0 + 1 ..
-                else
-                    ring[s] = cur;
-            }
-            const uint32_t dm[4] = {prev.dl[0], prev.dl[1], prev.dh[0], prev.dh[1]};
-            const uint32_t s[4] = {cur.sl[0], cur.sl[1], cur.sh[0], cur.sh[1]};
-            d0[0] = cur.dl[0];
-            d0[1] = cur.dl[1];
-            d0[2] = cur.dh[0];
-            d0[3] = cur.dh[1];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                xe[i] = s[i] - pq4(dm[i], d0[i]) + 0x20002000u;
-        }
-        const bool own = lane >= 1 && lane <= 30;
-        const uint64_t rstep = BYTES_OUT ? (uint64_t)Ws : 2ull * (uint64_t)Ws; // bytes per output row
-        uint8_t *po = j.out + (uint64_t)(2 * k0) * rstep + (BYTES_OUT ? c : 2 * c);
-        auto step = [&](const Coef &c1) {
-            uint32_t ev[4], xo[4], ve[4], vo[4];
-            col_unstep(c1, false, xe, d0, ev, xo);
-            unlift_row<false>(ev, c, Ws, false, ve);
-            unlift_row<false>(xo, c, Ws, false, vo);
-            if (own) {
-                if (BYTES_OUT) {
-                    *reinterpret_cast<uint2 *>(po) = make_uint2(__byte_perm(ve[0], ve[1], 0x6420),
-                                                                __byte_perm(ve[2], ve[3], 0x6420));
-                    *reinterpret_cast<uint2 *>(po + rstep) = make_uint2(
-                        __byte_perm(vo[0], vo[1], 0x6420), __byte_perm(vo[2], vo[3], 0x6420));
-                } else {
-                    *reinterpret_cast<uint4 *>(po) = make_uint4(ve[0], ve[1], ve[2], ve[3]);
-                    *reinterpret_cast<uint4 *>(po + rstep) = make_uint4(vo[0], vo[1], vo[2], vo[3]);
-                }
-            }
-            po += 2 * rstep;
-        };
-        int i = 0;
-        for (; i + D <= n_it; i += D) {
-#pragma unroll
-            for (int s = 0; s < D; ++s) {
-                const Coef c1 = ring[s];
-                if (i + s + D < n_it)
-                    ring[s] = ld();
-                step(c1);
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < D - 1; ++s)
-            if (i + s < n_it)
-                step(ring[s]);
-        return;
-    }
-
-    // general path: bounds checks and the border rules, a shorter ring of
-    // loads in flight
-    constexpr int D = FRAG_PREFETCH_GENERAL;
+    const bool edge = (kStripCols * sx + 248 >= Ws);
     const bool vec = ((j.Ws & 7u) == 0);
     const bool own = lane >= 1 && lane <= 30 && c < Ws;
     const int nv = min(8, Ws - c);
-    Coef ring[D];
+    uint32_t xe[4], d0[4];
     {
-        const Coef cur = load_coef<TOP>(j, k0, x, vec);
-        const Coef prev = load_coef<TOP>(j, max(k0 - 1, 0), x, vec);
-        const uint32_t dm[4] = {k0 == 0 ? cur.dl[0] : prev.dl[0], k0 == 0 ? cur.dl[1] : prev.dl[1],
-                                k0 == 0 ? cur.dh[0] : prev.dh[0], k0 == 0 ? cur.dh[1] : prev.dh[1]};
-        const uint32_t s[4] = {cur.sl[0], cur.sl[1], cur.sh[0], cur.sh[1]};
-        d0[0] = cur.dl[0];
-        d0[1] = cur.dl[1];
-        d0[2] = cur.dh[0];
-        d0[3] = cur.dh[1];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            xe[i] = s[i] - pq4(dm[i], d0[i]) + 0x20002000u; // undo Eq. 5.2 down the columns
-#pragma unroll
-        for (int t = 0; t < D; ++t)
-            ring[t] = t < n_it ? load_coef<TOP>(j, k0 + 1 + t, x, vec) : cur;
+        const Coef cur = load_coef(j, k0, x, vec);
+        const Coef prev = load_coef(j, max(k0 - 1, 0), x, vec);
+        col_unstart(prev, cur, k0 == 0, xe, d0);
     }
-    auto gstep = [&](int k, const Coef &c1) {
+    Coef nxt = load_coef(j, k0 + 1, x, vec);
+    for (int k = k0; k < k1; ++k) {
+        const Coef c1 = nxt;
+        if (k + 1 < k1)
+            nxt = load_coef(j, k + 2, x, vec);
         uint32_t ev[4], xo[4], ve[4], vo[4];
         col_unstep(c1, 2 * k + 2 == Hs, xe, d0, ev, xo); // x[m] = x[m-2] at the bottom
         unlift_row<true>(ev, c, Ws, edge, ve);
         unlift_row<true>(xo, c, Ws, edge, vo);
         store_row<BYTES_OUT>(j, 2 * k, c, own, nv, ve);
         store_row<BYTES_OUT>(j, 2 * k + 1, c, own, nv, vo);
-    };
-    int i = 0;
-    for (; i + D <= n_it; i += D) {
-#pragma unroll
-        for (int t = 0; t < D; ++t) {
-            const Coef c1 = ring[t];
-            if (i + t + D < n_it)
-                ring[t] = load_coef<TOP>(j, k0 + 1 + i + t + D, x, vec);
-            gstep(k0 + i + t, c1);
-        }
     }
-#pragma unroll
-    for (int t = 0; t < D - 1; ++t)
-        if (i + t < n_it)
-            gstep(k0 + i + t, ring[t]);
 }
 
 // ---------------------------------------------------------------------------
-// cipher unit: AES-128-CTR over the private fragment (LL_L, int16 LE, rows of
+// cipher: AES-128-CTR over the private fragment (LL_L, int16 LE, rows of
 // 2 Ws bytes).  Segment sy owns the blocks that start in its rows [q0, q1);
-// strip sx of it takes kCipherBlocks of them, one per lane at a time.
-// out = in XOR keystream (in may equal out).
+// unit sx of it takes kCipherBlocks of them, an equal share per consumer
+// warp, one per lane at a time.  out = in XOR keystream (in may equal out).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cipher_range(const LevelJob &j, int sx, int sy, uint64_t &bs,
                                              uint64_t &be)
@@ -792,14 +609,16 @@ __device__ __forceinline__ void cipher_range(const LevelJob &j, int sx, int sy, 
     be = min(bs + kCipherBlocks, b1);
 }
 
-__device__ void cipher_unit(const LevelJob &j, int sx, int sy, const AesTab &aes, int lane,
+__device__ void cipher_warp(const LevelJob &j, int sx, int sy, int w, const AesTab &aes, int lane,
                             const uint8_t *in, uint8_t *out, bool coherent)
 {
     const uint64_t total = 2ull * j.Ws * j.Hs;
     uint64_t bs, be;
     cipher_range(j, sx, sy, bs, be);
+    constexpr uint32_t per_warp = kCipherBlocks / kConsumerWarps;
+    const uint64_t ws = min(bs + (uint64_t)w * per_warp, be), we = min(ws + per_warp, be);
     const bool vec = (((uintptr_t)in | (uintptr_t)out) & 15u) == 0;
-    for (uint64_t b = bs + lane; b < be; b += 32) {
+    for (uint64_t b = ws + lane; b < we; b += 32) {
         uint32_t ks[4];
         aes_block(aes, j.nonce, b, ks);
         const uint64_t o = 16 * b;
@@ -824,10 +643,350 @@ __device__ void cipher_unit(const LevelJob &j, int sx, int sy, const AesTab &aes
 } // namespace strm
 
 // ---------------------------------------------------------------------------
-// kernel: persistent warps over a dependency-ordered queue of units
+// shared-memory stage ring
 // ---------------------------------------------------------------------------
-constexpr int kStreamThreads = 256;
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
 
+// one test of the phase; the thread may sleep up to about 1 us for it first
+__device__ __forceinline__ bool mbar_try_wait(const uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity), "n"(1000)
+                 : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the phase of the given parity; false if it ran out
+__device__ __forceinline__ bool mbar_wait(const uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < kStageSpin; ++it)
+        if (mbar_try_wait(bar, parity))
+            return true;
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy of `bytes` (16-byte aligned addresses, size a
+// multiple of 16), completion counted on `bar`
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+                     "r"(smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+struct Ring {
+    uint8_t *data;   // kStages x kStageBytes
+    uint64_t *full;  // producer arrival + copied bytes
+    uint64_t *empty; // one arrival per consumer warp
+    StageHdr *hdr;
+    int *err;
+};
+
+// consumer side: wait until stage `it` is full (all lanes); nullptr if the
+// wait ran out (error word set).  A phase, once complete, stays visible until
+// this warp releases the stage, so a lane that gave up just before another saw
+// it complete looks again.
+__device__ __forceinline__ const uint8_t *ring_wait(Ring r, uint32_t it)
+{
+    const uint32_t s = it % kStages, parity = (it / kStages) & 1u;
+    bool ok = mbar_wait(r.full + s, parity);
+    if (__any_sync(0xffffffffu, ok) && !ok)
+        ok = mbar_wait(r.full + s, parity);
+    if (!__all_sync(0xffffffffu, ok)) {
+        if ((threadIdx.x & 31) == 0)
+            atomicCAS(r.err, 0, 4);
+        return nullptr;
+    }
+    return r.data + s * kStageBytes;
+}
+
+// consumer side: this warp is done reading stage `it`
+__device__ __forceinline__ void ring_release(Ring r, uint32_t it)
+{
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0)
+        mbar_arrive(r.empty + it % kStages);
+}
+
+// ---------------------------------------------------------------------------
+// bulk consumers (one warp, one strip of the tile)
+// ---------------------------------------------------------------------------
+namespace strm {
+
+// The stages of one unit, read row by row: a warp holds one stage at a time and
+// releases it when its rows are used up.
+struct Cursor {
+    Ring ring;
+    uint32_t base;     // ring index of the unit's first stage
+    int cur;           // stage of the unit held now
+    const uint8_t *st; // its data
+
+    __device__ __forceinline__ Cursor(Ring r, uint32_t b, const uint8_t *first)
+        : ring(r), base(b), cur(0), st(first)
+    {
+    }
+
+    // slot of unit row t (rps rows of `slot` bytes per stage); nullptr if a
+    // stage wait ran out
+    __device__ __forceinline__ const uint8_t *row(int t, int rps, int slot)
+    {
+        const int k = t / rps;
+        if (k != cur) {
+            ring_release(ring, base + cur);
+            cur = k;
+            st = ring_wait(ring, base + k);
+            if (st == nullptr)
+                return nullptr;
+        }
+        return st + (t - k * rps) * slot;
+    }
+
+    __device__ __forceinline__ void finish(uint32_t &it, int nstages)
+    {
+        ring_release(ring, base + cur);
+        it = base + nstages;
+    }
+};
+
+// a warp with no strip in the tile still takes part in every stage
+__device__ __forceinline__ bool skip_stages(Ring ring, uint32_t &it, int nstages)
+{
+    ring_release(ring, it);
+    for (int k = 1; k < nstages; ++k) {
+        if (ring_wait(ring, it + k) == nullptr)
+            return false;
+        ring_release(ring, it + k);
+    }
+    it += nstages;
+    return true;
+}
+
+// samples of the lane from a row slot: the slot holds columns [C0 - 16, ...)
+// of the row; the lane's columns start `off` samples into the slot
+template <bool BYTES>
+__device__ __forceinline__ Raw slot_row(const uint8_t *slot, int off)
+{
+    Raw r;
+    if (BYTES) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(slot + off);
+        r.w[0] = t.x;
+        r.w[1] = t.y;
+        r.w[2] = r.w[3] = 0;
+    } else {
+        const uint4 t = *reinterpret_cast<const uint4 *>(slot + 2 * off);
+        r.w[0] = t.x;
+        r.w[1] = t.y;
+        r.w[2] = t.z;
+        r.w[3] = t.w;
+    }
+    return r;
+}
+
+template <bool BYTES>
+__host__ __device__ constexpr int fwd_slot_bytes()
+{
+    return BYTES ? 1024 : 2048;
+}
+
+// Forward bulk unit.  Unit rows t = 0 .. 2 n + 2 are image rows 2 q0 - 2 + t
+// (rows outside the image are not copied and not used), packed into stages
+// of kStageBytes / slot rows; stage 0 (already waited for) is at `it`.
+// border: the tile touches a column border (symmetric extension, checked
+// stores).  Returns false if a stage wait ran out.
+template <bool BYTES>
+__device__ bool fwd_bulk(const LevelJob &j, int tx, int sy, int w, int lane, bool border,
+                         Ring ring, uint32_t &it, const uint8_t *st0)
+{
+    constexpr int slot = fwd_slot_bytes<BYTES>(), rps = kStageBytes / slot;
+    const int Ws = (int)j.Ws, Hs = (int)j.Hs;
+    const int sx = kConsumerWarps * tx + w;
+    const int c = kStripCols * sx - 8 + 8 * lane;
+    const int off = kStripCols * w + 8 + 8 * lane; // slot column of c
+    const int q0 = sy * (int)j.seg_pairs;
+    const int q1 = min(q0 + (int)j.seg_pairs, Hs / 2);
+    const int n_it = q1 - q0;
+    const int nstages = (2 * n_it + 3 + rps - 1) / rps;
+    if (sx >= (int)j.wstrips)
+        return skip_stages(ring, it, nstages);
+    const int Wl = Ws / 2;
+    const int x = c / 2;
+    const bool edge = border && (kStripCols * sx + 248 >= Ws);
+    const bool own = lane >= 1 && lane <= 30 && x < Wl;
+    const int nval = min(4, Wl - x);
+    const bool top = q0 == 0, bottom = 2 * q1 >= Hs, final_level = j.final_level;
+    Cursor cu(ring, it, st0);
+    uint32_t e0[4], dp[4];
+    {
+        const uint8_t *p;
+        if ((p = cu.row(0, rps, slot)) == nullptr)
+            return false;
+        const Raw rm2 = slot_row<BYTES>(p, off);
+        if ((p = cu.row(1, rps, slot)) == nullptr)
+            return false;
+        const Raw rm1 = slot_row<BYTES>(p, off);
+        if ((p = cu.row(2, rps, slot)) == nullptr)
+            return false;
+        const Raw r0 = slot_row<BYTES>(p, off);
+        uint32_t a[4], o[4];
+        lift_row<BYTES, true>(r0, c, Ws, edge, e0);
+        lift_row<BYTES, true>(rm2, c, Ws, edge, a);
+        lift_row<BYTES, true>(rm1, c, Ws, edge, o);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            dp[i] = o[i] - pavg(a[i], e0[i]) + kB2; // (replaced at the top border)
+    }
+    const uint64_t ostep = 2ull * (uint64_t)Wl;
+    const uint64_t o0 = 2ull * ((uint64_t)q0 * (uint64_t)Wl + (uint64_t)x);
+    uint8_t *phl = j.hl + o0, *plh = j.lh + o0, *phh = j.hh + o0, *pll = j.ll + o0;
+    for (int q = q0; q < q1; ++q) {
+        const int t = 3 + 2 * (q - q0);
+        const uint8_t *p;
+        if ((p = cu.row(t, rps, slot)) == nullptr)
+            return false;
+        const Raw c1 = slot_row<BYTES>(p, off);
+        if ((p = cu.row(t + 1, rps, slot)) == nullptr)
+            return false;
+        const Raw c2 = slot_row<BYTES>(p, off);
+        uint32_t o[4], e1[4], sv[4], dv[4];
+        lift_row<BYTES, true>(c1, c, Ws, edge, o);
+        if (bottom && 2 * q + 2 == Hs) { // x[m] = x[m-2] at the bottom border
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                e1[k] = e0[k];
+        } else {
+            lift_row<BYTES, true>(c2, c, Ws, edge, e1);
+        }
+        col_step(o, e1, e0, dp, top && q == 0, sv, dv);
+        if (border) {
+            if (own)
+                fwd_store(j, Wl, q, x, nval, sv, dv);
+        } else if (own) {
+            *reinterpret_cast<uint2 *>(phl) = make_uint2(to_i16x2(sv[2]), to_i16x2(sv[3]));
+            *reinterpret_cast<uint2 *>(plh) = make_uint2(to_i16x2(dv[0]), to_i16x2(dv[1]));
+            *reinterpret_cast<uint2 *>(phh) = make_uint2(to_i16x2(dv[2]), to_i16x2(dv[3]));
+            *reinterpret_cast<uint2 *>(pll) = ll_out(final_level, sv);
+        }
+        phl += ostep;
+        plh += ostep;
+        phh += ostep;
+        pll += ostep;
+    }
+    cu.finish(it, nstages);
+    return true;
+}
+
+// coefficients of the lane from a coefficient-row slot: four 1 KB arrays (LL,
+// LH, HL, HH), each holding coefficient columns [C0/2 - 8, ...) of one row
+__device__ __forceinline__ Coef slot_coef(const uint8_t *st, int off, bool top)
+{
+    const uint2 a = *reinterpret_cast<const uint2 *>(st + off);
+    const uint2 b = *reinterpret_cast<const uint2 *>(st + kCoefSlot + off);
+    const uint2 h = *reinterpret_cast<const uint2 *>(st + 2 * kCoefSlot + off);
+    const uint2 d = *reinterpret_cast<const uint2 *>(st + 3 * kCoefSlot + off);
+    Coef cf;
+    cf.sl[0] = top ? from_i16x2(a.x) + 0x00800080u : a.x;
+    cf.sl[1] = top ? from_i16x2(a.y) + 0x00800080u : a.y;
+    cf.dl[0] = from_i16x2(b.x);
+    cf.dl[1] = from_i16x2(b.y);
+    cf.sh[0] = from_i16x2(h.x);
+    cf.sh[1] = from_i16x2(h.y);
+    cf.dh[0] = from_i16x2(d.x);
+    cf.dh[1] = from_i16x2(d.y);
+    return cf;
+}
+
+// Inverse bulk unit.  Unit rows t = 0 .. n + 1 are coefficient rows k0 - 1 + t
+// (rows outside the bands are not copied and not used), kStageBytes /
+// kCoefRow per stage; stage 0 (already waited for) is at `it`.  border: the
+// tile touches a column border or its rows run past the end of the output
+// bytes (symmetric extension, checked stores).  Returns false if a stage
+// wait ran out.
+template <bool BYTES_OUT>
+__device__ bool inv_bulk(const LevelJob &j, int tx, int sy, int w, int lane, bool border,
+                         Ring ring, uint32_t &it, const uint8_t *st0)
+{
+    constexpr int rps = kStageBytes / kCoefRow;
+    const int Ws = (int)j.Ws, Hs = (int)j.Hs;
+    const int sx = kConsumerWarps * tx + w;
+    const int c = kStripCols * sx - 8 + 8 * lane;
+    const int off = 2 * (kStripCols / 2 * w + 4 + 4 * lane); // slot byte offset of coefficient c/2
+    const int k0 = sy * (int)j.seg_pairs;
+    const int k1 = min(k0 + (int)j.seg_pairs, Hs / 2);
+    const int n_it = k1 - k0;
+    const int nstages = (n_it + 2 + rps - 1) / rps;
+    if (sx >= (int)j.wstrips)
+        return skip_stages(ring, it, nstages);
+    const bool edge = border && (kStripCols * sx + 248 >= Ws);
+    const bool own = lane >= 1 && lane <= 30 && c < Ws;
+    const int nv = min(8, Ws - c);
+    const bool bottom = 2 * k1 >= Hs, top_level = j.top_level;
+    Cursor cu(ring, it, st0);
+    uint32_t xe[4], d0[4];
+    {
+        const uint8_t *p;
+        if ((p = cu.row(0, rps, kCoefRow)) == nullptr)
+            return false;
+        const Coef prev = slot_coef(p, off, top_level);
+        if ((p = cu.row(1, rps, kCoefRow)) == nullptr)
+            return false;
+        const Coef cur = slot_coef(p, off, top_level);
+        col_unstart(prev, cur, k0 == 0, xe, d0);
+    }
+    const uint64_t rstep = BYTES_OUT ? (uint64_t)Ws : 2ull * (uint64_t)Ws; // bytes per output row
+    uint8_t *po = j.out + (uint64_t)(2 * k0) * rstep + (BYTES_OUT ? c : 2 * c);
+    for (int k = k0; k < k1; ++k) {
+        const uint8_t *p;
+        if ((p = cu.row(2 + (k - k0), rps, kCoefRow)) == nullptr)
+            return false;
+        const Coef c1 = slot_coef(p, off, top_level);
+        uint32_t ev[4], xo[4], ve[4], vo[4];
+        col_unstep(c1, bottom && 2 * k + 2 == Hs, xe, d0, ev, xo);
+        unlift_row<true>(ev, c, Ws, edge, ve);
+        unlift_row<true>(xo, c, Ws, edge, vo);
+        if (border) {
+            store_row<BYTES_OUT>(j, 2 * k, c, own, nv, ve);
+            store_row<BYTES_OUT>(j, 2 * k + 1, c, own, nv, vo);
+        } else if (own) {
+            if (BYTES_OUT) {
+                *reinterpret_cast<uint2 *>(po) = make_uint2(__byte_perm(ve[0], ve[1], 0x6420),
+                                                            __byte_perm(ve[2], ve[3], 0x6420));
+                *reinterpret_cast<uint2 *>(po + rstep) = make_uint2(__byte_perm(vo[0], vo[1], 0x6420),
+                                                                    __byte_perm(vo[2], vo[3], 0x6420));
+            } else {
+                *reinterpret_cast<uint4 *>(po) = make_uint4(ve[0], ve[1], ve[2], ve[3]);
+                *reinterpret_cast<uint4 *>(po + rstep) = make_uint4(vo[0], vo[1], vo[2], vo[3]);
+            }
+        }
+        po += 2 * rstep;
+    }
+    cu.finish(it, nstages);
+    return true;
+}
+
+} // namespace strm
+
+// ---------------------------------------------------------------------------
+// work queue, dependencies
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned ld_relaxed(const unsigned *p)
 {
     unsigned v;
@@ -835,13 +994,13 @@ __device__ __forceinline__ unsigned ld_relaxed(const unsigned *p)
     return v;
 }
 
-// lane 0: wait until done[lo .. hi] all reach `target`.  Polls are relaxed
-// loads with a growing sleep between them (no cache invalidation per poll);
-// one acquire fence orders the unit's reads after the counts it saw.
+// wait until done[lo .. hi] all reach `target`.  Polls are relaxed loads with
+// a growing sleep between them (no cache invalidation per poll); one acquire
+// fence orders what follows after the counts seen.
 __device__ __forceinline__ bool wait_segments(const unsigned *done, uint32_t lo, uint32_t hi,
                                               unsigned target, uint32_t spin_limit, int *err)
 {
-    uint32_t it = 0, ns = 128;
+    uint32_t it = 0, ns = 64;
     for (uint32_t s = lo; s <= hi; ++s) {
         while (ld_relaxed(done + s) < target) {
             if (++it > spin_limit) {
@@ -849,7 +1008,7 @@ __device__ __forceinline__ bool wait_segments(const unsigned *done, uint32_t lo,
                 return false;
             }
             __nanosleep(ns);
-            ns = min(2 * ns, 2048u);
+            ns = min(2 * ns, 1024u);
         }
     }
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
@@ -863,7 +1022,7 @@ __device__ __forceinline__ const LevelJob &dag_job(const DagWork &w, uint32_t i)
 
 // Implicit order for one buffer: job m (in processing order) runs its segment
 // sy in round sy + m * lag; rounds in order, jobs in order within a round,
-// strips within a job.  All jobs have the same segment count.
+// units within a job.  All jobs have the same segment count.
 __device__ __forceinline__ void implicit_unit(const DagWork &w, uint64_t t, uint32_t &job,
                                               uint32_t &sx, uint32_t &sy)
 {
@@ -902,11 +1061,12 @@ __device__ __forceinline__ void implicit_unit(const DagWork &w, uint64_t t, uint
     }
 }
 
-// Segments [slo, shi] of producer p that write the data unit (j, sy) reads.
+// Segments [slo, shi] of job j.dep that write the data unit (j, sx, sy) reads.
 template <bool FWD>
-__device__ __forceinline__ void producer_segments(const LevelJob &j, const LevelJob &p, int sx,
-                                                  int sy, uint32_t &slo, uint32_t &shi)
+__device__ __forceinline__ void producer_segments(const LevelJob &j, int sx, int sy, uint32_t &slo,
+                                                  uint32_t &shi)
 {
+    const uint32_t p_seg_pairs = j.dep_seg_pairs;
     if (j.kind == kJobCipher) {
         // forward cipher after the last level: the LL_L rows its blocks touch
         const uint64_t rowb = 2ull * j.Ws;
@@ -918,16 +1078,16 @@ __device__ __forceinline__ void producer_segments(const LevelJob &j, const Level
             return;
         }
         const uint64_t last = min(16 * be, rowb * j.Hs) - 1; // last byte touched
-        slo = (uint32_t)(((16 * bs) / rowb) / p.seg_pairs);
-        shi = (uint32_t)((last / rowb) / p.seg_pairs);
+        slo = (uint32_t)(((16 * bs) / rowb) / p_seg_pairs);
+        shi = (uint32_t)((last / rowb) / p_seg_pairs);
         return;
     }
     if (FWD) {
         // source rows 2 q0 - 2 .. 2 q1 of the level-(l-1) image = LL_{l-1} rows
         const int q0 = sy * (int)j.seg_pairs;
         const int q1 = min(q0 + (int)j.seg_pairs, (int)j.Hs / 2);
-        slo = (uint32_t)(max(2 * q0 - 2, 0) / (int)p.seg_pairs);
-        shi = (uint32_t)(min(2 * q1, (int)j.Hs - 1) / (int)p.seg_pairs);
+        slo = (uint32_t)(max(2 * q0 - 2, 0) / (int)p_seg_pairs);
+        shi = (uint32_t)(min(2 * q1, (int)j.Hs - 1) / (int)p_seg_pairs);
         return;
     }
     // inverse: coefficient rows k0 - 1 .. k1 of LL_l
@@ -935,107 +1095,336 @@ __device__ __forceinline__ void producer_segments(const LevelJob &j, const Level
     const int k1 = min(k0 + (int)j.seg_pairs, (int)j.Hs / 2);
     const int Hl = (int)j.Hs / 2;
     const int rlo = max(k0 - 1, 0), rhi = min(k1, Hl - 1);
-    if (p.kind == kJobCipher) {
+    if (j.dep_kind == kJobCipher) {
         // deciphered rows: a row is complete once every block overlapping it
         // is; block b belongs to the segment of the row it starts in
-        const uint64_t rowb = 2ull * p.Ws;
+        const uint64_t rowb = 2ull * j.dep_Ws;
         const uint64_t blo = ((uint64_t)rlo * rowb) / 16;
         const uint64_t bhi = (((uint64_t)rhi + 1) * rowb - 1) / 16;
-        slo = (uint32_t)(((16 * blo) / rowb) / p.seg_pairs);
-        shi = (uint32_t)(((16 * bhi) / rowb) / p.seg_pairs);
+        slo = (uint32_t)(((16 * blo) / rowb) / p_seg_pairs);
+        shi = (uint32_t)(((16 * bhi) / rowb) / p_seg_pairs);
         return;
     }
     // the previous inverse level's segment s writes LL_l rows
     // [2 s seg_pairs, 2 (s + 1) seg_pairs)
-    slo = (uint32_t)(rlo / (2 * (int)p.seg_pairs));
-    shi = (uint32_t)(rhi / (2 * (int)p.seg_pairs));
+    slo = (uint32_t)(rlo / (2 * (int)p_seg_pairs));
+    shi = (uint32_t)(rhi / (2 * (int)p_seg_pairs));
 }
 
-// true if the unit may run (its producers are complete)
-template <bool FWD>
-__device__ __forceinline__ bool wait_producers(const DagWork &w, const LevelJob &j, int sx, int sy,
-                                               int lane)
-{
-    int ok = 1;
-    if (j.dep >= 0) {
-        if (lane == 0) {
-            const LevelJob &p = dag_job(w, (uint32_t)j.dep);
-            uint32_t slo, shi;
-            producer_segments<FWD>(j, p, sx, sy, slo, shi);
-            shi = min(shi, p.segs - 1);
-            ok = slo > shi ||
-                         wait_segments(w.done + p.done_off, slo, shi, p.strips, w.spin_limit, w.err)
-                     ? 1
-                     : 0;
+// ---------------------------------------------------------------------------
+// producer: one elected lane of the producer warp
+// ---------------------------------------------------------------------------
+struct Producer {
+    Ring ring;
+    uint32_t it = 0; // stages issued
+
+    __device__ explicit Producer(Ring r) : ring(r) {}
+
+    // claim the next stage (bounded wait for the consumers to release it)
+    __device__ __forceinline__ uint8_t *claim(uint32_t &s)
+    {
+        s = it % kStages;
+        if (it >= (uint32_t)kStages && !mbar_wait(ring.empty + s, ((it / kStages) - 1) & 1u)) {
+            atomicCAS(ring.err, 0, 4);
+            return nullptr;
         }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        __syncwarp();
+        // the consumers' reads of the previous contents come before the copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        return ring.data + s * kStageBytes;
     }
-    return ok != 0;
+
+    // the header of a unit's first stage: the job descriptor and the unit
+    __device__ __forceinline__ void header(uint32_t s, const LevelJob &job, uint32_t x, uint32_t y,
+                                           uint32_t mode)
+    {
+        StageHdr &h = ring.hdr[s];
+        h.job = job;
+        h.x = x;
+        h.y = y;
+        h.mode = mode;
+    }
+
+    // a stage holding only a header
+    __device__ __forceinline__ bool emit(const LevelJob &job, uint32_t x, uint32_t y, uint32_t mode)
+    {
+        uint32_t s;
+        if (claim(s) == nullptr)
+            return false;
+        header(s, job, x, y, mode);
+        mbar_arrive(ring.full + s);
+        ++it;
+        return true;
+    }
+
+    // the end-of-work stage
+    __device__ __forceinline__ bool finish()
+    {
+        uint32_t s;
+        if (claim(s) == nullptr)
+            return false;
+        ring.hdr[s].mode = kModeEnd;
+        mbar_arrive(ring.full + s);
+        ++it;
+        return true;
+    }
+
+    // wait (bounded) for the copies of the last stages issued
+    __device__ void drain()
+    {
+        const uint32_t first = it > (uint32_t)kStages ? it - kStages : 0;
+        for (uint32_t i = first; i < it; ++i)
+            mbar_wait(ring.full + i % kStages, (i / kStages) & 1u);
+    }
+};
+
+// Forward bulk stages of unit (j, tx, sy): unit rows t = 0 .. 2 n + 2 are
+// image rows 2 q0 - 2 + t, each copied as columns [C0 - 16, C0 + 976) clipped
+// to the image (element size 1 for bytes, 2 for packed pairs) into a row slot.
+__device__ bool produce_fwd(Producer &pr, const LevelJob &j, int tx, int sy, uint32_t mode)
+{
+    const int Ws = (int)j.Ws, Hs = (int)j.Hs;
+    const bool bytes_src = j.src_bytes;
+    const uint32_t esz = bytes_src ? 1u : 2u;
+    const int slot = bytes_src ? strm::fwd_slot_bytes<true>() : strm::fwd_slot_bytes<false>();
+    const int rps = kStageBytes / slot;
+    const int C0 = kTileCols * tx;
+    const int lo = max(C0 - 16, 0), hi = min(C0 + kTileCols + 16, Ws);
+    const uint32_t bytes = (uint32_t)(hi - lo) * esz;
+    const uint32_t dst = (uint32_t)(lo - (C0 - 16)) * esz;
+    const int q0 = sy * (int)j.seg_pairs;
+    const int q1 = min(q0 + (int)j.seg_pairs, Hs / 2);
+    const int T = 2 * (q1 - q0) + 3, r0 = 2 * q0 - 2;
+    for (int t0 = 0; t0 < T; t0 += rps) {
+        const int t1 = min(t0 + rps, T);
+        uint32_t s;
+        uint8_t *st = pr.claim(s);
+        if (st == nullptr)
+            return false;
+        if (t0 == 0)
+            pr.header(s, j, (uint32_t)tx, (uint32_t)sy, mode);
+        // rows of the image in this stage: [ra, rb)
+        const int ra = max(r0 + t0, 0), rb = min(r0 + t1, Hs);
+        if (rb <= ra) {
+            mbar_arrive(pr.ring.full + s);
+        } else {
+            mbar_arrive_tx(pr.ring.full + s, (uint32_t)(rb - ra) * bytes);
+            for (int r = ra; r < rb; ++r)
+                bulk_copy(st + (r - r0 - t0) * slot + dst, j.src + ((uint64_t)r * Ws + lo) * esz,
+                          bytes, pr.ring.full + s);
+        }
+        ++pr.it;
+    }
+    return true;
 }
 
-template <bool FWD>
-__global__ void __launch_bounds__(kStreamThreads, FRAG_BLOCKS_PER_SM) dag_kernel(DagWork w)
+// Inverse bulk stages of unit (j, tx, sy): unit rows t = 0 .. n + 1 are
+// coefficient rows k0 - 1 + t of LL, LH, HL, HH, columns [C0/2 - 8,
+// C0/2 + 488) clipped to the band, one 4 KB coefficient-row slot each.
+__device__ bool produce_inv(Producer &pr, const LevelJob &j, int tx, int sy, uint32_t mode)
 {
-    __shared__ AesTab aes;
-    const int lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < kAesWords; i += blockDim.x)
-        (&aes.T[0][0])[i] = w.aes_tables[i];
-    for (int i = threadIdx.x; i < 44; i += blockDim.x)
-        aes.rk[i] = w.round_keys[i];
-    __syncthreads();
-    for (;;) {
-        unsigned long long t = 0;
-        if (lane == 0)
-            t = atomicAdd(w.queue, 1ull);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= w.total_units)
-            break;
-        uint32_t ji, ux, uy;
-        if (w.n_inline) {
-            implicit_unit(w, t, ji, ux, uy);
+    constexpr int rps = kStageBytes / kCoefRow;
+    const int Hl = (int)j.Hs / 2, Wl = (int)j.Ws / 2;
+    const int X0 = kTileCols / 2 * tx - 8;
+    const int lo = max(X0, 0), hi = min(X0 + kTileCols / 2 + 16, Wl);
+    const uint32_t bytes = 2u * (uint32_t)(hi - lo);
+    const uint32_t dst = 2u * (uint32_t)(lo - X0);
+    const int k0 = sy * (int)j.seg_pairs;
+    const int k1 = min(k0 + (int)j.seg_pairs, Hl);
+    const int T = k1 - k0 + 2, r0 = k0 - 1;
+    const uint8_t *arr[4] = {j.ll_in, j.lh, j.hl, j.hh};
+    for (int t0 = 0; t0 < T; t0 += rps) {
+        const int t1 = min(t0 + rps, T);
+        uint32_t s;
+        uint8_t *st = pr.claim(s);
+        if (st == nullptr)
+            return false;
+        if (t0 == 0)
+            pr.header(s, j, (uint32_t)tx, (uint32_t)sy, mode);
+        const int ra = max(r0 + t0, 0), rb = min(r0 + t1, Hl);
+        if (rb <= ra) {
+            mbar_arrive(pr.ring.full + s);
         } else {
-            const DagUnit un = w.units[t];
-            ji = un.job;
-            ux = un.sx;
-            uy = un.sy;
-        }
-        const LevelJob j = dag_job(w, ji);
-        const int sx = (int)ux, sy = (int)uy;
-        if (wait_producers<FWD>(w, j, sx, sy, lane)) {
-            if (j.kind == kJobCipher) {
-                if (FWD)
-                    strm::cipher_unit(j, sx, sy, aes, lane, j.ll, j.ll, true); // in place
-                else
-                    strm::cipher_unit(j, sx, sy, aes, lane, j.ll_in, j.out, false);
-            } else if (FWD) {
-                if (j.src_bytes) {
-                    if (j.final_level)
-                        strm::fwd_unit<true, true>(j, sx, sy, lane);
-                    else
-                        strm::fwd_unit<true, false>(j, sx, sy, lane);
-                } else {
-                    if (j.final_level)
-                        strm::fwd_unit<false, true>(j, sx, sy, lane);
-                    else
-                        strm::fwd_unit<false, false>(j, sx, sy, lane);
-                }
-            } else {
-                if (j.top_level) {
-                    if (j.out_bytes)
-                        strm::inv_unit<true, true>(j, sx, sy, lane);
-                    else
-                        strm::inv_unit<true, false>(j, sx, sy, lane);
-                } else {
-                    if (j.out_bytes)
-                        strm::inv_unit<false, true>(j, sx, sy, lane);
-                    else
-                        strm::inv_unit<false, false>(j, sx, sy, lane);
-                }
+            mbar_arrive_tx(pr.ring.full + s, (uint32_t)(rb - ra) * 4u * bytes);
+            for (int r = ra; r < rb; ++r) {
+                const uint64_t o = 2ull * ((uint64_t)r * Wl + lo);
+                uint8_t *row = st + (r - r0 - t0) * kCoefRow + dst;
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+                    bulk_copy(row + a * kCoefSlot, arr[a] + o, bytes, pr.ring.full + s);
             }
         }
-        // publish: every lane's stores before the count (jobs that nothing
-        // in the launch reads skip it)
+        ++pr.it;
+    }
+    return true;
+}
+
+// Which path unit (j, tx, sy) takes: bulk rows need whole aligned runs (the
+// host sets j.bulk when bases and pitches allow it); forward byte sources also
+// need every row read to lie before n.
+template <bool FWD>
+__device__ __forceinline__ uint32_t unit_mode(const LevelJob &j, int tx, int sy)
+{
+    if (!j.bulk)
+        return kModeGeneral;
+    const int Ws = (int)j.Ws, Hs = (int)j.Hs;
+    const bool col_edge = tx == 0 || kTileCols * tx + kTileCols + 8 >= Ws;
+    const int p0 = sy * (int)j.seg_pairs;
+    const int p1 = min(p0 + (int)j.seg_pairs, Hs / 2);
+    if (FWD) {
+        if (j.src_bytes && (uint64_t)(min(2 * p1, Hs - 1) + 1) * (uint64_t)Ws > j.n)
+            return kModeGeneral;
+        return col_edge ? kModeBulkEdge : kModeBulk;
+    }
+    const bool tail = j.out_bytes && (uint64_t)(2 * p1) * (uint64_t)Ws > j.n;
+    return (col_edge || tail) ? kModeBulkEdge : kModeBulk;
+}
+
+// unit t of the launch: (job, x, y)
+__device__ __forceinline__ void unit_at(const DagWork &w, uint64_t t, uint32_t &ji, uint32_t &ux,
+                                        uint32_t &uy)
+{
+    if (w.n_inline) {
+        implicit_unit(w, t, ji, ux, uy);
+    } else {
+        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(w.units + t));
+        ji = u.x;
+        ux = u.y;
+        uy = u.z;
+    }
+}
+
+// job descriptor i, through the read-only cache for a batch
+__device__ __forceinline__ LevelJob load_job(const DagWork &w, uint32_t i)
+{
+    if (w.n_inline)
+        return w.inline_jobs[i];
+    LevelJob j;
+    const uint4 *src = reinterpret_cast<const uint4 *>(w.jobs + i);
+    uint4 *dst = reinterpret_cast<uint4 *>(&j);
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(LevelJob) / 16); ++k)
+        dst[k] = __ldg(src + k);
+    return j;
+}
+
+// The producer claims units from the queue, one ahead: the claim of the next
+// unit and its index are in flight while the current unit streams.  A CTA
+// only ever holds the unit it streams and the one after it, both later in
+// the queue than everything they wait for, so every wait ends once earlier
+// units finish -- whether or not the whole grid is resident.
+template <bool FWD>
+__device__ void producer_loop(const DagWork &w, Ring ring)
+{
+    Producer pr(ring);
+    unsigned long long t = atomicAdd(w.queue, 1ull);
+    uint32_t ji = 0, ux = 0, uy = 0;
+    if (t < w.total_units)
+        unit_at(w, t, ji, ux, uy);
+    while (t < w.total_units) {
+        const unsigned long long nt = atomicAdd(w.queue, 1ull);
+        const LevelJob j = load_job(w, ji);
+        bool ok = true;
+        if (j.dep >= 0) {
+            uint32_t slo, shi;
+            producer_segments<FWD>(j, (int)ux, (int)uy, slo, shi);
+            shi = min(shi, j.dep_segs - 1);
+            if (slo <= shi)
+                ok = wait_segments(w.done + j.dep_done_off, slo, shi, j.dep_units * kConsumerWarps,
+                                   w.spin_limit, w.err);
+            // what other CTAs wrote through the generic proxy is read next by bulk copies
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+        }
+        bool fine;
+        if (!ok) {
+            fine = pr.emit(j, ux, uy, kModeSkip);
+        } else if (j.kind == kJobCipher) {
+            fine = pr.emit(j, ux, uy, kModeCipher);
+        } else {
+            const uint32_t mode = unit_mode<FWD>(j, (int)ux, (int)uy);
+            if (mode == kModeGeneral)
+                fine = pr.emit(j, ux, uy, kModeGeneral);
+            else
+                fine = FWD ? produce_fwd(pr, j, (int)ux, (int)uy, mode)
+                           : produce_inv(pr, j, (int)ux, (int)uy, mode);
+        }
+        if (!fine) { // a stage wait ran out: stop issuing, let the copies land
+            pr.drain();
+            return;
+        }
+        t = nt;
+        if (t < w.total_units)
+            unit_at(w, t, ji, ux, uy);
+    }
+    pr.finish();
+}
+
+// ---------------------------------------------------------------------------
+// consumers
+// ---------------------------------------------------------------------------
+template <bool FWD>
+__device__ bool run_bulk(const LevelJob &j, uint32_t mode, int tx, int sy, int w, int lane,
+                         Ring ring, uint32_t &it, const uint8_t *st0)
+{
+    const bool border = mode == kModeBulkEdge;
+    if (FWD)
+        return j.src_bytes ? strm::fwd_bulk<true>(j, tx, sy, w, lane, border, ring, it, st0)
+                           : strm::fwd_bulk<false>(j, tx, sy, w, lane, border, ring, it, st0);
+    return j.out_bytes ? strm::inv_bulk<true>(j, tx, sy, w, lane, border, ring, it, st0)
+                       : strm::inv_bulk<false>(j, tx, sy, w, lane, border, ring, it, st0);
+}
+
+template <bool FWD>
+__device__ void run_general(const LevelJob &j, int tx, int sy, int w, int lane)
+{
+    const int sx = kConsumerWarps * tx + w;
+    if (sx >= (int)j.wstrips)
+        return;
+    if (FWD) {
+        if (j.src_bytes)
+            strm::fwd_general<true>(j, sx, sy, lane);
+        else
+            strm::fwd_general<false>(j, sx, sy, lane);
+    } else {
+        if (j.out_bytes)
+            strm::inv_general<true>(j, sx, sy, lane);
+        else
+            strm::inv_general<false>(j, sx, sy, lane);
+    }
+}
+
+template <bool FWD>
+__device__ void consumer_loop(const DagWork &w, Ring ring, const AesTab &aes, int warp,
+                              int lane)
+{
+    uint32_t it = 0;
+    for (;;) {
+        const uint8_t *st = ring_wait(ring, it);
+        if (st == nullptr)
+            return;
+        const StageHdr &h = ring.hdr[it % kStages];
+        const uint32_t mode = h.mode;
+        if (mode == kModeEnd)
+            return;
+        // copied out before the stage is released
+        const LevelJob j = h.job;
+        const int tx = (int)h.x, sy = (int)h.y;
+        if (mode == kModeBulk || mode == kModeBulkEdge) {
+            if (!run_bulk<FWD>(j, mode, tx, sy, warp, lane, ring, it, st))
+                return;
+        } else {
+            ring_release(ring, it++);
+            if (mode == kModeCipher) {
+                if (FWD)
+                    strm::cipher_warp(j, tx, sy, warp, aes, lane, j.ll, j.ll, true); // in place
+                else
+                    strm::cipher_warp(j, tx, sy, warp, aes, lane, j.ll_in, j.out, false);
+            } else if (mode == kModeGeneral) {
+                run_general<FWD>(j, tx, sy, warp, lane);
+            } // kModeSkip: nothing
+        }
+        // publish: each consumer warp counts itself once its stores are
+        // visible (a segment is complete at strips x kConsumerWarps); jobs
+        // that nothing in the launch reads skip it
         if (j.publish) {
             __threadfence();
             __syncwarp();
@@ -1045,19 +1434,74 @@ __global__ void __launch_bounds__(kStreamThreads, FRAG_BLOCKS_PER_SM) dag_kernel
     }
 }
 
+// ---------------------------------------------------------------------------
+// kernel: persistent CTAs over a dependency-ordered queue of units
+// ---------------------------------------------------------------------------
+// dynamic shared memory: the stages, then AES tables, barriers, headers
+constexpr size_t kSmemData = (size_t)kStages * kStageBytes;
+constexpr size_t kSmemAes = kSmemData;
+constexpr size_t kSmemBars = kSmemAes + (sizeof(AesTab) + 15) / 16 * 16;
+constexpr size_t kSmemHdr = kSmemBars + 16 * (size_t)kStages;
+constexpr size_t kSmemBytes = kSmemHdr + sizeof(StageHdr) * (size_t)kStages;
+
+template <bool FWD>
+__global__ void __launch_bounds__(kCtaThreads, FRAG_CTAS_PER_SM) dag_kernel(DagWork w)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint8_t *data = smem;
+    AesTab &aes = *reinterpret_cast<AesTab *>(smem + kSmemAes);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kSmemBars);
+    uint64_t *empty = full + kStages;
+    StageHdr *hdr = reinterpret_cast<StageHdr *>(smem + kSmemHdr);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < kAesWords; i += blockDim.x)
+        (&aes.T[0][0])[i] = w.aes_tables[i];
+    for (int i = threadIdx.x; i < 44; i += blockDim.x)
+        aes.rk[i] = w.round_keys[i];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(full + s)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(empty + s)),
+                         "n"(kConsumerWarps)
+                         : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const Ring ring{data, full, empty, hdr, w.err};
+    if (warp == kConsumerWarps) {
+        if (lane == 0)
+            producer_loop<FWD>(w, ring);
+    } else {
+        consumer_loop<FWD>(w, ring, aes, warp, lane);
+    }
+}
+
+static cudaError_t dag_attr(const void *fn)
+{
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+}
+
 cudaError_t launch_dag(bool fwd, const DagWork &w, uint32_t grid, cudaStream_t stream)
 {
+    const void *fn = fwd ? (const void *)dag_kernel<true> : (const void *)dag_kernel<false>;
+    cudaError_t e = dag_attr(fn);
+    if (e != cudaSuccess)
+        return e;
     if (fwd)
-        dag_kernel<true><<<grid, kStreamThreads, 0, stream>>>(w);
+        dag_kernel<true><<<grid, kCtaThreads, kSmemBytes, stream>>>(w);
     else
-        dag_kernel<false><<<grid, kStreamThreads, 0, stream>>>(w);
+        dag_kernel<false><<<grid, kCtaThreads, kSmemBytes, stream>>>(w);
     return cudaGetLastError();
 }
 
 cudaError_t dag_occupancy(bool fwd, int *blocks_per_sm)
 {
     const void *fn = fwd ? (const void *)dag_kernel<true> : (const void *)dag_kernel<false>;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kStreamThreads, 0);
+    cudaError_t e = dag_attr(fn);
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kCtaThreads, kSmemBytes);
 }
 
 // A lone wait on a counter nothing increments: lets a test check that a wait
