@@ -122,8 +122,7 @@ constexpr uint32_t kStageSpin = 1u << 23;              // tests of a stage barri
 
 // stage kinds
 constexpr uint32_t kModeEnd = 0;      // no more units
-constexpr uint32_t kModeBulk = 1;     // rows streamed into the ring, away from column borders
-constexpr uint32_t kModeBulkEdge = 2; // rows streamed into the ring, tile touches a border
+constexpr uint32_t kModeBulk = 1;     // rows streamed into the ring
 constexpr uint32_t kModeGeneral = 3;  // consumers load their own strips (bounds checked)
 constexpr uint32_t kModeCipher = 4;   // AES-CTR blocks
 constexpr uint32_t kModeSkip = 5;     // a dependency wait ran out: report complete, do nothing
@@ -164,10 +163,11 @@ __device__ __forceinline__ void lift_row(const Raw &raw, int c, int Ws, bool edg
 {
     uint32_t e01, o01, e23, o23;
     if (BYTES) {
-        e01 = __byte_perm(raw.w[0], 0, 0x4240) + kB2;
-        o01 = __byte_perm(raw.w[0], 0, 0x4341) + kB2;
-        e23 = __byte_perm(raw.w[1], 0, 0x4240) + kB2;
-        o23 = __byte_perm(raw.w[1], 0, 0x4341) + kB2;
+        // bytes into 16-bit halves with 0x40 as the high byte: v + 0x4000
+        e01 = __byte_perm(raw.w[0], 0x40404040u, 0x4240);
+        o01 = __byte_perm(raw.w[0], 0x40404040u, 0x4341);
+        e23 = __byte_perm(raw.w[1], 0x40404040u, 0x4240);
+        o23 = __byte_perm(raw.w[1], 0x40404040u, 0x4341);
     } else {
         e01 = __byte_perm(raw.w[0], raw.w[1], 0x5410);
         o01 = __byte_perm(raw.w[0], raw.w[1], 0x7632);
@@ -732,8 +732,8 @@ __device__ __forceinline__ void ring_release(Ring r, uint32_t it)
 // ---------------------------------------------------------------------------
 namespace strm {
 
-// The stages of one unit, read row by row: a warp holds one stage at a time and
-// releases it when its rows are used up.
+// The stages of one unit, read in order: a warp holds one stage at a time and
+// releases it when it moves on.
 struct Cursor {
     Ring ring;
     uint32_t base;     // ring index of the unit's first stage
@@ -745,19 +745,13 @@ struct Cursor {
     {
     }
 
-    // slot of unit row t (rps rows of `slot` bytes per stage); nullptr if a
-    // stage wait ran out
-    __device__ __forceinline__ const uint8_t *row(int t, int rps, int slot)
+    // move to the next stage; false if the wait ran out
+    __device__ __forceinline__ bool next()
     {
-        const int k = t / rps;
-        if (k != cur) {
-            ring_release(ring, base + cur);
-            cur = k;
-            st = ring_wait(ring, base + k);
-            if (st == nullptr)
-                return nullptr;
-        }
-        return st + (t - k * rps) * slot;
+        ring_release(ring, base + cur);
+        ++cur;
+        st = ring_wait(ring, base + cur);
+        return st != nullptr;
     }
 
     __device__ __forceinline__ void finish(uint32_t &it, int nstages)
@@ -781,7 +775,7 @@ __device__ __forceinline__ bool skip_stages(Ring ring, uint32_t &it, int nstages
 }
 
 // samples of the lane from a row slot: the slot holds columns [C0 - 16, ...)
-// of the row; the lane's columns start `off` samples into the slot
+// of the row; the lane's columns start `off` bytes into the slot
 template <bool BYTES>
 __device__ __forceinline__ Raw slot_row(const uint8_t *slot, int off)
 {
@@ -792,7 +786,7 @@ __device__ __forceinline__ Raw slot_row(const uint8_t *slot, int off)
         r.w[1] = t.y;
         r.w[2] = r.w[3] = 0;
     } else {
-        const uint4 t = *reinterpret_cast<const uint4 *>(slot + 2 * off);
+        const uint4 t = *reinterpret_cast<const uint4 *>(slot + off);
         r.w[0] = t.x;
         r.w[1] = t.y;
         r.w[2] = t.z;
@@ -807,45 +801,40 @@ __host__ __device__ constexpr int fwd_slot_bytes()
     return BYTES ? 1024 : 2048;
 }
 
-// Forward bulk unit.  Unit rows t = 0 .. 2 n + 2 are image rows 2 q0 - 2 + t
-// (rows outside the image are not copied and not used), packed into stages
-// of kStageBytes / slot rows; stage 0 (already waited for) is at `it`.
-// border: the tile touches a column border (symmetric extension, checked
-// stores).  Returns false if a stage wait ran out.
+// Forward bulk unit.  Row slot u = 1 .. 2 n + 3 of the unit holds image row
+// 2 q0 - 3 + u (slot 0 stays empty so that every row pair 2q+1, 2q+2 sits in
+// one stage; rows outside the image are not copied and not used), rps slots
+// per stage; stage 0 (already waited for) is at `it`.  Stores are checked
+// and the symmetric extension applies where a strip reaches a border (one
+// code path for every tile keeps the kernel small enough for the instruction
+// cache).  Returns false if a stage wait ran out.
 template <bool BYTES>
-__device__ bool fwd_bulk(const LevelJob &j, int tx, int sy, int w, int lane, bool border,
-                         Ring ring, uint32_t &it, const uint8_t *st0)
+__device__ bool fwd_bulk(const LevelJob &j, int tx, int sy, int w, int lane, Ring ring,
+                         uint32_t &it, const uint8_t *st0)
 {
     constexpr int slot = fwd_slot_bytes<BYTES>(), rps = kStageBytes / slot;
     const int Ws = (int)j.Ws, Hs = (int)j.Hs;
     const int sx = kConsumerWarps * tx + w;
     const int c = kStripCols * sx - 8 + 8 * lane;
-    const int off = kStripCols * w + 8 + 8 * lane; // slot column of c
+    const int off = (kStripCols * w + 8 + 8 * lane) * (BYTES ? 1 : 2); // byte offset of c in a slot
     const int q0 = sy * (int)j.seg_pairs;
     const int q1 = min(q0 + (int)j.seg_pairs, Hs / 2);
     const int n_it = q1 - q0;
-    const int nstages = (2 * n_it + 3 + rps - 1) / rps;
+    const int nstages = (2 * n_it + 4 + rps - 1) / rps;
     if (sx >= (int)j.wstrips)
         return skip_stages(ring, it, nstages);
     const int Wl = Ws / 2;
     const int x = c / 2;
-    const bool edge = border && (kStripCols * sx + 248 >= Ws);
+    const bool edge = (kStripCols * sx + 248 >= Ws);
     const bool own = lane >= 1 && lane <= 30 && x < Wl;
     const int nval = min(4, Wl - x);
-    const bool top = q0 == 0, bottom = 2 * q1 >= Hs, final_level = j.final_level;
+    const bool top = q0 == 0, bottom = 2 * q1 >= Hs;
     Cursor cu(ring, it, st0);
     uint32_t e0[4], dp[4];
     {
-        const uint8_t *p;
-        if ((p = cu.row(0, rps, slot)) == nullptr)
-            return false;
-        const Raw rm2 = slot_row<BYTES>(p, off);
-        if ((p = cu.row(1, rps, slot)) == nullptr)
-            return false;
-        const Raw rm1 = slot_row<BYTES>(p, off);
-        if ((p = cu.row(2, rps, slot)) == nullptr)
-            return false;
-        const Raw r0 = slot_row<BYTES>(p, off);
+        const Raw rm2 = slot_row<BYTES>(cu.st + 1 * slot, off);
+        const Raw rm1 = slot_row<BYTES>(cu.st + 2 * slot, off);
+        const Raw r0 = slot_row<BYTES>(cu.st + 3 * slot, off);
         uint32_t a[4], o[4];
         lift_row<BYTES, true>(r0, c, Ws, edge, e0);
         lift_row<BYTES, true>(rm2, c, Ws, edge, a);
@@ -854,18 +843,18 @@ __device__ bool fwd_bulk(const LevelJob &j, int tx, int sy, int w, int lane, boo
         for (int i = 0; i < 4; ++i)
             dp[i] = o[i] - pavg(a[i], e0[i]) + kB2; // (replaced at the top border)
     }
-    const uint64_t ostep = 2ull * (uint64_t)Wl;
-    const uint64_t o0 = 2ull * ((uint64_t)q0 * (uint64_t)Wl + (uint64_t)x);
-    uint8_t *phl = j.hl + o0, *plh = j.lh + o0, *phh = j.hh + o0, *pll = j.ll + o0;
+    const uint8_t *p = cu.st + 4 * slot + off; // the lane's samples of row 2 q0 + 1
+    int left = rps - 4;                        // slots of the held stage still to read
     for (int q = q0; q < q1; ++q) {
-        const int t = 3 + 2 * (q - q0);
-        const uint8_t *p;
-        if ((p = cu.row(t, rps, slot)) == nullptr)
-            return false;
-        const Raw c1 = slot_row<BYTES>(p, off);
-        if ((p = cu.row(t + 1, rps, slot)) == nullptr)
-            return false;
-        const Raw c2 = slot_row<BYTES>(p, off);
+        if (left == 0) {
+            if (!cu.next())
+                return false;
+            p = cu.st + off;
+            left = rps;
+        }
+        const Raw c1 = slot_row<BYTES>(p, 0), c2 = slot_row<BYTES>(p + slot, 0);
+        p += 2 * slot;
+        left -= 2;
         uint32_t o[4], e1[4], sv[4], dv[4];
         lift_row<BYTES, true>(c1, c, Ws, edge, o);
         if (bottom && 2 * q + 2 == Hs) { // x[m] = x[m-2] at the bottom border
@@ -876,19 +865,8 @@ __device__ bool fwd_bulk(const LevelJob &j, int tx, int sy, int w, int lane, boo
             lift_row<BYTES, true>(c2, c, Ws, edge, e1);
         }
         col_step(o, e1, e0, dp, top && q == 0, sv, dv);
-        if (border) {
-            if (own)
-                fwd_store(j, Wl, q, x, nval, sv, dv);
-        } else if (own) {
-            *reinterpret_cast<uint2 *>(phl) = make_uint2(to_i16x2(sv[2]), to_i16x2(sv[3]));
-            *reinterpret_cast<uint2 *>(plh) = make_uint2(to_i16x2(dv[0]), to_i16x2(dv[1]));
-            *reinterpret_cast<uint2 *>(phh) = make_uint2(to_i16x2(dv[2]), to_i16x2(dv[3]));
-            *reinterpret_cast<uint2 *>(pll) = ll_out(final_level, sv);
-        }
-        phl += ostep;
-        plh += ostep;
-        phh += ostep;
-        pll += ostep;
+        if (own)
+            fwd_store(j, Wl, q, x, nval, sv, dv);
     }
     cu.finish(it, nstages);
     return true;
@@ -916,13 +894,12 @@ __device__ __forceinline__ Coef slot_coef(const uint8_t *st, int off, bool top)
 
 // Inverse bulk unit.  Unit rows t = 0 .. n + 1 are coefficient rows k0 - 1 + t
 // (rows outside the bands are not copied and not used), kStageBytes /
-// kCoefRow per stage; stage 0 (already waited for) is at `it`.  border: the
-// tile touches a column border or its rows run past the end of the output
-// bytes (symmetric extension, checked stores).  Returns false if a stage
-// wait ran out.
+// kCoefRow per stage; stage 0 (already waited for) is at `it`.  Stores are
+// checked and the symmetric extension applies where a strip reaches a
+// border.  Returns false if a stage wait ran out.
 template <bool BYTES_OUT>
-__device__ bool inv_bulk(const LevelJob &j, int tx, int sy, int w, int lane, bool border,
-                         Ring ring, uint32_t &it, const uint8_t *st0)
+__device__ bool inv_bulk(const LevelJob &j, int tx, int sy, int w, int lane, Ring ring,
+                         uint32_t &it, const uint8_t *st0)
 {
     constexpr int rps = kStageBytes / kCoefRow;
     const int Ws = (int)j.Ws, Hs = (int)j.Hs;
@@ -935,48 +912,35 @@ __device__ bool inv_bulk(const LevelJob &j, int tx, int sy, int w, int lane, boo
     const int nstages = (n_it + 2 + rps - 1) / rps;
     if (sx >= (int)j.wstrips)
         return skip_stages(ring, it, nstages);
-    const bool edge = border && (kStripCols * sx + 248 >= Ws);
+    const bool edge = (kStripCols * sx + 248 >= Ws);
     const bool own = lane >= 1 && lane <= 30 && c < Ws;
     const int nv = min(8, Ws - c);
     const bool bottom = 2 * k1 >= Hs, top_level = j.top_level;
     Cursor cu(ring, it, st0);
     uint32_t xe[4], d0[4];
     {
-        const uint8_t *p;
-        if ((p = cu.row(0, rps, kCoefRow)) == nullptr)
-            return false;
-        const Coef prev = slot_coef(p, off, top_level);
-        if ((p = cu.row(1, rps, kCoefRow)) == nullptr)
-            return false;
-        const Coef cur = slot_coef(p, off, top_level);
+        const Coef prev = slot_coef(cu.st + off, 0, top_level);
+        const Coef cur = slot_coef(cu.st + kCoefRow + off, 0, top_level);
         col_unstart(prev, cur, k0 == 0, xe, d0);
     }
-    const uint64_t rstep = BYTES_OUT ? (uint64_t)Ws : 2ull * (uint64_t)Ws; // bytes per output row
-    uint8_t *po = j.out + (uint64_t)(2 * k0) * rstep + (BYTES_OUT ? c : 2 * c);
+    const uint8_t *p = cu.st + 2 * kCoefRow + off;
+    int left = rps - 2;
     for (int k = k0; k < k1; ++k) {
-        const uint8_t *p;
-        if ((p = cu.row(2 + (k - k0), rps, kCoefRow)) == nullptr)
-            return false;
-        const Coef c1 = slot_coef(p, off, top_level);
+        if (left == 0) {
+            if (!cu.next())
+                return false;
+            p = cu.st + off;
+            left = rps;
+        }
+        const Coef c1 = slot_coef(p, 0, top_level);
+        p += kCoefRow;
+        --left;
         uint32_t ev[4], xo[4], ve[4], vo[4];
         col_unstep(c1, bottom && 2 * k + 2 == Hs, xe, d0, ev, xo);
         unlift_row<true>(ev, c, Ws, edge, ve);
         unlift_row<true>(xo, c, Ws, edge, vo);
-        if (border) {
-            store_row<BYTES_OUT>(j, 2 * k, c, own, nv, ve);
-            store_row<BYTES_OUT>(j, 2 * k + 1, c, own, nv, vo);
-        } else if (own) {
-            if (BYTES_OUT) {
-                *reinterpret_cast<uint2 *>(po) = make_uint2(__byte_perm(ve[0], ve[1], 0x6420),
-                                                            __byte_perm(ve[2], ve[3], 0x6420));
-                *reinterpret_cast<uint2 *>(po + rstep) = make_uint2(__byte_perm(vo[0], vo[1], 0x6420),
-                                                                    __byte_perm(vo[2], vo[3], 0x6420));
-            } else {
-                *reinterpret_cast<uint4 *>(po) = make_uint4(ve[0], ve[1], ve[2], ve[3]);
-                *reinterpret_cast<uint4 *>(po + rstep) = make_uint4(vo[0], vo[1], vo[2], vo[3]);
-            }
-        }
-        po += 2 * rstep;
+        store_row<BYTES_OUT>(j, 2 * k, c, own, nv, ve);
+        store_row<BYTES_OUT>(j, 2 * k + 1, c, own, nv, vo);
     }
     cu.finish(it, nstages);
     return true;
@@ -1177,9 +1141,9 @@ struct Producer {
     }
 };
 
-// Forward bulk stages of unit (j, tx, sy): unit rows t = 0 .. 2 n + 2 are
-// image rows 2 q0 - 2 + t, each copied as columns [C0 - 16, C0 + 976) clipped
-// to the image (element size 1 for bytes, 2 for packed pairs) into a row slot.
+// Forward bulk stages of unit (j, tx, sy): row slot u = 1 .. 2 n + 3 holds
+// image row 2 q0 - 3 + u, copied as columns [C0 - 16, C0 + 976) clipped to the
+// image (element size 1 for bytes, 2 for packed pairs).
 __device__ bool produce_fwd(Producer &pr, const LevelJob &j, int tx, int sy, uint32_t mode)
 {
     const int Ws = (int)j.Ws, Hs = (int)j.Hs;
@@ -1193,23 +1157,24 @@ __device__ bool produce_fwd(Producer &pr, const LevelJob &j, int tx, int sy, uin
     const uint32_t dst = (uint32_t)(lo - (C0 - 16)) * esz;
     const int q0 = sy * (int)j.seg_pairs;
     const int q1 = min(q0 + (int)j.seg_pairs, Hs / 2);
-    const int T = 2 * (q1 - q0) + 3, r0 = 2 * q0 - 2;
-    for (int t0 = 0; t0 < T; t0 += rps) {
-        const int t1 = min(t0 + rps, T);
+    // slot u = 1 .. 2 n + 3 holds image row r0 + u (slot 0 stays empty)
+    const int U = 2 * (q1 - q0) + 4, r0 = 2 * q0 - 3;
+    for (int u0 = 0; u0 < U; u0 += rps) {
+        const int u1 = min(u0 + rps, U);
         uint32_t s;
         uint8_t *st = pr.claim(s);
         if (st == nullptr)
             return false;
-        if (t0 == 0)
+        if (u0 == 0)
             pr.header(s, j, (uint32_t)tx, (uint32_t)sy, mode);
         // rows of the image in this stage: [ra, rb)
-        const int ra = max(r0 + t0, 0), rb = min(r0 + t1, Hs);
+        const int ra = max(r0 + max(u0, 1), 0), rb = min(r0 + u1, Hs);
         if (rb <= ra) {
             mbar_arrive(pr.ring.full + s);
         } else {
             mbar_arrive_tx(pr.ring.full + s, (uint32_t)(rb - ra) * bytes);
             for (int r = ra; r < rb; ++r)
-                bulk_copy(st + (r - r0 - t0) * slot + dst, j.src + ((uint64_t)r * Ws + lo) * esz,
+                bulk_copy(st + (r - r0 - u0) * slot + dst, j.src + ((uint64_t)r * Ws + lo) * esz,
                           bytes, pr.ring.full + s);
         }
         ++pr.it;
@@ -1262,21 +1227,17 @@ __device__ bool produce_inv(Producer &pr, const LevelJob &j, int tx, int sy, uin
 // host sets j.bulk when bases and pitches allow it); forward byte sources also
 // need every row read to lie before n.
 template <bool FWD>
-__device__ __forceinline__ uint32_t unit_mode(const LevelJob &j, int tx, int sy)
+__device__ __forceinline__ uint32_t unit_mode(const LevelJob &j, int sy)
 {
     if (!j.bulk)
         return kModeGeneral;
-    const int Ws = (int)j.Ws, Hs = (int)j.Hs;
-    const bool col_edge = tx == 0 || kTileCols * tx + kTileCols + 8 >= Ws;
-    const int p0 = sy * (int)j.seg_pairs;
-    const int p1 = min(p0 + (int)j.seg_pairs, Hs / 2);
-    if (FWD) {
-        if (j.src_bytes && (uint64_t)(min(2 * p1, Hs - 1) + 1) * (uint64_t)Ws > j.n)
+    if (FWD && j.src_bytes) {
+        const int Hs = (int)j.Hs;
+        const int p1 = min(sy * (int)j.seg_pairs + (int)j.seg_pairs, Hs / 2);
+        if ((uint64_t)(min(2 * p1, Hs - 1) + 1) * (uint64_t)j.Ws > j.n)
             return kModeGeneral;
-        return col_edge ? kModeBulkEdge : kModeBulk;
     }
-    const bool tail = j.out_bytes && (uint64_t)(2 * p1) * (uint64_t)Ws > j.n;
-    return (col_edge || tail) ? kModeBulkEdge : kModeBulk;
+    return kModeBulk;
 }
 
 // unit t of the launch: (job, x, y)
@@ -1340,7 +1301,7 @@ __device__ void producer_loop(const DagWork &w, Ring ring)
         } else if (j.kind == kJobCipher) {
             fine = pr.emit(j, ux, uy, kModeCipher);
         } else {
-            const uint32_t mode = unit_mode<FWD>(j, (int)ux, (int)uy);
+            const uint32_t mode = unit_mode<FWD>(j, (int)uy);
             if (mode == kModeGeneral)
                 fine = pr.emit(j, ux, uy, kModeGeneral);
             else
@@ -1362,15 +1323,14 @@ __device__ void producer_loop(const DagWork &w, Ring ring)
 // consumers
 // ---------------------------------------------------------------------------
 template <bool FWD>
-__device__ bool run_bulk(const LevelJob &j, uint32_t mode, int tx, int sy, int w, int lane,
-                         Ring ring, uint32_t &it, const uint8_t *st0)
+__device__ bool run_bulk(const LevelJob &j, int tx, int sy, int w, int lane, Ring ring,
+                         uint32_t &it, const uint8_t *st0)
 {
-    const bool border = mode == kModeBulkEdge;
     if (FWD)
-        return j.src_bytes ? strm::fwd_bulk<true>(j, tx, sy, w, lane, border, ring, it, st0)
-                           : strm::fwd_bulk<false>(j, tx, sy, w, lane, border, ring, it, st0);
-    return j.out_bytes ? strm::inv_bulk<true>(j, tx, sy, w, lane, border, ring, it, st0)
-                       : strm::inv_bulk<false>(j, tx, sy, w, lane, border, ring, it, st0);
+        return j.src_bytes ? strm::fwd_bulk<true>(j, tx, sy, w, lane, ring, it, st0)
+                           : strm::fwd_bulk<false>(j, tx, sy, w, lane, ring, it, st0);
+    return j.out_bytes ? strm::inv_bulk<true>(j, tx, sy, w, lane, ring, it, st0)
+                       : strm::inv_bulk<false>(j, tx, sy, w, lane, ring, it, st0);
 }
 
 template <bool FWD>
@@ -1408,8 +1368,8 @@ __device__ void consumer_loop(const DagWork &w, Ring ring, const AesTab &aes, in
         // copied out before the stage is released
         const LevelJob j = h.job;
         const int tx = (int)h.x, sy = (int)h.y;
-        if (mode == kModeBulk || mode == kModeBulkEdge) {
-            if (!run_bulk<FWD>(j, mode, tx, sy, warp, lane, ring, it, st))
+        if (mode == kModeBulk) {
+            if (!run_bulk<FWD>(j, tx, sy, warp, lane, ring, it, st))
                 return;
         } else {
             ring_release(ring, it++);
