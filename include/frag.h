@@ -214,6 +214,16 @@ frag_status frag_get_error(char *buf, size_t len);
  * descriptor), FRAG_ETIMEOUT (a bounded wait ran out) or FRAG_ECUDA. */
 frag_status frag_sync_status(frag_stream stream);
 
+/* Failure-path self-test (the thesis has no counterpart).  Every wait in the
+ * library's kernels is bounded: a unit that waits for another unit's output,
+ * or for a shared-memory stage, gives up after a fixed number of polls, sets
+ * the device error word and returns, so a launch always ends and the context
+ * stays usable.  This call enqueues on `stream` one such wait on a counter
+ * that nothing increments, bounded at `polls` polls (each poll sleeps at most
+ * about 1 us); the next frag_sync_status on the stream then returns
+ * FRAG_ETIMEOUT.  FRAG_EINVAL if polls is 0. */
+frag_status frag_check_wait_timeout(uint32_t polls, frag_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ EXPORTS = [
     "frag_protect", "frag_recover", "frag_protect_host", "frag_recover_host",
     "frag_protect_batch", "frag_recover_batch", "frag_batch_create_protect",
     "frag_batch_create_recover", "frag_batch_run", "frag_batch_destroy", "frag_batch_info",
-    "frag_get_error",
+    "frag_get_error", "frag_check_wait_timeout",
     "frag_sync_status",
 ]
 
@@ -94,6 +94,7 @@ def lib():
         "frag_batch_info": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u64)], ctypes.c_int),
         "frag_get_error": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
         "frag_sync_status": ([vp], ctypes.c_int),
+        "frag_check_wait_timeout": ([u32, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -297,3 +298,8 @@ class Batch:
 
 def sync_status(stream=None) -> None:
     check(lib().frag_sync_status(_stream(stream)))
+
+
+def check_wait_timeout(polls: int = 2000, stream=None) -> None:
+    """Enqueue one bounded wait that is bound to run out (see frag.h)."""
+    check(lib().frag_check_wait_timeout(polls, _stream(stream)))

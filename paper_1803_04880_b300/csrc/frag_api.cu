@@ -1174,8 +1174,31 @@ frag_status frag_sync_status(frag_stream stream)
         return FRAG_OK;
     cudaMemset(d->err, 0, sizeof(int));
     if (word == 3)
-        return fail(FRAG_ETIMEOUT, "a bounded device wait ran out");
+        return fail(FRAG_ETIMEOUT, "a bounded wait for another unit's output ran out");
+    if (word == 4)
+        return fail(FRAG_ETIMEOUT, "a bounded wait for a shared-memory stage ran out");
     return fail(FRAG_EDEVICE, "kernel reported inconsistent work descriptor (code %d)", word);
+}
+
+frag_status frag_check_wait_timeout(uint32_t polls, frag_stream stream)
+{
+    if (polls == 0)
+        return fail(FRAG_EINVAL, "polls must be positive");
+    DeviceState *d = nullptr;
+    frag_status st = device_state(&d, nullptr);
+    if (st != FRAG_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned *ctr = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&ctr, sizeof(unsigned), s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMallocAsync(counter)");
+    if ((e = cudaMemsetAsync(ctr, 0, sizeof(unsigned), s)) != cudaSuccess)
+        st = cuda_fail(e, "counter reset");
+    else if ((e = frag::launch_stall_probe(ctr, polls, d->err, s)) != cudaSuccess)
+        st = cuda_fail(e, "wait probe launch");
+    cudaFreeAsync(ctr, s);
+    return st;
 }
 
 } // extern "C"

@@ -74,3 +74,5 @@ def test_null_arguments_are_rejected(L):
     assert L.frag_protect(p.handle, None, 0, None, 16, None, None, None) == fr.FRAG_EINVAL
     assert L.frag_recover(None, None, 0, None, None, 16, None, None) == fr.FRAG_EINVAL
     assert L.frag_get_error(None, 0) == fr.FRAG_EINVAL
+    assert L.frag_batch_info(None, None, None) == fr.FRAG_EINVAL
+    assert L.frag_check_wait_timeout(0, None) == fr.FRAG_EINVAL
