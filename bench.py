@@ -39,7 +39,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3l2", "c3l4"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3l2", "c3l4", "c4", "c5"])
+    ap.add_argument("--items", type=int, default=10000, help="c4: number of buffers")
+    ap.add_argument("--requests", type=int, default=240, help="c5: requests per load level")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -374,6 +376,212 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+# -- C4: thousands of uneven buffers, one launch per direction vs one per file ----
+
+def _digest(t):
+    import torch
+    x = t.to(torch.int64)
+    w = torch.arange(1, x.numel() + 1, device=t.device, dtype=torch.int64) % 65521
+    return int(x.sum()), int((x * w).sum())
+
+
+def run_c4(args, rank, world, local_rank):
+    """10,000 buffers, log-uniform 4 KiB .. 64 MiB, width 2^round(log2(n)/2),
+    levels 1..4, nonce = index (about 69 GB of input).  Timed: protect of all
+    of them as one batch object replayed in a CUDA graph, then recover into
+    the input buffers (the fragments alone hold the data meanwhile), against
+    the same work as one frag_protect / frag_recover call per buffer.  Every
+    buffer is checked after each recover by a digest of its regenerated
+    contents; a seeded sample of small buffers against the oracle."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_1803_04880_b300 as fr
+    from paper_1803_04880_b300 import workloads as wl
+
+    fr.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    items = wl.c4_items(count=args.items)
+    key = fr.Key(wl.KEY)
+    plans = {}
+    data, privs, pubs, digests = [], [], [], []
+    for i, (n, W, L, nonce) in enumerate(items):
+        plan = plans.setdefault((W, L), fr.Plan(W, L))
+        _, pb, ub = plan.sizes(n)
+        t = wl.c4_content(i, n, device=dev)
+        data.append(t)
+        privs.append(torch.empty(pb, dtype=torch.uint8, device=dev))
+        pubs.append(torch.empty(ub, dtype=torch.uint8, device=dev))
+    torch.cuda.synchronize()
+    n_total = sum(n for (n, _, _, _) in items)
+    pentries = [(plans[(W, L)], nonce, n, d, p, u)
+                for (n, W, L, nonce), d, p, u in zip(items, data, privs, pubs)]
+    rentries = [(plans[(W, L)], nonce, n, p, u, d)
+                for (n, W, L, nonce), d, p, u in zip(items, data, privs, pubs)]
+    bp = fr.Batch(pentries, protect=True)
+    br = fr.Batch(rentries, protect=False)
+    s = torch.cuda.Stream(device=dev)
+    # graph: protect then recover in place
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        bp.run(key, s)
+        br.run(key, s)
+    # oracle sample: small buffers, checked after one run
+    rng = np.random.default_rng(11)
+    small = [i for i, (n, _, _, _) in enumerate(items) if n <= (1 << 18)]
+    sample = sorted(rng.choice(small, size=min(200, len(small)), replace=False).tolist())
+    g.replay()
+    torch.cuda.synchronize()
+    fr.sync_status(s)
+    bad = 0
+    for i in sample:
+        n, W, L, nonce = items[i]
+        ref = wl.c4_content(i, n, device=dev).cpu().numpy()  # the device generator's bytes
+        p_ref, u_ref = oracle.protect(ref, W, L, wl.KEY, nonce)
+        bad += int(not np.array_equal(privs[i].cpu().numpy(), p_ref))
+        bad += int(not np.array_equal(pubs[i].cpu().numpy(), u_ref))
+        bad += int(not np.array_equal(data[i].cpu().numpy(), ref))
+    assert bad == 0, "c4 oracle sample differs"
+    K, Wm = max(1, min(args.steps, 5)), max(1, min(args.warmup, 3))
+    for _ in range(Wm):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    with torch.cuda.stream(s):
+        for _ in range(K):
+            g.replay()
+    e1.record(s)
+    torch.cuda.synchronize()
+    fr.sync_status(s)
+    batched_ms = e0.elapsed_time(e1) / K
+    # every buffer after the replays: regenerate and compare
+    mism = 0
+    for i, (n, _, _, _) in enumerate(items):
+        mism += int(not torch.equal(data[i], wl.c4_content(i, n, device=dev)))
+    assert mism == 0, "c4 round trip differs on %d buffers" % mism
+    # per-file: one protect and one recover call per buffer
+    torch.cuda.synchronize()
+    e0.record(s)
+    for (plan, nonce, n, d, p, u) in pentries:
+        fr.protect(plan, key, nonce, d, n, p, u, stream=s)
+    for (plan, nonce, n, p, u, d) in rentries:
+        fr.recover(plan, key, nonce, p, u, n, d, stream=s)
+    e1.record(s)
+    torch.cuda.synchronize()
+    fr.sync_status(s)
+    per_file_ms = e0.elapsed_time(e1)
+    launches, held = bp.info()
+    if rank == 0:
+        value = world * n_total / (batched_ms / 1e3) / 1e9
+        line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+                "steps": K, "warmup": Wm, "ms_per_step": round(batched_ms, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic",
+                "config": {"workload": "batched: %d buffers log-uniform 4 KiB..64 MiB, width "
+                                       "2^round(log2(n)/2), levels 1..4" % len(items),
+                           "bytes": n_total, "l2": "inputs larger than L2",
+                           "path": "Batch objects (one launch per wave and direction) in one CUDA graph"},
+                "per_file": {"ms_per_step": round(per_file_ms, 3),
+                             "value": round(n_total / (per_file_ms / 1e3) / 1e9, 2),
+                             "batched_over_per_file": round(per_file_ms / batched_ms, 3)},
+                "gpu_launches": K * (launches + br.info()[0]),
+                "oracle_sample_items": len(sample), "batch_device_bytes": held}
+        print(json.dumps(line), flush=True)
+
+
+# -- C5: served stream of requests -------------------------------------------------
+
+def run_c5(args, rank, world, local_rank):
+    """Poisson stream of protect/recover requests (50/50), sizes log-uniform
+    1 KiB .. 256 MiB, width 4096, 3 levels, through the continuous-batching
+    server.  First the saturated rate (all requests queued at once), then
+    offered loads of 10 / 50 / 90 % of it; per level p50 / p99 latency (submit
+    to completion) and achieved GB/s of request bytes."""
+    import numpy as np
+    import torch
+    import paper_1803_04880_b300 as fr
+    from paper_1803_04880_b300 import workloads as wl
+    from paper_1803_04880_b300.serve import Server
+
+    fr.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    R = args.requests
+    pool = torch.randint(0, 256, (1 << 29,), dtype=torch.uint8, device=dev)  # 512 MiB of bytes
+    reqs = wl.c5_requests(R, 1.0, hi=1 << 28)
+    sizes = [n for (_, _, n) in reqs]
+    mean_size = float(np.mean(sizes))
+    rng = np.random.default_rng(5)
+    offs = [int(rng.integers(0, pool.numel() - n + 1)) for n in sizes]
+    srv = Server(wl.KEY, width=4096, levels=3, device=local_rank)
+    # fragments for the recover requests, made beforehand
+    frags = []
+    for i, (n, o) in enumerate(zip(sizes, offs)):
+        if reqs[i][1] == "recover":
+            r = srv.submit_protect(pool[o:o + n], nonce=i)
+            frags.append(r)
+    for r in frags:
+        r.wait()
+    srv.check()
+    fr_by_index = {r.nonce: r for r in frags}
+
+    def run_level(rate):
+        arr = wl.c5_requests(R, rate, hi=1 << 28) if rate else [(0.0, k, n) for (_, k, n) in reqs]
+        out = []
+        t0 = time.perf_counter()
+        for i, (a, kind, n) in enumerate(arr):
+            while time.perf_counter() - t0 < a:
+                time.sleep(0)
+            o = offs[i]
+            if kind == "protect":
+                out.append(srv.submit_protect(pool[o:o + sizes[i]], nonce=10_000 + i))
+            else:
+                f = fr_by_index.get(i)
+                if f is None:
+                    out.append(srv.submit_protect(pool[o:o + sizes[i]], nonce=10_000 + i))
+                else:
+                    out.append(srv.submit_recover(f.private, f.public, f.nbytes, f.nonce))
+        for r in out:
+            r.wait()
+        t1 = max(r.t_done for r in out)
+        lat = sorted(1e3 * r.latency_s for r in out)
+        nbytes = sum(r.nbytes for r in out)
+        return {"offered_req_per_s": round(rate, 1) if rate else None,
+                "achieved_gbps": round(nbytes / (t1 - t0) / 1e9, 2),
+                "p50_ms": round(lat[len(lat) // 2], 3),
+                "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
+                "requests": len(out)}
+
+    run_level(0)  # warm-up: fills the allocator's cache with output blocks
+    sat = run_level(0)  # everything queued at once: the saturated rate
+    peak_gbps = sat["achieved_gbps"]
+    levels = []
+    for load in (0.1, 0.5, 0.9):
+        rate = load * peak_gbps * 1e9 / mean_size
+        lv = run_level(rate)
+        lv["load"] = load
+        lv["offered_gbps"] = round(load * peak_gbps, 2)
+        levels.append(lv)
+    srv.check()
+    srv.close()
+    if rank == 0:
+        top = levels[-1]
+        line = {"metric": METRIC, "value": top["achieved_gbps"], "unit": UNIT, "n_gpus": world,
+                "steps": len(levels), "warmup": 1, "ms_per_step": None,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic",
+                "config": {"workload": "served: Poisson protect/recover 50/50, log-uniform "
+                                       "1 KiB..256 MiB, width 4096, 3 levels",
+                           "requests_per_level": R, "mean_request_bytes": int(mean_size),
+                           "path": "serve.Server (continuous batching, 2 groups in flight)"},
+                "saturated": sat, "levels": levels, "p50_ms": top["p50_ms"],
+                "p99_ms": top["p99_ms"], "gpu_launches": srv.launches}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -388,7 +596,12 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == "c4":
+            run_c4(args, rank, world, local_rank)
+        elif args.workload == "c5":
+            run_c5(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -132,7 +132,8 @@ def c4_items(count: int = 10000, lo: int = 4096, hi: int = 1 << 26, seed: int = 
 
 
 def c4_content(index: int, n: int, device="cpu", seed: int = 3):
-    """Uniform random bytes of item ``index`` (torch tensor on ``device``)."""
+    """Uniform random bytes of item ``index`` (torch tensor on ``device``; the
+    CPU and CUDA generators give different streams, so compare like with like)."""
     import torch
     g = torch.Generator(device=device)
     g.manual_seed(seed * 1_000_003 + index)
