@@ -89,14 +89,25 @@ frag_status frag_plan_destroy(frag_plan plan);
 frag_status frag_plan_sizes(frag_plan plan, uint64_t nbytes, uint32_t *height,
                             uint64_t *private_bytes, uint64_t *public_bytes);
 
-/* Launch tuning of the tiled kernels for this plan (the autotuner sets it;
- * 0 keeps the default).  tile_w / tile_h: owned tile size in pixels,
+/* Launch tuning of the shared-memory tile kernel that frag_protect_batch_noalloc
+ * runs (0 keeps the default).  tile_w / tile_h: owned tile size in pixels,
  * multiples of 16 and of 2^L, at most 256; ctas_per_sm: resident CTAs per SM
  * of the persistent grid (0 = as many as fit). */
 frag_status frag_plan_set_tiling(frag_plan plan, uint32_t tile_w, uint32_t tile_h,
                                  uint32_t ctas_per_sm);
 frag_status frag_plan_get_tiling(frag_plan plan, uint32_t *tile_w, uint32_t *tile_h,
                                  uint32_t *ctas_per_sm);
+
+/* Schedule of the streaming kernel that every other protect / recover call
+ * runs (the autotuner in the Python package sets it; 0 keeps the library's
+ * choice).  seg_rows: level-0 rows per work unit, a power of two in 16..256
+ * (raised to 2^levels when smaller); ctas: CTAs of the persistent grid at
+ * most (0 = every CTA that fits on the device).  A batch takes each
+ * buffer's seg_rows from that buffer's plan and the grid cap from its first
+ * item's plan.  Results do not depend on the schedule.  FRAG_EINVAL for a
+ * NULL plan or a seg_rows outside that set; get: either pointer may be NULL. */
+frag_status frag_plan_set_schedule(frag_plan plan, uint32_t seg_rows, uint32_t ctas);
+frag_status frag_plan_get_schedule(frag_plan plan, uint32_t *seg_rows, uint32_t *ctas);
 
 /* AES-128 key (Sec. 5.2.1 protects the private fragment with AES-128): the
  * round keys are expanded on the host (FIPS-197 Sec. 5.2) and kept resident on

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "FRAG_OK", 1: "FRAG_EINVAL", 2: "FRAG_EUNSUPPORTED", 3: "FRAG
 # every symbol include/frag.h declares
 EXPORTS = [
     "frag_abi_version", "frag_plan_create", "frag_plan_destroy", "frag_plan_sizes",
-    "frag_plan_set_tiling", "frag_plan_get_tiling", "frag_key_create", "frag_key_destroy",
+    "frag_plan_set_tiling", "frag_plan_get_tiling", "frag_plan_set_schedule",
+    "frag_plan_get_schedule", "frag_key_create", "frag_key_destroy",
     "frag_protect", "frag_recover", "frag_protect_host", "frag_recover_host",
     "frag_protect_batch", "frag_recover_batch", "frag_batch_create_protect",
     "frag_batch_create_recover", "frag_batch_run", "frag_batch_destroy", "frag_batch_info",
@@ -77,6 +78,8 @@ def lib():
         "frag_plan_set_tiling": ([vp, u32, u32, u32], ctypes.c_int),
         "frag_plan_get_tiling": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u32),
                                   ctypes.POINTER(u32)], ctypes.c_int),
+        "frag_plan_set_schedule": ([vp, u32, u32], ctypes.c_int),
+        "frag_plan_get_schedule": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u32)], ctypes.c_int),
         "frag_key_create": ([ctypes.POINTER(vp), ctypes.c_char_p], ctypes.c_int),
         "frag_key_destroy": ([vp], ctypes.c_int),
         "frag_protect": ([vp, vp, u64, vp, u64, vp, vp, vp], ctypes.c_int),
@@ -147,6 +150,15 @@ class Plan:
 
     def set_tiling(self, tile_w: int = 0, tile_h: int = 0, ctas_per_sm: int = 0) -> None:
         check(lib().frag_plan_set_tiling(self._h, tile_w, tile_h, ctas_per_sm))
+
+    def set_schedule(self, seg_rows: int = 0, ctas: int = 0) -> None:
+        """Rows per work unit and grid cap of the streaming kernel (0 = auto)."""
+        check(lib().frag_plan_set_schedule(self._h, seg_rows, ctas))
+
+    def schedule(self) -> Tuple[int, int]:
+        a, b = ctypes.c_uint32(), ctypes.c_uint32()
+        check(lib().frag_plan_get_schedule(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def tiling(self) -> Tuple[int, int, int]:
         a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()

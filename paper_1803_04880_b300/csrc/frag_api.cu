@@ -23,9 +23,11 @@ using frag::Work;
 struct frag_plan_s {
     uint32_t width;
     uint32_t levels;
-    uint32_t tile_w;
+    uint32_t tile_w;      // tile path (allocation-free call)
     uint32_t tile_h;
     uint32_t ctas_per_sm;
+    uint32_t seg_rows;    // streaming path: level-0 rows per unit (0: adaptive)
+    uint32_t max_ctas;    // streaming path: grid cap (0: all resident CTAs)
 };
 
 struct frag_key_s {
@@ -298,7 +300,8 @@ uint64_t scratch_bytes(bool fwd, uint32_t H, uint32_t W, uint32_t L, uint64_t *o
 
 struct Buf {
     uint32_t W, L, H;
-    uint32_t R0; // level-0 rows per work segment
+    uint32_t R0;       // level-0 rows per work segment
+    uint32_t R0_plan;  // the plan's choice (0: adaptive)
     uint64_t n, nonce;
     const uint8_t *in;
     uint8_t *priv, *pub;
@@ -310,9 +313,16 @@ struct Buf {
 // Level-0 rows per work segment, the same at every level: a power of two
 // >= 2^L, so every level has the same number of segments.  64 rows unless the
 // first level would then have fewer than two units per resident CTA; then
-// down to 16 (each segment re-reads three rows above it).
-uint32_t seg_rows0(uint32_t L, uint64_t l1_units_at_64, uint64_t resident_ctas)
+// down to 16 (each segment re-reads three rows above it).  A plan may fix it.
+uint32_t seg_rows0(uint32_t L, uint64_t l1_units_at_64, uint64_t resident_ctas,
+                   uint32_t plan_rows = 0)
 {
+    if (plan_rows) {
+        uint32_t r = plan_rows;
+        while (r < (1u << L))
+            r <<= 1;
+        return r;
+    }
     uint32_t r = 64;
     uint64_t u = l1_units_at_64;
     while (r > 16 && u < 2 * resident_ctas) {
@@ -487,7 +497,6 @@ frag_status dag_grid(DeviceState &d, bool fwd, uint64_t units, uint32_t *grid)
 
 frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream_t s)
 {
-    (void)plan;
     DeviceState *d = nullptr;
     int dev = 0;
     frag_status st = device_state(&d, &dev);
@@ -505,7 +514,9 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     uint32_t grid = 0;
     if ((st = dag_grid(*d, fwd, ~0ull, &grid)) != FRAG_OK)
         return st;
-    b.R0 = seg_rows0(b.L, l1_units_at_64(b), grid);
+    if (plan->max_ctas)
+        grid = std::min(grid, plan->max_ctas);
+    b.R0 = seg_rows0(b.L, l1_units_at_64(b), grid, plan->seg_rows);
     const uint32_t NS = (b.H + b.R0 - 1) / b.R0;
     const uint64_t cb = align256(4ull * NS * njobs);
     uint8_t *mem = nullptr;
@@ -558,6 +569,7 @@ struct DagWave {
 struct BatchPlan {
     bool fwd = true;
     uint64_t resident_ctas = 0; // CTAs one launch keeps resident
+    uint32_t max_ctas = 0;      // grid cap from the first item's plan (0: none)
     std::vector<Buf> bufs;
     std::vector<uint64_t> scr_off;
     std::vector<uint32_t> wave_of;
@@ -582,6 +594,9 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
         std::memset(&b, 0, sizeof(b));
         b.W = plan->width;
         b.L = plan->levels;
+        b.R0_plan = plan->seg_rows;
+        if (bp.max_ctas == 0)
+            bp.max_ctas = plan->max_ctas; // the grid of a launch: the first item's plan
         const uint64_t H = rows_for(n, b.W, b.L);
         if (H > 0xFFFFFFFFull)
             return fail(FRAG_EINVAL, "item %u is too tall for width %u", i, b.W);
@@ -644,7 +659,7 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
     for (size_t i = 0; i < bp.bufs.size(); ++i) {
         Buf &b = bp.bufs[i];
         uint64_t off[frag::kMaxInlineJobs + 1] = {0};
-        b.R0 = seg_rows0(b.L, u64, bp.resident_ctas);
+        b.R0 = seg_rows0(b.L, u64, bp.resident_ctas, b.R0_plan);
         scratch_bytes(bp.fwd, b.H, b.W, b.L, off);
         for (uint32_t l = 1; l < (bp.fwd ? b.L : b.L + 1); ++l)
             b.scr[l] = scratch_base + bp.scr_off[i] + off[l];
@@ -709,6 +724,8 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
         w.spin_limit = kSpinLimit;
         uint32_t grid = 0;
         frag_status st = dag_grid(d, bp.fwd, w.total_units, &grid);
+        if (bp.max_ctas)
+            grid = std::min(grid, bp.max_ctas);
         if (st != FRAG_OK)
             return st;
         if ((e = frag::launch_dag(bp.fwd, w, grid, s)) != cudaSuccess)
@@ -740,7 +757,7 @@ frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, 
     uint32_t grid = 0;
     if ((st = dag_grid(*d, fwd, ~0ull, &grid)) != FRAG_OK)
         return st;
-    bp.resident_ctas = grid;
+    bp.resident_ctas = bp.max_ctas ? std::min(grid, bp.max_ctas) : grid;
     BatchPlan sizing = bp; // the layout does not depend on the scratch base
     fill_batch(sizing, nullptr);
     uint8_t *mem = nullptr;
@@ -782,7 +799,7 @@ frag_status create_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, ui
         st = device_state(&d, &bt->device);
     uint32_t grid = 0;
     if (st == FRAG_OK && (st = dag_grid(*d, fwd, ~0ull, &grid)) == FRAG_OK)
-        bt->bp.resident_ctas = grid;
+        bt->bp.resident_ctas = bt->bp.max_ctas ? std::min(grid, bt->bp.max_ctas) : grid;
     if (st == FRAG_OK && !bt->bp.bufs.empty()) {
         BatchPlan sizing = bt->bp;
         fill_batch(sizing, nullptr);
@@ -919,6 +936,30 @@ frag_status frag_plan_get_tiling(frag_plan plan, uint32_t *tile_w, uint32_t *til
         *tile_h = plan->tile_h;
     if (ctas_per_sm)
         *ctas_per_sm = plan->ctas_per_sm;
+    return FRAG_OK;
+}
+
+frag_status frag_plan_set_schedule(frag_plan plan, uint32_t seg_rows, uint32_t ctas)
+{
+    frag_status st = check_plan(plan);
+    if (st != FRAG_OK)
+        return st;
+    if (seg_rows && (seg_rows < 16 || seg_rows > 256 || (seg_rows & (seg_rows - 1))))
+        return fail(FRAG_EINVAL, "seg_rows %u must be 0 or a power of two in 16..256", seg_rows);
+    plan->seg_rows = seg_rows;
+    plan->max_ctas = ctas;
+    return FRAG_OK;
+}
+
+frag_status frag_plan_get_schedule(frag_plan plan, uint32_t *seg_rows, uint32_t *ctas)
+{
+    frag_status st = check_plan(plan);
+    if (st != FRAG_OK)
+        return st;
+    if (seg_rows)
+        *seg_rows = plan->seg_rows;
+    if (ctas)
+        *ctas = plan->max_ctas;
     return FRAG_OK;
 }
 

@@ -1,0 +1,51 @@
+"""Schedule knobs and the autotuner's cache logic (no GPU needed)."""
+import pytest
+
+import paper_1803_04880_b300 as fr
+from paper_1803_04880_b300 import tune
+
+
+@pytest.fixture(scope="module")
+def L():
+    fr.build()
+    return fr.lib()
+
+
+def test_schedule_validation(L):
+    p = fr.Plan(4096, 3)
+    assert p.schedule() == (0, 0)
+    p.set_schedule(32, 300)
+    assert p.schedule() == (32, 300)
+    for bad in (8, 24, 512, 1000):
+        with pytest.raises(fr.FragError):
+            p.set_schedule(bad, 0)
+    assert p.schedule() == (32, 300)
+    p.set_schedule(0, 0)
+    assert p.schedule() == (0, 0)
+    assert L.frag_plan_set_schedule(None, 0, 0) == fr.FRAG_EINVAL
+
+
+def test_size_class():
+    assert tune.size_class(1) == 0
+    assert tune.size_class(1 << 20) == 20
+    assert tune.size_class(3 << 20) == 22  # rounds log2 to the nearest integer
+    assert tune.size_class(0) == 0
+
+
+def test_cache_round_trip_and_apply(tmp_path, L):
+    path = str(tmp_path / "sched.json")
+    assert tune.load_cache(path) == {}
+    key = tune._key("B300-test", 4096, 3, 1 << 24)
+    tune.save_cache({key: {"seg_rows": 64, "ctas": 296, "us": 1.0, "timings": {}}}, path)
+    p = fr.Plan(4096, 3)
+    assert tune.apply(p, 1 << 24, path=path, device_name="B300-test")
+    assert p.schedule() == (64, 296)
+    # a size in another bucket falls back to the library's choice
+    assert not tune.apply(p, 1 << 12, path=path, device_name="B300-test")
+    assert p.schedule() == (0, 0)
+
+
+def test_candidates_cover_rows_and_grids():
+    c = list(tune.candidates(148))
+    assert {r for r, _ in c} == set(tune.CANDIDATE_ROWS)
+    assert {g for _, g in c} == {0, 148, 296}
