@@ -801,13 +801,36 @@ __host__ __device__ constexpr int fwd_slot_bytes()
     return BYTES ? 1024 : 2048;
 }
 
+// The symmetric extension at the column borders, written into a row slot
+// before it is read: x[-k] = x[k] for k = 1..8 (the halo lane's samples: the
+// lifting needs x[-2], x[-1] for d[-1] = d[0], and every packed half must
+// hold an in-range value so that no carry crosses into its neighbour) and
+// x[Ws] = x[Ws - 2].  The slot holds columns [C0 - 16, ...); the copy leaves
+// those positions unwritten, and only the border warp's own lanes use them.
+template <bool BYTES>
+__device__ __forceinline__ void mirror_slot(uint8_t *slot, bool left, int right_col)
+{
+    constexpr int e = BYTES ? 1 : 2; // bytes per sample
+#pragma unroll
+    for (int b = 0; b < e; ++b) {
+        if (left) {
+#pragma unroll
+            for (int k = 1; k <= 8; ++k)
+                slot[(16 - k) * e + b] = slot[(16 + k) * e + b];
+        }
+        if (right_col >= 0)
+            slot[(right_col + 16) * e + b] = slot[(right_col + 14) * e + b];
+    }
+}
+
 // Forward bulk unit.  Row slot u = 1 .. 2 n + 3 of the unit holds image row
 // 2 q0 - 3 + u (slot 0 stays empty so that every row pair 2q+1, 2q+2 sits in
 // one stage; rows outside the image are not copied and not used), rps slots
-// per stage; stage 0 (already waited for) is at `it`.  Stores are checked
-// and the symmetric extension applies where a strip reaches a border (one
-// code path for every tile keeps the kernel small enough for the instruction
-// cache).  Returns false if a stage wait ran out.
+// per stage; stage 0 (already waited for) is at `it`.  The warps that hold
+// a column border mirror the samples beyond it into the slot first, so every
+// row lifts with the interior formula; bulk units have whole aligned rows, so
+// the outputs leave as plain vector stores.  Returns false if a stage wait
+// ran out.
 template <bool BYTES>
 __device__ bool fwd_bulk(const LevelJob &j, int tx, int sy, int w, int lane, Ring ring,
                          uint32_t &it, const uint8_t *st0)
@@ -815,6 +838,7 @@ __device__ bool fwd_bulk(const LevelJob &j, int tx, int sy, int w, int lane, Rin
     constexpr int slot = fwd_slot_bytes<BYTES>(), rps = kStageBytes / slot;
     const int Ws = (int)j.Ws, Hs = (int)j.Hs;
     const int sx = kConsumerWarps * tx + w;
+    const int C0 = kTileCols * tx;
     const int c = kStripCols * sx - 8 + 8 * lane;
     const int off = (kStripCols * w + 8 + 8 * lane) * (BYTES ? 1 : 2); // byte offset of c in a slot
     const int q0 = sy * (int)j.seg_pairs;
@@ -825,48 +849,71 @@ __device__ bool fwd_bulk(const LevelJob &j, int tx, int sy, int w, int lane, Rin
         return skip_stages(ring, it, nstages);
     const int Wl = Ws / 2;
     const int x = c / 2;
-    const bool edge = (kStripCols * sx + 248 >= Ws);
     const bool own = lane >= 1 && lane <= 30 && x < Wl;
-    const int nval = min(4, Wl - x);
-    const bool top = q0 == 0, bottom = 2 * q1 >= Hs;
+    const bool top = q0 == 0, bottom = 2 * q1 >= Hs, final_level = j.final_level;
+    // border work of this warp (uniform): left border, right border column
+    const bool left = sx == 0;
+    const int right_col = (kStripCols * sx + 248 >= Ws) ? Ws - C0 : -1;
+    const bool border = left || right_col >= 0;
+    auto row = [&](const uint8_t *slot_base) -> Raw {
+        if (border) {
+            if (lane == 0)
+                mirror_slot<BYTES>(const_cast<uint8_t *>(slot_base), left, right_col);
+            __syncwarp();
+            asm volatile("" ::: "memory"); // the slot reads below come after the patch
+        }
+        return slot_row<BYTES>(slot_base, off);
+    };
     Cursor cu(ring, it, st0);
     uint32_t e0[4], dp[4];
     {
-        const Raw rm2 = slot_row<BYTES>(cu.st + 1 * slot, off);
-        const Raw rm1 = slot_row<BYTES>(cu.st + 2 * slot, off);
-        const Raw r0 = slot_row<BYTES>(cu.st + 3 * slot, off);
+        const Raw rm2 = row(cu.st + 1 * slot);
+        const Raw rm1 = row(cu.st + 2 * slot);
+        const Raw r0 = row(cu.st + 3 * slot);
         uint32_t a[4], o[4];
-        lift_row<BYTES, true>(r0, c, Ws, edge, e0);
-        lift_row<BYTES, true>(rm2, c, Ws, edge, a);
-        lift_row<BYTES, true>(rm1, c, Ws, edge, o);
+        lift_row<BYTES, false>(r0, c, Ws, false, e0);
+        lift_row<BYTES, false>(rm2, c, Ws, false, a);
+        lift_row<BYTES, false>(rm1, c, Ws, false, o);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             dp[i] = o[i] - pavg(a[i], e0[i]) + kB2; // (replaced at the top border)
     }
-    const uint8_t *p = cu.st + 4 * slot + off; // the lane's samples of row 2 q0 + 1
-    int left = rps - 4;                        // slots of the held stage still to read
+    const uint64_t ostep = 2ull * (uint64_t)Wl;
+    const uint64_t o0 = 2ull * ((uint64_t)q0 * (uint64_t)Wl + (uint64_t)x);
+    uint8_t *phl = j.hl + o0, *plh = j.lh + o0, *phh = j.hh + o0, *pll = j.ll + o0;
+    const uint8_t *p = cu.st + 4 * slot; // slot of row 2 q0 + 1
+    int left_slots = rps - 4;            // slots of the held stage still to read
     for (int q = q0; q < q1; ++q) {
-        if (left == 0) {
+        if (left_slots == 0) {
             if (!cu.next())
                 return false;
-            p = cu.st + off;
-            left = rps;
+            p = cu.st;
+            left_slots = rps;
         }
-        const Raw c1 = slot_row<BYTES>(p, 0), c2 = slot_row<BYTES>(p + slot, 0);
+        const Raw c1 = row(p), c2 = row(p + slot);
         p += 2 * slot;
-        left -= 2;
+        left_slots -= 2;
         uint32_t o[4], e1[4], sv[4], dv[4];
-        lift_row<BYTES, true>(c1, c, Ws, edge, o);
+        lift_row<BYTES, false>(c1, c, Ws, false, o);
         if (bottom && 2 * q + 2 == Hs) { // x[m] = x[m-2] at the bottom border
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 e1[k] = e0[k];
         } else {
-            lift_row<BYTES, true>(c2, c, Ws, edge, e1);
+            lift_row<BYTES, false>(c2, c, Ws, false, e1);
         }
         col_step(o, e1, e0, dp, top && q == 0, sv, dv);
-        if (own)
-            fwd_store(j, Wl, q, x, nval, sv, dv);
+        // sv[0..1] = LL, sv[2..3] = HL, dv[0..1] = LH, dv[2..3] = HH
+        if (own) {
+            *reinterpret_cast<uint2 *>(phl) = make_uint2(to_i16x2(sv[2]), to_i16x2(sv[3]));
+            *reinterpret_cast<uint2 *>(plh) = make_uint2(to_i16x2(dv[0]), to_i16x2(dv[1]));
+            *reinterpret_cast<uint2 *>(phh) = make_uint2(to_i16x2(dv[2]), to_i16x2(dv[3]));
+            *reinterpret_cast<uint2 *>(pll) = ll_out(final_level, sv);
+        }
+        phl += ostep;
+        plh += ostep;
+        phh += ostep;
+        pll += ostep;
     }
     cu.finish(it, nstages);
     return true;
@@ -1383,9 +1430,11 @@ __device__ void consumer_loop(const DagWork &w, Ring ring, const AesTab &aes, in
             } // kModeSkip: nothing
         }
         // publish: each consumer warp counts itself once its stores are
-        // visible (a segment is complete at strips x kConsumerWarps); jobs
+        // visible (a segment is complete at strips x kConsumerWarps), also to
+        // the bulk copies (async proxy) that consumers of this data use; jobs
         // that nothing in the launch reads skip it
         if (j.publish) {
+            asm volatile("fence.proxy.async.global;" ::: "memory");
             __threadfence();
             __syncwarp();
             if (lane == 0)
