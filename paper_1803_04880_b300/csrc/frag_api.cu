@@ -412,18 +412,28 @@ LevelJob cipher_job(bool fwd, const Buf &b, uint32_t R0)
 // the L + 1 jobs of one buffer in processing order (forward: levels 1..L, then
 // the cipher; inverse: the cipher, then levels L..1); each reads what the
 // previous one writes
+// a buffer whose private fragment is large (few levels) is enciphered by
+// the separate CTR launch rather than by cipher units inside the launch
+bool separate_cipher(const Buf &b) { return b.L <= frag::kSeparateCipherMaxLevels; }
+
+uint32_t buffer_njobs(const Buf &b) { return separate_cipher(b) ? b.L : b.L + 1; }
+
 void buffer_jobs(bool fwd, const Buf &b, uint32_t first_job, uint32_t *counters,
                  std::vector<LevelJob> &jobs)
 {
     const uint32_t R0 = b.R0;
-    for (uint32_t m = 0; m <= b.L; ++m) {
+    const bool sep = separate_cipher(b);
+    const uint32_t njobs = buffer_njobs(b);
+    for (uint32_t m = 0; m < njobs; ++m) {
         LevelJob j;
         if (fwd)
             j = m < b.L ? level_job(true, b, m + 1, R0) : cipher_job(true, b, R0);
+        else if (sep)
+            j = level_job(false, b, b.L - m, R0);
         else
             j = m == 0 ? cipher_job(false, b, R0) : level_job(false, b, b.L + 1 - m, R0);
         j.dep = m ? (int32_t)(first_job + m - 1) : -1;
-        j.publish = m < b.L; // the last job's output is read by nothing in the launch
+        j.publish = m + 1 < njobs; // the last job's output is read by nothing in the launch
         j.done_off = *counters;
         *counters += j.segs;
         if (m) {
@@ -495,6 +505,57 @@ frag_status dag_grid(DeviceState &d, bool fwd, uint64_t units, uint32_t *grid)
     return FRAG_OK;
 }
 
+// the private fragment of a buffer as one CTR fragment: protect enciphers it
+// in place after the transform; recover deciphers it into the scratch the
+// top level reads, before the transform
+frag::CtrChunk ctr_fragment(bool fwd, const Buf &b)
+{
+    frag::CtrChunk c;
+    std::memset(&c, 0, sizeof(c));
+    c.in = fwd ? b.priv : b.priv_in;
+    c.out = fwd ? b.priv : b.scr[b.L];
+    c.nonce = b.nonce;
+    c.bytes = ll_bytes(b.H, b.W, b.L);
+    c.nblocks = (c.bytes + 15) / 16;
+    return c;
+}
+
+frag_status ctr_launch(DeviceState &d, const uint32_t *rk, const frag::CtrChunk *chunks,
+                       uint64_t nchunks, const frag::CtrChunk *single, cudaStream_t s)
+{
+    int occ = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        auto it = d.occ[0].find(8888);
+        if (it != d.occ[0].end())
+            occ = it->second;
+    }
+    if (occ == 0) {
+        cudaError_t e = frag::ctr_occupancy(&occ);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "occupancy query");
+        occ = std::max(occ, 1);
+        std::lock_guard<std::mutex> lock(g_mu);
+        d.occ[0][8888] = occ;
+    }
+    frag::CtrWork w;
+    std::memset(&w, 0, sizeof(w));
+    w.chunks = chunks;
+    w.nchunks = nchunks;
+    if (single)
+        w.single = *single;
+    w.aes_tables = d.tables;
+    w.round_keys = rk;
+    const uint64_t work = chunks ? nchunks : (single->nblocks + frag::kCtrChunkList - 1) / frag::kCtrChunkList;
+    if (work == 0)
+        return FRAG_OK;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)d.sms * occ, work);
+    cudaError_t e = frag::launch_ctr(w, grid, s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cipher launch");
+    return FRAG_OK;
+}
+
 frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream_t s)
 {
     DeviceState *d = nullptr;
@@ -505,7 +566,7 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     const uint32_t *rk = nullptr;
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
-    const uint32_t njobs = b.L + 1;
+    const uint32_t njobs = buffer_njobs(b);
     if (njobs > (uint32_t)frag::kMaxInlineJobs)
         return fail(FRAG_EUNSUPPORTED, "more than %d levels", frag::kMaxInlineJobs - 1);
     // one stream-ordered allocation: [scratch][counters][queue head]
@@ -544,12 +605,18 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     w.round_keys = rk;
     w.err = d->err;
     w.spin_limit = kSpinLimit;
+    const bool sep = separate_cipher(b);
+    const frag::CtrChunk frag_chunk = ctr_fragment(fwd, b);
     e = cudaMemsetAsync(mem + sb, 0, cb + 256, s);
     if (e != cudaSuccess)
         st = cuda_fail(e, "counter reset");
-    else if ((st = dag_grid(*d, fwd, units, &grid)) == FRAG_OK &&
-             (e = frag::launch_dag(fwd, w, grid, s)) != cudaSuccess)
+    if (st == FRAG_OK && sep && !fwd)
+        st = ctr_launch(*d, rk, nullptr, 0, &frag_chunk, s);
+    if (st == FRAG_OK && (st = dag_grid(*d, fwd, units, &grid)) == FRAG_OK &&
+        (e = frag::launch_dag(fwd, w, grid, s)) != cudaSuccess)
         st = cuda_fail(e, fwd ? "protect launch" : "recover launch");
+    if (st == FRAG_OK && sep && fwd)
+        st = ctr_launch(*d, rk, nullptr, 0, &frag_chunk, s);
     cudaFreeAsync(mem, s);
     return st;
 }
@@ -562,8 +629,9 @@ struct DagWave {
     std::vector<LevelJob> jobs;
     std::vector<uint32_t> first, levels; // per buffer: first job, number of jobs
     std::vector<DagUnit> units;
+    std::vector<frag::CtrChunk> chunks; // private fragments of the separate CTR launch
     uint32_t counters = 0;
-    size_t jobs_off = 0, units_off = 0, done_off = 0, queue_off = 0;
+    size_t jobs_off = 0, units_off = 0, done_off = 0, queue_off = 0, chunks_off = 0;
 };
 
 struct BatchPlan {
@@ -654,6 +722,7 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         wv.first.clear();
         wv.levels.clear();
         wv.units.clear();
+        wv.chunks.clear();
         wv.counters = 0;
     }
     for (size_t i = 0; i < bp.bufs.size(); ++i) {
@@ -667,7 +736,17 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         const uint32_t first = (uint32_t)wv.jobs.size();
         buffer_jobs(bp.fwd, b, first, &wv.counters, wv.jobs);
         wv.first.push_back(first);
-        wv.levels.push_back(b.L + 1);
+        wv.levels.push_back(buffer_njobs(b));
+        if (separate_cipher(b)) {
+            // the private fragment in chunks of kCtrChunkList blocks
+            const frag::CtrChunk whole = ctr_fragment(bp.fwd, b);
+            for (uint64_t f = 0; f < whole.nblocks; f += frag::kCtrChunkList) {
+                frag::CtrChunk c = whole;
+                c.first_block = f;
+                c.nblocks = std::min<uint64_t>(frag::kCtrChunkList, whole.nblocks - f);
+                wv.chunks.push_back(c);
+            }
+        }
     }
     for (auto &wv : bp.waves)
         wave_units(wv.jobs, wv.first, wv.levels, wv.units);
@@ -681,6 +760,8 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         off += align256(4ull * std::max(1u, wv.counters));
         wv.queue_off = off;
         off += 256;
+        wv.chunks_off = off;
+        off += align256(wv.chunks.size() * sizeof(frag::CtrChunk));
     }
     bp.desc_bytes = off - align256(bp.scratch);
 }
@@ -694,6 +775,9 @@ frag_status upload_batch(const BatchPlan &bp, uint8_t *mem, cudaStream_t s, bool
     for (const auto &wv : bp.waves) {
         std::memcpy(host.data() + (wv.jobs_off - base), wv.jobs.data(), wv.jobs.size() * sizeof(LevelJob));
         std::memcpy(host.data() + (wv.units_off - base), wv.units.data(), wv.units.size() * sizeof(DagUnit));
+        if (!wv.chunks.empty())
+            std::memcpy(host.data() + (wv.chunks_off - base), wv.chunks.data(),
+                        wv.chunks.size() * sizeof(frag::CtrChunk));
     }
     cudaError_t e = async ? cudaMemcpyAsync(mem + base, host.data(), host.size(), cudaMemcpyHostToDevice, s)
                           : cudaMemcpy(mem + base, host.data(), host.size(), cudaMemcpyHostToDevice);
@@ -708,6 +792,12 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
     for (const auto &wv : bp.waves) {
         if (wv.units.empty())
             continue;
+        const frag::CtrChunk *chunks = (const frag::CtrChunk *)(mem + wv.chunks_off);
+        if (!bp.fwd && !wv.chunks.empty()) { // decipher before the transform reads LL_L
+            frag_status st = ctr_launch(d, rk, chunks, wv.chunks.size(), nullptr, s);
+            if (st != FRAG_OK)
+                return st;
+        }
         cudaError_t e = cudaMemsetAsync(mem + wv.done_off, 0, wv.queue_off + 256 - wv.done_off, s);
         if (e != cudaSuccess)
             return cuda_fail(e, "counter reset");
@@ -730,6 +820,11 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
             return st;
         if ((e = frag::launch_dag(bp.fwd, w, grid, s)) != cudaSuccess)
             return cuda_fail(e, "batch launch");
+        if (bp.fwd && !wv.chunks.empty()) { // encipher after the transform wrote LL_L
+            st = ctr_launch(d, rk, chunks, wv.chunks.size(), nullptr, s);
+            if (st != FRAG_OK)
+                return st;
+        }
     }
     return FRAG_OK;
 }
@@ -1181,7 +1276,7 @@ frag_status frag_batch_info(frag_batch batch, uint32_t *launches, uint64_t *scra
         return fail(FRAG_EINVAL, "batch is NULL");
     uint32_t n = 0;
     for (const auto &wv : batch->bp.waves)
-        n += wv.units.empty() ? 0 : 1;
+        n += (wv.units.empty() ? 0 : 1) + (wv.chunks.empty() ? 0 : 1);
     if (launches)
         *launches = n;
     if (scratch_bytes)

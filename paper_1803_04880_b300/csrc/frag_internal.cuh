@@ -145,6 +145,33 @@ constexpr int kStripCols = 240;          // level-(l-1) columns owned by one war
 constexpr uint32_t kTileStrips = 4;      // warp strips (consumer warps) of one tile unit
 constexpr uint32_t kCipherBlocks = 512;  // AES blocks of one cipher unit
 
+// AES-128-CTR in a launch of its own (cipher_kernels.cu), for buffers whose
+// private fragment is large: levels <= kSeparateCipherMaxLevels
+constexpr uint32_t kSeparateCipherMaxLevels = 2;
+
+// blocks [first_block, first_block + nblocks) of one fragment of `bytes`
+// bytes: out = in XOR keystream(nonce)
+struct CtrChunk {
+    const uint8_t *in;
+    uint8_t *out;
+    uint64_t nonce;
+    uint64_t first_block;
+    uint64_t bytes;
+    uint64_t nblocks; // lone fragment: all of its blocks; chunk list: this chunk's
+};
+
+struct CtrWork {
+    const CtrChunk *chunks; // device array (nullptr: one fragment, `single`)
+    uint64_t nchunks;
+    CtrChunk single;
+    const uint32_t *aes_tables; // table 0 is the first 256 words
+    const uint32_t *round_keys;
+};
+
+cudaError_t launch_ctr(const CtrWork &w, uint32_t grid, cudaStream_t stream);
+cudaError_t ctr_occupancy(int *blocks_per_sm);
+constexpr uint32_t kCtrChunkList = 1024; // blocks per chunk of a chunk list
+
 // kernels (tile_kernels.cu)
 constexpr uint32_t kFastTile = 256;   // owned tile side of the row/column-pass body
 constexpr uint32_t kFastMaxLevels = 3;
