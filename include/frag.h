@@ -109,6 +109,22 @@ frag_status frag_plan_get_tiling(frag_plan plan, uint32_t *tile_w, uint32_t *til
 frag_status frag_plan_set_schedule(frag_plan plan, uint32_t seg_rows, uint32_t ctas);
 frag_status frag_plan_get_schedule(frag_plan plan, uint32_t *seg_rows, uint32_t *ctas);
 
+/* Kernels that run the levels of a plan's protect / recover calls (batches
+ * take each buffer's from that buffer's plan).  FRAG_PATH_AUTO (the default):
+ * levels 1..min(L, 3) of a buffer run in one fused pass down its rows that
+ * keeps LL_1 .. LL_{F-1} on chip, whenever the width is a multiple of 8, the
+ * input (protect) or output (recover) is 8-byte aligned, the level-1 bands
+ * are 8-byte and the level-2 and level-3 bands 4-byte aligned, and, when the
+ * fused levels are all of them (protect), the private fragment is 4-byte
+ * aligned (8-byte with one level); the levels above, and buffers that do not
+ * meet those conditions, run in the dependency-ordered level kernel.
+ * FRAG_PATH_LEVELS: every level in the dependency-ordered kernel.  Results do
+ * not depend on the path.  FRAG_EINVAL for a NULL plan or an unknown path;
+ * get: FRAG_EINVAL if path is NULL. */
+typedef enum { FRAG_PATH_AUTO = 0, FRAG_PATH_LEVELS = 1 } frag_path;
+frag_status frag_plan_set_path(frag_plan plan, frag_path path);
+frag_status frag_plan_get_path(frag_plan plan, frag_path *path);
+
 /* AES-128 key (Sec. 5.2.1 protects the private fragment with AES-128): the
  * round keys are expanded on the host (FIPS-197 Sec. 5.2) and kept resident on
  * each device that uses the key.  The 16 bytes are copied. */

@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "FRAG_OK", 1: "FRAG_EINVAL", 2: "FRAG_EUNSUPPORTED", 3: "FRAG
 EXPORTS = [
     "frag_abi_version", "frag_plan_create", "frag_plan_destroy", "frag_plan_sizes",
     "frag_plan_set_tiling", "frag_plan_get_tiling", "frag_plan_set_schedule",
-    "frag_plan_get_schedule", "frag_key_create", "frag_key_destroy",
+    "frag_plan_get_schedule", "frag_plan_set_path", "frag_plan_get_path",
+    "frag_key_create", "frag_key_destroy",
     "frag_protect", "frag_recover", "frag_protect_host", "frag_recover_host",
     "frag_protect_batch", "frag_recover_batch", "frag_batch_create_protect",
     "frag_batch_create_recover", "frag_batch_run", "frag_batch_destroy", "frag_batch_info",
@@ -80,6 +81,8 @@ def lib():
                                   ctypes.POINTER(u32)], ctypes.c_int),
         "frag_plan_set_schedule": ([vp, u32, u32], ctypes.c_int),
         "frag_plan_get_schedule": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u32)], ctypes.c_int),
+        "frag_plan_set_path": ([vp, ctypes.c_int], ctypes.c_int),
+        "frag_plan_get_path": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "frag_key_create": ([ctypes.POINTER(vp), ctypes.c_char_p], ctypes.c_int),
         "frag_key_destroy": ([vp], ctypes.c_int),
         "frag_protect": ([vp, vp, u64, vp, u64, vp, vp, vp], ctypes.c_int),
@@ -159,6 +162,19 @@ class Plan:
         a, b = ctypes.c_uint32(), ctypes.c_uint32()
         check(lib().frag_plan_get_schedule(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    PATH_AUTO = 0    # levels 1..min(L, 3) fused in one pass where alignment allows
+    PATH_LEVELS = 1  # every level in the dependency-ordered kernel
+
+    def set_path(self, path: int) -> None:
+        """Kernels that run the levels (PATH_AUTO or PATH_LEVELS); results do
+        not depend on it."""
+        check(lib().frag_plan_set_path(self._h, path))
+
+    def path(self) -> int:
+        v = ctypes.c_int()
+        check(lib().frag_plan_get_path(self._h, ctypes.byref(v)))
+        return v.value
 
     def tiling(self) -> Tuple[int, int, int]:
         a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()

@@ -28,6 +28,7 @@ struct frag_plan_s {
     uint32_t ctas_per_sm;
     uint32_t seg_rows;    // streaming path: level-0 rows per unit (0: adaptive)
     uint32_t max_ctas;    // streaming path: grid cap (0: all resident CTAs)
+    uint32_t path;        // frag_path: which kernels run the levels
 };
 
 struct frag_key_s {
@@ -284,13 +285,19 @@ uint64_t align256(uint64_t v) { return (v + 255) / 256 * 256; }
 
 uint64_t ll_bytes(uint32_t H, uint32_t W, uint32_t l) { return 2ull * (H >> l) * (uint64_t)(W >> l); }
 
-// scratch of one buffer: LL_1 .. LL_{L-1}, each in its own region (the jobs
+// first and last level whose LL band goes through scratch: the fused kernel
+// keeps LL_1 .. LL_{F-1} on chip and hands LL_F over in scratch when levels
+// remain above it
+uint32_t scratch_lo(uint32_t F) { return F > 1 ? F : 1; }
+uint32_t scratch_hi(bool fwd, uint32_t L) { return fwd ? L - 1 : L; }
+
+// scratch of one buffer: LL_lo .. LL_{L-1}, each in its own region (the jobs
 // of one buffer run concurrently, so no region can be reused), and for the
 // inverse the deciphered LL_L; off[l] is the offset of LL_l
-uint64_t scratch_bytes(bool fwd, uint32_t H, uint32_t W, uint32_t L, uint64_t *off)
+uint64_t scratch_bytes(bool fwd, uint32_t H, uint32_t W, uint32_t L, uint32_t F, uint64_t *off)
 {
     uint64_t total = 0;
-    for (uint32_t l = 1; l < (fwd ? L : L + 1); ++l) {
+    for (uint32_t l = scratch_lo(F); l <= scratch_hi(fwd, L); ++l) {
         if (off)
             off[l] = total;
         total += align256(ll_bytes(H, W, l));
@@ -300,6 +307,7 @@ uint64_t scratch_bytes(bool fwd, uint32_t H, uint32_t W, uint32_t L, uint64_t *o
 
 struct Buf {
     uint32_t W, L, H;
+    uint32_t F;        // levels 1..F run in the fused kernel (0: none)
     uint32_t R0;       // level-0 rows per work segment
     uint32_t R0_plan;  // the plan's choice (0: adaptive)
     uint64_t n, nonce;
@@ -409,14 +417,19 @@ LevelJob cipher_job(bool fwd, const Buf &b, uint32_t R0)
     return j;
 }
 
-// the L + 1 jobs of one buffer in processing order (forward: levels 1..L, then
-// the cipher; inverse: the cipher, then levels L..1); each reads what the
-// previous one writes
-// a buffer whose private fragment is large (few levels) is enciphered by
-// the separate CTR launch rather than by cipher units inside the launch
-bool separate_cipher(const Buf &b) { return b.L <= frag::kSeparateCipherMaxLevels; }
+// a buffer whose private fragment is large (few levels), or whose levels all
+// run in the fused kernel, is enciphered by the separate CTR launch rather
+// than by cipher units inside the dependency-ordered launch
+bool separate_cipher(const Buf &b)
+{
+    return b.L <= frag::kSeparateCipherMaxLevels || b.F == b.L;
+}
 
-uint32_t buffer_njobs(const Buf &b) { return separate_cipher(b) ? b.L : b.L + 1; }
+uint32_t buffer_njobs(const Buf &b) { return (b.L - b.F) + (separate_cipher(b) ? 0 : 1); }
+
+// the jobs of one buffer in the dependency-ordered launch, in processing
+// order (forward: levels F+1..L, then the cipher; inverse: the cipher, then
+// levels L..F+1); each reads what the previous one writes
 
 void buffer_jobs(bool fwd, const Buf &b, uint32_t first_job, uint32_t *counters,
                  std::vector<LevelJob> &jobs)
@@ -427,7 +440,7 @@ void buffer_jobs(bool fwd, const Buf &b, uint32_t first_job, uint32_t *counters,
     for (uint32_t m = 0; m < njobs; ++m) {
         LevelJob j;
         if (fwd)
-            j = m < b.L ? level_job(true, b, m + 1, R0) : cipher_job(true, b, R0);
+            j = m < b.L - b.F ? level_job(true, b, b.F + 1 + m, R0) : cipher_job(true, b, R0);
         else if (sep)
             j = level_job(false, b, b.L - m, R0);
         else
@@ -556,6 +569,119 @@ frag_status ctr_launch(DeviceState &d, const uint32_t *rk, const frag::CtrChunk 
     return FRAG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Fused path: levels 1..F of a buffer in one pass down its rows
+// ---------------------------------------------------------------------------
+constexpr uint32_t kFuseMinSegIters = 8; // iterations per unit at least (adaptive choice)
+
+// levels the fused kernel takes for buffer b (0: none): up to
+// kFuseMaxLevels, when the width and every pointer it accesses with vector
+// loads or stores allow it
+uint32_t fused_levels(bool fwd, const Buf &b, uint32_t path)
+{
+    if (path == FRAG_PATH_LEVELS || b.W % 8 != 0)
+        return 0;
+    const uint32_t F = std::min(b.L, frag::kFuseMaxLevels);
+    if (fwd ? !aligned(b.in, 8) : !aligned(b.out, 8))
+        return 0;
+    const uint8_t *pub = fwd ? b.pub : b.pub_in;
+    for (uint32_t l = 1; l <= F; ++l)
+        for (uint32_t k = 0; k < 3; ++k)
+            if (!aligned(pub + frag::band_offset(b.H, b.W, b.L, l, k), l == 1 ? 8 : 4))
+                return 0;
+    if (fwd && F == b.L && !aligned(b.priv, F == 1 ? 8 : 4))
+        return 0; // LL_L goes straight to the private fragment
+    return F;
+}
+
+// descriptor of buffer b for the fused kernel (schedule fields left 0)
+frag::FuseBuf fuse_buf(bool fwd, const Buf &b)
+{
+    frag::FuseBuf f;
+    std::memset(&f, 0, sizeof(f));
+    f.src = b.in;
+    f.out = b.out;
+    uint8_t *pub = fwd ? b.pub : const_cast<uint8_t *>(b.pub_in);
+    for (uint32_t l = 1; l <= b.F; ++l)
+        for (uint32_t k = 0; k < 3; ++k)
+            f.band[l - 1][k] = pub + frag::band_offset(b.H, b.W, b.L, l, k);
+    // LL_F: the private fragment (protect, last level), the deciphered copy
+    // (recover, last level) or the scratch the levels above read / write
+    f.ll = (fwd && b.F == b.L) ? b.priv : b.scr[b.F];
+    f.ll_final = b.F == b.L;
+    f.n = b.n;
+    f.W = b.W;
+    f.H = b.H;
+    f.F = b.F;
+    f.halo = (fwd && b.F == 3) ? 2 : 1;
+    f.strips = (b.W + 8 * (31 - f.halo) - 1) / (8 * (31 - f.halo));
+    f.iters = fwd ? b.H / 8 + 1 : (b.H + 6) / 8 + 1;
+    return f;
+}
+
+// units of each buffer: one segment height for a launch, chosen so that the
+// units about fill the resident warps once (or from the plan's seg_rows);
+// returns the launch's units
+uint64_t fuse_schedule(frag::FuseBuf *f, size_t nbufs, uint64_t warps, uint32_t plan_rows)
+{
+    uint32_t seg = 0;
+    if (plan_rows) {
+        seg = std::max(1u, plan_rows / 8);
+    } else {
+        uint64_t work = 0;
+        for (size_t i = 0; i < nbufs; ++i)
+            work += (uint64_t)f[i].strips * f[i].iters;
+        seg = (uint32_t)std::min<uint64_t>(
+            1u << 20, std::max<uint64_t>(kFuseMinSegIters, (work + warps - 1) / std::max<uint64_t>(1, warps)));
+    }
+    uint64_t units = 0;
+    for (size_t i = 0; i < nbufs; ++i) {
+        f[i].seg_iters = seg;
+        f[i].segs = (f[i].iters + seg - 1) / seg;
+        f[i].unit0 = units;
+        units += (uint64_t)f[i].strips * f[i].segs;
+    }
+    return units;
+}
+
+frag_status fuse_slots(DeviceState &d, bool fwd, uint32_t max_ctas, uint64_t *slots)
+{
+    int occ = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        auto it = d.occ[fwd].find(9999);
+        if (it != d.occ[fwd].end())
+            occ = it->second;
+    }
+    if (occ == 0) {
+        cudaError_t e = frag::fuse_occupancy(fwd, &occ);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "occupancy query");
+        occ = std::max(occ, 1);
+        std::lock_guard<std::mutex> lock(g_mu);
+        d.occ[fwd][9999] = occ;
+    }
+    *slots = (uint64_t)d.sms * occ;
+    if (max_ctas)
+        *slots = std::min<uint64_t>(*slots, max_ctas);
+    return FRAG_OK;
+}
+
+frag_status fuse_launch(DeviceState &d, bool fwd, frag::FuseWork &w, uint64_t slots, cudaStream_t s)
+{
+    if (w.total_units == 0)
+        return FRAG_OK;
+    const uint64_t need = (w.total_units + frag::kFuseWarps - 1) / frag::kFuseWarps;
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min(slots, need));
+    cudaError_t e = frag::launch_fuse(fwd, w, grid, s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, fwd ? "fused protect launch" : "fused recover launch");
+    return FRAG_OK;
+}
+
+// One buffer: protect runs the fused levels, then the dependency-ordered
+// launch for the levels above them (and the cipher units), then the CTR
+// launch; recover runs them in the reverse order.
 frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream_t s)
 {
     DeviceState *d = nullptr;
@@ -566,58 +692,86 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     const uint32_t *rk = nullptr;
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
+    b.F = fused_levels(fwd, b, plan->path);
     const uint32_t njobs = buffer_njobs(b);
     if (njobs > (uint32_t)frag::kMaxInlineJobs)
         return fail(FRAG_EUNSUPPORTED, "more than %d levels", frag::kMaxInlineJobs - 1);
     // one stream-ordered allocation: [scratch][counters][queue head]
     uint64_t off[frag::kMaxInlineJobs + 1] = {0};
-    const uint64_t sb = align256(scratch_bytes(fwd, b.H, b.W, b.L, off));
+    const uint64_t sb = align256(scratch_bytes(fwd, b.H, b.W, b.L, b.F, off));
     uint32_t grid = 0;
-    if ((st = dag_grid(*d, fwd, ~0ull, &grid)) != FRAG_OK)
-        return st;
-    if (plan->max_ctas)
-        grid = std::min(grid, plan->max_ctas);
-    b.R0 = seg_rows0(b.L, l1_units_at_64(b), grid, plan->seg_rows);
-    const uint32_t NS = (b.H + b.R0 - 1) / b.R0;
-    const uint64_t cb = align256(4ull * NS * njobs);
-    uint8_t *mem = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&mem, sb + cb + 256, s);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "cudaMallocAsync(level scratch)");
-    for (uint32_t l = 1; l < (fwd ? b.L : b.L + 1); ++l)
-        b.scr[l] = mem + off[l];
-    std::vector<LevelJob> jobs;
-    uint32_t counters = 0;
-    buffer_jobs(fwd, b, 0, &counters, jobs);
-    DagWork w;
-    std::memset(&w, 0, sizeof(w));
-    uint64_t units = 0;
-    for (uint32_t m = 0; m < njobs; ++m) {
-        w.inline_jobs[m] = jobs[m];
-        units += (uint64_t)jobs[m].strips * jobs[m].segs;
+    uint64_t cb = 0;
+    if (njobs) {
+        if ((st = dag_grid(*d, fwd, ~0ull, &grid)) != FRAG_OK)
+            return st;
+        if (plan->max_ctas)
+            grid = std::min(grid, plan->max_ctas);
+        b.R0 = seg_rows0(b.L, l1_units_at_64(b), grid, plan->seg_rows);
+        const uint32_t NS = (b.H + b.R0 - 1) / b.R0;
+        cb = align256(4ull * NS * njobs);
     }
-    w.n_inline = njobs;
-    w.lag = buffer_lag(jobs, 0, njobs, grid);
-    w.total_units = units;
-    w.done = (unsigned *)(mem + sb);
-    w.queue = (unsigned long long *)(mem + sb + cb);
-    w.aes_tables = d->tables;
-    w.round_keys = rk;
-    w.err = d->err;
-    w.spin_limit = kSpinLimit;
+    uint8_t *mem = nullptr;
+    if (sb + cb) {
+        cudaError_t e = cudaMallocAsync((void **)&mem, sb + cb + 256, s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaMallocAsync(level scratch)");
+    }
+    for (uint32_t l = scratch_lo(b.F); l <= scratch_hi(fwd, b.L); ++l)
+        b.scr[l] = mem + off[l];
+    frag::FuseWork fw;
+    std::memset(&fw, 0, sizeof(fw));
+    uint64_t fslots = 0;
+    if (b.F) {
+        if ((st = fuse_slots(*d, fwd, plan->max_ctas, &fslots)) != FRAG_OK) {
+            cudaFreeAsync(mem, s);
+            return st;
+        }
+        fw.single = fuse_buf(fwd, b);
+        fw.nbufs = 1;
+        fw.total_units = fuse_schedule(&fw.single, 1, fslots * frag::kFuseWarps, plan->seg_rows);
+    }
     const bool sep = separate_cipher(b);
     const frag::CtrChunk frag_chunk = ctr_fragment(fwd, b);
-    e = cudaMemsetAsync(mem + sb, 0, cb + 256, s);
-    if (e != cudaSuccess)
-        st = cuda_fail(e, "counter reset");
+    if (fwd && b.F)
+        st = fuse_launch(*d, true, fw, fslots, s);
     if (st == FRAG_OK && sep && !fwd)
         st = ctr_launch(*d, rk, nullptr, 0, &frag_chunk, s);
-    if (st == FRAG_OK && (st = dag_grid(*d, fwd, units, &grid)) == FRAG_OK &&
-        (e = frag::launch_dag(fwd, w, grid, s)) != cudaSuccess)
-        st = cuda_fail(e, fwd ? "protect launch" : "recover launch");
+    if (st == FRAG_OK && njobs) {
+        std::vector<LevelJob> jobs;
+        uint32_t counters = 0;
+        buffer_jobs(fwd, b, 0, &counters, jobs);
+        DagWork w;
+        std::memset(&w, 0, sizeof(w));
+        uint64_t units = 0;
+        for (uint32_t m = 0; m < njobs; ++m) {
+            w.inline_jobs[m] = jobs[m];
+            units += (uint64_t)jobs[m].strips * jobs[m].segs;
+        }
+        w.n_inline = njobs;
+        w.lag = buffer_lag(jobs, 0, njobs, grid);
+        w.total_units = units;
+        w.done = (unsigned *)(mem + sb);
+        w.queue = (unsigned long long *)(mem + sb + cb);
+        w.aes_tables = d->tables;
+        w.round_keys = rk;
+        w.err = d->err;
+        w.spin_limit = kSpinLimit;
+        cudaError_t e = cudaMemsetAsync(mem + sb, 0, cb + 256, s);
+        if (e != cudaSuccess)
+            st = cuda_fail(e, "counter reset");
+        if (st == FRAG_OK && (st = dag_grid(*d, fwd, units, &grid)) == FRAG_OK) {
+            if (plan->max_ctas)
+                grid = std::min(grid, plan->max_ctas);
+            if ((e = frag::launch_dag(fwd, w, grid, s)) != cudaSuccess)
+                st = cuda_fail(e, fwd ? "protect launch" : "recover launch");
+        }
+    }
     if (st == FRAG_OK && sep && fwd)
         st = ctr_launch(*d, rk, nullptr, 0, &frag_chunk, s);
-    cudaFreeAsync(mem, s);
+    if (st == FRAG_OK && !fwd && b.F)
+        st = fuse_launch(*d, false, fw, fslots, s);
+    if (mem)
+        cudaFreeAsync(mem, s);
     return st;
 }
 
@@ -630,14 +784,18 @@ struct DagWave {
     std::vector<uint32_t> first, levels; // per buffer: first job, number of jobs
     std::vector<DagUnit> units;
     std::vector<frag::CtrChunk> chunks; // private fragments of the separate CTR launch
+    std::vector<frag::FuseBuf> fbufs;   // buffers of the fused launch
+    uint64_t fuse_units = 0;
     uint32_t counters = 0;
-    size_t jobs_off = 0, units_off = 0, done_off = 0, queue_off = 0, chunks_off = 0;
+    size_t jobs_off = 0, units_off = 0, done_off = 0, queue_off = 0, chunks_off = 0, fbufs_off = 0;
 };
 
 struct BatchPlan {
     bool fwd = true;
     uint64_t resident_ctas = 0; // CTAs one launch keeps resident
     uint32_t max_ctas = 0;      // grid cap from the first item's plan (0: none)
+    uint32_t fuse_rows = 0;     // fused segment rows from the first item's plan (0: adaptive)
+    uint64_t fuse_slots = 0;    // fused CTAs one launch keeps resident
     std::vector<Buf> bufs;
     std::vector<uint64_t> scr_off;
     std::vector<uint32_t> wave_of;
@@ -663,8 +821,10 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
         b.W = plan->width;
         b.L = plan->levels;
         b.R0_plan = plan->seg_rows;
-        if (bp.max_ctas == 0)
+        if (bp.bufs.empty() && v.empty()) {
             bp.max_ctas = plan->max_ctas; // the grid of a launch: the first item's plan
+            bp.fuse_rows = plan->seg_rows;
+        }
         const uint64_t H = rows_for(n, b.W, b.L);
         if (H > 0xFFFFFFFFull)
             return fail(FRAG_EINVAL, "item %u is too tall for width %u", i, b.W);
@@ -685,6 +845,7 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
             if (!b.priv_in || !b.pub_in || !b.out)
                 return fail(FRAG_EINVAL, "item %u has a NULL buffer", i);
         }
+        b.F = fused_levels(fwd, b, plan->path);
         v.emplace_back(H * (uint64_t)b.W, b);
     }
     std::stable_sort(v.begin(), v.end(),
@@ -694,7 +855,8 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
     uint64_t used = 0;
     uint32_t wave = 0;
     for (auto &p : v) {
-        const uint64_t sb = align256(scratch_bytes(fwd, p.second.H, p.second.W, p.second.L, nullptr));
+        const uint64_t sb =
+            align256(scratch_bytes(fwd, p.second.H, p.second.W, p.second.L, p.second.F, nullptr));
         if (used > 0 && used + sb > kScratchBudget) {
             ++wave;
             used = 0;
@@ -723,20 +885,24 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         wv.levels.clear();
         wv.units.clear();
         wv.chunks.clear();
+        wv.fbufs.clear();
+        wv.fuse_units = 0;
         wv.counters = 0;
     }
     for (size_t i = 0; i < bp.bufs.size(); ++i) {
         Buf &b = bp.bufs[i];
         uint64_t off[frag::kMaxInlineJobs + 1] = {0};
         b.R0 = seg_rows0(b.L, u64, bp.resident_ctas, b.R0_plan);
-        scratch_bytes(bp.fwd, b.H, b.W, b.L, off);
-        for (uint32_t l = 1; l < (bp.fwd ? b.L : b.L + 1); ++l)
+        scratch_bytes(bp.fwd, b.H, b.W, b.L, b.F, off);
+        for (uint32_t l = scratch_lo(b.F); l <= scratch_hi(bp.fwd, b.L); ++l)
             b.scr[l] = scratch_base + bp.scr_off[i] + off[l];
         DagWave &wv = bp.waves[bp.wave_of[i]];
         const uint32_t first = (uint32_t)wv.jobs.size();
         buffer_jobs(bp.fwd, b, first, &wv.counters, wv.jobs);
         wv.first.push_back(first);
         wv.levels.push_back(buffer_njobs(b));
+        if (b.F)
+            wv.fbufs.push_back(fuse_buf(bp.fwd, b));
         if (separate_cipher(b)) {
             // the private fragment in chunks of kCtrChunkList blocks
             const frag::CtrChunk whole = ctr_fragment(bp.fwd, b);
@@ -748,8 +914,12 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
             }
         }
     }
-    for (auto &wv : bp.waves)
+    for (auto &wv : bp.waves) {
         wave_units(wv.jobs, wv.first, wv.levels, wv.units);
+        wv.fuse_units = fuse_schedule(wv.fbufs.data(), wv.fbufs.size(),
+                                      std::max<uint64_t>(1, bp.fuse_slots) * frag::kFuseWarps,
+                                      bp.fuse_rows);
+    }
     size_t off = align256(bp.scratch);
     for (auto &wv : bp.waves) {
         wv.jobs_off = off;
@@ -762,6 +932,8 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         off += 256;
         wv.chunks_off = off;
         off += align256(wv.chunks.size() * sizeof(frag::CtrChunk));
+        wv.fbufs_off = off;
+        off += align256(wv.fbufs.size() * sizeof(frag::FuseBuf));
     }
     bp.desc_bytes = off - align256(bp.scratch);
 }
@@ -778,6 +950,9 @@ frag_status upload_batch(const BatchPlan &bp, uint8_t *mem, cudaStream_t s, bool
         if (!wv.chunks.empty())
             std::memcpy(host.data() + (wv.chunks_off - base), wv.chunks.data(),
                         wv.chunks.size() * sizeof(frag::CtrChunk));
+        if (!wv.fbufs.empty())
+            std::memcpy(host.data() + (wv.fbufs_off - base), wv.fbufs.data(),
+                        wv.fbufs.size() * sizeof(frag::FuseBuf));
     }
     cudaError_t e = async ? cudaMemcpyAsync(mem + base, host.data(), host.size(), cudaMemcpyHostToDevice, s)
                           : cudaMemcpy(mem + base, host.data(), host.size(), cudaMemcpyHostToDevice);
@@ -786,47 +961,81 @@ frag_status upload_batch(const BatchPlan &bp, uint8_t *mem, cudaStream_t s, bool
     return FRAG_OK;
 }
 
+// the fused launch of a wave (its buffers' descriptors at fbufs_off)
+frag_status launch_wave_fused(const BatchPlan &bp, const DagWave &wv, uint8_t *mem, DeviceState &d,
+                              cudaStream_t s)
+{
+    if (wv.fbufs.empty())
+        return FRAG_OK;
+    frag::FuseWork w;
+    std::memset(&w, 0, sizeof(w));
+    w.nbufs = (uint32_t)wv.fbufs.size();
+    w.bufs = (const frag::FuseBuf *)(mem + wv.fbufs_off);
+    if (w.nbufs == 1)
+        w.single = wv.fbufs[0];
+    w.total_units = wv.fuse_units;
+    return fuse_launch(d, bp.fwd, w, std::max<uint64_t>(1, bp.fuse_slots), s);
+}
+
+// per wave, protect: fused levels, dependency-ordered levels above them,
+// CTR; recover: CTR, dependency-ordered levels, fused levels
 frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, const uint32_t *rk,
                          cudaStream_t s)
 {
     for (const auto &wv : bp.waves) {
-        if (wv.units.empty())
-            continue;
         const frag::CtrChunk *chunks = (const frag::CtrChunk *)(mem + wv.chunks_off);
+        frag_status st = FRAG_OK;
+        if (bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s)) != FRAG_OK)
+            return st;
         if (!bp.fwd && !wv.chunks.empty()) { // decipher before the transform reads LL_L
-            frag_status st = ctr_launch(d, rk, chunks, wv.chunks.size(), nullptr, s);
+            st = ctr_launch(d, rk, chunks, wv.chunks.size(), nullptr, s);
             if (st != FRAG_OK)
                 return st;
         }
-        cudaError_t e = cudaMemsetAsync(mem + wv.done_off, 0, wv.queue_off + 256 - wv.done_off, s);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "counter reset");
-        DagWork w;
-        std::memset(&w, 0, sizeof(w));
-        w.jobs = (const LevelJob *)(mem + wv.jobs_off);
-        w.units = (const DagUnit *)(mem + wv.units_off);
-        w.total_units = wv.units.size();
-        w.done = (unsigned *)(mem + wv.done_off);
-        w.queue = (unsigned long long *)(mem + wv.queue_off);
-        w.aes_tables = d.tables;
-        w.round_keys = rk;
-        w.err = d.err;
-        w.spin_limit = kSpinLimit;
-        uint32_t grid = 0;
-        frag_status st = dag_grid(d, bp.fwd, w.total_units, &grid);
-        if (bp.max_ctas)
-            grid = std::min(grid, bp.max_ctas);
-        if (st != FRAG_OK)
-            return st;
-        if ((e = frag::launch_dag(bp.fwd, w, grid, s)) != cudaSuccess)
-            return cuda_fail(e, "batch launch");
+        if (!wv.units.empty()) {
+            cudaError_t e = cudaMemsetAsync(mem + wv.done_off, 0, wv.queue_off + 256 - wv.done_off, s);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "counter reset");
+            DagWork w;
+            std::memset(&w, 0, sizeof(w));
+            w.jobs = (const LevelJob *)(mem + wv.jobs_off);
+            w.units = (const DagUnit *)(mem + wv.units_off);
+            w.total_units = wv.units.size();
+            w.done = (unsigned *)(mem + wv.done_off);
+            w.queue = (unsigned long long *)(mem + wv.queue_off);
+            w.aes_tables = d.tables;
+            w.round_keys = rk;
+            w.err = d.err;
+            w.spin_limit = kSpinLimit;
+            uint32_t grid = 0;
+            st = dag_grid(d, bp.fwd, w.total_units, &grid);
+            if (bp.max_ctas)
+                grid = std::min(grid, bp.max_ctas);
+            if (st != FRAG_OK)
+                return st;
+            if ((e = frag::launch_dag(bp.fwd, w, grid, s)) != cudaSuccess)
+                return cuda_fail(e, "batch launch");
+        }
         if (bp.fwd && !wv.chunks.empty()) { // encipher after the transform wrote LL_L
             st = ctr_launch(d, rk, chunks, wv.chunks.size(), nullptr, s);
             if (st != FRAG_OK)
                 return st;
         }
+        if (!bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s)) != FRAG_OK)
+            return st;
     }
     return FRAG_OK;
+}
+
+// CTAs the fused launches of a batch keep resident
+frag_status batch_fuse_slots(BatchPlan &bp, DeviceState &d)
+{
+    bool any = false;
+    for (const Buf &b : bp.bufs)
+        any = any || b.F != 0;
+    if (!any)
+        return FRAG_OK;
+    return fuse_slots(d, bp.fwd, bp.max_ctas, &bp.fuse_slots);
 }
 
 frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, uint32_t count,
@@ -853,6 +1062,8 @@ frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, 
     if ((st = dag_grid(*d, fwd, ~0ull, &grid)) != FRAG_OK)
         return st;
     bp.resident_ctas = bp.max_ctas ? std::min(grid, bp.max_ctas) : grid;
+    if ((st = batch_fuse_slots(bp, *d)) != FRAG_OK)
+        return st;
     BatchPlan sizing = bp; // the layout does not depend on the scratch base
     fill_batch(sizing, nullptr);
     uint8_t *mem = nullptr;
@@ -895,6 +1106,8 @@ frag_status create_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, ui
     uint32_t grid = 0;
     if (st == FRAG_OK && (st = dag_grid(*d, fwd, ~0ull, &grid)) == FRAG_OK)
         bt->bp.resident_ctas = bt->bp.max_ctas ? std::min(grid, bt->bp.max_ctas) : grid;
+    if (st == FRAG_OK)
+        st = batch_fuse_slots(bt->bp, *d);
     if (st == FRAG_OK && !bt->bp.bufs.empty()) {
         BatchPlan sizing = bt->bp;
         fill_batch(sizing, nullptr);
@@ -1055,6 +1268,28 @@ frag_status frag_plan_get_schedule(frag_plan plan, uint32_t *seg_rows, uint32_t 
         *seg_rows = plan->seg_rows;
     if (ctas)
         *ctas = plan->max_ctas;
+    return FRAG_OK;
+}
+
+frag_status frag_plan_set_path(frag_plan plan, frag_path path)
+{
+    frag_status st = check_plan(plan);
+    if (st != FRAG_OK)
+        return st;
+    if (path != FRAG_PATH_AUTO && path != FRAG_PATH_LEVELS)
+        return fail(FRAG_EINVAL, "unknown path %d", (int)path);
+    plan->path = (uint32_t)path;
+    return FRAG_OK;
+}
+
+frag_status frag_plan_get_path(frag_plan plan, frag_path *path)
+{
+    frag_status st = check_plan(plan);
+    if (st != FRAG_OK)
+        return st;
+    if (path == nullptr)
+        return fail(FRAG_EINVAL, "path is NULL");
+    *path = (frag_path)plan->path;
     return FRAG_OK;
 }
 
@@ -1276,7 +1511,7 @@ frag_status frag_batch_info(frag_batch batch, uint32_t *launches, uint64_t *scra
         return fail(FRAG_EINVAL, "batch is NULL");
     uint32_t n = 0;
     for (const auto &wv : batch->bp.waves)
-        n += (wv.units.empty() ? 0 : 1) + (wv.chunks.empty() ? 0 : 1);
+        n += (wv.units.empty() ? 0 : 1) + (wv.chunks.empty() ? 0 : 1) + (wv.fbufs.empty() ? 0 : 1);
     if (launches)
         *launches = n;
     if (scratch_bytes)

@@ -172,6 +172,44 @@ cudaError_t launch_ctr(const CtrWork &w, uint32_t grid, cudaStream_t stream);
 cudaError_t ctr_occupancy(int *blocks_per_sm);
 constexpr uint32_t kCtrChunkList = 1024; // blocks per chunk of a chunk list
 
+// Fused levels (fused_kernels.cu): up to kFuseMaxLevels levels of a buffer
+// in one pass down its rows, no intermediate LL in memory.  A unit is one
+// warp strip (8 (31 - halo) level-0 columns) by seg_iters iterations of 8
+// level-0 rows; forward iteration t reads rows 8t-1 .. 8t+6, inverse
+// iteration t writes rows 8t-7 .. 8t.
+constexpr uint32_t kFuseMaxLevels = 3;
+constexpr int kFuseWarps = 4; // warps per CTA (each runs its own units)
+constexpr int kFuseDepth = 3; // shared-memory stages per warp (iterations)
+
+struct __align__(16) FuseBuf {
+    const uint8_t *src;   // forward: the n bytes
+    uint8_t *out;         // inverse: the n recovered bytes
+    uint8_t *band[3][3];  // [l - 1][HL, LH, HH] of level l = 1..F (int16 LE)
+    uint8_t *ll;          // LL_F: forward output, inverse input
+    uint64_t n;
+    uint64_t unit0;       // first unit of this buffer in the launch
+    uint32_t W, H;        // level-0 matrix
+    uint32_t F;           // levels fused (1..kFuseMaxLevels)
+    uint32_t ll_final;    // LL_F is LL_L - 128 as int16 (else biased 16-bit scratch)
+    uint32_t halo;        // lanes left of the owned ones
+    uint32_t strips;      // warp strips across W
+    uint32_t iters;       // iterations covering the matrix
+    uint32_t seg_iters;   // iterations per unit
+    uint32_t segs;        // units per strip
+    uint32_t pad;
+};
+static_assert(sizeof(FuseBuf) % 16 == 0, "fused buffer descriptors are copied in 16-byte pieces");
+
+struct FuseWork {
+    const FuseBuf *bufs; // device array (nbufs > 1), ordered by unit0
+    FuseBuf single;      // nbufs == 1
+    uint32_t nbufs;
+    uint64_t total_units;
+};
+
+cudaError_t launch_fuse(bool fwd, const FuseWork &w, uint32_t grid, cudaStream_t stream);
+cudaError_t fuse_occupancy(bool fwd, int *blocks_per_sm);
+
 // kernels (tile_kernels.cu)
 constexpr uint32_t kFastTile = 256;   // owned tile side of the row/column-pass body
 constexpr uint32_t kFastMaxLevels = 3;

@@ -31,8 +31,9 @@ def key(fr):
     return fr.Key(KEY)
 
 
-def gpu_round_trip(fr, key, data, W, L, nonce, tiling=None, offset=0):
+def gpu_round_trip(fr, key, data, W, L, nonce, tiling=None, offset=0, path=0):
     plan = fr.Plan(W, L)
+    plan.set_path(path)
     if tiling:
         plan.set_tiling(*tiling)
     n = data.size
@@ -51,10 +52,10 @@ def gpu_round_trip(fr, key, data, W, L, nonce, tiling=None, offset=0):
     return priv[offset:].cpu().numpy(), pub[offset:].cpu().numpy(), o[offset:offset + n]
 
 
-def check_against_oracle(fr, key, data, W, L, nonce=0, tiling=None, offset=0):
+def check_against_oracle(fr, key, data, W, L, nonce=0, tiling=None, offset=0, path=0):
     data = np.ascontiguousarray(data).reshape(-1)
     p_ref, u_ref = oracle.protect(data, W, L, KEY, nonce)
-    p, u, r = gpu_round_trip(fr, key, data, W, L, nonce, tiling, offset)
+    p, u, r = gpu_round_trip(fr, key, data, W, L, nonce, tiling, offset, path)
     assert np.array_equal(p, p_ref), "private fragment differs"
     if not np.array_equal(u, u_ref):
         bad = np.flatnonzero(u != u_ref)
@@ -81,10 +82,53 @@ SWEEP = [
 ]
 
 
+# path 0: fused levels where alignment allows (the default); 1: every level
+# in the dependency-ordered kernel
+@pytest.mark.parametrize("path", [0, 1])
 @pytest.mark.parametrize("n,W,L,tiling", SWEEP)
-def test_sweep_random(fr, key, n, W, L, tiling):
+def test_sweep_random(fr, key, n, W, L, tiling, path):
     data = wl.random_bytes(n, seed=n + W + L)
-    check_against_oracle(fr, key, data, W, L, nonce=n % 7, tiling=tiling)
+    check_against_oracle(fr, key, data, W, L, nonce=n % 7, tiling=tiling, path=path)
+
+
+# the fused kernel's segment height: from one 8-row iteration per unit (the
+# most warm-up per unit) up to long units, at one to three fused levels and
+# with levels above them in the level kernel
+@pytest.mark.parametrize("seg_rows", [16, 32, 64, 256])
+@pytest.mark.parametrize("n,W,L", [(4096 * 200 + 5, 4096, 3), (1000 * 333, 1000, 2),
+                                   (2048 * 97, 2048, 1), (512 * 512, 512, 5)])
+def test_fused_segments(fr, key, n, W, L, seg_rows):
+    data = wl.random_bytes(n, seed=seg_rows + L)
+    p_ref, u_ref = oracle.protect(data, W, L, KEY, 11)
+    plan = fr.Plan(W, L)
+    plan.set_schedule(seg_rows, 0)
+    _, pb, ub = plan.sizes(n)
+    d = torch.from_numpy(data).cuda()
+    priv = torch.empty(pb, dtype=torch.uint8, device="cuda")
+    pub = torch.empty(ub, dtype=torch.uint8, device="cuda")
+    out = torch.empty(n, dtype=torch.uint8, device="cuda")
+    fr.protect(plan, key, 11, d, n, priv, pub)
+    fr.recover(plan, key, 11, priv, pub, n, out)
+    fr.sync_status()
+    assert np.array_equal(priv.cpu().numpy(), p_ref)
+    assert np.array_equal(pub.cpu().numpy(), u_ref)
+    assert torch.equal(out, d)
+
+
+def test_path_selects_kernels(fr, key):
+    """Three fused levels take the fused launch and the CTR launch; the level
+    path takes one dependency-ordered launch with in-launch cipher units."""
+    n, W, L = 4096 * 64, 4096, 3
+    plan = fr.Plan(W, L)
+    _, pb, ub = plan.sizes(n)
+    d = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    priv = torch.empty(pb, dtype=torch.uint8, device="cuda")
+    pub = torch.empty(ub, dtype=torch.uint8, device="cuda")
+    assert plan.path() == fr.Plan.PATH_AUTO
+    assert fr.Batch([(plan, 0, n, d, priv, pub)], True).launches == 2
+    plan.set_path(fr.Plan.PATH_LEVELS)
+    assert plan.path() == fr.Plan.PATH_LEVELS
+    assert fr.Batch([(plan, 0, n, d, priv, pub)], True).launches == 1
 
 
 @pytest.mark.parametrize("n,W,L", [(12345, 128, 2), (4096, 64, 3), (77777, 256, 5)])
@@ -118,6 +162,11 @@ def test_c2_full(fr, key):
 def test_c3_full(fr, key, L):
     data = wl.c3()
     check_against_oracle(fr, key, data, wl.C3_WIDTH, L, nonce=0)
+
+
+def test_c2_full_level_path(fr, key):
+    planes = wl.c2()
+    check_against_oracle(fr, key, planes[0], 4096, 3, nonce=0, path=1)
 
 
 def test_zero_bytes_is_noop(fr, key):
