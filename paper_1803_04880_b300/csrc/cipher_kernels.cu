@@ -17,7 +17,6 @@
 namespace frag {
 
 constexpr int kCtrThreads = 256;
-constexpr uint32_t kCtrChunkBlocks = 1024; // blocks of one chunk of a lone fragment
 
 struct CtrSmem {
     uint32_t te[256 * 32]; // table 0, one copy per lane
@@ -78,15 +77,15 @@ __global__ void __launch_bounds__(kCtrThreads) ctr_kernel(CtrWork w)
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t nchunks = w.chunks ? w.nchunks
-                                      : (w.single.nblocks + kCtrChunkBlocks - 1) / kCtrChunkBlocks;
+                                      : (w.single.nblocks + w.single_chunk - 1) / w.single_chunk;
     for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         CtrChunk ch;
         if (w.chunks) {
             ch = w.chunks[c];
         } else {
             ch = w.single;
-            ch.first_block = c * kCtrChunkBlocks;
-            ch.nblocks = min((uint64_t)kCtrChunkBlocks, w.single.nblocks - ch.first_block);
+            ch.first_block = c * w.single_chunk;
+            ch.nblocks = min(w.single_chunk, w.single.nblocks - ch.first_block);
         }
         const bool vec = (((uintptr_t)ch.in | (uintptr_t)ch.out) & 15u) == 0;
         for (uint64_t i = threadIdx.x; i < ch.nblocks; i += blockDim.x) {

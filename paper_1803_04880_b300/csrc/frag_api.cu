@@ -559,10 +559,16 @@ frag_status ctr_launch(DeviceState &d, const uint32_t *rk, const frag::CtrChunk 
         w.single = *single;
     w.aes_tables = d.tables;
     w.round_keys = rk;
-    const uint64_t work = chunks ? nchunks : (single->nblocks + frag::kCtrChunkList - 1) / frag::kCtrChunkList;
+    const uint64_t slots = (uint64_t)d.sms * occ;
+    if (!chunks) {
+        // a lone fragment spread over every resident CTA, whole thread turns
+        const uint64_t per = (single->nblocks + slots - 1) / slots;
+        w.single_chunk = std::max<uint64_t>(256, (per + 255) / 256 * 256);
+    }
+    const uint64_t work = chunks ? nchunks : (single->nblocks + w.single_chunk - 1) / w.single_chunk;
     if (work == 0)
         return FRAG_OK;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)d.sms * occ, work);
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(slots, work);
     cudaError_t e = frag::launch_ctr(w, grid, s);
     if (e != cudaSuccess)
         return cuda_fail(e, "cipher launch");
@@ -616,6 +622,7 @@ frag::FuseBuf fuse_buf(bool fwd, const Buf &b)
     f.halo = (fwd && b.F == 3) ? 2 : 1;
     f.strips = (b.W + 8 * (31 - f.halo) - 1) / (8 * (31 - f.halo));
     f.iters = fwd ? b.H / 8 + 1 : (b.H + 6) / 8 + 1;
+    f.full_rows = (uint32_t)std::min<uint64_t>(b.n / b.W, b.H);
     return f;
 }
 

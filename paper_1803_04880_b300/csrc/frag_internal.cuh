@@ -164,6 +164,7 @@ struct CtrWork {
     const CtrChunk *chunks; // device array (nullptr: one fragment, `single`)
     uint64_t nchunks;
     CtrChunk single;
+    uint64_t single_chunk;      // blocks per CTA turn over `single`
     const uint32_t *aes_tables; // table 0 is the first 256 words
     const uint32_t *round_keys;
 };
@@ -196,7 +197,7 @@ struct __align__(16) FuseBuf {
     uint32_t iters;       // iterations covering the matrix
     uint32_t seg_iters;   // iterations per unit
     uint32_t segs;        // units per strip
-    uint32_t pad;
+    uint32_t full_rows;   // leading rows made only of data bytes (n / W)
 };
 static_assert(sizeof(FuseBuf) % 16 == 0, "fused buffer descriptors are copied in 16-byte pieces");
 

@@ -45,12 +45,10 @@ namespace fuse {
 
 using strm::from_i16x2;
 using strm::kB2;
-using strm::lift_row;
 using strm::pavg;
 using strm::pq4;
-using strm::Raw;
 using strm::to_i16x2;
-using strm::unlift_row;
+
 
 constexpr int kWarps = kFuseWarps;
 constexpr int kThreads = 32 * kWarps;
@@ -116,84 +114,140 @@ __device__ __forceinline__ void st2(uint8_t *band, uint64_t idx, uint32_t a)
 }
 
 // ---------------------------------------------------------------------------
-// row lifting of the coarser levels
+// row lifting with the borders folded into byte-permute selectors
+//
+// With W a multiple of 8 a lane's 8 level-0 columns are all inside the row
+// or all outside, so only two lanes of a strip meet a border at any level:
+// the lane holding column 0 (left: d[-1] = d[0]) and the lane holding the
+// last 8 columns (right: x[m] = x[m-2]).  Each lane keeps two selectors for
+// the whole unit: sL picks (d[-1], d0) or (d0, d0), sR picks (x[m-2], x[m])
+// or (x[m-2], x[m-2]); the other permutes never change.
 // ---------------------------------------------------------------------------
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint32_t kSelNext = 0x5432; // (high half of a, low half of b)
+constexpr uint32_t kSelRight = 0x3232; // high half of a, twice
+constexpr uint32_t kSelLeft = 0x5454;  // low half of b, twice
 
-// Level-2 row lift of the lane's four LL_1 samples y0..y3 (columns c .. c+3
-// of a row of Wd samples; w0 = (y0, y1), w1 = (y2, y3)): L = (s0, s1),
-// H = (d0, d1).  y4 and d[-1] come from the adjacent lanes.
-__device__ __forceinline__ void lift4(uint32_t w0, uint32_t w1, int c, int Wd, bool edge,
+struct Lane {
+    int c0;         // level-0 column of the lane's first sample
+    bool loads;     // the lane's columns are inside the matrix
+    bool own;       // the lane's results belong to this strip
+    bool first;     // the lane holds column 0
+    bool last;      // the lane holds the last 8 columns
+    uint32_t sL, sR;
+};
+
+__device__ __forceinline__ Lane make_lane(const FuseBuf &b, uint32_t sx, int lane)
+{
+    Lane ln;
+    const int h = (int)b.halo;
+    ln.c0 = (int)sx * 8 * (31 - h) + 8 * (lane - h);
+    ln.loads = ln.c0 >= 0 && ln.c0 < (int)b.W;
+    ln.own = lane >= h && lane <= 30 && ln.c0 < (int)b.W;
+    ln.first = ln.c0 == 0;
+    ln.last = ln.c0 + 8 == (int)b.W;
+    ln.sL = ln.first ? kSelLeft : kSelNext;
+    ln.sR = ln.last ? kSelRight : kSelNext;
+    return ln;
+}
+
+// Level-1 row lift of the lane's 8 bytes (w0, w1) = x0..x7: P[0] = (s0, s1),
+// P[1] = (s2, s3), P[2] = (d0, d1), P[3] = (d2, d3), biased; x8 and d[-1]
+// come from the adjacent lanes
+__device__ __forceinline__ void lift8(uint32_t w0, uint32_t w1, uint32_t sR, uint32_t sL,
+                                      uint32_t (&P)[4])
+{
+    // bytes into 16-bit halves with 0x40 as the high byte: v + 0x4000
+    const uint32_t e01 = __byte_perm(w0, 0x40404040u, 0x4240);
+    const uint32_t o01 = __byte_perm(w0, 0x40404040u, 0x4341);
+    const uint32_t e23 = __byte_perm(w1, 0x40404040u, 0x4240);
+    const uint32_t o23 = __byte_perm(w1, 0x40404040u, 0x4341);
+    const uint32_t e01n = __shfl_down_sync(kFull, e01, 1);
+    const uint32_t e12 = __byte_perm(e01, e23, kSelNext); // (x2, x4)
+    const uint32_t e34 = __byte_perm(e23, e01n, sR);      // (x6, x8)
+    const uint32_t d01 = o01 - pavg(e01, e12) + kB2;      // Eq. 5.1
+    const uint32_t d23 = o23 - pavg(e23, e34) + kB2;
+    const uint32_t d23p = __shfl_up_sync(kFull, d23, 1);
+    const uint32_t dm0 = __byte_perm(d23p, d01, sL);      // (d[-1], d0)
+    const uint32_t d12 = __byte_perm(d01, d23, kSelNext); // (d1, d2)
+    P[0] = e01 + pq4(dm0, d01) - 0x20002000u;             // Eq. 5.2
+    P[1] = e23 + pq4(d12, d23) - 0x20002000u;
+    P[2] = d01;
+    P[3] = d23;
+}
+
+// Level-1 row inverse: w[0..1] = L words, w[2..3] = H words -> the 8 bytes
+__device__ __forceinline__ uint2 unlift8(const uint32_t (&w)[4], uint32_t sR, uint32_t sL)
+{
+    const uint32_t h23p = __shfl_up_sync(kFull, w[3], 1);
+    const uint32_t hm0 = __byte_perm(h23p, w[2], sL); // (d[-1], d0)
+    const uint32_t h12 = __byte_perm(w[2], w[3], kSelNext);
+    const uint32_t e01 = w[0] - pq4(hm0, w[2]) + 0x20002000u; // undo Eq. 5.2
+    const uint32_t e23 = w[1] - pq4(h12, w[3]) + 0x20002000u;
+    const uint32_t e01n = __shfl_down_sync(kFull, e01, 1);
+    const uint32_t e12 = __byte_perm(e01, e23, kSelNext);
+    const uint32_t e34 = __byte_perm(e23, e01n, sR);
+    const uint32_t o01 = w[2] + pavg(e01, e12) - kB2; // undo Eq. 5.1
+    const uint32_t o23 = w[3] + pavg(e23, e34) - kB2;
+    // biased halves: the low byte of each is the recovered byte
+    return make_uint2(__byte_perm(e01, o01, 0x6240), __byte_perm(e23, o23, 0x6240));
+}
+
+// Level-2 row lift of the lane's four LL_1 samples (w0 = (y0, y1),
+// w1 = (y2, y3)): L = (s0, s1), H = (d0, d1)
+__device__ __forceinline__ void lift4(uint32_t w0, uint32_t w1, uint32_t sR, uint32_t sL,
                                       uint32_t &L, uint32_t &H)
 {
     const uint32_t e = __byte_perm(w0, w1, 0x5410); // (y0, y2)
     const uint32_t o = __byte_perm(w0, w1, 0x7632); // (y1, y3)
-    const uint32_t en = __shfl_down_sync(0xffffffffu, e, 1);
-    uint32_t es = __byte_perm(e, en, 0x5432); // (y2, y4)
-    if (edge) {                               // x[m] = x[m-2]
-        if (c + 2 == Wd)
-            es = __byte_perm(e, es, 0x7610);
-        if (c + 4 == Wd)
-            es = __byte_perm(es, e, 0x7610);
-    }
-    const uint32_t d = o - pavg(e, es) + kB2; // Eq. 5.1
-    const uint32_t dpl = __shfl_up_sync(0xffffffffu, d, 1);
-    uint32_t dm = __byte_perm(dpl, d, 0x5432); // (d[-1], d0)
-    if (c == 0)
-        dm = __byte_perm(d, d, 0x1010); // d[-1] = d[0]
-    L = e + pq4(dm, d) - 0x20002000u;   // Eq. 5.2
+    const uint32_t en = __shfl_down_sync(kFull, e, 1);
+    const uint32_t es = __byte_perm(e, en, sR);    // (y2, y4)
+    const uint32_t d = o - pavg(e, es) + kB2;      // Eq. 5.1
+    const uint32_t dpl = __shfl_up_sync(kFull, d, 1);
+    const uint32_t dm = __byte_perm(dpl, d, sL);   // (d[-1], d0)
+    L = e + pq4(dm, d) - 0x20002000u;              // Eq. 5.2
     H = d;
 }
 
-// Level-3 row lift of the lane's two LL_2 samples z = (z0, z1) at columns
-// c, c+1: returns (s, d) of the pair in one word (s low, d high).
-__device__ __forceinline__ uint32_t lift2(uint32_t z, int c, int Wd, bool edge)
+// Level-2 row inverse: L = (s0, s1), H = (d0, d1) -> w0 = (y0, y1), w1 = (y2, y3)
+__device__ __forceinline__ void unlift4(uint32_t L, uint32_t H, uint32_t sR, uint32_t sL,
+                                        uint32_t &w0, uint32_t &w1)
 {
-    const uint32_t zn = __shfl_down_sync(0xffffffffu, z, 1);
+    const uint32_t hp = __shfl_up_sync(kFull, H, 1);
+    const uint32_t hm = __byte_perm(hp, H, sL);      // (d[-1], d0)
+    const uint32_t e = L - pq4(hm, H) + 0x20002000u; // undo Eq. 5.2: (y0, y2)
+    const uint32_t en = __shfl_down_sync(kFull, e, 1);
+    const uint32_t es = __byte_perm(e, en, sR);      // (y2, y4)
+    const uint32_t o = H + pavg(e, es) - kB2;        // undo Eq. 5.1: (y1, y3)
+    w0 = __byte_perm(e, o, 0x5410);
+    w1 = __byte_perm(e, o, 0x7632);
+}
+
+// Level-3 row lift of the lane's two LL_2 samples z = (z0, z1): returns
+// (s, d) of the pair in one word (s low, d high)
+__device__ __forceinline__ uint32_t lift2(uint32_t z, bool first, bool last)
+{
+    const uint32_t zn = __shfl_down_sync(kFull, z, 1);
     const uint32_t e = z & 0xffffu, o = z >> 16;
-    const uint32_t en = (edge && c + 2 == Wd) ? e : (zn & 0xffffu);
+    const uint32_t en = last ? e : (zn & 0xffffu);
     const uint32_t d = o - ((e + en) >> 1) + 0x4000u; // Eq. 5.1
-    uint32_t dp = __shfl_up_sync(0xffffffffu, d, 1);
-    if (c == 0)
-        dp = d;
+    const uint32_t dpl = __shfl_up_sync(kFull, d, 1);
+    const uint32_t dp = first ? d : dpl;
     const uint32_t s = e + ((dp + d + 2) >> 2) - 0x2000u; // Eq. 5.2
     return s | (d << 16);
 }
 
 // Level-3 row inverse: (s, d) word of a row-lifted LL_2 row -> (z0, z1)
-__device__ __forceinline__ uint32_t unlift2(uint32_t w, int c, int Wd, bool edge)
+__device__ __forceinline__ uint32_t unlift2(uint32_t w, bool first, bool last)
 {
     const uint32_t s = w & 0xffffu, d = w >> 16;
-    uint32_t dp = __shfl_up_sync(0xffffffffu, d, 1);
-    if (c == 0)
-        dp = d;
+    const uint32_t dpl = __shfl_up_sync(kFull, d, 1);
+    const uint32_t dp = first ? d : dpl;
     const uint32_t z0 = s - ((dp + d + 2) >> 2) + 0x2000u; // undo Eq. 5.2
-    uint32_t zn = __shfl_down_sync(0xffffffffu, z0, 1);
-    if (edge && c + 2 == Wd)
-        zn = z0;
-    const uint32_t z1 = d + ((z0 + zn) >> 1) - 0x4000u; // undo Eq. 5.1
+    const uint32_t zn = __shfl_down_sync(kFull, z0, 1);
+    const uint32_t z2 = last ? z0 : zn;
+    const uint32_t z1 = d + ((z0 + z2) >> 1) - 0x4000u; // undo Eq. 5.1
     return z0 | (z1 << 16);
-}
-
-// Level-2 row inverse: L = (s0, s1), H = (d0, d1) -> w0 = (y0, y1), w1 = (y2, y3)
-__device__ __forceinline__ void unlift4(uint32_t L, uint32_t H, int c, int Wd, bool edge,
-                                        uint32_t &w0, uint32_t &w1)
-{
-    const uint32_t hp = __shfl_up_sync(0xffffffffu, H, 1);
-    uint32_t hm = __byte_perm(hp, H, 0x5432); // (d[-1], d0)
-    if (c == 0)
-        hm = __byte_perm(H, H, 0x1010);
-    const uint32_t e = L - pq4(hm, H) + 0x20002000u; // undo Eq. 5.2: (y0, y2)
-    const uint32_t en = __shfl_down_sync(0xffffffffu, e, 1);
-    uint32_t es = __byte_perm(e, en, 0x5432); // (y2, y4)
-    if (edge) {
-        if (c + 2 == Wd)
-            es = __byte_perm(e, es, 0x7610);
-        if (c + 4 == Wd)
-            es = __byte_perm(es, e, 0x7610);
-    }
-    const uint32_t o = H + pavg(e, es) - kB2; // undo Eq. 5.1: (y1, y3)
-    w0 = __byte_perm(e, o, 0x5410);
-    w1 = __byte_perm(e, o, 0x7632);
 }
 
 // ---------------------------------------------------------------------------
@@ -201,18 +255,27 @@ __device__ __forceinline__ void unlift4(uint32_t L, uint32_t H, int c, int Wd, b
 // ---------------------------------------------------------------------------
 
 // the level-0 rows of iteration t into its stage: rows 8t-1 .. 8t+6
-__device__ __forceinline__ void fwd_issue(const FuseBuf &b, int t, int t_end, int c0, bool loads,
+__device__ __forceinline__ void fwd_issue(const FuseBuf &b, const Lane &ln, int t, int t_end,
                                           uint32_t ring_lane)
 {
-    if (t < t_end && loads) {
+    if (t < t_end && ln.loads) {
         const uint32_t st = ring_lane + (uint32_t)(t % kDepth) * kFwdStage;
+        const int r0 = 8 * t - 1;
+        if (r0 >= 0 && r0 + 8 <= (int)b.full_rows) { // eight whole rows of data
+            const uint8_t *p = b.src + (uint64_t)r0 * b.W + (uint64_t)ln.c0;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int r = 8 * t - 1 + j;
-            if (r >= 0 && r < (int)b.H) {
-                const uint64_t off = (uint64_t)r * b.W + (uint64_t)c0;
-                const uint32_t bytes = off >= b.n ? 0u : (uint32_t)(b.n - off < 8 ? b.n - off : 8);
-                cp8(st + 256 * j, bytes ? b.src + off : b.src, bytes);
+            for (int j = 0; j < 8; ++j)
+                cp8(st + 256 * j, p + (uint64_t)j * b.W, 8);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int r = r0 + j;
+                if (r >= 0 && r < (int)b.H) {
+                    const uint64_t off = (uint64_t)r * b.W + (uint64_t)ln.c0;
+                    const uint32_t bytes =
+                        off >= b.n ? 0u : (uint32_t)(b.n - off < 8 ? b.n - off : 8);
+                    cp8(st + 256 * j, bytes ? b.src + off : b.src, bytes);
+                }
             }
         }
     }
@@ -222,153 +285,161 @@ __device__ __forceinline__ void fwd_issue(const FuseBuf &b, int t, int t_end, in
 // LL_F of the final level: LL - 128 as int16 (both halves of each word)
 __device__ __forceinline__ uint32_t ll_final(uint32_t w) { return to_i16x2(w - 0x00800080u); }
 
-__device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t sy, uint32_t ring_lane,
-                                      int lane)
+struct FwdState {
+    uint32_t e0[4], dp[4]; // level 1: even row, d of the previous pair
+    uint32_t e2L, e2H, p2L, p2H;
+    uint32_t e3, p3;
+};
+
+// One iteration (rows 8t-1 .. 8t+6 in stage st).  CHECK: the iteration may
+// meet the top (a level's row 0) or the bottom (a level's last row) of the
+// matrix; no other iteration does, and none stores a row outside it.
+template <bool CHECK>
+__device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t, uint32_t st,
+                                         bool store, FwdState &S)
 {
-    const int h = (int)b.halo;
-    const int SW = 8 * (31 - h);
     const int W = (int)b.W, H = (int)b.H, F = (int)b.F;
-    const int c0 = (int)sx * SW + 8 * (lane - h);
-    const bool loads = c0 >= 0 && c0 < W;
-    const bool own = lane >= h && lane <= 30 && c0 < W;
-    const bool edge = (int)sx * SW + 8 * (32 - h) >= W;
     const int W1 = W >> 1, H1 = H >> 1, W2 = W >> 2, H2 = H >> 2, W3 = W >> 3, H3 = H >> 3;
-    const int c1 = c0 >> 1, c2 = c0 >> 2, c3 = c0 >> 3;
     const bool fin = b.ll_final != 0;
+    uint2 raw[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        raw[j] = lds8(st + 256 * j);
+
+    // level 1: pairs (8t-1+2j, 8t+2j) -> level-1 row 4t-1+j
+    uint32_t y[4][2];
+    const uint64_t col1 = (uint64_t)(ln.c0 >> 1);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t Po[4], Pe[4];
+        lift8(raw[2 * j].x, raw[2 * j].y, ln.sR, ln.sL, Po);
+        lift8(raw[2 * j + 1].x, raw[2 * j + 1].y, ln.sR, ln.sL, Pe);
+        const int q = 4 * t - 1 + j;
+        if (CHECK && 8 * t + 2 * j == H) { // x[m] = x[m-2] at the bottom border
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                Pe[k] = S.e0[k];
+        }
+        uint32_t dv[4], sv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            dv[k] = Po[k] - pavg(S.e0[k], Pe[k]) + kB2; // Eq. 5.1 down the columns
+        if (CHECK && q == 0) {                          // d[-1] = d[0] at the top border
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                S.dp[k] = dv[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            sv[k] = S.e0[k] + pq4(S.dp[k], dv[k]) - 0x20002000u; // Eq. 5.2 down the columns
+            S.e0[k] = Pe[k];
+            S.dp[k] = dv[k];
+        }
+        if (store && (!CHECK || (unsigned)q < (unsigned)H1)) {
+            const uint64_t idx = (uint64_t)q * (uint64_t)W1 + col1;
+            st8(b.band[0][0], idx, to_i16x2(sv[2]), to_i16x2(sv[3])); // HL_1
+            st8(b.band[0][1], idx, to_i16x2(dv[0]), to_i16x2(dv[1])); // LH_1
+            st8(b.band[0][2], idx, to_i16x2(dv[2]), to_i16x2(dv[3])); // HH_1
+            if (F == 1) {
+                if (fin)
+                    st8(b.ll, idx, ll_final(sv[0]), ll_final(sv[1]));
+                else
+                    st8(b.ll, idx, sv[0], sv[1]);
+            }
+        }
+        y[j][0] = sv[0];
+        y[j][1] = sv[1];
+    }
+    if (F < 2)
+        return;
+
+    // level 2: LL_1 pairs (4t-1+2k, 4t+2k) -> level-2 row 2t-1+k
+    uint32_t z[2];
+    const uint64_t col2 = (uint64_t)(ln.c0 >> 2);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        uint32_t Lo, Ho, Le, He;
+        lift4(y[2 * k][0], y[2 * k][1], ln.sR, ln.sL, Lo, Ho);
+        lift4(y[2 * k + 1][0], y[2 * k + 1][1], ln.sR, ln.sL, Le, He);
+        const int q2 = 2 * t - 1 + k;
+        if (CHECK && 4 * t + 2 * k == H1) {
+            Le = S.e2L;
+            He = S.e2H;
+        }
+        const uint32_t dL = Lo - pavg(S.e2L, Le) + kB2, dH = Ho - pavg(S.e2H, He) + kB2;
+        if (CHECK && q2 == 0) {
+            S.p2L = dL;
+            S.p2H = dH;
+        }
+        const uint32_t sL = S.e2L + pq4(S.p2L, dL) - 0x20002000u;
+        const uint32_t sH = S.e2H + pq4(S.p2H, dH) - 0x20002000u;
+        S.e2L = Le;
+        S.e2H = He;
+        S.p2L = dL;
+        S.p2H = dH;
+        if (store && (!CHECK || (unsigned)q2 < (unsigned)H2)) {
+            const uint64_t idx = (uint64_t)q2 * (uint64_t)W2 + col2;
+            st4(b.band[1][0], idx, to_i16x2(sH)); // HL_2
+            st4(b.band[1][1], idx, to_i16x2(dL)); // LH_2
+            st4(b.band[1][2], idx, to_i16x2(dH)); // HH_2
+            if (F == 2)
+                st4(b.ll, idx, fin ? ll_final(sL) : sL);
+        }
+        z[k] = sL;
+    }
+    if (F < 3)
+        return;
+
+    // level 3: LL_2 pair (2t-1, 2t) -> level-3 row t-1
+    const uint32_t wo = lift2(z[0], ln.first, ln.last);
+    uint32_t we = lift2(z[1], ln.first, ln.last);
+    const int q3 = t - 1;
+    if (CHECK && 2 * t == H2)
+        we = S.e3;
+    const uint32_t d3 = wo - pavg(S.e3, we) + kB2;
+    if (CHECK && q3 == 0)
+        S.p3 = d3;
+    const uint32_t s3 = S.e3 + pq4(S.p3, d3) - 0x20002000u;
+    S.e3 = we;
+    S.p3 = d3;
+    if (store && (!CHECK || (unsigned)q3 < (unsigned)H3)) {
+        const uint64_t idx = (uint64_t)q3 * (uint64_t)W3 + (uint64_t)(ln.c0 >> 3);
+        const uint32_t sw = to_i16x2(s3), dw = to_i16x2(d3);
+        st2(b.band[2][0], idx, sw >> 16); // HL_3
+        st2(b.band[2][1], idx, dw);       // LH_3
+        st2(b.band[2][2], idx, dw >> 16); // HH_3
+        st2(b.ll, idx, fin ? ll_final(s3) : s3);
+    }
+}
+
+__device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t sy, uint32_t ring_lane,
+                                         int lane)
+{
+    const Lane ln = make_lane(b, sx, lane);
     const int t_begin = (int)(sy * b.seg_iters);
     const int t_end = min(t_begin + (int)b.seg_iters, (int)b.iters);
-    const int t_first = max(t_begin - F, 0);
+    const int t_first = max(t_begin - (int)b.F, 0);
+    const int t_fast_end = (int)b.iters - 2; // iterations t >= 2 and below this skip the checks
 
 #pragma unroll
     for (int k = 0; k < kDepth - 1; ++k)
-        fwd_issue(b, t_first + k, t_end, c0, loads, ring_lane);
+        fwd_issue(b, ln, t_first + k, t_end, ring_lane);
 
-    uint32_t e0[4], dp[4], e2L = kB2, e2H = kB2, p2L = kB2, p2H = kB2, e3 = kB2, p3 = kB2;
+    FwdState S;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        e0[k] = dp[k] = kB2;
+        S.e0[k] = S.dp[k] = kB2;
+    S.e2L = S.e2H = S.p2L = S.p2H = S.e3 = S.p3 = kB2;
 
     for (int t = t_first; t < t_end; ++t) {
-        fwd_issue(b, t + kDepth - 1, t_end, c0, loads, ring_lane);
+        fwd_issue(b, ln, t + kDepth - 1, t_end, ring_lane);
         cp_wait<kDepth - 1>();
         const uint32_t st = ring_lane + (uint32_t)(t % kDepth) * kFwdStage;
-        uint2 raw[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            raw[j] = lds8(st + 256 * j);
-        const bool store = own && t >= t_begin;
-
-        // level 1: pairs (8t-1+2j, 8t+2j) -> level-1 row 4t-1+j
-        uint32_t y[4][2];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            Raw ro, re;
-            ro.w[0] = raw[2 * j].x;
-            ro.w[1] = raw[2 * j].y;
-            ro.w[2] = ro.w[3] = 0;
-            re.w[0] = raw[2 * j + 1].x;
-            re.w[1] = raw[2 * j + 1].y;
-            re.w[2] = re.w[3] = 0;
-            uint32_t Po[4], Pe[4];
-            lift_row<true, true>(ro, c0, W, edge, Po);
-            lift_row<true, true>(re, c0, W, edge, Pe);
-            const int q = 4 * t - 1 + j;
-            if (8 * t + 2 * j == H) { // x[m] = x[m-2] at the bottom border
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    Pe[k] = e0[k];
-            }
-            uint32_t dv[4], sv[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                dv[k] = Po[k] - pavg(e0[k], Pe[k]) + kB2; // Eq. 5.1 down the columns
-            if (q == 0) {                                 // d[-1] = d[0] at the top border
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    dp[k] = dv[k];
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                sv[k] = e0[k] + pq4(dp[k], dv[k]) - 0x20002000u; // Eq. 5.2 down the columns
-                e0[k] = Pe[k];
-                dp[k] = dv[k];
-            }
-            if (store && (unsigned)q < (unsigned)H1) {
-                const uint64_t idx = (uint64_t)q * (uint64_t)W1 + (uint64_t)c1;
-                st8(b.band[0][0], idx, to_i16x2(sv[2]), to_i16x2(sv[3])); // HL_1
-                st8(b.band[0][1], idx, to_i16x2(dv[0]), to_i16x2(dv[1])); // LH_1
-                st8(b.band[0][2], idx, to_i16x2(dv[2]), to_i16x2(dv[3])); // HH_1
-                if (F == 1) {
-                    if (fin)
-                        st8(b.ll, idx, ll_final(sv[0]), ll_final(sv[1]));
-                    else
-                        st8(b.ll, idx, sv[0], sv[1]);
-                }
-            }
-            y[j][0] = sv[0];
-            y[j][1] = sv[1];
-        }
-        if (F < 2)
-            continue;
-
-        // level 2: LL_1 pairs (4t-1+2k, 4t+2k) -> level-2 row 2t-1+k
-        uint32_t z[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            uint32_t Lo, Ho, Le, He;
-            lift4(y[2 * k][0], y[2 * k][1], c1, W1, edge, Lo, Ho);
-            lift4(y[2 * k + 1][0], y[2 * k + 1][1], c1, W1, edge, Le, He);
-            const int q2 = 2 * t - 1 + k;
-            if (4 * t + 2 * k == H1) {
-                Le = e2L;
-                He = e2H;
-            }
-            const uint32_t dL = Lo - pavg(e2L, Le) + kB2, dH = Ho - pavg(e2H, He) + kB2;
-            if (q2 == 0) {
-                p2L = dL;
-                p2H = dH;
-            }
-            const uint32_t sL = e2L + pq4(p2L, dL) - 0x20002000u;
-            const uint32_t sH = e2H + pq4(p2H, dH) - 0x20002000u;
-            e2L = Le;
-            e2H = He;
-            p2L = dL;
-            p2H = dH;
-            if (store && (unsigned)q2 < (unsigned)H2) {
-                const uint64_t idx = (uint64_t)q2 * (uint64_t)W2 + (uint64_t)c2;
-                st4(b.band[1][0], idx, to_i16x2(sH)); // HL_2
-                st4(b.band[1][1], idx, to_i16x2(dL)); // LH_2
-                st4(b.band[1][2], idx, to_i16x2(dH)); // HH_2
-                if (F == 2)
-                    st4(b.ll, idx, fin ? ll_final(sL) : sL);
-            }
-            z[k] = sL;
-        }
-        if (F < 3)
-            continue;
-
-        // level 3: LL_2 pair (2t-1, 2t) -> level-3 row t-1
-        {
-            const uint32_t wo = lift2(z[0], c2, W2, edge);
-            uint32_t we = lift2(z[1], c2, W2, edge);
-            const int q3 = t - 1;
-            if (2 * t == H2)
-                we = e3;
-            const uint32_t d3 = wo - pavg(e3, we) + kB2;
-            if (q3 == 0)
-                p3 = d3;
-            const uint32_t s3 = e3 + pq4(p3, d3) - 0x20002000u;
-            e3 = we;
-            p3 = d3;
-            if (store && (unsigned)q3 < (unsigned)H3) {
-                const uint64_t idx = (uint64_t)q3 * (uint64_t)W3 + (uint64_t)c3;
-                const uint32_t sw = to_i16x2(s3), dw = to_i16x2(d3);
-                st2(b.band[2][0], idx, sw >> 16); // HL_3
-                st2(b.band[2][1], idx, dw);       // LH_3
-                st2(b.band[2][2], idx, dw >> 16); // HH_3
-                st2(b.ll, idx, fin ? ll_final(s3) : s3);
-            }
-        }
+        const bool store = ln.own && t >= t_begin;
+        if (t >= 2 && t < t_fast_end)
+            fwd_iter<false>(b, ln, t, st, store, S);
+        else
+            fwd_iter<true>(b, ln, t, st, store, S);
     }
     cp_wait<0>();
 }
@@ -377,48 +448,79 @@ __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t
 // inverse unit
 // ---------------------------------------------------------------------------
 
-// int16 word(s) of the input -> biased values; LL_L - 128 gets its 128 back
+// int16 word(s) of the input -> biased values
 __device__ __forceinline__ uint32_t in16(uint32_t w) { return from_i16x2(w); }
 
 // the coefficient rows iteration t consumes, into its stage
-__device__ __forceinline__ void inv_issue(const FuseBuf &b, int t, int t_end, int c0, bool loads,
+__device__ __forceinline__ void inv_issue(const FuseBuf &b, const Lane &ln, int t, int t_end,
                                           uint32_t ring8, uint32_t ring4)
 {
-    if (t < t_end && loads) {
+    if (t < t_end && ln.loads) {
         const int F = (int)b.F;
         const uint32_t so = (uint32_t)(t % kDepth) * kInvStage;
         const uint32_t W1 = b.W >> 1, H1 = b.H >> 1, W2 = b.W >> 2, H2 = b.H >> 2;
-        const uint32_t c1 = (uint32_t)c0 >> 1, c2 = (uint32_t)c0 >> 2;
+        const uint32_t c1 = (uint32_t)ln.c0 >> 1, c2 = (uint32_t)ln.c0 >> 2;
+        // every row of the iteration inside its level: no per-row tests
+        const bool inside = t >= 1 && 4 * t < (int)H1 && (F < 2 || 2 * t < (int)H2) &&
+                            (F < 3 || t < (int)(b.H >> 3));
+        if (inside) {
+            const uint64_t o1 = 2ull * ((uint64_t)(4 * t - 3) * W1 + c1);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int q = 4 * t - 3 + j;
-            if (q >= 0 && q < (int)H1) {
-                const uint64_t off = 2ull * ((uint64_t)q * W1 + c1);
+            for (int j = 0; j < 4; ++j)
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
-                    cp8(ring8 + so + 256 * (3 * j + k), b.band[0][k] + off, 8);
-                if (F == 1)
-                    cp8(ring8 + so + kInvX + 256 * j, b.ll + off, 8);
-            }
-        }
-        if (F >= 2) {
+                    cp8(ring8 + so + 256 * (3 * j + k), b.band[0][k] + o1 + 2ull * j * W1, 8);
+            if (F == 1) {
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int q = 2 * t - 1 + k;
-                if (q >= 0 && q < (int)H2) {
-                    const uint64_t off = 2ull * ((uint64_t)q * W2 + c2);
+                for (int j = 0; j < 4; ++j)
+                    cp8(ring8 + so + kInvX + 256 * j, b.ll + o1 + 2ull * j * W1, 8);
+            } else {
+                const uint64_t o2 = 2ull * ((uint64_t)(2 * t - 1) * W2 + c2);
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
 #pragma unroll
                     for (int m = 0; m < 3; ++m)
-                        cp4(ring4 + so + kInvX + 128 * (3 * k + m), b.band[1][m] + off, 4);
-                    if (F == 2)
-                        cp4(ring4 + so + kInvL2Ll + 128 * k, b.ll + off, 4);
+                        cp4(ring4 + so + kInvX + 128 * (3 * k + m), b.band[1][m] + o2 + 2ull * k * W2, 4);
+                if (F == 2) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k)
+                        cp4(ring4 + so + kInvL2Ll + 128 * k, b.ll + o2 + 2ull * k * W2, 4);
+                }
+            }
+        } else {
+            const uint64_t off = 2ull * ((uint64_t)(4 * t - 3) * W1 + c1);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int q = 4 * t - 3 + j;
+                if (q >= 0 && q < (int)H1) {
+                    const uint64_t o = off + 2ull * j * W1;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        cp8(ring8 + so + 256 * (3 * j + k), b.band[0][k] + o, 8);
+                    if (F == 1)
+                        cp8(ring8 + so + kInvX + 256 * j, b.ll + o, 8);
+                }
+            }
+            if (F >= 2) {
+                const uint64_t off2 = 2ull * ((uint64_t)(2 * t - 1) * W2 + c2);
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int q = 2 * t - 1 + k;
+                    if (q >= 0 && q < (int)H2) {
+                        const uint64_t o = off2 + 2ull * k * W2;
+#pragma unroll
+                        for (int m = 0; m < 3; ++m)
+                            cp4(ring4 + so + kInvX + 128 * (3 * k + m), b.band[1][m] + o, 4);
+                        if (F == 2)
+                            cp4(ring4 + so + kInvL2Ll + 128 * k, b.ll + o, 4);
+                    }
                 }
             }
         }
-        if (F == 3 && t < (int)(b.H >> 3)) {
+        if (F == 3 && (inside || t < (int)(b.H >> 3))) {
             // one int16 per lane: copy the aligned word that holds it (band
             // bases are 4-byte aligned, so the word stays inside the band)
-            const uint64_t e = (uint64_t)t * (b.W >> 3) + ((uint32_t)c0 >> 3);
+            const uint64_t e = (uint64_t)t * (b.W >> 3) + ((uint32_t)ln.c0 >> 3);
             const uint64_t off = 2ull * (e & ~1ull);
             const uint32_t bytes = (e & 1ull) ? 4u : 2u;
 #pragma unroll
@@ -434,143 +536,159 @@ __device__ __forceinline__ void inv_issue(const FuseBuf &b, int t, int t_end, in
 // lane): xe = x[2q], xo = x[2q-1]; (xp, dp) = (x[2q-2], d[q-1]) carried.
 // top: q == 0 (d[-1] = d[0]); bottom: q is one past the last row (x[2q] =
 // x[2q-2], only the odd row is real)
+template <bool CHECK>
 __device__ __forceinline__ void col_inv(uint32_t s, uint32_t d, bool top, bool bottom, uint32_t &xp,
                                         uint32_t &dp, uint32_t &xo, uint32_t &xe)
 {
-    if (top)
+    if (CHECK && top)
         dp = d;
-    xe = bottom ? xp : s - pq4(dp, d) + 0x20002000u; // undo Eq. 5.2
-    xo = dp + pavg(xp, xe) - kB2;                    // undo Eq. 5.1
+    xe = (CHECK && bottom) ? xp : s - pq4(dp, d) + 0x20002000u; // undo Eq. 5.2
+    xo = dp + pavg(xp, xe) - kB2;                              // undo Eq. 5.1
     xp = xe;
     dp = d;
 }
 
-// 8 recovered bytes of row r at column c0 (biased halves: the low byte of
-// each is the byte)
-__device__ __forceinline__ void store_bytes(const FuseBuf &b, int r, int c0, const uint32_t (&p)[4])
+// 8 recovered bytes of row r at the lane's columns
+__device__ __forceinline__ void store_bytes(const FuseBuf &b, const Lane &ln, int r, uint2 v)
 {
-    const uint64_t g = (uint64_t)r * b.W + (uint64_t)c0;
-    if (g >= b.n)
-        return;
-    const uint32_t w0 = __byte_perm(p[0], p[1], 0x6420);
-    const uint32_t w1 = __byte_perm(p[2], p[3], 0x6420);
+    const uint64_t g = (uint64_t)r * b.W + (uint64_t)ln.c0;
     if (g + 8 <= b.n) {
-        __stcs(reinterpret_cast<uint2 *>(b.out + g), make_uint2(w0, w1));
+        __stcs(reinterpret_cast<uint2 *>(b.out + g), v);
     } else {
         for (int i = 0; i < 8 && g + (uint64_t)i < b.n; ++i)
-            b.out[g + i] = (uint8_t)((i < 4 ? w0 : w1) >> (8 * (i & 3)));
+            b.out[g + i] = (uint8_t)((i < 4 ? v.x : v.y) >> (8 * (i & 3)));
+    }
+}
+
+struct InvState {
+    uint32_t x1[4], d1[4]; // level 1: x[2q-2] and d[q-1] of each word
+    uint32_t x2[2], d2[2];
+    uint32_t x3, d3;
+};
+
+template <bool CHECK>
+__device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t, uint32_t s8,
+                                         uint32_t s4, bool store, bool whole, InvState &S)
+{
+    const int W = (int)b.W, H = (int)b.H, F = (int)b.F;
+    const int W3 = W >> 3, H1 = H >> 1, H2 = H >> 2, H3 = H >> 3;
+    const uint32_t llb = b.ll_final ? 0x00800080u : 0u; // LL_L - 128 -> LL_L
+
+    // level 3: row t -> LL_2 rows 2t-1, 2t
+    uint32_t z[2];
+    if (F == 3) {
+        const uint32_t sh = 16u * (uint32_t)(((uint64_t)t * (uint64_t)W3 + (uint64_t)(ln.c0 >> 3)) & 1ull);
+        const uint32_t hl = (lds4(s4 + kInvL3) >> sh) & 0xffffu;
+        const uint32_t lh = (lds4(s4 + kInvL3 + 128) >> sh) & 0xffffu;
+        const uint32_t hh = (lds4(s4 + kInvL3 + 256) >> sh) & 0xffffu;
+        const uint32_t ll = (lds4(s4 + kInvL3 + 384) >> sh) & 0xffffu;
+        const uint32_t s = b.ll_final ? in16(ll | (hl << 16)) + 0x80u
+                                      : (ll | (in16(hl << 16) & 0xffff0000u));
+        const uint32_t d = in16(lh | (hh << 16));
+        uint32_t xo, xe;
+        col_inv<CHECK>(s, d, t == 0, t == H3, S.x3, S.d3, xo, xe);
+        z[0] = unlift2(xo, ln.first, ln.last);
+        z[1] = unlift2(xe, ln.first, ln.last);
+    }
+
+    // level 2: rows 2t-1+k -> LL_1 rows 4t-3+2k, 4t-2+2k
+    uint32_t y[4][2];
+    if (F >= 2) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int q2 = 2 * t - 1 + k;
+            const uint32_t hl = in16(lds4(s4 + kInvX + 128 * (3 * k)));
+            const uint32_t lh = in16(lds4(s4 + kInvX + 128 * (3 * k + 1)));
+            const uint32_t hh = in16(lds4(s4 + kInvX + 128 * (3 * k + 2)));
+            uint32_t ll;
+            if (F == 3)
+                ll = z[k];
+            else if (b.ll_final)
+                ll = in16(lds4(s4 + kInvL2Ll + 128 * k)) + llb;
+            else
+                ll = lds4(s4 + kInvL2Ll + 128 * k);
+            uint32_t oL, eL, oH, eH;
+            col_inv<CHECK>(ll, lh, q2 == 0, q2 == H2, S.x2[0], S.d2[0], oL, eL);
+            col_inv<CHECK>(hl, hh, q2 == 0, q2 == H2, S.x2[1], S.d2[1], oH, eH);
+            unlift4(oL, oH, ln.sR, ln.sL, y[2 * k][0], y[2 * k][1]);
+            unlift4(eL, eH, ln.sR, ln.sL, y[2 * k + 1][0], y[2 * k + 1][1]);
+        }
+    }
+
+    // level 1: rows 4t-3+j -> level-0 rows 8t-7+2j, 8t-6+2j
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int q = 4 * t - 3 + j;
+        const uint2 hl = lds8(s8 + 256 * (3 * j));
+        const uint2 lh = lds8(s8 + 256 * (3 * j + 1));
+        const uint2 hh = lds8(s8 + 256 * (3 * j + 2));
+        uint32_t s[4], d[4];
+        if (F == 1) {
+            const uint2 ll = lds8(s8 + kInvX + 256 * j);
+            s[0] = b.ll_final ? in16(ll.x) + llb : ll.x;
+            s[1] = b.ll_final ? in16(ll.y) + llb : ll.y;
+        } else {
+            s[0] = y[j][0];
+            s[1] = y[j][1];
+        }
+        s[2] = in16(hl.x);
+        s[3] = in16(hl.y);
+        d[0] = in16(lh.x);
+        d[1] = in16(lh.y);
+        d[2] = in16(hh.x);
+        d[3] = in16(hh.y);
+        uint32_t xo[4], xe[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            col_inv<CHECK>(s[m], d[m], q == 0, q == H1, S.x1[m], S.d1[m], xo[m], xe[m]);
+        const uint2 vo = unlift8(xo, ln.sR, ln.sL);
+        const uint2 ve = unlift8(xe, ln.sR, ln.sL);
+        const int r = 2 * q - 1;
+        if (!CHECK && whole) { // both rows are whole rows of data
+            if (store) {
+                uint8_t *p = b.out + (uint64_t)r * b.W + (uint64_t)ln.c0;
+                __stcs(reinterpret_cast<uint2 *>(p), vo);
+                __stcs(reinterpret_cast<uint2 *>(p + b.W), ve);
+            }
+        } else {
+            if (store && (!CHECK || (r >= 0 && r < H)))
+                store_bytes(b, ln, r, vo);
+            if (store && (!CHECK || (r + 1 >= 0 && r + 1 < H)))
+                store_bytes(b, ln, r + 1, ve);
+        }
     }
 }
 
 __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t sy, uint32_t ring_lane8,
-                                      uint32_t ring_lane4, int lane)
+                                         uint32_t ring_lane4, int lane)
 {
-    const int h = (int)b.halo;
-    const int SW = 8 * (31 - h);
-    const int W = (int)b.W, H = (int)b.H, F = (int)b.F;
-    const int c0 = (int)sx * SW + 8 * (lane - h);
-    const bool loads = c0 >= 0 && c0 < W;
-    const bool own = lane >= h && lane <= 30 && c0 < W;
-    const bool edge = (int)sx * SW + 8 * (32 - h) >= W;
-    const int W1 = W >> 1, H1 = H >> 1, W2 = W >> 2, H2 = H >> 2, W3 = W >> 3, H3 = H >> 3;
-    const int c1 = c0 >> 1, c2 = c0 >> 2, c3 = c0 >> 3;
-    const uint32_t llb = b.ll_final ? 0x00800080u : 0u; // LL_L - 128 -> LL_L
+    const Lane ln = make_lane(b, sx, lane);
+    const int F = (int)b.F;
     const int t_begin = (int)(sy * b.seg_iters);
     const int t_end = min(t_begin + (int)b.seg_iters, (int)b.iters);
     const int t_first = max(t_begin - (F == 3 ? 2 : 1), 0);
+    const int t_fast_end = (int)b.iters - 2;
 
 #pragma unroll
     for (int k = 0; k < kDepth - 1; ++k)
-        inv_issue(b, t_first + k, t_end, c0, loads, ring_lane8, ring_lane4);
+        inv_issue(b, ln, t_first + k, t_end, ring_lane8, ring_lane4);
 
-    uint32_t x1[4], d1[4], x2[2], d2[2], x3 = kB2, d3 = kB2;
+    InvState S;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        x1[k] = d1[k] = kB2;
-    x2[0] = x2[1] = d2[0] = d2[1] = kB2;
+        S.x1[k] = S.d1[k] = kB2;
+    S.x2[0] = S.x2[1] = S.d2[0] = S.d2[1] = S.x3 = S.d3 = kB2;
 
     for (int t = t_first; t < t_end; ++t) {
-        inv_issue(b, t + kDepth - 1, t_end, c0, loads, ring_lane8, ring_lane4);
+        inv_issue(b, ln, t + kDepth - 1, t_end, ring_lane8, ring_lane4);
         cp_wait<kDepth - 1>();
         const uint32_t so = (uint32_t)(t % kDepth) * kInvStage;
-        const uint32_t s8 = ring_lane8 + so, s4 = ring_lane4 + so;
-        const bool store = own && t >= t_begin;
-
-        // level 3: row t -> LL_2 rows 2t-1, 2t
-        uint32_t z[2];
-        if (F == 3) {
-            const uint32_t sh = 16u * (uint32_t)(((uint64_t)t * (uint64_t)W3 + (uint64_t)c3) & 1ull);
-            const uint32_t hl = (lds4(s4 + kInvL3) >> sh) & 0xffffu;
-            const uint32_t lh = (lds4(s4 + kInvL3 + 128) >> sh) & 0xffffu;
-            const uint32_t hh = (lds4(s4 + kInvL3 + 256) >> sh) & 0xffffu;
-            const uint32_t ll = (lds4(s4 + kInvL3 + 384) >> sh) & 0xffffu;
-            const uint32_t s = b.ll_final ? in16(ll | (hl << 16)) + 0x80u : ((ll | (in16(hl << 16) & 0xffff0000u)));
-            const uint32_t d = in16(lh | (hh << 16));
-            uint32_t xo, xe;
-            col_inv(s, d, t == 0, t == H3, x3, d3, xo, xe);
-            z[0] = unlift2(xo, c2, W2, edge);
-            z[1] = unlift2(xe, c2, W2, edge);
-        }
-
-        // level 2: rows 2t-1+k -> LL_1 rows 4t-3+2k, 4t-2+2k
-        uint32_t y[4][2];
-        if (F >= 2) {
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int q2 = 2 * t - 1 + k;
-                const uint32_t hl = in16(lds4(s4 + kInvX + 128 * (3 * k)));
-                const uint32_t lh = in16(lds4(s4 + kInvX + 128 * (3 * k + 1)));
-                const uint32_t hh = in16(lds4(s4 + kInvX + 128 * (3 * k + 2)));
-                uint32_t ll;
-                if (F == 3)
-                    ll = z[k];
-                else if (b.ll_final)
-                    ll = in16(lds4(s4 + kInvL2Ll + 128 * k)) + llb;
-                else
-                    ll = lds4(s4 + kInvL2Ll + 128 * k);
-                uint32_t oL, eL, oH, eH;
-                col_inv(ll, lh, q2 == 0, q2 == H2, x2[0], d2[0], oL, eL);
-                col_inv(hl, hh, q2 == 0, q2 == H2, x2[1], d2[1], oH, eH);
-                unlift4(oL, oH, c1, W1, edge, y[2 * k][0], y[2 * k][1]);
-                unlift4(eL, eH, c1, W1, edge, y[2 * k + 1][0], y[2 * k + 1][1]);
-            }
-        }
-
-        // level 1: rows 4t-3+j -> level-0 rows 8t-7+2j, 8t-6+2j
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int q = 4 * t - 3 + j;
-            const uint2 hl = lds8(s8 + 256 * (3 * j));
-            const uint2 lh = lds8(s8 + 256 * (3 * j + 1));
-            const uint2 hh = lds8(s8 + 256 * (3 * j + 2));
-            uint32_t s[4], d[4];
-            if (F == 1) {
-                const uint2 ll = lds8(s8 + kInvX + 256 * j);
-                s[0] = b.ll_final ? in16(ll.x) + llb : ll.x;
-                s[1] = b.ll_final ? in16(ll.y) + llb : ll.y;
-            } else {
-                s[0] = y[j][0];
-                s[1] = y[j][1];
-            }
-            s[2] = in16(hl.x);
-            s[3] = in16(hl.y);
-            d[0] = in16(lh.x);
-            d[1] = in16(lh.y);
-            d[2] = in16(hh.x);
-            d[3] = in16(hh.y);
-            uint32_t xo[4], xe[4];
-#pragma unroll
-            for (int m = 0; m < 4; ++m)
-                col_inv(s[m], d[m], q == 0, q == H1, x1[m], d1[m], xo[m], xe[m]);
-            uint32_t vo[4], ve[4];
-            unlift_row<true>(xo, c0, W, edge, vo);
-            unlift_row<true>(xe, c0, W, edge, ve);
-            const int r = 2 * q - 1;
-            if (store && r >= 0 && r < H)
-                store_bytes(b, r, c0, vo);
-            if (store && r + 1 >= 0 && r + 1 < H)
-                store_bytes(b, r + 1, c0, ve);
-        }
+        const bool store = ln.own && t >= t_begin;
+        const bool whole = 8 * t < (int)b.full_rows; // rows 8t-7 .. 8t hold only data
+        if (t >= 1 && t < t_fast_end)
+            inv_iter<false>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S);
+        else
+            inv_iter<true>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S);
     }
     cp_wait<0>();
 }
