@@ -4,8 +4,8 @@ one B300 (replicas on N GPUs under torchrun).
 
 Workload (default "c2"): the 3-plane 4096 x 4096 synthetic bitmap, width 4096,
 3 levels, nonce = plane index, key 00..0f.  One step = protect of all three
-planes (one batched, dependency-ordered launch: every level and the AES pass)
-followed by recover of all three (one launch).  L2 is flushed before each
+planes (one batched call: the fused-level kernel, then the AES-CTR kernel)
+followed by recover of all three (AES-CTR, then the fused inverse).  L2 is flushed before each
 direction, outside the timed events: a 512 MiB write, then a read of the same
 buffer so that L2 holds clean lines and the timed launch pays for no write-back
 of the flush.  The step time is the sum of the two event-timed directions on
@@ -163,9 +163,13 @@ def run_reference(args, rank):
 
 # -- our arm ---------------------------------------------------------------------------
 
+# the files that define the dominant kernel (the fused-level kernel)
+KERNEL_SOURCES = ("fused_kernels.cu", "swar.cuh", "frag_internal.cuh")
+
+
 def _kernel_hash():
     h = hashlib.sha256()
-    for name in ("stream_kernels.cu", "frag_internal.cuh"):
+    for name in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1803_04880_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -252,6 +256,9 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
     K, Wm = args.steps, args.warmup
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    # per-kernel event pairs around each launch inside the library's calls
+    bp.set_timing(True)
+    br.set_timing(True)
     sampler = ClockSampler(local_rank)
     with torch.cuda.stream(s):
         for i in range(Wm):
@@ -260,6 +267,8 @@ def run_ours(args, rank, world, local_rank):
             flush_l2(i)
             br.run(key, s)
     torch.cuda.synchronize()
+    bp.launch_times()  # drop the warm-up pairs
+    br.launch_times()
     sampler.start()
     time.sleep(0.5)
     if dist:
@@ -283,6 +292,9 @@ def run_ours(args, rank, world, local_rank):
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
     fr.sync_status(s)
+    kt = {"protect": bp.launch_times(), "recover": br.launch_times()}
+    bp.set_timing(False)
+    br.set_timing(False)
     tp = [e[0].elapsed_time(e[1]) for e in ev]
     tr = [e[2].elapsed_time(e[3]) for e in ev]
     steps_ms = [a + b for a, b in zip(tp, tr)]
@@ -313,15 +325,29 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = _peaks()
     t_prot = statistics.mean(tp)
     t_rec = statistics.mean(tr)
-    dominant = "protect" if t_prot >= t_rec else "recover"
-    t_dom = max(t_prot, t_rec)
-    alg_bytes = 3 * n_total  # protect: read 1 + write 2; recover: read 2 + write 1 per byte
+    # the dominant kernel: the slower direction's fused-level launch (with
+    # fewer than two fused levels somewhere, whichever kind took longest)
+    per_launch = {}
+    for d, times in kt.items():
+        for kind, (ms, n) in times.items():
+            if n:
+                per_launch[(d, kind)] = ms / n
+    dom_dir, dom_kind = max(per_launch, key=per_launch.get)
+    t_dom = per_launch[(dom_dir, dom_kind)]
+    # the fused kernel reads 1 byte and writes 2 (int16 bands and LL) per
+    # input byte, or the reverse; the level kernel the same over all levels
+    alg_bytes = 3 * n_total
     achieved = alg_bytes / (t_dom / 1e3) / 1e9
+    names = {"fused": "fuse_kernel<%s> (%s: levels 1..3 of every plane, one launch)",
+             "levels": "dag_kernel<%s> (%s: dependency-ordered levels, one launch)",
+             "cipher": "ctr_kernel (%s%s: AES-128-CTR over the private fragments)"}
+    label = names[dom_kind] % ("true" if dom_dir == "protect" else "false", dom_dir) \
+        if dom_kind != "cipher" else names["cipher"] % (dom_dir, "")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": _traffic(args.workload, dominant),
-                "kernel": "dag_kernel<%s> (%s: every level and the AES pass, one launch)"
-                          % ("true" if dominant == "protect" else "false", dominant),
-                "peak_kind": peak_kind,
+                "frac": round(achieved / peak, 4), "traffic": _traffic(args.workload, dom_dir),
+                "kernel": label, "peak_kind": peak_kind,
+                "kernel_ms_per_launch": round(t_dom, 5),
+                "launch_ms": {"%s/%s" % k: round(v, 5) for k, v in per_launch.items()},
                 "algorithmic_bytes_per_launch": alg_bytes}
 
     # e2e through the host-buffer C-ABI calls, pinned host memory
@@ -362,7 +388,7 @@ def run_ours(args, rank, world, local_rank):
                 "dtype": "int32", "data": "synthetic",
                 "config": dict(desc, l2="flushed before each direction (512 MiB write, then read back)",
                                parallelism="replicas" if world > 1 else "single GPU",
-                               path="frag_batch_run (one dependency-ordered launch per direction)"),
+                               path="frag_batch_run (fused levels + AES-CTR, one launch each per direction)"),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": 2 * K * bp.launches,
                 "protect_gbps": round(n_total / (t_prot / 1e3) / 1e9, 2),

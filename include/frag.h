@@ -189,20 +189,40 @@ frag_status frag_recover_batch(const frag_ritem *items, uint32_t count, frag_key
 
 /* Batch objects for CUDA-graph capture: *_create builds the work queue and
  * uploads it (synchronously) to the current device; frag_batch_run enqueues
- * per wave only a memset of the completion counters and queue head and one
- * launch of the dependency-ordered kernel, so a capture of frag_batch_run
- * replays with no host work.  Buffers named in the items must stay valid
- * while the batch exists. */
+ * per wave only kernel launches -- the fused-level kernel for the buffers it
+ * takes, a memset of the completion counters and queue head and one launch of
+ * the dependency-ordered kernel for the remaining levels, and the AES-CTR
+ * kernel for private fragments enciphered outside it -- so a capture of
+ * frag_batch_run replays with no host work.  Buffers named in the items must
+ * stay valid while the batch exists. */
 frag_status frag_batch_create_protect(frag_batch *out, const frag_item *items, uint32_t count);
 frag_status frag_batch_create_recover(frag_batch *out, const frag_ritem *items, uint32_t count);
 frag_status frag_batch_run(frag_batch batch, frag_key key, frag_stream stream);
 frag_status frag_batch_destroy(frag_batch batch);
 
-/* What one frag_batch_run issues: *launches = kernel launches (one per wave
- * of buffers whose scratch fits the library's budget), *scratch_bytes =
- * device memory the batch holds for level scratch and descriptors.  Either
- * pointer may be NULL.  FRAG_EINVAL if batch is NULL. */
+/* What one frag_batch_run issues: *launches = kernel launches (up to three
+ * per wave of buffers whose scratch fits the library's budget),
+ * *scratch_bytes = device memory the batch holds for level scratch and
+ * descriptors.  Either pointer may be NULL.  FRAG_EINVAL if batch is NULL. */
 frag_status frag_batch_info(frag_batch batch, uint32_t *launches, uint64_t *scratch_bytes);
+
+/* Per-kernel timing of a batch (instrumentation; off by default).  While
+ * enabled, frag_batch_run records a CUDA event pair on the caller's stream
+ * around each kernel launch.  frag_batch_launch_times waits for the recorded
+ * events and adds, per kernel kind, the milliseconds between each pair to
+ * ms[kind] and the number of launches to launches[kind] (both arrays of
+ * FRAG_KERNEL_KINDS entries, zeroed first; either may be NULL), then
+ * forgets the recorded pairs.  The events cost a few microseconds of host
+ * time per run; they are not captured into CUDA graphs usefully, so disable
+ * timing before capturing.  FRAG_EINVAL if batch is NULL. */
+typedef enum {
+    FRAG_KERNEL_FUSED = 0,  /* levels 1..3 in one pass down the rows */
+    FRAG_KERNEL_LEVELS = 1, /* the dependency-ordered level kernel */
+    FRAG_KERNEL_CIPHER = 2, /* AES-128-CTR over private fragments */
+    FRAG_KERNEL_KINDS = 3
+} frag_kernel_kind;
+frag_status frag_batch_set_timing(frag_batch batch, int enable);
+frag_status frag_batch_launch_times(frag_batch batch, double *ms, uint32_t *launches);
 
 /* Batched protect that allocates nothing.  The thesis has no counterpart:
  * this is a deployment aid.  Some callers may not call cudaMalloc at all --

@@ -29,6 +29,7 @@ EXPORTS = [
     "frag_protect", "frag_recover", "frag_protect_host", "frag_recover_host",
     "frag_protect_batch", "frag_recover_batch", "frag_batch_create_protect",
     "frag_batch_create_recover", "frag_batch_run", "frag_batch_destroy", "frag_batch_info",
+    "frag_batch_set_timing", "frag_batch_launch_times",
     "frag_get_error", "frag_check_wait_timeout",
     "frag_sync_status",
 ]
@@ -98,6 +99,9 @@ def lib():
         "frag_batch_run": ([vp, vp, vp], ctypes.c_int),
         "frag_batch_destroy": ([vp], ctypes.c_int),
         "frag_batch_info": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u64)], ctypes.c_int),
+        "frag_batch_set_timing": ([vp, ctypes.c_int], ctypes.c_int),
+        "frag_batch_launch_times": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)],
+                                    ctypes.c_int),
         "frag_get_error": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
         "frag_sync_status": ([vp], ctypes.c_int),
         "frag_check_wait_timeout": ([u32, vp], ctypes.c_int),
@@ -317,6 +321,20 @@ class Batch:
     @property
     def launches(self) -> int:
         return self.info()[0]
+
+    KERNEL_KINDS = ("fused", "levels", "cipher")
+
+    def set_timing(self, enable: bool = True) -> None:
+        """Record a CUDA event pair around each kernel launch of run()."""
+        check(lib().frag_batch_set_timing(self._h, 1 if enable else 0))
+
+    def launch_times(self) -> dict:
+        """{kind: (total ms, launches)} over the timed runs since the last
+        call (waits for their events)."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_uint32 * 3)()
+        check(lib().frag_batch_launch_times(self._h, ms, n))
+        return {k: (ms[i], n[i]) for i, k in enumerate(self.KERNEL_KINDS)}
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

@@ -70,12 +70,19 @@ __global__ void __launch_bounds__(kCtrThreads) ctr_kernel(CtrWork w)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     CtrSmem &m = *reinterpret_cast<CtrSmem *>(smem);
-    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x)
-        m.te[i] = w.aes_tables[i >> 5];
+    // table 0 into shared memory, one copy per lane: each warp takes 32
+    // entries with one coalesced load and writes entry x as 32 consecutive
+    // words (x, lane), conflict-free
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t base = (threadIdx.x >> 5) * 32; base < 256; base += (blockDim.x >> 5) * 32) {
+        const uint32_t v = __ldg(w.aes_tables + base + lane);
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k)
+            m.te[(base + k) * 32 + lane] = __shfl_sync(0xffffffffu, v, k);
+    }
     for (int i = threadIdx.x; i < 44; i += blockDim.x)
         m.rk[i] = w.round_keys[i];
     __syncthreads();
-    const uint32_t lane = threadIdx.x & 31;
     const uint64_t nchunks = w.chunks ? w.nchunks
                                       : (w.single.nblocks + w.single_chunk - 1) / w.single_chunk;
     for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {

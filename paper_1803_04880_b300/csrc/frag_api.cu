@@ -968,9 +968,42 @@ frag_status upload_batch(const BatchPlan &bp, uint8_t *mem, cudaStream_t s, bool
     return FRAG_OK;
 }
 
+// event pair around one launch of a timed batch run
+struct TimedLaunch {
+    uint32_t kind;
+    cudaEvent_t a, b;
+};
+
+struct LaunchTimer {
+    std::vector<TimedLaunch> *out;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    void begin()
+    {
+        if (out && cudaEventCreate(&a) == cudaSuccess && cudaEventRecord(a, s) != cudaSuccess) {
+            cudaEventDestroy(a);
+            a = nullptr;
+        }
+    }
+    void end(uint32_t kind)
+    {
+        if (!out || !a)
+            return;
+        cudaEvent_t b = nullptr;
+        if (cudaEventCreate(&b) == cudaSuccess && cudaEventRecord(b, s) == cudaSuccess)
+            out->push_back(TimedLaunch{kind, a, b});
+        else {
+            cudaEventDestroy(a);
+            if (b)
+                cudaEventDestroy(b);
+        }
+        a = nullptr;
+    }
+};
+
 // the fused launch of a wave (its buffers' descriptors at fbufs_off)
 frag_status launch_wave_fused(const BatchPlan &bp, const DagWave &wv, uint8_t *mem, DeviceState &d,
-                              cudaStream_t s)
+                              cudaStream_t s, LaunchTimer &tm)
 {
     if (wv.fbufs.empty())
         return FRAG_OK;
@@ -981,21 +1014,27 @@ frag_status launch_wave_fused(const BatchPlan &bp, const DagWave &wv, uint8_t *m
     if (w.nbufs == 1)
         w.single = wv.fbufs[0];
     w.total_units = wv.fuse_units;
-    return fuse_launch(d, bp.fwd, w, std::max<uint64_t>(1, bp.fuse_slots), s);
+    tm.begin();
+    frag_status st = fuse_launch(d, bp.fwd, w, std::max<uint64_t>(1, bp.fuse_slots), s);
+    tm.end(FRAG_KERNEL_FUSED);
+    return st;
 }
 
 // per wave, protect: fused levels, dependency-ordered levels above them,
 // CTR; recover: CTR, dependency-ordered levels, fused levels
 frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, const uint32_t *rk,
-                         cudaStream_t s)
+                         cudaStream_t s, std::vector<TimedLaunch> *timed = nullptr)
 {
+    LaunchTimer tm{timed, s};
     for (const auto &wv : bp.waves) {
         const frag::CtrChunk *chunks = (const frag::CtrChunk *)(mem + wv.chunks_off);
         frag_status st = FRAG_OK;
-        if (bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s)) != FRAG_OK)
+        if (bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm)) != FRAG_OK)
             return st;
         if (!bp.fwd && !wv.chunks.empty()) { // decipher before the transform reads LL_L
+            tm.begin();
             st = ctr_launch(d, rk, chunks, wv.chunks.size(), nullptr, s);
+            tm.end(FRAG_KERNEL_CIPHER);
             if (st != FRAG_OK)
                 return st;
         }
@@ -1020,15 +1059,20 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
                 grid = std::min(grid, bp.max_ctas);
             if (st != FRAG_OK)
                 return st;
-            if ((e = frag::launch_dag(bp.fwd, w, grid, s)) != cudaSuccess)
+            tm.begin();
+            e = frag::launch_dag(bp.fwd, w, grid, s);
+            tm.end(FRAG_KERNEL_LEVELS);
+            if (e != cudaSuccess)
                 return cuda_fail(e, "batch launch");
         }
         if (bp.fwd && !wv.chunks.empty()) { // encipher after the transform wrote LL_L
+            tm.begin();
             st = ctr_launch(d, rk, chunks, wv.chunks.size(), nullptr, s);
+            tm.end(FRAG_KERNEL_CIPHER);
             if (st != FRAG_OK)
                 return st;
         }
-        if (!bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s)) != FRAG_OK)
+        if (!bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm)) != FRAG_OK)
             return st;
     }
     return FRAG_OK;
@@ -1091,6 +1135,8 @@ struct frag_batch_s {
     int device = 0;
     BatchPlan bp;
     uint8_t *mem = nullptr; // [scratch][descriptors, counters, queue heads]
+    bool timing = false;
+    std::vector<TimedLaunch> timed; // event pairs of timed runs not yet read
 };
 
 namespace {
@@ -1509,7 +1555,47 @@ frag_status frag_batch_run(frag_batch batch, frag_key key, frag_stream stream)
     const uint32_t *rk = nullptr;
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
-    return launch_batch(batch->bp, batch->mem, *d, rk, (cudaStream_t)stream);
+    return launch_batch(batch->bp, batch->mem, *d, rk, (cudaStream_t)stream,
+                        batch->timing ? &batch->timed : nullptr);
+}
+
+frag_status frag_batch_set_timing(frag_batch batch, int enable)
+{
+    if (batch == nullptr)
+        return fail(FRAG_EINVAL, "batch is NULL");
+    batch->timing = enable != 0;
+    return FRAG_OK;
+}
+
+frag_status frag_batch_launch_times(frag_batch batch, double *ms, uint32_t *launches)
+{
+    if (batch == nullptr)
+        return fail(FRAG_EINVAL, "batch is NULL");
+    double t[FRAG_KERNEL_KINDS] = {0};
+    uint32_t n[FRAG_KERNEL_KINDS] = {0};
+    frag_status st = FRAG_OK;
+    for (const TimedLaunch &x : batch->timed) {
+        float v = 0.f;
+        cudaError_t e = cudaEventSynchronize(x.b);
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&v, x.a, x.b);
+        if (e != cudaSuccess && st == FRAG_OK)
+            st = cuda_fail(e, "launch timing");
+        if (x.kind < FRAG_KERNEL_KINDS) {
+            t[x.kind] += v;
+            n[x.kind] += 1;
+        }
+        cudaEventDestroy(x.a);
+        cudaEventDestroy(x.b);
+    }
+    batch->timed.clear();
+    for (int k = 0; k < FRAG_KERNEL_KINDS; ++k) {
+        if (ms)
+            ms[k] = t[k];
+        if (launches)
+            launches[k] = n[k];
+    }
+    return st;
 }
 
 frag_status frag_batch_info(frag_batch batch, uint32_t *launches, uint64_t *scratch_bytes)
@@ -1530,6 +1616,10 @@ frag_status frag_batch_destroy(frag_batch batch)
 {
     if (batch == nullptr)
         return FRAG_OK;
+    for (const TimedLaunch &x : batch->timed) {
+        cudaEventDestroy(x.a);
+        cudaEventDestroy(x.b);
+    }
     if (batch->mem)
         cudaFree(batch->mem);
     delete batch;

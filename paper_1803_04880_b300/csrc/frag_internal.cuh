@@ -171,7 +171,7 @@ struct CtrWork {
 
 cudaError_t launch_ctr(const CtrWork &w, uint32_t grid, cudaStream_t stream);
 cudaError_t ctr_occupancy(int *blocks_per_sm);
-constexpr uint32_t kCtrChunkList = 1024; // blocks per chunk of a chunk list
+constexpr uint32_t kCtrChunkList = 256; // blocks per chunk of a chunk list (one per thread)
 
 // Fused levels (fused_kernels.cu): up to kFuseMaxLevels levels of a buffer
 // in one pass down its rows, no intermediate LL in memory.  A unit is one
@@ -180,7 +180,6 @@ constexpr uint32_t kCtrChunkList = 1024; // blocks per chunk of a chunk list
 // iteration t writes rows 8t-7 .. 8t.
 constexpr uint32_t kFuseMaxLevels = 3;
 constexpr int kFuseWarps = 4; // warps per CTA (each runs its own units)
-constexpr int kFuseDepth = 3; // shared-memory stages per warp (iterations)
 
 struct __align__(16) FuseBuf {
     const uint8_t *src;   // forward: the n bytes

@@ -52,7 +52,22 @@ using strm::to_i16x2;
 
 constexpr int kWarps = kFuseWarps;
 constexpr int kThreads = 32 * kWarps;
-constexpr int kDepth = kFuseDepth;
+// stages per warp (iterations in flight + the one being read) and resident
+// CTAs per SM the register budget is cut for, per direction
+#ifndef FUSE_FWD_DEPTH
+#define FUSE_FWD_DEPTH 3
+#endif
+#ifndef FUSE_INV_DEPTH
+#define FUSE_INV_DEPTH 2
+#endif
+#ifndef FUSE_FWD_MINB
+#define FUSE_FWD_MINB 4
+#endif
+#ifndef FUSE_INV_MINB
+#define FUSE_INV_MINB 5
+#endif
+constexpr int kFwdDepth = FUSE_FWD_DEPTH;
+constexpr int kInvDepth = FUSE_INV_DEPTH;
 constexpr int kFwdStage = 8 * 256; // 8 level-0 rows x 32 lanes x 8 bytes
 // inverse stage: level-1 rows j = 0..3, bands HL/LH/HH, 8 bytes a lane, then
 // region X: level-1 LL rows (one level), or level-2 rows k = 0..1 of the three
@@ -259,7 +274,7 @@ __device__ __forceinline__ void fwd_issue(const FuseBuf &b, const Lane &ln, int 
                                           uint32_t ring_lane)
 {
     if (t < t_end && ln.loads) {
-        const uint32_t st = ring_lane + (uint32_t)(t % kDepth) * kFwdStage;
+        const uint32_t st = ring_lane + (uint32_t)(t % kFwdDepth) * kFwdStage;
         const int r0 = 8 * t - 1;
         if (r0 >= 0 && r0 + 8 <= (int)b.full_rows) { // eight whole rows of data
             const uint8_t *p = b.src + (uint64_t)r0 * b.W + (uint64_t)ln.c0;
@@ -422,7 +437,7 @@ __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t
     const int t_fast_end = (int)b.iters - 2; // iterations t >= 2 and below this skip the checks
 
 #pragma unroll
-    for (int k = 0; k < kDepth - 1; ++k)
+    for (int k = 0; k < kFwdDepth - 1; ++k)
         fwd_issue(b, ln, t_first + k, t_end, ring_lane);
 
     FwdState S;
@@ -432,9 +447,9 @@ __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t
     S.e2L = S.e2H = S.p2L = S.p2H = S.e3 = S.p3 = kB2;
 
     for (int t = t_first; t < t_end; ++t) {
-        fwd_issue(b, ln, t + kDepth - 1, t_end, ring_lane);
-        cp_wait<kDepth - 1>();
-        const uint32_t st = ring_lane + (uint32_t)(t % kDepth) * kFwdStage;
+        fwd_issue(b, ln, t + kFwdDepth - 1, t_end, ring_lane);
+        cp_wait<kFwdDepth - 1>();
+        const uint32_t st = ring_lane + (uint32_t)(t % kFwdDepth) * kFwdStage;
         const bool store = ln.own && t >= t_begin;
         if (t >= 2 && t < t_fast_end)
             fwd_iter<false>(b, ln, t, st, store, S);
@@ -457,7 +472,7 @@ __device__ __forceinline__ void inv_issue(const FuseBuf &b, const Lane &ln, int 
 {
     if (t < t_end && ln.loads) {
         const int F = (int)b.F;
-        const uint32_t so = (uint32_t)(t % kDepth) * kInvStage;
+        const uint32_t so = (uint32_t)(t % kInvDepth) * kInvStage;
         const uint32_t W1 = b.W >> 1, H1 = b.H >> 1, W2 = b.W >> 2, H2 = b.H >> 2;
         const uint32_t c1 = (uint32_t)ln.c0 >> 1, c2 = (uint32_t)ln.c0 >> 2;
         // every row of the iteration inside its level: no per-row tests
@@ -670,7 +685,7 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
     const int t_fast_end = (int)b.iters - 2;
 
 #pragma unroll
-    for (int k = 0; k < kDepth - 1; ++k)
+    for (int k = 0; k < kInvDepth - 1; ++k)
         inv_issue(b, ln, t_first + k, t_end, ring_lane8, ring_lane4);
 
     InvState S;
@@ -680,9 +695,9 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
     S.x2[0] = S.x2[1] = S.d2[0] = S.d2[1] = S.x3 = S.d3 = kB2;
 
     for (int t = t_first; t < t_end; ++t) {
-        inv_issue(b, ln, t + kDepth - 1, t_end, ring_lane8, ring_lane4);
-        cp_wait<kDepth - 1>();
-        const uint32_t so = (uint32_t)(t % kDepth) * kInvStage;
+        inv_issue(b, ln, t + kInvDepth - 1, t_end, ring_lane8, ring_lane4);
+        cp_wait<kInvDepth - 1>();
+        const uint32_t so = (uint32_t)(t % kInvDepth) * kInvStage;
         const bool store = ln.own && t >= t_begin;
         const bool whole = 8 * t < (int)b.full_rows; // rows 8t-7 .. 8t hold only data
         if (t >= 1 && t < t_fast_end)
@@ -715,11 +730,11 @@ __device__ __forceinline__ const FuseBuf *unit_buf(const FuseWork &w, uint64_t u
 }
 
 template <bool FWD>
-__global__ void __launch_bounds__(kThreads) fuse_kernel(FuseWork w)
+__global__ void __launch_bounds__(kThreads, FWD ? FUSE_FWD_MINB : FUSE_INV_MINB) fuse_kernel(FuseWork w)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t ring = smem_addr(smem) + (uint32_t)warp * kDepth * (FWD ? kFwdStage : kInvStage);
+    const uint32_t ring = smem_addr(smem) + (uint32_t)warp * (FWD ? kFwdDepth * kFwdStage : kInvDepth * kInvStage);
     const uint64_t G = (uint64_t)gridDim.x * kWarps;
     for (uint64_t u = (uint64_t)blockIdx.x * kWarps + warp; u < w.total_units; u += G) {
         uint64_t local;
@@ -733,7 +748,7 @@ __global__ void __launch_bounds__(kThreads) fuse_kernel(FuseWork w)
     }
 }
 
-size_t smem_bytes(bool fwd) { return (size_t)kWarps * kDepth * (fwd ? kFwdStage : kInvStage); }
+size_t smem_bytes(bool fwd) { return (size_t)kWarps * (fwd ? kFwdDepth * kFwdStage : kInvDepth * kInvStage); }
 
 template <bool FWD>
 cudaError_t set_attr()

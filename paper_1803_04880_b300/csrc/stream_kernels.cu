@@ -1364,8 +1364,22 @@ __global__ void __launch_bounds__(kCtaThreads, FRAG_CTAS_PER_SM) dag_kernel(DagW
     uint64_t *empty = full + kStages;
     StageHdr *hdr = reinterpret_cast<StageHdr *>(smem + kSmemHdr);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < kAesWords; i += blockDim.x)
-        (&aes.T[0][0])[i] = w.aes_tables[i];
+    {
+        // all of a thread's table loads in flight at once
+        constexpr int kTabIters = (kAesWords + kCtaThreads - 1) / kCtaThreads;
+        uint32_t tv[kTabIters];
+#pragma unroll
+        for (int k = 0; k < kTabIters; ++k) {
+            const int i = (int)threadIdx.x + k * kCtaThreads;
+            tv[k] = i < kAesWords ? __ldg(w.aes_tables + i) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kTabIters; ++k) {
+            const int i = (int)threadIdx.x + k * kCtaThreads;
+            if (i < kAesWords)
+                (&aes.T[0][0])[i] = tv[k];
+        }
+    }
     for (int i = threadIdx.x; i < 44; i += blockDim.x)
         aes.rk[i] = w.round_keys[i];
     if (threadIdx.x == 0) {

@@ -76,3 +76,16 @@ def test_null_arguments_are_rejected(L):
     assert L.frag_get_error(None, 0) == fr.FRAG_EINVAL
     assert L.frag_batch_info(None, None, None) == fr.FRAG_EINVAL
     assert L.frag_check_wait_timeout(0, None) == fr.FRAG_EINVAL
+    assert L.frag_batch_set_timing(None, 1) == fr.FRAG_EINVAL
+    assert L.frag_batch_launch_times(None, None, None) == fr.FRAG_EINVAL
+    assert L.frag_plan_set_path(None, 0) == fr.FRAG_EINVAL
+    assert L.frag_plan_get_path(p.handle, None) == fr.FRAG_EINVAL
+
+
+def test_path_validation(L):
+    p = fr.Plan(256, 3)
+    assert p.path() == fr.Plan.PATH_AUTO
+    p.set_path(fr.Plan.PATH_LEVELS)
+    assert p.path() == fr.Plan.PATH_LEVELS
+    with pytest.raises(fr.FragError):
+        p.set_path(7)

@@ -131,6 +131,27 @@ def test_path_selects_kernels(fr, key):
     assert fr.Batch([(plan, 0, n, d, priv, pub)], True).launches == 1
 
 
+def test_batch_launch_times(fr, key):
+    """The per-kernel event pairs count every launch of the timed runs."""
+    n, W, L = 4096 * 64, 4096, 3
+    plan = fr.Plan(W, L)
+    _, pb, ub = plan.sizes(n)
+    d = torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda")
+    priv = torch.empty(pb, dtype=torch.uint8, device="cuda")
+    pub = torch.empty(ub, dtype=torch.uint8, device="cuda")
+    b = fr.Batch([(plan, 0, n, d, priv, pub)], True)
+    b.run(key)
+    assert b.launch_times() == {"fused": (0.0, 0), "levels": (0.0, 0), "cipher": (0.0, 0)}
+    b.set_timing(True)
+    for _ in range(3):
+        b.run(key)
+    t = b.launch_times()
+    assert t["fused"][1] == 3 and t["cipher"][1] == 3 and t["levels"][1] == 0
+    assert t["fused"][0] > 0 and t["cipher"][0] > 0
+    assert b.launch_times()["fused"] == (0.0, 0)  # read once
+    fr.sync_status()
+
+
 @pytest.mark.parametrize("n,W,L", [(12345, 128, 2), (4096, 64, 3), (77777, 256, 5)])
 def test_unaligned_buffers(fr, key, n, W, L):
     check_against_oracle(fr, key, wl.random_bytes(n, 5), W, L, nonce=3, offset=1)
