@@ -9,7 +9,11 @@
 // form are byte rotations of the first (FIPS-197 Sec. 5.1 combined into
 // table lookups), and the last round's S-box is a byte of the same entry.
 // The counter block is nonce (8 bytes big-endian) || block index (8 bytes
-// big-endian); out = in XOR keystream, in may equal out.  Buffers with three
+// big-endian); out = in XOR keystream, in may equal out.  The keystream does
+// not depend on the data, so the kernel is launched as a programmatic
+// dependent of the kernel before it: it builds its table and its first
+// keystream blocks while that kernel still runs, and waits for it only
+// before reading the fragment.  Buffers with three
 // or more levels keep their cipher units inside the dependency-ordered
 // launch, where the fragment is small.
 #include "frag_internal.cuh"
@@ -70,6 +74,7 @@ __global__ void __launch_bounds__(kCtrThreads) ctr_kernel(CtrWork w)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     CtrSmem &m = *reinterpret_cast<CtrSmem *>(smem);
+    grid_release();
     // table 0 into shared memory, one copy per lane: each warp takes 32
     // entries with one coalesced load and writes entry x as 32 consecutive
     // words (x, lane), conflict-free
@@ -99,9 +104,13 @@ __global__ void __launch_bounds__(kCtrThreads) ctr_kernel(CtrWork w)
             const uint64_t b = ch.first_block + i;
             uint32_t ks[4];
             ctr_block(m, lane, ch.nonce, b, ks);
+            grid_wait(); // the fragment is complete from here on (returns at once after the first)
             const uint64_t o = 16 * b;
             if (vec && o + 16 <= ch.bytes) {
-                const uint4 t = __ldg(reinterpret_cast<const uint4 *>(ch.in + o));
+                // L2-coherent load: the kernel before this one wrote the
+                // fragment while this grid was already resident, so the
+                // read-only (non-coherent) path is not allowed here
+                const uint4 t = __ldcg(reinterpret_cast<const uint4 *>(ch.in + o));
                 uint4 r; // keystream bytes in stream order = big-endian words
                 r.x = t.x ^ __byte_perm(ks[0], 0, 0x0123);
                 r.y = t.y ^ __byte_perm(ks[1], 0, 0x0123);
@@ -110,7 +119,7 @@ __global__ void __launch_bounds__(kCtrThreads) ctr_kernel(CtrWork w)
                 *reinterpret_cast<uint4 *>(ch.out + o) = r;
             } else {
                 for (int k = 0; k < 16 && o + (uint64_t)k < ch.bytes; ++k)
-                    ch.out[o + k] = (uint8_t)(ch.in[o + k] ^ (uint8_t)(ks[k >> 2] >> (24 - 8 * (k & 3))));
+                    ch.out[o + k] = (uint8_t)(__ldcg(ch.in + o + k) ^ (uint8_t)(ks[k >> 2] >> (24 - 8 * (k & 3))));
             }
         }
     }
@@ -127,8 +136,17 @@ cudaError_t launch_ctr(const CtrWork &w, uint32_t grid, cudaStream_t stream)
     cudaError_t e = ctr_attr();
     if (e != cudaSuccess)
         return e;
-    ctr_kernel<<<grid, kCtrThreads, sizeof(CtrSmem), stream>>>(w);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kCtrThreads);
+    cfg.dynamicSmemBytes = sizeof(CtrSmem);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ctr_kernel, w);
 }
 
 cudaError_t ctr_occupancy(int *blocks_per_sm)

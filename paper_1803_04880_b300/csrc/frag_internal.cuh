@@ -173,6 +173,13 @@ cudaError_t launch_ctr(const CtrWork &w, uint32_t grid, cudaStream_t stream);
 cudaError_t ctr_occupancy(int *blocks_per_sm);
 constexpr uint32_t kCtrChunkList = 256; // blocks per chunk of a chunk list (one per thread)
 
+// Programmatic dependent launch: a kernel launched with
+// launch_after_previous() may start while the kernel before it on the stream
+// is still running; it calls grid_wait() before touching anything that
+// kernel writes, and grid_release() lets the next kernel start early in turn.
+__device__ __forceinline__ void grid_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Fused levels (fused_kernels.cu): up to kFuseMaxLevels levels of a buffer
 // in one pass down its rows, no intermediate LL in memory.  A unit is one
 // warp strip (8 (31 - halo) level-0 columns) by seg_iters iterations of 8

@@ -733,6 +733,9 @@ template <bool FWD>
 __global__ void __launch_bounds__(kThreads, FWD ? FUSE_FWD_MINB : FUSE_INV_MINB) fuse_kernel(FuseWork w)
 {
     extern __shared__ __align__(16) uint8_t smem[];
+    // the next kernel (the CTR pass after a protect) may start its
+    // data-independent part now; it waits for this grid before reading
+    grid_release();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t ring = smem_addr(smem) + (uint32_t)warp * (FWD ? kFwdDepth * kFwdStage : kInvDepth * kInvStage);
     const uint64_t G = (uint64_t)gridDim.x * kWarps;
@@ -764,6 +767,8 @@ cudaError_t launch_fuse(bool fwd, const FuseWork &w, uint32_t grid, cudaStream_t
     cudaError_t e = fwd ? fuse::set_attr<true>() : fuse::set_attr<false>();
     if (e != cudaSuccess)
         return e;
+    // an ordinary launch (its loads go through L1, so it starts only once
+    // the kernel before it has finished)
     if (fwd)
         fuse::fuse_kernel<true><<<grid, fuse::kThreads, fuse::smem_bytes(true), stream>>>(w);
     else
