@@ -22,52 +22,65 @@ namespace frag {
 
 constexpr int kCtrThreads = 256;
 
-struct CtrSmem {
+struct __align__(16) CtrSmem {
     uint32_t te[256 * 32]; // table 0, one copy per lane
-    uint32_t rk[44];
+    uint4 rk[11];          // round keys, one 16-byte load per round
+    uint4 rk_last_le;      // last round key with its bytes in stream order
 };
 
-__device__ __forceinline__ uint32_t ror(uint32_t v, int s) { return __funnelshift_r(v, v, s); }
+// byte k of v, zero-extended
+__device__ __forceinline__ uint32_t byte_of(uint32_t v, uint32_t k) { return __byte_perm(v, 0u, 0x4440u | k); }
 
-// one AES-128 block (FIPS-197 cipher): counter nonce || blk, keystream words
-// in big-endian order
+// entry x of table 0 (lane-replicated: word 32 x + lane, so one multiply-add
+// gives the address)
+__device__ __forceinline__ uint32_t t0(const uint32_t *tel, uint32_t x) { return tel[x << 5]; }
+
+// rotations by whole bytes: tables 1..3 from table 0
+__device__ __forceinline__ uint32_t ror8(uint32_t v) { return __byte_perm(v, v, 0x0321); }
+__device__ __forceinline__ uint32_t ror16(uint32_t v) { return __byte_perm(v, v, 0x1032); }
+__device__ __forceinline__ uint32_t ror24(uint32_t v) { return __byte_perm(v, v, 0x2103); }
+
+// one AES-128 block (FIPS-197 cipher, 32-bit table form) of the counter
+// block nonce || blk; the keystream words come back with their bytes in
+// stream order (ks[0] byte 0 is keystream byte 0), ready to XOR with
+// little-endian loads
 __device__ __forceinline__ void ctr_block(const CtrSmem &m, uint32_t lane, uint64_t nonce,
                                           uint64_t blk, uint32_t ks[4])
 {
-    const uint32_t *te = m.te + lane;
-    uint32_t s0 = (uint32_t)(nonce >> 32) ^ m.rk[0];
-    uint32_t s1 = (uint32_t)nonce ^ m.rk[1];
-    uint32_t s2 = (uint32_t)(blk >> 32) ^ m.rk[2];
-    uint32_t s3 = (uint32_t)blk ^ m.rk[3];
+    const uint32_t *tel = m.te + lane;
+    const uint4 k0 = m.rk[0];
+    uint32_t s0 = (uint32_t)(nonce >> 32) ^ k0.x;
+    uint32_t s1 = (uint32_t)nonce ^ k0.y;
+    uint32_t s2 = (uint32_t)(blk >> 32) ^ k0.z;
+    uint32_t s3 = (uint32_t)blk ^ k0.w;
 #pragma unroll
     for (int r = 1; r < 10; ++r) {
-        const uint32_t t0 = te[(s0 >> 24) << 5] ^ ror(te[((s1 >> 16) & 255) << 5], 8) ^
-                            ror(te[((s2 >> 8) & 255) << 5], 16) ^ ror(te[(s3 & 255) << 5], 24) ^
-                            m.rk[4 * r];
-        const uint32_t t1 = te[(s1 >> 24) << 5] ^ ror(te[((s2 >> 16) & 255) << 5], 8) ^
-                            ror(te[((s3 >> 8) & 255) << 5], 16) ^ ror(te[(s0 & 255) << 5], 24) ^
-                            m.rk[4 * r + 1];
-        const uint32_t t2 = te[(s2 >> 24) << 5] ^ ror(te[((s3 >> 16) & 255) << 5], 8) ^
-                            ror(te[((s0 >> 8) & 255) << 5], 16) ^ ror(te[(s1 & 255) << 5], 24) ^
-                            m.rk[4 * r + 2];
-        const uint32_t t3 = te[(s3 >> 24) << 5] ^ ror(te[((s0 >> 16) & 255) << 5], 8) ^
-                            ror(te[((s1 >> 8) & 255) << 5], 16) ^ ror(te[(s2 & 255) << 5], 24) ^
-                            m.rk[4 * r + 3];
-        s0 = t0;
-        s1 = t1;
-        s2 = t2;
-        s3 = t3;
+        const uint4 k = m.rk[r];
+        const uint32_t n0 = t0(tel, byte_of(s0, 3)) ^ ror8(t0(tel, byte_of(s1, 2))) ^
+                            ror16(t0(tel, byte_of(s2, 1))) ^ ror24(t0(tel, byte_of(s3, 0))) ^ k.x;
+        const uint32_t n1 = t0(tel, byte_of(s1, 3)) ^ ror8(t0(tel, byte_of(s2, 2))) ^
+                            ror16(t0(tel, byte_of(s3, 1))) ^ ror24(t0(tel, byte_of(s0, 0))) ^ k.y;
+        const uint32_t n2 = t0(tel, byte_of(s2, 3)) ^ ror8(t0(tel, byte_of(s3, 2))) ^
+                            ror16(t0(tel, byte_of(s0, 1))) ^ ror24(t0(tel, byte_of(s1, 0))) ^ k.z;
+        const uint32_t n3 = t0(tel, byte_of(s3, 3)) ^ ror8(t0(tel, byte_of(s0, 2))) ^
+                            ror16(t0(tel, byte_of(s1, 1))) ^ ror24(t0(tel, byte_of(s2, 0))) ^ k.w;
+        s0 = n0;
+        s1 = n1;
+        s2 = n2;
+        s3 = n3;
     }
-    // last round: SubBytes, ShiftRows, AddRoundKey; S[x] is byte 2 of table 0
-    auto sb = [&](uint32_t x) { return (te[x << 5] >> 16) & 255u; };
-    ks[0] = ((sb(s0 >> 24) << 24) | (sb((s1 >> 16) & 255) << 16) | (sb((s2 >> 8) & 255) << 8) |
-             sb(s3 & 255)) ^ m.rk[40];
-    ks[1] = ((sb(s1 >> 24) << 24) | (sb((s2 >> 16) & 255) << 16) | (sb((s3 >> 8) & 255) << 8) |
-             sb(s0 & 255)) ^ m.rk[41];
-    ks[2] = ((sb(s2 >> 24) << 24) | (sb((s3 >> 16) & 255) << 16) | (sb((s0 >> 8) & 255) << 8) |
-             sb(s1 & 255)) ^ m.rk[42];
-    ks[3] = ((sb(s3 >> 24) << 24) | (sb((s0 >> 16) & 255) << 16) | (sb((s1 >> 8) & 255) << 8) |
-             sb(s2 & 255)) ^ m.rk[43];
+    // last round: SubBytes, ShiftRows, AddRoundKey.  S[x] is byte 1 (and 2)
+    // of table-0 entry x; the output bytes go straight to stream order.
+    auto sub4 = [&](uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+        const uint32_t lo = __byte_perm(t0(tel, byte_of(a, 3)), t0(tel, byte_of(b, 2)), 0x0051);
+        const uint32_t hi = __byte_perm(t0(tel, byte_of(c, 1)), t0(tel, byte_of(d, 0)), 0x0051);
+        return __byte_perm(lo, hi, 0x5410);
+    };
+    const uint4 kl = m.rk_last_le;
+    ks[0] = sub4(s0, s1, s2, s3) ^ kl.x;
+    ks[1] = sub4(s1, s2, s3, s0) ^ kl.y;
+    ks[2] = sub4(s2, s3, s0, s1) ^ kl.z;
+    ks[3] = sub4(s3, s0, s1, s2) ^ kl.w;
 }
 
 __global__ void __launch_bounds__(kCtrThreads) ctr_kernel(CtrWork w)
@@ -85,8 +98,12 @@ __global__ void __launch_bounds__(kCtrThreads) ctr_kernel(CtrWork w)
         for (int k = 0; k < 32; ++k)
             m.te[(base + k) * 32 + lane] = __shfl_sync(0xffffffffu, v, k);
     }
-    for (int i = threadIdx.x; i < 44; i += blockDim.x)
-        m.rk[i] = w.round_keys[i];
+    for (int i = threadIdx.x; i < 44; i += blockDim.x) {
+        const uint32_t k = w.round_keys[i];
+        (&m.rk[0].x)[i] = k;
+        if (i >= 40)
+            (&m.rk_last_le.x)[i - 40] = __byte_perm(k, 0, 0x0123);
+    }
     __syncthreads();
     const uint64_t nchunks = w.chunks ? w.nchunks
                                       : (w.single.nblocks + w.single_chunk - 1) / w.single_chunk;
@@ -111,15 +128,15 @@ __global__ void __launch_bounds__(kCtrThreads) ctr_kernel(CtrWork w)
                 // fragment while this grid was already resident, so the
                 // read-only (non-coherent) path is not allowed here
                 const uint4 t = __ldcg(reinterpret_cast<const uint4 *>(ch.in + o));
-                uint4 r; // keystream bytes in stream order = big-endian words
-                r.x = t.x ^ __byte_perm(ks[0], 0, 0x0123);
-                r.y = t.y ^ __byte_perm(ks[1], 0, 0x0123);
-                r.z = t.z ^ __byte_perm(ks[2], 0, 0x0123);
-                r.w = t.w ^ __byte_perm(ks[3], 0, 0x0123);
+                uint4 r;
+                r.x = t.x ^ ks[0];
+                r.y = t.y ^ ks[1];
+                r.z = t.z ^ ks[2];
+                r.w = t.w ^ ks[3];
                 *reinterpret_cast<uint4 *>(ch.out + o) = r;
             } else {
                 for (int k = 0; k < 16 && o + (uint64_t)k < ch.bytes; ++k)
-                    ch.out[o + k] = (uint8_t)(__ldcg(ch.in + o + k) ^ (uint8_t)(ks[k >> 2] >> (24 - 8 * (k & 3))));
+                    ch.out[o + k] = (uint8_t)(__ldcg(ch.in + o + k) ^ (uint8_t)(ks[k >> 2] >> (8 * (k & 3))));
             }
         }
     }

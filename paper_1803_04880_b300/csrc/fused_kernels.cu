@@ -64,7 +64,7 @@ constexpr int kThreads = 32 * kWarps;
 #define FUSE_FWD_MINB 4
 #endif
 #ifndef FUSE_INV_MINB
-#define FUSE_INV_MINB 5
+#define FUSE_INV_MINB 4
 #endif
 constexpr int kFwdDepth = FUSE_FWD_DEPTH;
 constexpr int kInvDepth = FUSE_INV_DEPTH;
@@ -101,18 +101,17 @@ __device__ __forceinline__ void cp_wait()
 {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
-__device__ __forceinline__ uint2 lds8(uint32_t a)
+// Shared-memory reads of the stage ring as ordinary loads, so the compiler
+// may schedule them freely; they stay after cp.async.wait_group, whose asm
+// clobbers memory.  `a` is a shared-window address like the cp.async
+// destinations.
+extern __shared__ __align__(16) uint8_t g_fuse_smem[];
+__device__ __forceinline__ const uint8_t *ring_ptr(uint32_t a)
 {
-    uint2 v;
-    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a) : "memory");
-    return v;
+    return g_fuse_smem + (a - (uint32_t)__cvta_generic_to_shared(g_fuse_smem));
 }
-__device__ __forceinline__ uint32_t lds4(uint32_t a)
-{
-    uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-    return v;
-}
+__device__ __forceinline__ uint2 lds8(uint32_t a) { return *reinterpret_cast<const uint2 *>(ring_ptr(a)); }
+__device__ __forceinline__ uint32_t lds4(uint32_t a) { return *reinterpret_cast<const uint32_t *>(ring_ptr(a)); }
 
 // int16 stores at element index idx of a band (streaming: never re-read here)
 __device__ __forceinline__ void st8(uint8_t *band, uint64_t idx, uint32_t a, uint32_t b)
