@@ -24,7 +24,8 @@
 //             (undo Eq. 5.2, then Eq. 5.1) emits two rows of the level below
 //             per coefficient row, the row inverse makes them LL samples, and
 //             level 1 ends in level-0 rows 8t-7 .. 8t.  A unit first runs one
-//             iteration (two with three levels) that stores nothing.
+//             iteration that stores nothing (with three levels it also loads
+//             the level-3 d row two above its first).
 //
 // Loads: each lane copies its own 8 (or 4) bytes of every row it needs into a
 // per-warp ring of shared-memory stages with cp.async, two iterations ahead,
@@ -680,7 +681,10 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
     const int F = (int)b.F;
     const int t_begin = (int)(sy * b.seg_iters);
     const int t_end = min(t_begin + (int)b.seg_iters, (int)b.iters);
-    const int t_first = max(t_begin - (F == 3 ? 2 : 1), 0);
+    // one iteration rebuilds the column state of every level above the
+    // unit's first row, given d of level-3 row t_begin - 2 (three levels),
+    // which is loaded here instead of running a second iteration
+    const int t_first = max(t_begin - 1, 0);
     const int t_fast_end = (int)b.iters - 2;
 
 #pragma unroll
@@ -692,6 +696,12 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
     for (int k = 0; k < 4; ++k)
         S.x1[k] = S.d1[k] = kB2;
     S.x2[0] = S.x2[1] = S.d2[0] = S.d2[1] = S.x3 = S.d3 = kB2;
+    if (F == 3 && t_begin >= 2 && ln.loads) {
+        const uint64_t e = (uint64_t)(t_begin - 2) * (b.W >> 3) + ((uint32_t)ln.c0 >> 3);
+        const uint32_t lh = __ldg(reinterpret_cast<const unsigned short *>(b.band[2][1]) + e);
+        const uint32_t hh = __ldg(reinterpret_cast<const unsigned short *>(b.band[2][2]) + e);
+        S.d3 = in16(lh | (hh << 16));
+    }
 
     for (int t = t_first; t < t_end; ++t) {
         inv_issue(b, ln, t + kInvDepth - 1, t_end, ring_lane8, ring_lane4);
