@@ -56,8 +56,17 @@ def _load():
                                        _u8p, ctypes.c_uint64, _u8p, _u8p]
         lib.oracle_recover.argtypes = [_u8p, _u8p, ctypes.c_uint64, ctypes.c_uint32,
                                        ctypes.c_uint32, _u8p, ctypes.c_uint64, _u8p]
+        lib.oracle_block_sizes.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                           ctypes.c_uint32, _u64p, _u64p, _u64p]
+        lib.oracle_protect_blocks.argtypes = [_u8p, ctypes.c_uint64, ctypes.c_uint32,
+                                              ctypes.c_uint32, ctypes.c_uint32, _u8p,
+                                              ctypes.c_uint64, _u8p, _u8p]
+        lib.oracle_recover_blocks.argtypes = [_u8p, _u8p, ctypes.c_uint64, ctypes.c_uint32,
+                                              ctypes.c_uint32, ctypes.c_uint32, _u8p,
+                                              ctypes.c_uint64, _u8p]
         for f in ("oracle_dwt53_fwd_2d", "oracle_dwt53_inv_2d", "oracle_sizes", "oracle_protect",
-                  "oracle_recover"):
+                  "oracle_recover", "oracle_block_sizes", "oracle_protect_blocks",
+                  "oracle_recover_blocks"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -128,41 +137,56 @@ def aes128_ctr_xor(key, nonce: int, first_block: int, data) -> bytes:
     return d.tobytes()
 
 
-def sizes(n: int, width: int, levels: int):
-    """(H, private_bytes, public_bytes) for n input bytes."""
+def sizes(n: int, width: int, levels: int, block: int = 0):
+    """(H, private_bytes, public_bytes) for n input bytes; block > 0: the
+    block mode with B x B blocks."""
     H, pb, ub = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
-    st = _load().oracle_sizes(n, width, levels, ctypes.byref(H), ctypes.byref(pb),
-                              ctypes.byref(ub))
+    if block:
+        st = _load().oracle_block_sizes(n, width, levels, block, ctypes.byref(H),
+                                        ctypes.byref(pb), ctypes.byref(ub))
+    else:
+        st = _load().oracle_sizes(n, width, levels, ctypes.byref(H), ctypes.byref(pb),
+                                  ctypes.byref(ub))
     if st:
-        raise ValueError("invalid plan: width=%d levels=%d" % (width, levels))
+        raise ValueError("invalid plan: width=%d levels=%d block=%d" % (width, levels, block))
     return H.value, pb.value, ub.value
 
 
-def protect(data, width: int, levels: int, key, nonce: int):
-    """Bytes -> (private fragment, public fragment), both uint8 arrays."""
+def protect(data, width: int, levels: int, key, nonce: int, block: int = 0):
+    """Bytes -> (private fragment, public fragment), both uint8 arrays;
+    block > 0: every B x B block transformed as an image of its own."""
     buf = np.ascontiguousarray(np.frombuffer(data, dtype=np.uint8) if isinstance(data, (bytes, bytearray)) else data, dtype=np.uint8).reshape(-1)
     n = buf.size
-    _, pb, ub = sizes(n, width, levels)
+    _, pb, ub = sizes(n, width, levels, block)
     priv = np.zeros(pb, dtype=np.uint8)
     pub = np.zeros(ub, dtype=np.uint8)
     k = _key(key)
-    st = _load().oracle_protect(_p(buf, _u8p), n, width, levels, _p(k, _u8p), nonce,
-                                _p(priv, _u8p), _p(pub, _u8p))
+    if block:
+        st = _load().oracle_protect_blocks(_p(buf, _u8p), n, width, levels, block, _p(k, _u8p),
+                                           nonce, _p(priv, _u8p), _p(pub, _u8p))
+    else:
+        st = _load().oracle_protect(_p(buf, _u8p), n, width, levels, _p(k, _u8p), nonce,
+                                    _p(priv, _u8p), _p(pub, _u8p))
     if st:
         raise RuntimeError("oracle_protect failed: %d" % st)
     return priv, pub
 
 
-def recover(priv, pub, n: int, width: int, levels: int, key, nonce: int) -> np.ndarray:
-    _, pb, ub = sizes(n, width, levels)
+def recover(priv, pub, n: int, width: int, levels: int, key, nonce: int,
+            block: int = 0) -> np.ndarray:
+    _, pb, ub = sizes(n, width, levels, block)
     priv = np.ascontiguousarray(priv, dtype=np.uint8).reshape(-1)
     pub = np.ascontiguousarray(pub, dtype=np.uint8).reshape(-1)
     if priv.size != pb or pub.size != ub:
         raise ValueError("fragment sizes do not match the plan")
     out = np.zeros(n, dtype=np.uint8)
     k = _key(key)
-    st = _load().oracle_recover(_p(priv, _u8p), _p(pub, _u8p), n, width, levels, _p(k, _u8p),
-                                nonce, _p(out, _u8p))
+    if block:
+        st = _load().oracle_recover_blocks(_p(priv, _u8p), _p(pub, _u8p), n, width, levels,
+                                           block, _p(k, _u8p), nonce, _p(out, _u8p))
+    else:
+        st = _load().oracle_recover(_p(priv, _u8p), _p(pub, _u8p), n, width, levels,
+                                    _p(k, _u8p), nonce, _p(out, _u8p))
     if st:
         raise RuntimeError("oracle_recover failed: %d" % st)
     return out

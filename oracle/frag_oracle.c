@@ -41,6 +41,10 @@
  *     (8 bytes, big-endian), block index = byte offset / 16 from 0; a short
  *     last block uses a prefix of its keystream block.
  *
+ * Block mode (Sec. 5.2.1): every B x B block (8 x 8 in the thesis) of the
+ * matrix is transformed as an image of its own; the band images keep the
+ * whole-matrix shapes, block (bi, bj) filling one tile of each.
+ *
  * Pins (tests/test_oracle_*.py): the thesis's matrix A and F(4,4) weights,
  * its magnitude bounds (as recomputed where misprinted), a hand-worked 2x2
  * example that fixes the row-before-column order, closed forms for length 2,
@@ -453,6 +457,187 @@ int oracle_recover(const uint8_t *priv, const uint8_t *pub, uint64_t n, uint32_t
         p += 2 * h * w;
     }
     st = oracle_dwt53_inv_2d(a, (int64_t)H, (int64_t)W, (int)L);
+    for (i = 0; i < n && st == ORACLE_OK; i++) {
+        int32_t v = a[i] + 128;
+        if (v < 0 || v > 255)
+            st = ORACLE_ERANGE;
+        else
+            out[i] = (uint8_t)v;
+    }
+    free(a);
+    free(plain);
+    return st;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Block mode (Sec. 5.2.1): the data is cut into chunks seen as matrices    */
+/* and every matrix is processed block by block (8 x 8 in the thesis, "the */
+/* block size chosen can be changed"), each block being transformed as an  */
+/* image of its own: L levels inside the block, the symmetric extension at  */
+/* the block's own borders.  Layout (a reading): band (l, k) of the whole   */
+/* matrix keeps its H_l x W_l shape and block (bi, bj) fills the tile of    */
+/* rows [bi B/2^l, (bi+1) B/2^l) and columns [bj B/2^l, (bj+1) B/2^l) of    */
+/* it; the fragments are then stored exactly as in the whole-matrix mode.   */
+/* ---------------------------------------------------------------------- */
+
+/* H = ceil(n / W) rounded up to a multiple of B; W must be a multiple of B
+ * and B a multiple of 2^L */
+int oracle_block_sizes(uint64_t n, uint32_t W, uint32_t L, uint32_t B, uint64_t *H,
+                       uint64_t *priv_bytes, uint64_t *pub_bytes)
+{
+    uint64_t rows;
+    if (W == 0 || L == 0 || L > 16 || B == 0 || (B % (1u << L)) != 0 || (W % B) != 0)
+        return ORACLE_EINVAL;
+    rows = (n + W - 1) / W;
+    rows = (rows + B - 1) / B * B;
+    *H = rows;
+    *priv_bytes = 2 * (rows >> L) * (uint64_t)(W >> L);
+    *pub_bytes = 2 * (rows * (uint64_t)W) - *priv_bytes;
+    return ORACLE_OK;
+}
+
+/* move the bands of one transformed block (Mallat layout in blk, B x B)
+ * to (to_global = 1) or from (0) their tiles in the whole-matrix Mallat
+ * layout of a (H x W) */
+static void block_tiles(int32_t *a, int64_t H, int64_t W, int32_t *blk, int64_t B, int L,
+                        int64_t bi, int64_t bj, int to_global)
+{
+    int l, k;
+    int64_t r, c;
+    for (l = L; l >= 1; l--) {
+        const int64_t b = B >> l, Hl = H >> l, Wl = W >> l;
+        for (k = (l == L ? -1 : 0); k < 3; k++) {
+            /* k = -1: LL_L; 0: HL (top-right); 1: LH (bottom-left); 2: HH */
+            const int64_t br = (k == 1 || k == 2) ? b : 0, bc = (k == 0 || k == 2) ? b : 0;
+            const int64_t gr = (k == 1 || k == 2) ? Hl : 0, gc = (k == 0 || k == 2) ? Wl : 0;
+            for (r = 0; r < b; r++)
+                for (c = 0; c < b; c++) {
+                    int32_t *g = &a[(gr + bi * b + r) * W + gc + bj * b + c];
+                    int32_t *t = &blk[(br + r) * B + bc + c];
+                    if (to_global)
+                        *g = *t;
+                    else
+                        *t = *g;
+                }
+        }
+    }
+}
+
+/* block-mode transform of the level-shifted matrix a, in place, forward or
+ * inverse */
+static int blocks_2d(int32_t *a, int64_t H, int64_t W, int L, int64_t B, int fwd)
+{
+    int64_t bi, bj, r, c;
+    int32_t *src = (int32_t *)malloc(sizeof(int32_t) * (size_t)(H * W));
+    int32_t *blk = (int32_t *)malloc(sizeof(int32_t) * (size_t)(B * B));
+    int st = ORACLE_OK;
+    if (!src || !blk) {
+        free(src);
+        free(blk);
+        return ORACLE_ENOMEM;
+    }
+    memcpy(src, a, sizeof(int32_t) * (size_t)(H * W));
+    for (bi = 0; bi < H / B && st == ORACLE_OK; bi++)
+        for (bj = 0; bj < W / B && st == ORACLE_OK; bj++) {
+            if (fwd) {
+                for (r = 0; r < B; r++)
+                    for (c = 0; c < B; c++)
+                        blk[r * B + c] = src[(bi * B + r) * W + bj * B + c];
+                st = oracle_dwt53_fwd_2d(blk, B, B, L);
+                block_tiles(a, H, W, blk, B, L, bi, bj, 1);
+            } else {
+                block_tiles(src, H, W, blk, B, L, bi, bj, 0);
+                st = oracle_dwt53_inv_2d(blk, B, B, L);
+                for (r = 0; r < B; r++)
+                    for (c = 0; c < B; c++)
+                        a[(bi * B + r) * W + bj * B + c] = blk[r * B + c];
+            }
+        }
+    free(src);
+    free(blk);
+    return st;
+}
+
+/* whole-matrix Mallat image <-> fragments (shared by both modes' callers) */
+static int store_fragments(const int32_t *a, uint64_t H, uint32_t W, uint32_t L,
+                           const uint8_t key[16], uint64_t nonce, uint64_t pb, uint8_t *priv,
+                           uint8_t *pub)
+{
+    int l, st;
+    uint8_t *p = pub;
+    st = store_band(a, W, 0, 0, (int64_t)(H >> L), (int64_t)(W >> L), priv); /* LL_L */
+    if (st == ORACLE_OK)
+        oracle_aes128_ctr_xor(key, nonce, 0, priv, pb);
+    for (l = (int)L; l >= 1 && st == ORACLE_OK; l--) {
+        int64_t h = (int64_t)(H >> l), w = (int64_t)(W >> l);
+        st = store_band(a, W, 0, w, h, w, p);
+        p += 2 * h * w;
+        if (st == ORACLE_OK)
+            st = store_band(a, W, h, 0, h, w, p);
+        p += 2 * h * w;
+        if (st == ORACLE_OK)
+            st = store_band(a, W, h, w, h, w, p);
+        p += 2 * h * w;
+    }
+    return st;
+}
+
+int oracle_protect_blocks(const uint8_t *in, uint64_t n, uint32_t W, uint32_t L, uint32_t B,
+                          const uint8_t key[16], uint64_t nonce, uint8_t *priv, uint8_t *pub)
+{
+    uint64_t H, pb, ub, i;
+    int32_t *a;
+    int st;
+    if (oracle_block_sizes(n, W, L, B, &H, &pb, &ub) != ORACLE_OK)
+        return ORACLE_EINVAL;
+    if (n == 0)
+        return ORACLE_OK;
+    a = (int32_t *)malloc(sizeof(int32_t) * (size_t)(H * W));
+    if (!a)
+        return ORACLE_ENOMEM;
+    for (i = 0; i < H * W; i++) /* map + level shift; past n the byte is 0 */
+        a[i] = (int32_t)(i < n ? in[i] : 0) - 128;
+    st = blocks_2d(a, (int64_t)H, (int64_t)W, (int)L, (int64_t)B, 1);
+    if (st == ORACLE_OK)
+        st = store_fragments(a, H, W, L, key, nonce, pb, priv, pub);
+    free(a);
+    return st;
+}
+
+int oracle_recover_blocks(const uint8_t *priv, const uint8_t *pub, uint64_t n, uint32_t W,
+                          uint32_t L, uint32_t B, const uint8_t key[16], uint64_t nonce,
+                          uint8_t *out)
+{
+    uint64_t H, pb, ub, i;
+    int32_t *a;
+    uint8_t *plain;
+    const uint8_t *p;
+    int l, st;
+    if (oracle_block_sizes(n, W, L, B, &H, &pb, &ub) != ORACLE_OK)
+        return ORACLE_EINVAL;
+    if (n == 0)
+        return ORACLE_OK;
+    a = (int32_t *)malloc(sizeof(int32_t) * (size_t)(H * W));
+    plain = (uint8_t *)malloc((size_t)pb);
+    if (!a || !plain) {
+        free(a);
+        free(plain);
+        return ORACLE_ENOMEM;
+    }
+    memcpy(plain, priv, (size_t)pb);
+    oracle_aes128_ctr_xor(key, nonce, 0, plain, pb);
+    load_band(a, W, 0, 0, (int64_t)(H >> L), (int64_t)(W >> L), plain);
+    p = pub;
+    for (l = (int)L; l >= 1; l--) {
+        int64_t h = (int64_t)(H >> l), w = (int64_t)(W >> l);
+        load_band(a, W, 0, w, h, w, p);
+        p += 2 * h * w;
+        load_band(a, W, h, 0, h, w, p);
+        p += 2 * h * w;
+        load_band(a, W, h, w, h, w, p);
+        p += 2 * h * w;
+    }
+    st = blocks_2d(a, (int64_t)H, (int64_t)W, (int)L, (int64_t)B, 0);
     for (i = 0; i < n && st == ORACLE_OK; i++) {
         int32_t v = a[i] + 128;
         if (v < 0 || v > 255)
