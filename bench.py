@@ -39,7 +39,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3l2", "c3l4", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2blocks", "c3l2", "c3l4", "c4", "c5"])
     ap.add_argument("--items", type=int, default=10000, help="c4: number of buffers")
     ap.add_argument("--requests", type=int, default=240, help="c5: requests per load level")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -64,6 +64,14 @@ def _workload(name):
         return ({"workload": "bitmap 3x4096x4096 u8, 5/3 DWT 3 levels, LL_3 AES-128-CTR",
                  "planes": 3, "width": 4096, "levels": 3},
                 [(4096, 3, i, planes[i].reshape(-1)) for i in range(planes.shape[0])])
+    if name == "c2blocks":
+        # the thesis's own arrangement (Sec. 5.2.1): every 8 x 8 block on its
+        # own, two levels, LL_2 (4 of 64 coefficients) private
+        planes = wl.c2()
+        return ({"workload": "bitmap 3x4096x4096 u8 in 8x8 blocks, 5/3 DWT 2 levels per block, "
+                             "LL_2 AES-128-CTR", "planes": 3, "width": 4096, "levels": 2,
+                 "block": 8},
+                [(4096, 2, i, planes[i].reshape(-1)) for i in range(planes.shape[0])])
     L = 2 if name == "c3l2" else 4
     return ({"workload": "256 MiB mixed buffer (uniform|text|int32 walk), width 8192, "
                          "5/3 DWT %d levels, LL_%d AES-128-CTR" % (L, L),
@@ -141,8 +149,8 @@ def run_reference(args, rank):
     times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        p, u = oracle.protect(sample, W, L, wl.KEY, nonce)
-        oracle.recover(p, u, n, W, L, wl.KEY, nonce)
+        p, u = oracle.protect(sample, W, L, wl.KEY, nonce, block=desc.get("block", 0))
+        oracle.recover(p, u, n, W, L, wl.KEY, nonce, block=desc.get("block", 0))
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt)
@@ -188,15 +196,15 @@ def _traffic(workload, kernel):
     return None
 
 
-def _cpu_baseline(items):
+def _cpu_baseline(items, block=0):
     import oracle
     from paper_1803_04880_b300 import workloads as wl
     W, L, nonce, data = items[0]
     n = data.size
     reps, t0 = 0, time.perf_counter()
     while True:
-        p, u = oracle.protect(data, W, L, wl.KEY, nonce)
-        oracle.recover(p, u, n, W, L, wl.KEY, nonce)
+        p, u = oracle.protect(data, W, L, wl.KEY, nonce, block=block)
+        oracle.recover(p, u, n, W, L, wl.KEY, nonce, block=block)
         reps += 1
         el = time.perf_counter() - t0
         if el >= 10.0 or reps >= 20:
@@ -221,7 +229,10 @@ def run_ours(args, rank, world, local_rank):
     ins, privs, pubs, outs, pitems, ritems = [], [], [], [], [], []
     n_total = 0
     for W, L, nonce, data in items:
-        plan = plans.setdefault((W, L), fr.Plan(W, L))
+        if (W, L) not in plans:
+            plans[(W, L)] = fr.Plan(W, L)
+            plans[(W, L)].set_block(desc.get("block", 0))
+        plan = plans[(W, L)]
         n = data.size
         _, pb, ub = plan.sizes(n)
         t = torch.from_numpy(data).to(dev)
@@ -346,6 +357,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = alg_bytes / (t_dom / 1e3) / 1e9
     names = {"fused": "fuse_kernel<%s> (%s: levels 1..3 of every plane, one launch)",
              "levels": "dag_kernel<%s> (%s: dependency-ordered levels, one launch)",
+             "blocks": "block_kernel<%s> (%s: every 8 x 8 block on its own, one launch)",
              "cipher": "ctr_kernel (%s%s: AES-128-CTR over the private fragments)"}
     label = names[dom_kind] % ("true" if dom_dir == "protect" else "false", dom_dir) \
         if dom_kind != "cipher" else names["cipher"] % (dom_dir, "")
@@ -384,7 +396,7 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = _cpu_baseline(items)
+        cpu = _cpu_baseline(items, desc.get("block", 0))
 
     if rank == 0:
         q = sorted(steps_ms)

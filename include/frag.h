@@ -125,6 +125,23 @@ typedef enum { FRAG_PATH_AUTO = 0, FRAG_PATH_LEVELS = 1 } frag_path;
 frag_status frag_plan_set_path(frag_plan plan, frag_path path);
 frag_status frag_plan_get_path(frag_plan plan, frag_path *path);
 
+/* Block mode (Sec. 5.2.1: every chunk is processed block by block, 8 x 8 in
+ * the thesis).  block = 0 (the default): the whole matrix is transformed.
+ * block = B: every B x B block of the matrix is transformed as an image of
+ * its own -- L levels inside the block, the symmetric extension at the
+ * block's own borders, so no block depends on another.  H becomes ceil(n /
+ * W) rounded up to a multiple of B, and the fragments keep the whole-matrix
+ * layout: band (l, k) is an H_l x W_l int16 image in which block (bi, bj)
+ * fills rows [bi B / 2^l, (bi + 1) B / 2^l) and columns [bj B / 2^l,
+ * (bj + 1) B / 2^l); the private fragment is LL_L - 128 laid out the same way
+ * and enciphered as always.  A chunk D_i of C x C bytes is a plan of width
+ * C.  FRAG_EINVAL for a NULL plan, a width that is not a multiple of B or a
+ * B below 2^L; FRAG_EUNSUPPORTED for B other than 0 or 8 (the CUDA path
+ * implements the thesis's 8 x 8 blocks, up to 3 levels).  The
+ * allocation-free call does not take block plans (FRAG_EUNSUPPORTED). */
+frag_status frag_plan_set_block(frag_plan plan, uint32_t block);
+frag_status frag_plan_get_block(frag_plan plan, uint32_t *block);
+
 /* AES-128 key (Sec. 5.2.1 protects the private fragment with AES-128): the
  * round keys are expanded on the host (FIPS-197 Sec. 5.2) and kept resident on
  * each device that uses the key.  The 16 bytes are copied. */
@@ -219,7 +236,8 @@ typedef enum {
     FRAG_KERNEL_FUSED = 0,  /* levels 1..3 in one pass down the rows */
     FRAG_KERNEL_LEVELS = 1, /* the dependency-ordered level kernel */
     FRAG_KERNEL_CIPHER = 2, /* AES-128-CTR over private fragments */
-    FRAG_KERNEL_KINDS = 3
+    FRAG_KERNEL_BLOCKS = 3, /* block mode (frag_plan_set_block) */
+    FRAG_KERNEL_KINDS = 4
 } frag_kernel_kind;
 frag_status frag_batch_set_timing(frag_batch batch, int enable);
 frag_status frag_batch_launch_times(frag_batch batch, double *ms, uint32_t *launches);

@@ -25,6 +25,7 @@ EXPORTS = [
     "frag_abi_version", "frag_plan_create", "frag_plan_destroy", "frag_plan_sizes",
     "frag_plan_set_tiling", "frag_plan_get_tiling", "frag_plan_set_schedule",
     "frag_plan_get_schedule", "frag_plan_set_path", "frag_plan_get_path",
+    "frag_plan_set_block", "frag_plan_get_block",
     "frag_key_create", "frag_key_destroy",
     "frag_protect", "frag_recover", "frag_protect_host", "frag_recover_host",
     "frag_protect_batch", "frag_recover_batch", "frag_batch_create_protect",
@@ -83,6 +84,8 @@ def lib():
         "frag_plan_set_schedule": ([vp, u32, u32], ctypes.c_int),
         "frag_plan_get_schedule": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u32)], ctypes.c_int),
         "frag_plan_set_path": ([vp, ctypes.c_int], ctypes.c_int),
+        "frag_plan_set_block": ([vp, u32], ctypes.c_int),
+        "frag_plan_get_block": ([vp, ctypes.POINTER(u32)], ctypes.c_int),
         "frag_plan_get_path": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "frag_key_create": ([ctypes.POINTER(vp), ctypes.c_char_p], ctypes.c_int),
         "frag_key_destroy": ([vp], ctypes.c_int),
@@ -178,6 +181,16 @@ class Plan:
     def path(self) -> int:
         v = ctypes.c_int()
         check(lib().frag_plan_get_path(self._h, ctypes.byref(v)))
+        return v.value
+
+    def set_block(self, block: int) -> None:
+        """Block mode: every block x block block transformed on its own
+        (0: the whole matrix; the CUDA path runs 8 x 8 blocks)."""
+        check(lib().frag_plan_set_block(self._h, block))
+
+    def block(self) -> int:
+        v = ctypes.c_uint32()
+        check(lib().frag_plan_get_block(self._h, ctypes.byref(v)))
         return v.value
 
     def tiling(self) -> Tuple[int, int, int]:
@@ -322,7 +335,7 @@ class Batch:
     def launches(self) -> int:
         return self.info()[0]
 
-    KERNEL_KINDS = ("fused", "levels", "cipher")
+    KERNEL_KINDS = ("fused", "levels", "cipher", "blocks")
 
     def set_timing(self, enable: bool = True) -> None:
         """Record a CUDA event pair around each kernel launch of run()."""
@@ -331,8 +344,8 @@ class Batch:
     def launch_times(self) -> dict:
         """{kind: (total ms, launches)} over the timed runs since the last
         call (waits for their events)."""
-        ms = (ctypes.c_double * 3)()
-        n = (ctypes.c_uint32 * 3)()
+        ms = (ctypes.c_double * len(self.KERNEL_KINDS))()
+        n = (ctypes.c_uint32 * len(self.KERNEL_KINDS))()
         check(lib().frag_batch_launch_times(self._h, ms, n))
         return {k: (ms[i], n[i]) for i, k in enumerate(self.KERNEL_KINDS)}
 

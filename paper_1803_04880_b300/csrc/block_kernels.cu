@@ -1,0 +1,634 @@
+// block_kernels.cu -- the block mode: every 8 x 8 block of the matrix is
+// transformed as an image of its own (Sec. 5.2.1: each chunk is processed
+// block by block, 8 x 8 in the thesis), up to three levels.
+//
+// One lane owns one block: it loads the block's 8 rows of 8 bytes (a warp
+// takes 32 neighbouring blocks, so every row it reads is 256 contiguous
+// bytes), runs every level in its registers and stores each band's tile of
+// the block.  The symmetric extension applies at the block's own borders,
+// so no lane needs another lane's samples: the mirrors x[8] = x[6] and
+// d[-1] = d[0] are fixed byte permutes.  Rows before columns at every level
+// (Eq. 5.1 predict, Eq. 5.2 update, Sec. 5.2.2), packed pairs as in the
+// other kernels (each 16-bit half holds v + 0x4000).
+//
+// Band layout (as in the whole-matrix mode): band (l, k) is an H_l x W_l
+// int16 image and block (bi, bj) fills rows [bi 8/2^l, (bi+1) 8/2^l) and
+// columns [bj 8/2^l, (bj+1) 8/2^l) of it; LL_L - 128 goes to `ll`.
+#include "frag_internal.cuh"
+#include "swar.cuh"
+
+namespace frag {
+namespace blk {
+
+using strm::from_i16x2;
+using strm::kB2;
+using strm::pavg;
+using strm::pq4;
+using strm::to_i16x2;
+
+constexpr int kWarps = 4;
+constexpr int kThreads = 32 * kWarps;
+constexpr uint32_t kQ4 = 0x20002000u; // the +2 of the update's floor, biased
+
+// ---------------------------------------------------------------------------
+// one row of the block, forward
+// ---------------------------------------------------------------------------
+
+// 8 bytes (w0, w1) -> P[0] = (s0, s1), P[1] = (s2, s3), P[2] = (d0, d1),
+// P[3] = (d2, d3)
+__device__ __forceinline__ void lift8(uint32_t w0, uint32_t w1, uint32_t (&P)[4])
+{
+    const uint32_t e01 = __byte_perm(w0, 0x40404040u, 0x4240); // (x0, x2)
+    const uint32_t o01 = __byte_perm(w0, 0x40404040u, 0x4341); // (x1, x3)
+    const uint32_t e23 = __byte_perm(w1, 0x40404040u, 0x4240); // (x4, x6)
+    const uint32_t o23 = __byte_perm(w1, 0x40404040u, 0x4341); // (x5, x7)
+    const uint32_t e12 = __byte_perm(e01, e23, 0x5432);         // (x2, x4)
+    const uint32_t e34 = __byte_perm(e23, e23, 0x3232);         // (x6, x8 = x6)
+    const uint32_t d01 = o01 - pavg(e01, e12) + kB2;            // Eq. 5.1
+    const uint32_t d23 = o23 - pavg(e23, e34) + kB2;
+    const uint32_t dm0 = __byte_perm(d01, d01, 0x1010);         // (d[-1] = d0, d0)
+    const uint32_t d12 = __byte_perm(d01, d23, 0x5432);         // (d1, d2)
+    P[0] = e01 + pq4(dm0, d01) - kQ4;                           // Eq. 5.2
+    P[1] = e23 + pq4(d12, d23) - kQ4;
+    P[2] = d01;
+    P[3] = d23;
+}
+
+// 4 samples (w0 = (y0, y1), w1 = (y2, y3)) -> L = (s0, s1), H = (d0, d1)
+__device__ __forceinline__ void lift4(uint32_t w0, uint32_t w1, uint32_t &L, uint32_t &H)
+{
+    const uint32_t e = __byte_perm(w0, w1, 0x5410);  // (y0, y2)
+    const uint32_t o = __byte_perm(w0, w1, 0x7632);  // (y1, y3)
+    const uint32_t es = __byte_perm(e, e, 0x3232);   // (y2, y4 = y2)
+    const uint32_t d = o - pavg(e, es) + kB2;
+    const uint32_t dm = __byte_perm(d, d, 0x1010);   // (d[-1] = d0, d0)
+    L = e + pq4(dm, d) - kQ4;
+    H = d;
+}
+
+// 2 samples z = (z0, z1) -> (s, d) in one word (s low, d high)
+__device__ __forceinline__ uint32_t lift2(uint32_t z)
+{
+    const uint32_t e = z & 0xffffu, o = z >> 16;
+    const uint32_t d = o - e + 0x4000u;                  // z2 = z0: o - floor((2 z0) / 2)
+    const uint32_t s = e + ((2 * d + 2) >> 2) - 0x2000u; // d[-1] = d0
+    return s | (d << 16);
+}
+
+// column lifting of R rows (R = 8, 4, 2) of NW words each, in place: rows
+// become s rows 0..R/2-1 then d rows (per word; the top d[-1] = d[0] and the
+// bottom x[R] = x[R-2] are the block's own borders)
+template <int R, int NW>
+__device__ __forceinline__ void col_lift(uint32_t (&x)[R][NW], uint32_t (&s)[R / 2][NW],
+                                         uint32_t (&d)[R / 2][NW])
+{
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q)
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const uint32_t e1 = (2 * q + 2 < R) ? x[2 * q + 2][k] : x[2 * q][k];
+            d[q][k] = x[2 * q + 1][k] - pavg(x[2 * q][k], e1) + kB2; // Eq. 5.1
+        }
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q)
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const uint32_t dm = q ? d[q - 1][k] : d[0][k];
+            s[q][k] = x[2 * q][k] + pq4(dm, d[q][k]) - kQ4; // Eq. 5.2
+        }
+}
+
+// inverse of col_lift: s, d rows -> R rows
+template <int R, int NW>
+__device__ __forceinline__ void col_unlift(const uint32_t (&s)[R / 2][NW], const uint32_t (&d)[R / 2][NW],
+                                           uint32_t (&x)[R][NW])
+{
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q)
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const uint32_t dm = q ? d[q - 1][k] : d[0][k];
+            x[2 * q][k] = s[q][k] - pq4(dm, d[q][k]) + kQ4; // undo Eq. 5.2
+        }
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q)
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const uint32_t e1 = (2 * q + 2 < R) ? x[2 * q + 2][k] : x[2 * q][k];
+            x[2 * q + 1][k] = d[q][k] + pavg(x[2 * q][k], e1) - kB2; // undo Eq. 5.1
+        }
+}
+
+// row inverses
+__device__ __forceinline__ uint2 unlift8(const uint32_t (&w)[4])
+{
+    const uint32_t hm0 = __byte_perm(w[2], w[2], 0x1010); // (d[-1] = d0, d0)
+    const uint32_t h12 = __byte_perm(w[2], w[3], 0x5432);
+    const uint32_t e01 = w[0] - pq4(hm0, w[2]) + kQ4;     // undo Eq. 5.2
+    const uint32_t e23 = w[1] - pq4(h12, w[3]) + kQ4;
+    const uint32_t e12 = __byte_perm(e01, e23, 0x5432);
+    const uint32_t e34 = __byte_perm(e23, e23, 0x3232);   // x8 = x6
+    const uint32_t o01 = w[2] + pavg(e01, e12) - kB2;     // undo Eq. 5.1
+    const uint32_t o23 = w[3] + pavg(e23, e34) - kB2;
+    return make_uint2(__byte_perm(e01, o01, 0x6240), __byte_perm(e23, o23, 0x6240));
+}
+
+__device__ __forceinline__ void unlift4(uint32_t L, uint32_t H, uint32_t &w0, uint32_t &w1)
+{
+    const uint32_t hm = __byte_perm(H, H, 0x1010);
+    const uint32_t e = L - pq4(hm, H) + kQ4;       // (y0, y2)
+    const uint32_t es = __byte_perm(e, e, 0x3232); // (y2, y4 = y2)
+    const uint32_t o = H + pavg(e, es) - kB2;      // (y1, y3)
+    w0 = __byte_perm(e, o, 0x5410);
+    w1 = __byte_perm(e, o, 0x7632);
+}
+
+__device__ __forceinline__ uint32_t unlift2(uint32_t w)
+{
+    const uint32_t s = w & 0xffffu, d = w >> 16;
+    const uint32_t z0 = s - ((2 * d + 2) >> 2) + 0x2000u;
+    const uint32_t z1 = d + z0 - 0x4000u;
+    return z0 | (z1 << 16);
+}
+
+// ---------------------------------------------------------------------------
+// band tiles
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ll_final(uint32_t w) { return to_i16x2(w - 0x00800080u); }
+
+// row r of the tile (b values) of block (bi, bj) in an H_l x W_l int16 band
+__device__ __forceinline__ uint8_t *tile_row(uint8_t *band, uint32_t Wl, uint32_t b, uint64_t bi,
+                                             uint32_t bj, uint32_t r)
+{
+    return band + 2 * ((bi * b + r) * (uint64_t)Wl + (uint64_t)bj * b);
+}
+
+// b int16 values (w0, w1 as int16 pairs); `vec`: p is aligned to the store
+__device__ __forceinline__ void st_tile(uint8_t *p, uint32_t b, uint32_t w0, uint32_t w1, bool vec)
+{
+    if (!vec) {
+        const uint32_t h[4] = {w0 & 0xffffu, w0 >> 16, w1 & 0xffffu, w1 >> 16};
+        for (uint32_t i = 0; i < b; ++i) {
+            p[2 * i] = (uint8_t)h[i];
+            p[2 * i + 1] = (uint8_t)(h[i] >> 8);
+        }
+    } else if (b == 4)
+        __stcs(reinterpret_cast<uint2 *>(p), make_uint2(w0, w1));
+    else if (b == 2)
+        __stcs(reinterpret_cast<unsigned int *>(p), w0);
+    else
+        __stcs(reinterpret_cast<unsigned short *>(p), (unsigned short)w0);
+}
+
+__device__ __forceinline__ void ld_tile(const uint8_t *p, uint32_t b, uint32_t &w0, uint32_t &w1,
+                                        bool vec)
+{
+    if (!vec) {
+        uint32_t h[4] = {0, 0, 0, 0};
+        for (uint32_t i = 0; i < b; ++i)
+            h[i] = (uint32_t)__ldg(p + 2 * i) | ((uint32_t)__ldg(p + 2 * i + 1) << 8);
+        w0 = h[0] | (h[1] << 16);
+        w1 = h[2] | (h[3] << 16);
+    } else if (b == 4) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+        w0 = v.x;
+        w1 = v.y;
+    } else if (b == 2) {
+        w0 = __ldg(reinterpret_cast<const unsigned int *>(p));
+        w1 = 0;
+    } else {
+        w0 = __ldg(reinterpret_cast<const unsigned short *>(p));
+        w1 = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one block, forward and inverse
+// ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// staged loads: each warp copies the rows of its next blocks into a ring of
+// shared-memory stages with cp.async (each lane its own bytes, so no
+// barrier), two blocks ahead of the one it computes
+// ---------------------------------------------------------------------------
+constexpr int kDepth = 3;
+constexpr int kFwdStage = 8 * 256; // 8 rows x 32 lanes x 8 bytes
+// inverse stage: level-1 bands (HL, LH, HH) x 4 rows, 8 bytes a lane, then
+// LL_1 rows (one level) or the level-2 bands x 2 rows (4 bytes a lane)
+// followed by LL_2 rows (two levels) or the four level-3 words (three)
+constexpr int kInvX = 12 * 256;
+constexpr int kInvL2Ll = kInvX + 6 * 128;
+constexpr int kInvL3 = kInvX + 6 * 128;
+constexpr int kInvStage = kInvL3 + 4 * 128;
+
+extern __shared__ __align__(16) uint8_t g_block_smem[];
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp8(uint32_t dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp4(uint32_t dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// plain loads of the ring (ordered after cp.async.wait_group by its memory clobber)
+__device__ __forceinline__ const uint8_t *ring_ptr(uint32_t a)
+{
+    return g_block_smem + (a - smem_addr(g_block_smem));
+}
+__device__ __forceinline__ uint2 lds8(uint32_t a) { return *reinterpret_cast<const uint2 *>(ring_ptr(a)); }
+__device__ __forceinline__ uint32_t lds4(uint32_t a) { return *reinterpret_cast<const uint32_t *>(ring_ptr(a)); }
+
+// the block a lane works on, or none
+struct Slot {
+    const FuseBuf *b;
+    uint64_t bi;
+    uint32_t bj;
+    bool on;  // the lane has a block in this unit
+    bool vec; // aligned: staged loads and vector accesses
+};
+
+__device__ __forceinline__ const FuseBuf *unit_buf(const FuseWork &w, uint64_t u, uint64_t &local)
+{
+    if (w.nbufs == 1) {
+        local = u;
+        return &w.single;
+    }
+    uint32_t lo = 0, hi = w.nbufs;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(&w.bufs[mid].unit0) <= u)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    local = u - __ldg(&w.bufs[lo].unit0);
+    return &w.bufs[lo];
+}
+
+// one unit = one block row of 32 blocks (a warp), lane = block column
+__device__ __forceinline__ Slot slot_of(const FuseWork &w, uint64_t u, int lane)
+{
+    Slot sl;
+    sl.on = false;
+    sl.vec = false;
+    sl.b = nullptr;
+    sl.bi = 0;
+    sl.bj = 0;
+    if (u >= w.total_units)
+        return sl;
+    uint64_t local;
+    sl.b = unit_buf(w, u, local);
+    const uint32_t strips = sl.b->strips;
+    sl.bi = local / strips;
+    sl.bj = (uint32_t)(local % strips) * 32 + lane;
+    sl.on = sl.bj * 8 < sl.b->W;
+    sl.vec = sl.b->vec != 0;
+    return sl;
+}
+
+__device__ __forceinline__ void fwd_issue(const Slot &sl, uint32_t st)
+{
+    if (sl.on && sl.vec) {
+        const FuseBuf &f = *sl.b;
+        const uint64_t base = sl.bi * 8 * f.W + (uint64_t)sl.bj * 8;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const uint64_t off = base + (uint64_t)r * f.W;
+            const uint32_t bytes = off >= f.n ? 0u : (uint32_t)(f.n - off < 8 ? f.n - off : 8);
+            cp8(st + 256 * r, bytes ? f.src + off : f.src, bytes);
+        }
+    }
+    cp_commit();
+}
+
+__device__ __forceinline__ void inv_issue(const Slot &sl, uint32_t s8, uint32_t s4)
+{
+    if (sl.on && sl.vec) {
+        const FuseBuf &f = *sl.b;
+        const uint32_t W = f.W, L = f.F;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                cp8(s8 + 256 * (3 * r + k), tile_row(f.band[0][k], W >> 1, 4, sl.bi, sl.bj, r), 8);
+            if (L == 1)
+                cp8(s8 + kInvX + 256 * r, tile_row(f.ll, W >> 1, 4, sl.bi, sl.bj, r), 8);
+        }
+        if (L >= 2) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    cp4(s4 + kInvX + 128 * (3 * r + k), tile_row(f.band[1][k], W >> 2, 2, sl.bi, sl.bj, r), 4);
+                if (L == 2)
+                    cp4(s4 + kInvL2Ll + 128 * r, tile_row(f.ll, W >> 2, 2, sl.bi, sl.bj, r), 4);
+            }
+        }
+        if (L == 3) {
+            // one int16 per band: the aligned word that holds it (the bases
+            // are 4-byte aligned, so the word stays inside the band)
+            const uint64_t e = sl.bi * (W >> 3) + sl.bj;
+            const uint64_t off = 2ull * (e & ~1ull);
+            const uint32_t bytes = (e & 1ull) ? 4u : 2u;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                cp4(s4 + kInvL3 + 128 * k, f.band[2][k] + off, bytes);
+            cp4(s4 + kInvL3 + 384, f.ll + off, bytes);
+        }
+    }
+    cp_commit();
+}
+
+// ---------------------------------------------------------------------------
+// one block, forward and inverse (rows from the stage, or straight from
+// global memory with byte accesses when the buffer is not aligned)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged,
+                                          uint32_t st)
+{
+    const uint32_t W = f.W, L = f.F;
+    uint32_t x1[8][4]; // row-lifted rows, 4 words each
+    const uint64_t base = bi * 8 * W + (uint64_t)bj * 8;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        uint2 v;
+        if (staged) {
+            v = lds8(st + 256 * r);
+        } else {
+            const uint64_t off = base + (uint64_t)r * W;
+            uint32_t b8[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                b8[i] = off + i < f.n ? (uint32_t)__ldg(f.src + off + i) : 0u;
+            v.x = b8[0] | (b8[1] << 8) | (b8[2] << 16) | (b8[3] << 24);
+            v.y = b8[4] | (b8[5] << 8) | (b8[6] << 16) | (b8[7] << 24);
+        }
+        lift8(v.x, v.y, x1[r]);
+    }
+    uint32_t s1[4][4], d1[4][4];
+    col_lift<8, 4>(x1, s1, d1);
+    // level-1 tiles: LL_1 = s1[][0..1], HL_1 = s1[][2..3], LH_1 = d1[][0..1], HH_1 = d1[][2..3]
+    const uint32_t W1 = W >> 1;
+    const bool vec = staged;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        st_tile(tile_row(f.band[0][0], W1, 4, bi, bj, r), 4, to_i16x2(s1[r][2]), to_i16x2(s1[r][3]), vec);
+        st_tile(tile_row(f.band[0][1], W1, 4, bi, bj, r), 4, to_i16x2(d1[r][0]), to_i16x2(d1[r][1]), vec);
+        st_tile(tile_row(f.band[0][2], W1, 4, bi, bj, r), 4, to_i16x2(d1[r][2]), to_i16x2(d1[r][3]), vec);
+    }
+    if (L == 1) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            st_tile(tile_row(f.ll, W1, 4, bi, bj, r), 4, ll_final(s1[r][0]), ll_final(s1[r][1]), vec);
+        return;
+    }
+    // level 2 on the 4 x 4 LL_1
+    uint32_t x2[4][2];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        lift4(s1[r][0], s1[r][1], x2[r][0], x2[r][1]);
+    uint32_t s2[2][2], d2[2][2];
+    col_lift<4, 2>(x2, s2, d2);
+    const uint32_t W2 = W >> 2;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        st_tile(tile_row(f.band[1][0], W2, 2, bi, bj, r), 2, to_i16x2(s2[r][1]), 0, vec);
+        st_tile(tile_row(f.band[1][1], W2, 2, bi, bj, r), 2, to_i16x2(d2[r][0]), 0, vec);
+        st_tile(tile_row(f.band[1][2], W2, 2, bi, bj, r), 2, to_i16x2(d2[r][1]), 0, vec);
+    }
+    if (L == 2) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            st_tile(tile_row(f.ll, W2, 2, bi, bj, r), 2, ll_final(s2[r][0]), 0, vec);
+        return;
+    }
+    // level 3 on the 2 x 2 LL_2: one (s, d) word per row
+    uint32_t x3[2][1];
+    x3[0][0] = lift2(s2[0][0]);
+    x3[1][0] = lift2(s2[1][0]);
+    uint32_t s3[1][1], d3[1][1];
+    col_lift<2, 1>(x3, s3, d3);
+    const uint32_t W3 = W >> 3;
+    const uint32_t sw = to_i16x2(s3[0][0]), dw = to_i16x2(d3[0][0]);
+    st_tile(tile_row(f.band[2][0], W3, 1, bi, bj, 0), 1, sw >> 16, 0, vec); // HL_3
+    st_tile(tile_row(f.band[2][1], W3, 1, bi, bj, 0), 1, dw, 0, vec);       // LH_3
+    st_tile(tile_row(f.band[2][2], W3, 1, bi, bj, 0), 1, dw >> 16, 0, vec); // HH_3
+    st_tile(tile_row(f.ll, W3, 1, bi, bj, 0), 1, ll_final(s3[0][0]), 0, vec);
+}
+
+__device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged,
+                                          bool vec, uint32_t s8, uint32_t s4)
+{
+    const uint32_t W = f.W, L = f.F;
+    const uint32_t W1 = W >> 1, W2 = W >> 2, W3 = W >> 3;
+    uint32_t s1[4][4], d1[4][4];
+    // LL_1: from the input (one level) or from the levels above
+    if (L >= 2) {
+        uint32_t s2[2][2], d2[2][2];
+        if (L == 3) {
+            uint32_t a, b, c, e, z;
+            if (staged) {
+                const uint32_t sh = 16u * (uint32_t)((bi * (uint64_t)W3 + bj) & 1ull);
+                b = (lds4(s4 + kInvL3) >> sh) & 0xffffu;
+                c = (lds4(s4 + kInvL3 + 128) >> sh) & 0xffffu;
+                e = (lds4(s4 + kInvL3 + 256) >> sh) & 0xffffu;
+                a = (lds4(s4 + kInvL3 + 384) >> sh) & 0xffffu;
+            } else {
+                ld_tile(tile_row(f.ll, W3, 1, bi, bj, 0), 1, a, z, vec);
+                ld_tile(tile_row(f.band[2][0], W3, 1, bi, bj, 0), 1, b, z, vec);
+                ld_tile(tile_row(f.band[2][1], W3, 1, bi, bj, 0), 1, c, z, vec);
+                ld_tile(tile_row(f.band[2][2], W3, 1, bi, bj, 0), 1, e, z, vec);
+            }
+            uint32_t s3[1][1], d3[1][1], x3[2][1];
+            s3[0][0] = from_i16x2(a | (b << 16)) + 0x80u;
+            d3[0][0] = from_i16x2(c | (e << 16));
+            col_unlift<2, 1>(s3, d3, x3);
+            s2[0][0] = unlift2(x3[0][0]);
+            s2[1][0] = unlift2(x3[1][0]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                uint32_t w, z;
+                if (staged)
+                    w = lds4(s4 + kInvL2Ll + 128 * r);
+                else
+                    ld_tile(tile_row(f.ll, W2, 2, bi, bj, r), 2, w, z, vec);
+                s2[r][0] = from_i16x2(w) + 0x00800080u;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            uint32_t w[3], z;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (staged)
+                    w[k] = lds4(s4 + kInvX + 128 * (3 * r + k));
+                else
+                    ld_tile(tile_row(f.band[1][k], W2, 2, bi, bj, r), 2, w[k], z, vec);
+            }
+            s2[r][1] = from_i16x2(w[0]);
+            d2[r][0] = from_i16x2(w[1]);
+            d2[r][1] = from_i16x2(w[2]);
+        }
+        uint32_t x2[4][2];
+        col_unlift<4, 2>(s2, d2, x2);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            unlift4(x2[r][0], x2[r][1], s1[r][0], s1[r][1]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            uint32_t a, b;
+            if (staged) {
+                const uint2 v = lds8(s8 + kInvX + 256 * r);
+                a = v.x;
+                b = v.y;
+            } else {
+                ld_tile(tile_row(f.ll, W1, 4, bi, bj, r), 4, a, b, vec);
+            }
+            s1[r][0] = from_i16x2(a) + 0x00800080u;
+            s1[r][1] = from_i16x2(b) + 0x00800080u;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        uint32_t v[3][2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (staged) {
+                const uint2 t = lds8(s8 + 256 * (3 * r + k));
+                v[k][0] = t.x;
+                v[k][1] = t.y;
+            } else {
+                ld_tile(tile_row(f.band[0][k], W1, 4, bi, bj, r), 4, v[k][0], v[k][1], vec);
+            }
+        }
+        s1[r][2] = from_i16x2(v[0][0]);
+        s1[r][3] = from_i16x2(v[0][1]);
+        d1[r][0] = from_i16x2(v[1][0]);
+        d1[r][1] = from_i16x2(v[1][1]);
+        d1[r][2] = from_i16x2(v[2][0]);
+        d1[r][3] = from_i16x2(v[2][1]);
+    }
+    uint32_t x1[8][4];
+    col_unlift<8, 4>(s1, d1, x1);
+    const uint64_t base = bi * 8 * W + (uint64_t)bj * 8;
+    const bool whole = bi * 8 + 8 <= f.full_rows && vec;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const uint2 v = unlift8(x1[r]);
+        const uint64_t off = base + (uint64_t)r * W;
+        if (whole) {
+            __stcs(reinterpret_cast<uint2 *>(f.out + off), v);
+        } else {
+            for (int i = 0; i < 8 && off + i < f.n; ++i)
+                f.out[off + i] = (uint8_t)((i < 4 ? v.x : v.y) >> (8 * (i & 3)));
+        }
+    }
+}
+
+// the inverse reads four times as many tiles per block as the forward;
+// it runs best with direct loads and many warps, the forward with the ring
+template <bool FWD>
+__global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
+{
+    if (!FWD) {
+        grid_release();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const uint64_t G = (uint64_t)gridDim.x * kWarps;
+        for (uint64_t u = (uint64_t)blockIdx.x * kWarps + warp; u < w.total_units; u += G) {
+            const Slot sl = slot_of(w, u, lane);
+            if (sl.on)
+                inv_block(*sl.b, sl.bi, sl.bj, false, sl.vec, 0, 0);
+        }
+        return;
+    }
+    // the next kernel (the CTR pass after a protect) may start its
+    // data-independent part now; it waits for this grid before reading
+    grid_release();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t stage = FWD ? kFwdStage : kInvStage;
+    const uint32_t ring = smem_addr(g_block_smem) + (uint32_t)warp * kDepth * stage;
+    const uint32_t ring8 = ring + 8u * lane, ring4 = ring + 4u * lane;
+    const uint64_t G = (uint64_t)gridDim.x * kWarps;
+    const uint64_t u0 = (uint64_t)blockIdx.x * kWarps + warp;
+    static_assert(kDepth == 3, "the unit loop below is unrolled for three stages");
+    // the blocks of the units in flight, in stages 0, 1, 2 (static indices
+    // keep them in registers)
+    Slot q0 = slot_of(w, u0, lane), q1 = slot_of(w, u0 + G, lane), q2;
+    if (FWD) {
+        fwd_issue(q0, ring8);
+        fwd_issue(q1, ring8 + stage);
+    } else {
+        inv_issue(q0, ring8, ring4);
+        inv_issue(q1, ring8 + stage, ring4 + stage);
+    }
+    // unit i computes from stage i % 3 after issuing unit i + 2 into stage
+    // (i + 2) % 3, the one unit i - 1 freed
+    auto step = [&](uint64_t i, Slot &cur, Slot &ahead, uint32_t cur_off, uint32_t ahead_off) {
+        ahead = slot_of(w, u0 + (i + 2) * G, lane);
+        if (FWD)
+            fwd_issue(ahead, ring8 + ahead_off);
+        else
+            inv_issue(ahead, ring8 + ahead_off, ring4 + ahead_off);
+        cp_wait<kDepth - 1>();
+        if (cur.on) {
+            if (FWD)
+                fwd_block(*cur.b, cur.bi, cur.bj, cur.vec, ring8 + cur_off);
+            else
+                inv_block(*cur.b, cur.bi, cur.bj, cur.vec, cur.vec, ring8 + cur_off, ring4 + cur_off);
+        }
+    };
+    for (uint64_t i = 0; u0 + i * G < w.total_units; i += 3) {
+        step(i, q0, q2, 0, 2 * stage);
+        if (u0 + (i + 1) * G >= w.total_units)
+            break;
+        step(i + 1, q1, q0, stage, 0);
+        if (u0 + (i + 2) * G >= w.total_units)
+            break;
+        step(i + 2, q2, q1, 2 * stage, stage);
+    }
+    cp_wait<0>();
+}
+
+size_t smem_bytes(bool fwd) { return fwd ? (size_t)kWarps * kDepth * kFwdStage : 0; }
+
+template <bool FWD>
+cudaError_t set_attr()
+{
+    return cudaFuncSetAttribute((const void *)block_kernel<FWD>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(FWD));
+}
+
+} // namespace blk
+
+cudaError_t launch_blocks(bool fwd, const FuseWork &w, uint32_t grid, cudaStream_t stream)
+{
+    cudaError_t e = fwd ? blk::set_attr<true>() : blk::set_attr<false>();
+    if (e != cudaSuccess)
+        return e;
+    if (fwd)
+        blk::block_kernel<true><<<grid, blk::kThreads, blk::smem_bytes(true), stream>>>(w);
+    else
+        blk::block_kernel<false><<<grid, blk::kThreads, blk::smem_bytes(false), stream>>>(w);
+    return cudaGetLastError();
+}
+
+cudaError_t block_occupancy(bool fwd, int *blocks_per_sm)
+{
+    cudaError_t e = fwd ? blk::set_attr<true>() : blk::set_attr<false>();
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, fwd ? (const void *)blk::block_kernel<true> : (const void *)blk::block_kernel<false>,
+        blk::kThreads, blk::smem_bytes(fwd));
+}
+
+} // namespace frag

@@ -29,6 +29,7 @@ struct frag_plan_s {
     uint32_t seg_rows;    // streaming path: level-0 rows per unit (0: adaptive)
     uint32_t max_ctas;    // streaming path: grid cap (0: all resident CTAs)
     uint32_t path;        // frag_path: which kernels run the levels
+    uint32_t block;       // block mode: side of the blocks (0: whole matrix)
 };
 
 struct frag_key_s {
@@ -226,15 +227,18 @@ frag_status check_plan(frag_plan plan)
     return FRAG_OK;
 }
 
-uint64_t rows_for(uint64_t n, uint32_t W, uint32_t L)
+// H: ceil(n / W) rounded up to a multiple of 2^L, or of the block side
+uint64_t rows_for(uint64_t n, uint32_t W, uint32_t L, uint32_t block = 0)
 {
-    const uint64_t step = 1ull << L;
+    const uint64_t step = std::max<uint64_t>(1ull << L, block);
     const uint64_t rows = (n + W - 1) / W;
     return (rows + step - 1) / step * step;
 }
 
 frag_status fill_job(frag_plan plan, uint64_t nonce, uint64_t n, Job &j)
 {
+    if (plan->block)
+        return fail(FRAG_EUNSUPPORTED, "the allocation-free call does not take block plans");
     const uint64_t H = rows_for(n, plan->width, plan->levels);
     if (H > 0xFFFFFFFFull || H * (uint64_t)plan->width / plan->width != H)
         return fail(FRAG_EINVAL, "buffer of %llu bytes is too tall for width %u",
@@ -308,6 +312,7 @@ uint64_t scratch_bytes(bool fwd, uint32_t H, uint32_t W, uint32_t L, uint32_t F,
 struct Buf {
     uint32_t W, L, H;
     uint32_t F;        // levels 1..F run in the fused kernel (0: none)
+    uint32_t block;    // block mode (every level in the block kernel)
     uint32_t R0;       // level-0 rows per work segment
     uint32_t R0_plan;  // the plan's choice (0: adaptive)
     uint64_t n, nonce;
@@ -585,6 +590,8 @@ constexpr uint32_t kFuseMinSegIters = 8; // iterations per unit at least (adapti
 // loads or stores allow it
 uint32_t fused_levels(bool fwd, const Buf &b, uint32_t path)
 {
+    if (b.block)
+        return b.L; // every level in the block kernel (no scratch but LL_L on recover)
     if (path == FRAG_PATH_LEVELS || b.W % 8 != 0)
         return 0;
     const uint32_t F = std::min(b.L, frag::kFuseMaxLevels);
@@ -686,6 +693,64 @@ frag_status fuse_launch(DeviceState &d, bool fwd, frag::FuseWork &w, uint64_t sl
     return FRAG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Block mode: every 8 x 8 block on its own, one lane a block
+// ---------------------------------------------------------------------------
+frag::FuseBuf block_buf(bool fwd, const Buf &b)
+{
+    frag::FuseBuf f = fuse_buf(fwd, b);
+    f.halo = 0;
+    f.strips = (b.W + 255) / 256; // 32 blocks of 8 columns a warp
+    f.iters = b.H / frag::kBlockSide;
+    f.seg_iters = 1;
+    f.segs = f.iters;
+    f.ll_final = 1;
+    bool v = fwd ? aligned(b.in, 8) : aligned(b.out, 8);
+    for (uint32_t l = 1; l <= b.L; ++l)
+        for (uint32_t k = 0; k < 3; ++k)
+            v = v && aligned(f.band[l - 1][k], l == 1 ? 8 : (l == 2 ? 4 : 2));
+    v = v && aligned(f.ll, b.L == 1 ? 8 : (b.L == 2 ? 4 : 2));
+    f.vec = v;
+    return f;
+}
+
+uint64_t block_units(frag::FuseBuf *f, size_t nbufs)
+{
+    uint64_t units = 0;
+    for (size_t i = 0; i < nbufs; ++i) {
+        f[i].unit0 = units;
+        units += (uint64_t)f[i].strips * f[i].segs;
+    }
+    return units;
+}
+
+frag_status block_launch(DeviceState &d, bool fwd, frag::FuseWork &w, cudaStream_t s)
+{
+    if (w.total_units == 0)
+        return FRAG_OK;
+    int occ = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        auto it = d.occ[fwd].find(6666);
+        if (it != d.occ[fwd].end())
+            occ = it->second;
+    }
+    if (occ == 0) {
+        cudaError_t e = frag::block_occupancy(fwd, &occ);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "occupancy query");
+        occ = std::max(occ, 1);
+        std::lock_guard<std::mutex> lock(g_mu);
+        d.occ[fwd][6666] = occ;
+    }
+    const uint64_t need = (w.total_units + 3) / 4; // 4 warps a CTA
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)d.sms * occ, need));
+    cudaError_t e = frag::launch_blocks(fwd, w, grid, s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, fwd ? "block protect launch" : "block recover launch");
+    return FRAG_OK;
+}
+
 // One buffer: protect runs the fused levels, then the dependency-ordered
 // launch for the levels above them (and the cipher units), then the CTR
 // launch; recover runs them in the reverse order.
@@ -700,6 +765,34 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
     b.F = fused_levels(fwd, b, plan->path);
+    if (b.block) {
+        // block mode: the block kernel and the CTR pass (recover deciphers
+        // LL_L into scratch first)
+        uint64_t off[frag::kMaxInlineJobs + 1] = {0};
+        const uint64_t sb = scratch_bytes(fwd, b.H, b.W, b.L, b.F, off);
+        uint8_t *mem = nullptr;
+        if (sb) {
+            cudaError_t e = cudaMallocAsync((void **)&mem, sb, s);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "cudaMallocAsync(level scratch)");
+            b.scr[b.L] = mem + off[b.L];
+        }
+        frag::FuseWork w;
+        std::memset(&w, 0, sizeof(w));
+        w.single = block_buf(fwd, b);
+        w.nbufs = 1;
+        w.total_units = block_units(&w.single, 1);
+        const frag::CtrChunk frag_chunk = ctr_fragment(fwd, b);
+        if (!fwd)
+            st = ctr_launch(*d, rk, nullptr, 0, &frag_chunk, s);
+        if (st == FRAG_OK)
+            st = block_launch(*d, fwd, w, s);
+        if (st == FRAG_OK && fwd)
+            st = ctr_launch(*d, rk, nullptr, 0, &frag_chunk, s);
+        if (mem)
+            cudaFreeAsync(mem, s);
+        return st;
+    }
     const uint32_t njobs = buffer_njobs(b);
     if (njobs > (uint32_t)frag::kMaxInlineJobs)
         return fail(FRAG_EUNSUPPORTED, "more than %d levels", frag::kMaxInlineJobs - 1);
@@ -793,8 +886,11 @@ struct DagWave {
     std::vector<frag::CtrChunk> chunks; // private fragments of the separate CTR launch
     std::vector<frag::FuseBuf> fbufs;   // buffers of the fused launch
     uint64_t fuse_units = 0;
+    std::vector<frag::FuseBuf> bbufs;   // buffers of the block launch
+    uint64_t block_units = 0;
     uint32_t counters = 0;
-    size_t jobs_off = 0, units_off = 0, done_off = 0, queue_off = 0, chunks_off = 0, fbufs_off = 0;
+    size_t jobs_off = 0, units_off = 0, done_off = 0, queue_off = 0, chunks_off = 0, fbufs_off = 0,
+           bbufs_off = 0;
 };
 
 struct BatchPlan {
@@ -828,11 +924,12 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
         b.W = plan->width;
         b.L = plan->levels;
         b.R0_plan = plan->seg_rows;
+        b.block = plan->block;
         if (bp.bufs.empty() && v.empty()) {
             bp.max_ctas = plan->max_ctas; // the grid of a launch: the first item's plan
             bp.fuse_rows = plan->seg_rows;
         }
-        const uint64_t H = rows_for(n, b.W, b.L);
+        const uint64_t H = rows_for(n, b.W, b.L, b.block);
         if (H > 0xFFFFFFFFull)
             return fail(FRAG_EINVAL, "item %u is too tall for width %u", i, b.W);
         b.H = (uint32_t)H;
@@ -894,6 +991,8 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         wv.chunks.clear();
         wv.fbufs.clear();
         wv.fuse_units = 0;
+        wv.bbufs.clear();
+        wv.block_units = 0;
         wv.counters = 0;
     }
     for (size_t i = 0; i < bp.bufs.size(); ++i) {
@@ -908,7 +1007,9 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         buffer_jobs(bp.fwd, b, first, &wv.counters, wv.jobs);
         wv.first.push_back(first);
         wv.levels.push_back(buffer_njobs(b));
-        if (b.F)
+        if (b.block)
+            wv.bbufs.push_back(block_buf(bp.fwd, b));
+        else if (b.F)
             wv.fbufs.push_back(fuse_buf(bp.fwd, b));
         if (separate_cipher(b)) {
             // the private fragment in chunks of kCtrChunkList blocks
@@ -926,6 +1027,7 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         wv.fuse_units = fuse_schedule(wv.fbufs.data(), wv.fbufs.size(),
                                       std::max<uint64_t>(1, bp.fuse_slots) * frag::kFuseWarps,
                                       bp.fuse_rows);
+        wv.block_units = block_units(wv.bbufs.data(), wv.bbufs.size());
     }
     size_t off = align256(bp.scratch);
     for (auto &wv : bp.waves) {
@@ -941,6 +1043,8 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         off += align256(wv.chunks.size() * sizeof(frag::CtrChunk));
         wv.fbufs_off = off;
         off += align256(wv.fbufs.size() * sizeof(frag::FuseBuf));
+        wv.bbufs_off = off;
+        off += align256(wv.bbufs.size() * sizeof(frag::FuseBuf));
     }
     bp.desc_bytes = off - align256(bp.scratch);
 }
@@ -960,6 +1064,9 @@ frag_status upload_batch(const BatchPlan &bp, uint8_t *mem, cudaStream_t s, bool
         if (!wv.fbufs.empty())
             std::memcpy(host.data() + (wv.fbufs_off - base), wv.fbufs.data(),
                         wv.fbufs.size() * sizeof(frag::FuseBuf));
+        if (!wv.bbufs.empty())
+            std::memcpy(host.data() + (wv.bbufs_off - base), wv.bbufs.data(),
+                        wv.bbufs.size() * sizeof(frag::FuseBuf));
     }
     cudaError_t e = async ? cudaMemcpyAsync(mem + base, host.data(), host.size(), cudaMemcpyHostToDevice, s)
                           : cudaMemcpy(mem + base, host.data(), host.size(), cudaMemcpyHostToDevice);
@@ -1020,8 +1127,28 @@ frag_status launch_wave_fused(const BatchPlan &bp, const DagWave &wv, uint8_t *m
     return st;
 }
 
-// per wave, protect: fused levels, dependency-ordered levels above them,
-// CTR; recover: CTR, dependency-ordered levels, fused levels
+// the block launch of a wave (its buffers' descriptors at bbufs_off)
+frag_status launch_wave_blocks(const BatchPlan &bp, const DagWave &wv, uint8_t *mem, DeviceState &d,
+                               cudaStream_t s, LaunchTimer &tm)
+{
+    if (wv.bbufs.empty())
+        return FRAG_OK;
+    frag::FuseWork w;
+    std::memset(&w, 0, sizeof(w));
+    w.nbufs = (uint32_t)wv.bbufs.size();
+    w.bufs = (const frag::FuseBuf *)(mem + wv.bbufs_off);
+    if (w.nbufs == 1)
+        w.single = wv.bbufs[0];
+    w.total_units = wv.block_units;
+    tm.begin();
+    frag_status st = block_launch(d, bp.fwd, w, s);
+    tm.end(FRAG_KERNEL_BLOCKS);
+    return st;
+}
+
+// per wave, protect: fused levels, block mode, dependency-ordered levels
+// above the fused ones, CTR; recover: CTR, dependency-ordered levels, block
+// mode, fused levels
 frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, const uint32_t *rk,
                          cudaStream_t s, std::vector<TimedLaunch> *timed = nullptr)
 {
@@ -1030,6 +1157,8 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
         const frag::CtrChunk *chunks = (const frag::CtrChunk *)(mem + wv.chunks_off);
         frag_status st = FRAG_OK;
         if (bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm)) != FRAG_OK)
+            return st;
+        if (bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm)) != FRAG_OK)
             return st;
         if (!bp.fwd && !wv.chunks.empty()) { // decipher before the transform reads LL_L
             tm.begin();
@@ -1072,6 +1201,8 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
             if (st != FRAG_OK)
                 return st;
         }
+        if (!bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm)) != FRAG_OK)
+            return st;
         if (!bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm)) != FRAG_OK)
             return st;
     }
@@ -1083,7 +1214,7 @@ frag_status batch_fuse_slots(BatchPlan &bp, DeviceState &d)
 {
     bool any = false;
     for (const Buf &b : bp.bufs)
-        any = any || b.F != 0;
+        any = any || (b.F != 0 && !b.block);
     if (!any)
         return FRAG_OK;
     return fuse_slots(d, bp.fwd, bp.max_ctas, &bp.fuse_slots);
@@ -1249,7 +1380,7 @@ frag_status frag_plan_sizes(frag_plan plan, uint64_t nbytes, uint32_t *height,
     frag_status st = check_plan(plan);
     if (st != FRAG_OK)
         return st;
-    const uint64_t H = rows_for(nbytes, plan->width, plan->levels);
+    const uint64_t H = rows_for(nbytes, plan->width, plan->levels, plan->block);
     if (H > 0xFFFFFFFFull)
         return fail(FRAG_EINVAL, "buffer too tall for width %u", plan->width);
     const uint64_t pb = 2 * (H >> plan->levels) * (uint64_t)(plan->width >> plan->levels);
@@ -1321,6 +1452,33 @@ frag_status frag_plan_get_schedule(frag_plan plan, uint32_t *seg_rows, uint32_t 
         *seg_rows = plan->seg_rows;
     if (ctas)
         *ctas = plan->max_ctas;
+    return FRAG_OK;
+}
+
+frag_status frag_plan_set_block(frag_plan plan, uint32_t block)
+{
+    frag_status st = check_plan(plan);
+    if (st != FRAG_OK)
+        return st;
+    if (block != 0) {
+        if (block < (1u << plan->levels) || plan->width % block != 0)
+            return fail(FRAG_EINVAL, "block %u must be >= 2^levels and divide the width %u", block,
+                        plan->width);
+        if (block != frag::kBlockSide || plan->levels > 3)
+            return fail(FRAG_EUNSUPPORTED, "the block mode runs 8 x 8 blocks with up to 3 levels");
+    }
+    plan->block = block;
+    return FRAG_OK;
+}
+
+frag_status frag_plan_get_block(frag_plan plan, uint32_t *block)
+{
+    frag_status st = check_plan(plan);
+    if (st != FRAG_OK)
+        return st;
+    if (block == nullptr)
+        return fail(FRAG_EINVAL, "block is NULL");
+    *block = plan->block;
     return FRAG_OK;
 }
 
@@ -1396,13 +1554,14 @@ frag_status frag_protect(frag_plan plan, frag_key key, uint64_t nonce, const voi
         return FRAG_OK;
     if (d_in == nullptr || d_private == nullptr || d_public == nullptr)
         return fail(FRAG_EINVAL, "NULL buffer");
-    const uint64_t H = rows_for(nbytes, plan->width, plan->levels);
+    const uint64_t H = rows_for(nbytes, plan->width, plan->levels, plan->block);
     if (H > 0xFFFFFFFFull)
         return fail(FRAG_EINVAL, "buffer too tall for width %u", plan->width);
     Buf b;
     std::memset(&b, 0, sizeof(b));
     b.W = plan->width;
     b.L = plan->levels;
+    b.block = plan->block;
     b.H = (uint32_t)H;
     b.n = nbytes;
     b.nonce = nonce;
@@ -1424,13 +1583,14 @@ frag_status frag_recover(frag_plan plan, frag_key key, uint64_t nonce, const voi
         return FRAG_OK;
     if (d_private == nullptr || d_public == nullptr || d_out == nullptr)
         return fail(FRAG_EINVAL, "NULL buffer");
-    const uint64_t H = rows_for(nbytes, plan->width, plan->levels);
+    const uint64_t H = rows_for(nbytes, plan->width, plan->levels, plan->block);
     if (H > 0xFFFFFFFFull)
         return fail(FRAG_EINVAL, "buffer too tall for width %u", plan->width);
     Buf b;
     std::memset(&b, 0, sizeof(b));
     b.W = plan->width;
     b.L = plan->levels;
+    b.block = plan->block;
     b.H = (uint32_t)H;
     b.n = nbytes;
     b.nonce = nonce;
@@ -1604,7 +1764,8 @@ frag_status frag_batch_info(frag_batch batch, uint32_t *launches, uint64_t *scra
         return fail(FRAG_EINVAL, "batch is NULL");
     uint32_t n = 0;
     for (const auto &wv : batch->bp.waves)
-        n += (wv.units.empty() ? 0 : 1) + (wv.chunks.empty() ? 0 : 1) + (wv.fbufs.empty() ? 0 : 1);
+        n += (wv.units.empty() ? 0 : 1) + (wv.chunks.empty() ? 0 : 1) + (wv.fbufs.empty() ? 0 : 1) +
+             (wv.bbufs.empty() ? 0 : 1);
     if (launches)
         *launches = n;
     if (scratch_bytes)

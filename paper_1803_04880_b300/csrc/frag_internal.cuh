@@ -204,6 +204,7 @@ struct __align__(16) FuseBuf {
     uint32_t seg_iters;   // iterations per unit
     uint32_t segs;        // units per strip
     uint32_t full_rows;   // leading rows made only of data bytes (n / W)
+    uint32_t vec;         // block mode: every access may use its vector width
 };
 static_assert(sizeof(FuseBuf) % 16 == 0, "fused buffer descriptors are copied in 16-byte pieces");
 
@@ -216,6 +217,13 @@ struct FuseWork {
 
 cudaError_t launch_fuse(bool fwd, const FuseWork &w, uint32_t grid, cudaStream_t stream);
 cudaError_t fuse_occupancy(bool fwd, int *blocks_per_sm);
+
+// Block mode (block_kernels.cu): every 8 x 8 block transformed on its own.
+// The same descriptors: strips = ceil(W / 256) (32 blocks a warp), iters =
+// block rows, F = levels (<= 3), ll = LL_L - 128 (int16).
+constexpr uint32_t kBlockSide = 8;
+cudaError_t launch_blocks(bool fwd, const FuseWork &w, uint32_t grid, cudaStream_t stream);
+cudaError_t block_occupancy(bool fwd, int *blocks_per_sm);
 
 // kernels (tile_kernels.cu)
 constexpr uint32_t kFastTile = 256;   // owned tile side of the row/column-pass body

@@ -82,6 +82,23 @@ def test_null_arguments_are_rejected(L):
     assert L.frag_plan_get_path(p.handle, None) == fr.FRAG_EINVAL
 
 
+def test_block_validation(L):
+    p = fr.Plan(64, 2)
+    assert p.block() == 0
+    p.set_block(8)
+    assert p.block() == 8
+    assert p.sizes(65)[0] == 8  # whole blocks: 2 rows pad to 8
+    p.set_block(0)
+    assert p.sizes(65)[0] == 4
+    with pytest.raises(fr.FragError):
+        fr.Plan(12, 2).set_block(8)  # width not a multiple of the block
+    with pytest.raises(fr.FragError):
+        fr.Plan(64, 4).set_block(8)  # block below 2^L
+    with pytest.raises(fr.FragError):
+        fr.Plan(64, 2).set_block(16)  # only 8 x 8 blocks on the CUDA path
+    assert L.frag_plan_get_block(p.handle, None) == fr.FRAG_EINVAL
+
+
 def test_path_validation(L):
     p = fr.Plan(256, 3)
     assert p.path() == fr.Plan.PATH_AUTO

@@ -141,12 +141,13 @@ def test_batch_launch_times(fr, key):
     pub = torch.empty(ub, dtype=torch.uint8, device="cuda")
     b = fr.Batch([(plan, 0, n, d, priv, pub)], True)
     b.run(key)
-    assert b.launch_times() == {"fused": (0.0, 0), "levels": (0.0, 0), "cipher": (0.0, 0)}
+    assert b.launch_times() == {"fused": (0.0, 0), "levels": (0.0, 0), "cipher": (0.0, 0),
+                                "blocks": (0.0, 0)}
     b.set_timing(True)
     for _ in range(3):
         b.run(key)
     t = b.launch_times()
-    assert t["fused"][1] == 3 and t["cipher"][1] == 3 and t["levels"][1] == 0
+    assert t["fused"][1] == 3 and t["cipher"][1] == 3 and t["levels"][1] == 0 and t["blocks"][1] == 0
     assert t["fused"][0] > 0 and t["cipher"][0] > 0
     assert b.launch_times()["fused"] == (0.0, 0)  # read once
     fr.sync_status()
