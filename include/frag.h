@@ -79,7 +79,8 @@ int frag_abi_version(void);
 /* Plan = matrix width W and number of levels L (Sec. 5.2.1: the chunk is a
  * matrix of configurable size; Sec. 5.1.1: two levels in the thesis, L here).
  * FRAG_EINVAL if out is NULL, levels == 0, levels > 8, width == 0 or width is
- * not a multiple of 2^levels; FRAG_EUNSUPPORTED for any other filter. */
+ * not a multiple of 2^levels; FRAG_EUNSUPPORTED for any other filter and for
+ * 6 to 8 levels (the level kernel keeps at most 5 levels of a tile). */
 frag_status frag_plan_create(frag_plan *out, uint32_t width, uint32_t levels, frag_filter filter);
 frag_status frag_plan_destroy(frag_plan plan);
 
@@ -237,7 +238,8 @@ typedef enum {
     FRAG_KERNEL_LEVELS = 1, /* the dependency-ordered level kernel */
     FRAG_KERNEL_CIPHER = 2, /* AES-128-CTR over private fragments */
     FRAG_KERNEL_BLOCKS = 3, /* block mode (frag_plan_set_block) */
-    FRAG_KERNEL_KINDS = 4
+    FRAG_KERNEL_FUSED_LOW = 4, /* levels 4..5 in one pass over the level-3 LL */
+    FRAG_KERNEL_KINDS = 5
 } frag_kernel_kind;
 frag_status frag_batch_set_timing(frag_batch batch, int enable);
 frag_status frag_batch_launch_times(frag_batch batch, double *ms, uint32_t *launches);

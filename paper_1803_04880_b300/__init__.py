@@ -335,7 +335,7 @@ class Batch:
     def launches(self) -> int:
         return self.info()[0]
 
-    KERNEL_KINDS = ("fused", "levels", "cipher", "blocks")
+    KERNEL_KINDS = ("fused", "levels", "cipher", "blocks", "fused_low")
 
     def set_timing(self, enable: bool = True) -> None:
         """Record a CUDA event pair around each kernel launch of run()."""

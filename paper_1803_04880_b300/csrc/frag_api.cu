@@ -311,7 +311,8 @@ uint64_t scratch_bytes(bool fwd, uint32_t H, uint32_t W, uint32_t L, uint32_t F,
 
 struct Buf {
     uint32_t W, L, H;
-    uint32_t F;        // levels 1..F run in the fused kernel (0: none)
+    uint32_t F;        // levels 1..F run in fused passes (0: none): F1 + F2
+    uint32_t F1, F2;   // levels of the first pass (bytes) and the second (packed LL_3)
     uint32_t block;    // block mode (every level in the block kernel)
     uint32_t R0;       // level-0 rows per work segment
     uint32_t R0_plan;  // the plan's choice (0: adaptive)
@@ -585,51 +586,72 @@ frag_status ctr_launch(DeviceState &d, const uint32_t *rk, const frag::CtrChunk 
 // ---------------------------------------------------------------------------
 constexpr uint32_t kFuseMinSegIters = 8; // iterations per unit at least (adaptive choice)
 
-// levels the fused kernel takes for buffer b (0: none): up to
-// kFuseMaxLevels, when the width and every pointer it accesses with vector
-// loads or stores allow it
-uint32_t fused_levels(bool fwd, const Buf &b, uint32_t path)
+// levels a fused pass over levels lo+1 .. lo+F can take (0: none): its
+// input width (W >> lo) a multiple of 8 and every band and the LL output it
+// writes with vector stores aligned
+uint32_t pass_levels(bool fwd, const Buf &b, uint32_t lo)
 {
-    if (b.block)
-        return b.L; // every level in the block kernel (no scratch but LL_L on recover)
-    if (path == FRAG_PATH_LEVELS || b.W % 8 != 0)
+    if ((b.W >> lo) % 8 != 0 || b.L <= lo)
         return 0;
-    const uint32_t F = std::min(b.L, frag::kFuseMaxLevels);
-    if (fwd ? !aligned(b.in, 8) : !aligned(b.out, 8))
-        return 0;
+    const uint32_t F = std::min(b.L - lo, frag::kFuseMaxLevels);
     const uint8_t *pub = fwd ? b.pub : b.pub_in;
     for (uint32_t l = 1; l <= F; ++l)
         for (uint32_t k = 0; k < 3; ++k)
-            if (!aligned(pub + frag::band_offset(b.H, b.W, b.L, l, k), l == 1 ? 8 : 4))
+            if (!aligned(pub + frag::band_offset(b.H, b.W, b.L, lo + l, k), l == 1 ? 8 : 4))
                 return 0;
-    if (fwd && F == b.L && !aligned(b.priv, F == 1 ? 8 : 4))
+    if (fwd && lo + F == b.L && !aligned(b.priv, F == 1 ? 8 : 4))
         return 0; // LL_L goes straight to the private fragment
     return F;
 }
 
-// descriptor of buffer b for the fused kernel (schedule fields left 0)
-frag::FuseBuf fuse_buf(bool fwd, const Buf &b)
+// how buffer b splits over the fused passes: the first (bytes in / out)
+// takes levels 1 .. F1 (up to 3), a second over the packed LL_3 scratch
+// levels 4 .. 3 + F2; the level kernel takes the rest
+void fused_split(bool fwd, Buf &b, uint32_t path)
+{
+    b.F1 = b.F2 = 0;
+    if (b.block)
+        b.F1 = b.L; // every level in the block kernel (no scratch but LL_L on recover)
+    else if (path != FRAG_PATH_LEVELS && (fwd ? aligned(b.in, 8) : aligned(b.out, 8)))
+        b.F1 = pass_levels(fwd, b, 0);
+    if (!b.block && b.F1 == frag::kFuseMaxLevels)
+        b.F2 = pass_levels(fwd, b, b.F1);
+    b.F = b.F1 + b.F2;
+}
+
+// descriptor of buffer b for a fused pass (schedule fields left 0): pass 1
+// works on the bytes, pass 2 on the packed LL_{F1} scratch (levels
+// F1+1 .. F1+F2)
+frag::FuseBuf fuse_buf(bool fwd, const Buf &b, int pass = 1)
 {
     frag::FuseBuf f;
     std::memset(&f, 0, sizeof(f));
-    f.src = b.in;
-    f.out = b.out;
+    const uint32_t lo = pass == 1 ? 0 : b.F1, F = pass == 1 ? b.F1 : b.F2, top = lo + F;
     uint8_t *pub = fwd ? b.pub : const_cast<uint8_t *>(b.pub_in);
-    for (uint32_t l = 1; l <= b.F; ++l)
+    for (uint32_t l = 1; l <= F; ++l)
         for (uint32_t k = 0; k < 3; ++k)
-            f.band[l - 1][k] = pub + frag::band_offset(b.H, b.W, b.L, l, k);
-    // LL_F: the private fragment (protect, last level), the deciphered copy
+            f.band[l - 1][k] = pub + frag::band_offset(b.H, b.W, b.L, lo + l, k);
+    // LL_top: the private fragment (protect, last level), the deciphered copy
     // (recover, last level) or the scratch the levels above read / write
-    f.ll = (fwd && b.F == b.L) ? b.priv : b.scr[b.F];
-    f.ll_final = b.F == b.L;
-    f.n = b.n;
-    f.W = b.W;
-    f.H = b.H;
-    f.F = b.F;
-    f.halo = (fwd && b.F == 3) ? 2 : 1;
-    f.strips = (b.W + 8 * (31 - f.halo) - 1) / (8 * (31 - f.halo));
-    f.iters = fwd ? b.H / 8 + 1 : (b.H + 6) / 8 + 1;
-    f.full_rows = (uint32_t)std::min<uint64_t>(b.n / b.W, b.H);
+    f.ll = (fwd && top == b.L) ? b.priv : b.scr[top];
+    f.ll_final = top == b.L;
+    f.W = b.W >> lo;
+    f.H = b.H >> lo;
+    if (pass == 1) {
+        f.src = b.in;
+        f.out = b.out;
+        f.n = b.n;
+        f.full_rows = (uint32_t)std::min<uint64_t>(b.n / b.W, b.H);
+    } else {
+        f.src = b.scr[lo];
+        f.out = b.scr[lo];
+        f.n = (uint64_t)f.H * f.W;
+        f.full_rows = f.H;
+    }
+    f.F = F;
+    f.halo = (fwd && F == 3) ? 2 : 1;
+    f.strips = (f.W + 8 * (31 - f.halo) - 1) / (8 * (31 - f.halo));
+    f.iters = fwd ? f.H / 8 + 1 : (f.H + 6) / 8 + 1;
     return f;
 }
 
@@ -658,22 +680,23 @@ uint64_t fuse_schedule(frag::FuseBuf *f, size_t nbufs, uint64_t warps, uint32_t 
     return units;
 }
 
-frag_status fuse_slots(DeviceState &d, bool fwd, uint32_t max_ctas, uint64_t *slots)
+frag_status fuse_slots(DeviceState &d, bool fwd, bool packed, uint32_t max_ctas, uint64_t *slots)
 {
     int occ = 0;
+    const size_t tag = packed ? 9998 : 9999;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        auto it = d.occ[fwd].find(9999);
+        auto it = d.occ[fwd].find(tag);
         if (it != d.occ[fwd].end())
             occ = it->second;
     }
     if (occ == 0) {
-        cudaError_t e = frag::fuse_occupancy(fwd, &occ);
+        cudaError_t e = frag::fuse_occupancy(fwd, packed, &occ);
         if (e != cudaSuccess)
             return cuda_fail(e, "occupancy query");
         occ = std::max(occ, 1);
         std::lock_guard<std::mutex> lock(g_mu);
-        d.occ[fwd][9999] = occ;
+        d.occ[fwd][tag] = occ;
     }
     *slots = (uint64_t)d.sms * occ;
     if (max_ctas)
@@ -681,13 +704,14 @@ frag_status fuse_slots(DeviceState &d, bool fwd, uint32_t max_ctas, uint64_t *sl
     return FRAG_OK;
 }
 
-frag_status fuse_launch(DeviceState &d, bool fwd, frag::FuseWork &w, uint64_t slots, cudaStream_t s)
+frag_status fuse_launch(DeviceState &d, bool fwd, bool packed, frag::FuseWork &w, uint64_t slots,
+                        cudaStream_t s)
 {
     if (w.total_units == 0)
         return FRAG_OK;
     const uint64_t need = (w.total_units + frag::kFuseWarps - 1) / frag::kFuseWarps;
     const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min(slots, need));
-    cudaError_t e = frag::launch_fuse(fwd, w, grid, s);
+    cudaError_t e = frag::launch_fuse(fwd, packed, w, grid, s);
     if (e != cudaSuccess)
         return cuda_fail(e, fwd ? "fused protect launch" : "fused recover launch");
     return FRAG_OK;
@@ -764,12 +788,12 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     const uint32_t *rk = nullptr;
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
-    b.F = fused_levels(fwd, b, plan->path);
+    fused_split(fwd, b, plan->path);
     if (b.block) {
         // block mode: the block kernel and the CTR pass (recover deciphers
         // LL_L into scratch first)
         uint64_t off[frag::kMaxInlineJobs + 1] = {0};
-        const uint64_t sb = scratch_bytes(fwd, b.H, b.W, b.L, b.F, off);
+        const uint64_t sb = scratch_bytes(fwd, b.H, b.W, b.L, b.F1, off);
         uint8_t *mem = nullptr;
         if (sb) {
             cudaError_t e = cudaMallocAsync((void **)&mem, sb, s);
@@ -798,7 +822,7 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
         return fail(FRAG_EUNSUPPORTED, "more than %d levels", frag::kMaxInlineJobs - 1);
     // one stream-ordered allocation: [scratch][counters][queue head]
     uint64_t off[frag::kMaxInlineJobs + 1] = {0};
-    const uint64_t sb = align256(scratch_bytes(fwd, b.H, b.W, b.L, b.F, off));
+    const uint64_t sb = align256(scratch_bytes(fwd, b.H, b.W, b.L, b.F1, off));
     uint32_t grid = 0;
     uint64_t cb = 0;
     if (njobs) {
@@ -816,24 +840,29 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
         if (e != cudaSuccess)
             return cuda_fail(e, "cudaMallocAsync(level scratch)");
     }
-    for (uint32_t l = scratch_lo(b.F); l <= scratch_hi(fwd, b.L); ++l)
+    for (uint32_t l = scratch_lo(b.F1); l <= scratch_hi(fwd, b.L); ++l)
         b.scr[l] = mem + off[l];
-    frag::FuseWork fw;
-    std::memset(&fw, 0, sizeof(fw));
-    uint64_t fslots = 0;
-    if (b.F) {
-        if ((st = fuse_slots(*d, fwd, plan->max_ctas, &fslots)) != FRAG_OK) {
+    // the fused passes: [0] over the bytes, [1] over the packed LL_3
+    frag::FuseWork fw[2];
+    std::memset(fw, 0, sizeof(fw));
+    uint64_t fslots[2] = {0, 0};
+    for (int p = 0; p < 2; ++p) {
+        if ((p == 0 ? b.F1 : b.F2) == 0)
+            continue;
+        if ((st = fuse_slots(*d, fwd, p == 1, plan->max_ctas, &fslots[p])) != FRAG_OK) {
             cudaFreeAsync(mem, s);
             return st;
         }
-        fw.single = fuse_buf(fwd, b);
-        fw.nbufs = 1;
-        fw.total_units = fuse_schedule(&fw.single, 1, fslots * frag::kFuseWarps, plan->seg_rows);
+        fw[p].single = fuse_buf(fwd, b, p + 1);
+        fw[p].nbufs = 1;
+        fw[p].total_units = fuse_schedule(&fw[p].single, 1, fslots[p] * frag::kFuseWarps, plan->seg_rows);
     }
     const bool sep = separate_cipher(b);
     const frag::CtrChunk frag_chunk = ctr_fragment(fwd, b);
-    if (fwd && b.F)
-        st = fuse_launch(*d, true, fw, fslots, s);
+    if (fwd && b.F1)
+        st = fuse_launch(*d, true, false, fw[0], fslots[0], s);
+    if (st == FRAG_OK && fwd && b.F2)
+        st = fuse_launch(*d, true, true, fw[1], fslots[1], s);
     if (st == FRAG_OK && sep && !fwd)
         st = ctr_launch(*d, rk, nullptr, 0, &frag_chunk, s);
     if (st == FRAG_OK && njobs) {
@@ -868,8 +897,10 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     }
     if (st == FRAG_OK && sep && fwd)
         st = ctr_launch(*d, rk, nullptr, 0, &frag_chunk, s);
-    if (st == FRAG_OK && !fwd && b.F)
-        st = fuse_launch(*d, false, fw, fslots, s);
+    if (st == FRAG_OK && !fwd && b.F2)
+        st = fuse_launch(*d, false, true, fw[1], fslots[1], s);
+    if (st == FRAG_OK && !fwd && b.F1)
+        st = fuse_launch(*d, false, false, fw[0], fslots[0], s);
     if (mem)
         cudaFreeAsync(mem, s);
     return st;
@@ -884,13 +915,15 @@ struct DagWave {
     std::vector<uint32_t> first, levels; // per buffer: first job, number of jobs
     std::vector<DagUnit> units;
     std::vector<frag::CtrChunk> chunks; // private fragments of the separate CTR launch
-    std::vector<frag::FuseBuf> fbufs;   // buffers of the fused launch
+    std::vector<frag::FuseBuf> fbufs;   // buffers of the fused launch (levels 1..3)
     uint64_t fuse_units = 0;
+    std::vector<frag::FuseBuf> fbufs2;  // buffers of the second fused pass (levels 4 and 5)
+    uint64_t fuse_units2 = 0;
     std::vector<frag::FuseBuf> bbufs;   // buffers of the block launch
     uint64_t block_units = 0;
     uint32_t counters = 0;
     size_t jobs_off = 0, units_off = 0, done_off = 0, queue_off = 0, chunks_off = 0, fbufs_off = 0,
-           bbufs_off = 0;
+           bbufs_off = 0, fbufs2_off = 0;
 };
 
 struct BatchPlan {
@@ -899,6 +932,7 @@ struct BatchPlan {
     uint32_t max_ctas = 0;      // grid cap from the first item's plan (0: none)
     uint32_t fuse_rows = 0;     // fused segment rows from the first item's plan (0: adaptive)
     uint64_t fuse_slots = 0;    // fused CTAs one launch keeps resident
+    uint64_t fuse_slots2 = 0;   // the same for the second (packed) pass
     std::vector<Buf> bufs;
     std::vector<uint64_t> scr_off;
     std::vector<uint32_t> wave_of;
@@ -949,7 +983,7 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
             if (!b.priv_in || !b.pub_in || !b.out)
                 return fail(FRAG_EINVAL, "item %u has a NULL buffer", i);
         }
-        b.F = fused_levels(fwd, b, plan->path);
+        fused_split(fwd, b, plan->path);
         v.emplace_back(H * (uint64_t)b.W, b);
     }
     std::stable_sort(v.begin(), v.end(),
@@ -960,7 +994,7 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
     uint32_t wave = 0;
     for (auto &p : v) {
         const uint64_t sb =
-            align256(scratch_bytes(fwd, p.second.H, p.second.W, p.second.L, p.second.F, nullptr));
+            align256(scratch_bytes(fwd, p.second.H, p.second.W, p.second.L, p.second.F1, nullptr));
         if (used > 0 && used + sb > kScratchBudget) {
             ++wave;
             used = 0;
@@ -993,14 +1027,16 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         wv.fuse_units = 0;
         wv.bbufs.clear();
         wv.block_units = 0;
+        wv.fbufs2.clear();
+        wv.fuse_units2 = 0;
         wv.counters = 0;
     }
     for (size_t i = 0; i < bp.bufs.size(); ++i) {
         Buf &b = bp.bufs[i];
         uint64_t off[frag::kMaxInlineJobs + 1] = {0};
         b.R0 = seg_rows0(b.L, u64, bp.resident_ctas, b.R0_plan);
-        scratch_bytes(bp.fwd, b.H, b.W, b.L, b.F, off);
-        for (uint32_t l = scratch_lo(b.F); l <= scratch_hi(bp.fwd, b.L); ++l)
+        scratch_bytes(bp.fwd, b.H, b.W, b.L, b.F1, off);
+        for (uint32_t l = scratch_lo(b.F1); l <= scratch_hi(bp.fwd, b.L); ++l)
             b.scr[l] = scratch_base + bp.scr_off[i] + off[l];
         DagWave &wv = bp.waves[bp.wave_of[i]];
         const uint32_t first = (uint32_t)wv.jobs.size();
@@ -1009,8 +1045,10 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         wv.levels.push_back(buffer_njobs(b));
         if (b.block)
             wv.bbufs.push_back(block_buf(bp.fwd, b));
-        else if (b.F)
-            wv.fbufs.push_back(fuse_buf(bp.fwd, b));
+        else if (b.F1)
+            wv.fbufs.push_back(fuse_buf(bp.fwd, b, 1));
+        if (b.F2)
+            wv.fbufs2.push_back(fuse_buf(bp.fwd, b, 2));
         if (separate_cipher(b)) {
             // the private fragment in chunks of kCtrChunkList blocks
             const frag::CtrChunk whole = ctr_fragment(bp.fwd, b);
@@ -1028,6 +1066,9 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
                                       std::max<uint64_t>(1, bp.fuse_slots) * frag::kFuseWarps,
                                       bp.fuse_rows);
         wv.block_units = block_units(wv.bbufs.data(), wv.bbufs.size());
+        wv.fuse_units2 = fuse_schedule(wv.fbufs2.data(), wv.fbufs2.size(),
+                                       std::max<uint64_t>(1, bp.fuse_slots2) * frag::kFuseWarps,
+                                       bp.fuse_rows);
     }
     size_t off = align256(bp.scratch);
     for (auto &wv : bp.waves) {
@@ -1045,6 +1086,8 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         off += align256(wv.fbufs.size() * sizeof(frag::FuseBuf));
         wv.bbufs_off = off;
         off += align256(wv.bbufs.size() * sizeof(frag::FuseBuf));
+        wv.fbufs2_off = off;
+        off += align256(wv.fbufs2.size() * sizeof(frag::FuseBuf));
     }
     bp.desc_bytes = off - align256(bp.scratch);
 }
@@ -1067,6 +1110,9 @@ frag_status upload_batch(const BatchPlan &bp, uint8_t *mem, cudaStream_t s, bool
         if (!wv.bbufs.empty())
             std::memcpy(host.data() + (wv.bbufs_off - base), wv.bbufs.data(),
                         wv.bbufs.size() * sizeof(frag::FuseBuf));
+        if (!wv.fbufs2.empty())
+            std::memcpy(host.data() + (wv.fbufs2_off - base), wv.fbufs2.data(),
+                        wv.fbufs2.size() * sizeof(frag::FuseBuf));
     }
     cudaError_t e = async ? cudaMemcpyAsync(mem + base, host.data(), host.size(), cudaMemcpyHostToDevice, s)
                           : cudaMemcpy(mem + base, host.data(), host.size(), cudaMemcpyHostToDevice);
@@ -1110,20 +1156,22 @@ struct LaunchTimer {
 
 // the fused launch of a wave (its buffers' descriptors at fbufs_off)
 frag_status launch_wave_fused(const BatchPlan &bp, const DagWave &wv, uint8_t *mem, DeviceState &d,
-                              cudaStream_t s, LaunchTimer &tm)
+                              cudaStream_t s, LaunchTimer &tm, int pass = 1)
 {
-    if (wv.fbufs.empty())
+    const std::vector<frag::FuseBuf> &bufs = pass == 1 ? wv.fbufs : wv.fbufs2;
+    if (bufs.empty())
         return FRAG_OK;
     frag::FuseWork w;
     std::memset(&w, 0, sizeof(w));
-    w.nbufs = (uint32_t)wv.fbufs.size();
-    w.bufs = (const frag::FuseBuf *)(mem + wv.fbufs_off);
+    w.nbufs = (uint32_t)bufs.size();
+    w.bufs = (const frag::FuseBuf *)(mem + (pass == 1 ? wv.fbufs_off : wv.fbufs2_off));
     if (w.nbufs == 1)
-        w.single = wv.fbufs[0];
-    w.total_units = wv.fuse_units;
+        w.single = bufs[0];
+    w.total_units = pass == 1 ? wv.fuse_units : wv.fuse_units2;
     tm.begin();
-    frag_status st = fuse_launch(d, bp.fwd, w, std::max<uint64_t>(1, bp.fuse_slots), s);
-    tm.end(FRAG_KERNEL_FUSED);
+    frag_status st = fuse_launch(d, bp.fwd, pass == 2, w,
+                                 std::max<uint64_t>(1, pass == 1 ? bp.fuse_slots : bp.fuse_slots2), s);
+    tm.end(pass == 1 ? FRAG_KERNEL_FUSED : FRAG_KERNEL_FUSED_LOW);
     return st;
 }
 
@@ -1157,6 +1205,8 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
         const frag::CtrChunk *chunks = (const frag::CtrChunk *)(mem + wv.chunks_off);
         frag_status st = FRAG_OK;
         if (bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm)) != FRAG_OK)
+            return st;
+        if (bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm, 2)) != FRAG_OK)
             return st;
         if (bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm)) != FRAG_OK)
             return st;
@@ -1203,6 +1253,8 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
         }
         if (!bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm)) != FRAG_OK)
             return st;
+        if (!bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm, 2)) != FRAG_OK)
+            return st;
         if (!bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm)) != FRAG_OK)
             return st;
     }
@@ -1212,12 +1264,17 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
 // CTAs the fused launches of a batch keep resident
 frag_status batch_fuse_slots(BatchPlan &bp, DeviceState &d)
 {
-    bool any = false;
-    for (const Buf &b : bp.bufs)
-        any = any || (b.F != 0 && !b.block);
-    if (!any)
-        return FRAG_OK;
-    return fuse_slots(d, bp.fwd, bp.max_ctas, &bp.fuse_slots);
+    bool any = false, any2 = false;
+    for (const Buf &b : bp.bufs) {
+        any = any || (b.F1 != 0 && !b.block);
+        any2 = any2 || b.F2 != 0;
+    }
+    frag_status st = FRAG_OK;
+    if (any)
+        st = fuse_slots(d, bp.fwd, false, bp.max_ctas, &bp.fuse_slots);
+    if (st == FRAG_OK && any2)
+        st = fuse_slots(d, bp.fwd, true, bp.max_ctas, &bp.fuse_slots2);
+    return st;
 }
 
 frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, uint32_t count,
@@ -1765,7 +1822,7 @@ frag_status frag_batch_info(frag_batch batch, uint32_t *launches, uint64_t *scra
     uint32_t n = 0;
     for (const auto &wv : batch->bp.waves)
         n += (wv.units.empty() ? 0 : 1) + (wv.chunks.empty() ? 0 : 1) + (wv.fbufs.empty() ? 0 : 1) +
-             (wv.bbufs.empty() ? 0 : 1);
+             (wv.bbufs.empty() ? 0 : 1) + (wv.fbufs2.empty() ? 0 : 1);
     if (launches)
         *launches = n;
     if (scratch_bytes)

@@ -215,8 +215,11 @@ struct FuseWork {
     uint64_t total_units;
 };
 
-cudaError_t launch_fuse(bool fwd, const FuseWork &w, uint32_t grid, cudaStream_t stream);
-cudaError_t fuse_occupancy(bool fwd, int *blocks_per_sm);
+// packed: the samples are 16-bit values (v + 0x4000) instead of bytes --
+// a second pass over LL_3 (levels 4 and 5) reads them (forward) or writes them
+// (inverse)
+cudaError_t launch_fuse(bool fwd, bool packed, const FuseWork &w, uint32_t grid, cudaStream_t stream);
+cudaError_t fuse_occupancy(bool fwd, bool packed, int *blocks_per_sm);
 
 // Block mode (block_kernels.cu): every 8 x 8 block transformed on its own.
 // The same descriptors: strips = ceil(W / 256) (32 blocks a warp), iters =

@@ -70,6 +70,10 @@ constexpr int kThreads = 32 * kWarps;
 constexpr int kFwdDepth = FUSE_FWD_DEPTH;
 constexpr int kInvDepth = FUSE_INV_DEPTH;
 constexpr int kFwdStage = 8 * 256; // 8 level-0 rows x 32 lanes x 8 bytes
+// packed samples (a second pass over LL_3, 16-bit values): 16 bytes a lane
+constexpr int kFwdStagePk = 8 * 512;
+template <bool PK>
+__host__ __device__ constexpr int fwd_stage() { return PK ? kFwdStagePk : kFwdStage; }
 // inverse stage: level-1 rows j = 0..3, bands HL/LH/HH, 8 bytes a lane, then
 // region X: level-1 LL rows (one level), or level-2 rows k = 0..1 of the three
 // bands (4 bytes a lane) followed by LL_2 rows (two levels) or the four
@@ -95,6 +99,10 @@ __device__ __forceinline__ void cp4(uint32_t dst, const void *src, uint32_t byte
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -191,6 +199,44 @@ __device__ __forceinline__ void lift8(uint32_t w0, uint32_t w1, uint32_t sR, uin
     P[3] = d23;
 }
 
+// The same lift on 8 packed 16-bit samples (w0 = (x0, x1) .. w3 = (x6, x7))
+__device__ __forceinline__ void lift8p(const uint4 &w, uint32_t sR, uint32_t sL, uint32_t (&P)[4])
+{
+    const uint32_t e01 = __byte_perm(w.x, w.y, 0x5410); // (x0, x2)
+    const uint32_t o01 = __byte_perm(w.x, w.y, 0x7632); // (x1, x3)
+    const uint32_t e23 = __byte_perm(w.z, w.w, 0x5410); // (x4, x6)
+    const uint32_t o23 = __byte_perm(w.z, w.w, 0x7632); // (x5, x7)
+    const uint32_t e01n = __shfl_down_sync(kFull, e01, 1);
+    const uint32_t e12 = __byte_perm(e01, e23, kSelNext);
+    const uint32_t e34 = __byte_perm(e23, e01n, sR);
+    const uint32_t d01 = o01 - pavg(e01, e12) + kB2;
+    const uint32_t d23 = o23 - pavg(e23, e34) + kB2;
+    const uint32_t d23p = __shfl_up_sync(kFull, d23, 1);
+    const uint32_t dm0 = __byte_perm(d23p, d01, sL);
+    const uint32_t d12 = __byte_perm(d01, d23, kSelNext);
+    P[0] = e01 + pq4(dm0, d01) - 0x20002000u;
+    P[1] = e23 + pq4(d12, d23) - 0x20002000u;
+    P[2] = d01;
+    P[3] = d23;
+}
+
+// Level-1 row inverse to packed samples: (x0, x1) .. (x6, x7)
+__device__ __forceinline__ uint4 unlift8p(const uint32_t (&w)[4], uint32_t sR, uint32_t sL)
+{
+    const uint32_t h23p = __shfl_up_sync(kFull, w[3], 1);
+    const uint32_t hm0 = __byte_perm(h23p, w[2], sL);
+    const uint32_t h12 = __byte_perm(w[2], w[3], kSelNext);
+    const uint32_t e01 = w[0] - pq4(hm0, w[2]) + 0x20002000u;
+    const uint32_t e23 = w[1] - pq4(h12, w[3]) + 0x20002000u;
+    const uint32_t e01n = __shfl_down_sync(kFull, e01, 1);
+    const uint32_t e12 = __byte_perm(e01, e23, kSelNext);
+    const uint32_t e34 = __byte_perm(e23, e01n, sR);
+    const uint32_t o01 = w[2] + pavg(e01, e12) - kB2;
+    const uint32_t o23 = w[3] + pavg(e23, e34) - kB2;
+    return make_uint4(__byte_perm(e01, o01, 0x5410), __byte_perm(e01, o01, 0x7632),
+                      __byte_perm(e23, o23, 0x5410), __byte_perm(e23, o23, 0x7632));
+}
+
 // Level-1 row inverse: w[0..1] = L words, w[2..3] = H words -> the 8 bytes
 __device__ __forceinline__ uint2 unlift8(const uint32_t (&w)[4], uint32_t sR, uint32_t sL)
 {
@@ -270,9 +316,24 @@ __device__ __forceinline__ uint32_t unlift2(uint32_t w, bool first, bool last)
 // ---------------------------------------------------------------------------
 
 // the level-0 rows of iteration t into its stage: rows 8t-1 .. 8t+6
+template <bool PK>
 __device__ __forceinline__ void fwd_issue(const FuseBuf &b, const Lane &ln, int t, int t_end,
                                           uint32_t ring_lane)
 {
+    if (PK) {
+        // packed samples: every row of the matrix is whole (no byte tail)
+        if (t < t_end && ln.loads) {
+            const uint32_t st = ring_lane + (uint32_t)(t % kFwdDepth) * kFwdStagePk;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int r = 8 * t - 1 + j;
+                if (r >= 0 && r < (int)b.H)
+                    cp16(st + 512 * j, b.src + 2 * ((uint64_t)r * b.W + (uint64_t)ln.c0));
+            }
+        }
+        cp_commit();
+        return;
+    }
     if (t < t_end && ln.loads) {
         const uint32_t st = ring_lane + (uint32_t)(t % kFwdDepth) * kFwdStage;
         const int r0 = 8 * t - 1;
@@ -309,7 +370,7 @@ struct FwdState {
 // One iteration (rows 8t-1 .. 8t+6 in stage st).  CHECK: the iteration may
 // meet the top (a level's row 0) or the bottom (a level's last row) of the
 // matrix; no other iteration does, and none stores a row outside it.
-template <bool CHECK>
+template <bool CHECK, bool PK>
 __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t, uint32_t st,
                                          bool store, FwdState &S)
 {
@@ -317,9 +378,14 @@ __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t
     const int W1 = W >> 1, H1 = H >> 1, W2 = W >> 2, H2 = H >> 2, W3 = W >> 3, H3 = H >> 3;
     const bool fin = b.ll_final != 0;
     uint2 raw[8];
+    uint4 rawp[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-        raw[j] = lds8(st + 256 * j);
+    for (int j = 0; j < 8; ++j) {
+        if (PK)
+            rawp[j] = *reinterpret_cast<const uint4 *>(ring_ptr(st + 512 * j));
+        else
+            raw[j] = lds8(st + 256 * j);
+    }
 
     // level 1: pairs (8t-1+2j, 8t+2j) -> level-1 row 4t-1+j
     uint32_t y[4][2];
@@ -327,8 +393,13 @@ __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         uint32_t Po[4], Pe[4];
-        lift8(raw[2 * j].x, raw[2 * j].y, ln.sR, ln.sL, Po);
-        lift8(raw[2 * j + 1].x, raw[2 * j + 1].y, ln.sR, ln.sL, Pe);
+        if (PK) {
+            lift8p(rawp[2 * j], ln.sR, ln.sL, Po);
+            lift8p(rawp[2 * j + 1], ln.sR, ln.sL, Pe);
+        } else {
+            lift8(raw[2 * j].x, raw[2 * j].y, ln.sR, ln.sL, Po);
+            lift8(raw[2 * j + 1].x, raw[2 * j + 1].y, ln.sR, ln.sL, Pe);
+        }
         const int q = 4 * t - 1 + j;
         if (CHECK && 8 * t + 2 * j == H) { // x[m] = x[m-2] at the bottom border
 #pragma unroll
@@ -427,6 +498,7 @@ __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t
     }
 }
 
+template <bool PK>
 __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t sy, uint32_t ring_lane,
                                          int lane)
 {
@@ -438,7 +510,7 @@ __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t
 
 #pragma unroll
     for (int k = 0; k < kFwdDepth - 1; ++k)
-        fwd_issue(b, ln, t_first + k, t_end, ring_lane);
+        fwd_issue<PK>(b, ln, t_first + k, t_end, ring_lane);
 
     FwdState S;
 #pragma unroll
@@ -447,14 +519,14 @@ __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t
     S.e2L = S.e2H = S.p2L = S.p2H = S.e3 = S.p3 = kB2;
 
     for (int t = t_first; t < t_end; ++t) {
-        fwd_issue(b, ln, t + kFwdDepth - 1, t_end, ring_lane);
+        fwd_issue<PK>(b, ln, t + kFwdDepth - 1, t_end, ring_lane);
         cp_wait<kFwdDepth - 1>();
-        const uint32_t st = ring_lane + (uint32_t)(t % kFwdDepth) * kFwdStage;
+        const uint32_t st = ring_lane + (uint32_t)(t % kFwdDepth) * fwd_stage<PK>();
         const bool store = ln.own && t >= t_begin;
         if (t >= 2 && t < t_fast_end)
-            fwd_iter<false>(b, ln, t, st, store, S);
+            fwd_iter<false, PK>(b, ln, t, st, store, S);
         else
-            fwd_iter<true>(b, ln, t, st, store, S);
+            fwd_iter<true, PK>(b, ln, t, st, store, S);
     }
     cp_wait<0>();
 }
@@ -581,7 +653,7 @@ struct InvState {
     uint32_t x3, d3;
 };
 
-template <bool CHECK>
+template <bool CHECK, bool PK>
 __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t, uint32_t s8,
                                          uint32_t s4, bool store, bool whole, InvState &S)
 {
@@ -656,9 +728,20 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
 #pragma unroll
         for (int m = 0; m < 4; ++m)
             col_inv<CHECK>(s[m], d[m], q == 0, q == H1, S.x1[m], S.d1[m], xo[m], xe[m]);
+        const int r = 2 * q - 1;
+        if (PK) {
+            // packed samples out (the LL_3 scratch a second pass hands down)
+            const uint4 po = unlift8p(xo, ln.sR, ln.sL);
+            const uint4 pe = unlift8p(xe, ln.sR, ln.sL);
+            uint8_t *p = b.out + 2 * ((uint64_t)r * b.W + (uint64_t)ln.c0);
+            if (store && (!CHECK || (r >= 0 && r < H)))
+                __stcg(reinterpret_cast<uint4 *>(p), po);
+            if (store && (!CHECK || (r + 1 >= 0 && r + 1 < H)))
+                __stcg(reinterpret_cast<uint4 *>(p + 2ull * b.W), pe);
+            continue;
+        }
         const uint2 vo = unlift8(xo, ln.sR, ln.sL);
         const uint2 ve = unlift8(xe, ln.sR, ln.sL);
-        const int r = 2 * q - 1;
         if (!CHECK && whole) { // both rows are whole rows of data
             if (store) {
                 uint8_t *p = b.out + (uint64_t)r * b.W + (uint64_t)ln.c0;
@@ -674,6 +757,7 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
     }
 }
 
+template <bool PK>
 __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t sy, uint32_t ring_lane8,
                                          uint32_t ring_lane4, int lane)
 {
@@ -710,9 +794,9 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
         const bool store = ln.own && t >= t_begin;
         const bool whole = 8 * t < (int)b.full_rows; // rows 8t-7 .. 8t hold only data
         if (t >= 1 && t < t_fast_end)
-            inv_iter<false>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S);
+            inv_iter<false, PK>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S);
         else
-            inv_iter<true>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S);
+            inv_iter<true, PK>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S);
     }
     cp_wait<0>();
 }
@@ -738,7 +822,7 @@ __device__ __forceinline__ const FuseBuf *unit_buf(const FuseWork &w, uint64_t u
     return &w.bufs[lo];
 }
 
-template <bool FWD>
+template <bool FWD, bool PK>
 __global__ void __launch_bounds__(kThreads, FWD ? FUSE_FWD_MINB : FUSE_INV_MINB) fuse_kernel(FuseWork w)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -746,7 +830,7 @@ __global__ void __launch_bounds__(kThreads, FWD ? FUSE_FWD_MINB : FUSE_INV_MINB)
     // data-independent part now; it waits for this grid before reading
     grid_release();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t ring = smem_addr(smem) + (uint32_t)warp * (FWD ? kFwdDepth * kFwdStage : kInvDepth * kInvStage);
+    const uint32_t ring = smem_addr(smem) + (uint32_t)warp * (FWD ? kFwdDepth * fwd_stage<PK>() : kInvDepth * kInvStage);
     const uint64_t G = (uint64_t)gridDim.x * kWarps;
     for (uint64_t u = (uint64_t)blockIdx.x * kWarps + warp; u < w.total_units; u += G) {
         uint64_t local;
@@ -754,45 +838,60 @@ __global__ void __launch_bounds__(kThreads, FWD ? FUSE_FWD_MINB : FUSE_INV_MINB)
         const FuseBuf b = *bp;
         const uint32_t sy = (uint32_t)(local / b.strips), sx = (uint32_t)(local % b.strips);
         if (FWD)
-            fwd_unit(b, sx, sy, ring + 8u * lane, lane);
+            fwd_unit<PK>(b, sx, sy, ring + (PK ? 16u : 8u) * lane, lane);
         else
-            inv_unit(b, sx, sy, ring + 8u * lane, ring + 4u * lane, lane);
+            inv_unit<PK>(b, sx, sy, ring + 8u * lane, ring + 4u * lane, lane);
     }
 }
 
-size_t smem_bytes(bool fwd) { return (size_t)kWarps * (fwd ? kFwdDepth * kFwdStage : kInvDepth * kInvStage); }
-
-template <bool FWD>
-cudaError_t set_attr()
+size_t smem_bytes(bool fwd, bool pk)
 {
-    return cudaFuncSetAttribute((const void *)fuse_kernel<FWD>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(FWD));
+    return (size_t)kWarps * (fwd ? kFwdDepth * (pk ? kFwdStagePk : kFwdStage) : kInvDepth * kInvStage);
 }
 
-} // namespace fuse
-
-cudaError_t launch_fuse(bool fwd, const FuseWork &w, uint32_t grid, cudaStream_t stream)
+template <bool FWD, bool PK>
+cudaError_t set_attr()
 {
-    cudaError_t e = fwd ? fuse::set_attr<true>() : fuse::set_attr<false>();
+    return cudaFuncSetAttribute((const void *)fuse_kernel<FWD, PK>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(FWD, PK));
+}
+
+template <bool FWD, bool PK>
+cudaError_t launch(const FuseWork &w, uint32_t grid, cudaStream_t stream)
+{
+    cudaError_t e = set_attr<FWD, PK>();
     if (e != cudaSuccess)
         return e;
     // an ordinary launch (its loads go through L1, so it starts only once
     // the kernel before it has finished)
-    if (fwd)
-        fuse::fuse_kernel<true><<<grid, fuse::kThreads, fuse::smem_bytes(true), stream>>>(w);
-    else
-        fuse::fuse_kernel<false><<<grid, fuse::kThreads, fuse::smem_bytes(false), stream>>>(w);
+    fuse_kernel<FWD, PK><<<grid, kThreads, smem_bytes(FWD, PK), stream>>>(w);
     return cudaGetLastError();
 }
 
-cudaError_t fuse_occupancy(bool fwd, int *blocks_per_sm)
+template <bool FWD, bool PK>
+cudaError_t occupancy(int *blocks_per_sm)
 {
-    cudaError_t e = fwd ? fuse::set_attr<true>() : fuse::set_attr<false>();
+    cudaError_t e = set_attr<FWD, PK>();
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, fwd ? (const void *)fuse::fuse_kernel<true> : (const void *)fuse::fuse_kernel<false>,
-        fuse::kThreads, fuse::smem_bytes(fwd));
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void *)fuse_kernel<FWD, PK>,
+                                                         kThreads, smem_bytes(FWD, PK));
+}
+
+} // namespace fuse
+
+cudaError_t launch_fuse(bool fwd, bool packed, const FuseWork &w, uint32_t grid, cudaStream_t stream)
+{
+    if (fwd)
+        return packed ? fuse::launch<true, true>(w, grid, stream) : fuse::launch<true, false>(w, grid, stream);
+    return packed ? fuse::launch<false, true>(w, grid, stream) : fuse::launch<false, false>(w, grid, stream);
+}
+
+cudaError_t fuse_occupancy(bool fwd, bool packed, int *blocks_per_sm)
+{
+    if (fwd)
+        return packed ? fuse::occupancy<true, true>(blocks_per_sm) : fuse::occupancy<true, false>(blocks_per_sm);
+    return packed ? fuse::occupancy<false, true>(blocks_per_sm) : fuse::occupancy<false, false>(blocks_per_sm);
 }
 
 } // namespace frag

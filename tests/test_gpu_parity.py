@@ -115,6 +115,37 @@ def test_fused_segments(fr, key, n, W, L, seg_rows):
     assert torch.equal(out, d)
 
 
+# the second fused pass (levels 4 and 5 over the level-3 LL): level-3 widths
+# from one lane's 8 columns to two strips, LL_3 heights from 2 rows up,
+# ragged tails
+PASS2 = [(64 * 16, 64, 4), (64 * 16 * 3 - 7, 64, 4), (128 * 64 + 1, 128, 5), (192 * 128 - 3, 192, 5),
+         (512 * 300 + 11, 512, 4), (2048 * 256, 2048, 5), (4096 * 256 + 99, 4096, 4),
+         (1024 * 512, 1024, 5), (1984 * 256 - 5, 1984, 5), (8192 * 64, 8192, 5), (64 * 64 - 1, 64, 5)]
+
+
+@pytest.mark.parametrize("seg_rows", [0, 16])
+@pytest.mark.parametrize("n,W,L", PASS2)
+def test_second_fused_pass(fr, key, n, W, L, seg_rows):
+    data = wl.random_bytes(n, seed=n + L)
+    p_ref, u_ref = oracle.protect(data, W, L, KEY, 4)
+    plan = fr.Plan(W, L)
+    plan.set_schedule(seg_rows, 0)
+    _, pb, ub = plan.sizes(n)
+    d = torch.from_numpy(data).cuda()
+    priv = torch.empty(pb, dtype=torch.uint8, device="cuda")
+    pub = torch.empty(ub, dtype=torch.uint8, device="cuda")
+    out = torch.empty(n, dtype=torch.uint8, device="cuda")
+    b = fr.Batch([(plan, 4, n, d, priv, pub)], True)
+    b.set_timing(True)
+    b.run(key)
+    assert b.launch_times()["fused_low"][1] == 1  # the case runs the second pass
+    fr.recover(plan, key, 4, priv, pub, n, out)
+    fr.sync_status()
+    assert np.array_equal(priv.cpu().numpy(), p_ref)
+    assert np.array_equal(pub.cpu().numpy(), u_ref)
+    assert torch.equal(out, d)
+
+
 def test_path_selects_kernels(fr, key):
     """Three fused levels take the fused launch and the CTR launch; the level
     path takes one dependency-ordered launch with in-launch cipher units."""
@@ -131,9 +162,12 @@ def test_path_selects_kernels(fr, key):
     assert fr.Batch([(plan, 0, n, d, priv, pub)], True).launches == 1
 
 
-def test_batch_launch_times(fr, key):
-    """The per-kernel event pairs count every launch of the timed runs."""
-    n, W, L = 4096 * 64, 4096, 3
+@pytest.mark.parametrize("L", [3, 4])
+def test_batch_launch_times(fr, key, L):
+    """The per-kernel event pairs count every launch of the timed runs; with
+    four levels the second fused pass (levels 4.. over the level-3 LL) is
+    counted as its own kind."""
+    n, W = 4096 * 64, 4096
     plan = fr.Plan(W, L)
     _, pb, ub = plan.sizes(n)
     d = torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda")
@@ -142,12 +176,14 @@ def test_batch_launch_times(fr, key):
     b = fr.Batch([(plan, 0, n, d, priv, pub)], True)
     b.run(key)
     assert b.launch_times() == {"fused": (0.0, 0), "levels": (0.0, 0), "cipher": (0.0, 0),
-                                "blocks": (0.0, 0)}
+                                "blocks": (0.0, 0), "fused_low": (0.0, 0)}
     b.set_timing(True)
     for _ in range(3):
         b.run(key)
     t = b.launch_times()
+    low = 3 if L > 3 else 0
     assert t["fused"][1] == 3 and t["cipher"][1] == 3 and t["levels"][1] == 0 and t["blocks"][1] == 0
+    assert t["fused_low"][1] == low and (t["fused_low"][0] > 0) == (low > 0)
     assert t["fused"][0] > 0 and t["cipher"][0] > 0
     assert b.launch_times()["fused"] == (0.0, 0)  # read once
     fr.sync_status()
