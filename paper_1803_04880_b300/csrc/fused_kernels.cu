@@ -122,18 +122,55 @@ __device__ __forceinline__ const uint8_t *ring_ptr(uint32_t a)
 __device__ __forceinline__ uint2 lds8(uint32_t a) { return *reinterpret_cast<const uint2 *>(ring_ptr(a)); }
 __device__ __forceinline__ uint32_t lds4(uint32_t a) { return *reinterpret_cast<const uint32_t *>(ring_ptr(a)); }
 
-// int16 stores at element index idx of a band (streaming: never re-read here)
-__device__ __forceinline__ void st8(uint8_t *band, uint64_t idx, uint32_t a, uint32_t b)
+// int16 stores at element index idx of a band (streaming: never re-read
+// here), predicated on p: a lane with p false issues the store but writes
+// nothing, so the lanes that do not own their columns (and the warm-up
+// iterations) need no branch around a group of stores
+__device__ __forceinline__ void pst8(bool p, uint8_t *band, uint64_t idx, uint32_t a, uint32_t b)
 {
-    __stcs(reinterpret_cast<uint2 *>(band + 2 * idx), make_uint2(a, b));
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t"
+                 "@q st.global.cs.v2.b32 [%1], {%2, %3};\n\t}" ::"r"((uint32_t)p),
+                 "l"(band + 2 * idx), "r"(a), "r"(b));
 }
-__device__ __forceinline__ void st4(uint8_t *band, uint64_t idx, uint32_t a)
+__device__ __forceinline__ void pst4(bool p, uint8_t *band, uint64_t idx, uint32_t a)
 {
-    __stcs(reinterpret_cast<unsigned int *>(band + 2 * idx), a);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t"
+                 "@q st.global.cs.b32 [%1], %2;\n\t}" ::"r"((uint32_t)p),
+                 "l"(band + 2 * idx), "r"(a));
 }
-__device__ __forceinline__ void st2(uint8_t *band, uint64_t idx, uint32_t a)
+__device__ __forceinline__ void pst2(bool p, uint8_t *band, uint64_t idx, uint32_t a)
 {
-    __stcs(reinterpret_cast<unsigned short *>(band + 2 * idx), (unsigned short)a);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t"
+                 "@q st.global.cs.b16 [%1], %2;\n\t}" ::"r"((uint32_t)p),
+                 "l"(band + 2 * idx), "h"((unsigned short)a));
+}
+// raw byte addresses: 8 bytes streaming, 16 bytes L2-cached (a scratch the
+// next pass reads)
+__device__ __forceinline__ void pst8b(bool p, uint8_t *at, uint2 v)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t"
+                 "@q st.global.cs.v2.b32 [%1], {%2, %3};\n\t}" ::"r"((uint32_t)p),
+                 "l"(at), "r"(v.x), "r"(v.y));
+}
+__device__ __forceinline__ void pst16b(bool p, uint8_t *at, uint4 v)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t"
+                 "@q st.global.cg.v4.b32 [%1], {%2, %3, %4, %5};\n\t}" ::"r"((uint32_t)p),
+                 "l"(at), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w));
+}
+
+// Store-ready bias.  A detail word that goes to a band is kept as
+// v + 0x8000 per half (the usual bias plus 0x4000), so its int16 form is one
+// XOR.  The lifting steps that read such a word fold the extra 0x40004000
+// into their add constants: a chain of 32-bit adds and subtractions of
+// packed words is exact whenever every half of the final result is in
+// [0, 2^16), whatever the intermediate carries.
+constexpr uint32_t kQ = 0x80008000u; // v + 0x8000 per half, from v - 0x8000 per half
+__device__ __forceinline__ uint32_t q_i16(uint32_t w) { return w ^ kQ; } // to int16 pairs
+// pq4 of two store-ready words: ((a + b - 0x80008000) + 0x20002) >> 2, masked
+__device__ __forceinline__ uint32_t pq4q(uint32_t a, uint32_t b)
+{
+    return ((a + b + 0x80018002u) >> 2) & 0x3fff3fffu;
 }
 
 // ---------------------------------------------------------------------------
@@ -362,8 +399,8 @@ __device__ __forceinline__ void fwd_issue(const FuseBuf &b, const Lane &ln, int 
 __device__ __forceinline__ uint32_t ll_final(uint32_t w) { return to_i16x2(w - 0x00800080u); }
 
 struct FwdState {
-    uint32_t e0[4], dp[4]; // level 1: even row, d of the previous pair
-    uint32_t e2L, e2H, p2L, p2H;
+    uint32_t e0[4], dp[4]; // level 1: even row, d of the previous pair (store-ready)
+    uint32_t e2L, e2H, p2L, p2H; // level 2 (p2L, p2H store-ready)
     uint32_t e3, p3;
 };
 
@@ -406,31 +443,35 @@ __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t
             for (int k = 0; k < 4; ++k)
                 Pe[k] = S.e0[k];
         }
+        // d store-ready (LH_1, HH_1), and so the carried d[-1]
         uint32_t dv[4], sv[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            dv[k] = Po[k] - pavg(S.e0[k], Pe[k]) + kB2; // Eq. 5.1 down the columns
-        if (CHECK && q == 0) {                          // d[-1] = d[0] at the top border
+            dv[k] = Po[k] - pavg(S.e0[k], Pe[k]) + kQ; // Eq. 5.1 down the columns
+        if (CHECK && q == 0) {                         // d[-1] = d[0] at the top border
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 S.dp[k] = dv[k];
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            sv[k] = S.e0[k] + pq4(S.dp[k], dv[k]) - 0x20002000u; // Eq. 5.2 down the columns
+            // Eq. 5.2 down the columns: LL_1 (k < 2) biased, HL_1 store-ready
+            const uint32_t u = S.e0[k] + pq4q(S.dp[k], dv[k]);
+            sv[k] = k < 2 ? u - 0x20002000u : u + 0x20002000u;
             S.e0[k] = Pe[k];
             S.dp[k] = dv[k];
         }
-        if (store && (!CHECK || (unsigned)q < (unsigned)H1)) {
+        {
             const uint64_t idx = (uint64_t)q * (uint64_t)W1 + col1;
-            st8(b.band[0][0], idx, to_i16x2(sv[2]), to_i16x2(sv[3])); // HL_1
-            st8(b.band[0][1], idx, to_i16x2(dv[0]), to_i16x2(dv[1])); // LH_1
-            st8(b.band[0][2], idx, to_i16x2(dv[2]), to_i16x2(dv[3])); // HH_1
+            const bool p = store && (!CHECK || (unsigned)q < (unsigned)H1);
+            pst8(p, b.band[0][0], idx, q_i16(sv[2]), q_i16(sv[3])); // HL_1
+            pst8(p, b.band[0][1], idx, q_i16(dv[0]), q_i16(dv[1])); // LH_1
+            pst8(p, b.band[0][2], idx, q_i16(dv[2]), q_i16(dv[3])); // HH_1
             if (F == 1) {
                 if (fin)
-                    st8(b.ll, idx, ll_final(sv[0]), ll_final(sv[1]));
+                    pst8(p, b.ll, idx, ll_final(sv[0]), ll_final(sv[1]));
                 else
-                    st8(b.ll, idx, sv[0], sv[1]);
+                    pst8(p, b.ll, idx, sv[0], sv[1]);
             }
         }
         y[j][0] = sv[0];
@@ -452,24 +493,26 @@ __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t
             Le = S.e2L;
             He = S.e2H;
         }
-        const uint32_t dL = Lo - pavg(S.e2L, Le) + kB2, dH = Ho - pavg(S.e2H, He) + kB2;
+        // dL, dH (LH_2, HH_2) and sH (HL_2) store-ready, sL (LL_2) biased
+        const uint32_t dL = Lo - pavg(S.e2L, Le) + kQ, dH = Ho - pavg(S.e2H, He) + kQ;
         if (CHECK && q2 == 0) {
             S.p2L = dL;
             S.p2H = dH;
         }
-        const uint32_t sL = S.e2L + pq4(S.p2L, dL) - 0x20002000u;
-        const uint32_t sH = S.e2H + pq4(S.p2H, dH) - 0x20002000u;
+        const uint32_t sL = S.e2L + pq4q(S.p2L, dL) - 0x20002000u;
+        const uint32_t sH = S.e2H + pq4q(S.p2H, dH) + 0x20002000u;
         S.e2L = Le;
         S.e2H = He;
         S.p2L = dL;
         S.p2H = dH;
-        if (store && (!CHECK || (unsigned)q2 < (unsigned)H2)) {
+        {
             const uint64_t idx = (uint64_t)q2 * (uint64_t)W2 + col2;
-            st4(b.band[1][0], idx, to_i16x2(sH)); // HL_2
-            st4(b.band[1][1], idx, to_i16x2(dL)); // LH_2
-            st4(b.band[1][2], idx, to_i16x2(dH)); // HH_2
+            const bool p = store && (!CHECK || (unsigned)q2 < (unsigned)H2);
+            pst4(p, b.band[1][0], idx, q_i16(sH)); // HL_2
+            pst4(p, b.band[1][1], idx, q_i16(dL)); // LH_2
+            pst4(p, b.band[1][2], idx, q_i16(dH)); // HH_2
             if (F == 2)
-                st4(b.ll, idx, fin ? ll_final(sL) : sL);
+                pst4(p, b.ll, idx, fin ? ll_final(sL) : sL);
         }
         z[k] = sL;
     }
@@ -488,13 +531,14 @@ __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t
     const uint32_t s3 = S.e3 + pq4(S.p3, d3) - 0x20002000u;
     S.e3 = we;
     S.p3 = d3;
-    if (store && (!CHECK || (unsigned)q3 < (unsigned)H3)) {
+    {
         const uint64_t idx = (uint64_t)q3 * (uint64_t)W3 + (uint64_t)(ln.c0 >> 3);
+        const bool p = store && (!CHECK || (unsigned)q3 < (unsigned)H3);
         const uint32_t sw = to_i16x2(s3), dw = to_i16x2(d3);
-        st2(b.band[2][0], idx, sw >> 16); // HL_3
-        st2(b.band[2][1], idx, dw);       // LH_3
-        st2(b.band[2][2], idx, dw >> 16); // HH_3
-        st2(b.ll, idx, fin ? ll_final(s3) : s3);
+        pst2(p, b.band[2][0], idx, sw >> 16); // HL_3
+        pst2(p, b.band[2][1], idx, dw);       // LH_3
+        pst2(p, b.band[2][2], idx, dw >> 16); // HH_3
+        pst2(p, b.ll, idx, fin ? ll_final(s3) : s3);
     }
 }
 
@@ -512,11 +556,14 @@ __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t
     for (int k = 0; k < kFwdDepth - 1; ++k)
         fwd_issue<PK>(b, ln, t_first + k, t_end, ring_lane);
 
-    FwdState S;
+    FwdState S; // zeros, in each word's form
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        S.e0[k] = S.dp[k] = kB2;
-    S.e2L = S.e2H = S.p2L = S.p2H = S.e3 = S.p3 = kB2;
+    for (int k = 0; k < 4; ++k) {
+        S.e0[k] = kB2;
+        S.dp[k] = kQ;
+    }
+    S.e2L = S.e2H = S.e3 = S.p3 = kB2;
+    S.p2L = S.p2H = kQ;
 
     for (int t = t_first; t < t_end; ++t) {
         fwd_issue<PK>(b, ln, t + kFwdDepth - 1, t_end, ring_lane);
@@ -622,15 +669,17 @@ __device__ __forceinline__ void inv_issue(const FuseBuf &b, const Lane &ln, int 
 // eager column inverse of one coefficient row q of a level (words of the
 // lane): xe = x[2q], xo = x[2q-1]; (xp, dp) = (x[2q-2], d[q-1]) carried.
 // top: q == 0 (d[-1] = d[0]); bottom: q is one past the last row (x[2q] =
-// x[2q-2], only the odd row is real)
-template <bool CHECK>
+// x[2q-2], only the odd row is real).  SQ / DQ: s / d (and dp) come
+// store-ready (a band read as one XOR) instead of biased; xe, xo are biased.
+template <bool CHECK, bool SQ, bool DQ>
 __device__ __forceinline__ void col_inv(uint32_t s, uint32_t d, bool top, bool bottom, uint32_t &xp,
                                         uint32_t &dp, uint32_t &xo, uint32_t &xe)
 {
     if (CHECK && top)
         dp = d;
-    xe = (CHECK && bottom) ? xp : s - pq4(dp, d) + 0x20002000u; // undo Eq. 5.2
-    xo = dp + pavg(xp, xe) - kB2;                              // undo Eq. 5.1
+    const uint32_t q = DQ ? pq4q(dp, d) : pq4(dp, d);
+    xe = (CHECK && bottom) ? xp : (SQ ? s - q - 0x20002000u : s - q + 0x20002000u); // undo Eq. 5.2
+    xo = DQ ? dp + pavg(xp, xe) - kQ : dp + pavg(xp, xe) - kB2;                      // undo Eq. 5.1
     xp = xe;
     dp = d;
 }
@@ -648,8 +697,8 @@ __device__ __forceinline__ void store_bytes(const FuseBuf &b, const Lane &ln, in
 }
 
 struct InvState {
-    uint32_t x1[4], d1[4]; // level 1: x[2q-2] and d[q-1] of each word
-    uint32_t x2[2], d2[2];
+    uint32_t x1[4], d1[4]; // level 1: x[2q-2] and d[q-1] (store-ready) of each word
+    uint32_t x2[2], d2[2]; // level 2 (d2 store-ready)
     uint32_t x3, d3;
 };
 
@@ -673,7 +722,7 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
                                       : (ll | (in16(hl << 16) & 0xffff0000u));
         const uint32_t d = in16(lh | (hh << 16));
         uint32_t xo, xe;
-        col_inv<CHECK>(s, d, t == 0, t == H3, S.x3, S.d3, xo, xe);
+        col_inv<CHECK, false, false>(s, d, t == 0, t == H3, S.x3, S.d3, xo, xe);
         z[0] = unlift2(xo, ln.first, ln.last);
         z[1] = unlift2(xe, ln.first, ln.last);
     }
@@ -684,9 +733,9 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int q2 = 2 * t - 1 + k;
-            const uint32_t hl = in16(lds4(s4 + kInvX + 128 * (3 * k)));
-            const uint32_t lh = in16(lds4(s4 + kInvX + 128 * (3 * k + 1)));
-            const uint32_t hh = in16(lds4(s4 + kInvX + 128 * (3 * k + 2)));
+            const uint32_t hl = q_i16(lds4(s4 + kInvX + 128 * (3 * k))); // store-ready
+            const uint32_t lh = q_i16(lds4(s4 + kInvX + 128 * (3 * k + 1)));
+            const uint32_t hh = q_i16(lds4(s4 + kInvX + 128 * (3 * k + 2)));
             uint32_t ll;
             if (F == 3)
                 ll = z[k];
@@ -695,8 +744,8 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
             else
                 ll = lds4(s4 + kInvL2Ll + 128 * k);
             uint32_t oL, eL, oH, eH;
-            col_inv<CHECK>(ll, lh, q2 == 0, q2 == H2, S.x2[0], S.d2[0], oL, eL);
-            col_inv<CHECK>(hl, hh, q2 == 0, q2 == H2, S.x2[1], S.d2[1], oH, eH);
+            col_inv<CHECK, false, true>(ll, lh, q2 == 0, q2 == H2, S.x2[0], S.d2[0], oL, eL);
+            col_inv<CHECK, true, true>(hl, hh, q2 == 0, q2 == H2, S.x2[1], S.d2[1], oH, eH);
             unlift4(oL, oH, ln.sR, ln.sL, y[2 * k][0], y[2 * k][1]);
             unlift4(eL, eH, ln.sR, ln.sL, y[2 * k + 1][0], y[2 * k + 1][1]);
         }
@@ -718,36 +767,36 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
             s[0] = y[j][0];
             s[1] = y[j][1];
         }
-        s[2] = in16(hl.x);
-        s[3] = in16(hl.y);
-        d[0] = in16(lh.x);
-        d[1] = in16(lh.y);
-        d[2] = in16(hh.x);
-        d[3] = in16(hh.y);
+        // the bands store-ready (one XOR each), LL biased
+        s[2] = q_i16(hl.x);
+        s[3] = q_i16(hl.y);
+        d[0] = q_i16(lh.x);
+        d[1] = q_i16(lh.y);
+        d[2] = q_i16(hh.x);
+        d[3] = q_i16(hh.y);
         uint32_t xo[4], xe[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m)
-            col_inv<CHECK>(s[m], d[m], q == 0, q == H1, S.x1[m], S.d1[m], xo[m], xe[m]);
+        for (int m = 0; m < 2; ++m)
+            col_inv<CHECK, false, true>(s[m], d[m], q == 0, q == H1, S.x1[m], S.d1[m], xo[m], xe[m]);
+#pragma unroll
+        for (int m = 2; m < 4; ++m)
+            col_inv<CHECK, true, true>(s[m], d[m], q == 0, q == H1, S.x1[m], S.d1[m], xo[m], xe[m]);
         const int r = 2 * q - 1;
         if (PK) {
             // packed samples out (the LL_3 scratch a second pass hands down)
             const uint4 po = unlift8p(xo, ln.sR, ln.sL);
             const uint4 pe = unlift8p(xe, ln.sR, ln.sL);
             uint8_t *p = b.out + 2 * ((uint64_t)r * b.W + (uint64_t)ln.c0);
-            if (store && (!CHECK || (r >= 0 && r < H)))
-                __stcg(reinterpret_cast<uint4 *>(p), po);
-            if (store && (!CHECK || (r + 1 >= 0 && r + 1 < H)))
-                __stcg(reinterpret_cast<uint4 *>(p + 2ull * b.W), pe);
+            pst16b(store && (!CHECK || (r >= 0 && r < H)), p, po);
+            pst16b(store && (!CHECK || (r + 1 >= 0 && r + 1 < H)), p + 2ull * b.W, pe);
             continue;
         }
         const uint2 vo = unlift8(xo, ln.sR, ln.sL);
         const uint2 ve = unlift8(xe, ln.sR, ln.sL);
         if (!CHECK && whole) { // both rows are whole rows of data
-            if (store) {
-                uint8_t *p = b.out + (uint64_t)r * b.W + (uint64_t)ln.c0;
-                __stcs(reinterpret_cast<uint2 *>(p), vo);
-                __stcs(reinterpret_cast<uint2 *>(p + b.W), ve);
-            }
+            uint8_t *p = b.out + (uint64_t)r * b.W + (uint64_t)ln.c0;
+            pst8b(store, p, vo);
+            pst8b(store, p + b.W, ve);
         } else {
             if (store && (!CHECK || (r >= 0 && r < H)))
                 store_bytes(b, ln, r, vo);
@@ -775,11 +824,14 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
     for (int k = 0; k < kInvDepth - 1; ++k)
         inv_issue(b, ln, t_first + k, t_end, ring_lane8, ring_lane4);
 
-    InvState S;
+    InvState S; // zeros, in each word's form
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        S.x1[k] = S.d1[k] = kB2;
-    S.x2[0] = S.x2[1] = S.d2[0] = S.d2[1] = S.x3 = S.d3 = kB2;
+    for (int k = 0; k < 4; ++k) {
+        S.x1[k] = kB2;
+        S.d1[k] = kQ;
+    }
+    S.x2[0] = S.x2[1] = S.x3 = S.d3 = kB2;
+    S.d2[0] = S.d2[1] = kQ;
     if (F == 3 && t_begin >= 2 && ln.loads) {
         const uint64_t e = (uint64_t)(t_begin - 2) * (b.W >> 3) + ((uint32_t)ln.c0 >> 3);
         const uint32_t lh = __ldg(reinterpret_cast<const unsigned short *>(b.band[2][1]) + e);
