@@ -18,14 +18,15 @@
 //             input rows exist.  A unit first runs F iterations that store
 //             nothing: they rebuild the column state of every level above
 //             its first row (the lifting's support grows by two rows per
-//             level).
+//             level), computing only what that state needs (fwd_warm).
 //   inverse   iteration t consumes level-3 row t, level-2 rows 2t-1, 2t and
 //             level-1 rows 4t-3 .. 4t; the column inverse of each level
 //             (undo Eq. 5.2, then Eq. 5.1) emits two rows of the level below
 //             per coefficient row, the row inverse makes them LL samples, and
 //             level 1 ends in level-0 rows 8t-7 .. 8t.  A unit first runs one
-//             iteration that stores nothing (with three levels it also loads
-//             the level-3 d row two above its first).
+//             iteration that stores nothing and only rebuilds the column
+//             state (inv_warm; with three levels it also loads the level-3 d
+//             row two above its first).
 //
 // Loads: each lane copies its own 8 (or 4) bytes of every row it needs into a
 // per-warp ring of shared-memory stages with cp.async, two iterations ahead,
@@ -542,6 +543,92 @@ __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t
     }
 }
 
+// A warm-up iteration away from the matrix's top and bottom (t >= 2, before
+// the last two): it rebuilds only the state the next iteration reads.
+//   first: the unit's first iteration (F before its first stored row) --
+//          the level-1 column state and the even row level 2 reads next,
+//          from rows 8t+2 .. 8t+6 (8t+4 .. 8t+6 with one level);
+//   last:  the iteration right before the first stored row -- every word of
+//          the state;
+//   else:  the LL halves of levels 1 and 2 and level 3's even row.
+// The row-H halves of the level-1 column lifting, the level-2 H column and
+// the level-3 column are read again only through state the last warm-up
+// iteration rebuilds from the rows it holds, and no band is written.
+template <bool PK>
+__device__ __forceinline__ void fwd_warm(const FuseBuf &b, const Lane &ln, uint32_t st, bool first, bool last,
+                                         FwdState &S)
+{
+    const int F = (int)b.F;
+    auto lift = [&](int r, uint32_t(&P)[4]) {
+        if (PK) {
+            lift8p(*reinterpret_cast<const uint4 *>(ring_ptr(st + 512 * r)), ln.sR, ln.sL, P);
+        } else {
+            const uint2 w = lds8(st + 256 * r);
+            lift8(w.x, w.y, ln.sR, ln.sL, P);
+        }
+    };
+    // level 1: pairs j0 .. 3 of rows (8t-1+2j, 8t+2j)
+    const int j0 = first ? (F == 1 ? 3 : 2) : 0;
+    if (first) {
+        uint32_t P[4];
+        lift(2 * j0 - 1, P); // the even row before pair j0
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            S.e0[k] = P[k];
+    }
+    uint32_t y[4][2];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (j < j0)
+            continue;
+        uint32_t Po[4], Pe[4];
+        lift(2 * j, Po);
+        lift(2 * j + 1, Pe);
+        if (last && j == 3) {
+#pragma unroll
+            for (int k = 2; k < 4; ++k)
+                S.dp[k] = Po[k] - pavg(S.e0[k], Pe[k]) + kQ;
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const uint32_t dv = Po[k] - pavg(S.e0[k], Pe[k]) + kQ; // Eq. 5.1
+            y[j][k] = S.e0[k] + pq4q(S.dp[k], dv) - 0x20002000u;   // Eq. 5.2: LL_1
+            S.dp[k] = dv;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            S.e0[k] = Pe[k];
+    }
+    if (F < 2)
+        return;
+    if (first) { // level 2 reads only the even row next
+        lift4(y[3][0], y[3][1], ln.sR, ln.sL, S.e2L, S.e2H);
+        return;
+    }
+    // level 2: the L column (LL_2 for level 3), the H column's d only last
+    uint32_t z[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        uint32_t Lo, Ho, Le, He;
+        lift4(y[2 * k][0], y[2 * k][1], ln.sR, ln.sL, Lo, Ho);
+        lift4(y[2 * k + 1][0], y[2 * k + 1][1], ln.sR, ln.sL, Le, He);
+        const uint32_t dL = Lo - pavg(S.e2L, Le) + kQ;
+        z[k] = S.e2L + pq4q(S.p2L, dL) - 0x20002000u;
+        if (last && k == 1)
+            S.p2H = Ho - pavg(S.e2H, He) + kQ;
+        S.e2L = Le;
+        S.e2H = He;
+        S.p2L = dL;
+    }
+    if (F < 3)
+        return;
+    // level 3: the even row, and the column's d last
+    const uint32_t we = lift2(z[1], ln.first, ln.last);
+    if (last)
+        S.p3 = lift2(z[0], ln.first, ln.last) - pavg(S.e3, we) + kB2;
+    S.e3 = we;
+}
+
 template <bool PK>
 __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t sy, uint32_t ring_lane,
                                          int lane)
@@ -570,10 +657,14 @@ __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t
         cp_wait<kFwdDepth - 1>();
         const uint32_t st = ring_lane + (uint32_t)(t % kFwdDepth) * fwd_stage<PK>();
         const bool store = ln.own && t >= t_begin;
-        if (t >= 2 && t < t_fast_end)
-            fwd_iter<false, PK>(b, ln, t, st, store, S);
-        else
+        if (t >= 2 && t < t_fast_end) {
+            if (t < t_begin)
+                fwd_warm<PK>(b, ln, st, t == t_first && t_first == t_begin - (int)b.F, t == t_begin - 1, S);
+            else
+                fwd_iter<false, PK>(b, ln, t, st, store, S);
+        } else {
             fwd_iter<true, PK>(b, ln, t, st, store, S);
+        }
     }
     cp_wait<0>();
 }
@@ -806,6 +897,78 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
     }
 }
 
+// The warm-up iteration of an inverse unit away from the matrix's top and
+// bottom (t >= 1, before the last two): only the column state of every level
+// for the unit's first stored rows -- no row inverse of level 1, nothing
+// stored.  Each level needs just the even sample x[2q] of its last
+// coefficient row in the iteration, whose d[q-1] is the row before it,
+// loaded in the same iteration (level 3: the d preloaded at the unit's
+// start); level 2 hands down its row-inversed even row, LL_1 row 4t.
+__device__ __forceinline__ void inv_warm(const FuseBuf &b, const Lane &ln, int t, uint32_t s8, uint32_t s4,
+                                         InvState &S)
+{
+    const int F = (int)b.F;
+    const uint32_t llb = b.ll_final ? 0x00800080u : 0u;
+    uint32_t y3[2] = {0u, 0u};
+    uint32_t z1 = 0u;
+    if (F == 3) { // level-3 row t
+        const uint32_t sh = 16u * (uint32_t)(((uint64_t)t * (uint64_t)(b.W >> 3) + (uint64_t)(ln.c0 >> 3)) & 1ull);
+        const uint32_t hl = (lds4(s4 + kInvL3) >> sh) & 0xffffu;
+        const uint32_t lh = (lds4(s4 + kInvL3 + 128) >> sh) & 0xffffu;
+        const uint32_t hh = (lds4(s4 + kInvL3 + 256) >> sh) & 0xffffu;
+        const uint32_t ll = (lds4(s4 + kInvL3 + 384) >> sh) & 0xffffu;
+        const uint32_t s = b.ll_final ? in16(ll | (hl << 16)) + 0x80u
+                                      : (ll | (in16(hl << 16) & 0xffff0000u));
+        const uint32_t d = in16(lh | (hh << 16));
+        S.x3 = s - pq4(S.d3, d) + 0x20002000u; // undo Eq. 5.2
+        S.d3 = d;
+        z1 = unlift2(S.x3, ln.first, ln.last);
+    }
+    if (F >= 2) { // level-2 row 2t; d[-1] from row 2t-1
+        const uint32_t lh0 = q_i16(lds4(s4 + kInvX + 128 * 1));
+        const uint32_t hh0 = q_i16(lds4(s4 + kInvX + 128 * 2));
+        const uint32_t hl1 = q_i16(lds4(s4 + kInvX + 128 * 3));
+        const uint32_t lh1 = q_i16(lds4(s4 + kInvX + 128 * 4));
+        const uint32_t hh1 = q_i16(lds4(s4 + kInvX + 128 * 5));
+        uint32_t ll;
+        if (F == 3)
+            ll = z1;
+        else if (b.ll_final)
+            ll = in16(lds4(s4 + kInvL2Ll + 128)) + llb;
+        else
+            ll = lds4(s4 + kInvL2Ll + 128);
+        const uint32_t eL = ll - pq4q(lh0, lh1) + 0x20002000u;
+        const uint32_t eH = hl1 - pq4q(hh0, hh1) - 0x20002000u;
+        S.x2[0] = eL;
+        S.d2[0] = lh1;
+        S.x2[1] = eH;
+        S.d2[1] = hh1;
+        unlift4(eL, eH, ln.sR, ln.sL, y3[0], y3[1]);
+    }
+    // level-1 row 4t (pair j = 3); d[-1] from row 4t-1 (j = 2)
+    const uint2 lh2 = lds8(s8 + 256 * 7), hh2 = lds8(s8 + 256 * 8);
+    const uint2 hl3 = lds8(s8 + 256 * 9), lh3 = lds8(s8 + 256 * 10), hh3 = lds8(s8 + 256 * 11);
+    uint32_t s[4];
+    if (F == 1) {
+        const uint2 ll = lds8(s8 + kInvX + 256 * 3);
+        s[0] = b.ll_final ? in16(ll.x) + llb : ll.x;
+        s[1] = b.ll_final ? in16(ll.y) + llb : ll.y;
+    } else {
+        s[0] = y3[0];
+        s[1] = y3[1];
+    }
+    s[2] = q_i16(hl3.x);
+    s[3] = q_i16(hl3.y);
+    const uint32_t d[4] = {q_i16(lh3.x), q_i16(lh3.y), q_i16(hh3.x), q_i16(hh3.y)};
+    const uint32_t dp[4] = {q_i16(lh2.x), q_i16(lh2.y), q_i16(hh2.x), q_i16(hh2.y)};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const uint32_t u = s[m] - pq4q(dp[m], d[m]);
+        S.x1[m] = m < 2 ? u + 0x20002000u : u - 0x20002000u;
+        S.d1[m] = d[m];
+    }
+}
+
 template <bool PK>
 __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t sy, uint32_t ring_lane8,
                                          uint32_t ring_lane4, int lane)
@@ -845,10 +1008,14 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
         const uint32_t so = (uint32_t)(t % kInvDepth) * kInvStage;
         const bool store = ln.own && t >= t_begin;
         const bool whole = 8 * t < (int)b.full_rows; // rows 8t-7 .. 8t hold only data
-        if (t >= 1 && t < t_fast_end)
-            inv_iter<false, PK>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S);
-        else
+        if (t >= 1 && t < t_fast_end) {
+            if (t < t_begin)
+                inv_warm(b, ln, t, ring_lane8 + so, ring_lane4 + so, S);
+            else
+                inv_iter<false, PK>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S);
+        } else {
             inv_iter<true, PK>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S);
+        }
     }
     cp_wait<0>();
 }
