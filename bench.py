@@ -13,6 +13,10 @@ the launch stream.  value = input bytes of all ranks / max-over-ranks time.
 
 --impl reference times the oracle (plain single-threaded C) on the host cores
 as the reference arm, one bounded sample per step.
+
+Workload "aesfull" is the thesis's full-encryption comparator: AES-128-CTR
+over the whole 256 MiB mixed buffer (encrypt, then decrypt), the same unit
+as protect+recover, so it reads beside c3l2 / c3l4.
 """
 from __future__ import annotations
 
@@ -39,7 +43,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2blocks", "c3l2", "c3l4", "c4", "c5"])
+    ap.add_argument("--workload", default="c2",
+                    choices=["c2", "c2blocks", "c3l2", "c3l4", "c4", "c5", "aesfull"])
     ap.add_argument("--items", type=int, default=10000, help="c4: number of buffers")
     ap.add_argument("--requests", type=int, default=240, help="c5: requests per load level")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -141,6 +146,8 @@ def run_reference(args, rank):
     import numpy as np  # noqa: F401
     import oracle
     from paper_1803_04880_b300 import workloads as wl
+    if args.workload == "aesfull":
+        return _reference_aes(args)
     desc, items = _workload(args.workload)
     W, L, nonce, data = items[0]
     # a bounded sample per step: the first 1/4 of item 0 (whole rows)
@@ -631,6 +638,204 @@ def run_c5(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+# -- the full-encryption comparator ------------------------------------------------
+
+AES_DESC = {"workload": "full-buffer AES-128-CTR of the 256 MiB mixed buffer (encrypt + decrypt), "
+                        "the thesis's full-encryption comparator", "planes": 1, "width": None,
+            "levels": 0}
+# the T-table AES's own ceiling: 160 four-byte table lookups per 16-byte block
+# (16 per round, 10 rounds), at most 32 of them per SM per clock from shared
+# memory -> SMs x clock x 32 / 160 blocks per second
+AES_LOOKUPS_PER_BLOCK = 160
+AES_LOOKUPS_PER_SM_CLOCK = 32
+
+
+def _reference_aes(args):
+    import oracle
+    from paper_1803_04880_b300 import workloads as wl
+    data = wl.c3()
+    n = 8 << 20  # a bounded sample per step: the first 8 MiB
+    sample = data[:n].tobytes()
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        c = oracle.aes128_ctr_xor(wl.KEY, 0, 0, sample)
+        oracle.aes128_ctr_xor(wl.KEY, 0, 0, c)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = n * len(times) / total / 1e9
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * total / len(times), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": AES_DESC,
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "first %d bytes, encrypt+decrypt per step" % n},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_aesfull(args, rank, world, local_rank):
+    import torch
+    import paper_1803_04880_b300 as fr
+    from paper_1803_04880_b300 import workloads as wl
+
+    fr.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    data = wl.c3()
+    n = data.size
+    key = fr.Key(wl.KEY)
+    src = torch.from_numpy(data).to(dev)
+    ct = torch.empty(n, dtype=torch.uint8, device=dev)
+    out = torch.empty(n, dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    flush_words = flush.view(torch.int32)
+    s = torch.cuda.Stream(device=dev)
+
+    def flush_l2(i):
+        flush.fill_(i & 255)
+        torch.sum(flush_words, dtype=torch.int32)
+
+    with torch.cuda.stream(s):
+        fr.aes_ctr(key, 0, src, ct, stream=s)
+        fr.aes_ctr(key, 0, ct, out, stream=s)
+    torch.cuda.synchronize()
+    fr.sync_status(s)
+    assert torch.equal(src, out), "round trip failed"
+    import oracle
+    head = oracle.aes128_ctr_xor(wl.KEY, 0, 0, data[:1 << 16].tobytes())
+    assert ct[:1 << 16].cpu().numpy().tobytes() == head, "differs from the oracle"
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    K, Wm = args.steps, args.warmup
+    with torch.cuda.stream(s):
+        for i in range(Wm):
+            flush_l2(i)
+            fr.aes_ctr(key, 0, src, ct, stream=s)
+            flush_l2(i)
+            fr.aes_ctr(key, 0, ct, out, stream=s)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.5)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(s):
+        for i in range(K):
+            e = ev[i]
+            flush_l2(i)
+            e[0].record(s)
+            fr.aes_ctr(key, 0, src, ct, stream=s)
+            e[1].record(s)
+            flush_l2(i)
+            e[2].record(s)
+            fr.aes_ctr(key, 0, ct, out, stream=s)
+            e[3].record(s)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    fr.sync_status(s)
+    te = [e[0].elapsed_time(e[1]) for e in ev]
+    td = [e[2].elapsed_time(e[3]) for e in ev]
+    steps_ms = [a + b for a, b in zip(te, td)]
+    total_ms = sum(steps_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / K
+    value = world * n * K / (total_ms / 1e3) / 1e9
+    # one launch per direction: the event pair around it is the kernel's time
+    t_launch = statistics.mean(te + td)
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2032.0
+    blocks = (n + 15) // 16
+    lookups_peak = props.multi_processor_count * sm_mhz * 1e6 * AES_LOOKUPS_PER_SM_CLOCK
+    achieved = blocks * AES_LOOKUPS_PER_BLOCK / (t_launch / 1e3)
+    peak_hbm, peak_kind = _peaks()
+    roofline = {"bound": "alu", "achieved": round(achieved / 1e12, 3),
+                "peak": round(lookups_peak / 1e12, 3), "unit": "T table lookups/s",
+                "frac": round(achieved / lookups_peak, 4), "traffic": None,
+                "kernel": "ctr_kernel (T-table AES-128-CTR over the whole buffer, one launch)",
+                "peak_kind": "shared-memory lookup rate: %d SMs x %.0f MHz x %d lookups per SM "
+                             "per clock" % (props.multi_processor_count, sm_mhz,
+                                            AES_LOOKUPS_PER_SM_CLOCK),
+                "kernel_ms_per_launch": round(t_launch, 5),
+                "hbm_frac": round(2 * n / (t_launch / 1e3) / 1e9 / peak_hbm, 4),
+                "hbm_peak": peak_hbm, "hbm_peak_kind": peak_kind}
+
+    # e2e: pinned host buffers, copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        hin = torch.from_numpy(data).pin_memory()
+        hct = torch.empty(n, dtype=torch.uint8).pin_memory()
+        hout = torch.empty(n, dtype=torch.uint8).pin_memory()
+        dbuf = torch.empty(n, dtype=torch.uint8, device=dev)
+        times = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(s):
+                dbuf.copy_(hin, non_blocking=True)
+                fr.aes_ctr(key, 0, dbuf, dbuf, stream=s)
+                hct.copy_(dbuf, non_blocking=True)
+                dbuf.copy_(hct, non_blocking=True)
+                fr.aes_ctr(key, 0, dbuf, dbuf, stream=s)
+                hout.copy_(dbuf, non_blocking=True)
+            s.synchronize()
+            dt = time.perf_counter() - t0
+            if i > 0:
+                times.append(dt)
+        assert torch.equal(hin, hout), "host round trip failed"
+        e2e = {"value": round(n / statistics.mean(times) / 1e9, 3), "unit": UNIT,
+               "h2d_bytes_per_step": 2 * n, "d2h_bytes_per_step": 2 * n,
+               "api": "frag_aes128_ctr on device copies of pinned host buffers, both directions"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        m = 16 << 20
+        sample = data[:m].tobytes()
+        reps, t0 = 0, time.perf_counter()
+        while True:
+            c = oracle.aes128_ctr_xor(wl.KEY, 0, 0, sample)
+            oracle.aes128_ctr_xor(wl.KEY, 0, 0, c)
+            reps += 1
+            el = time.perf_counter() - t0
+            if el >= 10.0 or reps >= 20:
+                break
+        cpu = {"value": round(m * reps / el / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first %d bytes, encrypt+decrypt x%d, one thread" % (m, reps)}
+
+    if rank == 0:
+        q = sorted(steps_ms)
+        line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+                "steps": K, "warmup": Wm, "ms_per_step": round(ms_per_step, 5),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u8", "data": "synthetic",
+                "config": dict(AES_DESC, l2="flushed before each direction (512 MiB write, then read back)",
+                               parallelism="replicas" if world > 1 else "single GPU",
+                               path="frag_aes128_ctr, one launch per direction"),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": 2 * K,
+                "encrypt_gbps": round(n / (statistics.mean(te) / 1e3) / 1e9, 2),
+                "decrypt_gbps": round(n / (statistics.mean(td) / 1e3) / 1e9, 2),
+                "p50_ms": round(q[len(q) // 2], 5), "p99_ms": round(q[min(len(q) - 1, int(0.99 * len(q)))], 5),
+                "wall_s_timed_region": round(wall, 3)}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -649,6 +854,8 @@ def main():
             run_c4(args, rank, world, local_rank)
         elif args.workload == "c5":
             run_c5(args, rank, world, local_rank)
+        elif args.workload == "aesfull":
+            run_aesfull(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

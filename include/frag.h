@@ -163,6 +163,19 @@ frag_status frag_protect(frag_plan plan, frag_key key, uint64_t nonce, const voi
 frag_status frag_recover(frag_plan plan, frag_key key, uint64_t nonce, const void *d_private,
                          const void *d_public, uint64_t nbytes, void *d_out, frag_stream stream);
 
+/* Full-buffer AES-128-CTR: the thesis's full-encryption comparator for its
+ * selective method (Sec. 5.4 and Chapter 4: the whole data encrypted with
+ * AES-128, against which the fragmentation's speed is judged).  d_out[i] =
+ * d_in[i] XOR keystream byte i, the keystream being AES-128 of the counter
+ * blocks nonce (8 bytes big-endian) || block index (8 bytes big-endian) from
+ * 0 -- the private fragment's cipher, so applying it twice gives the input
+ * back.  Device buffers of nbytes bytes at any alignment (16-byte aligned
+ * ones take 16-byte accesses); d_out may equal d_in (in place) but must not
+ * overlap it otherwise.  nbytes == 0 is a no-op; FRAG_EINVAL if key is NULL
+ * or a buffer is NULL with nbytes > 0.  Asynchronous on stream. */
+frag_status frag_aes128_ctr(frag_key key, uint64_t nonce, const void *d_in, void *d_out,
+                            uint64_t nbytes, frag_stream stream);
+
 /* Host-buffer forms of the two calls: copy the host input into stream-ordered
  * device memory (cudaMallocAsync), run the same kernels, copy the results
  * back, and return once they are in host memory.  Pinned (cudaHostAlloc) host

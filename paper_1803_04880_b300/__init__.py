@@ -27,7 +27,7 @@ EXPORTS = [
     "frag_plan_get_schedule", "frag_plan_set_path", "frag_plan_get_path",
     "frag_plan_set_block", "frag_plan_get_block",
     "frag_key_create", "frag_key_destroy",
-    "frag_protect", "frag_recover", "frag_protect_host", "frag_recover_host",
+    "frag_protect", "frag_recover", "frag_aes128_ctr", "frag_protect_host", "frag_recover_host",
     "frag_protect_batch", "frag_recover_batch", "frag_batch_create_protect",
     "frag_batch_create_recover", "frag_batch_run", "frag_batch_destroy", "frag_batch_info",
     "frag_batch_set_timing", "frag_batch_launch_times",
@@ -91,6 +91,7 @@ def lib():
         "frag_key_destroy": ([vp], ctypes.c_int),
         "frag_protect": ([vp, vp, u64, vp, u64, vp, vp, vp], ctypes.c_int),
         "frag_recover": ([vp, vp, u64, vp, vp, u64, vp, vp], ctypes.c_int),
+        "frag_aes128_ctr": ([vp, u64, vp, vp, u64, vp], ctypes.c_int),
         "frag_protect_host": ([vp, vp, u64, vp, u64, vp, vp, vp], ctypes.c_int),
         "frag_recover_host": ([vp, vp, u64, vp, vp, u64, vp, vp], ctypes.c_int),
         "frag_protect_batch": ([ctypes.POINTER(frag_item), u32, vp, vp], ctypes.c_int),
@@ -252,6 +253,17 @@ def recover(plan: Plan, key: Key, nonce: int, private, public, nbytes: int, out=
         out = _empty(nbytes, private.device)
     check(lib().frag_recover(plan.handle, key.handle, nonce, _ptr(private), _ptr(public),
                              nbytes, _ptr(out), _stream(stream)))
+    return out
+
+
+def aes_ctr(key: Key, nonce: int, data, out=None, stream=None):
+    """Full-buffer AES-128-CTR of a device uint8 tensor (the comparator for
+    the selective method; its own inverse): returns out (in place when out is
+    data)."""
+    if out is None:
+        out = _empty(data.numel(), data.device)
+    check(lib().frag_aes128_ctr(key.handle, nonce, _ptr(data), _ptr(out), data.numel(),
+                                _stream(stream)))
     return out
 
 

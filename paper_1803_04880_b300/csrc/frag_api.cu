@@ -1628,6 +1628,34 @@ frag_status frag_protect(frag_plan plan, frag_key key, uint64_t nonce, const voi
     return run_single(true, plan, key, b, (cudaStream_t)stream);
 }
 
+frag_status frag_aes128_ctr(frag_key key, uint64_t nonce, const void *d_in, void *d_out, uint64_t nbytes,
+                            frag_stream stream)
+{
+    if (key == nullptr)
+        return fail(FRAG_EINVAL, "key is NULL");
+    if (nbytes == 0)
+        return FRAG_OK;
+    if (d_in == nullptr || d_out == nullptr)
+        return fail(FRAG_EINVAL, "NULL buffer");
+    DeviceState *d = nullptr;
+    int dev = 0;
+    frag_status st = device_state(&d, &dev);
+    if (st != FRAG_OK)
+        return st;
+    const uint32_t *rk = nullptr;
+    if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
+        return st;
+    // the whole buffer as one fragment of the CTR pass
+    frag::CtrChunk c;
+    std::memset(&c, 0, sizeof(c));
+    c.in = (const uint8_t *)d_in;
+    c.out = (uint8_t *)d_out;
+    c.nonce = nonce;
+    c.bytes = nbytes;
+    c.nblocks = (nbytes + 15) / 16;
+    return ctr_launch(*d, rk, nullptr, 0, &c, (cudaStream_t)stream);
+}
+
 frag_status frag_recover(frag_plan plan, frag_key key, uint64_t nonce, const void *d_private,
                          const void *d_public, uint64_t nbytes, void *d_out, frag_stream stream)
 {

@@ -80,6 +80,8 @@ def test_null_arguments_are_rejected(L):
     assert L.frag_batch_launch_times(None, None, None) == fr.FRAG_EINVAL
     assert L.frag_plan_set_path(None, 0) == fr.FRAG_EINVAL
     assert L.frag_plan_get_path(p.handle, None) == fr.FRAG_EINVAL
+    # full-buffer AES-CTR: a NULL key is refused before any device work
+    assert L.frag_aes128_ctr(None, 0, None, None, 16, None) == fr.FRAG_EINVAL
 
 
 def test_block_validation(L):
