@@ -64,9 +64,16 @@ def _load():
         lib.oracle_recover_blocks.argtypes = [_u8p, _u8p, ctypes.c_uint64, ctypes.c_uint32,
                                               ctypes.c_uint32, ctypes.c_uint32, _u8p,
                                               ctypes.c_uint64, _u8p]
+        lib.oracle_packed_sizes.argtypes = [ctypes.c_uint64, ctypes.c_uint32, _u64p, _u64p,
+                                            _u64p, _u64p]
+        lib.oracle_protect_packed.argtypes = [_u8p, ctypes.c_uint64, ctypes.c_uint32, _u8p,
+                                              ctypes.c_uint64, _u8p, _u8p, _u8p]
+        lib.oracle_recover_packed.argtypes = [_u8p, _u8p, _u8p, ctypes.c_uint64, ctypes.c_uint32,
+                                              _u8p, ctypes.c_uint64, _u8p]
         for f in ("oracle_dwt53_fwd_2d", "oracle_dwt53_inv_2d", "oracle_sizes", "oracle_protect",
                   "oracle_recover", "oracle_block_sizes", "oracle_protect_blocks",
-                  "oracle_recover_blocks"):
+                  "oracle_recover_blocks", "oracle_packed_sizes", "oracle_protect_packed",
+                  "oracle_recover_packed"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -189,4 +196,51 @@ def recover(priv, pub, n: int, width: int, levels: int, key, nonce: int,
                                     _p(k, _u8p), nonce, _p(out, _u8p))
     if st:
         raise RuntimeError("oracle_recover failed: %d" % st)
+    return out
+
+
+# -- the thesis's packed three fragments (8 x 8 blocks, two levels) ----------
+
+def packed_sizes(n: int, width: int):
+    """(H, A bytes, B bytes, C bytes): the private fragment (40 bits a
+    block), the first public fragment (124 bits a block, every block row
+    starting on a byte) and the second (480 bits a block)."""
+    H, a, b, c = (ctypes.c_uint64() for _ in range(4))
+    st = _load().oracle_packed_sizes(n, width, ctypes.byref(H), ctypes.byref(a), ctypes.byref(b),
+                                     ctypes.byref(c))
+    if st:
+        raise ValueError("invalid width %d for 8 x 8 blocks" % width)
+    return H.value, a.value, b.value, c.value
+
+
+def protect_packed(data, width: int, key, nonce: int):
+    """Bytes -> (private fragment A, public fragment B || C) in the packed
+    storage, both uint8 arrays."""
+    buf = np.ascontiguousarray(data, dtype=np.uint8).reshape(-1)
+    n = buf.size
+    _, sa, sb, sc = packed_sizes(n, width)
+    a = np.zeros(sa, dtype=np.uint8)
+    pub = np.zeros(sb + sc, dtype=np.uint8)
+    b, c = pub[:sb], pub[sb:]
+    k = _key(key)
+    st = _load().oracle_protect_packed(_p(buf, _u8p), n, width, _p(k, _u8p), nonce, _p(a, _u8p),
+                                       _p(b, _u8p), _p(c, _u8p))
+    if st:
+        raise RuntimeError("oracle_protect_packed failed: %d" % st)
+    return a, pub
+
+
+def recover_packed(a, pub, n: int, width: int, key, nonce: int) -> np.ndarray:
+    _, sa, sb, sc = packed_sizes(n, width)
+    a = np.ascontiguousarray(a, dtype=np.uint8).reshape(-1)
+    pub = np.ascontiguousarray(pub, dtype=np.uint8).reshape(-1)
+    if a.size != sa or pub.size != sb + sc:
+        raise ValueError("fragment sizes do not match")
+    b, c = np.ascontiguousarray(pub[:sb]), np.ascontiguousarray(pub[sb:])
+    out = np.zeros(n, dtype=np.uint8)
+    k = _key(key)
+    st = _load().oracle_recover_packed(_p(a, _u8p), _p(b, _u8p), _p(c, _u8p), n, width,
+                                       _p(k, _u8p), nonce, _p(out, _u8p))
+    if st:
+        raise RuntimeError("oracle_recover_packed failed: %d" % st)
     return out

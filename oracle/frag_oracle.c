@@ -649,3 +649,205 @@ int oracle_recover_blocks(const uint8_t *priv, const uint8_t *pub, uint64_t n, u
     free(plain);
     return st;
 }
+
+/* ---------------------------------------------------------------------- */
+/* The thesis's three fragments in its own storage (Sec. 5.2.1 and Sec.    */
+/* 5.2.3, "Evaluation of the storage necessary for DWT"): 8 x 8 blocks, two */
+/* levels; per block the private fragment LL_2 takes 4 x 10 bits (40), the  */
+/* first public fragment HL_2 and LH_2 at 10 bits and HH_2 at 11 bits      */
+/* (40 + 40 + 44 = 124), the second public fragment the 48 level-1 details */
+/* at 10 bits (480): 644 bits for the block's 512.  The bounds of the      */
+/* level-2 coefficients (338 / 468 / 648) and of level 1 (every detail     */
+/* within +-510 by the floors of Eq. 5.1 / 5.2) are what make the widths    */
+/* enough; a value outside its width is reported, never stored.            */
+/*                                                                          */
+/* Layout (a reading: the thesis gives the widths, not the order):          */
+/*   - a value is its two's complement in `width` bits; a record's values   */
+/*     follow each other from bit 0, each band's tile row-major, and a      */
+/*     record's bits fill bytes from the least significant bit;             */
+/*   - A (private, then AES-128-CTR as every private fragment): one 5-byte  */
+/*     record per block, blocks row-major;                                  */
+/*   - B (first public): the blocks of a block row follow each other every  */
+/*     124 bits, and every block row starts on a byte (ceil(124 nbx / 8)    */
+/*     bytes a row);                                                        */
+/*   - C (second public): one 60-byte record per block, blocks row-major;   */
+/*     the public fragment of the call is B followed by C.                  */
+/* ---------------------------------------------------------------------- */
+
+#define PK_B 8
+#define PK_L 2
+
+int oracle_packed_sizes(uint64_t n, uint32_t W, uint64_t *H, uint64_t *a_bytes, uint64_t *b_bytes,
+                        uint64_t *c_bytes)
+{
+    uint64_t pb, ub, nbx, nby;
+    if (oracle_block_sizes(n, W, PK_L, PK_B, H, &pb, &ub) != ORACLE_OK)
+        return ORACLE_EINVAL;
+    nbx = W / PK_B;
+    nby = *H / PK_B;
+    *a_bytes = 5 * nbx * nby;
+    *b_bytes = nby * ((124 * nbx + 7) / 8);
+    *c_bytes = 60 * nbx * nby;
+    return ORACLE_OK;
+}
+
+/* value v as `width` bits at bit position pos of buf (buf zeroed first) */
+static int put_bits(uint8_t *buf, uint64_t pos, int32_t v, int width)
+{
+    int i;
+    const int32_t lo = -(1 << (width - 1)), hi = (1 << (width - 1)) - 1;
+    if (v < lo || v > hi)
+        return ORACLE_ERANGE;
+    for (i = 0; i < width; i++)
+        if (((uint32_t)v >> i) & 1u)
+            buf[(pos + (uint64_t)i) / 8] |= (uint8_t)(1u << ((pos + (uint64_t)i) % 8));
+    return ORACLE_OK;
+}
+
+static int32_t get_bits(const uint8_t *buf, uint64_t pos, int width)
+{
+    int i;
+    uint32_t u = 0;
+    for (i = 0; i < width; i++)
+        u |= (uint32_t)((buf[(pos + (uint64_t)i) / 8] >> ((pos + (uint64_t)i) % 8)) & 1u) << i;
+    if (u & (1u << (width - 1))) /* sign */
+        return (int32_t)u - (int32_t)(1u << width);
+    return (int32_t)u;
+}
+
+/* the values of one block's three records, in record order, with their
+ * widths: walks the block's Mallat layout (blk, 8 x 8) in the order above */
+static void record_fields(int rec, int64_t idx[48], int width[48], int *count)
+{
+    int k = 0, t, r, c;
+    if (rec == 0) { /* A: LL_2 at rows 0..1, cols 0..1 */
+        for (r = 0; r < 2; r++)
+            for (c = 0; c < 2; c++, k++) {
+                idx[k] = r * PK_B + c;
+                width[k] = 10;
+            }
+    } else if (rec == 1) { /* B: HL_2 (top-right), LH_2 (bottom-left), HH_2 */
+        for (t = 0; t < 3; t++)
+            for (r = 0; r < 2; r++)
+                for (c = 0; c < 2; c++, k++) {
+                    idx[k] = (r + (t >= 1 ? 2 : 0)) * PK_B + c + (t != 1 ? 2 : 0);
+                    width[k] = t == 2 ? 11 : 10;
+                }
+    } else { /* C: HL_1, LH_1, HH_1 (4 x 4 each) */
+        for (t = 0; t < 3; t++)
+            for (r = 0; r < 4; r++)
+                for (c = 0; c < 4; c++, k++) {
+                    idx[k] = (r + (t >= 1 ? 4 : 0)) * PK_B + c + (t != 1 ? 4 : 0);
+                    width[k] = 10;
+                }
+    }
+    *count = k;
+}
+
+/* bit position of block (bi, bj)'s record rec */
+static uint64_t record_pos(int rec, uint64_t bi, uint64_t bj, uint64_t nbx)
+{
+    if (rec == 0)
+        return 40 * (bi * nbx + bj);
+    if (rec == 1)
+        return 8 * (bi * ((124 * nbx + 7) / 8)) + 124 * bj;
+    return 480 * (bi * nbx + bj);
+}
+
+int oracle_protect_packed(const uint8_t *in, uint64_t n, uint32_t W, const uint8_t key[16],
+                          uint64_t nonce, uint8_t *a_out, uint8_t *b_out, uint8_t *c_out)
+{
+    uint64_t H, sa, sb, sc, i, bi, bj, nbx;
+    int32_t *a, blk[PK_B * PK_B];
+    int st = ORACLE_OK, rec, k, cnt;
+    int64_t idx[48];
+    int width[48];
+    uint8_t *outs[3];
+    if (oracle_packed_sizes(n, W, &H, &sa, &sb, &sc) != ORACLE_OK)
+        return ORACLE_EINVAL;
+    if (n == 0)
+        return ORACLE_OK;
+    a = (int32_t *)malloc(sizeof(int32_t) * (size_t)(H * W));
+    if (!a)
+        return ORACLE_ENOMEM;
+    for (i = 0; i < H * W; i++) /* map + level shift; past n the byte is 0 */
+        a[i] = (int32_t)(i < n ? in[i] : 0) - 128;
+    st = blocks_2d(a, (int64_t)H, (int64_t)W, PK_L, PK_B, 1);
+    memset(a_out, 0, (size_t)sa);
+    memset(b_out, 0, (size_t)sb);
+    memset(c_out, 0, (size_t)sc);
+    outs[0] = a_out;
+    outs[1] = b_out;
+    outs[2] = c_out;
+    nbx = W / PK_B;
+    for (bi = 0; bi < H / PK_B && st == ORACLE_OK; bi++)
+        for (bj = 0; bj < nbx && st == ORACLE_OK; bj++) {
+            block_tiles(a, (int64_t)H, (int64_t)W, blk, PK_B, PK_L, (int64_t)bi, (int64_t)bj, 0);
+            for (rec = 0; rec < 3 && st == ORACLE_OK; rec++) {
+                uint64_t pos = record_pos(rec, bi, bj, nbx);
+                record_fields(rec, idx, width, &cnt);
+                for (k = 0; k < cnt && st == ORACLE_OK; k++) {
+                    st = put_bits(outs[rec], pos, blk[idx[k]], width[k]);
+                    pos += (uint64_t)width[k];
+                }
+            }
+        }
+    if (st == ORACLE_OK)
+        oracle_aes128_ctr_xor(key, nonce, 0, a_out, sa);
+    free(a);
+    return st;
+}
+
+int oracle_recover_packed(const uint8_t *a_in, const uint8_t *b_in, const uint8_t *c_in, uint64_t n,
+                          uint32_t W, const uint8_t key[16], uint64_t nonce, uint8_t *out)
+{
+    uint64_t H, sa, sb, sc, i, bi, bj, nbx;
+    int32_t *a, blk[PK_B * PK_B];
+    uint8_t *plain;
+    const uint8_t *ins[3];
+    int st = ORACLE_OK, rec, k, cnt;
+    int64_t idx[48];
+    int width[48];
+    if (oracle_packed_sizes(n, W, &H, &sa, &sb, &sc) != ORACLE_OK)
+        return ORACLE_EINVAL;
+    if (n == 0)
+        return ORACLE_OK;
+    a = (int32_t *)malloc(sizeof(int32_t) * (size_t)(H * W));
+    plain = (uint8_t *)malloc((size_t)sa);
+    if (!a || !plain) {
+        free(a);
+        free(plain);
+        return ORACLE_ENOMEM;
+    }
+    memcpy(plain, a_in, (size_t)sa);
+    oracle_aes128_ctr_xor(key, nonce, 0, plain, sa);
+    ins[0] = plain;
+    ins[1] = b_in;
+    ins[2] = c_in;
+    nbx = W / PK_B;
+    for (bi = 0; bi < H / PK_B; bi++)
+        for (bj = 0; bj < nbx; bj++) {
+            for (k = 0; k < PK_B * PK_B; k++)
+                blk[k] = 0;
+            for (rec = 0; rec < 3; rec++) {
+                uint64_t pos = record_pos(rec, bi, bj, nbx);
+                record_fields(rec, idx, width, &cnt);
+                for (k = 0; k < cnt; k++) {
+                    blk[idx[k]] = get_bits(ins[rec], pos, width[k]);
+                    pos += (uint64_t)width[k];
+                }
+            }
+            block_tiles(a, (int64_t)H, (int64_t)W, blk, PK_B, PK_L, (int64_t)bi, (int64_t)bj, 1);
+        }
+    st = blocks_2d(a, (int64_t)H, (int64_t)W, PK_L, PK_B, 0);
+    for (i = 0; i < n && st == ORACLE_OK; i++) {
+        int32_t v = a[i] + 128;
+        if (v < 0 || v > 255)
+            st = ORACLE_ERANGE;
+        else
+            out[i] = (uint8_t)v;
+    }
+    free(a);
+    free(plain);
+    return st;
+}
