@@ -44,7 +44,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2",
-                    choices=["c2", "c2blocks", "c3l2", "c3l4", "c4", "c5", "aesfull"])
+                    choices=["c2", "c2blocks", "c2packed", "c3l2", "c3l4", "c4", "c5", "aesfull"])
     ap.add_argument("--items", type=int, default=10000, help="c4: number of buffers")
     ap.add_argument("--requests", type=int, default=240, help="c5: requests per load level")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -76,6 +76,15 @@ def _workload(name):
         return ({"workload": "bitmap 3x4096x4096 u8 in 8x8 blocks, 5/3 DWT 2 levels per block, "
                              "LL_2 AES-128-CTR", "planes": 3, "width": 4096, "levels": 2,
                  "block": 8},
+                [(4096, 2, i, planes[i].reshape(-1)) for i in range(planes.shape[0])])
+    if name == "c2packed":
+        # the thesis's storage of its three fragments (Sec. 5.2.3): 40 / 124 /
+        # 480 bits a block for the private, first and second public fragment
+        planes = wl.c2()
+        return ({"workload": "bitmap 3x4096x4096 u8 in 8x8 blocks, 5/3 DWT 2 levels per block, "
+                             "packed three fragments (40 / 124 / 480 bits a block), private "
+                             "AES-128-CTR", "planes": 3, "width": 4096, "levels": 2, "block": 8,
+                 "packed": True},
                 [(4096, 2, i, planes[i].reshape(-1)) for i in range(planes.shape[0])])
     L = 2 if name == "c3l2" else 4
     return ({"workload": "256 MiB mixed buffer (uniform|text|int32 walk), width 8192, "
@@ -156,8 +165,12 @@ def run_reference(args, rank):
     times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        p, u = oracle.protect(sample, W, L, wl.KEY, nonce, block=desc.get("block", 0))
-        oracle.recover(p, u, n, W, L, wl.KEY, nonce, block=desc.get("block", 0))
+        if desc.get("packed"):
+            p, u = oracle.protect_packed(sample, W, wl.KEY, nonce)
+            oracle.recover_packed(p, u, n, W, wl.KEY, nonce)
+        else:
+            p, u = oracle.protect(sample, W, L, wl.KEY, nonce, block=desc.get("block", 0))
+            oracle.recover(p, u, n, W, L, wl.KEY, nonce, block=desc.get("block", 0))
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt)
@@ -203,15 +216,19 @@ def _traffic(workload, kernel):
     return None
 
 
-def _cpu_baseline(items, block=0):
+def _cpu_baseline(items, block=0, packed=False):
     import oracle
     from paper_1803_04880_b300 import workloads as wl
     W, L, nonce, data = items[0]
     n = data.size
     reps, t0 = 0, time.perf_counter()
     while True:
-        p, u = oracle.protect(data, W, L, wl.KEY, nonce, block=block)
-        oracle.recover(p, u, n, W, L, wl.KEY, nonce, block=block)
+        if packed:
+            p, u = oracle.protect_packed(data, W, wl.KEY, nonce)
+            oracle.recover_packed(p, u, n, W, wl.KEY, nonce)
+        else:
+            p, u = oracle.protect(data, W, L, wl.KEY, nonce, block=block)
+            oracle.recover(p, u, n, W, L, wl.KEY, nonce, block=block)
         reps += 1
         el = time.perf_counter() - t0
         if el >= 10.0 or reps >= 20:
@@ -219,6 +236,45 @@ def _cpu_baseline(items, block=0):
     return {"value": round(n * reps / el / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "item 0 of the workload (%d bytes), protect+recover x%d, one thread"
                       % (n, reps)}
+
+
+class _Singles:
+    """The batch object's interface over single-buffer calls, for plans that
+    batches refuse (the packed storage): a direction is one call per item,
+    three launches each (block kernel, pack kernel, CTR); with timing on,
+    an event pair around each call."""
+
+    def __init__(self, fr, entries, protect):
+        self.fr, self.entries, self.protect = fr, entries, protect
+        self.launches = 3 * len(entries)
+        self.timing, self.ev = False, []
+
+    def run(self, key, s):
+        import torch
+        for e in self.entries:
+            if self.timing:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+            if self.protect:
+                plan, nonce, n, t, p, u = e
+                self.fr.protect(plan, key, nonce, t, n, p, u, stream=s)
+            else:
+                plan, nonce, n, p, u, o = e
+                self.fr.recover(plan, key, nonce, p, u, n, o, stream=s)
+            if self.timing:
+                e1.record(s)
+                self.ev.append((e0, e1))
+
+    def set_timing(self, on):
+        self.timing = bool(on)
+
+    def launch_times(self):
+        import torch
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in self.ev)
+        n = len(self.ev)
+        self.ev = []
+        return {"call": (ms, n)}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -239,6 +295,8 @@ def run_ours(args, rank, world, local_rank):
         if (W, L) not in plans:
             plans[(W, L)] = fr.Plan(W, L)
             plans[(W, L)].set_block(desc.get("block", 0))
+            if desc.get("packed"):
+                plans[(W, L)].set_packed(True)
         plan = plans[(W, L)]
         n = data.size
         _, pb, ub = plan.sizes(n)
@@ -250,8 +308,13 @@ def run_ours(args, rank, world, local_rank):
         pitems.append((plan, nonce, n, t, p, u))
         ritems.append((plan, nonce, n, p, u, o))
         n_total += n
-    bp = fr.Batch(pitems, protect=True)
-    br = fr.Batch(ritems, protect=False)
+    if desc.get("packed"):
+        bp = _Singles(fr, pitems, True)
+        br = _Singles(fr, ritems, False)
+    else:
+        bp = fr.Batch(pitems, protect=True)
+        br = fr.Batch(ritems, protect=False)
+    frag_total = sum(p.numel() + u.numel() for p, u in zip(privs, pubs))
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     flush_words = flush.view(torch.int32)
     s = torch.cuda.Stream(device=dev)
@@ -363,15 +426,23 @@ def run_ours(args, rank, world, local_rank):
     # the fused kernel reads 1 byte and writes 2 (int16 bands and LL) per
     # input byte, or the reverse; the level kernel the same over all levels
     # (with a second fused pass, the first writes LL_3 to scratch instead of
-    # the private fragment: the same 2 bytes a sample)
+    # the private fragment: the same 2 bytes a sample).  A single call (the
+    # packed storage) moves one item's bytes and fragments.
     alg_bytes = 3 * n_total
+    if dom_kind == "call":
+        alg_bytes = (n_total + frag_total) / len(pitems)
     achieved = alg_bytes / (t_dom / 1e3) / 1e9
     names = {"fused": "fuse_kernel<%s, packed=false> (%s: levels 1..3 of every plane, one launch)",
              "levels": "dag_kernel<%s> (%s: dependency-ordered levels, one launch)",
              "blocks": "block_kernel<%s> (%s: every 8 x 8 block on its own, one launch)",
-             "cipher": "ctr_kernel (%s%s: AES-128-CTR over the private fragments)"}
-    label = names[dom_kind] % ("true" if dom_dir == "protect" else "false", dom_dir) \
-        if dom_kind != "cipher" else names["cipher"] % (dom_dir, "")
+             "cipher": "ctr_kernel (%s%s: AES-128-CTR over the private fragments)",
+             "call": "the packed %s call of one plane (%s: block kernel, pack kernel, CTR)"}
+    if dom_kind == "call":
+        label = names["call"] % (dom_dir, "frag_protect" if dom_dir == "protect" else "frag_recover")
+    elif dom_kind == "cipher":
+        label = names["cipher"] % (dom_dir, "")
+    else:
+        label = names[dom_kind] % ("true" if dom_dir == "protect" else "false", dom_dir)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": _traffic(args.workload, dom_dir),
                 "kernel": label, "peak_kind": peak_kind,
@@ -407,7 +478,7 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = _cpu_baseline(items, desc.get("block", 0))
+        cpu = _cpu_baseline(items, desc.get("block", 0), bool(desc.get("packed")))
 
     if rank == 0:
         q = sorted(steps_ms)
@@ -417,12 +488,15 @@ def run_ours(args, rank, world, local_rank):
                 "dtype": "int32", "data": "synthetic",
                 "config": dict(desc, l2="flushed before each direction (512 MiB write, then read back)",
                                parallelism="replicas" if world > 1 else "single GPU",
-                               path="frag_batch_run (fused levels + AES-CTR, one launch each per direction)"),
+                               path=("frag_protect / frag_recover per plane (block kernel, pack "
+                                     "kernel, AES-CTR)" if desc.get("packed") else
+                                     "frag_batch_run (fused levels + AES-CTR, one launch each per "
+                                     "direction)")),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": 2 * K * bp.launches,
                 "protect_gbps": round(n_total / (t_prot / 1e3) / 1e9, 2),
                 "recover_gbps": round(n_total / (t_rec / 1e3) / 1e9, 2),
-                "hbm_frac_protect_recover": round(2 * alg_bytes / (ms_per_step / 1e3) / 1e9 / peak, 4),
+                "hbm_frac_protect_recover": round(2 * (n_total + frag_total) / (ms_per_step / 1e3) / 1e9 / peak, 4),
                 "per_file": {"ms_per_step": round(pf, 5),
                              "value": round(n_total / (pf / 1e3) / 1e9, 2),
                              "batched_over_per_file": round(pf / ms_per_step, 3)},

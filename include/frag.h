@@ -143,6 +143,36 @@ frag_status frag_plan_get_path(frag_plan plan, frag_path *path);
 frag_status frag_plan_set_block(frag_plan plan, uint32_t block);
 frag_status frag_plan_get_block(frag_plan plan, uint32_t *block);
 
+/* The thesis's storage of its three fragments (Sec. 5.2.1: the private, the
+ * first and the second public and protected fragment; Sec. 5.2.3: 10 or 11
+ * bits a coefficient), for 8 x 8 blocks at two levels only: packed != 0
+ * makes frag_protect / frag_recover of this plan read and write
+ *   private  A: per block LL_2 - 128 as 4 x 10 bits (5 bytes), blocks
+ *              row-major, enciphered with the same AES-128-CTR;
+ *   public   B then C: B holds per block HL_2 and LH_2 at 10 bits and HH_2
+ *              at 11 (124 bits), the blocks of a block row every 124 bits,
+ *              each block row starting on a byte; C per block HL_1, LH_1,
+ *              HH_1 at 10 bits (60 bytes), blocks row-major.
+ * A value is its two's complement in its width; a record's values follow
+ * each other from bit 0 (each band's tile row-major, bands in the order
+ * above) and fill bytes from the least significant bit.  The coefficient
+ * bounds (Sec. 5.2.3) make the widths enough; a value outside its width
+ * makes frag_sync_status report FRAG_EDEVICE.  frag_plan_sizes gives
+ * |A| and |B| + |C|; frag_plan_fragment_sizes splits the public part.
+ * Batched calls refuse packed plans (FRAG_EUNSUPPORTED).  FRAG_EUNSUPPORTED
+ * unless the plan has levels == 2 and block 8; frag_plan_set_block on a
+ * packed plan to anything but 8 is FRAG_EINVAL. */
+frag_status frag_plan_set_packed(frag_plan plan, uint32_t packed);
+frag_status frag_plan_get_packed(frag_plan plan, uint32_t *packed);
+
+/* The three fragments of nbytes bytes under the plan (Sec. 5.2.1): sizes[0]
+ * the private fragment, sizes[1] the first public and protected fragment
+ * (the detail bands of level L, which lead the public fragment; B when
+ * packed), sizes[2] the second (the other levels' bands; C when packed).
+ * sizes[1] + sizes[2] is frag_plan_sizes' public_bytes.  FRAG_EINVAL if
+ * sizes is NULL. */
+frag_status frag_plan_fragment_sizes(frag_plan plan, uint64_t nbytes, uint64_t sizes[3]);
+
 /* AES-128 key (Sec. 5.2.1 protects the private fragment with AES-128): the
  * round keys are expanded on the host (FIPS-197 Sec. 5.2) and kept resident on
  * each device that uses the key.  The 16 bytes are copied. */

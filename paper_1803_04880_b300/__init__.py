@@ -25,7 +25,8 @@ EXPORTS = [
     "frag_abi_version", "frag_plan_create", "frag_plan_destroy", "frag_plan_sizes",
     "frag_plan_set_tiling", "frag_plan_get_tiling", "frag_plan_set_schedule",
     "frag_plan_get_schedule", "frag_plan_set_path", "frag_plan_get_path",
-    "frag_plan_set_block", "frag_plan_get_block",
+    "frag_plan_set_block", "frag_plan_get_block", "frag_plan_set_packed", "frag_plan_get_packed",
+    "frag_plan_fragment_sizes",
     "frag_key_create", "frag_key_destroy",
     "frag_protect", "frag_recover", "frag_aes128_ctr", "frag_protect_host", "frag_recover_host",
     "frag_protect_batch", "frag_recover_batch", "frag_batch_create_protect",
@@ -86,6 +87,9 @@ def lib():
         "frag_plan_set_path": ([vp, ctypes.c_int], ctypes.c_int),
         "frag_plan_set_block": ([vp, u32], ctypes.c_int),
         "frag_plan_get_block": ([vp, ctypes.POINTER(u32)], ctypes.c_int),
+        "frag_plan_set_packed": ([vp, u32], ctypes.c_int),
+        "frag_plan_get_packed": ([vp, ctypes.POINTER(u32)], ctypes.c_int),
+        "frag_plan_fragment_sizes": ([vp, u64, ctypes.POINTER(u64)], ctypes.c_int),
         "frag_plan_get_path": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "frag_key_create": ([ctypes.POINTER(vp), ctypes.c_char_p], ctypes.c_int),
         "frag_key_destroy": ([vp], ctypes.c_int),
@@ -193,6 +197,22 @@ class Plan:
         v = ctypes.c_uint32()
         check(lib().frag_plan_get_block(self._h, ctypes.byref(v)))
         return v.value
+
+    def set_packed(self, packed: bool) -> None:
+        """The thesis's packed three fragments (8 x 8 blocks, two levels):
+        private A (40 bits a block), public B (124) then C (480)."""
+        check(lib().frag_plan_set_packed(self._h, 1 if packed else 0))
+
+    def packed(self) -> bool:
+        v = ctypes.c_uint32()
+        check(lib().frag_plan_get_packed(self._h, ctypes.byref(v)))
+        return bool(v.value)
+
+    def fragment_sizes(self, nbytes: int) -> Tuple[int, int, int]:
+        """(private, first public, second public) bytes of nbytes bytes."""
+        v = (ctypes.c_uint64 * 3)()
+        check(lib().frag_plan_fragment_sizes(self._h, nbytes, v))
+        return v[0], v[1], v[2]
 
     def tiling(self) -> Tuple[int, int, int]:
         a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()

@@ -30,6 +30,7 @@ struct frag_plan_s {
     uint32_t max_ctas;    // streaming path: grid cap (0: all resident CTAs)
     uint32_t path;        // frag_path: which kernels run the levels
     uint32_t block;       // block mode: side of the blocks (0: whole matrix)
+    uint32_t packed;      // the thesis's packed three fragments (8 x 8 blocks, two levels)
 };
 
 struct frag_key_s {
@@ -288,6 +289,19 @@ constexpr uint32_t kSpinLimit = 1u << 22;       // polls of a dependency before 
 uint64_t align256(uint64_t v) { return (v + 255) / 256 * 256; }
 
 uint64_t ll_bytes(uint32_t H, uint32_t W, uint32_t l) { return 2ull * (H >> l) * (uint64_t)(W >> l); }
+
+// the packed three fragments of an H x W matrix of 8 x 8 blocks: A (40 bits a
+// block), B (124 bits a block, every block row starting on a byte), C (480)
+void packed_sizes(uint64_t H, uint32_t W, uint64_t *a, uint64_t *b, uint64_t *c, uint64_t *brow = nullptr)
+{
+    const uint64_t nbx = W / frag::kBlockSide, nby = H / frag::kBlockSide;
+    const uint64_t row = (124 * nbx + 7) / 8;
+    *a = 5 * nbx * nby;
+    *b = nby * row;
+    *c = 60 * nbx * nby;
+    if (brow)
+        *brow = row;
+}
 
 // first and last level whose LL band goes through scratch: the fused kernel
 // keeps LL_1 .. LL_{F-1} on chip and hands LL_F over in scratch when levels
@@ -775,11 +789,92 @@ frag_status block_launch(DeviceState &d, bool fwd, frag::FuseWork &w, cudaStream
     return FRAG_OK;
 }
 
+// One buffer in the thesis's packed storage: protect runs the block kernel
+// into an int16 scratch, packs it into the three fragments and enciphers the
+// private one; recover deciphers, unpacks into the scratch and runs the
+// block inverse
+frag_status run_packed(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream_t s)
+{
+    DeviceState *d = nullptr;
+    int dev = 0;
+    frag_status st = device_state(&d, &dev);
+    if (st != FRAG_OK)
+        return st;
+    const uint32_t *rk = nullptr;
+    if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
+        return st;
+    uint64_t sa = 0, sb = 0, sc = 0, brow = 0;
+    packed_sizes(b.H, b.W, &sa, &sb, &sc, &brow);
+    const uint64_t llb = ll_bytes(b.H, b.W, 2), pubu = 2ull * b.H * b.W - llb;
+    uint8_t *mem = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&mem, align256(llb) + align256(pubu) + align256(sa), s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMallocAsync(packing scratch)");
+    uint8_t *sll = mem, *spub = mem + align256(llb), *sA = spub + align256(pubu);
+    frag::PackWork pw;
+    std::memset(&pw, 0, sizeof(pw));
+    pw.ll = sll;
+    for (uint32_t l = 1; l <= 2; ++l)
+        for (uint32_t k = 0; k < 3; ++k)
+            pw.band[l - 1][k] = spub + frag::band_offset(b.H, b.W, 2, l, k);
+    pw.a = fwd ? b.priv : sA;
+    pw.b = fwd ? b.pub : const_cast<uint8_t *>(b.pub_in);
+    pw.c = pw.b + sb;
+    pw.brow = brow;
+    pw.nbx = b.W / frag::kBlockSide;
+    pw.nby = b.H / frag::kBlockSide;
+    pw.W = b.W;
+    pw.cvec = aligned(pw.c, 4) ? 1u : 0u;
+    pw.err = d->err;
+    const uint64_t units = (uint64_t)pw.nby * ((pw.nbx + 31) / 32);
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(
+        1, std::min<uint64_t>((units + frag::kPackWarps - 1) / frag::kPackWarps, 8ull * d->sms));
+    // the block kernel on the int16 layout in scratch
+    Buf t = b;
+    if (fwd) {
+        t.priv = sll;
+        t.pub = spub;
+    } else {
+        t.pub_in = spub;
+        t.scr[2] = sll;
+    }
+    fused_split(fwd, t, plan->path);
+    frag::FuseWork w;
+    std::memset(&w, 0, sizeof(w));
+    w.single = block_buf(fwd, t);
+    w.nbufs = 1;
+    w.total_units = block_units(&w.single, 1);
+    frag::CtrChunk c;
+    std::memset(&c, 0, sizeof(c));
+    c.in = fwd ? b.priv : b.priv_in;
+    c.out = fwd ? b.priv : sA;
+    c.nonce = b.nonce;
+    c.bytes = sa;
+    c.nblocks = (sa + 15) / 16;
+    if (fwd) {
+        st = block_launch(*d, true, w, s);
+        if (st == FRAG_OK && (e = frag::launch_pack(true, pw, grid, s)) != cudaSuccess)
+            st = cuda_fail(e, "pack launch");
+        if (st == FRAG_OK)
+            st = ctr_launch(*d, rk, nullptr, 0, &c, s);
+    } else {
+        st = ctr_launch(*d, rk, nullptr, 0, &c, s);
+        if (st == FRAG_OK && (e = frag::launch_pack(false, pw, grid, s)) != cudaSuccess)
+            st = cuda_fail(e, "unpack launch");
+        if (st == FRAG_OK)
+            st = block_launch(*d, false, w, s);
+    }
+    cudaFreeAsync(mem, s);
+    return st;
+}
+
 // One buffer: protect runs the fused levels, then the dependency-ordered
 // launch for the levels above them (and the cipher units), then the CTR
 // launch; recover runs them in the reverse order.
 frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream_t s)
 {
+    if (plan->packed)
+        return run_packed(fwd, plan, key, b, s);
     DeviceState *d = nullptr;
     int dev = 0;
     frag_status st = device_state(&d, &dev);
@@ -959,6 +1054,8 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
         b.L = plan->levels;
         b.R0_plan = plan->seg_rows;
         b.block = plan->block;
+        if (plan->packed)
+            return fail(FRAG_EUNSUPPORTED, "item %u: packed fragments run through frag_protect / frag_recover", i);
         if (bp.bufs.empty() && v.empty()) {
             bp.max_ctas = plan->max_ctas; // the grid of a launch: the first item's plan
             bp.fuse_rows = plan->seg_rows;
@@ -1443,10 +1540,42 @@ frag_status frag_plan_sizes(frag_plan plan, uint64_t nbytes, uint32_t *height,
     const uint64_t pb = 2 * (H >> plan->levels) * (uint64_t)(plan->width >> plan->levels);
     if (height)
         *height = (uint32_t)H;
+    if (plan->packed) {
+        uint64_t a, b, c;
+        packed_sizes(H, plan->width, &a, &b, &c);
+        if (private_bytes)
+            *private_bytes = a;
+        if (public_bytes)
+            *public_bytes = b + c;
+        return FRAG_OK;
+    }
     if (private_bytes)
         *private_bytes = pb;
     if (public_bytes)
         *public_bytes = 2 * H * (uint64_t)plan->width - pb;
+    return FRAG_OK;
+}
+
+frag_status frag_plan_fragment_sizes(frag_plan plan, uint64_t nbytes, uint64_t sizes[3])
+{
+    frag_status st = check_plan(plan);
+    if (st != FRAG_OK)
+        return st;
+    if (sizes == nullptr)
+        return fail(FRAG_EINVAL, "sizes is NULL");
+    uint32_t H = 0;
+    uint64_t pb = 0, ub = 0;
+    if ((st = frag_plan_sizes(plan, nbytes, &H, &pb, &ub)) != FRAG_OK)
+        return st;
+    if (plan->packed) {
+        packed_sizes(H, plan->width, &sizes[0], &sizes[1], &sizes[2]);
+        return FRAG_OK;
+    }
+    // the detail bands of level L lead the public fragment
+    const uint64_t first = 3 * ll_bytes(H, plan->width, plan->levels);
+    sizes[0] = pb;
+    sizes[1] = first;
+    sizes[2] = ub - first;
     return FRAG_OK;
 }
 
@@ -1524,7 +1653,32 @@ frag_status frag_plan_set_block(frag_plan plan, uint32_t block)
         if (block != frag::kBlockSide || plan->levels > 3)
             return fail(FRAG_EUNSUPPORTED, "the block mode runs 8 x 8 blocks with up to 3 levels");
     }
+    if (plan->packed && block != frag::kBlockSide)
+        return fail(FRAG_EINVAL, "the plan stores packed fragments: clear that first");
     plan->block = block;
+    return FRAG_OK;
+}
+
+frag_status frag_plan_set_packed(frag_plan plan, uint32_t packed)
+{
+    frag_status st = check_plan(plan);
+    if (st != FRAG_OK)
+        return st;
+    if (packed && (plan->block != frag::kBlockSide || plan->levels != 2))
+        return fail(FRAG_EUNSUPPORTED, "packed fragments are the thesis's storage of 8 x 8 blocks at two "
+                                       "levels (frag_plan_set_block(plan, 8) on a 2-level plan first)");
+    plan->packed = packed ? 1u : 0u;
+    return FRAG_OK;
+}
+
+frag_status frag_plan_get_packed(frag_plan plan, uint32_t *packed)
+{
+    frag_status st = check_plan(plan);
+    if (st != FRAG_OK)
+        return st;
+    if (packed == nullptr)
+        return fail(FRAG_EINVAL, "packed is NULL");
+    *packed = plan->packed;
     return FRAG_OK;
 }
 
@@ -1891,6 +2045,8 @@ frag_status frag_sync_status(frag_stream stream)
         return fail(FRAG_ETIMEOUT, "a bounded wait for another unit's output ran out");
     if (word == 4)
         return fail(FRAG_ETIMEOUT, "a bounded wait for a shared-memory stage ran out");
+    if (word == 5)
+        return fail(FRAG_EDEVICE, "a coefficient did not fit its width in the packed fragments");
     return fail(FRAG_EDEVICE, "kernel reported inconsistent work descriptor (code %d)", word);
 }
 

@@ -84,6 +84,35 @@ def test_null_arguments_are_rejected(L):
     assert L.frag_aes128_ctr(None, 0, None, None, 16, None) == fr.FRAG_EINVAL
 
 
+def test_packed_validation(L):
+    import oracle
+    p = fr.Plan(64, 2)
+    with pytest.raises(fr.FragError):
+        p.set_packed(True)  # not in block mode
+    p.set_block(8)
+    p.set_packed(True)
+    assert p.packed()
+    with pytest.raises(fr.FragError):
+        p.set_block(0)  # packed plans keep their 8 x 8 blocks
+    for n in (1, 64 * 8, 64 * 24 - 5, 64 * 4096):
+        H, a, b, c = oracle.packed_sizes(n, 64)
+        assert p.sizes(n) == (H, a, b + c)
+        assert p.fragment_sizes(n) == (a, b, c)
+    p.set_packed(False)
+    assert not p.packed()
+    q = fr.Plan(64, 3)
+    q.set_block(8)
+    with pytest.raises(fr.FragError):
+        q.set_packed(True)  # the thesis's storage is for two levels
+    # unpacked plans: the first public fragment is level L's three bands
+    for W, Lv, n in ((64, 2, 64 * 30), (256, 3, 256 * 100 + 7)):
+        r = fr.Plan(W, Lv)
+        H, pb, ub = r.sizes(n)
+        assert r.fragment_sizes(n) == (pb, 3 * pb, ub - 3 * pb)
+    assert L.frag_plan_fragment_sizes(q.handle, 16, None) == fr.FRAG_EINVAL
+    assert L.frag_plan_get_packed(q.handle, None) == fr.FRAG_EINVAL
+
+
 def test_block_validation(L):
     p = fr.Plan(64, 2)
     assert p.block() == 0
