@@ -238,45 +238,6 @@ def _cpu_baseline(items, block=0, packed=False):
                       % (n, reps)}
 
 
-class _Singles:
-    """The batch object's interface over single-buffer calls, for plans that
-    batches refuse (the packed storage): a direction is one call per item,
-    three launches each (block kernel, pack kernel, CTR); with timing on,
-    an event pair around each call."""
-
-    def __init__(self, fr, entries, protect):
-        self.fr, self.entries, self.protect = fr, entries, protect
-        self.launches = 3 * len(entries)
-        self.timing, self.ev = False, []
-
-    def run(self, key, s):
-        import torch
-        for e in self.entries:
-            if self.timing:
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(s)
-            if self.protect:
-                plan, nonce, n, t, p, u = e
-                self.fr.protect(plan, key, nonce, t, n, p, u, stream=s)
-            else:
-                plan, nonce, n, p, u, o = e
-                self.fr.recover(plan, key, nonce, p, u, n, o, stream=s)
-            if self.timing:
-                e1.record(s)
-                self.ev.append((e0, e1))
-
-    def set_timing(self, on):
-        self.timing = bool(on)
-
-    def launch_times(self):
-        import torch
-        torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in self.ev)
-        n = len(self.ev)
-        self.ev = []
-        return {"call": (ms, n)}
-
-
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -308,12 +269,8 @@ def run_ours(args, rank, world, local_rank):
         pitems.append((plan, nonce, n, t, p, u))
         ritems.append((plan, nonce, n, p, u, o))
         n_total += n
-    if desc.get("packed"):
-        bp = _Singles(fr, pitems, True)
-        br = _Singles(fr, ritems, False)
-    else:
-        bp = fr.Batch(pitems, protect=True)
-        br = fr.Batch(ritems, protect=False)
+    bp = fr.Batch(pitems, protect=True)
+    br = fr.Batch(ritems, protect=False)
     frag_total = sum(p.numel() + u.numel() for p, u in zip(privs, pubs))
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     flush_words = flush.view(torch.int32)
@@ -426,20 +383,17 @@ def run_ours(args, rank, world, local_rank):
     # the fused kernel reads 1 byte and writes 2 (int16 bands and LL) per
     # input byte, or the reverse; the level kernel the same over all levels
     # (with a second fused pass, the first writes LL_3 to scratch instead of
-    # the private fragment: the same 2 bytes a sample).  A single call (the
-    # packed storage) moves one item's bytes and fragments.
-    alg_bytes = 3 * n_total
-    if dom_kind == "call":
-        alg_bytes = (n_total + frag_total) / len(pitems)
+    # the private fragment: the same 2 bytes a sample); the block kernel of
+    # the packed storage moves the input and the three packed fragments
+    alg_bytes = n_total + frag_total if desc.get("packed") else 3 * n_total
     achieved = alg_bytes / (t_dom / 1e3) / 1e9
     names = {"fused": "fuse_kernel<%s, packed=false> (%s: levels 1..3 of every plane, one launch)",
              "levels": "dag_kernel<%s> (%s: dependency-ordered levels, one launch)",
              "blocks": "block_kernel<%s> (%s: every 8 x 8 block on its own, one launch)",
-             "cipher": "ctr_kernel (%s%s: AES-128-CTR over the private fragments)",
-             "call": "the packed %s call of one plane (%s: block kernel, pack kernel, CTR)"}
-    if dom_kind == "call":
-        label = names["call"] % (dom_dir, "frag_protect" if dom_dir == "protect" else "frag_recover")
-    elif dom_kind == "cipher":
+             "cipher": "ctr_kernel (%s%s: AES-128-CTR over the private fragments)"}
+    if desc.get("packed"):
+        names["blocks"] = "block_kernel<%s, packed=true> (%s: every 8 x 8 block, its bit records, one launch)"
+    if dom_kind == "cipher":
         label = names["cipher"] % (dom_dir, "")
     else:
         label = names[dom_kind] % ("true" if dom_dir == "protect" else "false", dom_dir)
@@ -488,8 +442,8 @@ def run_ours(args, rank, world, local_rank):
                 "dtype": "int32", "data": "synthetic",
                 "config": dict(desc, l2="flushed before each direction (512 MiB write, then read back)",
                                parallelism="replicas" if world > 1 else "single GPU",
-                               path=("frag_protect / frag_recover per plane (block kernel, pack "
-                                     "kernel, AES-CTR)" if desc.get("packed") else
+                               path=("frag_batch_run (the packed block kernel + AES-CTR, one launch "
+                                     "each per direction)" if desc.get("packed") else
                                      "frag_batch_run (fused levels + AES-CTR, one launch each per "
                                      "direction)")),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

@@ -159,7 +159,7 @@ frag_status frag_plan_get_block(frag_plan plan, uint32_t *block);
  * bounds (Sec. 5.2.3) make the widths enough; a value outside its width
  * makes frag_sync_status report FRAG_EDEVICE.  frag_plan_sizes gives
  * |A| and |B| + |C|; frag_plan_fragment_sizes splits the public part.
- * Batched calls refuse packed plans (FRAG_EUNSUPPORTED).  FRAG_EUNSUPPORTED
+ * Batched calls take packed plans beside any others.  FRAG_EUNSUPPORTED
  * unless the plan has levels == 2 and block 8; frag_plan_set_block on a
  * packed plan to anything but 8 is FRAG_EINVAL. */
 frag_status frag_plan_set_packed(frag_plan plan, uint32_t packed);

@@ -13,8 +13,12 @@
 //
 // Band layout (as in the whole-matrix mode): band (l, k) is an H_l x W_l
 // int16 image and block (bi, bj) fills rows [bi 8/2^l, (bi+1) 8/2^l) and
-// columns [bj 8/2^l, (bj+1) 8/2^l) of it; LL_L - 128 goes to `ll`.
+// columns [bj 8/2^l, (bj+1) 8/2^l) of it; LL_L - 128 goes to `ll`.  A
+// packed buffer (two levels) instead gets the thesis's bit records of its
+// three fragments straight from the registers (pack_bits.cuh): the lane
+// writes its block's A and C records, the warp its 32 blocks' B records.
 #include "frag_internal.cuh"
+#include "pack_bits.cuh"
 #include "swar.cuh"
 
 namespace frag {
@@ -350,38 +354,52 @@ __device__ __forceinline__ void inv_issue(const Slot &sl, uint32_t s8, uint32_t 
 // one block, forward and inverse (rows from the stage, or straight from
 // global memory with byte accesses when the buffer is not aligned)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged,
-                                          uint32_t st)
+// the block's 8 rows of 8 bytes from the stage, or straight from global
+// memory (8-byte loads where the row is whole data and aligned)
+__device__ __forceinline__ void block_rows(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged, bool vec8,
+                                           uint32_t st, uint2 (&v)[8])
 {
-    const uint32_t W = f.W, L = f.F;
-    uint32_t x1[8][4]; // row-lifted rows, 4 words each
+    const uint32_t W = f.W;
     const uint64_t base = bi * 8 * W + (uint64_t)bj * 8;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-        uint2 v;
         if (staged) {
-            v = lds8(st + 256 * r);
+            v[r] = lds8(st + 256 * r);
+        } else if (vec8 && bi * 8 + r < f.full_rows) {
+            v[r] = __ldg(reinterpret_cast<const uint2 *>(f.src + base + (uint64_t)r * W));
         } else {
             const uint64_t off = base + (uint64_t)r * W;
             uint32_t b8[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 b8[i] = off + i < f.n ? (uint32_t)__ldg(f.src + off + i) : 0u;
-            v.x = b8[0] | (b8[1] << 8) | (b8[2] << 16) | (b8[3] << 24);
-            v.y = b8[4] | (b8[5] << 8) | (b8[6] << 16) | (b8[7] << 24);
+            v[r].x = b8[0] | (b8[1] << 8) | (b8[2] << 16) | (b8[3] << 24);
+            v[r].y = b8[4] | (b8[5] << 8) | (b8[6] << 16) | (b8[7] << 24);
         }
-        lift8(v.x, v.y, x1[r]);
     }
+}
+
+template <bool PACKED>
+__device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged,
+                                          const uint2 (&v)[8], uint32_t (&rb)[4], int *err)
+{
+    const uint32_t W = f.W, L = f.F;
+    uint32_t x1[8][4]; // row-lifted rows, 4 words each
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+        lift8(v[r].x, v[r].y, x1[r]);
     uint32_t s1[4][4], d1[4][4];
     col_lift<8, 4>(x1, s1, d1);
     // level-1 tiles: LL_1 = s1[][0..1], HL_1 = s1[][2..3], LH_1 = d1[][0..1], HH_1 = d1[][2..3]
     const uint32_t W1 = W >> 1;
     const bool vec = staged;
+    if (!PACKED) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        st_tile(tile_row(f.band[0][0], W1, 4, bi, bj, r), 4, to_i16x2(s1[r][2]), to_i16x2(s1[r][3]), vec);
-        st_tile(tile_row(f.band[0][1], W1, 4, bi, bj, r), 4, to_i16x2(d1[r][0]), to_i16x2(d1[r][1]), vec);
-        st_tile(tile_row(f.band[0][2], W1, 4, bi, bj, r), 4, to_i16x2(d1[r][2]), to_i16x2(d1[r][3]), vec);
+        for (int r = 0; r < 4; ++r) {
+            st_tile(tile_row(f.band[0][0], W1, 4, bi, bj, r), 4, to_i16x2(s1[r][2]), to_i16x2(s1[r][3]), vec);
+            st_tile(tile_row(f.band[0][1], W1, 4, bi, bj, r), 4, to_i16x2(d1[r][0]), to_i16x2(d1[r][1]), vec);
+            st_tile(tile_row(f.band[0][2], W1, 4, bi, bj, r), 4, to_i16x2(d1[r][2]), to_i16x2(d1[r][3]), vec);
+        }
     }
     if (L == 1) {
 #pragma unroll
@@ -396,6 +414,55 @@ __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_
         lift4(s1[r][0], s1[r][1], x2[r][0], x2[r][1]);
     uint32_t s2[2][2], d2[2][2];
     col_lift<4, 2>(x2, s2, d2);
+    if (PACKED) {
+        // A: LL_2 - 128 (10 bits); B: HL_2, LH_2 (10), HH_2 (11); C: the
+        // level-1 details (10); B goes back to the warp (store_b)
+        bool ok = true;
+        uint32_t ra[2] = {0u, 0u}, rc[15];
+#pragma unroll
+        for (int i = 0; i < 15; ++i)
+            rc[i] = 0u;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            pkb::put_pair(ra, 20 * r, ll_final(s2[r][0]), 10, ok);     // LL_2 - 128
+            pkb::put_pair(rb, 20 * r, to_i16x2(s2[r][1]), 10, ok);     // HL_2
+            pkb::put_pair(rb, 40 + 20 * r, to_i16x2(d2[r][0]), 10, ok); // LH_2
+            pkb::put_pair(rb, 80 + 22 * r, to_i16x2(d2[r][1]), 11, ok); // HH_2
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            pkb::put_pair(rc, 40 * r, to_i16x2(s1[r][2]), 10, ok); // HL_1
+            pkb::put_pair(rc, 40 * r + 20, to_i16x2(s1[r][3]), 10, ok);
+            pkb::put_pair(rc, 160 + 40 * r, to_i16x2(d1[r][0]), 10, ok); // LH_1
+            pkb::put_pair(rc, 180 + 40 * r, to_i16x2(d1[r][1]), 10, ok);
+            pkb::put_pair(rc, 320 + 40 * r, to_i16x2(d1[r][2]), 10, ok); // HH_1
+            pkb::put_pair(rc, 340 + 40 * r, to_i16x2(d1[r][3]), 10, ok);
+        }
+        if (!ok)
+            atomicCAS(err, 0, pkb::kErrWidth);
+        const uint64_t idx = bi * (uint64_t)(W >> 3) + bj;
+        uint8_t *pa = f.pk[0] + 5 * idx;
+        pa[0] = (uint8_t)ra[0];
+        pa[1] = (uint8_t)(ra[0] >> 8);
+        pa[2] = (uint8_t)(ra[0] >> 16);
+        pa[3] = (uint8_t)(ra[0] >> 24);
+        pa[4] = (uint8_t)ra[1];
+        uint8_t *pc = f.pk[2] + 60 * idx;
+        if ((reinterpret_cast<uintptr_t>(f.pk[2]) & 3u) == 0) {
+#pragma unroll
+            for (int i = 0; i < 15; ++i)
+                __stcs(reinterpret_cast<unsigned int *>(pc) + i, rc[i]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 15; ++i) {
+                pc[4 * i] = (uint8_t)rc[i];
+                pc[4 * i + 1] = (uint8_t)(rc[i] >> 8);
+                pc[4 * i + 2] = (uint8_t)(rc[i] >> 16);
+                pc[4 * i + 3] = (uint8_t)(rc[i] >> 24);
+            }
+        }
+        return;
+    }
     const uint32_t W2 = W >> 2;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -423,12 +490,53 @@ __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_
     st_tile(tile_row(f.ll, W3, 1, bi, bj, 0), 1, ll_final(s3[0][0]), 0, vec);
 }
 
+template <bool PACKED>
 __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged,
-                                          bool vec, uint32_t s8, uint32_t s4)
+                                          bool vec, uint32_t s8, uint32_t s4, const uint32_t (&rb)[4])
 {
     const uint32_t W = f.W, L = f.F;
     const uint32_t W1 = W >> 1, W2 = W >> 2, W3 = W >> 3;
     uint32_t s1[4][4], d1[4][4];
+    if (PACKED) {
+        // the block's A (deciphered) and C records, and its B record from the warp
+        const uint64_t idx = bi * (uint64_t)W3 + bj;
+        const uint8_t *pa = f.pk[0] + 5 * idx;
+        const uint32_t ra[2] = {(uint32_t)pa[0] | ((uint32_t)pa[1] << 8) | ((uint32_t)pa[2] << 16) |
+                                    ((uint32_t)pa[3] << 24),
+                                (uint32_t)pa[4]};
+        uint32_t rc[15];
+        const uint8_t *pc = f.pk[2] + 60 * idx;
+        if ((reinterpret_cast<uintptr_t>(f.pk[2]) & 3u) == 0) {
+#pragma unroll
+            for (int i = 0; i < 15; ++i)
+                rc[i] = __ldg(reinterpret_cast<const unsigned int *>(pc) + i);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 15; ++i)
+                rc[i] = (uint32_t)pc[4 * i] | ((uint32_t)pc[4 * i + 1] << 8) | ((uint32_t)pc[4 * i + 2] << 16) |
+                        ((uint32_t)pc[4 * i + 3] << 24);
+        }
+        uint32_t s2[2][2], d2[2][2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            s2[r][0] = from_i16x2(pkb::get_pair(ra, 20 * r, 10)) + 0x00800080u;
+            s2[r][1] = from_i16x2(pkb::get_pair(rb, 20 * r, 10));
+            d2[r][0] = from_i16x2(pkb::get_pair(rb, 40 + 20 * r, 10));
+            d2[r][1] = from_i16x2(pkb::get_pair(rb, 80 + 22 * r, 11));
+        }
+        uint32_t x2[4][2];
+        col_unlift<4, 2>(s2, d2, x2);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            unlift4(x2[r][0], x2[r][1], s1[r][0], s1[r][1]);
+            s1[r][2] = from_i16x2(pkb::get_pair(rc, 40 * r, 10));
+            s1[r][3] = from_i16x2(pkb::get_pair(rc, 40 * r + 20, 10));
+            d1[r][0] = from_i16x2(pkb::get_pair(rc, 160 + 40 * r, 10));
+            d1[r][1] = from_i16x2(pkb::get_pair(rc, 180 + 40 * r, 10));
+            d1[r][2] = from_i16x2(pkb::get_pair(rc, 320 + 40 * r, 10));
+            d1[r][3] = from_i16x2(pkb::get_pair(rc, 340 + 40 * r, 10));
+        }
+    } else {
     // LL_1: from the input (one level) or from the levels above
     if (L >= 2) {
         uint32_t s2[2][2], d2[2][2];
@@ -517,6 +625,7 @@ __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_
         d1[r][2] = from_i16x2(v[2][0]);
         d1[r][3] = from_i16x2(v[2][1]);
     }
+    } // not packed
     uint32_t x1[8][4];
     col_unlift<8, 4>(s1, d1, x1);
     const uint64_t base = bi * 8 * W + (uint64_t)bj * 8;
@@ -536,17 +645,49 @@ __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_
 
 // the inverse reads four times as many tiles per block as the forward;
 // it runs best with direct loads and many warps, the forward with the ring
-template <bool FWD>
+// PACKED: every buffer of the launch is packed (the warp stores or loads its
+// blocks' B records between blocks, which the staged loop below does not
+// allow for); the inverse, and any packed launch, take direct loads
+template <bool FWD, bool PACKED>
 __global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
 {
-    if (!FWD) {
+    if (!FWD || PACKED) {
+        __shared__ uint32_t sb[kWarps][pkb::kPackBWords]; // a warp's B records
         grid_release();
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const uint64_t G = (uint64_t)gridDim.x * kWarps;
+        // forward: the rows of the unit after the current one, fetched while
+        // the current one is transformed
+        uint2 rows[8];
+        if (FWD) {
+            const Slot s0 = slot_of(w, (uint64_t)blockIdx.x * kWarps + warp, lane);
+            if (s0.on)
+                block_rows(*s0.b, s0.bi, s0.bj, false, s0.vec, 0, rows);
+        }
         for (uint64_t u = (uint64_t)blockIdx.x * kWarps + warp; u < w.total_units; u += G) {
             const Slot sl = slot_of(w, u, lane);
-            if (sl.on)
-                inv_block(*sl.b, sl.bi, sl.bj, false, sl.vec, 0, 0);
+            uint32_t rb[4] = {0u, 0u, 0u, 0u};
+            const uint32_t nbx = sl.b->W >> 3, s = sl.bj >> 5, nvalid = min(32u, nbx - 32 * s);
+            uint8_t *bbase = PACKED ? sl.b->pk[1] + sl.bi * pkb::b_row_bytes(nbx) + 496ull * s : nullptr;
+            const uint32_t bcount = (124 * nvalid + 7) / 8;
+            if (PACKED && !FWD) // the whole warp: its blocks' B records
+                pkb::load_b(sb[warp], bbase, bcount, sl.on, lane, rb);
+            if (FWD) {
+                // this block's rows came with the previous unit; fetch the next unit's
+                uint2 v[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    v[r] = rows[r];
+                const Slot nx = slot_of(w, u + G, lane);
+                if (nx.on)
+                    block_rows(*nx.b, nx.bi, nx.bj, false, nx.vec, 0, rows);
+                if (sl.on)
+                    fwd_block<PACKED>(*sl.b, sl.bi, sl.bj, false, v, rb, w.err);
+            } else if (sl.on) {
+                inv_block<PACKED>(*sl.b, sl.bi, sl.bj, false, sl.vec, 0, 0, rb);
+            }
+            if (PACKED && FWD)
+                pkb::store_b(sb[warp], bbase, bcount, sl.on, lane, rb);
         }
         return;
     }
@@ -579,11 +720,14 @@ __global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
         else
             inv_issue(ahead, ring8 + ahead_off, ring4 + ahead_off);
         cp_wait<kDepth - 1>();
+        uint32_t rb[4] = {0u, 0u, 0u, 0u};
         if (cur.on) {
-            if (FWD)
-                fwd_block(*cur.b, cur.bi, cur.bj, cur.vec, ring8 + cur_off);
-            else
-                inv_block(*cur.b, cur.bi, cur.bj, cur.vec, cur.vec, ring8 + cur_off, ring4 + cur_off);
+            if (FWD) {
+                uint2 v[8];
+                block_rows(*cur.b, cur.bi, cur.bj, cur.vec, false, ring8 + cur_off, v);
+                fwd_block<false>(*cur.b, cur.bi, cur.bj, cur.vec, v, rb, w.err);
+            } else
+                inv_block<false>(*cur.b, cur.bi, cur.bj, cur.vec, cur.vec, ring8 + cur_off, ring4 + cur_off, rb);
         }
     };
     for (uint64_t i = 0; u0 + i * G < w.total_units; i += 3) {
@@ -598,37 +742,49 @@ __global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
     cp_wait<0>();
 }
 
-size_t smem_bytes(bool fwd) { return fwd ? (size_t)kWarps * kDepth * kFwdStage : 0; }
+size_t smem_bytes(bool fwd, bool packed) { return fwd && !packed ? (size_t)kWarps * kDepth * kFwdStage : 0; }
 
-template <bool FWD>
+template <bool FWD, bool PACKED>
 cudaError_t set_attr()
 {
-    return cudaFuncSetAttribute((const void *)block_kernel<FWD>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(FWD));
+    return cudaFuncSetAttribute((const void *)block_kernel<FWD, PACKED>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(FWD, PACKED));
+}
+
+template <bool FWD, bool PACKED>
+cudaError_t launch(const FuseWork &w, uint32_t grid, cudaStream_t stream)
+{
+    cudaError_t e = set_attr<FWD, PACKED>();
+    if (e != cudaSuccess)
+        return e;
+    block_kernel<FWD, PACKED><<<grid, kThreads, smem_bytes(FWD, PACKED), stream>>>(w);
+    return cudaGetLastError();
+}
+
+template <bool FWD, bool PACKED>
+cudaError_t occupancy(int *blocks_per_sm)
+{
+    cudaError_t e = set_attr<FWD, PACKED>();
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void *)block_kernel<FWD, PACKED>,
+                                                         kThreads, smem_bytes(FWD, PACKED));
 }
 
 } // namespace blk
 
-cudaError_t launch_blocks(bool fwd, const FuseWork &w, uint32_t grid, cudaStream_t stream)
+cudaError_t launch_blocks(bool fwd, bool packed, const FuseWork &w, uint32_t grid, cudaStream_t stream)
 {
-    cudaError_t e = fwd ? blk::set_attr<true>() : blk::set_attr<false>();
-    if (e != cudaSuccess)
-        return e;
     if (fwd)
-        blk::block_kernel<true><<<grid, blk::kThreads, blk::smem_bytes(true), stream>>>(w);
-    else
-        blk::block_kernel<false><<<grid, blk::kThreads, blk::smem_bytes(false), stream>>>(w);
-    return cudaGetLastError();
+        return packed ? blk::launch<true, true>(w, grid, stream) : blk::launch<true, false>(w, grid, stream);
+    return packed ? blk::launch<false, true>(w, grid, stream) : blk::launch<false, false>(w, grid, stream);
 }
 
-cudaError_t block_occupancy(bool fwd, int *blocks_per_sm)
+cudaError_t block_occupancy(bool fwd, bool packed, int *blocks_per_sm)
 {
-    cudaError_t e = fwd ? blk::set_attr<true>() : blk::set_attr<false>();
-    if (e != cudaSuccess)
-        return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, fwd ? (const void *)blk::block_kernel<true> : (const void *)blk::block_kernel<false>,
-        blk::kThreads, blk::smem_bytes(fwd));
+    if (fwd)
+        return packed ? blk::occupancy<true, true>(blocks_per_sm) : blk::occupancy<true, false>(blocks_per_sm);
+    return packed ? blk::occupancy<false, true>(blocks_per_sm) : blk::occupancy<false, false>(blocks_per_sm);
 }
 
 } // namespace frag

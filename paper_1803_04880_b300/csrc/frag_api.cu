@@ -328,6 +328,7 @@ struct Buf {
     uint32_t F;        // levels 1..F run in fused passes (0: none): F1 + F2
     uint32_t F1, F2;   // levels of the first pass (bytes) and the second (packed LL_3)
     uint32_t block;    // block mode (every level in the block kernel)
+    uint32_t packed;   // block mode with the packed three fragments
     uint32_t R0;       // level-0 rows per work segment
     uint32_t R0_plan;  // the plan's choice (0: adaptive)
     uint64_t n, nonce;
@@ -549,6 +550,10 @@ frag::CtrChunk ctr_fragment(bool fwd, const Buf &b)
     c.out = fwd ? b.priv : b.scr[b.L];
     c.nonce = b.nonce;
     c.bytes = ll_bytes(b.H, b.W, b.L);
+    if (b.packed) { // A: 5 bytes a block (fits the LL_2 scratch, 8 bytes a block)
+        uint64_t sb, sc;
+        packed_sizes(b.H, b.W, &c.bytes, &sb, &sc);
+    }
     c.nblocks = (c.bytes + 15) / 16;
     return c;
 }
@@ -752,6 +757,21 @@ frag::FuseBuf block_buf(bool fwd, const Buf &b)
     return f;
 }
 
+// a packed buffer's descriptor: the block kernel writes (reads) the bit
+// records; A is the private fragment (protect) or its deciphered copy in the
+// LL_2 scratch (recover), the public fragment is B then C
+frag::FuseBuf packed_buf(bool fwd, const Buf &b)
+{
+    frag::FuseBuf f = block_buf(fwd, b);
+    uint64_t sa, sb, sc;
+    packed_sizes(b.H, b.W, &sa, &sb, &sc);
+    f.packed = 1;
+    f.pk[0] = fwd ? b.priv : b.scr[b.L];
+    f.pk[1] = fwd ? b.pub : const_cast<uint8_t *>(b.pub_in);
+    f.pk[2] = f.pk[1] + sb;
+    return f;
+}
+
 uint64_t block_units(frag::FuseBuf *f, size_t nbufs)
 {
     uint64_t units = 0;
@@ -762,37 +782,39 @@ uint64_t block_units(frag::FuseBuf *f, size_t nbufs)
     return units;
 }
 
-frag_status block_launch(DeviceState &d, bool fwd, frag::FuseWork &w, cudaStream_t s)
+frag_status block_launch(DeviceState &d, bool fwd, frag::FuseWork &w, cudaStream_t s, bool packed = false)
 {
     if (w.total_units == 0)
         return FRAG_OK;
     int occ = 0;
+    const size_t tag = packed ? 6667 : 6666;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        auto it = d.occ[fwd].find(6666);
+        auto it = d.occ[fwd].find(tag);
         if (it != d.occ[fwd].end())
             occ = it->second;
     }
     if (occ == 0) {
-        cudaError_t e = frag::block_occupancy(fwd, &occ);
+        cudaError_t e = frag::block_occupancy(fwd, packed, &occ);
         if (e != cudaSuccess)
             return cuda_fail(e, "occupancy query");
         occ = std::max(occ, 1);
         std::lock_guard<std::mutex> lock(g_mu);
-        d.occ[fwd][6666] = occ;
+        d.occ[fwd][tag] = occ;
     }
+    w.err = d.err;
     const uint64_t need = (w.total_units + 3) / 4; // 4 warps a CTA
     const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)d.sms * occ, need));
-    cudaError_t e = frag::launch_blocks(fwd, w, grid, s);
+    cudaError_t e = frag::launch_blocks(fwd, packed, w, grid, s);
     if (e != cudaSuccess)
         return cuda_fail(e, fwd ? "block protect launch" : "block recover launch");
     return FRAG_OK;
 }
 
-// One buffer in the thesis's packed storage: protect runs the block kernel
-// into an int16 scratch, packs it into the three fragments and enciphers the
-// private one; recover deciphers, unpacks into the scratch and runs the
-// block inverse
+// One buffer in the thesis's packed storage: protect runs the block kernel,
+// which writes the three fragments' bit records, then enciphers the private
+// one in place; recover deciphers it into scratch and runs the block inverse
+// on the records
 frag_status run_packed(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream_t s)
 {
     DeviceState *d = nullptr;
@@ -803,68 +825,41 @@ frag_status run_packed(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     const uint32_t *rk = nullptr;
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
-    uint64_t sa = 0, sb = 0, sc = 0, brow = 0;
-    packed_sizes(b.H, b.W, &sa, &sb, &sc, &brow);
-    const uint64_t llb = ll_bytes(b.H, b.W, 2), pubu = 2ull * b.H * b.W - llb;
-    uint8_t *mem = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&mem, align256(llb) + align256(pubu) + align256(sa), s);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "cudaMallocAsync(packing scratch)");
-    uint8_t *sll = mem, *spub = mem + align256(llb), *sA = spub + align256(pubu);
-    frag::PackWork pw;
-    std::memset(&pw, 0, sizeof(pw));
-    pw.ll = sll;
-    for (uint32_t l = 1; l <= 2; ++l)
-        for (uint32_t k = 0; k < 3; ++k)
-            pw.band[l - 1][k] = spub + frag::band_offset(b.H, b.W, 2, l, k);
-    pw.a = fwd ? b.priv : sA;
-    pw.b = fwd ? b.pub : const_cast<uint8_t *>(b.pub_in);
-    pw.c = pw.b + sb;
-    pw.brow = brow;
-    pw.nbx = b.W / frag::kBlockSide;
-    pw.nby = b.H / frag::kBlockSide;
-    pw.W = b.W;
-    pw.cvec = aligned(pw.c, 4) ? 1u : 0u;
-    pw.err = d->err;
-    const uint64_t units = (uint64_t)pw.nby * ((pw.nbx + 31) / 32);
-    const uint32_t grid = (uint32_t)std::max<uint64_t>(
-        1, std::min<uint64_t>((units + frag::kPackWarps - 1) / frag::kPackWarps, 8ull * d->sms));
-    // the block kernel on the int16 layout in scratch
-    Buf t = b;
-    if (fwd) {
-        t.priv = sll;
-        t.pub = spub;
-    } else {
-        t.pub_in = spub;
-        t.scr[2] = sll;
+    uint64_t sa = 0, sb = 0, sc = 0;
+    packed_sizes(b.H, b.W, &sa, &sb, &sc);
+    uint8_t *plainA = nullptr; // recover: the deciphered private fragment
+    if (!fwd) {
+        cudaError_t e = cudaMallocAsync((void **)&plainA, align256(sa), s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaMallocAsync(private fragment)");
     }
-    fused_split(fwd, t, plan->path);
+    fused_split(fwd, b, plan->path);
     frag::FuseWork w;
     std::memset(&w, 0, sizeof(w));
-    w.single = block_buf(fwd, t);
+    w.single = block_buf(fwd, b);
+    w.single.packed = 1;
+    w.single.pk[0] = fwd ? b.priv : plainA;
+    w.single.pk[1] = fwd ? b.pub : const_cast<uint8_t *>(b.pub_in);
+    w.single.pk[2] = w.single.pk[1] + sb;
     w.nbufs = 1;
     w.total_units = block_units(&w.single, 1);
     frag::CtrChunk c;
     std::memset(&c, 0, sizeof(c));
     c.in = fwd ? b.priv : b.priv_in;
-    c.out = fwd ? b.priv : sA;
+    c.out = fwd ? b.priv : plainA;
     c.nonce = b.nonce;
     c.bytes = sa;
     c.nblocks = (sa + 15) / 16;
     if (fwd) {
-        st = block_launch(*d, true, w, s);
-        if (st == FRAG_OK && (e = frag::launch_pack(true, pw, grid, s)) != cudaSuccess)
-            st = cuda_fail(e, "pack launch");
+        st = block_launch(*d, true, w, s, true);
         if (st == FRAG_OK)
             st = ctr_launch(*d, rk, nullptr, 0, &c, s);
     } else {
         st = ctr_launch(*d, rk, nullptr, 0, &c, s);
-        if (st == FRAG_OK && (e = frag::launch_pack(false, pw, grid, s)) != cudaSuccess)
-            st = cuda_fail(e, "unpack launch");
         if (st == FRAG_OK)
-            st = block_launch(*d, false, w, s);
+            st = block_launch(*d, false, w, s, true);
+        cudaFreeAsync(plainA, s);
     }
-    cudaFreeAsync(mem, s);
     return st;
 }
 
@@ -1016,9 +1011,11 @@ struct DagWave {
     uint64_t fuse_units2 = 0;
     std::vector<frag::FuseBuf> bbufs;   // buffers of the block launch
     uint64_t block_units = 0;
+    std::vector<frag::FuseBuf> pbufs;   // buffers of the packed block launch
+    uint64_t packed_units = 0;
     uint32_t counters = 0;
     size_t jobs_off = 0, units_off = 0, done_off = 0, queue_off = 0, chunks_off = 0, fbufs_off = 0,
-           bbufs_off = 0, fbufs2_off = 0;
+           bbufs_off = 0, fbufs2_off = 0, pbufs_off = 0;
 };
 
 struct BatchPlan {
@@ -1054,8 +1051,7 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
         b.L = plan->levels;
         b.R0_plan = plan->seg_rows;
         b.block = plan->block;
-        if (plan->packed)
-            return fail(FRAG_EUNSUPPORTED, "item %u: packed fragments run through frag_protect / frag_recover", i);
+        b.packed = plan->packed;
         if (bp.bufs.empty() && v.empty()) {
             bp.max_ctas = plan->max_ctas; // the grid of a launch: the first item's plan
             bp.fuse_rows = plan->seg_rows;
@@ -1124,6 +1120,8 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         wv.fuse_units = 0;
         wv.bbufs.clear();
         wv.block_units = 0;
+        wv.pbufs.clear();
+        wv.packed_units = 0;
         wv.fbufs2.clear();
         wv.fuse_units2 = 0;
         wv.counters = 0;
@@ -1140,7 +1138,9 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         buffer_jobs(bp.fwd, b, first, &wv.counters, wv.jobs);
         wv.first.push_back(first);
         wv.levels.push_back(buffer_njobs(b));
-        if (b.block)
+        if (b.block && b.packed)
+            wv.pbufs.push_back(packed_buf(bp.fwd, b));
+        else if (b.block)
             wv.bbufs.push_back(block_buf(bp.fwd, b));
         else if (b.F1)
             wv.fbufs.push_back(fuse_buf(bp.fwd, b, 1));
@@ -1163,6 +1163,7 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
                                       std::max<uint64_t>(1, bp.fuse_slots) * frag::kFuseWarps,
                                       bp.fuse_rows);
         wv.block_units = block_units(wv.bbufs.data(), wv.bbufs.size());
+        wv.packed_units = block_units(wv.pbufs.data(), wv.pbufs.size());
         wv.fuse_units2 = fuse_schedule(wv.fbufs2.data(), wv.fbufs2.size(),
                                        std::max<uint64_t>(1, bp.fuse_slots2) * frag::kFuseWarps,
                                        bp.fuse_rows);
@@ -1185,6 +1186,8 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         off += align256(wv.bbufs.size() * sizeof(frag::FuseBuf));
         wv.fbufs2_off = off;
         off += align256(wv.fbufs2.size() * sizeof(frag::FuseBuf));
+        wv.pbufs_off = off;
+        off += align256(wv.pbufs.size() * sizeof(frag::FuseBuf));
     }
     bp.desc_bytes = off - align256(bp.scratch);
 }
@@ -1210,6 +1213,9 @@ frag_status upload_batch(const BatchPlan &bp, uint8_t *mem, cudaStream_t s, bool
         if (!wv.fbufs2.empty())
             std::memcpy(host.data() + (wv.fbufs2_off - base), wv.fbufs2.data(),
                         wv.fbufs2.size() * sizeof(frag::FuseBuf));
+        if (!wv.pbufs.empty())
+            std::memcpy(host.data() + (wv.pbufs_off - base), wv.pbufs.data(),
+                        wv.pbufs.size() * sizeof(frag::FuseBuf));
     }
     cudaError_t e = async ? cudaMemcpyAsync(mem + base, host.data(), host.size(), cudaMemcpyHostToDevice, s)
                           : cudaMemcpy(mem + base, host.data(), host.size(), cudaMemcpyHostToDevice);
@@ -1274,19 +1280,20 @@ frag_status launch_wave_fused(const BatchPlan &bp, const DagWave &wv, uint8_t *m
 
 // the block launch of a wave (its buffers' descriptors at bbufs_off)
 frag_status launch_wave_blocks(const BatchPlan &bp, const DagWave &wv, uint8_t *mem, DeviceState &d,
-                               cudaStream_t s, LaunchTimer &tm)
+                               cudaStream_t s, LaunchTimer &tm, bool packed = false)
 {
-    if (wv.bbufs.empty())
+    const std::vector<frag::FuseBuf> &bufs = packed ? wv.pbufs : wv.bbufs;
+    if (bufs.empty())
         return FRAG_OK;
     frag::FuseWork w;
     std::memset(&w, 0, sizeof(w));
-    w.nbufs = (uint32_t)wv.bbufs.size();
-    w.bufs = (const frag::FuseBuf *)(mem + wv.bbufs_off);
+    w.nbufs = (uint32_t)bufs.size();
+    w.bufs = (const frag::FuseBuf *)(mem + (packed ? wv.pbufs_off : wv.bbufs_off));
     if (w.nbufs == 1)
-        w.single = wv.bbufs[0];
-    w.total_units = wv.block_units;
+        w.single = bufs[0];
+    w.total_units = packed ? wv.packed_units : wv.block_units;
     tm.begin();
-    frag_status st = block_launch(d, bp.fwd, w, s);
+    frag_status st = block_launch(d, bp.fwd, w, s, packed);
     tm.end(FRAG_KERNEL_BLOCKS);
     return st;
 }
@@ -1306,6 +1313,8 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
         if (bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm, 2)) != FRAG_OK)
             return st;
         if (bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm)) != FRAG_OK)
+            return st;
+        if (bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm, true)) != FRAG_OK)
             return st;
         if (!bp.fwd && !wv.chunks.empty()) { // decipher before the transform reads LL_L
             tm.begin();
@@ -1349,6 +1358,8 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
                 return st;
         }
         if (!bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm)) != FRAG_OK)
+            return st;
+        if (!bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm, true)) != FRAG_OK)
             return st;
         if (!bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm, 2)) != FRAG_OK)
             return st;
@@ -1773,6 +1784,7 @@ frag_status frag_protect(frag_plan plan, frag_key key, uint64_t nonce, const voi
     b.W = plan->width;
     b.L = plan->levels;
     b.block = plan->block;
+    b.packed = plan->packed;
     b.H = (uint32_t)H;
     b.n = nbytes;
     b.nonce = nonce;
@@ -1830,6 +1842,7 @@ frag_status frag_recover(frag_plan plan, frag_key key, uint64_t nonce, const voi
     b.W = plan->width;
     b.L = plan->levels;
     b.block = plan->block;
+    b.packed = plan->packed;
     b.H = (uint32_t)H;
     b.n = nbytes;
     b.nonce = nonce;
@@ -2004,7 +2017,7 @@ frag_status frag_batch_info(frag_batch batch, uint32_t *launches, uint64_t *scra
     uint32_t n = 0;
     for (const auto &wv : batch->bp.waves)
         n += (wv.units.empty() ? 0 : 1) + (wv.chunks.empty() ? 0 : 1) + (wv.fbufs.empty() ? 0 : 1) +
-             (wv.bbufs.empty() ? 0 : 1) + (wv.fbufs2.empty() ? 0 : 1);
+             (wv.bbufs.empty() ? 0 : 1) + (wv.fbufs2.empty() ? 0 : 1) + (wv.pbufs.empty() ? 0 : 1);
     if (launches)
         *launches = n;
     if (scratch_bytes)

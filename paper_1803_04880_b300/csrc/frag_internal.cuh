@@ -205,6 +205,8 @@ struct __align__(16) FuseBuf {
     uint32_t segs;        // units per strip
     uint32_t full_rows;   // leading rows made only of data bytes (n / W)
     uint32_t vec;         // block mode: every access may use its vector width
+    uint32_t packed;      // block mode: the packed three fragments pk instead of int16 bands
+    uint8_t *pk[3];       // packed: A (private, plaintext), B, C (pack_bits.cuh)
 };
 static_assert(sizeof(FuseBuf) % 16 == 0, "fused buffer descriptors are copied in 16-byte pieces");
 
@@ -213,6 +215,7 @@ struct FuseWork {
     FuseBuf single;      // nbufs == 1
     uint32_t nbufs;
     uint64_t total_units;
+    int *err;            // device error word (block mode, packed: 5 = a value outside its width)
 };
 
 // packed: the samples are 16-bit values (v + 0x4000) instead of bytes --
@@ -221,27 +224,13 @@ struct FuseWork {
 cudaError_t launch_fuse(bool fwd, bool packed, const FuseWork &w, uint32_t grid, cudaStream_t stream);
 cudaError_t fuse_occupancy(bool fwd, bool packed, int *blocks_per_sm);
 
-// Packed three fragments (pack_kernels.cu): the thesis's storage of 8 x 8
-// blocks at two levels, to (fwd) and from the block mode's int16 layout
-struct PackWork {
-    uint8_t *ll;         // LL_2 - 128 (int16), H/4 x W/4
-    uint8_t *band[2][3]; // [l - 1][HL, LH, HH] (int16) of levels 1, 2
-    uint8_t *a, *b, *c;  // private (plaintext), first and second public fragment
-    uint64_t brow;       // bytes a block row of b
-    uint32_t nbx, nby;   // blocks across and down
-    uint32_t W;          // matrix width
-    uint32_t cvec;       // c is 4-byte aligned
-    int *err;            // device error word (5: a value outside its width)
-};
-constexpr int kPackWarps = 4;
-cudaError_t launch_pack(bool fwd, const PackWork &w, uint32_t grid, cudaStream_t stream);
-
 // Block mode (block_kernels.cu): every 8 x 8 block transformed on its own.
 // The same descriptors: strips = ceil(W / 256) (32 blocks a warp), iters =
 // block rows, F = levels (<= 3), ll = LL_L - 128 (int16).
 constexpr uint32_t kBlockSide = 8;
-cudaError_t launch_blocks(bool fwd, const FuseWork &w, uint32_t grid, cudaStream_t stream);
-cudaError_t block_occupancy(bool fwd, int *blocks_per_sm);
+// packed: every buffer of the launch stores the packed three fragments
+cudaError_t launch_blocks(bool fwd, bool packed, const FuseWork &w, uint32_t grid, cudaStream_t stream);
+cudaError_t block_occupancy(bool fwd, bool packed, int *blocks_per_sm);
 
 // kernels (tile_kernels.cu)
 constexpr uint32_t kFastTile = 256;   // owned tile side of the row/column-pass body

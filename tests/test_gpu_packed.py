@@ -92,12 +92,34 @@ def test_extremes_round_trip(fr, key):
     assert torch.equal(out, d)
 
 
-def test_batches_refuse_packed_plans(fr, key):
-    plan = _packed_plan(fr, 64)
-    n = 64 * 8
-    d = torch.zeros(n, dtype=torch.uint8, device="cuda")
-    _, pb, ub = plan.sizes(n)
-    p = torch.empty(pb, dtype=torch.uint8, device="cuda")
-    u = torch.empty(ub, dtype=torch.uint8, device="cuda")
-    with pytest.raises(fr.FragError):
-        fr.protect_batch([(plan, 0, n, d, p, u)], key)
+def test_batch_mixes_packed_block_and_whole_matrix(fr, key):
+    """One batch per direction over packed, unpacked block-mode and
+    whole-matrix buffers: every fragment as the oracle's."""
+    specs = [("packed", 64, 64 * 40 - 7), ("packed", 4096, 4096 * 24), ("block", 64, 64 * 16 + 3),
+             ("whole", 256, 256 * 50 + 1), ("packed", 72, 72 * 8)]
+    ents, rents, refs, outs = [], [], [], []
+    for i, (kind, W, n) in enumerate(specs):
+        data = wl.random_bytes(n, seed=100 + i)
+        plan = fr.Plan(W, 2)
+        if kind != "whole":
+            plan.set_block(8)
+        if kind == "packed":
+            plan.set_packed(True)
+            ref = oracle.protect_packed(data, W, KEY, i)
+        else:
+            ref = oracle.protect(data, W, 2, KEY, i, block=8 if kind == "block" else 0)
+        _, pb, ub = plan.sizes(n)
+        d = torch.from_numpy(data).cuda()
+        p = torch.empty(pb, dtype=torch.uint8, device="cuda")
+        u = torch.empty(ub, dtype=torch.uint8, device="cuda")
+        o = torch.empty(n, dtype=torch.uint8, device="cuda")
+        ents.append((plan, i, n, d, p, u))
+        rents.append((plan, i, n, p, u, o))
+        refs.append((data, ref, p, u, o))
+    fr.protect_batch(ents, key)
+    fr.recover_batch(rents, key)
+    fr.sync_status()
+    for data, (p_ref, u_ref), p, u, o in refs:
+        assert np.array_equal(p.cpu().numpy(), p_ref)
+        assert np.array_equal(u.cpu().numpy(), u_ref)
+        assert np.array_equal(o.cpu().numpy(), data)
