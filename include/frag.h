@@ -18,7 +18,9 @@
  *   - Memory: the caller owns every data buffer.  Pointers named d_* are CUDA
  *     DEVICE pointers of the current device; pointers named h_* are HOST
  *     pointers.  The library owns plans, keys, batches and its own small
- *     device tables.
+ *     device tables; the scratch of a call comes stream-ordered from a
+ *     memory pool of the library's on each device, which keeps up to 8 GiB
+ *     of freed scratch for the next calls (so they map no device pages).
  *   - Streams: work is enqueued on the caller's stream (frag_stream, a
  *     cudaStream_t; NULL is the legacy default stream) and the call returns
  *     without waiting, except the h_* entry points, which wait for their own
@@ -207,7 +209,7 @@ frag_status frag_aes128_ctr(frag_key key, uint64_t nonce, const void *d_in, void
                             uint64_t nbytes, frag_stream stream);
 
 /* Host-buffer forms of the two calls: copy the host input into stream-ordered
- * device memory (cudaMallocAsync), run the same kernels, copy the results
+ * device memory (the library's pool), run the same kernels, copy the results
  * back, and return once they are in host memory.  Pinned (cudaHostAlloc) host
  * buffers give full copy bandwidth. */
 frag_status frag_protect_host(frag_plan plan, frag_key key, uint64_t nonce, const void *h_in,

@@ -135,6 +135,7 @@ struct DeviceState {
     bool ready = false;
     uint32_t *tables = nullptr;
     int *err = nullptr;
+    cudaMemPool_t pool = nullptr; // the calls' stream-ordered scratch
     int sms = 0;
     size_t smem_set[2] = {0, 0};
     std::map<size_t, int> occ[2];
@@ -142,6 +143,8 @@ struct DeviceState {
 
 std::mutex g_mu;
 std::vector<DeviceState> g_devices;
+// scratch the pool keeps between calls (one wave of a batch)
+constexpr uint64_t kPoolKeepBytes = 8ull << 30;
 
 frag_status device_state(DeviceState **out, int *dev_out)
 {
@@ -165,12 +168,34 @@ frag_status device_state(DeviceState **out, int *dev_out)
             return cuda_fail(e, "cudaMalloc(error word)");
         if ((e = cudaMemset(d.err, 0, sizeof(int))) != cudaSuccess)
             return cuda_fail(e, "cudaMemset(error word)");
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if ((e = cudaMemPoolCreate(&d.pool, &props)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemPoolCreate");
+        uint64_t keep = kPoolKeepBytes;
+        if ((e = cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemPoolSetAttribute");
         d.ready = true;
     }
     *out = &d;
     if (dev_out)
         *dev_out = dev;
     return FRAG_OK;
+}
+
+// stream-ordered scratch from the library's pool on the current device:
+// freed memory stays pooled up to kPoolKeepBytes, so a call does not map
+// device pages again after the previous one released them
+cudaError_t pool_malloc(void **p, size_t n, cudaStream_t s)
+{
+    DeviceState *d = nullptr;
+    if (device_state(&d, nullptr) != FRAG_OK)
+        return cudaErrorInitializationError;
+    return cudaMallocFromPoolAsync(p, n, d->pool, s);
 }
 
 frag_status key_on_device(frag_key key, int dev, const uint32_t **out)
@@ -829,9 +854,9 @@ frag_status run_packed(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     packed_sizes(b.H, b.W, &sa, &sb, &sc);
     uint8_t *plainA = nullptr; // recover: the deciphered private fragment
     if (!fwd) {
-        cudaError_t e = cudaMallocAsync((void **)&plainA, align256(sa), s);
+        cudaError_t e = pool_malloc((void **)&plainA, align256(sa), s);
         if (e != cudaSuccess)
-            return cuda_fail(e, "cudaMallocAsync(private fragment)");
+            return cuda_fail(e, "pool_malloc(private fragment)");
     }
     fused_split(fwd, b, plan->path);
     frag::FuseWork w;
@@ -886,9 +911,9 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
         const uint64_t sb = scratch_bytes(fwd, b.H, b.W, b.L, b.F1, off);
         uint8_t *mem = nullptr;
         if (sb) {
-            cudaError_t e = cudaMallocAsync((void **)&mem, sb, s);
+            cudaError_t e = pool_malloc((void **)&mem, sb, s);
             if (e != cudaSuccess)
-                return cuda_fail(e, "cudaMallocAsync(level scratch)");
+                return cuda_fail(e, "pool_malloc(level scratch)");
             b.scr[b.L] = mem + off[b.L];
         }
         frag::FuseWork w;
@@ -926,9 +951,9 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     }
     uint8_t *mem = nullptr;
     if (sb + cb) {
-        cudaError_t e = cudaMallocAsync((void **)&mem, sb + cb + 256, s);
+        cudaError_t e = pool_malloc((void **)&mem, sb + cb + 256, s);
         if (e != cudaSuccess)
-            return cuda_fail(e, "cudaMallocAsync(level scratch)");
+            return cuda_fail(e, "pool_malloc(level scratch)");
     }
     for (uint32_t l = scratch_lo(b.F1); l <= scratch_hi(fwd, b.L); ++l)
         b.scr[l] = mem + off[l];
@@ -1414,9 +1439,9 @@ frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, 
     BatchPlan sizing = bp; // the layout does not depend on the scratch base
     fill_batch(sizing, nullptr);
     uint8_t *mem = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&mem, batch_mem_bytes(sizing), s);
+    cudaError_t e = pool_malloc((void **)&mem, batch_mem_bytes(sizing), s);
     if (e != cudaSuccess)
-        return cuda_fail(e, "cudaMallocAsync(batch)");
+        return cuda_fail(e, "pool_malloc(batch)");
     fill_batch(bp, mem);
     st = upload_batch(bp, mem, s, true);
     if (st == FRAG_OK)
@@ -1864,9 +1889,9 @@ frag_status frag_protect_host(frag_plan plan, frag_key key, uint64_t nonce, cons
         return fail(FRAG_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t *mem = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&mem, nbytes + pb + ub + 512, s);
+    cudaError_t e = pool_malloc((void **)&mem, nbytes + pb + ub + 512, s);
     if (e != cudaSuccess)
-        return cuda_fail(e, "cudaMallocAsync");
+        return cuda_fail(e, "pool_malloc(host-form buffers)");
     uint8_t *d_in = mem, *d_priv = mem + ((nbytes + 255) / 256 * 256);
     uint8_t *d_pub = d_priv + ((pb + 255) / 256 * 256);
     e = cudaMemcpyAsync(d_in, h_in, nbytes, cudaMemcpyHostToDevice, s);
@@ -1901,9 +1926,9 @@ frag_status frag_recover_host(frag_plan plan, frag_key key, uint64_t nonce, cons
         return fail(FRAG_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t *mem = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&mem, nbytes + pb + ub + 512, s);
+    cudaError_t e = pool_malloc((void **)&mem, nbytes + pb + ub + 512, s);
     if (e != cudaSuccess)
-        return cuda_fail(e, "cudaMallocAsync");
+        return cuda_fail(e, "pool_malloc(host-form buffers)");
     uint8_t *d_out = mem, *d_priv = mem + ((nbytes + 255) / 256 * 256);
     uint8_t *d_pub = d_priv + ((pb + 255) / 256 * 256);
     e = cudaMemcpyAsync(d_priv, h_private, pb, cudaMemcpyHostToDevice, s);
@@ -2073,9 +2098,9 @@ frag_status frag_check_wait_timeout(uint32_t polls, frag_stream stream)
         return st;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned *ctr = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&ctr, sizeof(unsigned), s);
+    cudaError_t e = pool_malloc((void **)&ctr, sizeof(unsigned), s);
     if (e != cudaSuccess)
-        return cuda_fail(e, "cudaMallocAsync(counter)");
+        return cuda_fail(e, "pool_malloc(counter)");
     if ((e = cudaMemsetAsync(ctr, 0, sizeof(unsigned), s)) != cudaSuccess)
         st = cuda_fail(e, "counter reset");
     else if ((e = frag::launch_stall_probe(ctr, polls, d->err, s)) != cudaSuccess)
