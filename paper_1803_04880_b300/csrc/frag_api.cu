@@ -702,7 +702,13 @@ frag::FuseBuf fuse_buf(bool fwd, const Buf &b, int pass = 1)
 // units of each buffer: one segment height for a launch, chosen so that the
 // units about fill the resident warps once (or from the plan's seg_rows);
 // returns the launch's units
-uint64_t fuse_schedule(frag::FuseBuf *f, size_t nbufs, uint64_t warps, uint32_t plan_rows)
+// a batch's launch: units of at most this many iterations, so that the
+// warps of many buffers of very different heights share the work evenly
+// (10,000 buffers of 4 KiB .. 64 MiB: one unit a strip took 71 ms to
+// protect, units of 32 iterations 60.5 ms, of 16 or 8 iterations 62.5 ms)
+constexpr uint32_t kFuseBatchSegIters = 32;
+
+uint64_t fuse_schedule(frag::FuseBuf *f, size_t nbufs, uint64_t warps, uint32_t plan_rows, bool batch = false)
 {
     uint32_t seg = 0;
     if (plan_rows) {
@@ -711,8 +717,10 @@ uint64_t fuse_schedule(frag::FuseBuf *f, size_t nbufs, uint64_t warps, uint32_t 
         uint64_t work = 0;
         for (size_t i = 0; i < nbufs; ++i)
             work += (uint64_t)f[i].strips * f[i].iters;
-        seg = (uint32_t)std::min<uint64_t>(
-            1u << 20, std::max<uint64_t>(kFuseMinSegIters, (work + warps - 1) / std::max<uint64_t>(1, warps)));
+        uint64_t per = (work + warps - 1) / std::max<uint64_t>(1, warps);
+        if (batch && nbufs > 1) // one buffer's units are all alike
+            per = std::min<uint64_t>(per, kFuseBatchSegIters);
+        seg = (uint32_t)std::min<uint64_t>(1u << 20, std::max<uint64_t>(kFuseMinSegIters, per));
     }
     uint64_t units = 0;
     for (size_t i = 0; i < nbufs; ++i) {
@@ -1186,12 +1194,12 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         wave_units(wv.jobs, wv.first, wv.levels, wv.units);
         wv.fuse_units = fuse_schedule(wv.fbufs.data(), wv.fbufs.size(),
                                       std::max<uint64_t>(1, bp.fuse_slots) * frag::kFuseWarps,
-                                      bp.fuse_rows);
+                                      bp.fuse_rows, true);
         wv.block_units = block_units(wv.bbufs.data(), wv.bbufs.size());
         wv.packed_units = block_units(wv.pbufs.data(), wv.pbufs.size());
         wv.fuse_units2 = fuse_schedule(wv.fbufs2.data(), wv.fbufs2.size(),
                                        std::max<uint64_t>(1, bp.fuse_slots2) * frag::kFuseWarps,
-                                       bp.fuse_rows);
+                                       bp.fuse_rows, true);
     }
     size_t off = align256(bp.scratch);
     for (auto &wv : bp.waves) {
