@@ -1,13 +1,17 @@
 """The oracle: plain single-threaded C statement of the Chapter 5 method
 (LeGall 5/3 integer lifting, Eq. 5.1/5.2; dyadic 2-D decomposition, Sec. 5.1.1;
-AES-128-CTR on the final LL band, Sec. 5.2.1), wrapped with ctypes.
+AES-128-CTR on the final LL band, Sec. 5.2.1), wrapped with ctypes, and the
+keyed SHA-256 / SHA-512 protection of the packed public fragments (Sec. 5.2.1)
+in plain Python on top of it (sha2.py).
 
 TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` are its only users.  The CUDA library never loads
 it, and the two share no code.  Parity unpinned: none (every function is pinned
 by tests/test_oracle_*.py against the thesis's printed matrix A and F(4,4)
 weights, its magnitude bounds, hand-worked examples, closed forms, invariants
-and the FIPS-197 / SP 800-38A vectors).
+and the FIPS-197 / SP 800-38A vectors; SHA-2 by FIPS 180-4's example and
+hashlib, the keyed framing by a hashlib restatement and the scheme's
+properties in tests/test_oracle_sha.py).
 """
 from __future__ import annotations
 
@@ -244,3 +248,69 @@ def recover_packed(a, pub, n: int, width: int, key, nonce: int) -> np.ndarray:
     if st:
         raise RuntimeError("oracle_recover_packed failed: %d" % st)
     return out
+
+
+# -- keyed protection of the public fragments (Sec. 5.2.1) ------------------
+# Per 8 x 8 block (idx = bi * nbx + bj, blocks row-major):
+#   H1 = SHA-256(key || nonce || idx || A record),  B' = B XOR H1 (124 bits)
+#   H2 = SHA-512(key || nonce || idx || B' record), C' = C XOR H2 (480 bits)
+# key: the 16 AES key bytes; nonce and idx: 8 bytes each, big-endian; the A
+# record is its 5 plaintext bytes and the B' record its 124 bits in 16 bytes
+# (the 4 top bits zero).  Digest bit i (bit i % 8 of byte i // 8) masks bit i
+# of the record, records reading bits from the least significant bit of each
+# byte as in the packed storage.  Recover takes H2 from the stored B' first,
+# then H1 from the deciphered A.
+
+_B_BITS = 124
+_C_BITS = 480
+
+
+def _digest_bits(digest: bytes, bits: int) -> int:
+    return int.from_bytes(digest, "little") & ((1 << bits) - 1)
+
+
+def _xor_public(pub: np.ndarray, plain_a: bytes, H: int, width: int, key, nonce: int,
+                protect: bool) -> None:
+    """Protect (B -> B', C -> C') or unprotect the public fragment in place."""
+    from . import sha2
+    k = bytes(_key(key))
+    nbx, nby = width // 8, H // 8
+    brow = (_B_BITS * nbx + 7) // 8
+    sb = nby * brow
+    mask_b = (1 << _B_BITS) - 1
+    for bi in range(nby):
+        row = int.from_bytes(pub[bi * brow:(bi + 1) * brow].tobytes(), "little")
+        for bj in range(nbx):
+            idx = bi * nbx + bj
+            prefix = k + int(nonce).to_bytes(8, "big") + idx.to_bytes(8, "big")
+            h1 = _digest_bits(sha2.sha256(prefix + plain_a[5 * idx:5 * idx + 5]), _B_BITS)
+            b_stored = (row >> (_B_BITS * bj)) & mask_b
+            b_prot = b_stored ^ h1 if protect else b_stored
+            h2 = _digest_bits(sha2.sha512(prefix + b_prot.to_bytes(16, "little")), _C_BITS)
+            off = sb + 60 * idx
+            c = int.from_bytes(pub[off:off + 60].tobytes(), "little") ^ h2
+            pub[off:off + 60] = np.frombuffer(c.to_bytes(60, "little"), dtype=np.uint8)
+            row ^= h1 << (_B_BITS * bj)
+        pub[bi * brow:(bi + 1) * brow] = np.frombuffer(row.to_bytes(brow, "little"), dtype=np.uint8)
+
+
+def protect_keyed(data, width: int, key, nonce: int):
+    """The packed three fragments with the public ones protected by the
+    keyed hashes: (A enciphered, B' || C')."""
+    n = np.asarray(data).size
+    H, _, _, _ = packed_sizes(n, width)
+    a, pub = protect_packed(data, width, key, nonce)
+    if n:
+        _xor_public(pub, aes128_ctr_xor(key, nonce, 0, a), H, width, key, nonce, True)
+    return a, pub
+
+
+def recover_keyed(a, pub, n: int, width: int, key, nonce: int) -> np.ndarray:
+    H, sa, sb, sc = packed_sizes(n, width)
+    a = np.ascontiguousarray(a, dtype=np.uint8).reshape(-1)
+    pub = np.array(pub, dtype=np.uint8).reshape(-1)
+    if a.size != sa or pub.size != sb + sc:
+        raise ValueError("fragment sizes do not match")
+    if n:
+        _xor_public(pub, aes128_ctr_xor(key, nonce, 0, a), H, width, key, nonce, False)
+    return recover_packed(a, pub, n, width, key, nonce)
