@@ -44,7 +44,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2",
-                    choices=["c2", "c2blocks", "c2packed", "c3l2", "c3l4", "c4", "c5", "aesfull"])
+                    choices=["c2", "c2blocks", "c2packed", "c2keyed", "c3l2", "c3l4", "c4", "c5", "aesfull"])
     ap.add_argument("--items", type=int, default=10000, help="c4: number of buffers")
     ap.add_argument("--requests", type=int, default=240, help="c5: requests per load level")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -85,6 +85,16 @@ def _workload(name):
                              "packed three fragments (40 / 124 / 480 bits a block), private "
                              "AES-128-CTR", "planes": 3, "width": 4096, "levels": 2, "block": 8,
                  "packed": True},
+                [(4096, 2, i, planes[i].reshape(-1)) for i in range(planes.shape[0])])
+    if name == "c2keyed":
+        # the packed fragments with the public ones protected by the keyed
+        # hashes (Sec. 5.2.1: SHA-256 of the private fragment, SHA-512 of the
+        # first protected fragment, each with the key, once per block)
+        planes = wl.c2()
+        return ({"workload": "bitmap 3x4096x4096 u8 in 8x8 blocks, 5/3 DWT 2 levels per block, "
+                             "packed three fragments, private AES-128-CTR, public protected by "
+                             "keyed SHA-256 / SHA-512 per block", "planes": 3, "width": 4096,
+                 "levels": 2, "block": 8, "packed": True, "keyed": True},
                 [(4096, 2, i, planes[i].reshape(-1)) for i in range(planes.shape[0])])
     L = 2 if name == "c3l2" else 4
     return ({"workload": "256 MiB mixed buffer (uniform|text|int32 walk), width 8192, "
@@ -159,13 +169,19 @@ def run_reference(args, rank):
         return _reference_aes(args)
     desc, items = _workload(args.workload)
     W, L, nonce, data = items[0]
-    # a bounded sample per step: the first 1/4 of item 0 (whole rows)
+    # a bounded sample per step: the first 1/4 of item 0 (whole rows); the
+    # keyed hashes run in plain Python, so 64 rows of it there
     n = min(data.size, max(W * (1 << L), (data.size // 4) // (W << L) * (W << L)))
+    if desc.get("keyed"):
+        n = min(n, 64 * W)
     sample = data[:n]
     times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        if desc.get("packed"):
+        if desc.get("keyed"):
+            p, u = oracle.protect_keyed(sample, W, wl.KEY, nonce)
+            oracle.recover_keyed(p, u, n, W, wl.KEY, nonce)
+        elif desc.get("packed"):
             p, u = oracle.protect_packed(sample, W, wl.KEY, nonce)
             oracle.recover_packed(p, u, n, W, wl.KEY, nonce)
         else:
@@ -190,6 +206,14 @@ def run_reference(args, rank):
 
 
 # -- our arm ---------------------------------------------------------------------------
+
+# the keyed hashes of one 8 x 8 block as the fewest 32-bit integer
+# instructions (3-input add and logic, funnel-shift rotates; a 64-bit add or
+# logic op as two): SHA-256 64 x 14 per round + 48 x 10 per schedule word + 8,
+# SHA-512 80 x 28 + 64 x 20 + 16
+SHA_INST_PER_BLOCK = (64 * 14 + 48 * 10 + 8) + (80 * 28 + 64 * 20 + 16)
+# 32-bit integer add, logic and shift instructions an SM issues a clock
+ALU_LANES_PER_SM_CLOCK = 64
 
 # the files that define the dominant kernel (the fused-level kernel)
 KERNEL_SOURCES = ("fused_kernels.cu", "swar.cuh", "frag_internal.cuh")
@@ -216,14 +240,19 @@ def _traffic(workload, kernel):
     return None
 
 
-def _cpu_baseline(items, block=0, packed=False):
+def _cpu_baseline(items, block=0, packed=False, keyed=False):
     import oracle
     from paper_1803_04880_b300 import workloads as wl
     W, L, nonce, data = items[0]
+    if keyed:  # the keyed hashes run in plain Python: the first 64 rows
+        data = data[:64 * W]
     n = data.size
     reps, t0 = 0, time.perf_counter()
     while True:
-        if packed:
+        if keyed:
+            p, u = oracle.protect_keyed(data, W, wl.KEY, nonce)
+            oracle.recover_keyed(p, u, n, W, wl.KEY, nonce)
+        elif packed:
             p, u = oracle.protect_packed(data, W, wl.KEY, nonce)
             oracle.recover_packed(p, u, n, W, wl.KEY, nonce)
         else:
@@ -234,8 +263,8 @@ def _cpu_baseline(items, block=0, packed=False):
         if el >= 10.0 or reps >= 20:
             break
     return {"value": round(n * reps / el / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "item 0 of the workload (%d bytes), protect+recover x%d, one thread"
-                      % (n, reps)}
+            "sample": "%s of item 0 of the workload (%d bytes), protect+recover x%d, one thread"
+                      % ("the first 64 rows" if keyed else "all", n, reps)}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -258,6 +287,8 @@ def run_ours(args, rank, world, local_rank):
             plans[(W, L)].set_block(desc.get("block", 0))
             if desc.get("packed"):
                 plans[(W, L)].set_packed(True)
+            if desc.get("keyed"):
+                plans[(W, L)].set_protect_public(True)
         plan = plans[(W, L)]
         n = data.size
         _, pb, ub = plan.sizes(n)
@@ -393,6 +424,9 @@ def run_ours(args, rank, world, local_rank):
              "cipher": "ctr_kernel (%s%s: AES-128-CTR over the private fragments)"}
     if desc.get("packed"):
         names["blocks"] = "block_kernel<%s, packed=true> (%s: every 8 x 8 block, its bit records, one launch)"
+    if desc.get("keyed"):
+        names["blocks"] = ("block_kernel<%s, packed=true, keyed=true> (%s: every 8 x 8 block, its bit "
+                           "records, SHA-256 + SHA-512 of each, one launch)")
     if dom_kind == "cipher":
         label = names["cipher"] % (dom_dir, "")
     else:
@@ -403,6 +437,25 @@ def run_ours(args, rank, world, local_rank):
                 "kernel_ms_per_launch": round(t_dom, 5),
                 "launch_ms": {"%s/%s" % k: round(v, 5) for k, v in per_launch.items()},
                 "algorithmic_bytes_per_launch": alg_bytes}
+    if desc.get("keyed") and dom_kind == "blocks":
+        # bound by the integer pipe: the two compressions of every block
+        blocks = n_total // 64
+        sm_mhz = (clocks or {}).get("sm_mhz") or 2032.0
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        inst_peak = sms * ALU_LANES_PER_SM_CLOCK * sm_mhz * 1e6
+        inst = SHA_INST_PER_BLOCK * blocks / (t_dom / 1e3)
+        roofline = {"bound": "alu", "achieved": round(inst / 1e9, 1), "peak": round(inst_peak / 1e9, 1),
+                    "unit": "G instructions/s", "frac": round(inst / inst_peak, 4), "traffic": None,
+                    "kernel": label,
+                    "peak_kind": "integer pipe: %d SMs x %d lanes a clock x %.0f MHz (median SM clock "
+                                 "of the timed region)" % (sms, ALU_LANES_PER_SM_CLOCK, sm_mhz),
+                    "algorithmic_instructions_per_launch": SHA_INST_PER_BLOCK * blocks,
+                    "instructions_per_block": SHA_INST_PER_BLOCK,
+                    "kernel_ms_per_launch": round(t_dom, 5),
+                    "launch_ms": {"%s/%s" % k: round(v, 5) for k, v in per_launch.items()},
+                    "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                            "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                            "algorithmic_bytes_per_launch": alg_bytes}}
 
     # e2e through the host-buffer C-ABI calls, pinned host memory
     e2e = None
@@ -432,7 +485,7 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = _cpu_baseline(items, desc.get("block", 0), bool(desc.get("packed")))
+        cpu = _cpu_baseline(items, desc.get("block", 0), bool(desc.get("packed")), bool(desc.get("keyed")))
 
     if rank == 0:
         q = sorted(steps_ms)

@@ -175,6 +175,25 @@ frag_status frag_plan_get_packed(frag_plan plan, uint32_t *packed);
  * sizes is NULL. */
 frag_status frag_plan_fragment_sizes(frag_plan plan, uint64_t nbytes, uint64_t sizes[3]);
 
+/* Keyed protection of the public fragments (Sec. 5.2.1: the private fragment
+ * of a block and the key give, through SHA-256, the bit sequence XORed into
+ * the first public and protected fragment; that protected fragment and the
+ * key give, through SHA-512, the one XORed into the second).  On a packed
+ * plan, on != 0 makes protect write, per 8 x 8 block idx = bi * (W / 8) + bj,
+ *   B' = B XOR the first 124 bits of SHA-256(K || N || I || A record)
+ *   C' = C XOR the first 480 bits of SHA-512(K || N || I || B' record)
+ * with K the 16 AES key bytes, N the call's nonce and I = idx as 8 bytes
+ * big-endian, the A record its 5 plaintext bytes and the B' record its 124
+ * bits in 16 bytes (4 zero bits at the top); digest bit i (bit i % 8 of byte
+ * i / 8) masks record bit i.  Recover takes SHA-512 of the stored B' first,
+ * then SHA-256 of the deciphered A.  Sizes and the private fragment are
+ * those of the packed plan.  The hashes run in the block kernel, on the
+ * records in registers.  FRAG_EUNSUPPORTED unless the plan is packed;
+ * frag_plan_set_packed(plan, 0) on a keyed plan is FRAG_EINVAL; FRAG_EINVAL
+ * if on is NULL (get). */
+frag_status frag_plan_set_protect_public(frag_plan plan, uint32_t on);
+frag_status frag_plan_get_protect_public(frag_plan plan, uint32_t *on);
+
 /* AES-128 key (Sec. 5.2.1 protects the private fragment with AES-128): the
  * round keys are expanded on the host (FIPS-197 Sec. 5.2) and kept resident on
  * each device that uses the key.  The 16 bytes are copied. */

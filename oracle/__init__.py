@@ -314,3 +314,20 @@ def recover_keyed(a, pub, n: int, width: int, key, nonce: int) -> np.ndarray:
     if n:
         _xor_public(pub, aes128_ctr_xor(key, nonce, 0, a), H, width, key, nonce, False)
     return recover_packed(a, pub, n, width, key, nonce)
+
+
+def keyed_block_records(block, key, nonce: int, idx: int):
+    """One 8 x 8 block's records as block idx of a keyed buffer: (A plaintext
+    5 bytes, B' as a 124-bit int, C' as a 480-bit int).  Blocks are
+    transformed on their own, so any block of a large buffer can be checked
+    from its 64 bytes alone."""
+    from . import sha2
+    blk = np.ascontiguousarray(block, dtype=np.uint8).reshape(8, 8)
+    a, pub = protect_packed(blk.reshape(-1), 8, key, nonce)
+    a_plain = aes128_ctr_xor(key, nonce, 0, a)
+    b = int.from_bytes(pub[:16].tobytes(), "little") & ((1 << _B_BITS) - 1)
+    c = int.from_bytes(pub[16:76].tobytes(), "little")
+    prefix = bytes(_key(key)) + int(nonce).to_bytes(8, "big") + int(idx).to_bytes(8, "big")
+    b ^= _digest_bits(sha2.sha256(prefix + a_plain), _B_BITS)
+    c ^= _digest_bits(sha2.sha512(prefix + b.to_bytes(16, "little")), _C_BITS)
+    return a_plain, b, c

@@ -26,7 +26,7 @@ EXPORTS = [
     "frag_plan_set_tiling", "frag_plan_get_tiling", "frag_plan_set_schedule",
     "frag_plan_get_schedule", "frag_plan_set_path", "frag_plan_get_path",
     "frag_plan_set_block", "frag_plan_get_block", "frag_plan_set_packed", "frag_plan_get_packed",
-    "frag_plan_fragment_sizes",
+    "frag_plan_fragment_sizes", "frag_plan_set_protect_public", "frag_plan_get_protect_public",
     "frag_key_create", "frag_key_destroy",
     "frag_protect", "frag_recover", "frag_aes128_ctr", "frag_protect_host", "frag_recover_host",
     "frag_protect_batch", "frag_recover_batch", "frag_batch_create_protect",
@@ -90,6 +90,8 @@ def lib():
         "frag_plan_set_packed": ([vp, u32], ctypes.c_int),
         "frag_plan_get_packed": ([vp, ctypes.POINTER(u32)], ctypes.c_int),
         "frag_plan_fragment_sizes": ([vp, u64, ctypes.POINTER(u64)], ctypes.c_int),
+        "frag_plan_set_protect_public": ([vp, u32], ctypes.c_int),
+        "frag_plan_get_protect_public": ([vp, ctypes.POINTER(u32)], ctypes.c_int),
         "frag_plan_get_path": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "frag_key_create": ([ctypes.POINTER(vp), ctypes.c_char_p], ctypes.c_int),
         "frag_key_destroy": ([vp], ctypes.c_int),
@@ -206,6 +208,16 @@ class Plan:
     def packed(self) -> bool:
         v = ctypes.c_uint32()
         check(lib().frag_plan_get_packed(self._h, ctypes.byref(v)))
+        return bool(v.value)
+
+    def set_protect_public(self, on: bool) -> None:
+        """Packed plans: protect B and C with the keyed SHA-256 / SHA-512
+        bit sequences of each block (Sec. 5.2.1)."""
+        check(lib().frag_plan_set_protect_public(self._h, 1 if on else 0))
+
+    def protect_public(self) -> bool:
+        v = ctypes.c_uint32()
+        check(lib().frag_plan_get_protect_public(self._h, ctypes.byref(v)))
         return bool(v.value)
 
     def fragment_sizes(self, nbytes: int) -> Tuple[int, int, int]:

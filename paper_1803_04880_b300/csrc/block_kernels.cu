@@ -17,8 +17,11 @@
 // packed buffer (two levels) instead gets the thesis's bit records of its
 // three fragments straight from the registers (pack_bits.cuh): the lane
 // writes its block's A and C records, the warp its 32 blocks' B records.
+// A keyed buffer's B and C records are protected in the registers on the
+// way out (and unprotected on the way in) with the keyed hashes of sha2.cuh.
 #include "frag_internal.cuh"
 #include "pack_bits.cuh"
+#include "sha2.cuh"
 #include "swar.cuh"
 
 namespace frag {
@@ -379,9 +382,10 @@ __device__ __forceinline__ void block_rows(const FuseBuf &f, uint64_t bi, uint32
     }
 }
 
-template <bool PACKED>
+template <bool PACKED, bool KEYED>
 __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged,
-                                          const uint2 (&v)[8], uint32_t (&rb)[4], int *err)
+                                          const uint2 (&v)[8], uint32_t (&rb)[4], int *err,
+                                          const uint32_t (&key)[4])
 {
     const uint32_t W = f.W, L = f.F;
     uint32_t x1[8][4]; // row-lifted rows, 4 words each
@@ -441,6 +445,10 @@ __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_
         if (!ok)
             atomicCAS(err, 0, pkb::kErrWidth);
         const uint64_t idx = bi * (uint64_t)(W >> 3) + bj;
+        if (KEYED && f.keyed) { // B' = B ^ H1(A), then C' = C ^ H2(B')
+            sha::mask_b(key, f.nonce, idx, ra, rb);
+            sha::mask_c(key, f.nonce, idx, rb, rc);
+        }
         uint8_t *pa = f.pk[0] + 5 * idx;
         pa[0] = (uint8_t)ra[0];
         pa[1] = (uint8_t)(ra[0] >> 8);
@@ -490,9 +498,10 @@ __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_
     st_tile(tile_row(f.ll, W3, 1, bi, bj, 0), 1, ll_final(s3[0][0]), 0, vec);
 }
 
-template <bool PACKED>
+template <bool PACKED, bool KEYED>
 __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged,
-                                          bool vec, uint32_t s8, uint32_t s4, const uint32_t (&rb)[4])
+                                          bool vec, uint32_t s8, uint32_t s4, const uint32_t (&rb_in)[4],
+                                          const uint32_t (&key)[4])
 {
     const uint32_t W = f.W, L = f.F;
     const uint32_t W1 = W >> 1, W2 = W >> 2, W3 = W >> 3;
@@ -515,6 +524,11 @@ __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_
             for (int i = 0; i < 15; ++i)
                 rc[i] = (uint32_t)pc[4 * i] | ((uint32_t)pc[4 * i + 1] << 8) | ((uint32_t)pc[4 * i + 2] << 16) |
                         ((uint32_t)pc[4 * i + 3] << 24);
+        }
+        uint32_t rb[4] = {rb_in[0], rb_in[1], rb_in[2], rb_in[3]};
+        if (KEYED && f.keyed) { // C = C' ^ H2(B') first, then B = B' ^ H1(A)
+            sha::mask_c(key, f.nonce, idx, rb, rc);
+            sha::mask_b(key, f.nonce, idx, ra, rb);
         }
         uint32_t s2[2][2], d2[2][2];
 #pragma unroll
@@ -648,9 +662,15 @@ __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_
 // PACKED: every buffer of the launch is packed (the warp stores or loads its
 // blocks' B records between blocks, which the staged loop below does not
 // allow for); the inverse, and any packed launch, take direct loads
-template <bool FWD, bool PACKED>
+template <bool FWD, bool PACKED, bool KEYED>
 __global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
 {
+    uint32_t key[4] = {0u, 0u, 0u, 0u}; // the AES key's words, big-endian (keyed buffers)
+    if (KEYED) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            key[i] = __ldg(w.key_words + i);
+    }
     if (!FWD || PACKED) {
         __shared__ uint32_t sb[kWarps][pkb::kPackBWords]; // a warp's B records
         grid_release();
@@ -682,9 +702,9 @@ __global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
                 if (nx.on)
                     block_rows(*nx.b, nx.bi, nx.bj, false, nx.vec, 0, rows);
                 if (sl.on)
-                    fwd_block<PACKED>(*sl.b, sl.bi, sl.bj, false, v, rb, w.err);
+                    fwd_block<PACKED, KEYED>(*sl.b, sl.bi, sl.bj, false, v, rb, w.err, key);
             } else if (sl.on) {
-                inv_block<PACKED>(*sl.b, sl.bi, sl.bj, false, sl.vec, 0, 0, rb);
+                inv_block<PACKED, KEYED>(*sl.b, sl.bi, sl.bj, false, sl.vec, 0, 0, rb, key);
             }
             if (PACKED && FWD)
                 pkb::store_b(sb[warp], bbase, bcount, sl.on, lane, rb);
@@ -725,9 +745,10 @@ __global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
             if (FWD) {
                 uint2 v[8];
                 block_rows(*cur.b, cur.bi, cur.bj, cur.vec, false, ring8 + cur_off, v);
-                fwd_block<false>(*cur.b, cur.bi, cur.bj, cur.vec, v, rb, w.err);
+                fwd_block<false, false>(*cur.b, cur.bi, cur.bj, cur.vec, v, rb, w.err, key);
             } else
-                inv_block<false>(*cur.b, cur.bi, cur.bj, cur.vec, cur.vec, ring8 + cur_off, ring4 + cur_off, rb);
+                inv_block<false, false>(*cur.b, cur.bi, cur.bj, cur.vec, cur.vec, ring8 + cur_off, ring4 + cur_off,
+                                        rb, key);
         }
     };
     for (uint64_t i = 0; u0 + i * G < w.total_units; i += 3) {
@@ -744,47 +765,62 @@ __global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
 
 size_t smem_bytes(bool fwd, bool packed) { return fwd && !packed ? (size_t)kWarps * kDepth * kFwdStage : 0; }
 
-template <bool FWD, bool PACKED>
+template <bool FWD, bool PACKED, bool KEYED>
 cudaError_t set_attr()
 {
-    return cudaFuncSetAttribute((const void *)block_kernel<FWD, PACKED>,
+    return cudaFuncSetAttribute((const void *)block_kernel<FWD, PACKED, KEYED>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(FWD, PACKED));
 }
 
-template <bool FWD, bool PACKED>
+template <bool FWD, bool PACKED, bool KEYED>
 cudaError_t launch(const FuseWork &w, uint32_t grid, cudaStream_t stream)
 {
-    cudaError_t e = set_attr<FWD, PACKED>();
+    cudaError_t e = set_attr<FWD, PACKED, KEYED>();
     if (e != cudaSuccess)
         return e;
-    block_kernel<FWD, PACKED><<<grid, kThreads, smem_bytes(FWD, PACKED), stream>>>(w);
+    block_kernel<FWD, PACKED, KEYED><<<grid, kThreads, smem_bytes(FWD, PACKED), stream>>>(w);
     return cudaGetLastError();
 }
 
-template <bool FWD, bool PACKED>
+template <bool FWD, bool PACKED, bool KEYED>
 cudaError_t occupancy(int *blocks_per_sm)
 {
-    cudaError_t e = set_attr<FWD, PACKED>();
+    cudaError_t e = set_attr<FWD, PACKED, KEYED>();
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void *)block_kernel<FWD, PACKED>,
-                                                         kThreads, smem_bytes(FWD, PACKED));
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, (const void *)block_kernel<FWD, PACKED, KEYED>, kThreads, smem_bytes(FWD, PACKED));
+}
+
+template <bool FWD>
+cudaError_t launch_dir(bool packed, bool keyed, const FuseWork &w, uint32_t grid, cudaStream_t stream)
+{
+    if (!packed)
+        return launch<FWD, false, false>(w, grid, stream);
+    return keyed ? launch<FWD, true, true>(w, grid, stream) : launch<FWD, true, false>(w, grid, stream);
+}
+
+template <bool FWD>
+cudaError_t occupancy_dir(bool packed, bool keyed, int *blocks_per_sm)
+{
+    if (!packed)
+        return occupancy<FWD, false, false>(blocks_per_sm);
+    return keyed ? occupancy<FWD, true, true>(blocks_per_sm) : occupancy<FWD, true, false>(blocks_per_sm);
 }
 
 } // namespace blk
 
-cudaError_t launch_blocks(bool fwd, bool packed, const FuseWork &w, uint32_t grid, cudaStream_t stream)
+cudaError_t launch_blocks(bool fwd, bool packed, bool keyed, const FuseWork &w, uint32_t grid,
+                          cudaStream_t stream)
 {
-    if (fwd)
-        return packed ? blk::launch<true, true>(w, grid, stream) : blk::launch<true, false>(w, grid, stream);
-    return packed ? blk::launch<false, true>(w, grid, stream) : blk::launch<false, false>(w, grid, stream);
+    return fwd ? blk::launch_dir<true>(packed, keyed, w, grid, stream)
+               : blk::launch_dir<false>(packed, keyed, w, grid, stream);
 }
 
-cudaError_t block_occupancy(bool fwd, bool packed, int *blocks_per_sm)
+cudaError_t block_occupancy(bool fwd, bool packed, bool keyed, int *blocks_per_sm)
 {
-    if (fwd)
-        return packed ? blk::occupancy<true, true>(blocks_per_sm) : blk::occupancy<true, false>(blocks_per_sm);
-    return packed ? blk::occupancy<false, true>(blocks_per_sm) : blk::occupancy<false, false>(blocks_per_sm);
+    return fwd ? blk::occupancy_dir<true>(packed, keyed, blocks_per_sm)
+               : blk::occupancy_dir<false>(packed, keyed, blocks_per_sm);
 }
 
 } // namespace frag

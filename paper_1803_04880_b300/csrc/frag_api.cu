@@ -31,6 +31,7 @@ struct frag_plan_s {
     uint32_t path;        // frag_path: which kernels run the levels
     uint32_t block;       // block mode: side of the blocks (0: whole matrix)
     uint32_t packed;      // the thesis's packed three fragments (8 x 8 blocks, two levels)
+    uint32_t keyed;       // packed: the public fragments protected by the keyed hashes
 };
 
 struct frag_key_s {
@@ -354,6 +355,7 @@ struct Buf {
     uint32_t F1, F2;   // levels of the first pass (bytes) and the second (packed LL_3)
     uint32_t block;    // block mode (every level in the block kernel)
     uint32_t packed;   // block mode with the packed three fragments
+    uint32_t keyed;    // packed: B and C protected by the keyed hashes
     uint32_t R0;       // level-0 rows per work segment
     uint32_t R0_plan;  // the plan's choice (0: adaptive)
     uint64_t n, nonce;
@@ -799,6 +801,8 @@ frag::FuseBuf packed_buf(bool fwd, const Buf &b)
     uint64_t sa, sb, sc;
     packed_sizes(b.H, b.W, &sa, &sb, &sc);
     f.packed = 1;
+    f.keyed = b.keyed;
+    f.nonce = b.nonce;
     f.pk[0] = fwd ? b.priv : b.scr[b.L];
     f.pk[1] = fwd ? b.pub : const_cast<uint8_t *>(b.pub_in);
     f.pk[2] = f.pk[1] + sb;
@@ -815,12 +819,14 @@ uint64_t block_units(frag::FuseBuf *f, size_t nbufs)
     return units;
 }
 
-frag_status block_launch(DeviceState &d, bool fwd, frag::FuseWork &w, cudaStream_t s, bool packed = false)
+// keyed: some packed buffer is keyed; rk (device) holds the key's words
+frag_status block_launch(DeviceState &d, bool fwd, frag::FuseWork &w, cudaStream_t s, bool packed = false,
+                         bool keyed = false, const uint32_t *rk = nullptr)
 {
     if (w.total_units == 0)
         return FRAG_OK;
     int occ = 0;
-    const size_t tag = packed ? 6667 : 6666;
+    const size_t tag = packed ? (keyed ? 6668 : 6667) : 6666;
     {
         std::lock_guard<std::mutex> lock(g_mu);
         auto it = d.occ[fwd].find(tag);
@@ -828,7 +834,7 @@ frag_status block_launch(DeviceState &d, bool fwd, frag::FuseWork &w, cudaStream
             occ = it->second;
     }
     if (occ == 0) {
-        cudaError_t e = frag::block_occupancy(fwd, packed, &occ);
+        cudaError_t e = frag::block_occupancy(fwd, packed, keyed, &occ);
         if (e != cudaSuccess)
             return cuda_fail(e, "occupancy query");
         occ = std::max(occ, 1);
@@ -836,9 +842,10 @@ frag_status block_launch(DeviceState &d, bool fwd, frag::FuseWork &w, cudaStream
         d.occ[fwd][tag] = occ;
     }
     w.err = d.err;
+    w.key_words = rk;
     const uint64_t need = (w.total_units + 3) / 4; // 4 warps a CTA
     const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)d.sms * occ, need));
-    cudaError_t e = frag::launch_blocks(fwd, packed, w, grid, s);
+    cudaError_t e = frag::launch_blocks(fwd, packed, keyed && rk != nullptr, w, grid, s);
     if (e != cudaSuccess)
         return cuda_fail(e, fwd ? "block protect launch" : "block recover launch");
     return FRAG_OK;
@@ -871,6 +878,8 @@ frag_status run_packed(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     std::memset(&w, 0, sizeof(w));
     w.single = block_buf(fwd, b);
     w.single.packed = 1;
+    w.single.keyed = b.keyed;
+    w.single.nonce = b.nonce;
     w.single.pk[0] = fwd ? b.priv : plainA;
     w.single.pk[1] = fwd ? b.pub : const_cast<uint8_t *>(b.pub_in);
     w.single.pk[2] = w.single.pk[1] + sb;
@@ -884,13 +893,13 @@ frag_status run_packed(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     c.bytes = sa;
     c.nblocks = (sa + 15) / 16;
     if (fwd) {
-        st = block_launch(*d, true, w, s, true);
+        st = block_launch(*d, true, w, s, true, b.keyed != 0, rk);
         if (st == FRAG_OK)
             st = ctr_launch(*d, rk, nullptr, 0, &c, s);
     } else {
         st = ctr_launch(*d, rk, nullptr, 0, &c, s);
         if (st == FRAG_OK)
-            st = block_launch(*d, false, w, s, true);
+            st = block_launch(*d, false, w, s, true, b.keyed != 0, rk);
         cudaFreeAsync(plainA, s);
     }
     return st;
@@ -1085,6 +1094,7 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
         b.R0_plan = plan->seg_rows;
         b.block = plan->block;
         b.packed = plan->packed;
+        b.keyed = plan->keyed;
         if (bp.bufs.empty() && v.empty()) {
             bp.max_ctas = plan->max_ctas; // the grid of a launch: the first item's plan
             bp.fuse_rows = plan->seg_rows;
@@ -1313,7 +1323,7 @@ frag_status launch_wave_fused(const BatchPlan &bp, const DagWave &wv, uint8_t *m
 
 // the block launch of a wave (its buffers' descriptors at bbufs_off)
 frag_status launch_wave_blocks(const BatchPlan &bp, const DagWave &wv, uint8_t *mem, DeviceState &d,
-                               cudaStream_t s, LaunchTimer &tm, bool packed = false)
+                               cudaStream_t s, LaunchTimer &tm, bool packed = false, const uint32_t *rk = nullptr)
 {
     const std::vector<frag::FuseBuf> &bufs = packed ? wv.pbufs : wv.bbufs;
     if (bufs.empty())
@@ -1326,7 +1336,10 @@ frag_status launch_wave_blocks(const BatchPlan &bp, const DagWave &wv, uint8_t *
         w.single = bufs[0];
     w.total_units = packed ? wv.packed_units : wv.block_units;
     tm.begin();
-    frag_status st = block_launch(d, bp.fwd, w, s, packed);
+    bool keyed = false;
+    for (const auto &f : bufs)
+        keyed = keyed || f.keyed;
+    frag_status st = block_launch(d, bp.fwd, w, s, packed, keyed, rk);
     tm.end(FRAG_KERNEL_BLOCKS);
     return st;
 }
@@ -1347,7 +1360,7 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
             return st;
         if (bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm)) != FRAG_OK)
             return st;
-        if (bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm, true)) != FRAG_OK)
+        if (bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm, true, rk)) != FRAG_OK)
             return st;
         if (!bp.fwd && !wv.chunks.empty()) { // decipher before the transform reads LL_L
             tm.begin();
@@ -1392,7 +1405,7 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
         }
         if (!bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm)) != FRAG_OK)
             return st;
-        if (!bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm, true)) != FRAG_OK)
+        if (!bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm, true, rk)) != FRAG_OK)
             return st;
         if (!bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm, 2)) != FRAG_OK)
             return st;
@@ -1711,7 +1724,32 @@ frag_status frag_plan_set_packed(frag_plan plan, uint32_t packed)
     if (packed && (plan->block != frag::kBlockSide || plan->levels != 2))
         return fail(FRAG_EUNSUPPORTED, "packed fragments are the thesis's storage of 8 x 8 blocks at two "
                                        "levels (frag_plan_set_block(plan, 8) on a 2-level plan first)");
+    if (!packed && plan->keyed)
+        return fail(FRAG_EINVAL, "the plan protects its public fragments: clear that first");
     plan->packed = packed ? 1u : 0u;
+    return FRAG_OK;
+}
+
+frag_status frag_plan_set_protect_public(frag_plan plan, uint32_t on)
+{
+    frag_status st = check_plan(plan);
+    if (st != FRAG_OK)
+        return st;
+    if (on && !plan->packed)
+        return fail(FRAG_EUNSUPPORTED, "the keyed protection of the public fragments works on the packed "
+                                       "fragments (frag_plan_set_packed(plan, 1) first)");
+    plan->keyed = on ? 1u : 0u;
+    return FRAG_OK;
+}
+
+frag_status frag_plan_get_protect_public(frag_plan plan, uint32_t *on)
+{
+    frag_status st = check_plan(plan);
+    if (st != FRAG_OK)
+        return st;
+    if (on == nullptr)
+        return fail(FRAG_EINVAL, "on is NULL");
+    *on = plan->keyed;
     return FRAG_OK;
 }
 
@@ -1818,6 +1856,7 @@ frag_status frag_protect(frag_plan plan, frag_key key, uint64_t nonce, const voi
     b.L = plan->levels;
     b.block = plan->block;
     b.packed = plan->packed;
+    b.keyed = plan->keyed;
     b.H = (uint32_t)H;
     b.n = nbytes;
     b.nonce = nonce;
@@ -1876,6 +1915,7 @@ frag_status frag_recover(frag_plan plan, frag_key key, uint64_t nonce, const voi
     b.L = plan->levels;
     b.block = plan->block;
     b.packed = plan->packed;
+    b.keyed = plan->keyed;
     b.H = (uint32_t)H;
     b.n = nbytes;
     b.nonce = nonce;

@@ -206,7 +206,9 @@ struct __align__(16) FuseBuf {
     uint32_t full_rows;   // leading rows made only of data bytes (n / W)
     uint32_t vec;         // block mode: every access may use its vector width
     uint32_t packed;      // block mode: the packed three fragments pk instead of int16 bands
+    uint32_t keyed;       // packed: B and C protected by the keyed hashes (sha2.cuh)
     uint8_t *pk[3];       // packed: A (private, plaintext), B, C (pack_bits.cuh)
+    uint64_t nonce;       // keyed: the buffer's nonce (hash input)
 };
 static_assert(sizeof(FuseBuf) % 16 == 0, "fused buffer descriptors are copied in 16-byte pieces");
 
@@ -216,6 +218,7 @@ struct FuseWork {
     uint32_t nbufs;
     uint64_t total_units;
     int *err;            // device error word (block mode, packed: 5 = a value outside its width)
+    const uint32_t *key_words; // device: the 4 big-endian AES key words (keyed packed launches)
 };
 
 // packed: the samples are 16-bit values (v + 0x4000) instead of bytes --
@@ -228,9 +231,11 @@ cudaError_t fuse_occupancy(bool fwd, bool packed, int *blocks_per_sm);
 // The same descriptors: strips = ceil(W / 256) (32 blocks a warp), iters =
 // block rows, F = levels (<= 3), ll = LL_L - 128 (int16).
 constexpr uint32_t kBlockSide = 8;
-// packed: every buffer of the launch stores the packed three fragments
-cudaError_t launch_blocks(bool fwd, bool packed, const FuseWork &w, uint32_t grid, cudaStream_t stream);
-cudaError_t block_occupancy(bool fwd, bool packed, int *blocks_per_sm);
+// packed: every buffer of the launch stores the packed three fragments;
+// keyed: some of them are keyed (FuseBuf::keyed), w.key_words is set
+cudaError_t launch_blocks(bool fwd, bool packed, bool keyed, const FuseWork &w, uint32_t grid,
+                          cudaStream_t stream);
+cudaError_t block_occupancy(bool fwd, bool packed, bool keyed, int *blocks_per_sm);
 
 // kernels (tile_kernels.cu)
 constexpr uint32_t kFastTile = 256;   // owned tile side of the row/column-pass body

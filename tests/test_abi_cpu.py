@@ -113,6 +113,31 @@ def test_packed_validation(L):
     assert L.frag_plan_get_packed(q.handle, None) == fr.FRAG_EINVAL
 
 
+def test_protect_public_validation(L):
+    p = fr.Plan(64, 2)
+    assert not p.protect_public()
+    with pytest.raises(fr.FragError):
+        p.set_protect_public(True)  # the keyed hashes work on the packed records
+    p.set_block(8)
+    p.set_packed(True)
+    p.set_protect_public(True)
+    assert p.protect_public()
+    with pytest.raises(fr.FragError):
+        p.set_packed(False)  # clear the keyed protection first
+    assert p.fragment_sizes(64 * 24) == oracle_sizes(64 * 24, 64)  # the packed sizes
+    p.set_protect_public(False)
+    p.set_packed(False)
+    assert not p.protect_public() and not p.packed()
+    assert L.frag_plan_get_protect_public(p.handle, None) == fr.FRAG_EINVAL
+    assert L.frag_plan_set_protect_public(None, 1) == fr.FRAG_EINVAL
+
+
+def oracle_sizes(n, W):
+    import oracle
+    _, a, b, c = oracle.packed_sizes(n, W)
+    return a, b, c
+
+
 def test_block_validation(L):
     p = fr.Plan(64, 2)
     assert p.block() == 0
@@ -137,3 +162,11 @@ def test_path_validation(L):
     assert p.path() == fr.Plan.PATH_LEVELS
     with pytest.raises(fr.FragError):
         p.set_path(7)
+
+
+def test_sha2_constants_header_is_current():
+    """The library's SHA-2 constants header is what its generator derives."""
+    import subprocess
+    import sys
+    gen = os.path.join(os.path.dirname(fr.__file__), "csrc", "gen_sha2_constants.py")
+    assert subprocess.run([sys.executable, gen, "--check"]).returncode == 0

@@ -152,3 +152,18 @@ def test_an_error_stays_in_its_block(which):
         assert b_err == 0 and c_err == 1 << 100
     else:  # the B bit itself, and the block's C through H2
         assert b_err == 1 << 7 and bin(c_err).count("1") > 100
+
+
+def test_block_records_match_the_whole_buffer():
+    """The per-block form (used to sample large buffers) gives every block's
+    records as the whole-buffer protection does."""
+    W = 64
+    x = np.random.default_rng(5).integers(0, 256, W * 24, dtype=np.uint8)
+    a, pub = oracle.protect_keyed(x, W, KEY, 77)
+    plain_a = oracle.aes128_ctr_xor(KEY, 77, 0, a)
+    recs = _records(W, x.size, plain_a, pub)
+    img = x.reshape(-1, W)
+    for idx, want in recs.items():
+        bi, bj = divmod(idx, W // 8)
+        got = oracle.keyed_block_records(img[8 * bi:8 * bi + 8, 8 * bj:8 * bj + 8], KEY, 77, idx)
+        assert got == want
