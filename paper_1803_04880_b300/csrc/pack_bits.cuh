@@ -109,6 +109,7 @@ __device__ __forceinline__ void load_b(uint32_t *sb, const uint8_t *base, uint32
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             rb[i] = sh ? (sb[q + i] >> sh) | (sb[q + i + 1] << (32 - sh)) : sb[q + i];
+        rb[3] &= 0x0fffffffu; // bits 124..127 are the next block's
     }
     __syncwarp();
 }
