@@ -38,71 +38,101 @@ __device__ __forceinline__ uint64_t rotr64(uint64_t x, int n)
 
 __device__ __forceinline__ uint32_t bswap(uint32_t x) { return __byte_perm(x, 0u, 0x0123); }
 
-// digest h of the one padded block m (the schedule is built in m)
+// One round on the working variables (a..h) with schedule word w and
+// constant kt; the caller rotates the names, so 8 calls in a row return to
+// the same assignment.
+#define FRAG_SHA256_ROUND(a, b, c, d, e, f, g, h, kt, w)                                                      \
+    do {                                                                                                      \
+        const uint32_t t1_ = h + (rotr(e, 6) ^ rotr(e, 11) ^ rotr(e, 25)) + ((e & f) ^ (~e & g)) + (kt) + (w);  \
+        d += t1_;                                                                                             \
+        h = t1_ + (rotr(a, 2) ^ rotr(a, 13) ^ rotr(a, 22)) + ((a & b) ^ (a & c) ^ (b & c));                   \
+    } while (0)
+
+#define FRAG_SHA512_ROUND(a, b, c, d, e, f, g, h, kt, w)                                                      \
+    do {                                                                                                      \
+        const uint64_t t1_ =                                                                                  \
+            h + (rotr64(e, 14) ^ rotr64(e, 18) ^ rotr64(e, 41)) + ((e & f) ^ (~e & g)) + (kt) + (w);            \
+        d += t1_;                                                                                             \
+        h = t1_ + (rotr64(a, 28) ^ rotr64(a, 34) ^ rotr64(a, 39)) + ((a & b) ^ (a & c) ^ (b & c));            \
+    } while (0)
+
+__device__ __forceinline__ uint32_t s256_0(uint32_t x) { return rotr(x, 7) ^ rotr(x, 18) ^ (x >> 3); }
+__device__ __forceinline__ uint32_t s256_1(uint32_t x) { return rotr(x, 17) ^ rotr(x, 19) ^ (x >> 10); }
+__device__ __forceinline__ uint64_t s512_0(uint64_t x) { return rotr64(x, 1) ^ rotr64(x, 8) ^ (x >> 7); }
+__device__ __forceinline__ uint64_t s512_1(uint64_t x) { return rotr64(x, 19) ^ rotr64(x, 61) ^ (x >> 6); }
+
+// Eight rounds starting at round t0 + q0 with the names in their home order
+// (a..h at rounds = 0 mod 8), words m[q0..q0+7]
+__device__ __forceinline__ void sha256_8(const uint32_t (&m)[16], uint32_t (&v)[8], int t0, int q0)
+{
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint32_t &a = v[(8 - j) & 7], &b = v[(9 - j) & 7], &c = v[(10 - j) & 7], &d = v[(11 - j) & 7];
+        uint32_t &e = v[(12 - j) & 7], &f = v[(13 - j) & 7], &g = v[(14 - j) & 7], &h = v[(15 - j) & 7];
+        FRAG_SHA256_ROUND(a, b, c, d, e, f, g, h, kSha256K[t0 + q0 + j], m[q0 + j]);
+    }
+}
+
+__device__ __forceinline__ void sha512_8(const uint64_t (&m)[16], uint64_t (&v)[8], int t0, int q0)
+{
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint64_t &a = v[(8 - j) & 7], &b = v[(9 - j) & 7], &c = v[(10 - j) & 7], &d = v[(11 - j) & 7];
+        uint64_t &e = v[(12 - j) & 7], &f = v[(13 - j) & 7], &g = v[(14 - j) & 7], &h = v[(15 - j) & 7];
+        FRAG_SHA512_ROUND(a, b, c, d, e, f, g, h, kSha512K[t0 + q0 + j], m[q0 + j]);
+    }
+}
+
+// the next 16 schedule words in place of the last 16 (word q needs words
+// q - 2 and q - 7 of the new 16 and q - 15, q - 16 of the old)
+template <typename T, T (*S0)(T), T (*S1)(T)>
+__device__ __forceinline__ void schedule16(T (&m)[16])
+{
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        m[q] += S0(m[(q + 1) & 15]) + m[(q + 9) & 15] + S1(m[(q + 14) & 15]);
+}
+
+// digest h of the one padded block m (the schedule is built in m): a loop
+// of 16 rounds, then the next 16 schedule words, so each compression is a
+// few KB of code (unrolled whole, the two compressions outgrow the
+// instruction cache and the warps wait on fetches)
 __device__ __forceinline__ void sha256_block(uint32_t (&m)[16], uint32_t (&h)[8])
 {
-    uint32_t a = kSha256H[0], b = kSha256H[1], c = kSha256H[2], d = kSha256H[3];
-    uint32_t e = kSha256H[4], f = kSha256H[5], g = kSha256H[6], k = kSha256H[7];
+    uint32_t v[8];
 #pragma unroll
-    for (int t = 0; t < 64; ++t) {
-        if (t >= 16) {
-            const uint32_t x = m[(t - 15) & 15], y = m[(t - 2) & 15];
-            m[t & 15] += (rotr(x, 7) ^ rotr(x, 18) ^ (x >> 3)) + m[(t - 7) & 15] +
-                         (rotr(y, 17) ^ rotr(y, 19) ^ (y >> 10));
-        }
-        const uint32_t t1 = k + (rotr(e, 6) ^ rotr(e, 11) ^ rotr(e, 25)) + ((e & f) ^ (~e & g)) + kSha256K[t] +
-                            m[t & 15];
-        const uint32_t t2 = (rotr(a, 2) ^ rotr(a, 13) ^ rotr(a, 22)) + ((a & b) ^ (a & c) ^ (b & c));
-        k = g;
-        g = f;
-        f = e;
-        e = d + t1;
-        d = c;
-        c = b;
-        b = a;
-        a = t1 + t2;
+    for (int i = 0; i < 8; ++i)
+        v[i] = kSha256H[i];
+#pragma unroll 1
+    for (int t0 = 0;; t0 += 16) {
+        sha256_8(m, v, t0, 0);
+        sha256_8(m, v, t0, 8);
+        if (t0 == 48)
+            break;
+        schedule16<uint32_t, s256_0, s256_1>(m);
     }
-    h[0] = kSha256H[0] + a;
-    h[1] = kSha256H[1] + b;
-    h[2] = kSha256H[2] + c;
-    h[3] = kSha256H[3] + d;
-    h[4] = kSha256H[4] + e;
-    h[5] = kSha256H[5] + f;
-    h[6] = kSha256H[6] + g;
-    h[7] = kSha256H[7] + k;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        h[i] = kSha256H[i] + v[i];
 }
 
 __device__ __forceinline__ void sha512_block(uint64_t (&m)[16], uint64_t (&h)[8])
 {
-    uint64_t a = kSha512H[0], b = kSha512H[1], c = kSha512H[2], d = kSha512H[3];
-    uint64_t e = kSha512H[4], f = kSha512H[5], g = kSha512H[6], k = kSha512H[7];
+    uint64_t v[8];
 #pragma unroll
-    for (int t = 0; t < 80; ++t) {
-        if (t >= 16) {
-            const uint64_t x = m[(t - 15) & 15], y = m[(t - 2) & 15];
-            m[t & 15] += (rotr64(x, 1) ^ rotr64(x, 8) ^ (x >> 7)) + m[(t - 7) & 15] +
-                         (rotr64(y, 19) ^ rotr64(y, 61) ^ (y >> 6));
-        }
-        const uint64_t t1 = k + (rotr64(e, 14) ^ rotr64(e, 18) ^ rotr64(e, 41)) + ((e & f) ^ (~e & g)) +
-                            kSha512K[t] + m[t & 15];
-        const uint64_t t2 = (rotr64(a, 28) ^ rotr64(a, 34) ^ rotr64(a, 39)) + ((a & b) ^ (a & c) ^ (b & c));
-        k = g;
-        g = f;
-        f = e;
-        e = d + t1;
-        d = c;
-        c = b;
-        b = a;
-        a = t1 + t2;
+    for (int i = 0; i < 8; ++i)
+        v[i] = kSha512H[i];
+#pragma unroll 1
+    for (int t0 = 0;; t0 += 16) {
+        sha512_8(m, v, t0, 0);
+        sha512_8(m, v, t0, 8);
+        if (t0 == 64)
+            break;
+        schedule16<uint64_t, s512_0, s512_1>(m);
     }
-    h[0] = kSha512H[0] + a;
-    h[1] = kSha512H[1] + b;
-    h[2] = kSha512H[2] + c;
-    h[3] = kSha512H[3] + d;
-    h[4] = kSha512H[4] + e;
-    h[5] = kSha512H[5] + f;
-    h[6] = kSha512H[6] + g;
-    h[7] = kSha512H[7] + k;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        h[i] = kSha512H[i] + v[i];
 }
 
 // B ^= the first 124 bits of SHA-256(key || nonce || idx || A record)
