@@ -6,12 +6,16 @@ in plain Python on top of it (sha2.py).
 
 TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` are its only users.  The CUDA library never loads
-it, and the two share no code.  Parity unpinned: none (every function is pinned
-by tests/test_oracle_*.py against the thesis's printed matrix A and F(4,4)
+it, and the two share no code.  Every function is pinned by
+tests/test_oracle_*.py against the thesis's printed matrix A and F(4,4)
 weights, its magnitude bounds, hand-worked examples, closed forms, invariants
 and the FIPS-197 / SP 800-38A vectors; SHA-2 by FIPS 180-4's example and
-hashlib, the keyed framing by a hashlib restatement and the scheme's
-properties in tests/test_oracle_sha.py).
+hashlib.  Parity unpinned: the hash-input framing of protect_keyed /
+recover_keyed / keyed_block_records (which bytes enter SHA-256 and SHA-512,
+and how digest bits map onto record bits), which the thesis does not give;
+tests/test_oracle_sha.py checks it only by a hashlib restatement and by the
+scheme's properties (exact inverse, key sensitivity, identical blocks
+protected differently, errors that stay in their block).
 """
 from __future__ import annotations
 
