@@ -20,6 +20,7 @@ seeing its group's completion event.
 from __future__ import annotations
 
 import collections
+import contextlib
 import threading
 import time
 from typing import List, Optional
@@ -96,6 +97,7 @@ class Server:
         self._used = 0
         self._cv = threading.Condition()
         self._stop = False
+        self._hold = 0
         self.launches = 0
         self._thread = threading.Thread(target=self._loop, name="frag-serve", daemon=True)
         self._thread.start()
@@ -140,7 +142,23 @@ class Server:
             if self._stop:
                 raise RuntimeError("server is closed")
             self._pending.append(r)
-            self._cv.notify()
+            if not self._hold:  # a held scheduler has nothing to do yet
+                self._cv.notify()
+
+    @contextlib.contextmanager
+    def held(self):
+        """Admit nothing while the block runs: the requests submitted inside
+        it wait and are admitted together when it ends (in arrival order,
+        within the memory budget), so their grouping does not depend on how
+        the scheduler thread interleaves with the submitting one."""
+        with self._cv:
+            self._hold += 1
+        try:
+            yield self
+        finally:
+            with self._cv:
+                self._hold -= 1
+                self._cv.notify()
 
     def close(self) -> None:
         """Finish every submitted request, then stop the scheduler."""
@@ -235,7 +253,8 @@ class Server:
             with self._cv:
                 if self._stop and not self._pending and not self._inflight:
                     return
-                reqs = self._admit() if len(self._inflight) < self.max_groups else []
+                free_slot = len(self._inflight) < self.max_groups
+                reqs = self._admit() if free_slot and not self._hold else []
             if reqs:
                 self._launch(reqs)
                 continue

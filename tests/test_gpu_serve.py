@@ -96,3 +96,29 @@ def test_small_memory_budget_admits_in_turn(fr):
         assert srv.launches >= 4  # the budget forced several groups
     for r, d in zip(backs, datas):
         assert torch.equal(r.out, d)
+
+
+def test_held_requests_launch_together(fr):
+    """Requests submitted while the scheduler holds are admitted as one group
+    when the hold ends: one protect launch and one recover launch in all."""
+    from paper_1803_04880_b300.serve import Server
+    sizes = _sizes(24, 11, hi=1 << 20)
+    datas = [torch.from_numpy(wl.random_bytes(int(n), 300 + i)).cuda() for i, n in enumerate(sizes)]
+    torch.cuda.synchronize()
+    with Server(wl.KEY, width=4096, levels=3, max_groups=2) as srv:
+        with srv.held():
+            first = [srv.submit_protect(d, i) for i, d in enumerate(datas)]
+            time.sleep(0.05)
+            assert not any(r.done for r in first)  # nothing admitted while held
+        for r in first:
+            assert r.wait(60)
+        assert srv.launches == 1
+        with srv.held():
+            back = [srv.submit_recover(r.private, r.public, r.nbytes, r.nonce) for r in first]
+            again = [srv.submit_protect(d, 100 + i) for i, d in enumerate(datas[:5])]
+        for r in back + again:
+            assert r.wait(60)
+        assert srv.launches == 3  # one protect batch and one recover batch for the mixed group
+        srv.check()
+    for r, d in zip(back, datas):
+        assert torch.equal(r.out, d)
