@@ -263,7 +263,7 @@ def _cpu_baseline(items, block=0, packed=False, keyed=False):
         el = time.perf_counter() - t0
         if el >= 10.0 or reps >= 20:
             break
-    return {"value": round(n * reps / el / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": float("%.4g" % (n * reps / el / 1e9)), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%s of item 0 of the workload (%d bytes), protect+recover x%d, one thread"
                       % ("the first 64 rows" if keyed else "all", n, reps)}
 
