@@ -158,6 +158,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _sig(v, digits=4):
+    """v to `digits` significant digits (the oracle's rates are far below 1 GB/s)."""
+    return float("%.*g" % (digits, v))
+
+
 # -- reference arm: the oracle on the host cores -----------------------------------
 
 def run_reference(args, rank):
@@ -193,15 +198,15 @@ def run_reference(args, rank):
             times.append(dt)
     total = sum(times)
     value = n * len(times) / total / 1e9
-    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "impl": "reference",
+    line = {"metric": METRIC, "value": _sig(value), "unit": UNIT, "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * total / len(times), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": desc,
-            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": _sig(value), "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d bytes (first rows of item 0) protect+recover per step"
                                        % n},
-            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+            "e2e": {"value": _sig(value), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -263,7 +268,7 @@ def _cpu_baseline(items, block=0, packed=False, keyed=False):
         el = time.perf_counter() - t0
         if el >= 10.0 or reps >= 20:
             break
-    return {"value": float("%.4g" % (n * reps / el / 1e9)), "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": _sig(n * reps / el / 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%s of item 0 of the workload (%d bytes), protect+recover x%d, one thread"
                       % ("the first 64 rows" if keyed else "all", n, reps)}
 
@@ -758,14 +763,14 @@ def _reference_aes(args):
             times.append(dt)
     total = sum(times)
     value = n * len(times) / total / 1e9
-    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "impl": "reference",
+    line = {"metric": METRIC, "value": _sig(value), "unit": UNIT, "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * total / len(times), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": AES_DESC,
-            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": _sig(value), "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "first %d bytes, encrypt+decrypt per step" % n},
-            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+            "e2e": {"value": _sig(value), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
