@@ -1153,6 +1153,18 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
     uint64_t u64 = 0;
     for (const Buf &b : bp.bufs)
         u64 += l1_units_at_64(b);
+    // CTR chunks: kCtrChunkList blocks, doubled (up to 16x) while the batch
+    // keeps more than 16 chunks per resident CTA, so a batch of large
+    // private fragments builds and uploads fewer descriptors with the same
+    // parallelism
+    uint64_t ctr_blocks = 0;
+    for (const Buf &b : bp.bufs)
+        if (separate_cipher(b))
+            ctr_blocks += ctr_fragment(bp.fwd, b).nblocks;
+    uint64_t chunk = frag::kCtrChunkList;
+    const uint64_t per_cta = 16 * std::max<uint64_t>(1, bp.resident_ctas);
+    while (chunk < 16 * frag::kCtrChunkList && ctr_blocks / (2 * chunk) >= per_cta)
+        chunk *= 2;
     for (auto &wv : bp.waves) {
         wv.jobs.clear();
         wv.first.clear();
@@ -1190,12 +1202,12 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         if (b.F2)
             wv.fbufs2.push_back(fuse_buf(bp.fwd, b, 2));
         if (separate_cipher(b)) {
-            // the private fragment in chunks of kCtrChunkList blocks
+            // the private fragment in chunks of `chunk` blocks
             const frag::CtrChunk whole = ctr_fragment(bp.fwd, b);
-            for (uint64_t f = 0; f < whole.nblocks; f += frag::kCtrChunkList) {
+            for (uint64_t f = 0; f < whole.nblocks; f += chunk) {
                 frag::CtrChunk c = whole;
                 c.first_block = f;
-                c.nblocks = std::min<uint64_t>(frag::kCtrChunkList, whole.nblocks - f);
+                c.nblocks = std::min<uint64_t>(chunk, whole.nblocks - f);
                 wv.chunks.push_back(c);
             }
         }

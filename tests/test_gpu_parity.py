@@ -320,3 +320,40 @@ def test_batch_object_in_cuda_graph(fr, key):
         for o, d in zip(outs, refs):
             assert np.array_equal(o.cpu().numpy(), d)
     fr.sync_status()
+
+
+def test_batch_of_large_private_fragments(fr, key):
+    """A batch whose private fragments total about 16 M AES blocks (the CTR
+    pass then takes chunks of several times 256 blocks): every fragment
+    equals that of a single call on the same buffer (the single call's CTR
+    pass is pinned against the oracle at full size), ragged chunk ends
+    included, and the batch recovers every byte."""
+    specs = [(8192, 1, (64 << 20) + 12345), (8192, 1, 64 << 20), (4096, 2, (48 << 20) - 7),
+             (8192, 1, (64 << 20) - 4096 * 3), (256, 1, 1000)]
+    entries, rentries, singles, outs, ins = [], [], [], [], []
+    for i, (W, L, n) in enumerate(specs):
+        plan = fr.Plan(W, L)
+        g = torch.Generator(device="cuda").manual_seed(40 + i)
+        t = torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda", generator=g)
+        _, pb, ub = plan.sizes(n)
+        p = torch.empty(pb, dtype=torch.uint8, device="cuda")
+        u = torch.empty(ub, dtype=torch.uint8, device="cuda")
+        o = torch.empty(n, dtype=torch.uint8, device="cuda")
+        entries.append((plan, 500 + i, n, t, p, u))
+        rentries.append((plan, 500 + i, n, p, u, o))
+        singles.append((plan, 500 + i, t))
+        outs.append(o)
+        ins.append(t)
+    fr.protect_batch(entries, key)
+    fr.recover_batch(rentries, key)
+    fr.sync_status()
+    for (plan, nonce, t), (_, _, _, _, p, u), o in zip(singles, entries, outs):
+        p1, u1 = fr.protect(plan, key, nonce, t)
+        fr.sync_status()
+        assert torch.equal(p, p1), "private fragment differs from the single call"
+        assert torch.equal(u, u1), "public fragment differs from the single call"
+        assert torch.equal(o, t), "recovered bytes differ"
+    # the small buffer against the oracle as well
+    plan, nonce, t = singles[-1]
+    p_ref, u_ref = oracle.protect(t.cpu().numpy(), 256, 1, KEY, nonce)
+    assert np.array_equal(entries[-1][4].cpu().numpy(), p_ref)
