@@ -1,7 +1,8 @@
 """Pins of the oracle's keyed protection of the public fragments (Sec. 5.2.1:
 SHA-256 of the private fragment and the key protects the first public and
 protected fragment, SHA-512 of that protected fragment and the key the
-second; Sec. 5.2.4: an error stays inside its block).
+second; Sec. 5.3.5: a counter among the hash inputs makes identical blocks
+protect differently; Sec. 5.3.7: an error stays inside its block).
 
 SHA-2 is pinned against FIPS 180-4's published "abc" example and against
 Python's hashlib over every padding case.  The framing of the hash inputs
