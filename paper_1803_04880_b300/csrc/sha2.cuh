@@ -38,23 +38,24 @@ __device__ __forceinline__ uint64_t rotr64(uint64_t x, int n)
 
 __device__ __forceinline__ uint32_t bswap(uint32_t x) { return __byte_perm(x, 0u, 0x0123); }
 
-// One round on the working variables (a..h) with schedule word w and
-// constant kt; the caller rotates the names, so 8 calls in a row return to
-// the same assignment.
-#define FRAG_SHA256_ROUND(a, b, c, d, e, f, g, h, kt, w)                                                      \
-    do {                                                                                                      \
-        const uint32_t t1_ = h + (rotr(e, 6) ^ rotr(e, 11) ^ rotr(e, 25)) + ((e & f) ^ (~e & g)) + (kt) + (w);  \
-        d += t1_;                                                                                             \
-        h = t1_ + (rotr(a, 2) ^ rotr(a, 13) ^ rotr(a, 22)) + ((a & b) ^ (a & c) ^ (b & c));                   \
-    } while (0)
+// One round on the working variables a..h with schedule word w and constant
+// kt: d becomes the next e and h the next a; the caller rotates the names,
+// so 8 calls in a row return to the same assignment.
+__device__ __forceinline__ void round256(uint32_t a, uint32_t b, uint32_t c, uint32_t &d, uint32_t e,
+                                         uint32_t f, uint32_t g, uint32_t &h, uint32_t kt, uint32_t w)
+{
+    const uint32_t t1 = h + (rotr(e, 6) ^ rotr(e, 11) ^ rotr(e, 25)) + ((e & f) ^ (~e & g)) + kt + w;
+    d += t1;
+    h = t1 + (rotr(a, 2) ^ rotr(a, 13) ^ rotr(a, 22)) + ((a & b) ^ (a & c) ^ (b & c));
+}
 
-#define FRAG_SHA512_ROUND(a, b, c, d, e, f, g, h, kt, w)                                                      \
-    do {                                                                                                      \
-        const uint64_t t1_ =                                                                                  \
-            h + (rotr64(e, 14) ^ rotr64(e, 18) ^ rotr64(e, 41)) + ((e & f) ^ (~e & g)) + (kt) + (w);            \
-        d += t1_;                                                                                             \
-        h = t1_ + (rotr64(a, 28) ^ rotr64(a, 34) ^ rotr64(a, 39)) + ((a & b) ^ (a & c) ^ (b & c));            \
-    } while (0)
+__device__ __forceinline__ void round512(uint64_t a, uint64_t b, uint64_t c, uint64_t &d, uint64_t e,
+                                         uint64_t f, uint64_t g, uint64_t &h, uint64_t kt, uint64_t w)
+{
+    const uint64_t t1 = h + (rotr64(e, 14) ^ rotr64(e, 18) ^ rotr64(e, 41)) + ((e & f) ^ (~e & g)) + kt + w;
+    d += t1;
+    h = t1 + (rotr64(a, 28) ^ rotr64(a, 34) ^ rotr64(a, 39)) + ((a & b) ^ (a & c) ^ (b & c));
+}
 
 __device__ __forceinline__ uint32_t s256_0(uint32_t x) { return rotr(x, 7) ^ rotr(x, 18) ^ (x >> 3); }
 __device__ __forceinline__ uint32_t s256_1(uint32_t x) { return rotr(x, 17) ^ rotr(x, 19) ^ (x >> 10); }
@@ -67,9 +68,8 @@ __device__ __forceinline__ void sha256_8(const uint32_t (&m)[16], uint32_t (&v)[
 {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        uint32_t &a = v[(8 - j) & 7], &b = v[(9 - j) & 7], &c = v[(10 - j) & 7], &d = v[(11 - j) & 7];
-        uint32_t &e = v[(12 - j) & 7], &f = v[(13 - j) & 7], &g = v[(14 - j) & 7], &h = v[(15 - j) & 7];
-        FRAG_SHA256_ROUND(a, b, c, d, e, f, g, h, kSha256K[t0 + q0 + j], m[q0 + j]);
+        round256(v[(8 - j) & 7], v[(9 - j) & 7], v[(10 - j) & 7], v[(11 - j) & 7], v[(12 - j) & 7],
+                 v[(13 - j) & 7], v[(14 - j) & 7], v[(15 - j) & 7], kSha256K[t0 + q0 + j], m[q0 + j]);
     }
 }
 
@@ -77,9 +77,8 @@ __device__ __forceinline__ void sha512_8(const uint64_t (&m)[16], uint64_t (&v)[
 {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        uint64_t &a = v[(8 - j) & 7], &b = v[(9 - j) & 7], &c = v[(10 - j) & 7], &d = v[(11 - j) & 7];
-        uint64_t &e = v[(12 - j) & 7], &f = v[(13 - j) & 7], &g = v[(14 - j) & 7], &h = v[(15 - j) & 7];
-        FRAG_SHA512_ROUND(a, b, c, d, e, f, g, h, kSha512K[t0 + q0 + j], m[q0 + j]);
+        round512(v[(8 - j) & 7], v[(9 - j) & 7], v[(10 - j) & 7], v[(11 - j) & 7], v[(12 - j) & 7],
+                 v[(13 - j) & 7], v[(14 - j) & 7], v[(15 - j) & 7], kSha512K[t0 + q0 + j], m[q0 + j]);
     }
 }
 
