@@ -164,3 +164,17 @@ def test_full_plane_sampled_blocks(fr, key):
         got_b = (row >> (124 * bj)) & ((1 << 124) - 1)
         got_c = int.from_bytes(pub[sb + 60 * idx:sb + 60 * idx + 60].tobytes(), "little")
         assert (got_a, got_b, got_c) == want, "block %d" % idx
+
+
+def test_host_buffer_forms(fr, key):
+    """frag_protect_host / frag_recover_host on a keyed plan: host buffers in
+    and out, the same fragments as the oracle."""
+    W, n = 200, 200 * 48 + 17
+    data = wl.random_bytes(n, seed=23)
+    plan = _keyed_plan(fr, W)
+    p, u = fr.protect_host(plan, key, 77, data)
+    a_ref, pub_ref = oracle.protect_keyed(data, W, KEY, 77)
+    assert np.array_equal(p.numpy(), a_ref)
+    assert np.array_equal(u.numpy(), pub_ref)
+    out = fr.recover_host(plan, key, 77, p, u, n)
+    assert np.array_equal(out.numpy(), data)
