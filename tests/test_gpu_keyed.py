@@ -178,3 +178,32 @@ def test_host_buffer_forms(fr, key):
     assert np.array_equal(u.numpy(), pub_ref)
     out = fr.recover_host(plan, key, 77, p, u, n)
     assert np.array_equal(out.numpy(), data)
+
+
+def test_resident_batch_object(fr, key):
+    """A keyed plan in a resident batch (frag_batch_create_*), run twice."""
+    W = 64
+    datas = [wl.random_bytes(64 * 24 + i * 64, seed=30 + i) for i in range(3)]
+    plan = _keyed_plan(fr, W)
+    ents, rents, refs = [], [], []
+    for i, d in enumerate(datas):
+        _, pb, ub = plan.sizes(d.size)
+        t = torch.from_numpy(d).cuda()
+        p = torch.empty(pb, dtype=torch.uint8, device="cuda")
+        u = torch.empty(ub, dtype=torch.uint8, device="cuda")
+        o = torch.empty(d.size, dtype=torch.uint8, device="cuda")
+        ents.append((plan, 40 + i, d.size, t, p, u))
+        rents.append((plan, 40 + i, d.size, p, u, o))
+        refs.append((d, oracle.protect_keyed(d, W, KEY, 40 + i), p, u, o))
+    bp = fr.Batch(ents, protect=True)
+    br = fr.Batch(rents, protect=False)
+    for _ in range(2):
+        for _, _, _, _, o in refs:
+            o.zero_()
+        bp.run(key)
+        br.run(key)
+        fr.sync_status()
+        for d, (a_ref, pub_ref), p, u, o in refs:
+            assert np.array_equal(p.cpu().numpy(), a_ref)
+            assert np.array_equal(u.cpu().numpy(), pub_ref)
+            assert np.array_equal(o.cpu().numpy(), d)
