@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -115,7 +116,10 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # the raw samples (the JSON line carries their summary); FRAG_CLOCKS_CSV
+        # names another file to keep them
+        self.path = os.environ.get("FRAG_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(),
+                                                                      "frag_clocks_bench.csv")
 
     def start(self):
         try:
