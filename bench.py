@@ -162,6 +162,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def job_rate(dist, total_ms, bytes_per_rank_step, K, world, device):
+    """(ms per step, whole-job GB/s) of K timed steps: the slowest rank's
+    time (max over ranks when dist is a process group module) and the bytes
+    every rank processed (each rank the same bytes a step: weak scaling)."""
+    import torch
+    if dist is not None:
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms / K, world * bytes_per_rank_step * K / (total_ms / 1e3) / 1e9
+
+
 def _sig(v, digits=4):
     """v to `digits` significant digits (the oracle's rates are far below 1 GB/s)."""
     return float("%.*g" % (digits, v))
@@ -383,13 +395,7 @@ def run_ours(args, rank, world, local_rank):
     tp = [e[0].elapsed_time(e[1]) for e in ev]
     tr = [e[2].elapsed_time(e[3]) for e in ev]
     steps_ms = [a + b for a, b in zip(tp, tr)]
-    total_ms = sum(steps_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / K
-    value = world * n_total * K / (total_ms / 1e3) / 1e9
+    ms_per_step, value = job_rate(dist, sum(steps_ms), n_total, K, world, dev)
 
     # per-file: the same step as 2 x planes single-buffer calls
     pf_ms = []
@@ -850,13 +856,7 @@ def run_aesfull(args, rank, world, local_rank):
     te = [e[0].elapsed_time(e[1]) for e in ev]
     td = [e[2].elapsed_time(e[3]) for e in ev]
     steps_ms = [a + b for a, b in zip(te, td)]
-    total_ms = sum(steps_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / K
-    value = world * n * K / (total_ms / 1e3) / 1e9
+    ms_per_step, value = job_rate(dist, sum(steps_ms), n, K, world, dev)
     # one launch per direction: the event pair around it is the kernel's time
     t_launch = statistics.mean(te + td)
     props = torch.cuda.get_device_properties(dev)
