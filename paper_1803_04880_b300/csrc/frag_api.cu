@@ -1063,7 +1063,6 @@ struct DagWave {
 struct BatchPlan {
     bool fwd = true;
     uint64_t resident_ctas = 0; // CTAs one launch keeps resident
-    uint32_t sms = 0;           // SMs of the device
     uint32_t max_ctas = 0;      // grid cap from the first item's plan (0: none)
     uint32_t fuse_rows = 0;     // fused segment rows from the first item's plan (0: adaptive)
     uint64_t fuse_slots = 0;    // fused CTAs one launch keeps resident
@@ -1154,21 +1153,15 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
     uint64_t u64 = 0;
     for (const Buf &b : bp.bufs)
         u64 += l1_units_at_64(b);
-    // CTR chunks (one CTA each): when the batch has more than one chunk of
-    // kCtrChunkList blocks per SM, the fewest whole waves of k CTAs per SM
-    // with chunks of at most kCtrChunkList blocks (every SM the same share);
-    // then doubled (up to 16x) while the batch keeps more than 16 chunks per
-    // resident CTA, so a batch of large private fragments builds and uploads
-    // fewer descriptors with the same parallelism
+    // CTR chunks: kCtrChunkList blocks, doubled (up to 16x) while the batch
+    // keeps more than 16 chunks per resident CTA, so a batch of large
+    // private fragments builds and uploads fewer descriptors with the same
+    // parallelism
     uint64_t ctr_blocks = 0;
     for (const Buf &b : bp.bufs)
         if (separate_cipher(b))
             ctr_blocks += ctr_fragment(bp.fwd, b).nblocks;
     uint64_t chunk = frag::kCtrChunkList;
-    if (bp.sms && ctr_blocks > chunk * bp.sms) {
-        const uint64_t k = (ctr_blocks + chunk * bp.sms - 1) / (chunk * bp.sms);
-        chunk = (ctr_blocks + k * bp.sms - 1) / (k * bp.sms);
-    }
     const uint64_t per_cta = 16 * std::max<uint64_t>(1, bp.resident_ctas);
     while (chunk < 16 * frag::kCtrChunkList && ctr_blocks / (2 * chunk) >= per_cta)
         chunk *= 2;
@@ -1474,7 +1467,6 @@ frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, 
     if ((st = dag_grid(*d, fwd, ~0ull, &grid)) != FRAG_OK)
         return st;
     bp.resident_ctas = bp.max_ctas ? std::min(grid, bp.max_ctas) : grid;
-    bp.sms = (uint32_t)d->sms;
     if ((st = batch_fuse_slots(bp, *d)) != FRAG_OK)
         return st;
     BatchPlan sizing = bp; // the layout does not depend on the scratch base
@@ -1519,10 +1511,8 @@ frag_status create_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, ui
     if (st == FRAG_OK)
         st = device_state(&d, &bt->device);
     uint32_t grid = 0;
-    if (st == FRAG_OK && (st = dag_grid(*d, fwd, ~0ull, &grid)) == FRAG_OK) {
+    if (st == FRAG_OK && (st = dag_grid(*d, fwd, ~0ull, &grid)) == FRAG_OK)
         bt->bp.resident_ctas = bt->bp.max_ctas ? std::min(grid, bt->bp.max_ctas) : grid;
-        bt->bp.sms = (uint32_t)d->sms;
-    }
     if (st == FRAG_OK)
         st = batch_fuse_slots(bt->bp, *d);
     if (st == FRAG_OK && !bt->bp.bufs.empty()) {
