@@ -1,4 +1,4 @@
-"""Autotuner for the streaming kernel's schedule.
+"""Autotuner for the kernels' schedule.
 
 The schedule of a plan (``Plan.set_schedule``) has two knobs: the level-0
 rows of one work unit (the tile height: 16 .. 256, a power of two) and the
@@ -7,14 +7,16 @@ does, and the best pair moves with the buffer's shape and size.  ``tune``
 times protect + recover of synthetic bytes of a given shape for every
 candidate on the current GPU and keeps the fastest; results are cached in a
 JSON file per (device name, width, levels, size class) and ``apply`` sets a
-plan's schedule from that cache.
+plan's schedule from that cache.  ``tune_batch`` does the same for a whole
+batch (which takes its schedule from its first item's plan) by timing the
+batch itself over ``batch_candidates``.
 """
 from __future__ import annotations
 
 import json
 import math
 import os
-from typing import Dict, Iterable, Optional, Tuple
+from typing import Callable, Dict, Iterable, Optional, Tuple
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_schedules.json")
 CANDIDATE_ROWS = (16, 32, 64, 128)
@@ -99,6 +101,50 @@ def tune(width: int, levels: int, nbytes: int, reps: int = 3, path: Optional[str
         cache[_key(props.name, width, levels, nbytes)] = result
         save_cache(cache, path)
     return result
+
+
+# a batch's schedule: fused-unit rows (0: the library's adaptive units,
+# sized to the batch's work and capped when it mixes buffers) and grid cap
+BATCH_ROWS = (0, 64, 128, 256)
+
+
+def batch_candidates(sms: int) -> Iterable[Tuple[int, int]]:
+    for rows in BATCH_ROWS:
+        for ctas in (0, 2 * sms):
+            yield rows, ctas
+
+
+def _event_ms(fn) -> float:
+    """Device time of one call of fn, by CUDA events on the current stream."""
+    import torch
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    fn()
+    e1.record(s)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def tune_batch(make_run: Callable[[int, int], Callable[[], None]], cands: Iterable[Tuple[int, int]],
+               reps: int = 2, clock: Optional[Callable[[Callable[[], None]], float]] = None) -> dict:
+    """Pick a batch's schedule by timing the batch itself.  make_run(rows,
+    ctas) sets that schedule on the batch's plans (a batch takes it from its
+    first item's plan), builds the batch and returns a callable that runs it
+    once; the results do not depend on the schedule (the caller checks them
+    afterwards).  clock(fn) gives the milliseconds of one call (default: CUDA
+    events on the current stream).  Returns {"seg_rows", "ctas", "ms",
+    "timings"} with the fastest candidate."""
+    clock = clock or _event_ms
+    timings = {}
+    for rows, ctas in cands:
+        run = make_run(rows, ctas)
+        run()  # warm-up
+        timings["%d/%d" % (rows, ctas)] = round(min(clock(run) for _ in range(max(1, reps))), 3)
+        del run
+    best = min(timings, key=timings.get)
+    rows, ctas = map(int, best.split("/"))
+    return {"seg_rows": rows, "ctas": ctas, "ms": timings[best], "timings": timings}
 
 
 def apply(plan, nbytes: int, path: str = DEFAULT_CACHE, device_name: Optional[str] = None) -> bool:
