@@ -577,12 +577,13 @@ def run_c4(args, rank, world, local_rank):
     # (in place: the round trip restores them)
     from paper_1803_04880_b300 import tune
 
-    def set_schedule(rows, ctas):
+    def set_schedule(rows, ctas, path=0):
         for p in plans.values():
             p.set_schedule(rows, ctas)
+            p.set_path(path)
 
-    def make_run(rows, ctas):
-        set_schedule(rows, ctas)
+    def make_run(rows, ctas, path):
+        set_schedule(rows, ctas, path)
         b1, b2 = fr.Batch(pentries, protect=True), fr.Batch(rentries, protect=False)
 
         def run():
@@ -594,7 +595,7 @@ def run_c4(args, rank, world, local_rank):
         tuned = tune.tune_batch(make_run, tune.batch_candidates(torch.cuda.get_device_properties(dev)
                                                                  .multi_processor_count))
     torch.cuda.synchronize()
-    set_schedule(tuned["seg_rows"], tuned["ctas"])
+    set_schedule(tuned["seg_rows"], tuned["ctas"], tuned["path"])
     bp = fr.Batch(pentries, protect=True)
     br = fr.Batch(rentries, protect=False)
     # graph: protect then recover in place
@@ -661,9 +662,10 @@ def run_c4(args, rank, world, local_rank):
                                        "2^round(log2(n)/2), levels 1..4" % len(items),
                            "bytes": n_total, "l2": "inputs larger than L2",
                            "schedule": {"seg_rows": tuned["seg_rows"], "ctas": tuned["ctas"],
-                                        "autotuned_ms": tuned["timings"],
-                                        "note": "rows 0 / ctas 0: the library's adaptive units "
-                                                "and full grid"},
+                                        "path": tuned["path"], "autotuned_ms": tuned["timings"],
+                                        "note": "rows/ctas/path; rows 0, ctas 0: the library's "
+                                                "adaptive units and full grid; path 0 fused "
+                                                "levels, 1 level kernel only"},
                            "path": "Batch objects (one launch per wave and direction) in one CUDA graph"},
                 "per_file": {"ms_per_step": round(per_file_ms, 3),
                              "value": round(n_total / (per_file_ms / 1e3) / 1e9, 2),

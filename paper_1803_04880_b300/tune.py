@@ -104,14 +104,18 @@ def tune(width: int, levels: int, nbytes: int, reps: int = 3, path: Optional[str
 
 
 # a batch's schedule: fused-unit rows (0: the library's adaptive units,
-# sized to the batch's work and capped when it mixes buffers) and grid cap
+# sized to the batch's work and capped when it mixes buffers), grid cap, and
+# level-fusion depth (path 0: up to three levels fused per pass, the rest in
+# a second pass or the level kernel; path 1: every level in the level kernel)
 BATCH_ROWS = (0, 64, 128, 256)
 
 
-def batch_candidates(sms: int) -> Iterable[Tuple[int, int]]:
+def batch_candidates(sms: int) -> Iterable[Tuple[int, int, int]]:
     for rows in BATCH_ROWS:
         for ctas in (0, 2 * sms):
-            yield rows, ctas
+            yield rows, ctas, 0
+    for ctas in (0, 2 * sms):
+        yield 0, ctas, 1
 
 
 def _event_ms(fn) -> float:
@@ -126,25 +130,26 @@ def _event_ms(fn) -> float:
     return e0.elapsed_time(e1)
 
 
-def tune_batch(make_run: Callable[[int, int], Callable[[], None]], cands: Iterable[Tuple[int, int]],
+def tune_batch(make_run: Callable[..., Callable[[], None]], cands: Iterable[Tuple[int, ...]],
                reps: int = 2, clock: Optional[Callable[[Callable[[], None]], float]] = None) -> dict:
     """Pick a batch's schedule by timing the batch itself.  make_run(rows,
-    ctas) sets that schedule on the batch's plans (a batch takes it from its
-    first item's plan), builds the batch and returns a callable that runs it
-    once; the results do not depend on the schedule (the caller checks them
-    afterwards).  clock(fn) gives the milliseconds of one call (default: CUDA
-    events on the current stream).  Returns {"seg_rows", "ctas", "ms",
-    "timings"} with the fastest candidate."""
+    ctas, path) sets that schedule and path on the batch's plans (a batch
+    takes rows and cap from its first item's plan, each buffer's path from
+    its own), builds the batch and returns a callable that runs it once; the
+    results do not depend on the schedule (the caller checks them
+    afterwards).  clock(fn) gives the milliseconds of one call (default:
+    CUDA events on the current stream).  Returns {"seg_rows", "ctas",
+    "path", "ms", "timings"} with the fastest candidate."""
     clock = clock or _event_ms
     timings = {}
-    for rows, ctas in cands:
-        run = make_run(rows, ctas)
+    for cand in cands:
+        run = make_run(*cand)
         run()  # warm-up
-        timings["%d/%d" % (rows, ctas)] = round(min(clock(run) for _ in range(max(1, reps))), 3)
+        timings["/".join(map(str, cand))] = round(min(clock(run) for _ in range(max(1, reps))), 3)
         del run
     best = min(timings, key=timings.get)
-    rows, ctas = map(int, best.split("/"))
-    return {"seg_rows": rows, "ctas": ctas, "ms": timings[best], "timings": timings}
+    rows, ctas, path = (list(map(int, best.split("/"))) + [0])[:3]
+    return {"seg_rows": rows, "ctas": ctas, "path": path, "ms": timings[best], "timings": timings}
 
 
 def apply(plan, nbytes: int, path: str = DEFAULT_CACHE, device_name: Optional[str] = None) -> bool:

@@ -53,19 +53,21 @@ def test_candidates_cover_rows_and_grids():
 
 def test_tune_batch_picks_the_fastest_candidate():
     from paper_1803_04880_b300 import tune
-    cost = {(0, 0): 5.0, (64, 0): 4.0, (128, 296): 3.5, (256, 0): 6.0}
+    cost = {(0, 0, 0): 5.0, (64, 0, 0): 4.0, (128, 296, 0): 3.5, (256, 0, 0): 6.0, (0, 0, 1): 7.0}
     built, runs = [], []
 
-    def make_run(rows, ctas):
-        built.append((rows, ctas))
-        return lambda: runs.append((rows, ctas))
+    def make_run(rows, ctas, path):
+        built.append((rows, ctas, path))
+        return lambda: runs.append((rows, ctas, path))
 
     def clock(fn):
         fn()
         return cost[runs[-1]]
 
     r = tune.tune_batch(make_run, list(cost), reps=2, clock=clock)
-    assert (r["seg_rows"], r["ctas"], r["ms"]) == (128, 296, 3.5)
+    assert (r["seg_rows"], r["ctas"], r["path"], r["ms"]) == (128, 296, 0, 3.5)
     assert built == list(cost) and len(runs) == 3 * len(cost)  # a warm-up and two timed runs each
-    assert r["timings"] == {"0/0": 5.0, "64/0": 4.0, "128/296": 3.5, "256/0": 6.0}
-    assert list(tune.batch_candidates(148)) == [(rows, c) for rows in tune.BATCH_ROWS for c in (0, 296)]
+    assert r["timings"] == {"0/0/0": 5.0, "64/0/0": 4.0, "128/296/0": 3.5, "256/0/0": 6.0, "0/0/1": 7.0}
+    cands = list(tune.batch_candidates(148))
+    assert cands[:8] == [(rows, c, 0) for rows in tune.BATCH_ROWS for c in (0, 296)]
+    assert cands[8:] == [(0, 0, 1), (0, 296, 1)]
