@@ -219,7 +219,7 @@ def run_reference(args, rank):
             "ms_per_step": round(1e3 * total / len(times), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": desc,
-            "cpu_baseline": {"value": _sig(value), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": _sig(value), "unit": UNIT, "cores": 1, "kind": "oracle", "host": _host_info(),
                              "sample": "%d bytes (first rows of item 0) protect+recover per step"
                                        % n},
             "e2e": {"value": _sig(value), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -870,7 +870,7 @@ def _reference_aes(args):
             "ms_per_step": round(1e3 * total / len(times), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": AES_DESC,
-            "cpu_baseline": {"value": _sig(value), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": _sig(value), "unit": UNIT, "cores": 1, "kind": "oracle", "host": _host_info(),
                              "sample": "first %d bytes, encrypt+decrypt per step" % n},
             "e2e": {"value": _sig(value), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
