@@ -46,7 +46,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2",
-                    choices=["c2", "c2blocks", "c2packed", "c2keyed", "c3l2", "c3l4", "c4", "c5", "aesfull"])
+                    choices=["c1", "c2", "c2blocks", "c2packed", "c2keyed", "c3l2", "c3l4", "c4", "c5", "aesfull"])
     ap.add_argument("--items", type=int, default=10000, help="c4: number of buffers")
     ap.add_argument("--requests", type=int, default=240, help="c5: requests per load level")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -66,6 +66,10 @@ def _peaks():
 def _workload(name):
     """(description, list of (width, levels, nonce, uint8 numpy array))."""
     from paper_1803_04880_b300 import workloads as wl
+    if name == "c1":
+        return ({"workload": "256 x 256 random bytes (seed 0), 5/3 DWT 1 level, LL_1 AES-128-CTR",
+                 "planes": 1, "width": 256, "levels": 1},
+                [(256, 1, 0, wl.c1().reshape(-1))])
     if name == "c2":
         planes = wl.c2()
         return ({"workload": "bitmap 3x4096x4096 u8, 5/3 DWT 3 levels, LL_3 AES-128-CTR",
@@ -877,6 +881,112 @@ def _reference_aes(args):
     print(json.dumps(line), flush=True)
 
 
+def run_c1(args, rank, world, local_rank):
+    """The 256 x 256 matrix of random bytes, one level: it fits in L2, so it
+    is a latency figure: one frag_protect + one frag_recover call per step
+    (device buffers; an event pair around each call), p50 / p99 per call,
+    and the same through the host-buffer calls (wall clock, pinned)."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_1803_04880_b300 as fr
+    from paper_1803_04880_b300 import workloads as wl
+
+    fr.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    data = wl.c1().reshape(-1)
+    n, W, L = data.size, 256, 1
+    plan = fr.Plan(W, L)
+    key = fr.Key(wl.KEY)
+    _, pb, ub = plan.sizes(n)
+    d = torch.from_numpy(data).to(dev)
+    p = torch.empty(pb, dtype=torch.uint8, device=dev)
+    u = torch.empty(ub, dtype=torch.uint8, device=dev)
+    o = torch.empty(n, dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    K, Wm = args.steps, max(3, args.warmup)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    with torch.cuda.stream(s):
+        for _ in range(Wm):
+            fr.protect(plan, key, 0, d, n, p, u, stream=s)
+            fr.recover(plan, key, 0, p, u, n, o, stream=s)
+    torch.cuda.synchronize()
+    p_ref, u_ref = oracle.protect(data, W, L, wl.KEY, 0)
+    assert np.array_equal(p.cpu().numpy(), p_ref) and np.array_equal(u.cpu().numpy(), u_ref)
+    assert torch.equal(o, d), "c1 round trip differs"
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.5)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        for e in ev:
+            e[0].record(s)
+            fr.protect(plan, key, 0, d, n, p, u, stream=s)
+            e[1].record(s)
+            fr.recover(plan, key, 0, p, u, n, o, stream=s)
+            e[2].record(s)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    fr.sync_status(s)
+    tp = sorted(1e3 * e[0].elapsed_time(e[1]) for e in ev)
+    tr = sorted(1e3 * e[1].elapsed_time(e[2]) for e in ev)
+    steps_us = [1e3 * e[0].elapsed_time(e[2]) for e in ev]
+    ms_per_step = statistics.mean(steps_us) / 1e3
+    value = n / (ms_per_step / 1e3) / 1e9
+
+    def pct(v, q):
+        return round(v[min(len(v) - 1, int(q * len(v)))], 2)
+
+    # host buffers: wall clock of protect_host + recover_host
+    hin = torch.from_numpy(data).pin_memory()
+    hp = torch.empty(pb, dtype=torch.uint8).pin_memory()
+    hu = torch.empty(ub, dtype=torch.uint8).pin_memory()
+    ho = torch.empty(n, dtype=torch.uint8).pin_memory()
+    wall = []
+    for i in range(min(K, 2000) + Wm):
+        t0 = time.perf_counter()
+        fr.protect_host(plan, key, 0, hin, hp, hu, stream=s)
+        fr.recover_host(plan, key, 0, hp, hu, n, ho, stream=s)
+        if i >= Wm:
+            wall.append(1e6 * (time.perf_counter() - t0))
+    assert torch.equal(ho, hin), "c1 host round trip differs"
+    wall.sort()
+    # kernels a call launches: those of a one-item batch of the same buffer
+    launches = (fr.Batch([(plan, 0, n, d, p, u)], protect=True).launches +
+                fr.Batch([(plan, 0, n, p, u, o)], protect=False).launches)
+    peak, peak_kind = _peaks()
+    alg = 3 * n  # per direction
+    t_dir = statistics.mean(tp + tr) / 1e6
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+                "steps": K, "warmup": Wm, "ms_per_step": round(ms_per_step, 5),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic",
+                "config": {"workload": "256 x 256 random bytes (seed 0), 5/3 DWT 1 level, LL_1 "
+                                       "AES-128-CTR (key 00..0f, nonce 0): latency class",
+                           "planes": 1, "width": W, "levels": L,
+                           "l2": "fits in L2 (64 KiB): not flushed; a latency figure",
+                           "path": "frag_protect + frag_recover, one call each per step"},
+                "latency_us": {"protect_p50": pct(tp, 0.5), "protect_p99": pct(tp, 0.99),
+                               "recover_p50": pct(tr, 0.5), "recover_p99": pct(tr, 0.99),
+                               "host_round_trip_p50": pct(wall, 0.5),
+                               "host_round_trip_p99": pct(wall, 0.99)},
+                "p50_ms": round(statistics.median(steps_us) / 1e3, 5),
+                "p99_ms": round(sorted(steps_us)[min(K - 1, int(0.99 * K))] / 1e3, 5),
+                "roofline": {"bound": "hbm", "achieved": round(alg / t_dir / 1e9, 2), "peak": peak,
+                             "unit": "GB/s", "frac": round(alg / t_dir / 1e9 / peak, 5),
+                             "traffic": None, "peak_kind": peak_kind,
+                             "kernel": "one frag_protect / frag_recover call (its kernels and "
+                                       "launch gaps): launch-latency bound at 64 KiB"},
+                "cpu_baseline": None,
+                "e2e": {"value": round(n / (statistics.mean(wall) / 1e6) / 1e9, 4), "unit": UNIT,
+                        "h2d_bytes_per_step": n + pb + ub, "d2h_bytes_per_step": pb + ub + n,
+                        "api": "frag_protect_host + frag_recover_host (pinned host buffers)"},
+                "clocks": clocks, "gpu_launches": K * launches}
+        print(json.dumps(line), flush=True)
+
+
 def run_aesfull(args, rank, world, local_rank):
     import torch
     import paper_1803_04880_b300 as fr
@@ -1043,7 +1153,9 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        if args.workload == "c4":
+        if args.workload == "c1":
+            run_c1(args, rank, world, local_rank)
+        elif args.workload == "c4":
             run_c4(args, rank, world, local_rank)
         elif args.workload == "c5":
             run_c5(args, rank, world, local_rank)
