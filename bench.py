@@ -979,7 +979,8 @@ def run_c1(args, rank, world, local_rank):
                              "traffic": None, "peak_kind": peak_kind,
                              "kernel": "one frag_protect / frag_recover call (its kernels and "
                                        "launch gaps): launch-latency bound at 64 KiB"},
-                "cpu_baseline": None,
+                "cpu_baseline": (None if world > 1 or args.no_cpu_baseline
+                                 else _cpu_baseline([(W, L, 0, data)])),
                 "e2e": {"value": round(n / (statistics.mean(wall) / 1e6) / 1e9, 4), "unit": UNIT,
                         "h2d_bytes_per_step": n + pb + ub, "d2h_bytes_per_step": pb + ub + n,
                         "api": "frag_protect_host + frag_recover_host (pinned host buffers)"},
