@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
             uint8_t *bbase = PACKED ? sl.b->pk[1] + sl.bi * pkb::b_row_bytes(nbx) + 496ull * s : nullptr;
             const uint32_t bcount = (124 * nvalid + 7) / 8;
             if (PACKED && !FWD) // the whole warp: its blocks' B records
-                pkb::load_b(sb[warp], bbase, bcount, sl.on, lane, rb);
+                pkb::get_b(sb[warp], bbase, bcount, sl.on, lane, rb);
             if (FWD) {
                 // this block's rows came with the previous unit; fetch the next unit's
                 uint2 v[8];
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
                 inv_block<PACKED, KEYED>(*sl.b, sl.bi, sl.bj, false, sl.vec, 0, 0, rb, key);
             }
             if (PACKED && FWD)
-                pkb::store_b(sb[warp], bbase, bcount, sl.on, lane, rb);
+                pkb::put_b(sb[warp], bbase, bcount, sl.on, lane, rb);
         }
         return;
     }

@@ -114,5 +114,114 @@ __device__ __forceinline__ void load_b(uint32_t *sb, const uint8_t *base, uint32
     __syncwarp();
 }
 
+// -- the same without shared memory, for a 16-byte aligned warp area ------
+// The warp's 31 chunks of 128 bits: chunk j (bytes 16 j .. 16 j + 15) holds
+// bits 4 j .. 123 of block j's record, then bits 0 .. 4 j + 3 of block
+// j + 1's; so lane j writes (reads) chunk j with its neighbour's record (the
+// previous chunk) from one shuffle.  Every lane of the warp calls these.
+struct U128 {
+    uint64_t lo, hi;
+};
+
+__device__ __forceinline__ U128 u128(const uint32_t (&r)[4])
+{
+    return {r[0] | ((uint64_t)r[1] << 32), r[2] | ((uint64_t)r[3] << 32)};
+}
+
+__device__ __forceinline__ U128 shr128(U128 x, uint32_t s) // 0 <= s <= 128
+{
+    if (s >= 128)
+        return {0ull, 0ull};
+    if (s >= 64)
+        return {x.hi >> (s - 64), 0ull};
+    if (s == 0)
+        return x;
+    return {(x.lo >> s) | (x.hi << (64 - s)), x.hi >> s};
+}
+
+__device__ __forceinline__ U128 shl128(U128 x, uint32_t s) // 0 <= s <= 128
+{
+    if (s >= 128)
+        return {0ull, 0ull};
+    if (s >= 64)
+        return {0ull, x.lo << (s - 64)};
+    if (s == 0)
+        return x;
+    return {x.lo << s, (x.hi << s) | (x.lo >> (64 - s))};
+}
+
+__device__ __forceinline__ void store_b_vec(uint8_t *base, uint32_t count, int lane, const uint32_t (&rb)[4])
+{
+    uint32_t nx[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        nx[i] = __shfl_down_sync(0xffffffffu, rb[i], 1); // block lane + 1 (lanes without a block hold 0)
+    const U128 a = shr128(u128(rb), 4u * (uint32_t)lane);
+    const U128 b = shl128(u128(nx), 124u - 4u * (uint32_t)lane);
+    const uint32_t c[4] = {(uint32_t)(a.lo | b.lo), (uint32_t)((a.lo | b.lo) >> 32), (uint32_t)(a.hi | b.hi),
+                           (uint32_t)((a.hi | b.hi) >> 32)};
+    const uint32_t off = 16u * (uint32_t)lane;
+    if (off + 16 <= count) {
+        __stcs(reinterpret_cast<uint4 *>(base + off), make_uint4(c[0], c[1], c[2], c[3]));
+    } else {
+#pragma unroll
+        for (uint32_t k = 0; k < 16; ++k)
+            if (off + k < count)
+                base[off + k] = (uint8_t)(c[k >> 2] >> (8 * (k & 3)));
+    }
+}
+
+__device__ __forceinline__ void load_b_vec(const uint8_t *base, uint32_t count, bool valid, int lane,
+                                           uint32_t (&rb)[4])
+{
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    const uint32_t off = 16u * (uint32_t)lane;
+    if (off + 16 <= count) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(base + off));
+        w[0] = v.x;
+        w[1] = v.y;
+        w[2] = v.z;
+        w[3] = v.w;
+    } else {
+#pragma unroll
+        for (uint32_t k = 0; k < 16; ++k)
+            if (off + k < count)
+                w[k >> 2] |= (uint32_t)__ldg(base + off + k) << (8 * (k & 3));
+    }
+    uint32_t pv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        pv[i] = __shfl_up_sync(0xffffffffu, w[i], 1); // chunk lane - 1
+    // block j: the top 4 j bits of chunk j - 1, then chunk j (block 0: chunk 0)
+    const U128 a = shr128(u128(pv), 128u - 4u * (uint32_t)lane);
+    const U128 b = shl128(u128(w), 4u * (uint32_t)lane);
+    if (valid) {
+        rb[0] = (uint32_t)(a.lo | b.lo);
+        rb[1] = (uint32_t)((a.lo | b.lo) >> 32);
+        rb[2] = (uint32_t)(a.hi | b.hi);
+        rb[3] = (uint32_t)((a.hi | b.hi) >> 32) & 0x0fffffffu;
+    }
+}
+
+// the warp's B records out of (into) the registers: vector accesses when
+// the warp's area is 16-byte aligned, else through the shared area sb
+__device__ __forceinline__ void put_b(uint32_t *sb, uint8_t *base, uint32_t count, bool valid, int lane,
+                                      const uint32_t (&rb)[4])
+{
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) == 0)
+        store_b_vec(base, count, lane, rb);
+    else
+        store_b(sb, base, count, valid, lane, rb);
+}
+
+__device__ __forceinline__ void get_b(uint32_t *sb, const uint8_t *base, uint32_t count, bool valid, int lane,
+                                      uint32_t (&rb)[4])
+{
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) == 0)
+        load_b_vec(base, count, valid, lane, rb);
+    else
+        load_b(sb, base, count, valid, lane, rb);
+}
+
 } // namespace pkb
 } // namespace frag
