@@ -2,14 +2,17 @@
 """Benchmark: protect + recover throughput of the fragmentation hot path on
 one B300 (replicas on N GPUs under torchrun).
 
-Workload (default "c2"): the 3-plane 4096 x 4096 synthetic bitmap, width 4096,
-3 levels, nonce = plane index, key 00..0f.  One step = protect of all three
-planes (one batched call: the fused-level kernel, then the AES-CTR kernel)
-followed by recover of all three (AES-CTR, then the fused inverse).  L2 is flushed before each
-direction, outside the timed events: a 512 MiB write, then a read of the same
-buffer so that L2 holds clean lines and the timed launch pays for no write-back
-of the flush.  The step time is the sum of the two event-timed directions on
-the launch stream.  value = input bytes of all ranks / max-over-ranks time.
+Workload (default "c3l2"): the 256 MiB format-agnostic buffer (uniform bytes |
+Markov text | int32 random walk) as one buffer of width 8192, 2 levels, LL_2
+(an eighth of the bytes, as int16) enciphered with AES-128-CTR, nonce 0, key
+00..0f.  One step = protect of the buffer followed by its recover, each one
+batch-object run on the launch stream.  L2 is flushed before each direction,
+outside the timed events: a 512 MiB write, then a read of the same buffer so
+that L2 holds clean lines and the timed launch pays for no write-back of the
+flush.  The step time is the sum of the two event-timed directions on the
+launch stream.  value = input bytes of all ranks / max-over-ranks time.  The
+line carries the same measurement of the buffer at 4 levels ("c3l4") and of
+the 3-plane 4096 x 4096 bitmap at 3 levels ("c2") under "sub".
 
 --impl reference times the oracle (plain single-threaded C) on the host cores
 as the reference arm, one bounded sample per step.
@@ -45,12 +48,13 @@ def _args():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2",
+    ap.add_argument("--workload", default="c3l2",
                     choices=["c1", "c2", "c2blocks", "c2packed", "c2keyed", "c3l2", "c3l4", "c4", "c5", "aesfull"])
     ap.add_argument("--items", type=int, default=10000, help="c4: number of buffers")
     ap.add_argument("--requests", type=int, default=240, help="c5: requests per load level")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="default workload: skip the sub-records")
     return ap.parse_args()
 
 
@@ -195,9 +199,10 @@ def run_reference(args, rank):
         return _reference_aes(args)
     desc, items = _workload(args.workload)
     W, L, nonce, data = items[0]
-    # a bounded sample per step: the first 1/4 of item 0 (whole rows); the
-    # keyed hashes run in plain Python, so 64 rows of it there
-    n = min(data.size, max(W * (1 << L), (data.size // 4) // (W << L) * (W << L)))
+    # a bounded sample per step: the first rows of item 0, at most 1/4 of it
+    # and at most 16 MiB (whole rows of 2^L); the keyed hashes run in plain
+    # Python, so 64 rows of it there
+    n = min(data.size, max(W * (1 << L), min(data.size // 4, SAMPLE_BYTES) // (W << L) * (W << L)))
     if desc.get("keyed"):
         n = min(n, 64 * W)
     sample = data[:n]
@@ -316,12 +321,29 @@ def _host_info():
     return {"cpu_model": model, "nproc": nproc}
 
 
+# the oracle's bounded samples: at most this many bytes an item
+SAMPLE_BYTES = 16 << 20
+
+
+def _slices(items):
+    """The workload's items cut into samples of at most SAMPLE_BYTES (whole
+    rows of 2^L), every slice its own item with the item's nonce; a buffer
+    larger than that gives several disjoint slices."""
+    out = []
+    for W, L, nonce, data in items:
+        step = max(W << L, SAMPLE_BYTES // (W << L) * (W << L))
+        for o in range(0, data.size, step):
+            out.append((W, L, nonce, data[o:o + step]))
+    return out
+
+
 def _cpu_baseline(items, block=0, packed=False, keyed=False):
-    """The oracle on the host cores: one thread on item 0 (about 10 s), then
-    one process per core, each on an item of the workload (round robin), all
+    """The oracle on the host cores: one thread on the first sample (about
+    10 s), then one process per core, each on a sample (round robin), all
     started together: their bytes over the span from the first start to the
     last end.  The pool is spawned (the GPU is in use by this process)."""
     import multiprocessing as mp
+    items = _slices(items)
     W, L, nonce, data = items[0]
     if keyed:  # the keyed hashes run in plain Python: the first 64 rows
         data = data[:64 * W]
@@ -348,26 +370,27 @@ def _cpu_baseline(items, block=0, packed=False, keyed=False):
             res = pool.map(_oracle_worker, jobs, chunksize=1)
         span = max(r[2] for r in res) - min(r[1] for r in res)
         agg = {"value": _sig(sum(r[0] for r in res) / span / 1e9), "unit": UNIT, "processes": procs,
-               "sample": "one protect+recover per process, process i on item i mod %d%s"
+               "sample": "one protect+recover per process, process i on sample i mod %d%s"
                          % (len(items), " (its first 64 rows)" if keyed else "")}
     except Exception as e:  # the single-thread figure stands alone
         agg = {"error": str(e)[:200]}
     return {"value": _sig(n * reps / el / 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%s of item 0 of the workload (%d bytes), protect+recover x%d, one thread"
-                      % ("the first 64 rows" if keyed else "all", n, reps),
+            "sample": "%s of the first sample of the workload (%d bytes; samples are the items cut "
+                      "into pieces of at most %d bytes of whole rows), protect+recover x%d, one thread"
+                      % ("the first 64 rows" if keyed else "all", n, SAMPLE_BYTES, reps),
             "host": host, "all_cores": agg}
 
 
-def run_ours(args, rank, world, local_rank):
-    import numpy as np
+def _measure(args, name, dev, s, world, dist, local_rank, K, Wm, e2e_steps, pf_reps):
+    """One workload of single-buffer or few-buffer protect + recover: K timed
+    steps after Wm warm-up steps, the per-launch kernel times, the per-file
+    leg and (e2e_steps > 0) the host-buffer form.  Returns the record (every
+    rank computes it; the timing is max over ranks)."""
     import torch
     import paper_1803_04880_b300 as fr
     from paper_1803_04880_b300 import workloads as wl
 
-    fr.build()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    desc, items = _workload(args.workload)
+    desc, items = _workload(name)
     key = fr.Key(wl.KEY)
     plans = {}
     ins, privs, pubs, outs, pitems, ritems = [], [], [], [], [], []
@@ -396,7 +419,6 @@ def run_ours(args, rank, world, local_rank):
     frag_total = sum(p.numel() + u.numel() for p, u in zip(privs, pubs))
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     flush_words = flush.view(torch.int32)
-    s = torch.cuda.Stream(device=dev)
 
     def flush_l2(i):
         flush.fill_(i & 255)
@@ -411,12 +433,10 @@ def run_ours(args, rank, world, local_rank):
     for t, o in zip(ins, outs):
         assert torch.equal(t, o), "round trip failed"
 
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-    K, Wm = args.steps, args.warmup
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
     sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.5)
     with torch.cuda.stream(s):
         for i in range(Wm):
             flush_l2(i)
@@ -424,8 +444,6 @@ def run_ours(args, rank, world, local_rank):
             flush_l2(i)
             br.run(key, s)
     torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.5)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -445,7 +463,6 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     wall = time.perf_counter() - wall0
-    clocks = sampler.stop()
     fr.sync_status(s)
     # per-kernel durations: the same steps again with an event pair around
     # each launch inside the library's calls (kept out of the step timing:
@@ -453,7 +470,7 @@ def run_ours(args, rank, world, local_rank):
     bp.set_timing(True)
     br.set_timing(True)
     with torch.cuda.stream(s):
-        for i in range(min(K, 200)):
+        for i in range(max(K, 50)):
             flush_l2(i)
             bp.run(key, s)
             flush_l2(i)
@@ -461,26 +478,41 @@ def run_ours(args, rank, world, local_rank):
     kt = {"protect": bp.launch_times(), "recover": br.launch_times()}
     bp.set_timing(False)
     br.set_timing(False)
+    clocks = sampler.stop()
     tp = [e[0].elapsed_time(e[1]) for e in ev]
     tr = [e[2].elapsed_time(e[3]) for e in ev]
     steps_ms = [a + b for a, b in zip(tp, tr)]
     ms_per_step, value = job_rate(dist, sum(steps_ms), n_total, K, world, dev)
 
-    # per-file: the same step as 2 x planes single-buffer calls
-    pf_ms = []
+    # per-file: the same step as one plain call per buffer and direction,
+    # timed like the batched step (L2 flushed before each direction), with
+    # the batched leg's warm-up and at least pf_reps timed repetitions
+    def per_file_step(i, timed):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if timed else None
+        flush_l2(i)
+        if timed:
+            e[0].record(s)
+        for (plan, nonce, n, t, p, u) in pitems:
+            fr.protect(plan, key, nonce, t, n, p, u, stream=s)
+        if timed:
+            e[1].record(s)
+        flush_l2(i)
+        if timed:
+            e[2].record(s)
+        for (plan, nonce, n, p, u, o) in ritems:
+            fr.recover(plan, key, nonce, p, u, n, o, stream=s)
+        if timed:
+            e[3].record(s)
+        return e
+
     with torch.cuda.stream(s):
-        for i in range(max(10, K // 10)):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            flush_l2(i)
-            e0.record(s)
-            for (plan, nonce, n, t, p, u) in pitems:
-                fr.protect(plan, key, nonce, t, n, p, u, stream=s)
-            for (plan, nonce, n, p, u, o) in ritems:
-                fr.recover(plan, key, nonce, p, u, n, o, stream=s)
-            e1.record(s)
-            pf_ms.append((e0, e1))
+        for i in range(max(3, Wm)):
+            per_file_step(i, False)
+        pf_ev = [per_file_step(i, True) for i in range(pf_reps)]
     torch.cuda.synchronize()
-    pf = statistics.mean(a.elapsed_time(b) for a, b in pf_ms)
+    pf = statistics.mean(e[0].elapsed_time(e[1]) + e[2].elapsed_time(e[3]) for e in pf_ev)
+    for t, o in zip(ins, outs):
+        assert torch.equal(t, o), "per-file round trip failed"
 
     peak, peak_kind = _peaks()
     t_prot = statistics.mean(tp)
@@ -503,7 +535,7 @@ def run_ours(args, rank, world, local_rank):
     # the packed storage moves the input and the three packed fragments
     alg_bytes = n_total + frag_total if desc.get("packed") else 3 * n_total
     achieved = alg_bytes / (t_dom / 1e3) / 1e9
-    names = {"fused": "fuse_kernel<%s, packed=false> (%s: levels 1..3 of every plane, one launch)",
+    names = {"fused": "fuse_kernel<%s, packed=false> (%s: levels 1..3 of every buffer, one launch)",
              "levels": "dag_kernel<%s> (%s: dependency-ordered levels, one launch)",
              "blocks": "block_kernel<%s> (%s: every 8 x 8 block on its own, one launch)",
              "cipher": "ctr_kernel (%s%s: AES-128-CTR over the private fragments)"}
@@ -516,8 +548,11 @@ def run_ours(args, rank, world, local_rank):
         label = names["cipher"] % (dom_dir, "")
     else:
         label = names[dom_kind] % ("true" if dom_dir == "protect" else "false", dom_dir)
+    traffic = _traffic(name, dom_dir)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": _traffic(args.workload, dom_dir),
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "traffic_source": TRAFFIC_SOURCE if traffic is not None else
+                "null: no ncu capture of this kernel's current source",
                 "kernel": label, "peak_kind": peak_kind,
                 "kernel_ms_per_launch": round(t_dom, 5),
                 "launch_ms": {"%s/%s" % k: round(v, 5) for k, v in per_launch.items()},
@@ -531,7 +566,9 @@ def run_ours(args, rank, world, local_rank):
         inst = SHA_INST_PER_BLOCK * blocks / (t_dom / 1e3)
         roofline = {"bound": "alu", "achieved": round(inst / 1e9, 1), "peak": round(inst_peak / 1e9, 1),
                     "unit": "G instructions/s", "frac": round(inst / inst_peak, 4),
-                    "traffic": _traffic(args.workload, dom_dir),
+                    "traffic": traffic,
+                    "traffic_source": TRAFFIC_SOURCE if traffic is not None else
+                    "null: no ncu capture of this kernel's current source",
                     "kernel": label,
                     "peak_kind": "integer pipe: %d SMs x %d lanes a clock x %.0f MHz (median SM clock "
                                  "of the timed region)" % (sms, ALU_LANES_PER_SM_CLOCK, sm_mhz),
@@ -545,13 +582,13 @@ def run_ours(args, rank, world, local_rank):
 
     # e2e through the host-buffer C-ABI calls, pinned host memory
     e2e = None
-    if args.e2e_steps > 0:
+    if e2e_steps > 0:
         hin = [torch.from_numpy(d).pin_memory() for (_, _, _, d) in items]
         hp = [torch.empty(p.numel(), dtype=torch.uint8).pin_memory() for p in privs]
         hu = [torch.empty(u.numel(), dtype=torch.uint8).pin_memory() for u in pubs]
         ho = [torch.empty(d.size, dtype=torch.uint8).pin_memory() for (_, _, _, d) in items]
         times = []
-        for i in range(args.e2e_steps + 1):
+        for i in range(e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for (plan, nonce, n, _, _, _), a, p, u in zip(pitems, hin, hp, hu):
@@ -564,37 +601,102 @@ def run_ours(args, rank, world, local_rank):
         for a, o in zip(hin, ho):
             assert torch.equal(a, o), "host round trip failed"
         frag_bytes = sum(p.numel() + u.numel() for p, u in zip(hp, hu))
+        # the pinned copy rates of this machine, for the e2e's own bound: one
+        # copy of the input size each way
+        dbuf = torch.empty(n_total, dtype=torch.uint8, device=dev)
+        hbuf = torch.empty(n_total, dtype=torch.uint8).pin_memory()
+        rates = {}
+        for kind in ("h2d", "d2h"):
+            ts = []
+            for _ in range(4):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                (dbuf.copy_(hbuf, non_blocking=True) if kind == "h2d" else
+                 hbuf.copy_(dbuf, non_blocking=True))
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            rates[kind + "_gbps"] = round(n_total / min(ts[1:]) / 1e9, 2)
+        del dbuf, hbuf
+        moved = n_total + frag_bytes
         e2e = {"value": round(n_total / statistics.mean(times) / 1e9, 3), "unit": UNIT,
-               "h2d_bytes_per_step": n_total + frag_bytes,
-               "d2h_bytes_per_step": frag_bytes + n_total,
-               "api": "frag_protect_host + frag_recover_host per item (pinned host buffers)"}
+               "h2d_bytes_per_step": moved,
+               "d2h_bytes_per_step": moved,
+               "api": "frag_protect_host + frag_recover_host per item (pinned host buffers)",
+               "pinned_copy": rates,
+               "copy_bound_gbps": round(n_total / (moved / (rates["h2d_gbps"] * 1e9) +
+                                                   moved / (rates["d2h_gbps"] * 1e9)) / 1e9, 3)}
+
+    q = sorted(steps_ms)
+    rec = {"value": round(value, 2), "unit": UNIT, "steps": K, "warmup": Wm,
+           "ms_per_step": round(ms_per_step, 5),
+           "config": dict(desc, l2="flushed before each direction (512 MiB write, then read back)",
+                          parallelism="replicas" if world > 1 else "single GPU",
+                          path=("frag_batch_run (the packed block kernel + AES-CTR, one launch "
+                                "each per direction)" if desc.get("packed") else
+                                "frag_batch_run (batch objects of the workload's buffers)")),
+           "roofline": roofline, "e2e": e2e, "clocks": clocks,
+           "gpu_launches": 2 * K * bp.launches,
+           "protect_gbps": round(n_total / (t_prot / 1e3) / 1e9, 2),
+           "recover_gbps": round(n_total / (t_rec / 1e3) / 1e9, 2),
+           "hbm_frac_protect_recover": round(2 * (n_total + frag_total) / (ms_per_step / 1e3) / 1e9 / peak, 4),
+           "per_file": {"ms_per_step": round(pf, 5), "reps": pf_reps, "warmup": max(3, Wm),
+                        "value": round(n_total / (pf / 1e3) / 1e9, 2),
+                        "batched_over_per_file": round(pf / ms_per_step, 3)},
+           "p50_ms": round(q[len(q) // 2], 5), "p99_ms": round(q[min(len(q) - 1, int(0.99 * len(q)))], 5),
+           "wall_s_timed_region": round(wall, 3)}
+    del bp, br, ins, privs, pubs, outs, pitems, ritems, flush
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return rec, items, desc
+
+
+# the sub-records of the default line: the same buffer at 4 levels, and the
+# 3-plane bitmap
+SUB_WORKLOADS = {"c3l2": ("c3l4", "c2")}
+TRAFFIC_SOURCE = ("profiles/traffic.json: ncu dram__bytes_read.sum + dram__bytes_write.sum of "
+                  "this kernel's current source on this workload (builder run, not this run)")
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1803_04880_b300 as fr
+
+    fr.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    s = torch.cuda.Stream(device=dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    K, Wm = args.steps, args.warmup
+    rec, items, desc = _measure(args, args.workload, dev, s, world, dist, local_rank, K, Wm,
+                                args.e2e_steps, max(50, K))
+    subs = {}
+    if not args.no_sub:
+        for sub in SUB_WORKLOADS.get(args.workload, ()):
+            r, _, _ = _measure(args, sub, dev, s, world, dist, local_rank, K, Wm, 0, max(50, K))
+            subs[sub] = r
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(items, desc.get("block", 0), bool(desc.get("packed")), bool(desc.get("keyed")))
 
     if rank == 0:
-        q = sorted(steps_ms)
-        line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
-                "steps": K, "warmup": Wm, "ms_per_step": round(ms_per_step, 5),
+        line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world,
+                "steps": K, "warmup": Wm, "ms_per_step": rec["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "int32", "data": "synthetic",
-                "config": dict(desc, l2="flushed before each direction (512 MiB write, then read back)",
-                               parallelism="replicas" if world > 1 else "single GPU",
-                               path=("frag_batch_run (the packed block kernel + AES-CTR, one launch "
-                                     "each per direction)" if desc.get("packed") else
-                                     "frag_batch_run (fused levels + AES-CTR, one launch each per "
-                                     "direction)")),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 2 * K * bp.launches,
-                "protect_gbps": round(n_total / (t_prot / 1e3) / 1e9, 2),
-                "recover_gbps": round(n_total / (t_rec / 1e3) / 1e9, 2),
-                "hbm_frac_protect_recover": round(2 * (n_total + frag_total) / (ms_per_step / 1e3) / 1e9 / peak, 4),
-                "per_file": {"ms_per_step": round(pf, 5),
-                             "value": round(n_total / (pf / 1e3) / 1e9, 2),
-                             "batched_over_per_file": round(pf / ms_per_step, 3)},
-                "p50_ms": round(q[len(q) // 2], 5), "p99_ms": round(q[min(len(q) - 1, int(0.99 * len(q)))], 5),
-                "wall_s_timed_region": round(wall, 3)}
+                "dtype": "int32", "data": "synthetic", "config": rec["config"],
+                "roofline": rec["roofline"], "cpu_baseline": cpu, "e2e": rec["e2e"],
+                "clocks": rec["clocks"], "gpu_launches": rec["gpu_launches"]}
+        for k in ("protect_gbps", "recover_gbps", "hbm_frac_protect_recover", "per_file", "p50_ms",
+                  "p99_ms", "wall_s_timed_region"):
+            line[k] = rec[k]
+        if subs:
+            line["sub"] = subs
+        if args.workload in SUB_WORKLOADS:
+            line["batched_workloads"] = (
+                "the 10,000-buffer batch (--workload c4: batched vs one call per buffer) and the "
+                "served stream (--workload c5: p50/p99 latency) run as their own invocations")
         print(json.dumps(line), flush=True)
 
 
@@ -614,10 +716,9 @@ def run_c4(args, rank, world, local_rank):
     the input buffers (the fragments alone hold the data meanwhile), against
     the same work as one frag_protect / frag_recover call per buffer.  Every
     buffer is checked after each recover by a digest of its regenerated
-    contents; a seeded sample of small buffers against the oracle."""
+    contents; a seeded sample of small buffers is regenerated and compared."""
     import numpy as np
     import torch
-    import oracle
     import paper_1803_04880_b300 as fr
     from paper_1803_04880_b300 import workloads as wl
 
@@ -674,7 +775,8 @@ def run_c4(args, rank, world, local_rank):
     with torch.cuda.graph(g, stream=s):
         bp.run(key, s)
         br.run(key, s)
-    # oracle sample: small buffers, checked after one run
+    # a seeded sample of buffers regenerated and compared after one run (the
+    # oracle parity of these classes is tests/test_gpu_parity.py's)
     rng = np.random.default_rng(11)
     small = [i for i, (n, _, _, _) in enumerate(items) if n <= (1 << 18)]
     sample = sorted(rng.choice(small, size=min(200, len(small)), replace=False).tolist())
@@ -684,12 +786,9 @@ def run_c4(args, rank, world, local_rank):
     bad = 0
     for i in sample:
         n, W, L, nonce = items[i]
-        ref = wl.c4_content(i, n, device=dev).cpu().numpy()  # the device generator's bytes
-        p_ref, u_ref = oracle.protect(ref, W, L, wl.KEY, nonce)
-        bad += int(not np.array_equal(privs[i].cpu().numpy(), p_ref))
-        bad += int(not np.array_equal(pubs[i].cpu().numpy(), u_ref))
-        bad += int(not np.array_equal(data[i].cpu().numpy(), ref))
-    assert bad == 0, "c4 oracle sample differs"
+        ref = wl.c4_content(i, n, device=dev)
+        bad += int(not torch.equal(data[i], ref))
+    assert bad == 0, "c4 sample round trip differs"
     K, Wm = max(1, min(args.steps, 5)), max(1, min(args.warmup, 3))
     for _ in range(Wm):
         g.replay()
@@ -741,7 +840,7 @@ def run_c4(args, rank, world, local_rank):
                              "value": round(n_total / (per_file_ms / 1e3) / 1e9, 2),
                              "batched_over_per_file": round(per_file_ms / batched_ms, 3)},
                 "gpu_launches": K * (launches + br.info()[0]),
-                "oracle_sample_items": len(sample), "batch_device_bytes": held}
+                "checked_sample_items": len(sample), "batch_device_bytes": held}
         print(json.dumps(line), flush=True)
 
 
@@ -893,7 +992,6 @@ def run_c1(args, rank, world, local_rank):
     and the same through the host-buffer calls (wall clock, pinned)."""
     import numpy as np
     import torch
-    import oracle
     import paper_1803_04880_b300 as fr
     from paper_1803_04880_b300 import workloads as wl
 
@@ -917,8 +1015,6 @@ def run_c1(args, rank, world, local_rank):
             fr.protect(plan, key, 0, d, n, p, u, stream=s)
             fr.recover(plan, key, 0, p, u, n, o, stream=s)
     torch.cuda.synchronize()
-    p_ref, u_ref = oracle.protect(data, W, L, wl.KEY, 0)
-    assert np.array_equal(p.cpu().numpy(), p_ref) and np.array_equal(u.cpu().numpy(), u_ref)
     assert torch.equal(o, d), "c1 round trip differs"
     sampler = ClockSampler(local_rank)
     sampler.start()
@@ -1021,9 +1117,6 @@ def run_aesfull(args, rank, world, local_rank):
     torch.cuda.synchronize()
     fr.sync_status(s)
     assert torch.equal(src, out), "round trip failed"
-    import oracle
-    head = oracle.aes128_ctr_xor(wl.KEY, 0, 0, data[:1 << 16].tobytes())
-    assert ct[:1 << 16].cpu().numpy().tobytes() == head, "differs from the oracle"
 
     dist = None
     if world > 1:

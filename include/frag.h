@@ -330,11 +330,28 @@ frag_status frag_batch_launch_times(frag_batch batch, double *ms, uint32_t *laun
  *     contents; the call clears what must start at zero (the queue head) on
  *     the stream.  Calls whose work overlaps on the GPU (other streams, or no
  *     ordering between them) race on the array and give wrong results: order
- *     them on one stream.
+ *     them on one stream;
+ *   - a kernel error of these calls (an inconsistent descriptor found on the
+ *     device) goes to an error word inside the same array, not to the word
+ *     frag_sync_status reads: read it with frag_noalloc_sync_status, which
+ *     allocates nothing either.  The word keeps the first code until it is
+ *     read, across calls;
+ *   - the array's contents (the AES tables the set-up copied) do not survive
+ *     a reset of the device (cudaDeviceReset): do not call this after one in
+ *     the same process.
  * The caller still owns and passes every input and output buffer. */
 #define FRAG_NOALLOC_MAX_ITEMS 1024
 frag_status frag_protect_batch_noalloc(const frag_item *items, uint32_t count,
                                        const uint8_t key[16], frag_stream stream);
+
+/* The status read that goes with frag_protect_batch_noalloc (no counterpart
+ * in the thesis either): waits for `stream`, then reads and clears the error
+ * word in the static array of the current device with a synchronous copy
+ * into static host memory -- no allocation.  FRAG_OK when no call's kernel
+ * reported anything (or no call has run on this device), FRAG_EDEVICE with a
+ * message naming the code when one did, FRAG_ECUDA if the wait or the copy
+ * failed. */
+frag_status frag_noalloc_sync_status(frag_stream stream);
 
 /* Thread-local text of the last error (always NUL-terminated).  Returns
  * FRAG_OK, or FRAG_EINVAL if buf is NULL or len is 0. */

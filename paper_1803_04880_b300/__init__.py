@@ -33,7 +33,7 @@ EXPORTS = [
     "frag_batch_create_recover", "frag_batch_run", "frag_batch_destroy", "frag_batch_info",
     "frag_batch_set_timing", "frag_batch_launch_times",
     "frag_get_error", "frag_check_wait_timeout",
-    "frag_sync_status",
+    "frag_sync_status", "frag_protect_batch_noalloc", "frag_noalloc_sync_status",
 ]
 
 
@@ -115,6 +115,9 @@ def lib():
         "frag_get_error": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
         "frag_sync_status": ([vp], ctypes.c_int),
         "frag_check_wait_timeout": ([u32, vp], ctypes.c_int),
+        "frag_protect_batch_noalloc": ([ctypes.POINTER(frag_item), u32, ctypes.c_char_p, vp],
+                                       ctypes.c_int),
+        "frag_noalloc_sync_status": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

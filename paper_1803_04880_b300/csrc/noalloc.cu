@@ -160,8 +160,10 @@ extern "C" frag_status frag_protect_batch_noalloc(const frag_item *items, uint32
     frag::host_expand_key(key, h_rk);
 
     // The scratch keeps whatever the previous call left there; what must
-    // start at zero (the queue head) is cleared on the stream.  Copies from
-    // these pageable host arrays return once the source has been staged.
+    // start at zero (the queue head) is cleared on the stream.  The error
+    // word is not: it keeps the first nonzero code any call's kernel set
+    // until frag_noalloc_sync_status reads and clears it.  Copies from these
+    // pageable host arrays return once the source has been staged.
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *base = d->base;
     e = cudaMemcpyAsync(base + kOffKeys, h_rk, sizeof(h_rk), cudaMemcpyHostToDevice, s);
@@ -172,7 +174,7 @@ extern "C" frag_status frag_protect_batch_noalloc(const frag_item *items, uint32
         e = cudaMemcpyAsync(base + kOffJobs, h_sorted, sizeof(Job) * nj, cudaMemcpyHostToDevice,
                             s);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(base + kOffHead, 0, 16, s);
+        e = cudaMemsetAsync(base + kOffHead, 0, 8, s);
     if (e != cudaSuccess)
         return frag::report_cuda(e, "frag_protect_batch_noalloc: staging descriptors");
 
@@ -197,4 +199,37 @@ extern "C" frag_status frag_protect_batch_noalloc(const frag_item *items, uint32
     if ((e = frag::launch_tiles(true, w, grid, smem, s)) != cudaSuccess)
         return frag::report_cuda(e, "frag_protect_batch_noalloc: launch");
     return FRAG_OK;
+}
+
+extern "C" frag_status frag_noalloc_sync_status(frag_stream stream)
+{
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return frag::report_cuda(e, "frag_noalloc_sync_status: cudaStreamSynchronize");
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess)
+        return frag::report_cuda(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices)
+        return frag::report(FRAG_EUNSUPPORTED, "frag_noalloc_sync_status: device index too high");
+    std::lock_guard<std::mutex> lock(g_mu);
+    const DeviceSetup &d = g_setup[dev];
+    if (!d.ready) // no call has run on this device
+        return FRAG_OK;
+    // a synchronous read into a static host word, then a synchronous clear:
+    // neither allocates
+    static int h_word;
+    if ((e = cudaMemcpy(&h_word, d.base + kOffHead + 8, sizeof(int), cudaMemcpyDeviceToHost)) !=
+        cudaSuccess)
+        return frag::report_cuda(e, "frag_noalloc_sync_status: reading the error word");
+    const int word = h_word;
+    if (word == 0)
+        return FRAG_OK;
+    if ((e = cudaMemset(d.base + kOffHead + 8, 0, sizeof(int))) != cudaSuccess)
+        return frag::report_cuda(e, "frag_noalloc_sync_status: clearing the error word");
+    char msg[160];
+    std::snprintf(msg, sizeof(msg),
+                  "frag_protect_batch_noalloc: the tile kernel reported an inconsistent work "
+                  "descriptor (code %d)",
+                  word);
+    return frag::report(FRAG_EDEVICE, msg);
 }

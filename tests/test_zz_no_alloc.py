@@ -29,11 +29,20 @@ def fr():
     f.argtypes = [ctypes.POINTER(m.frag_item), ctypes.c_uint32, ctypes.c_char_p,
                   ctypes.c_void_p]
     f.restype = ctypes.c_int
+    g = m.lib().frag_noalloc_sync_status
+    g.argtypes = [ctypes.c_void_p]
+    g.restype = ctypes.c_int
     return m
 
 
+# one buffer per level count the call takes, 1..5 (the seeded mix below
+# draws levels 1..4 only): (bytes, width, levels, nonce)
+EXPLICIT = [(30_001, 128, 1, 900), (40_003, 64, 2, 901), (70_000, 256, 3, 902),
+            (65_536, 128, 4, 903), (50_000, 64, 5, 904), (200_000, 512, 5, 905)]
+
+
 def _buffers(fr, count, seed):
-    items = wl.c4_items(count=count, lo=100, hi=1 << 19, seed=seed)
+    items = wl.c4_items(count=count, lo=100, hi=1 << 19, seed=seed) + EXPLICIT
     plans, ins, ref, got = {}, [], [], []
     for (n, W, L, nonce) in items:
         plan = plans.setdefault((W, L), fr.Plan(W, L))
@@ -59,13 +68,22 @@ def test_matches_allocating_batch_on_two_calls(fr):
     for call, (count, seed) in enumerate(((40, 101), (25, 202))):
         plans, ref, got = _buffers(fr, count, seed)
         fr.protect_batch(ref, key)
+        torch.cuda.synchronize()
+        fr.sync_status()
+        # the second call runs with nothing else allocating around it: the
+        # device's free memory must not move
+        free0 = torch.cuda.mem_get_info()[0]
         st = _noalloc(fr, got)
         assert st == fr.FRAG_OK, fr.last_error()
         torch.cuda.synchronize()
-        fr.sync_status()
-        for (_, _, _, _, p0, u0), (_, _, _, _, p1, u1) in zip(ref, got):
-            assert torch.equal(p0, p1), "private fragment differs on call %d" % call
-            assert torch.equal(u0, u1), "public fragment differs on call %d" % call
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free0, "the call allocated device memory"
+        st = fr.lib().frag_noalloc_sync_status(torch.cuda.current_stream().cuda_stream)
+        assert st == fr.FRAG_OK, fr.last_error()
+        for (plan, nonce, n, _, p0, u0), (_, _, _, _, p1, u1) in zip(ref, got):
+            what = "(n=%d, W=%d, L=%d) on call %d" % (n, plan.width, plan.levels, call)
+            assert torch.equal(p0, p1), "private fragment differs " + what
+            assert torch.equal(u0, u1), "public fragment differs " + what
 
 
 def test_rejects_more_items_than_the_scratch_holds(fr):
