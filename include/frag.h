@@ -81,8 +81,9 @@ int frag_abi_version(void);
 /* Plan = matrix width W and number of levels L (Sec. 5.2.1: the chunk is a
  * matrix of configurable size; Sec. 5.1.1: two levels in the thesis, L here).
  * FRAG_EINVAL if out is NULL, levels == 0, levels > 8, width == 0 or width is
- * not a multiple of 2^levels; FRAG_EUNSUPPORTED for any other filter and for
- * 6 to 8 levels (the level kernel keeps at most 5 levels of a tile). */
+ * not a multiple of 2^levels; FRAG_EUNSUPPORTED for any other filter.  Every
+ * call takes 1..8 levels except the allocation-free one (at most 5) and the
+ * block mode (at most 3). */
 frag_status frag_plan_create(frag_plan *out, uint32_t width, uint32_t levels, frag_filter filter);
 frag_status frag_plan_destroy(frag_plan plan);
 
@@ -119,12 +120,28 @@ frag_status frag_plan_get_schedule(frag_plan plan, uint32_t *seg_rows, uint32_t 
  * input (protect) or output (recover) is 8-byte aligned, the level-1 bands
  * are 8-byte and the level-2 and level-3 bands 4-byte aligned, and, when the
  * fused levels are all of them (protect), the private fragment is 4-byte
- * aligned (8-byte with one level); the levels above, and buffers that do not
- * meet those conditions, run in the dependency-ordered level kernel.
- * FRAG_PATH_LEVELS: every level in the dependency-ordered kernel.  Results do
- * not depend on the path.  FRAG_EINVAL for a NULL plan or an unknown path;
- * get: FRAG_EINVAL if path is NULL. */
-typedef enum { FRAG_PATH_AUTO = 0, FRAG_PATH_LEVELS = 1 } frag_path;
+ * aligned (8-byte with one level); levels 4..6 of such a buffer run in a
+ * second fused pass over LL_3 under the same conditions one level down.  The
+ * levels above, and buffers that do not meet those conditions, run in the
+ * dependency-ordered level kernel.  The private fragment is enciphered by the
+ * AES-CTR launch after the levels (protect) and deciphered by it before them
+ * (recover), or, with three or more levels in the level kernel, by cipher
+ * units inside that kernel's launch.
+ * FRAG_PATH_LEVELS: every level in the dependency-ordered kernel.
+ * FRAG_PATH_FUSED_CIPHER: as AUTO, but when the fused passes reach level L
+ * the last of them also enciphers LL_L with AES-128-CTR before storing it
+ * (protect), or deciphers it right after loading it (recover, private
+ * fragment 4-byte aligned, 8-byte with one fused level in that pass), so the
+ * private fragment makes no extra trip through memory (measured slower than
+ * AUTO on this GPU: the cipher's table lookups then share the fused kernel's
+ * issue slots and shared memory).  Results do not depend on the path.
+ * FRAG_EINVAL for a NULL plan or an unknown path; get: FRAG_EINVAL if path is
+ * NULL. */
+typedef enum {
+    FRAG_PATH_AUTO = 0,
+    FRAG_PATH_LEVELS = 1,
+    FRAG_PATH_FUSED_CIPHER = 2
+} frag_path;
 frag_status frag_plan_set_path(frag_plan plan, frag_path path);
 frag_status frag_plan_get_path(frag_plan plan, frag_path *path);
 
@@ -302,7 +319,7 @@ typedef enum {
     FRAG_KERNEL_LEVELS = 1, /* the dependency-ordered level kernel */
     FRAG_KERNEL_CIPHER = 2, /* AES-128-CTR over private fragments */
     FRAG_KERNEL_BLOCKS = 3, /* block mode (frag_plan_set_block) */
-    FRAG_KERNEL_FUSED_LOW = 4, /* levels 4..5 in one pass over the level-3 LL */
+    FRAG_KERNEL_FUSED_LOW = 4, /* levels 4..6 in one pass over the level-3 LL */
     FRAG_KERNEL_KINDS = 5
 } frag_kernel_kind;
 frag_status frag_batch_set_timing(frag_batch batch, int enable);

@@ -182,9 +182,11 @@ class Plan:
 
     PATH_AUTO = 0    # levels 1..min(L, 3) fused in one pass where alignment allows
     PATH_LEVELS = 1  # every level in the dependency-ordered kernel
+    PATH_FUSED_CIPHER = 2  # AUTO, with LL_L enciphered inside the fused pass that reaches it
 
     def set_path(self, path: int) -> None:
-        """Kernels that run the levels (PATH_AUTO or PATH_LEVELS); results do
+        """Kernels that run the levels (PATH_AUTO, PATH_LEVELS or
+        PATH_FUSED_CIPHER); results do
         not depend on it."""
         check(lib().frag_plan_set_path(self._h, path))
 

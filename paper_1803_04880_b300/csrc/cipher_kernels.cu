@@ -1,113 +1,43 @@
-// cipher_kernels.cu -- AES-128-CTR over large private fragments in a launch
-// of its own.
+// cipher_kernels.cu -- AES-128-CTR over private fragments in a launch of
+// their own (Sec. 5.2.1: the private fragment is encrypted with AES; CTR as
+// in SP 800-38A).
 //
-// With one or two levels the private fragment (LL_L as int16) is half or an
-// eighth of the input, and the cipher, not the transform, bounds the time.
-// This kernel keeps one AES table in shared memory replicated once per lane
-// (entry x of lane t at word 32 x + t), so the 32 lookups of a warp always
-// fall in 32 different banks; the other three tables of the 32-bit table
-// form are byte rotations of the first (FIPS-197 Sec. 5.1 combined into
-// table lookups), and the last round's S-box is a byte of the same entry.
-// The counter block is nonce (8 bytes big-endian) || block index (8 bytes
-// big-endian); out = in XOR keystream, in may equal out.  The keystream does
-// not depend on the data, so the kernel is launched as a programmatic
-// dependent of the kernel before it: it builds its table and its first
-// keystream blocks while that kernel still runs, and waits for it only
-// before reading the fragment.  Buffers with three
-// or more levels keep their cipher units inside the dependency-ordered
-// launch, where the fragment is small.
-#include "frag_internal.cuh"
+// Buffers whose levels the fused kernel does not finish, the block mode, the
+// packed fragments and the full-buffer comparator encipher here.  The kernel
+// uses the two-table AES of aes_tt.cuh: T0 and T2 once per lane in 64 KB of
+// shared memory placed on a 64 KB boundary of the shared window, so every
+// lookup is one byte permute and one shared load, and a round column one
+// rotation.  One block of 1024 threads an SM; work goes by warps: a warp
+// takes a chunk of a fragment (a chunk of the chunk list, or a slice of a
+// lone fragment) and its lanes take every 32nd block of it.  The round-1
+// constants of the chunk's nonce are computed once per chunk (only the
+// low block word varies within it).  The counter block is nonce (8 bytes
+// big-endian) || block index (8 bytes big-endian); out = in XOR keystream,
+// in may equal out.  Launched as a programmatic dependent of the kernel
+// before it: the table is built while that kernel drains, and the fragment
+// is read only after griddepcontrol.wait.
+#include "aes_tt.cuh"
 
 namespace frag {
 
-constexpr int kCtrThreads = 256;
+// dynamic shared memory: enough to place the 64 KB table on a 64 KB window
+// boundary wherever the dynamic part starts, from 0 up to 64 KB
+constexpr size_t kCtrSmem = 2 * aes::kDualBytes;
 
-struct __align__(16) CtrSmem {
-    uint32_t te[256 * 32]; // table 0, one copy per lane
-    uint4 rk[11];          // round keys, one 16-byte load per round
-    uint4 rk_last_le;      // last round key with its bytes in stream order
-};
-
-// byte k of v, zero-extended
-__device__ __forceinline__ uint32_t byte_of(uint32_t v, uint32_t k) { return __byte_perm(v, 0u, 0x4440u | k); }
-
-// entry x of table 0 (lane-replicated: word 32 x + lane, so one multiply-add
-// gives the address)
-__device__ __forceinline__ uint32_t t0(const uint32_t *tel, uint32_t x) { return tel[x << 5]; }
-
-// rotations by whole bytes: tables 1..3 from table 0
-__device__ __forceinline__ uint32_t ror8(uint32_t v) { return __byte_perm(v, v, 0x0321); }
-__device__ __forceinline__ uint32_t ror16(uint32_t v) { return __byte_perm(v, v, 0x1032); }
-__device__ __forceinline__ uint32_t ror24(uint32_t v) { return __byte_perm(v, v, 0x2103); }
-
-// one AES-128 block (FIPS-197 cipher, 32-bit table form) of the counter
-// block nonce || blk; the keystream words come back with their bytes in
-// stream order (ks[0] byte 0 is keystream byte 0), ready to XOR with
-// little-endian loads
-__device__ __forceinline__ void ctr_block(const CtrSmem &m, uint32_t lane, uint64_t nonce,
-                                          uint64_t blk, uint32_t ks[4])
-{
-    const uint32_t *tel = m.te + lane;
-    const uint4 k0 = m.rk[0];
-    uint32_t s0 = (uint32_t)(nonce >> 32) ^ k0.x;
-    uint32_t s1 = (uint32_t)nonce ^ k0.y;
-    uint32_t s2 = (uint32_t)(blk >> 32) ^ k0.z;
-    uint32_t s3 = (uint32_t)blk ^ k0.w;
-#pragma unroll
-    for (int r = 1; r < 10; ++r) {
-        const uint4 k = m.rk[r];
-        const uint32_t n0 = t0(tel, byte_of(s0, 3)) ^ ror8(t0(tel, byte_of(s1, 2))) ^
-                            ror16(t0(tel, byte_of(s2, 1))) ^ ror24(t0(tel, byte_of(s3, 0))) ^ k.x;
-        const uint32_t n1 = t0(tel, byte_of(s1, 3)) ^ ror8(t0(tel, byte_of(s2, 2))) ^
-                            ror16(t0(tel, byte_of(s3, 1))) ^ ror24(t0(tel, byte_of(s0, 0))) ^ k.y;
-        const uint32_t n2 = t0(tel, byte_of(s2, 3)) ^ ror8(t0(tel, byte_of(s3, 2))) ^
-                            ror16(t0(tel, byte_of(s0, 1))) ^ ror24(t0(tel, byte_of(s1, 0))) ^ k.z;
-        const uint32_t n3 = t0(tel, byte_of(s3, 3)) ^ ror8(t0(tel, byte_of(s0, 2))) ^
-                            ror16(t0(tel, byte_of(s1, 1))) ^ ror24(t0(tel, byte_of(s2, 0))) ^ k.w;
-        s0 = n0;
-        s1 = n1;
-        s2 = n2;
-        s3 = n3;
-    }
-    // last round: SubBytes, ShiftRows, AddRoundKey.  S[x] is byte 1 (and 2)
-    // of table-0 entry x; the output bytes go straight to stream order.
-    auto sub4 = [&](uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-        const uint32_t lo = __byte_perm(t0(tel, byte_of(a, 3)), t0(tel, byte_of(b, 2)), 0x0051);
-        const uint32_t hi = __byte_perm(t0(tel, byte_of(c, 1)), t0(tel, byte_of(d, 0)), 0x0051);
-        return __byte_perm(lo, hi, 0x5410);
-    };
-    const uint4 kl = m.rk_last_le;
-    ks[0] = sub4(s0, s1, s2, s3) ^ kl.x;
-    ks[1] = sub4(s1, s2, s3, s0) ^ kl.y;
-    ks[2] = sub4(s2, s3, s0, s1) ^ kl.z;
-    ks[3] = sub4(s3, s0, s1, s2) ^ kl.w;
-}
-
-__global__ void __launch_bounds__(kCtrThreads) ctr_kernel(CtrWork w)
+__global__ void __launch_bounds__(kCtrThreads, 1) ctr_kernel(CtrWork w)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    CtrSmem &m = *reinterpret_cast<CtrSmem *>(smem);
     grid_release();
-    // table 0 into shared memory, one copy per lane: each warp takes 32
-    // entries with one coalesced load and writes entry x as 32 consecutive
-    // words (x, lane), conflict-free
     const uint32_t lane = threadIdx.x & 31;
-    for (uint32_t base = (threadIdx.x >> 5) * 32; base < 256; base += (blockDim.x >> 5) * 32) {
-        const uint32_t v = __ldg(w.aes_tables + base + lane);
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k)
-            m.te[(base + k) * 32 + lane] = __shfl_sync(0xffffffffu, v, k);
-    }
-    for (int i = threadIdx.x; i < 44; i += blockDim.x) {
-        const uint32_t k = w.round_keys[i];
-        (&m.rk[0].x)[i] = k;
-        if (i >= 40)
-            (&m.rk_last_le.x)[i - 40] = __byte_perm(k, 0, 0x0123);
-    }
+    const uint32_t tab = aes::dual_table_at((uint32_t)__cvta_generic_to_shared(smem));
+    aes::build_dual(tab, w.aes_tables);
     __syncthreads();
+    const aes::Lut L = aes::make_lut(tab, lane);
+    grid_wait(); // the fragment is complete from here on
     const uint64_t nchunks = w.chunks ? w.nchunks
                                       : (w.single.nblocks + w.single_chunk - 1) / w.single_chunk;
-    for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const uint64_t warps = (uint64_t)gridDim.x * (kCtrThreads / 32);
+    for (uint64_t c = (uint64_t)blockIdx.x * (kCtrThreads / 32) + (threadIdx.x >> 5); c < nchunks; c += warps) {
         CtrChunk ch;
         if (w.chunks) {
             ch = w.chunks[c];
@@ -117,17 +47,22 @@ __global__ void __launch_bounds__(kCtrThreads) ctr_kernel(CtrWork w)
             ch.nblocks = min(w.single_chunk, w.single.nblocks - ch.first_block);
         }
         const bool vec = (((uintptr_t)ch.in | (uintptr_t)ch.out) & 15u) == 0;
-        for (uint64_t i = threadIdx.x; i < ch.nblocks; i += blockDim.x) {
+        aes::Round1 R = aes::round1_consts(L, w.keys, ch.nonce, (uint32_t)(ch.first_block >> 32));
+        for (uint64_t i = lane; i < ch.nblocks; i += 32) {
             const uint64_t b = ch.first_block + i;
-            uint32_t ks[4];
-            ctr_block(m, lane, ch.nonce, b, ks);
-            grid_wait(); // the fragment is complete from here on (returns at once after the first)
+            if ((uint32_t)(b >> 32) != R.hi) // a 2^32-block boundary (fragments of 64 GiB)
+                R = aes::round1_consts(L, w.keys, ch.nonce, (uint32_t)(b >> 32));
             const uint64_t o = 16 * b;
-            if (vec && o + 16 <= ch.bytes) {
-                // L2-coherent load: the kernel before this one wrote the
-                // fragment while this grid was already resident, so the
-                // read-only (non-coherent) path is not allowed here
-                const uint4 t = __ldcg(reinterpret_cast<const uint4 *>(ch.in + o));
+            const bool whole = vec && o + 16 <= ch.bytes;
+            // L2-coherent load, issued before the rounds: the kernel before
+            // this one wrote the fragment while this grid was already
+            // resident, so the read-only (non-coherent) path is not allowed
+            uint4 t = make_uint4(0, 0, 0, 0);
+            if (whole)
+                t = __ldcg(reinterpret_cast<const uint4 *>(ch.in + o));
+            uint32_t ks[4];
+            aes::ctr_block2(L, w.keys, R, (uint32_t)b, ks);
+            if (whole) {
                 uint4 r;
                 r.x = t.x ^ ks[0];
                 r.y = t.y ^ ks[1];
@@ -145,7 +80,7 @@ __global__ void __launch_bounds__(kCtrThreads) ctr_kernel(CtrWork w)
 static cudaError_t ctr_attr()
 {
     return cudaFuncSetAttribute((const void *)ctr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(CtrSmem));
+                                (int)kCtrSmem);
 }
 
 cudaError_t launch_ctr(const CtrWork &w, uint32_t grid, cudaStream_t stream)
@@ -156,7 +91,7 @@ cudaError_t launch_ctr(const CtrWork &w, uint32_t grid, cudaStream_t stream)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kCtrThreads);
-    cfg.dynamicSmemBytes = sizeof(CtrSmem);
+    cfg.dynamicSmemBytes = kCtrSmem;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -172,7 +107,7 @@ cudaError_t ctr_occupancy(int *blocks_per_sm)
     if (e != cudaSuccess)
         return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void *)ctr_kernel,
-                                                         kCtrThreads, sizeof(CtrSmem));
+                                                         kCtrThreads, kCtrSmem);
 }
 
 } // namespace frag

@@ -4,6 +4,7 @@
 // resident on each device that uses them, and every device gets one copy of
 // the AES tables and a device error word.  All work is enqueued on the
 // caller's stream; nothing here falls back to the CPU.
+#include "aes_tt.cuh"
 #include "frag.h"
 #include "frag_internal.cuh"
 
@@ -44,7 +45,7 @@ struct frag_key_s {
 namespace {
 
 constexpr uint32_t kMaxLevels = 8;
-constexpr uint32_t kMaxFusedLevels = 5; // one tile window in shared memory
+constexpr uint32_t kMaxTileLevels = 5; // the tile kernel: one tile window in shared memory
 constexpr uint32_t kDefaultTile = 64;
 
 thread_local char g_err[512] = "";
@@ -266,6 +267,9 @@ frag_status fill_job(frag_plan plan, uint64_t nonce, uint64_t n, Job &j)
 {
     if (plan->block)
         return fail(FRAG_EUNSUPPORTED, "the allocation-free call does not take block plans");
+    if (plan->levels > kMaxTileLevels)
+        return fail(FRAG_EUNSUPPORTED, "the allocation-free call takes at most %u levels, got %u",
+                    kMaxTileLevels, plan->levels);
     const uint64_t H = rows_for(n, plan->width, plan->levels);
     if (H > 0xFFFFFFFFull || H * (uint64_t)plan->width / plan->width != H)
         return fail(FRAG_EINVAL, "buffer of %llu bytes is too tall for width %u",
@@ -333,15 +337,18 @@ void packed_sizes(uint64_t H, uint32_t W, uint64_t *a, uint64_t *b, uint64_t *c,
 // keeps LL_1 .. LL_{F-1} on chip and hands LL_F over in scratch when levels
 // remain above it
 uint32_t scratch_lo(uint32_t F) { return F > 1 ? F : 1; }
-uint32_t scratch_hi(bool fwd, uint32_t L) { return fwd ? L - 1 : L; }
+// kc: the fused kernel deciphers LL_L as it loads it (no plaintext copy)
+uint32_t scratch_hi(bool fwd, uint32_t L, bool kc = false) { return fwd || kc ? L - 1 : L; }
 
 // scratch of one buffer: LL_lo .. LL_{L-1}, each in its own region (the jobs
 // of one buffer run concurrently, so no region can be reused), and for the
-// inverse the deciphered LL_L; off[l] is the offset of LL_l
-uint64_t scratch_bytes(bool fwd, uint32_t H, uint32_t W, uint32_t L, uint32_t F, uint64_t *off)
+// inverse the deciphered LL_L unless the fused kernel deciphers it on chip;
+// off[l] is the offset of LL_l
+uint64_t scratch_bytes(bool fwd, uint32_t H, uint32_t W, uint32_t L, uint32_t F, uint64_t *off,
+                       bool kc = false)
 {
     uint64_t total = 0;
-    for (uint32_t l = scratch_lo(F); l <= scratch_hi(fwd, L); ++l) {
+    for (uint32_t l = scratch_lo(F); l <= scratch_hi(fwd, L, kc); ++l) {
         if (off)
             off[l] = total;
         total += align256(ll_bytes(H, W, l));
@@ -356,6 +363,7 @@ struct Buf {
     uint32_t block;    // block mode (every level in the block kernel)
     uint32_t packed;   // block mode with the packed three fragments
     uint32_t keyed;    // packed: B and C protected by the keyed hashes
+    uint32_t kc;       // the fused pass of level L enciphers / deciphers LL_L on chip
     uint32_t R0;       // level-0 rows per work segment
     uint32_t R0_plan;  // the plan's choice (0: adaptive)
     uint64_t n, nonce;
@@ -475,6 +483,10 @@ bool separate_cipher(const Buf &b)
 
 uint32_t buffer_njobs(const Buf &b) { return (b.L - b.F) + (separate_cipher(b) ? 0 : 1); }
 
+// the private fragment goes through the separate CTR launch: enciphered
+// neither by the fused kernel nor by cipher units of the level kernel
+bool ctr_pass(const Buf &b) { return separate_cipher(b) && !b.kc; }
+
 // the jobs of one buffer in the dependency-ordered launch, in processing
 // order (forward: levels F+1..L, then the cipher; inverse: the cipher, then
 // levels L..F+1); each reads what the previous one writes
@@ -585,7 +597,7 @@ frag::CtrChunk ctr_fragment(bool fwd, const Buf &b)
     return c;
 }
 
-frag_status ctr_launch(DeviceState &d, const uint32_t *rk, const frag::CtrChunk *chunks,
+frag_status ctr_launch(DeviceState &d, const frag::AesKeys &keys, const frag::CtrChunk *chunks,
                        uint64_t nchunks, const frag::CtrChunk *single, cudaStream_t s)
 {
     int occ = 0;
@@ -610,17 +622,19 @@ frag_status ctr_launch(DeviceState &d, const uint32_t *rk, const frag::CtrChunk 
     if (single)
         w.single = *single;
     w.aes_tables = d.tables;
-    w.round_keys = rk;
+    w.keys = keys;
     const uint64_t slots = (uint64_t)d.sms * occ;
     if (!chunks) {
-        // a lone fragment spread over every resident CTA, whole thread turns
-        const uint64_t per = (single->nblocks + slots - 1) / slots;
-        w.single_chunk = std::max<uint64_t>(256, (per + 255) / 256 * 256);
+        // a lone fragment spread over every resident warp, whole warp turns
+        const uint64_t warps = slots * (frag::kCtrThreads / 32);
+        const uint64_t per = (single->nblocks + warps - 1) / warps;
+        w.single_chunk = std::max<uint64_t>(32, (per + 31) / 32 * 32);
     }
     const uint64_t work = chunks ? nchunks : (single->nblocks + w.single_chunk - 1) / w.single_chunk;
     if (work == 0)
         return FRAG_OK;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(slots, work);
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(slots, (work + frag::kCtrThreads / 32 - 1) /
+                                                                    (frag::kCtrThreads / 32));
     cudaError_t e = frag::launch_ctr(w, grid, s);
     if (e != cudaSuccess)
         return cuda_fail(e, "cipher launch");
@@ -652,10 +666,12 @@ uint32_t pass_levels(bool fwd, const Buf &b, uint32_t lo)
 
 // how buffer b splits over the fused passes: the first (bytes in / out)
 // takes levels 1 .. F1 (up to 3), a second over the packed LL_3 scratch
-// levels 4 .. 3 + F2; the level kernel takes the rest
+// levels 4 .. 3 + F2 (up to level 6); the level kernel takes the rest
+// (levels 7 and 8, or every level of a buffer neither pass takes)
 void fused_split(bool fwd, Buf &b, uint32_t path)
 {
     b.F1 = b.F2 = 0;
+    b.kc = 0;
     if (b.block)
         b.F1 = b.L; // every level in the block kernel (no scratch but LL_L on recover)
     else if (path != FRAG_PATH_LEVELS && (fwd ? aligned(b.in, 8) : aligned(b.out, 8)))
@@ -663,6 +679,14 @@ void fused_split(bool fwd, Buf &b, uint32_t path)
     if (!b.block && b.F1 == frag::kFuseMaxLevels)
         b.F2 = pass_levels(fwd, b, b.F1);
     b.F = b.F1 + b.F2;
+    // on request, the pass that reaches level L enciphers LL_L before
+    // storing it, or deciphers it right after loading it from the private
+    // fragment (whose words it then reads with the same vector width as the
+    // bands)
+    if (!b.block && b.F == b.L && path == FRAG_PATH_FUSED_CIPHER) {
+        const uint32_t last = b.F2 ? b.F2 : b.F1;
+        b.kc = aligned(fwd ? (const void *)b.priv : (const void *)b.priv_in, last == 1 ? 8 : 4);
+    }
 }
 
 // descriptor of buffer b for a fused pass (schedule fields left 0): pass 1
@@ -677,9 +701,12 @@ frag::FuseBuf fuse_buf(bool fwd, const Buf &b, int pass = 1)
     for (uint32_t l = 1; l <= F; ++l)
         for (uint32_t k = 0; k < 3; ++k)
             f.band[l - 1][k] = pub + frag::band_offset(b.H, b.W, b.L, lo + l, k);
-    // LL_top: the private fragment (protect, last level), the deciphered copy
-    // (recover, last level) or the scratch the levels above read / write
-    f.ll = (fwd && top == b.L) ? b.priv : b.scr[top];
+    // LL_top: the private fragment (protect, last level; recover, last level
+    // deciphered on chip), the deciphered copy (recover, last level, after
+    // the CTR launch) or the scratch the levels above read / write
+    f.cipher = b.kc && top == b.L;
+    f.nonce = b.nonce;
+    f.ll = (fwd && top == b.L) ? b.priv : f.cipher ? const_cast<uint8_t *>(b.priv_in) : b.scr[top];
     f.ll_final = top == b.L;
     f.W = b.W >> lo;
     f.H = b.H >> lo;
@@ -734,37 +761,59 @@ uint64_t fuse_schedule(frag::FuseBuf *f, size_t nbufs, uint64_t warps, uint32_t 
     return units;
 }
 
-frag_status fuse_slots(DeviceState &d, bool fwd, bool packed, uint32_t max_ctas, uint64_t *slots)
+// shape of a fused launch (CTAs an SM holds, warps per CTA), cached per device
+frag_status fuse_shape(DeviceState &d, bool fwd, bool packed, bool cipher, int *ctas, int *warps)
 {
-    int occ = 0;
-    const size_t tag = packed ? 9998 : 9999;
+    const size_t tag = 9990 + (packed ? 2 : 0) + (cipher ? 1 : 0);
+    int v = 0;
     {
         std::lock_guard<std::mutex> lock(g_mu);
         auto it = d.occ[fwd].find(tag);
         if (it != d.occ[fwd].end())
-            occ = it->second;
+            v = it->second;
     }
-    if (occ == 0) {
-        cudaError_t e = frag::fuse_occupancy(fwd, packed, &occ);
+    if (v == 0) {
+        int occ = 0, wpc = 0;
+        cudaError_t e = frag::fuse_shape(fwd, packed, cipher, &occ, &wpc);
         if (e != cudaSuccess)
             return cuda_fail(e, "occupancy query");
-        occ = std::max(occ, 1);
+        v = std::max(occ, 1) * 1000 + wpc;
         std::lock_guard<std::mutex> lock(g_mu);
-        d.occ[fwd][tag] = occ;
+        d.occ[fwd][tag] = v;
     }
-    *slots = (uint64_t)d.sms * occ;
-    if (max_ctas)
-        *slots = std::min<uint64_t>(*slots, max_ctas);
+    *ctas = v / 1000;
+    *warps = v % 1000;
     return FRAG_OK;
 }
 
+// warps a fused launch keeps resident on the device; a plan's grid cap
+// counts them in groups of 4 (the level kernel's consumer warps per CTA)
+frag_status fuse_slots(DeviceState &d, bool fwd, bool packed, uint32_t max_ctas, uint64_t *slots)
+{
+    int ctas = 0, wpc = 0;
+    frag_status st = fuse_shape(d, fwd, packed, false, &ctas, &wpc);
+    if (st != FRAG_OK)
+        return st;
+    *slots = (uint64_t)d.sms * ctas * wpc;
+    if (max_ctas)
+        *slots = std::min<uint64_t>(*slots, 4ull * max_ctas);
+    return FRAG_OK;
+}
+
+// slots: the resident warps fuse_slots gave
 frag_status fuse_launch(DeviceState &d, bool fwd, bool packed, frag::FuseWork &w, uint64_t slots,
                         cudaStream_t s)
 {
     if (w.total_units == 0)
         return FRAG_OK;
-    const uint64_t need = (w.total_units + frag::kFuseWarps - 1) / frag::kFuseWarps;
-    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min(slots, need));
+    w.aes_t0 = d.tables; // table 0: the first 256 words
+    int ctas = 0, wpc = 0;
+    frag_status st = fuse_shape(d, fwd, packed, w.cipher != 0, &ctas, &wpc);
+    if (st != FRAG_OK)
+        return st;
+    const uint64_t need = (w.total_units + wpc - 1) / wpc;
+    const uint64_t cap = std::min<uint64_t>((uint64_t)d.sms * ctas, (slots + wpc - 1) / wpc);
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min(cap, need));
     cudaError_t e = frag::launch_fuse(fwd, packed, w, grid, s);
     if (e != cudaSuccess)
         return cuda_fail(e, fwd ? "fused protect launch" : "fused recover launch");
@@ -895,9 +944,9 @@ frag_status run_packed(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     if (fwd) {
         st = block_launch(*d, true, w, s, true, b.keyed != 0, rk);
         if (st == FRAG_OK)
-            st = ctr_launch(*d, rk, nullptr, 0, &c, s);
+            st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &c, s);
     } else {
-        st = ctr_launch(*d, rk, nullptr, 0, &c, s);
+        st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &c, s);
         if (st == FRAG_OK)
             st = block_launch(*d, false, w, s, true, b.keyed != 0, rk);
         cudaFreeAsync(plainA, s);
@@ -940,11 +989,11 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
         w.total_units = block_units(&w.single, 1);
         const frag::CtrChunk frag_chunk = ctr_fragment(fwd, b);
         if (!fwd)
-            st = ctr_launch(*d, rk, nullptr, 0, &frag_chunk, s);
+            st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &frag_chunk, s);
         if (st == FRAG_OK)
             st = block_launch(*d, fwd, w, s);
         if (st == FRAG_OK && fwd)
-            st = ctr_launch(*d, rk, nullptr, 0, &frag_chunk, s);
+            st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &frag_chunk, s);
         if (mem)
             cudaFreeAsync(mem, s);
         return st;
@@ -954,7 +1003,7 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
         return fail(FRAG_EUNSUPPORTED, "more than %d levels", frag::kMaxInlineJobs - 1);
     // one stream-ordered allocation: [scratch][counters][queue head]
     uint64_t off[frag::kMaxInlineJobs + 1] = {0};
-    const uint64_t sb = align256(scratch_bytes(fwd, b.H, b.W, b.L, b.F1, off));
+    const uint64_t sb = align256(scratch_bytes(fwd, b.H, b.W, b.L, b.F1, off, b.kc));
     uint32_t grid = 0;
     uint64_t cb = 0;
     if (njobs) {
@@ -972,7 +1021,7 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
         if (e != cudaSuccess)
             return cuda_fail(e, "pool_malloc(level scratch)");
     }
-    for (uint32_t l = scratch_lo(b.F1); l <= scratch_hi(fwd, b.L); ++l)
+    for (uint32_t l = scratch_lo(b.F1); l <= scratch_hi(fwd, b.L, b.kc); ++l)
         b.scr[l] = mem + off[l];
     // the fused passes: [0] over the bytes, [1] over the packed LL_3
     frag::FuseWork fw[2];
@@ -987,16 +1036,20 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
         }
         fw[p].single = fuse_buf(fwd, b, p + 1);
         fw[p].nbufs = 1;
-        fw[p].total_units = fuse_schedule(&fw[p].single, 1, fslots[p] * frag::kFuseWarps, plan->seg_rows);
+        fw[p].total_units = fuse_schedule(&fw[p].single, 1, fslots[p], plan->seg_rows);
+        if (fw[p].single.cipher) {
+            fw[p].cipher = 1;
+            fw[p].keys = frag::aes::keys_from_words(key->rk);
+        }
     }
-    const bool sep = separate_cipher(b);
+    const bool sep = ctr_pass(b);
     const frag::CtrChunk frag_chunk = ctr_fragment(fwd, b);
     if (fwd && b.F1)
         st = fuse_launch(*d, true, false, fw[0], fslots[0], s);
     if (st == FRAG_OK && fwd && b.F2)
         st = fuse_launch(*d, true, true, fw[1], fslots[1], s);
     if (st == FRAG_OK && sep && !fwd)
-        st = ctr_launch(*d, rk, nullptr, 0, &frag_chunk, s);
+        st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &frag_chunk, s);
     if (st == FRAG_OK && njobs) {
         std::vector<LevelJob> jobs;
         uint32_t counters = 0;
@@ -1028,7 +1081,7 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
         }
     }
     if (st == FRAG_OK && sep && fwd)
-        st = ctr_launch(*d, rk, nullptr, 0, &frag_chunk, s);
+        st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &frag_chunk, s);
     if (st == FRAG_OK && !fwd && b.F2)
         st = fuse_launch(*d, false, true, fw[1], fslots[1], s);
     if (st == FRAG_OK && !fwd && b.F1)
@@ -1049,7 +1102,7 @@ struct DagWave {
     std::vector<frag::CtrChunk> chunks; // private fragments of the separate CTR launch
     std::vector<frag::FuseBuf> fbufs;   // buffers of the fused launch (levels 1..3)
     uint64_t fuse_units = 0;
-    std::vector<frag::FuseBuf> fbufs2;  // buffers of the second fused pass (levels 4 and 5)
+    std::vector<frag::FuseBuf> fbufs2;  // buffers of the second fused pass (levels 4 to 6)
     uint64_t fuse_units2 = 0;
     std::vector<frag::FuseBuf> bbufs;   // buffers of the block launch
     uint64_t block_units = 0;
@@ -1063,9 +1116,10 @@ struct DagWave {
 struct BatchPlan {
     bool fwd = true;
     uint64_t resident_ctas = 0; // CTAs one launch keeps resident
+    uint64_t sms = 0;           // the device's SMs
     uint32_t max_ctas = 0;      // grid cap from the first item's plan (0: none)
     uint32_t fuse_rows = 0;     // fused segment rows from the first item's plan (0: adaptive)
-    uint64_t fuse_slots = 0;    // fused CTAs one launch keeps resident
+    uint64_t fuse_slots = 0;    // fused warps one launch keeps resident
     uint64_t fuse_slots2 = 0;   // the same for the second (packed) pass
     std::vector<Buf> bufs;
     std::vector<uint64_t> scr_off;
@@ -1129,8 +1183,8 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
     uint64_t used = 0;
     uint32_t wave = 0;
     for (auto &p : v) {
-        const uint64_t sb =
-            align256(scratch_bytes(fwd, p.second.H, p.second.W, p.second.L, p.second.F1, nullptr));
+        const uint64_t sb = align256(
+            scratch_bytes(fwd, p.second.H, p.second.W, p.second.L, p.second.F1, nullptr, p.second.kc));
         if (used > 0 && used + sb > kScratchBudget) {
             ++wave;
             used = 0;
@@ -1153,17 +1207,18 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
     uint64_t u64 = 0;
     for (const Buf &b : bp.bufs)
         u64 += l1_units_at_64(b);
-    // CTR chunks: kCtrChunkList blocks, doubled (up to 16x) while the batch
-    // keeps more than 16 chunks per resident CTA, so a batch of large
-    // private fragments builds and uploads fewer descriptors with the same
-    // parallelism
+    // CTR chunks (a warp's turn): kCtrChunkList blocks, one a lane, doubled
+    // (up to 128x) while the batch keeps more than 4 chunks per resident
+    // warp of the CTR launch, so a batch of large private fragments builds
+    // and uploads fewer descriptors with the same parallelism and a batch of
+    // small ones still spreads over every SM
     uint64_t ctr_blocks = 0;
     for (const Buf &b : bp.bufs)
-        if (separate_cipher(b))
+        if (ctr_pass(b))
             ctr_blocks += ctr_fragment(bp.fwd, b).nblocks;
     uint64_t chunk = frag::kCtrChunkList;
-    const uint64_t per_cta = 16 * std::max<uint64_t>(1, bp.resident_ctas);
-    while (chunk < 16 * frag::kCtrChunkList && ctr_blocks / (2 * chunk) >= per_cta)
+    const uint64_t per_warp = 4 * std::max<uint64_t>(1, bp.sms) * (frag::kCtrThreads / 32);
+    while (chunk < 128 * frag::kCtrChunkList && ctr_blocks / (2 * chunk) >= per_warp)
         chunk *= 2;
     for (auto &wv : bp.waves) {
         wv.jobs.clear();
@@ -1185,8 +1240,8 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         Buf &b = bp.bufs[i];
         uint64_t off[frag::kMaxInlineJobs + 1] = {0};
         b.R0 = seg_rows0(b.L, u64, bp.resident_ctas, b.R0_plan);
-        scratch_bytes(bp.fwd, b.H, b.W, b.L, b.F1, off);
-        for (uint32_t l = scratch_lo(b.F1); l <= scratch_hi(bp.fwd, b.L); ++l)
+        scratch_bytes(bp.fwd, b.H, b.W, b.L, b.F1, off, b.kc);
+        for (uint32_t l = scratch_lo(b.F1); l <= scratch_hi(bp.fwd, b.L, b.kc); ++l)
             b.scr[l] = scratch_base + bp.scr_off[i] + off[l];
         DagWave &wv = bp.waves[bp.wave_of[i]];
         const uint32_t first = (uint32_t)wv.jobs.size();
@@ -1201,7 +1256,7 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
             wv.fbufs.push_back(fuse_buf(bp.fwd, b, 1));
         if (b.F2)
             wv.fbufs2.push_back(fuse_buf(bp.fwd, b, 2));
-        if (separate_cipher(b)) {
+        if (ctr_pass(b)) {
             // the private fragment in chunks of `chunk` blocks
             const frag::CtrChunk whole = ctr_fragment(bp.fwd, b);
             for (uint64_t f = 0; f < whole.nblocks; f += chunk) {
@@ -1215,12 +1270,12 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
     for (auto &wv : bp.waves) {
         wave_units(wv.jobs, wv.first, wv.levels, wv.units);
         wv.fuse_units = fuse_schedule(wv.fbufs.data(), wv.fbufs.size(),
-                                      std::max<uint64_t>(1, bp.fuse_slots) * frag::kFuseWarps,
+                                      std::max<uint64_t>(1, bp.fuse_slots),
                                       bp.fuse_rows, true);
         wv.block_units = block_units(wv.bbufs.data(), wv.bbufs.size());
         wv.packed_units = block_units(wv.pbufs.data(), wv.pbufs.size());
         wv.fuse_units2 = fuse_schedule(wv.fbufs2.data(), wv.fbufs2.size(),
-                                       std::max<uint64_t>(1, bp.fuse_slots2) * frag::kFuseWarps,
+                                       std::max<uint64_t>(1, bp.fuse_slots2),
                                        bp.fuse_rows, true);
     }
     size_t off = align256(bp.scratch);
@@ -1314,13 +1369,17 @@ struct LaunchTimer {
 
 // the fused launch of a wave (its buffers' descriptors at fbufs_off)
 frag_status launch_wave_fused(const BatchPlan &bp, const DagWave &wv, uint8_t *mem, DeviceState &d,
-                              cudaStream_t s, LaunchTimer &tm, int pass = 1)
+                              cudaStream_t s, LaunchTimer &tm, const frag::AesKeys &keys, int pass = 1)
 {
     const std::vector<frag::FuseBuf> &bufs = pass == 1 ? wv.fbufs : wv.fbufs2;
     if (bufs.empty())
         return FRAG_OK;
     frag::FuseWork w;
     std::memset(&w, 0, sizeof(w));
+    for (const auto &f : bufs)
+        w.cipher |= f.cipher;
+    if (w.cipher)
+        w.keys = keys;
     w.nbufs = (uint32_t)bufs.size();
     w.bufs = (const frag::FuseBuf *)(mem + (pass == 1 ? wv.fbufs_off : wv.fbufs2_off));
     if (w.nbufs == 1)
@@ -1360,15 +1419,15 @@ frag_status launch_wave_blocks(const BatchPlan &bp, const DagWave &wv, uint8_t *
 // above the fused ones, CTR; recover: CTR, dependency-ordered levels, block
 // mode, fused levels
 frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, const uint32_t *rk,
-                         cudaStream_t s, std::vector<TimedLaunch> *timed = nullptr)
+                         const frag::AesKeys &keys, cudaStream_t s, std::vector<TimedLaunch> *timed = nullptr)
 {
     LaunchTimer tm{timed, s};
     for (const auto &wv : bp.waves) {
         const frag::CtrChunk *chunks = (const frag::CtrChunk *)(mem + wv.chunks_off);
         frag_status st = FRAG_OK;
-        if (bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm)) != FRAG_OK)
+        if (bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm, keys)) != FRAG_OK)
             return st;
-        if (bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm, 2)) != FRAG_OK)
+        if (bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm, keys, 2)) != FRAG_OK)
             return st;
         if (bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm)) != FRAG_OK)
             return st;
@@ -1376,7 +1435,7 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
             return st;
         if (!bp.fwd && !wv.chunks.empty()) { // decipher before the transform reads LL_L
             tm.begin();
-            st = ctr_launch(d, rk, chunks, wv.chunks.size(), nullptr, s);
+            st = ctr_launch(d, keys, chunks, wv.chunks.size(), nullptr, s);
             tm.end(FRAG_KERNEL_CIPHER);
             if (st != FRAG_OK)
                 return st;
@@ -1410,7 +1469,7 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
         }
         if (bp.fwd && !wv.chunks.empty()) { // encipher after the transform wrote LL_L
             tm.begin();
-            st = ctr_launch(d, rk, chunks, wv.chunks.size(), nullptr, s);
+            st = ctr_launch(d, keys, chunks, wv.chunks.size(), nullptr, s);
             tm.end(FRAG_KERNEL_CIPHER);
             if (st != FRAG_OK)
                 return st;
@@ -1419,15 +1478,15 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
             return st;
         if (!bp.fwd && (st = launch_wave_blocks(bp, wv, mem, d, s, tm, true, rk)) != FRAG_OK)
             return st;
-        if (!bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm, 2)) != FRAG_OK)
+        if (!bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm, keys, 2)) != FRAG_OK)
             return st;
-        if (!bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm)) != FRAG_OK)
+        if (!bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm, keys)) != FRAG_OK)
             return st;
     }
     return FRAG_OK;
 }
 
-// CTAs the fused launches of a batch keep resident
+// warps the fused launches of a batch keep resident
 frag_status batch_fuse_slots(BatchPlan &bp, DeviceState &d)
 {
     bool any = false, any2 = false;
@@ -1467,6 +1526,7 @@ frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, 
     if ((st = dag_grid(*d, fwd, ~0ull, &grid)) != FRAG_OK)
         return st;
     bp.resident_ctas = bp.max_ctas ? std::min(grid, bp.max_ctas) : grid;
+    bp.sms = (uint64_t)d->sms;
     if ((st = batch_fuse_slots(bp, *d)) != FRAG_OK)
         return st;
     BatchPlan sizing = bp; // the layout does not depend on the scratch base
@@ -1478,7 +1538,7 @@ frag_status run_batch_once(bool fwd, const frag_item *pi, const frag_ritem *ri, 
     fill_batch(bp, mem);
     st = upload_batch(bp, mem, s, true);
     if (st == FRAG_OK)
-        st = launch_batch(bp, mem, *d, rk, s);
+        st = launch_batch(bp, mem, *d, rk, frag::aes::keys_from_words(key->rk), s);
     cudaFreeAsync(mem, s); // released once the launches have completed
     return st;
 }
@@ -1511,8 +1571,10 @@ frag_status create_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, ui
     if (st == FRAG_OK)
         st = device_state(&d, &bt->device);
     uint32_t grid = 0;
-    if (st == FRAG_OK && (st = dag_grid(*d, fwd, ~0ull, &grid)) == FRAG_OK)
+    if (st == FRAG_OK && (st = dag_grid(*d, fwd, ~0ull, &grid)) == FRAG_OK) {
         bt->bp.resident_ctas = bt->bp.max_ctas ? std::min(grid, bt->bp.max_ctas) : grid;
+        bt->bp.sms = (uint64_t)d->sms;
+    }
     if (st == FRAG_OK)
         st = batch_fuse_slots(bt->bp, *d);
     if (st == FRAG_OK && !bt->bp.bufs.empty()) {
@@ -1577,8 +1639,6 @@ frag_status frag_plan_create(frag_plan *out, uint32_t width, uint32_t levels, fr
         return fail(FRAG_EINVAL, "levels must be 1..%u, got %u", kMaxLevels, levels);
     if (width == 0 || (width % (1u << levels)) != 0)
         return fail(FRAG_EINVAL, "width %u is not a positive multiple of 2^%u", width, levels);
-    if (levels > kMaxFusedLevels)
-        return fail(FRAG_EUNSUPPORTED, "levels above %u are not implemented", kMaxFusedLevels);
     frag_plan p = new (std::nothrow) frag_plan_s();
     if (p == nullptr)
         return fail(FRAG_ENOMEM, "out of host memory");
@@ -1792,7 +1852,7 @@ frag_status frag_plan_set_path(frag_plan plan, frag_path path)
     frag_status st = check_plan(plan);
     if (st != FRAG_OK)
         return st;
-    if (path != FRAG_PATH_AUTO && path != FRAG_PATH_LEVELS)
+    if (path != FRAG_PATH_AUTO && path != FRAG_PATH_LEVELS && path != FRAG_PATH_FUSED_CIPHER)
         return fail(FRAG_EINVAL, "unknown path %d", (int)path);
     plan->path = (uint32_t)path;
     return FRAG_OK;
@@ -1903,7 +1963,7 @@ frag_status frag_aes128_ctr(frag_key key, uint64_t nonce, const void *d_in, void
     c.nonce = nonce;
     c.bytes = nbytes;
     c.nblocks = (nbytes + 15) / 16;
-    return ctr_launch(*d, rk, nullptr, 0, &c, (cudaStream_t)stream);
+    return ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &c, (cudaStream_t)stream);
 }
 
 frag_status frag_recover(frag_plan plan, frag_key key, uint64_t nonce, const void *d_private,
@@ -2052,8 +2112,8 @@ frag_status frag_batch_run(frag_batch batch, frag_key key, frag_stream stream)
     const uint32_t *rk = nullptr;
     if ((st = key_on_device(key, dev, &rk)) != FRAG_OK)
         return st;
-    return launch_batch(batch->bp, batch->mem, *d, rk, (cudaStream_t)stream,
-                        batch->timing ? &batch->timed : nullptr);
+    return launch_batch(batch->bp, batch->mem, *d, rk, frag::aes::keys_from_words(key->rk),
+                        (cudaStream_t)stream, batch->timing ? &batch->timed : nullptr);
 }
 
 frag_status frag_batch_set_timing(frag_batch batch, int enable)

@@ -76,7 +76,8 @@ struct DagUnit {
     uint32_t job, sx, sy, pad; // 16 bytes: one vector load
 };
 
-constexpr int kMaxInlineJobs = 8;
+// jobs of one buffer in one launch: up to 8 levels and the cipher units
+constexpr int kMaxInlineJobs = 10;
 
 struct DagWork {
     // one buffer: its jobs inline, units implied (wavefront rounds); many
@@ -149,6 +150,16 @@ constexpr uint32_t kCipherBlocks = 512;  // AES blocks of one cipher unit
 // private fragment is large: levels <= kSeparateCipherMaxLevels
 constexpr uint32_t kSeparateCipherMaxLevels = 2;
 
+// AES-128 round keys as a launch carries them in its parameters: rounds 0..9
+// as big-endian words, the same rotated left by 8 bits (the form the
+// two-table rounds XOR in), and the last round's with its bytes in stream
+// order
+struct __align__(16) AesKeys {
+    uint4 k[10];
+    uint4 kr[10];
+    uint4 last_le;
+};
+
 // blocks [first_block, first_block + nblocks) of one fragment of `bytes`
 // bytes: out = in XOR keystream(nonce)
 struct CtrChunk {
@@ -164,14 +175,15 @@ struct CtrWork {
     const CtrChunk *chunks; // device array (nullptr: one fragment, `single`)
     uint64_t nchunks;
     CtrChunk single;
-    uint64_t single_chunk;      // blocks per CTA turn over `single`
+    uint64_t single_chunk;      // blocks per warp turn over `single` (a multiple of 32)
     const uint32_t *aes_tables; // table 0 is the first 256 words
-    const uint32_t *round_keys;
+    AesKeys keys;
 };
 
 cudaError_t launch_ctr(const CtrWork &w, uint32_t grid, cudaStream_t stream);
 cudaError_t ctr_occupancy(int *blocks_per_sm);
-constexpr uint32_t kCtrChunkList = 256; // blocks per chunk of a chunk list (one per thread)
+constexpr uint32_t kCtrChunkList = 32;  // blocks per chunk of a chunk list at least (a warp turn)
+constexpr int kCtrThreads = 1024;       // one CTA an SM (the two-table AES in shared memory)
 
 // Programmatic dependent launch: a kernel launched with
 // launch_after_previous() may start while the kernel before it on the stream
@@ -186,7 +198,9 @@ __device__ __forceinline__ void grid_release() { asm volatile("griddepcontrol.la
 // level-0 rows; forward iteration t reads rows 8t-1 .. 8t+6, inverse
 // iteration t writes rows 8t-7 .. 8t.
 constexpr uint32_t kFuseMaxLevels = 3;
-constexpr int kFuseWarps = 4; // warps per CTA (each runs its own units)
+// resident warps of a fused launch an SM holds, whatever its CTA shape
+constexpr int kFuseWarpsPerSm = 16;
+
 
 struct __align__(16) FuseBuf {
     const uint8_t *src;   // forward: the n bytes
@@ -207,8 +221,10 @@ struct __align__(16) FuseBuf {
     uint32_t vec;         // block mode: every access may use its vector width
     uint32_t packed;      // block mode: the packed three fragments pk instead of int16 bands
     uint32_t keyed;       // packed: B and C protected by the keyed hashes (sha2.cuh)
+    uint32_t cipher;      // LL_F is the private fragment, enciphered (protect) or
+                          // deciphered (recover) with AES-128-CTR inside the fused kernel
     uint8_t *pk[3];       // packed: A (private, plaintext), B, C (pack_bits.cuh)
-    uint64_t nonce;       // keyed: the buffer's nonce (hash input)
+    uint64_t nonce;       // the buffer's nonce (AES-CTR counter blocks, hash input)
 };
 static_assert(sizeof(FuseBuf) % 16 == 0, "fused buffer descriptors are copied in 16-byte pieces");
 
@@ -216,16 +232,22 @@ struct FuseWork {
     const FuseBuf *bufs; // device array (nbufs > 1), ordered by unit0
     FuseBuf single;      // nbufs == 1
     uint32_t nbufs;
+    uint32_t cipher;     // some buffer of the launch has `cipher` set
     uint64_t total_units;
     int *err;            // device error word (block mode, packed: 5 = a value outside its width)
     const uint32_t *key_words; // device: the 4 big-endian AES key words (keyed packed launches)
+    const uint32_t *aes_t0;    // device: AES table 0 (256 words), when `cipher`
+    AesKeys keys;              // round keys, when `cipher`
 };
 
 // packed: the samples are 16-bit values (v + 0x4000) instead of bytes --
 // a second pass over LL_3 (levels 4 and 5) reads them (forward) or writes them
 // (inverse)
 cudaError_t launch_fuse(bool fwd, bool packed, const FuseWork &w, uint32_t grid, cudaStream_t stream);
-cudaError_t fuse_occupancy(bool fwd, bool packed, int *blocks_per_sm);
+// a fused launch's CTAs an SM holds and warps per CTA (cipher: some buffer
+// of the launch enciphers its LL in the kernel); every shape keeps 16 warps
+// an SM
+cudaError_t fuse_shape(bool fwd, bool packed, bool cipher, int *ctas_per_sm, int *warps_per_cta);
 
 // Block mode (block_kernels.cu): every 8 x 8 block transformed on its own.
 // The same descriptors: strips = ceil(W / 256) (32 blocks a warp), iters =

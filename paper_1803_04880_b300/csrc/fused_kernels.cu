@@ -39,6 +39,7 @@
 // fragment; LL_F goes to the private fragment as LL_L - 128 (int16) when F is
 // the last level, else to scratch as biased 16-bit values (the packed-pair
 // layout the dependency-ordered kernel reads for the levels above).
+#include "aes_tt.cuh"
 #include "frag_internal.cuh"
 #include "swar.cuh"
 
@@ -52,8 +53,24 @@ using strm::pq4;
 using strm::to_i16x2;
 
 
-constexpr int kWarps = kFuseWarps;
-constexpr int kThreads = 32 * kWarps;
+// warps per CTA (each warp runs its own units): a launch that enciphers
+// keeps one CTA an SM around its AES table; otherwise the forward passes
+// measured fastest as one CTA of 16 warps an SM, the inverse and the small
+// second pass as four CTAs of 4 warps
+#ifndef FUSE_FWD_WARPS
+#define FUSE_FWD_WARPS 16
+#endif
+#ifndef FUSE_INV_WARPS
+#define FUSE_INV_WARPS 4
+#endif
+#ifndef FUSE_PK_WARPS
+#define FUSE_PK_WARPS 4
+#endif
+template <bool FWD, bool PK, bool CIPH>
+__host__ __device__ constexpr int cta_warps()
+{
+    return CIPH ? 16 : PK ? FUSE_PK_WARPS : FWD ? FUSE_FWD_WARPS : FUSE_INV_WARPS;
+}
 // stages per warp (iterations in flight + the one being read) and resident
 // CTAs per SM the register budget is cut for, per direction
 #ifndef FUSE_FWD_DEPTH
@@ -62,19 +79,17 @@ constexpr int kThreads = 32 * kWarps;
 #ifndef FUSE_INV_DEPTH
 #define FUSE_INV_DEPTH 2
 #endif
-#ifndef FUSE_FWD_MINB
-#define FUSE_FWD_MINB 4
-#endif
-#ifndef FUSE_INV_MINB
-#define FUSE_INV_MINB 4
-#endif
 constexpr int kFwdDepth = FUSE_FWD_DEPTH;
 constexpr int kInvDepth = FUSE_INV_DEPTH;
 constexpr int kFwdStage = 8 * 256; // 8 level-0 rows x 32 lanes x 8 bytes
-// packed samples (a second pass over LL_3, 16-bit values): 16 bytes a lane
+// packed samples (a second pass over LL_3, 16-bit values): 16 bytes a lane,
+// two stages (the shared memory of three does not fit beside the AES table)
 constexpr int kFwdStagePk = 8 * 512;
+constexpr int kFwdDepthPk = 2;
 template <bool PK>
 __host__ __device__ constexpr int fwd_stage() { return PK ? kFwdStagePk : kFwdStage; }
+template <bool PK>
+__host__ __device__ constexpr int fwd_depth() { return PK ? kFwdDepthPk : kFwdDepth; }
 // inverse stage: level-1 rows j = 0..3, bands HL/LH/HH, 8 bytes a lane, then
 // region X: level-1 LL rows (one level), or level-2 rows k = 0..1 of the three
 // bands (4 bytes a lane) followed by LL_2 rows (two levels) or the four
@@ -122,6 +137,93 @@ __device__ __forceinline__ const uint8_t *ring_ptr(uint32_t a)
 }
 __device__ __forceinline__ uint2 lds8(uint32_t a) { return *reinterpret_cast<const uint2 *>(ring_ptr(a)); }
 __device__ __forceinline__ uint32_t lds4(uint32_t a) { return *reinterpret_cast<const uint32_t *>(ring_ptr(a)); }
+__device__ __forceinline__ uint32_t lds2(uint32_t a) { return *reinterpret_cast<const uint16_t *>(ring_ptr(a)); }
+
+// ---------------------------------------------------------------------------
+// AES-128-CTR of the private fragment while LL_L is on chip (Sec. 5.2.1: the
+// private fragment is encrypted with AES)
+//
+// The keystream does not depend on the data, so a warp computes it ahead of
+// the rows that need it, 32 blocks at a time (one a lane, every lane busy),
+// into a ring of 16-byte slots in shared memory; the lanes then XOR their LL
+// words with it right before the store (protect) or right after the load
+// (recover).  The slots follow the LL rows of the unit in order: row r takes
+// nb slots, the blocks of the private fragment from the one that holds the
+// warp's first LL column of that row on (nb covers the warp's 32 lanes of
+// columns whatever the row's offset modulo 16 bytes), so slot
+// (r - r_first) nb + (block - first block of row r) holds a block of row r.
+// Before an iteration the warp fills the ring up to the last row the
+// iteration touches; the ring keeps the iteration's slots (at most 4 rows of
+// 17) and the up to 31 filled ahead.
+// ---------------------------------------------------------------------------
+constexpr int kKsSlots = 128;
+constexpr int kKsBytes = 16 * kKsSlots;
+constexpr int kTableBytes = 4 * aes::kTableWords;
+
+struct Ks {
+    uint32_t ring;       // this warp's keystream ring (shared-window address)
+    uint32_t nb;         // slots a row takes
+    uint32_t q32, r32;   // 32 = q32 nb + r32
+    uint32_t produced;   // slots filled so far
+    uint32_t prow, pmod; // the slot this lane fills next: block pmod of row r_first + prow
+    uint32_t col_lo;     // first LL column of the warp's lanes
+    uint64_t r_first;    // LL row of slot 0
+    uint64_t WF;         // LL row length
+};
+
+__device__ __forceinline__ Ks ks_init(const FuseBuf &b, uint32_t sx, int lane, uint32_t ring, int r_first)
+{
+    Ks K;
+    const int h = (int)b.halo;
+    const int c_first = (int)sx * 8 * (31 - h) - 8 * h; // lane 0's first level-0 column
+    const uint32_t lo = (uint32_t)max(c_first, 0) >> b.F;
+    const uint32_t hi = (uint32_t)min(c_first + 256, (int)b.W) >> b.F;
+    K.ring = ring;
+    K.col_lo = lo;
+    K.nb = ((hi - lo + 7) >> 3) + 1;
+    K.q32 = 32u / K.nb;
+    K.r32 = 32u - K.q32 * K.nb;
+    K.produced = 0;
+    K.prow = (uint32_t)lane / K.nb;
+    K.pmod = (uint32_t)lane - K.prow * K.nb;
+    K.r_first = (uint64_t)max(r_first, 0);
+    K.WF = b.W >> b.F;
+    return K;
+}
+
+// fill the ring through slot upto - 1 (warp-uniform)
+__device__ __forceinline__ void ks_fill(Ks &K, uint32_t upto, const uint32_t *tel, const AesKeys &keys,
+                                        uint64_t nonce, int lane)
+{
+    while (K.produced < upto) {
+        const uint64_t r = K.r_first + K.prow;
+        const uint64_t blk = ((r * K.WF + K.col_lo) >> 3) + K.pmod;
+        uint32_t ks[4];
+        aes::ctr_block(tel, keys, nonce, blk, ks);
+        __syncwarp(); // every lane is done with the slots about to be refilled
+        const uint32_t a = K.ring + ((K.produced + (uint32_t)lane) & (kKsSlots - 1)) * 16;
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(ks[0]), "r"(ks[1]),
+                     "r"(ks[2]), "r"(ks[3])
+                     : "memory");
+        __syncwarp();
+        K.prow += K.q32;
+        K.pmod += K.r32;
+        if (K.pmod >= K.nb) {
+            K.pmod -= K.nb;
+            ++K.prow;
+        }
+        K.produced += 32;
+    }
+}
+
+// shared-window address of the keystream bytes of LL element e of row r
+// (rows below r_first, which no lane uses, land on some slot of the ring)
+__device__ __forceinline__ uint32_t ks_at(const Ks &K, uint64_t r, uint64_t e)
+{
+    const uint32_t slot = (uint32_t)(r - K.r_first) * K.nb +
+                          (uint32_t)((e >> 3) - ((r * K.WF + K.col_lo) >> 3));
+    return K.ring + (slot & (kKsSlots - 1)) * 16 + ((uint32_t)e & 7u) * 2;
+}
 
 // int16 stores at element index idx of a band (streaming: never re-read
 // here), predicated on p: a lane with p false issues the store but writes
@@ -361,7 +463,7 @@ __device__ __forceinline__ void fwd_issue(const FuseBuf &b, const Lane &ln, int 
     if (PK) {
         // packed samples: every row of the matrix is whole (no byte tail)
         if (t < t_end && ln.loads) {
-            const uint32_t st = ring_lane + (uint32_t)(t % kFwdDepth) * kFwdStagePk;
+            const uint32_t st = ring_lane + (uint32_t)(t % kFwdDepthPk) * kFwdStagePk;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int r = 8 * t - 1 + j;
@@ -408,13 +510,14 @@ struct FwdState {
 // One iteration (rows 8t-1 .. 8t+6 in stage st).  CHECK: the iteration may
 // meet the top (a level's row 0) or the bottom (a level's last row) of the
 // matrix; no other iteration does, and none stores a row outside it.
-template <bool CHECK, bool PK>
+template <bool CHECK, bool PK, bool CIPH>
 __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t, uint32_t st,
-                                         bool store, FwdState &S)
+                                         bool store, FwdState &S, const Ks &K)
 {
     const int W = (int)b.W, H = (int)b.H, F = (int)b.F;
     const int W1 = W >> 1, H1 = H >> 1, W2 = W >> 2, H2 = H >> 2, W3 = W >> 3, H3 = H >> 3;
     const bool fin = b.ll_final != 0;
+    const bool ciph = CIPH && b.cipher != 0; // LL_F is the private fragment, enciphered here
     uint2 raw[8];
     uint4 rawp[8];
 #pragma unroll
@@ -469,10 +572,17 @@ __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t
             pst8(p, b.band[0][1], idx, q_i16(dv[0]), q_i16(dv[1])); // LH_1
             pst8(p, b.band[0][2], idx, q_i16(dv[2]), q_i16(dv[3])); // HH_1
             if (F == 1) {
-                if (fin)
-                    pst8(p, b.ll, idx, ll_final(sv[0]), ll_final(sv[1]));
-                else
+                if (fin) {
+                    uint32_t l0 = ll_final(sv[0]), l1 = ll_final(sv[1]);
+                    if (ciph) {
+                        const uint2 k = lds8(ks_at(K, (uint64_t)q, idx));
+                        l0 ^= k.x;
+                        l1 ^= k.y;
+                    }
+                    pst8(p, b.ll, idx, l0, l1);
+                } else {
                     pst8(p, b.ll, idx, sv[0], sv[1]);
+                }
             }
         }
         y[j][0] = sv[0];
@@ -512,8 +622,12 @@ __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t
             pst4(p, b.band[1][0], idx, q_i16(sH)); // HL_2
             pst4(p, b.band[1][1], idx, q_i16(dL)); // LH_2
             pst4(p, b.band[1][2], idx, q_i16(dH)); // HH_2
-            if (F == 2)
-                pst4(p, b.ll, idx, fin ? ll_final(sL) : sL);
+            if (F == 2) {
+                uint32_t v = fin ? ll_final(sL) : sL;
+                if (ciph)
+                    v ^= lds4(ks_at(K, (uint64_t)q2, idx));
+                pst4(p, b.ll, idx, v);
+            }
         }
         z[k] = sL;
     }
@@ -539,7 +653,10 @@ __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t
         pst2(p, b.band[2][0], idx, sw >> 16); // HL_3
         pst2(p, b.band[2][1], idx, dw);       // LH_3
         pst2(p, b.band[2][2], idx, dw >> 16); // HH_3
-        pst2(p, b.ll, idx, fin ? ll_final(s3) : s3);
+        uint32_t v = fin ? ll_final(s3) : s3;
+        if (ciph)
+            v ^= lds2(ks_at(K, (uint64_t)q3, idx));
+        pst2(p, b.ll, idx, v);
     }
 }
 
@@ -629,18 +746,23 @@ __device__ __forceinline__ void fwd_warm(const FuseBuf &b, const Lane &ln, uint3
     S.e3 = we;
 }
 
-template <bool PK>
+template <bool PK, bool CIPH>
 __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t sy, uint32_t ring_lane,
-                                         int lane)
+                                         int lane, uint32_t ks_ring, const uint32_t *tel, const AesKeys &keys)
 {
     const Lane ln = make_lane(b, sx, lane);
     const int t_begin = (int)(sy * b.seg_iters);
     const int t_end = min(t_begin + (int)b.seg_iters, (int)b.iters);
     const int t_first = max(t_begin - (int)b.F, 0);
     const int t_fast_end = (int)b.iters - 2; // iterations t >= 2 and below this skip the checks
+    // LL rows a stored iteration t writes: R t - 1 .. R t + R - 2
+    const int R = 8 >> b.F;
+    Ks K = {};
+    if (CIPH && b.cipher)
+        K = ks_init(b, sx, lane, ks_ring, R * t_begin - 1);
 
 #pragma unroll
-    for (int k = 0; k < kFwdDepth - 1; ++k)
+    for (int k = 0; k < fwd_depth<PK>() - 1; ++k)
         fwd_issue<PK>(b, ln, t_first + k, t_end, ring_lane);
 
     FwdState S; // zeros, in each word's form
@@ -653,17 +775,20 @@ __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t
     S.p2L = S.p2H = kQ;
 
     for (int t = t_first; t < t_end; ++t) {
-        fwd_issue<PK>(b, ln, t + kFwdDepth - 1, t_end, ring_lane);
-        cp_wait<kFwdDepth - 1>();
-        const uint32_t st = ring_lane + (uint32_t)(t % kFwdDepth) * fwd_stage<PK>();
+        fwd_issue<PK>(b, ln, t + fwd_depth<PK>() - 1, t_end, ring_lane);
+        // the keystream of the iteration's LL rows (while its loads land)
+        if (CIPH && b.cipher && t >= t_begin)
+            ks_fill(K, (uint32_t)((uint64_t)(R * t + R - 1) - K.r_first) * K.nb, tel, keys, b.nonce, lane);
+        cp_wait<fwd_depth<PK>() - 1>();
+        const uint32_t st = ring_lane + (uint32_t)(t % fwd_depth<PK>()) * fwd_stage<PK>();
         const bool store = ln.own && t >= t_begin;
         if (t >= 2 && t < t_fast_end) {
             if (t < t_begin)
                 fwd_warm<PK>(b, ln, st, t == t_first && t_first == t_begin - (int)b.F, t == t_begin - 1, S);
             else
-                fwd_iter<false, PK>(b, ln, t, st, store, S);
+                fwd_iter<false, PK, CIPH>(b, ln, t, st, store, S, K);
         } else {
-            fwd_iter<true, PK>(b, ln, t, st, store, S);
+            fwd_iter<true, PK, CIPH>(b, ln, t, st, store, S, K);
         }
     }
     cp_wait<0>();
@@ -793,22 +918,26 @@ struct InvState {
     uint32_t x3, d3;
 };
 
-template <bool CHECK, bool PK>
+template <bool CHECK, bool PK, bool CIPH>
 __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t, uint32_t s8,
-                                         uint32_t s4, bool store, bool whole, InvState &S)
+                                         uint32_t s4, bool store, bool whole, InvState &S, const Ks &K)
 {
     const int W = (int)b.W, H = (int)b.H, F = (int)b.F;
     const int W3 = W >> 3, H1 = H >> 1, H2 = H >> 2, H3 = H >> 3;
     const uint32_t llb = b.ll_final ? 0x00800080u : 0u; // LL_L - 128 -> LL_L
+    const bool ciph = CIPH && b.cipher != 0; // LL_F is the private fragment, deciphered here
 
     // level 3: row t -> LL_2 rows 2t-1, 2t
     uint32_t z[2];
     if (F == 3) {
-        const uint32_t sh = 16u * (uint32_t)(((uint64_t)t * (uint64_t)W3 + (uint64_t)(ln.c0 >> 3)) & 1ull);
+        const uint64_t e3 = (uint64_t)t * (uint64_t)W3 + (uint64_t)(ln.c0 >> 3);
+        const uint32_t sh = 16u * (uint32_t)(e3 & 1ull);
         const uint32_t hl = (lds4(s4 + kInvL3) >> sh) & 0xffffu;
         const uint32_t lh = (lds4(s4 + kInvL3 + 128) >> sh) & 0xffffu;
         const uint32_t hh = (lds4(s4 + kInvL3 + 256) >> sh) & 0xffffu;
-        const uint32_t ll = (lds4(s4 + kInvL3 + 384) >> sh) & 0xffffu;
+        uint32_t ll = (lds4(s4 + kInvL3 + 384) >> sh) & 0xffffu;
+        if (ciph)
+            ll ^= lds2(ks_at(K, (uint64_t)t, e3));
         const uint32_t s = b.ll_final ? in16(ll | (hl << 16)) + 0x80u
                                       : (ll | (in16(hl << 16) & 0xffff0000u));
         const uint32_t d = in16(lh | (hh << 16));
@@ -828,12 +957,17 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
             const uint32_t lh = q_i16(lds4(s4 + kInvX + 128 * (3 * k + 1)));
             const uint32_t hh = q_i16(lds4(s4 + kInvX + 128 * (3 * k + 2)));
             uint32_t ll;
-            if (F == 3)
+            if (F == 3) {
                 ll = z[k];
-            else if (b.ll_final)
-                ll = in16(lds4(s4 + kInvL2Ll + 128 * k)) + llb;
-            else
+            } else if (b.ll_final) {
+                uint32_t c = lds4(s4 + kInvL2Ll + 128 * k);
+                if (ciph)
+                    c ^= lds4(ks_at(K, (uint64_t)q2,
+                                    (uint64_t)q2 * (uint64_t)(W >> 2) + (uint64_t)(ln.c0 >> 2)));
+                ll = in16(c) + llb;
+            } else {
                 ll = lds4(s4 + kInvL2Ll + 128 * k);
+            }
             uint32_t oL, eL, oH, eH;
             col_inv<CHECK, false, true>(ll, lh, q2 == 0, q2 == H2, S.x2[0], S.d2[0], oL, eL);
             col_inv<CHECK, true, true>(hl, hh, q2 == 0, q2 == H2, S.x2[1], S.d2[1], oH, eH);
@@ -851,7 +985,12 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
         const uint2 hh = lds8(s8 + 256 * (3 * j + 2));
         uint32_t s[4], d[4];
         if (F == 1) {
-            const uint2 ll = lds8(s8 + kInvX + 256 * j);
+            uint2 ll = lds8(s8 + kInvX + 256 * j);
+            if (ciph) {
+                const uint2 k = lds8(ks_at(K, (uint64_t)q, (uint64_t)q * (uint64_t)(W >> 1) + (uint64_t)(ln.c0 >> 1)));
+                ll.x ^= k.x;
+                ll.y ^= k.y;
+            }
             s[0] = b.ll_final ? in16(ll.x) + llb : ll.x;
             s[1] = b.ll_final ? in16(ll.y) + llb : ll.y;
         } else {
@@ -904,19 +1043,24 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
 // coefficient row in the iteration, whose d[q-1] is the row before it,
 // loaded in the same iteration (level 3: the d preloaded at the unit's
 // start); level 2 hands down its row-inversed even row, LL_1 row 4t.
+template <bool CIPH>
 __device__ __forceinline__ void inv_warm(const FuseBuf &b, const Lane &ln, int t, uint32_t s8, uint32_t s4,
-                                         InvState &S)
+                                         InvState &S, const Ks &K)
 {
     const int F = (int)b.F;
     const uint32_t llb = b.ll_final ? 0x00800080u : 0u;
+    const bool ciph = CIPH && b.cipher != 0;
     uint32_t y3[2] = {0u, 0u};
     uint32_t z1 = 0u;
     if (F == 3) { // level-3 row t
-        const uint32_t sh = 16u * (uint32_t)(((uint64_t)t * (uint64_t)(b.W >> 3) + (uint64_t)(ln.c0 >> 3)) & 1ull);
+        const uint64_t e3 = (uint64_t)t * (uint64_t)(b.W >> 3) + (uint64_t)(ln.c0 >> 3);
+        const uint32_t sh = 16u * (uint32_t)(e3 & 1ull);
         const uint32_t hl = (lds4(s4 + kInvL3) >> sh) & 0xffffu;
         const uint32_t lh = (lds4(s4 + kInvL3 + 128) >> sh) & 0xffffu;
         const uint32_t hh = (lds4(s4 + kInvL3 + 256) >> sh) & 0xffffu;
-        const uint32_t ll = (lds4(s4 + kInvL3 + 384) >> sh) & 0xffffu;
+        uint32_t ll = (lds4(s4 + kInvL3 + 384) >> sh) & 0xffffu;
+        if (ciph)
+            ll ^= lds2(ks_at(K, (uint64_t)t, e3));
         const uint32_t s = b.ll_final ? in16(ll | (hl << 16)) + 0x80u
                                       : (ll | (in16(hl << 16) & 0xffff0000u));
         const uint32_t d = in16(lh | (hh << 16));
@@ -931,12 +1075,17 @@ __device__ __forceinline__ void inv_warm(const FuseBuf &b, const Lane &ln, int t
         const uint32_t lh1 = q_i16(lds4(s4 + kInvX + 128 * 4));
         const uint32_t hh1 = q_i16(lds4(s4 + kInvX + 128 * 5));
         uint32_t ll;
-        if (F == 3)
+        if (F == 3) {
             ll = z1;
-        else if (b.ll_final)
-            ll = in16(lds4(s4 + kInvL2Ll + 128)) + llb;
-        else
+        } else if (b.ll_final) {
+            uint32_t c = lds4(s4 + kInvL2Ll + 128);
+            if (ciph)
+                c ^= lds4(ks_at(K, (uint64_t)(2 * t),
+                                (uint64_t)(2 * t) * (uint64_t)(b.W >> 2) + (uint64_t)(ln.c0 >> 2)));
+            ll = in16(c) + llb;
+        } else {
             ll = lds4(s4 + kInvL2Ll + 128);
+        }
         const uint32_t eL = ll - pq4q(lh0, lh1) + 0x20002000u;
         const uint32_t eH = hl1 - pq4q(hh0, hh1) - 0x20002000u;
         S.x2[0] = eL;
@@ -950,7 +1099,13 @@ __device__ __forceinline__ void inv_warm(const FuseBuf &b, const Lane &ln, int t
     const uint2 hl3 = lds8(s8 + 256 * 9), lh3 = lds8(s8 + 256 * 10), hh3 = lds8(s8 + 256 * 11);
     uint32_t s[4];
     if (F == 1) {
-        const uint2 ll = lds8(s8 + kInvX + 256 * 3);
+        uint2 ll = lds8(s8 + kInvX + 256 * 3);
+        if (ciph) {
+            const uint2 k = lds8(ks_at(K, (uint64_t)(4 * t),
+                                       (uint64_t)(4 * t) * (uint64_t)(b.W >> 1) + (uint64_t)(ln.c0 >> 1)));
+            ll.x ^= k.x;
+            ll.y ^= k.y;
+        }
         s[0] = b.ll_final ? in16(ll.x) + llb : ll.x;
         s[1] = b.ll_final ? in16(ll.y) + llb : ll.y;
     } else {
@@ -969,9 +1124,10 @@ __device__ __forceinline__ void inv_warm(const FuseBuf &b, const Lane &ln, int t
     }
 }
 
-template <bool PK>
+template <bool PK, bool CIPH>
 __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t sy, uint32_t ring_lane8,
-                                         uint32_t ring_lane4, int lane)
+                                         uint32_t ring_lane4, int lane, uint32_t ks_ring, const uint32_t *tel,
+                                         const AesKeys &keys)
 {
     const Lane ln = make_lane(b, sx, lane);
     const int F = (int)b.F;
@@ -982,6 +1138,14 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
     // which is loaded here instead of running a second iteration
     const int t_first = max(t_begin - 1, 0);
     const int t_fast_end = (int)b.iters - 2;
+    // LL rows iteration t reads: R t - R + 1 .. R t (the warm-up iteration
+    // only the last of them)
+    const int R = 8 >> F;
+    Ks K = {};
+    if (CIPH && b.cipher) {
+        const bool warm = t_first >= 1 && t_first < t_fast_end && t_first < t_begin;
+        K = ks_init(b, sx, lane, ks_ring, warm ? R * t_first : R * t_first - R + 1);
+    }
 
 #pragma unroll
     for (int k = 0; k < kInvDepth - 1; ++k)
@@ -1004,17 +1168,19 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
 
     for (int t = t_first; t < t_end; ++t) {
         inv_issue(b, ln, t + kInvDepth - 1, t_end, ring_lane8, ring_lane4);
+        if (CIPH && b.cipher)
+            ks_fill(K, (uint32_t)((uint64_t)(R * t + 1) - K.r_first) * K.nb, tel, keys, b.nonce, lane);
         cp_wait<kInvDepth - 1>();
         const uint32_t so = (uint32_t)(t % kInvDepth) * kInvStage;
         const bool store = ln.own && t >= t_begin;
         const bool whole = 8 * t < (int)b.full_rows; // rows 8t-7 .. 8t hold only data
         if (t >= 1 && t < t_fast_end) {
             if (t < t_begin)
-                inv_warm(b, ln, t, ring_lane8 + so, ring_lane4 + so, S);
+                inv_warm<CIPH>(b, ln, t, ring_lane8 + so, ring_lane4 + so, S, K);
             else
-                inv_iter<false, PK>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S);
+                inv_iter<false, PK, CIPH>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S, K);
         } else {
-            inv_iter<true, PK>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S);
+            inv_iter<true, PK, CIPH>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S, K);
         }
     }
     cp_wait<0>();
@@ -1041,15 +1207,33 @@ __device__ __forceinline__ const FuseBuf *unit_buf(const FuseWork &w, uint64_t u
     return &w.bufs[lo];
 }
 
+// shared memory of a block: every warp's stage ring, then (launches that
+// encipher) the lane-replicated AES table and every warp's keystream ring
 template <bool FWD, bool PK>
-__global__ void __launch_bounds__(kThreads, FWD ? FUSE_FWD_MINB : FUSE_INV_MINB) fuse_kernel(FuseWork w)
+__host__ __device__ constexpr uint32_t stage_ring_bytes()
+{
+    return FWD ? fwd_depth<PK>() * fwd_stage<PK>() : kInvDepth * kInvStage;
+}
+
+template <bool FWD, bool PK, bool CIPH>
+__global__ void __launch_bounds__(32 * cta_warps<FWD, PK, CIPH>(), 16 / cta_warps<FWD, PK, CIPH>())
+    fuse_kernel(FuseWork w)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     // the next kernel (the CTR pass after a protect) may start its
     // data-independent part now; it waits for this grid before reading
     grid_release();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t ring = smem_addr(smem) + (uint32_t)warp * (FWD ? kFwdDepth * fwd_stage<PK>() : kInvDepth * kInvStage);
+    constexpr int kWarps = cta_warps<FWD, PK, CIPH>();
+    constexpr uint32_t kStages = (uint32_t)kWarps * stage_ring_bytes<FWD, PK>();
+    uint32_t *te = reinterpret_cast<uint32_t *>(smem + kStages);
+    if (CIPH) { // some buffer of the launch enciphers its LL here
+        aes::build_table(te, w.aes_t0);
+        __syncthreads();
+    }
+    const uint32_t ring = smem_addr(smem) + (uint32_t)warp * stage_ring_bytes<FWD, PK>();
+    const uint32_t ks_ring = smem_addr(smem) + kStages + (uint32_t)kTableBytes + (uint32_t)warp * kKsBytes;
+    const uint32_t *tel = te + lane;
     const uint64_t G = (uint64_t)gridDim.x * kWarps;
     for (uint64_t u = (uint64_t)blockIdx.x * kWarps + warp; u < w.total_units; u += G) {
         uint64_t local;
@@ -1057,48 +1241,60 @@ __global__ void __launch_bounds__(kThreads, FWD ? FUSE_FWD_MINB : FUSE_INV_MINB)
         const FuseBuf b = *bp;
         const uint32_t sy = (uint32_t)(local / b.strips), sx = (uint32_t)(local % b.strips);
         if (FWD)
-            fwd_unit<PK>(b, sx, sy, ring + (PK ? 16u : 8u) * lane, lane);
+            fwd_unit<PK, CIPH>(b, sx, sy, ring + (PK ? 16u : 8u) * lane, lane, ks_ring, tel, w.keys);
         else
-            inv_unit<PK>(b, sx, sy, ring + 8u * lane, ring + 4u * lane, lane);
+            inv_unit<PK, CIPH>(b, sx, sy, ring + 8u * lane, ring + 4u * lane, lane, ks_ring, tel, w.keys);
     }
 }
 
-size_t smem_bytes(bool fwd, bool pk)
+// CIPH: the launch enciphers some buffer's LL (table and keystream rings);
+// the others leave that shared memory to L1
+template <bool FWD, bool PK, bool CIPH>
+constexpr size_t smem_bytes()
 {
-    return (size_t)kWarps * (fwd ? kFwdDepth * (pk ? kFwdStagePk : kFwdStage) : kInvDepth * kInvStage);
+    constexpr int warps = cta_warps<FWD, PK, CIPH>();
+    return (size_t)warps * stage_ring_bytes<FWD, PK>() + (CIPH ? (size_t)kTableBytes + (size_t)warps * kKsBytes : 0);
 }
 
-template <bool FWD, bool PK>
+template <bool FWD, bool PK, bool CIPH>
 cudaError_t set_attr()
 {
-    return cudaFuncSetAttribute((const void *)fuse_kernel<FWD, PK>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(FWD, PK));
+    return cudaFuncSetAttribute((const void *)fuse_kernel<FWD, PK, CIPH>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<FWD, PK, CIPH>());
+}
+
+template <bool FWD, bool PK, bool CIPH>
+cudaError_t launch(const FuseWork &w, uint32_t grid, cudaStream_t stream)
+{
+    cudaError_t e = set_attr<FWD, PK, CIPH>();
+    if (e != cudaSuccess)
+        return e;
+    // an ordinary launch (its loads go through L1, so it starts only once
+    // the kernel before it has finished)
+    fuse_kernel<FWD, PK, CIPH><<<grid, 32 * cta_warps<FWD, PK, CIPH>(), smem_bytes<FWD, PK, CIPH>(), stream>>>(w);
+    return cudaGetLastError();
 }
 
 template <bool FWD, bool PK>
 cudaError_t launch(const FuseWork &w, uint32_t grid, cudaStream_t stream)
 {
-    cudaError_t e = set_attr<FWD, PK>();
-    if (e != cudaSuccess)
-        return e;
-    // an ordinary launch (its loads go through L1, so it starts only once
-    // the kernel before it has finished)
-    fuse_kernel<FWD, PK><<<grid, kThreads, smem_bytes(FWD, PK), stream>>>(w);
-    return cudaGetLastError();
+    return w.cipher ? launch<FWD, PK, true>(w, grid, stream) : launch<FWD, PK, false>(w, grid, stream);
 }
 
-template <bool FWD, bool PK>
-cudaError_t occupancy(int *blocks_per_sm)
+// the CTAs of a launch an SM holds, and its warps per CTA
+template <bool FWD, bool PK, bool CIPH>
+cudaError_t shape(int *ctas_per_sm, int *warps_per_cta)
 {
-    cudaError_t e = set_attr<FWD, PK>();
+    cudaError_t e = set_attr<FWD, PK, CIPH>();
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void *)fuse_kernel<FWD, PK>,
-                                                         kThreads, smem_bytes(FWD, PK));
+    *warps_per_cta = cta_warps<FWD, PK, CIPH>();
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, (const void *)fuse_kernel<FWD, PK, CIPH>,
+                                                         32 * cta_warps<FWD, PK, CIPH>(),
+                                                         smem_bytes<FWD, PK, CIPH>());
 }
 
 } // namespace fuse
-
 cudaError_t launch_fuse(bool fwd, bool packed, const FuseWork &w, uint32_t grid, cudaStream_t stream)
 {
     if (fwd)
@@ -1106,11 +1302,20 @@ cudaError_t launch_fuse(bool fwd, bool packed, const FuseWork &w, uint32_t grid,
     return packed ? fuse::launch<false, true>(w, grid, stream) : fuse::launch<false, false>(w, grid, stream);
 }
 
-cudaError_t fuse_occupancy(bool fwd, bool packed, int *blocks_per_sm)
+cudaError_t fuse_shape(bool fwd, bool packed, bool cipher, int *ctas_per_sm, int *warps_per_cta)
 {
-    if (fwd)
-        return packed ? fuse::occupancy<true, true>(blocks_per_sm) : fuse::occupancy<true, false>(blocks_per_sm);
-    return packed ? fuse::occupancy<false, true>(blocks_per_sm) : fuse::occupancy<false, false>(blocks_per_sm);
+    if (fwd) {
+        if (packed)
+            return cipher ? fuse::shape<true, true, true>(ctas_per_sm, warps_per_cta)
+                          : fuse::shape<true, true, false>(ctas_per_sm, warps_per_cta);
+        return cipher ? fuse::shape<true, false, true>(ctas_per_sm, warps_per_cta)
+                      : fuse::shape<true, false, false>(ctas_per_sm, warps_per_cta);
+    }
+    if (packed)
+        return cipher ? fuse::shape<false, true, true>(ctas_per_sm, warps_per_cta)
+                      : fuse::shape<false, true, false>(ctas_per_sm, warps_per_cta);
+    return cipher ? fuse::shape<false, false, true>(ctas_per_sm, warps_per_cta)
+                  : fuse::shape<false, false, false>(ctas_per_sm, warps_per_cta);
 }
 
 } // namespace frag

@@ -38,11 +38,19 @@ def test_abi_version(L):
 
 @pytest.mark.parametrize("w,l,status", [(0, 1, fr.FRAG_EINVAL), (12, 3, fr.FRAG_EINVAL),
                                         (64, 0, fr.FRAG_EINVAL), (1024, 9, fr.FRAG_EINVAL),
-                                        (1024, 6, fr.FRAG_EUNSUPPORTED)])
+                                        (64, 7, fr.FRAG_EINVAL), (384, 8, fr.FRAG_EINVAL)])
 def test_plan_validation(L, w, l, status):
     h = ctypes.c_void_p()
     assert L.frag_plan_create(ctypes.byref(h), w, l, 0) == status
     assert "width" in fr.last_error() or "levels" in fr.last_error()
+
+
+@pytest.mark.parametrize("w,l", [(64, 6), (128, 7), (256, 8), (8192, 8)])
+def test_plans_of_six_to_eight_levels(L, w, l):
+    """Every level count 1..8 makes a plan; its sizes are the oracle's."""
+    p = fr.Plan(w, l)
+    for n in (1, w * 3 + 1, w * (1 << l) * 5 - 7):
+        assert p.sizes(n) == oracle.sizes(n, w, l)
 
 
 def test_unknown_filter(L):

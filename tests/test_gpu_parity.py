@@ -79,12 +79,18 @@ SWEEP = [
     (224 * 230, 224, 3, None), (448 * 449 + 3, 448, 2, None), (240 * 500, 240, 3, None),
     (672 * 225 + 100, 672, 1, None), (16 * 1000, 16, 3, None), (8 * 7, 8, 3, None),
     (232 * 232, 232, 3, None), (456 * 456 - 1, 456, 3, None), (904 * 220, 904, 2, None),
+    # six to eight levels (W a multiple of 2^L, ragged heights and tails)
+    (64 * 130 + 5, 64, 6, None), (128 * 200 - 1, 128, 7, None), (256 * 300 + 13, 256, 8, None),
+    (1024 * 1024 + 777, 1024, 6, None), (512 * 600, 512, 7, None), (2048 * 300 + 1, 2048, 8, None),
+    (768 * 256, 768, 8, None), (320 * 999, 320, 6, None),
 ]
 
 
-# path 0: fused levels where alignment allows (the default); 1: every level
-# in the dependency-ordered kernel
-@pytest.mark.parametrize("path", [0, 1])
+# path 0: fused levels where alignment allows, the private fragment through
+# the AES-CTR launch (the default); 1: every level in the dependency-ordered
+# kernel; 2: the fused levels with the private fragment enciphered inside the
+# fused pass that reaches level L
+@pytest.mark.parametrize("path", [0, 1, 2])
 @pytest.mark.parametrize("n,W,L,tiling", SWEEP)
 def test_sweep_random(fr, key, n, W, L, tiling, path):
     data = wl.random_bytes(n, seed=n + W + L)
@@ -115,12 +121,15 @@ def test_fused_segments(fr, key, n, W, L, seg_rows):
     assert torch.equal(out, d)
 
 
-# the second fused pass (levels 4 and 5 over the level-3 LL): level-3 widths
+# the second fused pass (levels 4 to 6 over the level-3 LL): level-3 widths
 # from one lane's 8 columns to two strips, LL_3 heights from 2 rows up,
-# ragged tails
+# ragged tails; with 7 and 8 levels the level kernel takes the levels above
+# the sixth from the pass's LL_6
 PASS2 = [(64 * 16, 64, 4), (64 * 16 * 3 - 7, 64, 4), (128 * 64 + 1, 128, 5), (192 * 128 - 3, 192, 5),
          (512 * 300 + 11, 512, 4), (2048 * 256, 2048, 5), (4096 * 256 + 99, 4096, 4),
-         (1024 * 512, 1024, 5), (1984 * 256 - 5, 1984, 5), (8192 * 64, 8192, 5), (64 * 64 - 1, 64, 5)]
+         (1024 * 512, 1024, 5), (1984 * 256 - 5, 1984, 5), (8192 * 64, 8192, 5), (64 * 64 - 1, 64, 5),
+         (128 * 128, 128, 6), (512 * 512 - 9, 512, 6), (4096 * 200 + 3, 4096, 6), (1984 * 1280, 1984, 6),
+         (1024 * 1024, 1024, 7), (2048 * 512 + 5, 2048, 7), (4096 * 256, 4096, 8), (256 * 1024 - 1, 256, 8)]
 
 
 @pytest.mark.parametrize("seg_rows", [0, 16])
@@ -147,19 +156,27 @@ def test_second_fused_pass(fr, key, n, W, L, seg_rows):
 
 
 def test_path_selects_kernels(fr, key):
-    """Three fused levels take the fused launch and the CTR launch; the level
-    path takes one dependency-ordered launch with in-launch cipher units."""
+    """Three fused levels take the fused launch and the CTR launch; with the
+    cipher in the fused pass, one fused launch, except for a private fragment
+    the fused recover cannot read with 4-byte words (an odd address), which
+    goes through the CTR launch; the level path takes one dependency-ordered
+    launch with in-launch cipher units."""
     n, W, L = 4096 * 64, 4096, 3
     plan = fr.Plan(W, L)
     _, pb, ub = plan.sizes(n)
     d = torch.zeros(n, dtype=torch.uint8, device="cuda")
-    priv = torch.empty(pb, dtype=torch.uint8, device="cuda")
+    priv = torch.empty(pb + 1, dtype=torch.uint8, device="cuda")
     pub = torch.empty(ub, dtype=torch.uint8, device="cuda")
     assert plan.path() == fr.Plan.PATH_AUTO
-    assert fr.Batch([(plan, 0, n, d, priv, pub)], True).launches == 2
+    assert fr.Batch([(plan, 0, n, d, priv[:pb], pub)], True).launches == 2
+    plan.set_path(fr.Plan.PATH_FUSED_CIPHER)
+    assert plan.path() == fr.Plan.PATH_FUSED_CIPHER
+    assert fr.Batch([(plan, 0, n, d, priv[:pb], pub)], True).launches == 1
+    assert fr.Batch([(plan, 0, n, priv[:pb], pub, d)], False).launches == 1
+    assert fr.Batch([(plan, 0, n, priv[1:], pub, d)], False).launches == 2
     plan.set_path(fr.Plan.PATH_LEVELS)
     assert plan.path() == fr.Plan.PATH_LEVELS
-    assert fr.Batch([(plan, 0, n, d, priv, pub)], True).launches == 1
+    assert fr.Batch([(plan, 0, n, d, priv[:pb], pub)], True).launches == 1
 
 
 @pytest.mark.parametrize("L", [3, 4])
@@ -192,6 +209,36 @@ def test_batch_launch_times(fr, key, L):
 @pytest.mark.parametrize("n,W,L", [(12345, 128, 2), (4096, 64, 3), (77777, 256, 5)])
 def test_unaligned_buffers(fr, key, n, W, L):
     check_against_oracle(fr, key, wl.random_bytes(n, 5), W, L, nonce=3, offset=1)
+
+
+@pytest.mark.parametrize("poff", [0, 1, 2, 4, 8])
+@pytest.mark.parametrize("n,W,L", [(4096 * 40 + 3, 4096, 1), (2048 * 64 - 7, 2048, 2),
+                                   (1024 * 96, 1024, 3), (512 * 512 + 1, 512, 5)])
+def test_private_fragment_offsets(fr, key, n, W, L, poff):
+    """Only the private fragment moves (to an offset of 1, 2, 4 or 8 bytes):
+    with the cipher in the fused pass, that pass enciphers / deciphers it on
+    chip when its words are aligned for the pass, the CTR launch takes it
+    otherwise; either way every byte equals the oracle's, and a protect by
+    one path recovers by the other."""
+    data = wl.random_bytes(n, seed=n + poff)
+    p_ref, u_ref = oracle.protect(data, W, L, KEY, 6)
+    d = torch.from_numpy(data).cuda()
+    for pp, rp in ((0, 0), (0, 2), (2, 0)):
+        plan_p, plan_r = fr.Plan(W, L), fr.Plan(W, L)
+        plan_p.set_path(pp)
+        plan_r.set_path(rp)
+        _, pb, ub = plan_p.sizes(n)
+        pbuf = torch.full((pb + 16,), 0xAA, dtype=torch.uint8, device="cuda")
+        priv = pbuf[poff:poff + pb]
+        pub = torch.empty(ub, dtype=torch.uint8, device="cuda")
+        out = torch.full((n,), 0x55, dtype=torch.uint8, device="cuda")
+        fr.protect(plan_p, key, 6, d, n, priv, pub)
+        fr.recover(plan_r, key, 6, priv, pub, n, out)
+        fr.sync_status()
+        assert np.array_equal(priv.cpu().numpy(), p_ref), (pp, rp)
+        assert np.array_equal(pub.cpu().numpy(), u_ref), (pp, rp)
+        assert torch.equal(out, d), (pp, rp)
+        assert (pbuf[:poff] == 0xAA).all() and (pbuf[poff + pb:] == 0xAA).all(), "wrote outside the fragment"
 
 
 @pytest.mark.parametrize("kind", ["zeros", "ones", "checker", "ramp", "c3mix"])
@@ -287,6 +334,39 @@ def test_batch_matches_single_calls_and_oracle(fr, key):
         assert np.array_equal(p.cpu().numpy(), p_ref)
         assert np.array_equal(u.cpu().numpy(), u_ref)
         assert np.array_equal(o.cpu().numpy(), d)
+
+
+def test_batch_of_six_to_eight_levels(fr, key):
+    """A batch of buffers at 6, 7 and 8 levels (with buffers of 1..5 levels
+    beside them), on both kernel paths, against the oracle."""
+    items = [(64 * 130 + 5, 64, 6, 1), (128 * 200 - 1, 128, 7, 2), (256 * 300 + 13, 256, 8, 3),
+             (4096 * 64, 4096, 6, 4), (1024 * 512 + 1, 1024, 7, 5), (2048 * 512, 2048, 8, 6),
+             (5000, 16, 4, 7), (77777, 256, 5, 8), (12345, 128, 2, 9), (40000, 512, 1, 10)]
+    for path in (0, 1):
+        plans = {}
+        entries, rentries, refs = [], [], []
+        for (n, W, L, nonce) in items:
+            if (W, L) not in plans:
+                plans[(W, L)] = fr.Plan(W, L)
+                plans[(W, L)].set_path(path)
+            plan = plans[(W, L)]
+            d = wl.random_bytes(n, seed=n + 3 * L + path)
+            _, pb, ub = plan.sizes(n)
+            t = torch.from_numpy(d).cuda()
+            p = torch.empty(pb, dtype=torch.uint8, device="cuda")
+            u = torch.empty(ub, dtype=torch.uint8, device="cuda")
+            o = torch.empty(n, dtype=torch.uint8, device="cuda")
+            entries.append((plan, nonce, n, t, p, u))
+            rentries.append((plan, nonce, n, p, u, o))
+            refs.append((d, W, L, nonce, p, u, o))
+        fr.protect_batch(entries, key)
+        fr.recover_batch(rentries, key)
+        fr.sync_status()
+        for d, W, L, nonce, p, u, o in refs:
+            p_ref, u_ref = oracle.protect(d, W, L, KEY, nonce)
+            assert np.array_equal(p.cpu().numpy(), p_ref), (W, L, path)
+            assert np.array_equal(u.cpu().numpy(), u_ref), (W, L, path)
+            assert np.array_equal(o.cpu().numpy(), d), (W, L, path)
 
 
 def test_batch_object_in_cuda_graph(fr, key):

@@ -92,3 +92,16 @@ def test_rejects_more_items_than_the_scratch_holds(fr):
     st = fr.lib().frag_protect_batch_noalloc(arr, limit + 1, wl.KEY, None)
     assert st == fr.FRAG_EINVAL
     assert "limit" in fr.last_error()
+
+
+def test_rejects_more_than_five_levels(fr):
+    """The tile kernel behind this call keeps a tile and its halo in shared
+    memory, which bounds it at 5 levels; 6 to 8 are refused with a message."""
+    plan = fr.Plan(64, 6)
+    t = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    _, pb, ub = plan.sizes(t.numel())
+    p = torch.empty(pb, dtype=torch.uint8, device="cuda")
+    u = torch.empty(ub, dtype=torch.uint8, device="cuda")
+    st = _noalloc(fr, [(plan, 0, t.numel(), t, p, u)])
+    assert st == fr.FRAG_EUNSUPPORTED
+    assert "at most 5 levels" in fr.last_error()
