@@ -950,10 +950,11 @@ def run_c5(args, rank, world, local_rank):
 AES_DESC = {"workload": "full-buffer AES-128-CTR of the 256 MiB mixed buffer (encrypt + decrypt), "
                         "the thesis's full-encryption comparator", "planes": 1, "width": None,
             "levels": 0}
-# the T-table AES's own ceiling: 160 four-byte table lookups per 16-byte block
-# (16 per round, 10 rounds), at most 32 of them per SM per clock from shared
-# memory -> SMs x clock x 32 / 160 blocks per second
-AES_LOOKUPS_PER_BLOCK = 160
+# the table AES's own ceiling: 148 four-byte table lookups per 16-byte block
+# (16 in each of rounds 2..10, 4 in round 1, whose other terms depend only on
+# the nonce and are computed once per chunk), at most 32 of them per SM per
+# clock from shared memory -> SMs x clock x 32 / 148 blocks per second
+AES_LOOKUPS_PER_BLOCK = 148
 AES_LOOKUPS_PER_SM_CLOCK = 32
 
 
