@@ -261,11 +261,15 @@ struct Slot {
     bool vec; // aligned: staged loads and vector accesses
 };
 
-__device__ __forceinline__ const FuseBuf *unit_buf(const FuseWork &w, uint64_t u, uint64_t &local)
+// single: the launch's lone descriptor, copied to shared memory by the block
+// (a pointer to the kernel parameter itself would make the compiler copy the
+// whole parameter block into local memory)
+__device__ __forceinline__ const FuseBuf *unit_buf(const FuseWork &w, const FuseBuf *single, uint64_t u,
+                                                  uint64_t &local)
 {
     if (w.nbufs == 1) {
         local = u;
-        return &w.single;
+        return single;
     }
     uint32_t lo = 0, hi = w.nbufs;
     while (hi - lo > 1) {
@@ -280,7 +284,7 @@ __device__ __forceinline__ const FuseBuf *unit_buf(const FuseWork &w, uint64_t u
 }
 
 // one unit = one block row of 32 blocks (a warp), lane = block column
-__device__ __forceinline__ Slot slot_of(const FuseWork &w, uint64_t u, int lane)
+__device__ __forceinline__ Slot slot_of(const FuseWork &w, const FuseBuf *single, uint64_t u, int lane)
 {
     Slot sl;
     sl.on = false;
@@ -291,10 +295,16 @@ __device__ __forceinline__ Slot slot_of(const FuseWork &w, uint64_t u, int lane)
     if (u >= w.total_units)
         return sl;
     uint64_t local;
-    sl.b = unit_buf(w, u, local);
+    sl.b = unit_buf(w, single, u, local);
     const uint32_t strips = sl.b->strips;
-    sl.bi = local / strips;
-    sl.bj = (uint32_t)(local % strips) * 32 + lane;
+    if (local < (1ull << 32)) { // 32-bit division: a unit is one warp's 32 blocks, so it counts
+        const uint32_t l32 = (uint32_t)local, q = l32 / strips;
+        sl.bi = q;
+        sl.bj = (l32 - q * strips) * 32 + lane;
+    } else {
+        sl.bi = local / strips;
+        sl.bj = (uint32_t)(local % strips) * 32 + lane;
+    }
     sl.on = sl.bj * 8 < sl.b->W;
     sl.vec = sl.b->vec != 0;
     return sl;
@@ -385,7 +395,7 @@ __device__ __forceinline__ void block_rows(const FuseBuf &f, uint64_t bi, uint32
 template <bool PACKED, bool KEYED>
 __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged,
                                           const uint2 (&v)[8], uint32_t (&rb)[4], int *err,
-                                          const uint32_t (&key)[4])
+                                          const uint32_t (&key)[4], pkb::Stage *stg = nullptr, int lane = 0)
 {
     const uint32_t W = f.W, L = f.F;
     uint32_t x1[8][4]; // row-lifted rows, 4 words each
@@ -420,55 +430,50 @@ __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_
     col_lift<4, 2>(x2, s2, d2);
     if (PACKED) {
         // A: LL_2 - 128 (10 bits); B: HL_2, LH_2 (10), HH_2 (11); C: the
-        // level-1 details (10); B goes back to the warp (store_b)
-        bool ok = true;
-        uint32_t ra[2] = {0u, 0u}, rc[15];
+        // level-1 details (10), each pair of coefficients one field from its
+        // biased word; B goes back to the warp (put_b), A and C to the warp's
+        // staging area (copy_out)
+        uint32_t bad = 0u, ra[2] = {0u, 0u}, rc[15];
 #pragma unroll
         for (int i = 0; i < 15; ++i)
             rc[i] = 0u;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            pkb::put_pair(ra, 20 * r, ll_final(s2[r][0]), 10, ok);     // LL_2 - 128
-            pkb::put_pair(rb, 20 * r, to_i16x2(s2[r][1]), 10, ok);     // HL_2
-            pkb::put_pair(rb, 40 + 20 * r, to_i16x2(d2[r][0]), 10, ok); // LH_2
-            pkb::put_pair(rb, 80 + 22 * r, to_i16x2(d2[r][1]), 11, ok); // HH_2
+            const uint32_t a = s2[r][0] - 0x00800080u; // LL_2 - 128
+            bad |= pkb::range_bits<10>(a) | pkb::range_bits<10>(s2[r][1]) | pkb::range_bits<10>(d2[r][0]) |
+                   pkb::range_bits<11>(d2[r][1]);
+            pkb::ins(ra, 20 * r, pkb::field2<10>(a), 20);
+            pkb::ins(rb, 20 * r, pkb::field2<10>(s2[r][1]), 20);      // HL_2
+            pkb::ins(rb, 40 + 20 * r, pkb::field2<10>(d2[r][0]), 20); // LH_2
+            pkb::ins(rb, 80 + 22 * r, pkb::field2<11>(d2[r][1]), 22); // HH_2
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            pkb::put_pair(rc, 40 * r, to_i16x2(s1[r][2]), 10, ok); // HL_1
-            pkb::put_pair(rc, 40 * r + 20, to_i16x2(s1[r][3]), 10, ok);
-            pkb::put_pair(rc, 160 + 40 * r, to_i16x2(d1[r][0]), 10, ok); // LH_1
-            pkb::put_pair(rc, 180 + 40 * r, to_i16x2(d1[r][1]), 10, ok);
-            pkb::put_pair(rc, 320 + 40 * r, to_i16x2(d1[r][2]), 10, ok); // HH_1
-            pkb::put_pair(rc, 340 + 40 * r, to_i16x2(d1[r][3]), 10, ok);
+            bad |= pkb::range_bits<10>(s1[r][2]) | pkb::range_bits<10>(s1[r][3]) | pkb::range_bits<10>(d1[r][0]) |
+                   pkb::range_bits<10>(d1[r][1]) | pkb::range_bits<10>(d1[r][2]) | pkb::range_bits<10>(d1[r][3]);
+            pkb::ins(rc, 40 * r, pkb::field2<10>(s1[r][2]), 20); // HL_1
+            pkb::ins(rc, 40 * r + 20, pkb::field2<10>(s1[r][3]), 20);
+            pkb::ins(rc, 160 + 40 * r, pkb::field2<10>(d1[r][0]), 20); // LH_1
+            pkb::ins(rc, 180 + 40 * r, pkb::field2<10>(d1[r][1]), 20);
+            pkb::ins(rc, 320 + 40 * r, pkb::field2<10>(d1[r][2]), 20); // HH_1
+            pkb::ins(rc, 340 + 40 * r, pkb::field2<10>(d1[r][3]), 20);
         }
-        if (!ok)
+        if (bad)
             atomicCAS(err, 0, pkb::kErrWidth);
         const uint64_t idx = bi * (uint64_t)(W >> 3) + bj;
         if (KEYED && f.keyed) { // B' = B ^ H1(A), then C' = C ^ H2(B')
             sha::mask_b(key, f.nonce, idx, ra, rb);
             sha::mask_c(key, f.nonce, idx, rb, rc);
         }
-        uint8_t *pa = f.pk[0] + 5 * idx;
-        pa[0] = (uint8_t)ra[0];
-        pa[1] = (uint8_t)(ra[0] >> 8);
-        pa[2] = (uint8_t)(ra[0] >> 16);
-        pa[3] = (uint8_t)(ra[0] >> 24);
-        pa[4] = (uint8_t)ra[1];
-        uint8_t *pc = f.pk[2] + 60 * idx;
-        if ((reinterpret_cast<uintptr_t>(f.pk[2]) & 3u) == 0) {
+        uint8_t *sa = stg->a + 5 * lane;
+        sa[0] = (uint8_t)ra[0];
+        sa[1] = (uint8_t)(ra[0] >> 8);
+        sa[2] = (uint8_t)(ra[0] >> 16);
+        sa[3] = (uint8_t)(ra[0] >> 24);
+        sa[4] = (uint8_t)ra[1];
 #pragma unroll
-            for (int i = 0; i < 15; ++i)
-                __stcs(reinterpret_cast<unsigned int *>(pc) + i, rc[i]);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 15; ++i) {
-                pc[4 * i] = (uint8_t)rc[i];
-                pc[4 * i + 1] = (uint8_t)(rc[i] >> 8);
-                pc[4 * i + 2] = (uint8_t)(rc[i] >> 16);
-                pc[4 * i + 3] = (uint8_t)(rc[i] >> 24);
-            }
-        }
+        for (int i = 0; i < 15; ++i)
+            stg->c[15 * lane + i] = rc[i];
         return;
     }
     const uint32_t W2 = W >> 2;
@@ -501,30 +506,24 @@ __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_
 template <bool PACKED, bool KEYED>
 __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged,
                                           bool vec, uint32_t s8, uint32_t s4, const uint32_t (&rb_in)[4],
-                                          const uint32_t (&key)[4])
+                                          const uint32_t (&key)[4], const pkb::StageIn *stg = nullptr,
+                                          int lane = 0)
 {
     const uint32_t W = f.W, L = f.F;
     const uint32_t W1 = W >> 1, W2 = W >> 2, W3 = W >> 3;
     uint32_t s1[4][4], d1[4][4];
     if (PACKED) {
-        // the block's A (deciphered) and C records, and its B record from the warp
+        // the block's A (deciphered) and C records from the warp's staging
+        // area, and its B record from the warp
         const uint64_t idx = bi * (uint64_t)W3 + bj;
-        const uint8_t *pa = f.pk[0] + 5 * idx;
-        const uint32_t ra[2] = {(uint32_t)pa[0] | ((uint32_t)pa[1] << 8) | ((uint32_t)pa[2] << 16) |
-                                    ((uint32_t)pa[3] << 24),
-                                (uint32_t)pa[4]};
+        const uint8_t *sa = stg->a + 5 * lane;
+        const uint32_t ra[2] = {(uint32_t)sa[0] | ((uint32_t)sa[1] << 8) | ((uint32_t)sa[2] << 16) |
+                                    ((uint32_t)sa[3] << 24),
+                                (uint32_t)sa[4]};
         uint32_t rc[15];
-        const uint8_t *pc = f.pk[2] + 60 * idx;
-        if ((reinterpret_cast<uintptr_t>(f.pk[2]) & 3u) == 0) {
 #pragma unroll
-            for (int i = 0; i < 15; ++i)
-                rc[i] = __ldg(reinterpret_cast<const unsigned int *>(pc) + i);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 15; ++i)
-                rc[i] = (uint32_t)pc[4 * i] | ((uint32_t)pc[4 * i + 1] << 8) | ((uint32_t)pc[4 * i + 2] << 16) |
-                        ((uint32_t)pc[4 * i + 3] << 24);
-        }
+        for (int i = 0; i < 15; ++i)
+            rc[i] = stg->c[15 * lane + i];
         uint32_t rb[4] = {rb_in[0], rb_in[1], rb_in[2], rb_in[3]};
         if (KEYED && f.keyed) { // C = C' ^ H2(B') first, then B = B' ^ H1(A)
             sha::mask_c(key, f.nonce, idx, rb, rc);
@@ -533,22 +532,22 @@ __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_
         uint32_t s2[2][2], d2[2][2];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            s2[r][0] = from_i16x2(pkb::get_pair(ra, 20 * r, 10)) + 0x00800080u;
-            s2[r][1] = from_i16x2(pkb::get_pair(rb, 20 * r, 10));
-            d2[r][0] = from_i16x2(pkb::get_pair(rb, 40 + 20 * r, 10));
-            d2[r][1] = from_i16x2(pkb::get_pair(rb, 80 + 22 * r, 11));
+            s2[r][0] = pkb::unfield2<10>(pkb::ext(ra, 20 * r, 20)) + 0x00800080u;
+            s2[r][1] = pkb::unfield2<10>(pkb::ext(rb, 20 * r, 20));
+            d2[r][0] = pkb::unfield2<10>(pkb::ext(rb, 40 + 20 * r, 20));
+            d2[r][1] = pkb::unfield2<11>(pkb::ext(rb, 80 + 22 * r, 22));
         }
         uint32_t x2[4][2];
         col_unlift<4, 2>(s2, d2, x2);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             unlift4(x2[r][0], x2[r][1], s1[r][0], s1[r][1]);
-            s1[r][2] = from_i16x2(pkb::get_pair(rc, 40 * r, 10));
-            s1[r][3] = from_i16x2(pkb::get_pair(rc, 40 * r + 20, 10));
-            d1[r][0] = from_i16x2(pkb::get_pair(rc, 160 + 40 * r, 10));
-            d1[r][1] = from_i16x2(pkb::get_pair(rc, 180 + 40 * r, 10));
-            d1[r][2] = from_i16x2(pkb::get_pair(rc, 320 + 40 * r, 10));
-            d1[r][3] = from_i16x2(pkb::get_pair(rc, 340 + 40 * r, 10));
+            s1[r][2] = pkb::unfield2<10>(pkb::ext(rc, 40 * r, 20));
+            s1[r][3] = pkb::unfield2<10>(pkb::ext(rc, 40 * r + 20, 20));
+            d1[r][0] = pkb::unfield2<10>(pkb::ext(rc, 160 + 40 * r, 20));
+            d1[r][1] = pkb::unfield2<10>(pkb::ext(rc, 180 + 40 * r, 20));
+            d1[r][2] = pkb::unfield2<10>(pkb::ext(rc, 320 + 40 * r, 20));
+            d1[r][3] = pkb::unfield2<10>(pkb::ext(rc, 340 + 40 * r, 20));
         }
     } else {
     // LL_1: from the input (one level) or from the levels above
@@ -657,22 +656,102 @@ __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_
     }
 }
 
+// the packed record areas of a unit (A, B and C of its 32 blocks), and
+// whether the warp can prefetch them whole
+struct Areas {
+    const uint8_t *a, *b, *c;
+    uint32_t nvalid;
+    bool full;
+};
+__device__ __forceinline__ Areas areas_of(const Slot &sl)
+{
+    Areas r{nullptr, nullptr, nullptr, 0u, false};
+    if (!sl.b)
+        return r;
+    const uint32_t nbx = sl.b->W >> 3, s = sl.bj >> 5;
+    const uint64_t idx0 = sl.bi * (uint64_t)nbx + 32ull * s;
+    r.nvalid = min(32u, nbx - 32 * s);
+    r.a = sl.b->pk[0] + 5 * idx0;
+    r.b = sl.b->pk[1] + sl.bi * pkb::b_row_bytes(nbx) + 496ull * s;
+    r.c = sl.b->pk[2] + 60 * idx0;
+    r.full = pkb::full_aligned(r.nvalid, r.a, r.b, r.c);
+    return r;
+}
+
 // the inverse reads four times as many tiles per block as the forward;
 // it runs best with direct loads and many warps, the forward with the ring
 // PACKED: every buffer of the launch is packed (the warp stores or loads its
 // blocks' B records between blocks, which the staged loop below does not
 // allow for); the inverse, and any packed launch, take direct loads
+#ifndef BLOCK_PACKED_FWD_MINB
+#define BLOCK_PACKED_FWD_MINB 5
+#endif
+// the packed forward: five 4-warp blocks an SM (registers capped at 102)
 template <bool FWD, bool PACKED, bool KEYED>
-__global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
+__global__ void __launch_bounds__(kThreads, (FWD && PACKED && !KEYED) ? BLOCK_PACKED_FWD_MINB : 1)
+    block_kernel(FuseWork w)
 {
+    __shared__ FuseBuf s_single;
+    if (threadIdx.x == 0)
+        s_single = w.single;
+    __syncthreads();
     uint32_t key[4] = {0u, 0u, 0u, 0u}; // the AES key's words, big-endian (keyed buffers)
     if (KEYED) {
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             key[i] = __ldg(w.key_words + i);
     }
+    if (PACKED && !FWD) {
+        // the packed inverse: a warp's records (A deciphered, B, C) come into
+        // one of two staging areas with cp.async while the unit before is
+        // transformed (full warps whose three areas are 16-byte aligned);
+        // other units load them synchronously
+        __shared__ uint32_t sb[kWarps][pkb::kPackBWords];
+        __shared__ pkb::StageIn stg_in[kWarps][2];
+        grid_release();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const uint64_t G = (uint64_t)gridDim.x * kWarps;
+        const uint64_t u0 = (uint64_t)blockIdx.x * kWarps + warp;
+        {
+            const Slot s0 = slot_of(w, &s_single, u0, lane);
+            const Areas a0 = areas_of(s0);
+            if (a0.full)
+                pkb::prefetch_full(stg_in[warp][0], a0.a, a0.b, a0.c, lane);
+            cp_commit();
+        }
+        uint32_t i = 0;
+        for (uint64_t u = u0; u < w.total_units; u += G, ++i) {
+            const Slot sl = slot_of(w, &s_single, u, lane);
+            const Areas ar = areas_of(sl);
+            {
+                const Slot nx = slot_of(w, &s_single, u + G, lane);
+                const Areas an = areas_of(nx);
+                if (an.full)
+                    pkb::prefetch_full(stg_in[warp][(i + 1) & 1], an.a, an.b, an.c, lane);
+                cp_commit();
+            }
+            cp_wait<1>(); // this unit's group has landed
+            __syncwarp();
+            pkb::StageIn &cur = stg_in[warp][i & 1];
+            uint32_t rb[4] = {0u, 0u, 0u, 0u};
+            if (ar.full) {
+                pkb::b_from_stage(cur, sl.on, lane, rb);
+            } else {
+                pkb::get_b(sb[warp], ar.b, (124 * ar.nvalid + 7) / 8, sl.on, lane, rb);
+                pkb::copy_in(cur.a, ar.a, 5 * ar.nvalid, lane);
+                pkb::copy_in(reinterpret_cast<uint8_t *>(cur.c), ar.c, 60 * ar.nvalid, lane);
+                __syncwarp();
+            }
+            if (sl.on)
+                inv_block<true, KEYED>(*sl.b, sl.bi, sl.bj, false, sl.vec, 0, 0, rb, key, &cur, lane);
+            __syncwarp(); // every lane is done with this area before it is refilled
+        }
+        cp_wait<0>();
+        return;
+    }
     if (!FWD || PACKED) {
         __shared__ uint32_t sb[kWarps][pkb::kPackBWords]; // a warp's B records
+        __shared__ pkb::Stage stg_all[PACKED ? kWarps : 1]; // a warp's A and C records
         grid_release();
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const uint64_t G = (uint64_t)gridDim.x * kWarps;
@@ -680,34 +759,44 @@ __global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
         // the current one is transformed
         uint2 rows[8];
         if (FWD) {
-            const Slot s0 = slot_of(w, (uint64_t)blockIdx.x * kWarps + warp, lane);
+            const Slot s0 = slot_of(w, &s_single, (uint64_t)blockIdx.x * kWarps + warp, lane);
             if (s0.on)
                 block_rows(*s0.b, s0.bi, s0.bj, false, s0.vec, 0, rows);
         }
         for (uint64_t u = (uint64_t)blockIdx.x * kWarps + warp; u < w.total_units; u += G) {
-            const Slot sl = slot_of(w, u, lane);
+            const Slot sl = slot_of(w, &s_single, u, lane);
             uint32_t rb[4] = {0u, 0u, 0u, 0u};
             const uint32_t nbx = sl.b->W >> 3, s = sl.bj >> 5, nvalid = min(32u, nbx - 32 * s);
             uint8_t *bbase = PACKED ? sl.b->pk[1] + sl.bi * pkb::b_row_bytes(nbx) + 496ull * s : nullptr;
             const uint32_t bcount = (124 * nvalid + 7) / 8;
-            if (PACKED && !FWD) // the whole warp: its blocks' B records
-                pkb::get_b(sb[warp], bbase, bcount, sl.on, lane, rb);
+            pkb::Stage *stg = &stg_all[PACKED ? warp : 0];
+            const uint64_t idx0 = PACKED ? sl.bi * (uint64_t)nbx + 32ull * s : 0;
             if (FWD) {
                 // this block's rows came with the previous unit; fetch the next unit's
                 uint2 v[8];
 #pragma unroll
                 for (int r = 0; r < 8; ++r)
                     v[r] = rows[r];
-                const Slot nx = slot_of(w, u + G, lane);
+                const Slot nx = slot_of(w, &s_single, u + G, lane);
                 if (nx.on)
                     block_rows(*nx.b, nx.bi, nx.bj, false, nx.vec, 0, rows);
                 if (sl.on)
-                    fwd_block<PACKED, KEYED>(*sl.b, sl.bi, sl.bj, false, v, rb, w.err, key);
+                    fwd_block<PACKED, KEYED>(*sl.b, sl.bi, sl.bj, false, v, rb, w.err, key, stg, lane);
             } else if (sl.on) {
-                inv_block<PACKED, KEYED>(*sl.b, sl.bi, sl.bj, false, sl.vec, 0, 0, rb, key);
+                inv_block<false, KEYED>(*sl.b, sl.bi, sl.bj, false, sl.vec, 0, 0, rb, key);
             }
-            if (PACKED && FWD)
+            if (PACKED && FWD) {
                 pkb::put_b(sb[warp], bbase, bcount, sl.on, lane, rb);
+                __syncwarp();
+                uint8_t *pa = sl.b->pk[0] + 5 * idx0, *pc = sl.b->pk[2] + 60 * idx0;
+                if (pkb::full_aligned(nvalid, pa, bbase, pc)) {
+                    pkb::copy_out_full(pa, pc, *stg, lane);
+                } else {
+                    pkb::copy_out(pa, stg->a, 5 * nvalid, lane);
+                    pkb::copy_out(pc, reinterpret_cast<const uint8_t *>(stg->c), 60 * nvalid, lane);
+                }
+                __syncwarp();
+            }
         }
         return;
     }
@@ -723,7 +812,7 @@ __global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
     static_assert(kDepth == 3, "the unit loop below is unrolled for three stages");
     // the blocks of the units in flight, in stages 0, 1, 2 (static indices
     // keep them in registers)
-    Slot q0 = slot_of(w, u0, lane), q1 = slot_of(w, u0 + G, lane), q2;
+    Slot q0 = slot_of(w, &s_single, u0, lane), q1 = slot_of(w, &s_single, u0 + G, lane), q2;
     if (FWD) {
         fwd_issue(q0, ring8);
         fwd_issue(q1, ring8 + stage);
@@ -734,7 +823,7 @@ __global__ void __launch_bounds__(kThreads) block_kernel(FuseWork w)
     // unit i computes from stage i % 3 after issuing unit i + 2 into stage
     // (i + 2) % 3, the one unit i - 1 freed
     auto step = [&](uint64_t i, Slot &cur, Slot &ahead, uint32_t cur_off, uint32_t ahead_off) {
-        ahead = slot_of(w, u0 + (i + 2) * G, lane);
+        ahead = slot_of(w, &s_single, u0 + (i + 2) * G, lane);
         if (FWD)
             fwd_issue(ahead, ring8 + ahead_off);
         else

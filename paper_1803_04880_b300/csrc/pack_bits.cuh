@@ -9,8 +9,11 @@
 // one record per block (5 and 60 bytes), blocks row-major; in B the blocks
 // of a block row follow each other every 124 bits and every block row starts
 // on a byte.  A warp owns 32 neighbouring blocks of a block row, so its B
-// records are 496 contiguous bytes, assembled in (or read from) a shared
-// area of kPackBWords words.
+// records are 496 contiguous bytes, assembled from the lanes' registers
+// with shuffles (or in a shared area of kPackBWords words when unaligned),
+// and its A and C records are 160 and 1,920 contiguous bytes, which the
+// lanes write to (read from) a shared staging area and the warp moves with
+// 16-byte accesses.
 #pragma once
 
 #include <cstdint>
@@ -20,55 +23,6 @@ namespace pkb {
 
 constexpr int kPackBWords = 125; // 124 words of a warp's B records and one more read on unpack
 constexpr int kErrWidth = 5;     // device error code: a coefficient outside its width
-
-__device__ __forceinline__ bool fits(int32_t v, int width)
-{
-    return v >= -(1 << (width - 1)) && v < (1 << (width - 1));
-}
-
-// value v as `width` bits at bit pos of the record r (zeroed first)
-template <int N>
-__device__ __forceinline__ void put(uint32_t (&r)[N], int pos, int32_t v, int width)
-{
-    const uint32_t u = (uint32_t)v & ((1u << width) - 1u);
-    const int q = pos >> 5, sh = pos & 31;
-    r[q] |= u << sh;
-    if (sh + width > 32)
-        r[q + 1] |= u >> (32 - sh);
-}
-
-template <int N>
-__device__ __forceinline__ int32_t get(const uint32_t (&r)[N], int pos, int width)
-{
-    const int q = pos >> 5, sh = pos & 31;
-    uint32_t u = r[q] >> sh;
-    if (sh + width > 32)
-        u |= r[q + 1] << (32 - sh);
-    return (int32_t)(u << (32 - width)) >> (32 - width); // sign-extend
-}
-
-__device__ __forceinline__ int32_t lo16(uint32_t w) { return (int32_t)(int16_t)(w & 0xffffu); }
-__device__ __forceinline__ int32_t hi16(uint32_t w) { return (int32_t)(int16_t)(w >> 16); }
-__device__ __forceinline__ uint32_t pair16(int32_t a, int32_t b)
-{
-    return ((uint32_t)a & 0xffffu) | ((uint32_t)b << 16);
-}
-
-// the two int16 halves of w at bits pos and pos + width of r; ok &= both fit
-template <int N>
-__device__ __forceinline__ void put_pair(uint32_t (&r)[N], int pos, uint32_t w, int width, bool &ok)
-{
-    ok = ok && fits(lo16(w), width) && fits(hi16(w), width);
-    put(r, pos, lo16(w), width);
-    put(r, pos + width, hi16(w), width);
-}
-
-// the int16 pair at bits pos and pos + width of r
-template <int N>
-__device__ __forceinline__ uint32_t get_pair(const uint32_t (&r)[N], int pos, int width)
-{
-    return pair16(get(r, pos, width), get(r, pos + width, width));
-}
 
 // bytes of B a block row of nbx blocks takes
 __host__ __device__ inline uint64_t b_row_bytes(uint64_t nbx) { return (124 * nbx + 7) / 8; }
@@ -221,6 +175,194 @@ __device__ __forceinline__ void get_b(uint32_t *sb, const uint8_t *base, uint32_
         load_b_vec(base, count, valid, lane, rb);
     else
         load_b(sb, base, count, valid, lane, rb);
+}
+
+// -- biased pairs straight to fields -------------------------------------
+// The kernels carry a pair of coefficients as one word, v + 0x4000 in each
+// 16-bit half (|v| < 0x4000).  0x4000 is a multiple of 2^K for the widths
+// here, so the low K bits of a half are v's K-bit two's complement: a pair
+// becomes its 2K-bit field (low value first) with one shift and one select,
+// and both halves are range-checked with one subtraction and one mask.
+
+// the pair's 2K-bit field: (v_lo mod 2^K) | (v_hi mod 2^K) << K
+template <int K>
+__device__ __forceinline__ uint32_t field2(uint32_t w)
+{
+    constexpr uint32_t m = (1u << K) - 1u;
+    return (w & m) | ((w >> (16 - K)) & (m << K));
+}
+
+// nonzero when a half of the pair is outside [-2^(K-1), 2^(K-1)): v + 0x4000
+// - (0x4000 - 2^(K-1)) is in [0, 2^K) exactly when v fits (a borrow out of
+// the low half only happens when the low half is already out of range)
+template <int K>
+__device__ __forceinline__ uint32_t range_bits(uint32_t w)
+{
+    constexpr uint32_t c = (0x4000u - (1u << (K - 1))) * 0x10001u;
+    constexpr uint32_t hi = (0xffffu & ~((1u << K) - 1u)) * 0x10001u;
+    return (w - c) & hi;
+}
+
+// the biased pair of a 2K-bit field: flipping a K-bit two's complement's
+// sign bit adds 2^(K-1), then the bias less 2^(K-1)
+template <int K>
+__device__ __forceinline__ uint32_t unfield2(uint32_t f)
+{
+    constexpr uint32_t m = (1u << K) - 1u, h = 1u << (K - 1), c = 0x4000u - h;
+    const uint32_t p = (f & m) | ((f << (16 - K)) & (m << 16));
+    return (p ^ (h * 0x10001u)) + c * 0x10001u;
+}
+
+// field f of `bits` bits (at most 32) into record r at bit pos, r zeroed
+// first (pos and bits are constants once the callers' loops unroll)
+template <int N>
+__device__ __forceinline__ void ins(uint32_t (&r)[N], int pos, uint32_t f, int bits)
+{
+    const int q = pos >> 5, sh = pos & 31;
+    r[q] |= f << sh;
+    if (sh + bits > 32)
+        r[q + 1] |= f >> (32 - sh);
+}
+
+template <int N>
+__device__ __forceinline__ uint32_t ext(const uint32_t (&r)[N], int pos, int bits)
+{
+    const int q = pos >> 5, sh = pos & 31;
+    const uint32_t u = (sh + bits > 32) ? __funnelshift_r(r[q], r[q + 1], (uint32_t)sh) : (r[q] >> sh);
+    return bits == 32 ? u : (u & ((1u << bits) - 1u));
+}
+
+// -- a warp's A or C records between its shared staging area and memory ----
+// The records of the warp's 32 blocks are contiguous (count bytes at dst /
+// src); every lane of the warp calls these.  16-byte accesses when the
+// global address allows, else 4-byte, else bytes.
+__device__ __forceinline__ void copy_out(uint8_t *dst, const uint8_t *sm, uint32_t count, int lane)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(dst);
+    uint32_t done = 0;
+    if ((a & 15u) == 0) {
+        const uint32_t n = count >> 4;
+        for (uint32_t j = (uint32_t)lane; j < n; j += 32)
+            __stcs(reinterpret_cast<uint4 *>(dst) + j, reinterpret_cast<const uint4 *>(sm)[j]);
+        done = n << 4;
+    } else if ((a & 3u) == 0) {
+        const uint32_t n = count >> 2;
+        for (uint32_t j = (uint32_t)lane; j < n; j += 32)
+            __stcs(reinterpret_cast<unsigned int *>(dst) + j, reinterpret_cast<const unsigned int *>(sm)[j]);
+        done = n << 2;
+    }
+    for (uint32_t j = done + (uint32_t)lane; j < count; j += 32)
+        dst[j] = sm[j];
+}
+
+__device__ __forceinline__ void copy_in(uint8_t *sm, const uint8_t *src, uint32_t count, int lane)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+    uint32_t done = 0;
+    if ((a & 15u) == 0) {
+        const uint32_t n = count >> 4;
+        for (uint32_t j = (uint32_t)lane; j < n; j += 32)
+            reinterpret_cast<uint4 *>(sm)[j] = __ldg(reinterpret_cast<const uint4 *>(src) + j);
+        done = n << 4;
+    } else if ((a & 3u) == 0) {
+        const uint32_t n = count >> 2;
+        for (uint32_t j = (uint32_t)lane; j < n; j += 32)
+            reinterpret_cast<unsigned int *>(sm)[j] = __ldg(reinterpret_cast<const unsigned int *>(src) + j);
+        done = n << 2;
+    }
+    for (uint32_t j = done + (uint32_t)lane; j < count; j += 32)
+        sm[j] = __ldg(src + j);
+}
+
+// a warp's staging area: C records (15 words a block, block j at word 15 j:
+// 15 is odd, so the 32 lanes' words fall in 32 banks), A records (5 bytes a
+// block) and, on the way in, the raw B bytes (496 and a zero chunk)
+constexpr int kStageCWords = 15 * 32;
+constexpr int kStageABytes = 5 * 32;
+constexpr int kStageBBytes = 512;
+struct __align__(16) Stage {
+    uint32_t c[kStageCWords];
+    uint8_t a[kStageABytes];
+};
+struct __align__(16) StageIn {
+    uint32_t c[kStageCWords];
+    uint8_t a[kStageABytes];
+    uint8_t b[kStageBBytes];
+};
+
+// A full warp of 32 blocks whose three record areas are 16-byte aligned:
+// 1,920 bytes of C, 160 of A, 496 of B, all whole 16-byte pieces
+constexpr uint32_t kFullC16 = 120, kFullA16 = 10, kFullB16 = 31;
+__device__ __forceinline__ bool full_aligned(uint32_t nvalid, const void *a, const void *b, const void *c)
+{
+    return nvalid == 32 &&
+           ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(c)) & 15u) ==
+               0;
+}
+
+// the A and C records of a full aligned warp out of its staging area: fixed
+// trip counts, no loop control
+__device__ __forceinline__ void copy_out_full(uint8_t *a, uint8_t *c, const Stage &st, int lane)
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t j = (uint32_t)lane + 32u * k;
+        if (j < kFullC16)
+            __stcs(reinterpret_cast<uint4 *>(c) + j, reinterpret_cast<const uint4 *>(st.c)[j]);
+    }
+    if ((uint32_t)lane < kFullA16)
+        __stcs(reinterpret_cast<uint4 *>(a) + lane, reinterpret_cast<const uint4 *>(st.a)[lane]);
+}
+
+// the next unit's A, B and C records of a full aligned warp into a staging
+// area with cp.async (16 bytes a copy, every lane its share); the caller
+// commits the group and waits for it before reading
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void prefetch_full(StageIn &st, const uint8_t *a, const uint8_t *b, const uint8_t *c,
+                                              int lane)
+{
+    const uint32_t sc = (uint32_t)__cvta_generic_to_shared(st.c);
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(st.a);
+    const uint32_t sbb = (uint32_t)__cvta_generic_to_shared(st.b);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t j = (uint32_t)lane + 32u * k;
+        if (j < kFullC16)
+            cp16(sc + 16u * j, c + 16u * j);
+    }
+    if ((uint32_t)lane < kFullA16)
+        cp16(sa + 16u * lane, a + 16u * lane);
+    if ((uint32_t)lane < kFullB16)
+        cp16(sbb + 16u * lane, b + 16u * lane);
+}
+
+// the lane's B record from the raw B bytes of its warp in shared memory
+// (chunk j holds bits 4 j .. 123 of block j and the start of block j + 1's)
+__device__ __forceinline__ void b_from_stage(const StageIn &st, bool valid, int lane, uint32_t (&rb)[4])
+{
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    if ((uint32_t)lane < kFullB16) {
+        const uint4 v = reinterpret_cast<const uint4 *>(st.b)[lane];
+        w[0] = v.x;
+        w[1] = v.y;
+        w[2] = v.z;
+        w[3] = v.w;
+    }
+    uint32_t pv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        pv[i] = __shfl_up_sync(0xffffffffu, w[i], 1);
+    const U128 x = shr128(u128(pv), 128u - 4u * (uint32_t)lane);
+    const U128 y = shl128(u128(w), 4u * (uint32_t)lane);
+    if (valid) {
+        rb[0] = (uint32_t)(x.lo | y.lo);
+        rb[1] = (uint32_t)((x.lo | y.lo) >> 32);
+        rb[2] = (uint32_t)(x.hi | y.hi);
+        rb[3] = (uint32_t)((x.hi | y.hi) >> 32) & 0x0fffffffu;
+    }
 }
 
 } // namespace pkb

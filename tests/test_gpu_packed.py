@@ -37,7 +37,7 @@ def _packed_plan(fr, W):
     return plan
 
 
-@pytest.mark.parametrize("offset", [0, 1])
+@pytest.mark.parametrize("offset", [0, 1, 4])
 @pytest.mark.parametrize("W,n", [(64, 64 * 16), (72, 72 * 24 - 5), (264, 264 * 40 - 3),
                                  (8, 8 * 8 * 5), (4096, 4096 * 64 + 11), (512, 512 * 100)])
 def test_matches_oracle(fr, key, W, n, offset):
