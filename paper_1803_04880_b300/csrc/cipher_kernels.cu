@@ -43,8 +43,8 @@ __global__ void __launch_bounds__(kCtrThreads, 1) ctr_kernel(CtrWork w)
             ch = w.chunks[c];
         } else {
             ch = w.single;
-            ch.first_block = c * w.single_chunk;
-            ch.nblocks = min(w.single_chunk, w.single.nblocks - ch.first_block);
+            ch.first_block = w.single.first_block + c * w.single_chunk;
+            ch.nblocks = min(w.single_chunk, w.single.nblocks - c * w.single_chunk);
         }
         const bool vec = (((uintptr_t)ch.in | (uintptr_t)ch.out) & 15u) == 0;
         aes::Round1 R = aes::round1_consts(L, w.keys, ch.nonce, (uint32_t)(ch.first_block >> 32));

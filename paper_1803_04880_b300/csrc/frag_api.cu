@@ -1092,6 +1092,254 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
 }
 
 // ---------------------------------------------------------------------------
+// Host-buffer forms pipelined by row bands
+//
+// A buffer whose levels all run in the first fused pass (L <= 3) is cut into
+// bands of whole fused segments.  Band k's copies in, its kernels and its
+// copies out run on three streams, so band k + 1 arrives over PCIe while
+// band k is transformed and band k - 1 leaves.  What a band needs and makes
+// follows from the fused kernel's row schedule: the forward's iteration t
+// reads level-0 rows 8t-1 .. 8t+6 and writes level-l rows (8>>l) t - 1 ..
+// (8>>l) t + (8>>l) - 2; the inverse's iteration t reads level-l rows up to
+// (8>>l) t and writes level-0 rows 8t-7 .. 8t.  A band enciphers only the
+// AES blocks whose bytes are all written by then (CTR is its own inverse, so
+// no block may be done twice); recover deciphers, band by band, every block
+// the band's rows touch into the plaintext scratch the inverse reads.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kHostBands = 8;
+constexpr uint64_t kHostBandMin = 16ull << 20; // smaller buffers run in one piece
+
+struct Pipe {
+    cudaStream_t in = nullptr, out = nullptr;
+    std::vector<cudaEvent_t> ev;
+    ~Pipe()
+    {
+        for (cudaEvent_t e : ev)
+            cudaEventDestroy(e);
+        if (in)
+            cudaStreamDestroy(in);
+        if (out)
+            cudaStreamDestroy(out);
+    }
+    cudaError_t make(size_t events)
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&in, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking);
+        for (size_t i = 0; e == cudaSuccess && i < events; ++i) {
+            cudaEvent_t v = nullptr;
+            e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
+            if (e == cudaSuccess)
+                ev.push_back(v);
+        }
+        return e;
+    }
+};
+
+cudaError_t copy_async(void *dst, const void *src, uint64_t bytes, cudaMemcpyKind kind, cudaStream_t s)
+{
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, kind, s) : cudaSuccess;
+}
+
+// *done false: the buffer does not take the banded form (the caller runs
+// the plain one).  mem: device scratch of n + pb + ub bytes (each part at
+// a 256-byte boundary) and, for recover, the plaintext LL_L after them.
+frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t nonce, const uint8_t *h_a,
+                            const uint8_t *h_b, uint8_t *h_c, uint8_t *h_d, uint64_t n, cudaStream_t s,
+                            bool *done)
+{
+    *done = false;
+    if (n < kHostBandMin || plan->block || plan->packed || plan->levels > frag::kFuseMaxLevels ||
+        plan->path != FRAG_PATH_AUTO)
+        return FRAG_OK;
+    DeviceState *d = nullptr;
+    int dev = 0;
+    frag_status st = device_state(&d, &dev);
+    if (st != FRAG_OK)
+        return st;
+    const uint32_t W = plan->width, L = plan->levels;
+    const uint64_t H = rows_for(n, W, L);
+    if (H > 0xFFFFFFFFull)
+        return fail(FRAG_EINVAL, "buffer too tall for width %u", W);
+    const uint64_t pb = ll_bytes(H, W, L), ub = 2ull * H * W - pb;
+    const uint64_t a_n = align256(n), a_pb = align256(pb), a_ub = align256(ub);
+    const uint64_t ll_scr = fwd ? 0 : a_pb;
+    Buf b;
+    std::memset(&b, 0, sizeof(b));
+    b.W = W;
+    b.L = L;
+    b.H = (uint32_t)H;
+    b.n = n;
+    b.nonce = nonce;
+    uint8_t *mem = nullptr;
+    cudaError_t e = pool_malloc((void **)&mem, a_n + a_pb + a_ub + ll_scr, s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "pool_malloc(host-form buffers)");
+    uint8_t *d_data = mem, *d_priv = mem + a_n, *d_pub = d_priv + a_pb;
+    if (fwd) {
+        b.in = d_data;
+        b.priv = d_priv;
+        b.pub = d_pub;
+    } else {
+        b.out = d_data;
+        b.priv_in = d_priv;
+        b.pub_in = d_pub;
+        b.scr[L] = d_pub + a_ub;
+    }
+    fused_split(fwd, b, plan->path);
+    const uint32_t *rk = nullptr;
+    frag::FuseWork fw;
+    std::memset(&fw, 0, sizeof(fw));
+    uint64_t slots = 0;
+    bool ok = b.F1 == L && b.F2 == 0 && !b.kc;
+    if (ok && (st = key_on_device(key, dev, &rk)) == FRAG_OK &&
+        (st = fuse_slots(*d, fwd, false, plan->max_ctas, &slots)) == FRAG_OK) {
+        fw.single = fuse_buf(fwd, b, 1);
+        fw.nbufs = 1;
+        // units for kHostBands times the resident warps, so that every
+        // band's launch still fills the device
+        fuse_schedule(&fw.single, 1, slots * kHostBands, plan->seg_rows);
+        ok = fw.single.segs >= 2;
+    }
+    if (st != FRAG_OK || !ok) {
+        cudaFreeAsync(mem, s);
+        return st;
+    }
+    *done = true;
+    const frag::AesKeys keys = frag::aes::keys_from_words(key->rk);
+    const uint32_t segs = fw.single.segs, strips = fw.single.strips, seg = fw.single.seg_iters;
+    const uint32_t iters = fw.single.iters, K = std::min(kHostBands, segs);
+    Pipe p;
+    if ((e = p.make(2 * K + 1)) != cudaSuccess) {
+        cudaFreeAsync(mem, s);
+        return cuda_fail(e, "host-form streams");
+    }
+    const uint32_t WL = W >> L;
+    uint64_t row0 = 0;                     // level-0 rows moved so far
+    uint64_t lrow[frag::kFuseMaxLevels + 1] = {0, 0, 0, 0}; // level-l rows moved so far
+    uint64_t blk0 = 0;                     // AES blocks handled so far
+    const uint64_t nblk = (pb + 15) / 16;
+    const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
+    // the band pieces of level-l rows [r0, r1) of every detail band: in
+    // (recover) or out (protect)
+    auto band_rows = [&](uint32_t l, uint64_t r0, uint64_t r1, bool in, cudaStream_t cs) {
+        const uint64_t rowb = 2ull * (W >> l);
+        cudaError_t r = cudaSuccess;
+        for (uint32_t k = 0; k < 3 && r == cudaSuccess; ++k) {
+            const uint64_t off = frag::band_offset(b.H, W, L, l, k) + rowb * r0, len = rowb * (r1 - r0);
+            r = in ? copy_async(d_pub + off, h_b + off, len, h2d, cs) : copy_async(h_d + off, d_pub + off, len, d2h, cs);
+        }
+        return r;
+    };
+    for (uint32_t k = 0; k < K && e == cudaSuccess && st == FRAG_OK; ++k) {
+        const bool last = k + 1 == K;
+        const uint64_t sy0 = (uint64_t)k * segs / K, sy1 = (uint64_t)(k + 1) * segs / K;
+        const uint64_t t1 = last ? iters : std::min<uint64_t>(sy1 * seg, iters);
+        cudaEvent_t ev_in = p.ev[2 * k], ev_comp = p.ev[2 * k + 1];
+        frag::CtrChunk c;
+        std::memset(&c, 0, sizeof(c));
+        c.nonce = nonce;
+        c.bytes = pb;
+        if (fwd) {
+            // in: level-0 rows the band's iterations read
+            const uint64_t r1 = last ? H : std::min<uint64_t>(H, 8 * t1 + 8);
+            const uint64_t lo = std::min(n, row0 * W), hi = std::min(n, r1 * W);
+            e = copy_async(d_data + lo, h_a + lo, hi - lo, h2d, p.in);
+            row0 = r1;
+        } else {
+            // in: coefficient rows the band's iterations read, and the
+            // private blocks that cover its LL_L rows
+            for (uint32_t l = 1; l <= L && e == cudaSuccess; ++l) {
+                const uint64_t Hl = H >> l, r1 = last ? Hl : std::min<uint64_t>(Hl, (8u >> l) * t1 + 1);
+                if (r1 > lrow[l])
+                    e = band_rows(l, lrow[l], r1, true, p.in);
+                lrow[l] = std::max(lrow[l], r1);
+            }
+            const uint64_t bhi = last ? nblk : std::min<uint64_t>(nblk, (2ull * WL * lrow[L] + 15) / 16);
+            if (e == cudaSuccess && bhi > blk0)
+                e = copy_async(d_priv + 16 * blk0, h_a + 16 * blk0, std::min(pb, 16 * bhi) - 16 * blk0, h2d, p.in);
+            if (bhi > blk0) {
+                c.in = d_priv;
+                c.out = b.scr[L];
+                c.first_block = blk0;
+                c.nblocks = bhi - blk0;
+                blk0 = bhi;
+            }
+        }
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ev_in, p.in);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(s, ev_in, 0);
+        if (e != cudaSuccess)
+            break;
+        fw.unit_lo = sy0 * strips;
+        fw.total_units = (sy1 - sy0) * strips;
+        if (!fwd && c.nblocks)
+            st = ctr_launch(*d, keys, nullptr, 0, &c, s);
+        if (st == FRAG_OK)
+            st = fuse_launch(*d, fwd, false, fw, slots, s);
+        if (st == FRAG_OK && fwd) {
+            // encipher the blocks whose bytes are all written now
+            const uint64_t Hl = H >> L, r1 = last ? Hl : std::min<uint64_t>(Hl, (8u >> L) * t1 - 1);
+            const uint64_t bhi = last ? nblk : std::min<uint64_t>(nblk, 2ull * WL * r1 / 16);
+            if (bhi > blk0) {
+                c.in = d_priv;
+                c.out = d_priv;
+                c.first_block = blk0;
+                c.nblocks = bhi - blk0;
+                st = ctr_launch(*d, keys, nullptr, 0, &c, s);
+            }
+        }
+        if (st != FRAG_OK)
+            break;
+        if ((e = cudaEventRecord(ev_comp, s)) == cudaSuccess)
+            e = cudaStreamWaitEvent(p.out, ev_comp, 0);
+        if (e != cudaSuccess)
+            break;
+        if (fwd) {
+            // out: the detail rows and the enciphered blocks the band finished
+            for (uint32_t l = 1; l <= L && e == cudaSuccess; ++l) {
+                const uint64_t Hl = H >> l, r1 = last ? Hl : std::min<uint64_t>(Hl, (8u >> l) * t1 - 1);
+                if (r1 > lrow[l])
+                    e = band_rows(l, lrow[l], r1, false, p.out);
+                lrow[l] = std::max(lrow[l], r1);
+            }
+            const uint64_t Hl = H >> L, r1 = last ? Hl : std::min<uint64_t>(Hl, (8u >> L) * t1 - 1);
+            const uint64_t bhi = last ? nblk : std::min<uint64_t>(nblk, 2ull * WL * r1 / 16);
+            if (e == cudaSuccess && bhi > blk0)
+                e = copy_async(h_c + 16 * blk0, d_priv + 16 * blk0, std::min(pb, 16 * bhi) - 16 * blk0, d2h, p.out);
+            blk0 = std::max(blk0, bhi);
+        } else {
+            // out: the level-0 rows the band wrote
+            const uint64_t r1 = last ? H : std::min<uint64_t>(H, 8 * t1 - 7);
+            const uint64_t lo = std::min(n, row0 * W), hi = std::min(n, r1 * W);
+            e = copy_async(h_c + lo, d_data + lo, hi - lo, d2h, p.out);
+            row0 = std::max(row0, r1);
+        }
+    }
+    if (e == cudaSuccess && st == FRAG_OK && (e = cudaEventRecord(p.ev[2 * K], p.out)) == cudaSuccess)
+        e = cudaStreamWaitEvent(s, p.ev[2 * K], 0);
+    if (e != cudaSuccess || st != FRAG_OK) { // copies may still be in flight on the side streams
+        cudaStreamSynchronize(p.in);
+        cudaStreamSynchronize(p.out);
+    }
+    cudaFreeAsync(mem, s);
+    // the copies read and write the caller's host buffers: nothing returns
+    // before they are done
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaError_t e3 = cudaStreamSynchronize(p.out);
+    if (st != FRAG_OK)
+        return st;
+    if (e != cudaSuccess)
+        return cuda_fail(e, "host-form band copies");
+    if (e2 != cudaSuccess)
+        return cuda_fail(e2, "cudaStreamSynchronize");
+    if (e3 != cudaSuccess)
+        return cuda_fail(e3, "cudaStreamSynchronize");
+    return FRAG_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Batches: buffers, most work first, cut into waves whose scratch fits a
 // budget; one launch per wave over an explicit dependency-ordered unit list
 // ---------------------------------------------------------------------------
@@ -2008,6 +2256,11 @@ frag_status frag_protect_host(frag_plan plan, frag_key key, uint64_t nonce, cons
     if (key == nullptr || h_in == nullptr || h_private == nullptr || h_public == nullptr)
         return fail(FRAG_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
+    bool banded = false;
+    st = run_host_banded(true, plan, key, nonce, (const uint8_t *)h_in, nullptr, (uint8_t *)h_private,
+                         (uint8_t *)h_public, nbytes, s, &banded);
+    if (st != FRAG_OK || banded)
+        return st;
     uint8_t *mem = nullptr;
     cudaError_t e = pool_malloc((void **)&mem, nbytes + pb + ub + 512, s);
     if (e != cudaSuccess)
@@ -2045,6 +2298,11 @@ frag_status frag_recover_host(frag_plan plan, frag_key key, uint64_t nonce, cons
     if (key == nullptr || h_out == nullptr || h_private == nullptr || h_public == nullptr)
         return fail(FRAG_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
+    bool banded = false;
+    st = run_host_banded(false, plan, key, nonce, (const uint8_t *)h_private, (const uint8_t *)h_public,
+                         (uint8_t *)h_out, nullptr, nbytes, s, &banded);
+    if (st != FRAG_OK || banded)
+        return st;
     uint8_t *mem = nullptr;
     cudaError_t e = pool_malloc((void **)&mem, nbytes + pb + ub + 512, s);
     if (e != cudaSuccess)

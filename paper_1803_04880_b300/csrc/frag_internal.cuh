@@ -168,7 +168,7 @@ struct CtrChunk {
     uint64_t nonce;
     uint64_t first_block;
     uint64_t bytes;
-    uint64_t nblocks; // lone fragment: all of its blocks; chunk list: this chunk's
+    uint64_t nblocks; // this chunk's blocks (a lone fragment: from first_block on)
 };
 
 struct CtrWork {
@@ -233,6 +233,7 @@ struct FuseWork {
     FuseBuf single;      // nbufs == 1
     uint32_t nbufs;
     uint32_t cipher;     // some buffer of the launch has `cipher` set
+    uint64_t unit_lo;    // the launch runs units unit_lo .. unit_lo + total_units - 1
     uint64_t total_units;
     int *err;            // device error word (block mode, packed: 5 = a value outside its width)
     const uint32_t *key_words; // device: the 4 big-endian AES key words (keyed packed launches)

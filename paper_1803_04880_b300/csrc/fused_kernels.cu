@@ -1235,7 +1235,8 @@ __global__ void __launch_bounds__(32 * cta_warps<FWD, PK, CIPH>(), 16 / cta_warp
     const uint32_t ks_ring = smem_addr(smem) + kStages + (uint32_t)kTableBytes + (uint32_t)warp * kKsBytes;
     const uint32_t *tel = te + lane;
     const uint64_t G = (uint64_t)gridDim.x * kWarps;
-    for (uint64_t u = (uint64_t)blockIdx.x * kWarps + warp; u < w.total_units; u += G) {
+    const uint64_t u_end = w.unit_lo + w.total_units;
+    for (uint64_t u = w.unit_lo + (uint64_t)blockIdx.x * kWarps + warp; u < u_end; u += G) {
         uint64_t local;
         const FuseBuf *bp = unit_buf(w, u, local);
         const FuseBuf b = *bp;

@@ -306,6 +306,39 @@ def test_host_buffer_forms(fr, key):
     assert np.array_equal(r.numpy(), data)
 
 
+# buffers of 16 MiB and more take the banded host form: copies in, kernels
+# and copies out of row bands overlap on three streams
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("n,W,L", [((16 << 20) + 12345, 4096, 3), ((20 << 20) - 7, 8192, 2),
+                                   ((17 << 20) + 1, 2048, 1), (24 << 20, 1024, 3),
+                                   ((18 << 20) + 999, 4000, 2)])
+def test_host_forms_in_bands(fr, key, n, W, L, pinned):
+    """The banded host forms give the device calls' fragments byte for byte
+    and recover every byte (and, on one case, the oracle's fragments)."""
+    data = wl.random_bytes(n, seed=n % 1000 + L)
+    plan = fr.Plan(W, L)
+    _, pb, ub = plan.sizes(n)
+    h = torch.from_numpy(data)
+    hp = torch.full((pb,), 0xAA, dtype=torch.uint8)
+    hu = torch.full((ub,), 0xAA, dtype=torch.uint8)
+    ho = torch.full((n,), 0x55, dtype=torch.uint8)
+    if pinned:
+        h, hp, hu, ho = h.pin_memory(), hp.pin_memory(), hu.pin_memory(), ho.pin_memory()
+    fr.protect_host(plan, key, 5, h, hp, hu)
+    d = h.cuda()
+    dp = torch.empty(pb, dtype=torch.uint8, device="cuda")
+    du = torch.empty(ub, dtype=torch.uint8, device="cuda")
+    fr.protect(plan, key, 5, d, n, dp, du)
+    fr.sync_status()
+    assert torch.equal(hp, dp.cpu()), "private fragment differs from the device call"
+    assert torch.equal(hu, du.cpu()), "public fragment differs from the device call"
+    fr.recover_host(plan, key, 5, hp, hu, n, ho)
+    assert torch.equal(ho, h), "recovered bytes differ"
+    if n == (16 << 20) + 12345 and pinned:
+        p_ref, u_ref = oracle.protect(data, W, L, KEY, 5)
+        assert np.array_equal(hp.numpy(), p_ref) and np.array_equal(hu.numpy(), u_ref)
+
+
 def _mixed_items(count, seed, hi=1 << 18):
     items = wl.c4_items(count=count, lo=64, hi=hi, seed=seed)
     datas = [wl.random_bytes(n, seed=i) for i, (n, _, _, _) in enumerate(items)]
