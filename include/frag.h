@@ -375,6 +375,66 @@ frag_status frag_protect_batch_noalloc(const frag_item *items, uint32_t count,
  * failed. */
 frag_status frag_noalloc_sync_status(frag_stream stream);
 
+/* Serving: protect / recover requests with continuous batching (the thesis
+ * has no counterpart; it is the deployment form of the batched calls).
+ *
+ * A server owns a scheduler thread and max_groups streams on the current
+ * device.  Submitting records the position of the caller's `ready` stream
+ * (work queued there before the call, that fills the input, comes first)
+ * and queues the request; it allocates nothing and returns at once with a
+ * request id.  The scheduler admits waiting requests in arrival order while
+ * their device memory -- outputs plus the library's level scratch, about
+ * (private + public) / 3 -- fits memory_budget (0: free memory at creation
+ * less 4 GiB; a request alone is always admitted, so none starves) and a
+ * stream is free; allocates their outputs from a memory pool of the
+ * server's own that keeps freed memory mapped for the next requests;
+ * and launches the group as one frag_protect_batch and one
+ * frag_recover_batch (at most max_items requests a group).  Requests that
+ * arrive while groups run are admitted as streams and memory free up, so
+ * their work overlaps on the device.  A host function after each group's
+ * launches marks its requests done.  Every result is byte-identical to a lone
+ * call's.  The caller keeps every input alive until its request is done.
+ *
+ * create: FRAG_EINVAL for a NULL argument, max_groups outside 1..16 or
+ * max_items 0.  stop: finishes every submitted request and ends the thread;
+ * wait, release and check still work, submit then fails.  destroy: stops,
+ * then frees the outputs not released and the server.  submit: FRAG_EINVAL for a NULL argument
+ * or a stopping server; errors of the plan as frag_plan_sizes gives them.
+ * wait: blocks until the request is done (timeout_s < 0: no limit; else
+ * FRAG_ETIMEOUT when it runs out), fills info (may be NULL) and returns the
+ * status of the request's launch.  release: gives the request's outputs
+ * back to the pool, ordered after the work on `after`; FRAG_EINVAL for an
+ * unknown or unfinished request.  hold: while held (nonzero, counted), the
+ * scheduler admits nothing; requests submitted meanwhile are admitted
+ * together afterwards.  check: waits for the server's streams and reports
+ * the device error word as frag_sync_status does. */
+typedef struct frag_server_s *frag_server;
+typedef struct {
+    uint32_t done;            /* 1: the request's work has completed on the device */
+    int32_t status;           /* FRAG_OK, or the error of its group's launch */
+    void *d_private;          /* protect: the fragments the server allocated */
+    void *d_public;
+    uint64_t private_bytes, public_bytes;
+    void *d_out;              /* recover: the recovered bytes the server allocated */
+    uint64_t nbytes;          /* the request's buffer size */
+    double t_submit, t_launch, t_done; /* seconds, the server's steady clock */
+} frag_request_info;
+frag_status frag_server_create(frag_server *out, frag_key key, uint64_t memory_budget, uint32_t max_groups,
+                               uint32_t max_items);
+frag_status frag_server_stop(frag_server server);
+frag_status frag_server_destroy(frag_server server);
+frag_status frag_server_submit_protect(frag_server server, frag_plan plan, uint64_t nonce, const void *d_in,
+                                       uint64_t nbytes, frag_stream ready, uint64_t *id);
+frag_status frag_server_submit_recover(frag_server server, frag_plan plan, uint64_t nonce,
+                                       const void *d_private, const void *d_public, uint64_t nbytes,
+                                       frag_stream ready, uint64_t *id);
+frag_status frag_server_wait(frag_server server, uint64_t id, double timeout_s, frag_request_info *info);
+frag_status frag_server_release(frag_server server, uint64_t id, frag_stream after);
+frag_status frag_server_hold(frag_server server, int hold);
+frag_status frag_server_stats(frag_server server, uint64_t *launches, uint64_t *used_bytes, uint32_t *pending,
+                              uint32_t *in_flight);
+frag_status frag_server_check(frag_server server);
+
 /* Thread-local text of the last error (always NUL-terminated).  Returns
  * FRAG_OK, or FRAG_EINVAL if buf is NULL or len is 0. */
 frag_status frag_get_error(char *buf, size_t len);

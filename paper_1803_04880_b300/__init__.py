@@ -34,6 +34,9 @@ EXPORTS = [
     "frag_batch_set_timing", "frag_batch_launch_times",
     "frag_get_error", "frag_check_wait_timeout",
     "frag_sync_status", "frag_protect_batch_noalloc", "frag_noalloc_sync_status",
+    "frag_server_create", "frag_server_stop", "frag_server_destroy", "frag_server_submit_protect",
+    "frag_server_submit_recover", "frag_server_wait", "frag_server_release", "frag_server_hold",
+    "frag_server_stats", "frag_server_check",
 ]
 
 
@@ -47,6 +50,13 @@ class frag_item(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("nonce", ctypes.c_uint64),
                 ("nbytes", ctypes.c_uint64), ("d_in", ctypes.c_void_p),
                 ("d_private", ctypes.c_void_p), ("d_public", ctypes.c_void_p)]
+
+
+class frag_request_info(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_uint32), ("status", ctypes.c_int32), ("d_private", ctypes.c_void_p),
+                ("d_public", ctypes.c_void_p), ("private_bytes", ctypes.c_uint64),
+                ("public_bytes", ctypes.c_uint64), ("d_out", ctypes.c_void_p), ("nbytes", ctypes.c_uint64),
+                ("t_submit", ctypes.c_double), ("t_launch", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 class frag_ritem(ctypes.Structure):
@@ -118,6 +128,17 @@ def lib():
         "frag_protect_batch_noalloc": ([ctypes.POINTER(frag_item), u32, ctypes.c_char_p, vp],
                                        ctypes.c_int),
         "frag_noalloc_sync_status": ([vp], ctypes.c_int),
+        "frag_server_create": ([ctypes.POINTER(vp), vp, u64, u32, u32], ctypes.c_int),
+        "frag_server_stop": ([vp], ctypes.c_int),
+        "frag_server_destroy": ([vp], ctypes.c_int),
+        "frag_server_submit_protect": ([vp, vp, u64, vp, u64, vp, ctypes.POINTER(u64)], ctypes.c_int),
+        "frag_server_submit_recover": ([vp, vp, u64, vp, vp, u64, vp, ctypes.POINTER(u64)], ctypes.c_int),
+        "frag_server_wait": ([vp, u64, ctypes.c_double, ctypes.POINTER(frag_request_info)], ctypes.c_int),
+        "frag_server_release": ([vp, u64, vp], ctypes.c_int),
+        "frag_server_hold": ([vp, ctypes.c_int], ctypes.c_int),
+        "frag_server_stats": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u32),
+                               ctypes.POINTER(u32)], ctypes.c_int),
+        "frag_server_check": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfrag.so")
-SOURCES = ["frag_api.cu", "tile_kernels.cu", "stream_kernels.cu", "cipher_kernels.cu", "fused_kernels.cu", "block_kernels.cu", "noalloc.cu"]
+SOURCES = ["frag_api.cu", "tile_kernels.cu", "stream_kernels.cu", "cipher_kernels.cu", "fused_kernels.cu", "block_kernels.cu", "noalloc.cu", "server.cu"]
 HEADERS = [os.path.join(ROOT, "include", "frag.h"), os.path.join(CSRC, "frag_internal.cuh")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

@@ -8,8 +8,9 @@
 // shared memory placed on a 64 KB boundary of the shared window, so every
 // lookup is one byte permute and one shared load, and a round column one
 // rotation.  One block of 1024 threads an SM; work goes by warps: a warp
-// takes a chunk of a fragment (a chunk of the chunk list, or a slice of a
-// lone fragment) and its lanes take every 32nd block of it.  The round-1
+// takes a turn of a fragment (a fragment of the launch's list, found by
+// binary search over the turns, or a slice of a lone fragment) and its lanes
+// take every 32nd block of it.  The round-1
 // constants of the chunk's nonce are computed once per chunk (only the
 // low block word varies within it).  The counter block is nonce (8 bytes
 // big-endian) || block index (8 bytes big-endian); out = in XOR keystream,
@@ -34,18 +35,28 @@ __global__ void __launch_bounds__(kCtrThreads, 1) ctr_kernel(CtrWork w)
     __syncthreads();
     const aes::Lut L = aes::make_lut(tab, lane);
     grid_wait(); // the fragment is complete from here on
-    const uint64_t nchunks = w.chunks ? w.nchunks
-                                      : (w.single.nblocks + w.single_chunk - 1) / w.single_chunk;
+    const uint64_t nturns = w.frags ? w.nturns : (w.single.nblocks + w.turn_blocks - 1) / w.turn_blocks;
     const uint64_t warps = (uint64_t)gridDim.x * (kCtrThreads / 32);
-    for (uint64_t c = (uint64_t)blockIdx.x * (kCtrThreads / 32) + (threadIdx.x >> 5); c < nchunks; c += warps) {
+    for (uint64_t c = (uint64_t)blockIdx.x * (kCtrThreads / 32) + (threadIdx.x >> 5); c < nturns; c += warps) {
         CtrChunk ch;
-        if (w.chunks) {
-            ch = w.chunks[c];
+        uint64_t first;
+        if (w.frags) { // the fragment whose turns hold c
+            uint64_t lo = 0, hi = w.nfrags;
+            while (hi - lo > 1) {
+                const uint64_t mid = (lo + hi) >> 1;
+                if (__ldg(w.turn_start + mid) <= c)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            ch = w.frags[lo];
+            first = (c - __ldg(w.turn_start + lo)) * w.turn_blocks;
         } else {
             ch = w.single;
-            ch.first_block = w.single.first_block + c * w.single_chunk;
-            ch.nblocks = min(w.single_chunk, w.single.nblocks - c * w.single_chunk);
+            first = c * w.turn_blocks;
         }
+        ch.nblocks = min(w.turn_blocks, ch.nblocks - first);
+        ch.first_block += first;
         const bool vec = (((uintptr_t)ch.in | (uintptr_t)ch.out) & 15u) == 0;
         aes::Round1 R = aes::round1_consts(L, w.keys, ch.nonce, (uint32_t)(ch.first_block >> 32));
         for (uint64_t i = lane; i < ch.nblocks; i += 32) {

@@ -597,8 +597,17 @@ frag::CtrChunk ctr_fragment(bool fwd, const Buf &b)
     return c;
 }
 
-frag_status ctr_launch(DeviceState &d, const frag::AesKeys &keys, const frag::CtrChunk *chunks,
-                       uint64_t nchunks, const frag::CtrChunk *single, cudaStream_t s)
+// A CTR launch over a fragment list (frags, device; turn_start, device,
+// nfrags + 1 entries; nturns warp turns of turn_blocks blocks) or over one
+// fragment (single: blocks first_block .. + nblocks, turns sized here).
+struct CtrList {
+    const frag::CtrChunk *frags = nullptr;
+    const uint64_t *turn_start = nullptr;
+    uint64_t nfrags = 0, nturns = 0, turn_blocks = 0;
+};
+
+frag_status ctr_launch(DeviceState &d, const frag::AesKeys &keys, const CtrList *list,
+                       const frag::CtrChunk *single, cudaStream_t s)
 {
     int occ = 0;
     {
@@ -617,20 +626,25 @@ frag_status ctr_launch(DeviceState &d, const frag::AesKeys &keys, const frag::Ct
     }
     frag::CtrWork w;
     std::memset(&w, 0, sizeof(w));
-    w.chunks = chunks;
-    w.nchunks = nchunks;
-    if (single)
-        w.single = *single;
     w.aes_tables = d.tables;
     w.keys = keys;
     const uint64_t slots = (uint64_t)d.sms * occ;
-    if (!chunks) {
+    uint64_t work = 0;
+    if (list) {
+        w.frags = list->frags;
+        w.turn_start = list->turn_start;
+        w.nfrags = list->nfrags;
+        w.nturns = list->nturns;
+        w.turn_blocks = list->turn_blocks;
+        work = list->nturns;
+    } else {
         // a lone fragment spread over every resident warp, whole warp turns
+        w.single = *single;
         const uint64_t warps = slots * (frag::kCtrThreads / 32);
         const uint64_t per = (single->nblocks + warps - 1) / warps;
-        w.single_chunk = std::max<uint64_t>(32, (per + 31) / 32 * 32);
+        w.turn_blocks = std::max<uint64_t>(frag::kCtrTurn, (per + 31) / 32 * 32);
+        work = (single->nblocks + w.turn_blocks - 1) / w.turn_blocks;
     }
-    const uint64_t work = chunks ? nchunks : (single->nblocks + w.single_chunk - 1) / w.single_chunk;
     if (work == 0)
         return FRAG_OK;
     const uint32_t grid = (uint32_t)std::min<uint64_t>(slots, (work + frag::kCtrThreads / 32 - 1) /
@@ -944,9 +958,9 @@ frag_status run_packed(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     if (fwd) {
         st = block_launch(*d, true, w, s, true, b.keyed != 0, rk);
         if (st == FRAG_OK)
-            st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &c, s);
+            st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, &c, s);
     } else {
-        st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &c, s);
+        st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, &c, s);
         if (st == FRAG_OK)
             st = block_launch(*d, false, w, s, true, b.keyed != 0, rk);
         cudaFreeAsync(plainA, s);
@@ -989,11 +1003,11 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
         w.total_units = block_units(&w.single, 1);
         const frag::CtrChunk frag_chunk = ctr_fragment(fwd, b);
         if (!fwd)
-            st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &frag_chunk, s);
+            st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, &frag_chunk, s);
         if (st == FRAG_OK)
             st = block_launch(*d, fwd, w, s);
         if (st == FRAG_OK && fwd)
-            st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &frag_chunk, s);
+            st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, &frag_chunk, s);
         if (mem)
             cudaFreeAsync(mem, s);
         return st;
@@ -1049,7 +1063,7 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
     if (st == FRAG_OK && fwd && b.F2)
         st = fuse_launch(*d, true, true, fw[1], fslots[1], s);
     if (st == FRAG_OK && sep && !fwd)
-        st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &frag_chunk, s);
+        st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, &frag_chunk, s);
     if (st == FRAG_OK && njobs) {
         std::vector<LevelJob> jobs;
         uint32_t counters = 0;
@@ -1081,7 +1095,7 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
         }
     }
     if (st == FRAG_OK && sep && fwd)
-        st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &frag_chunk, s);
+        st = ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, &frag_chunk, s);
     if (st == FRAG_OK && !fwd && b.F2)
         st = fuse_launch(*d, false, true, fw[1], fslots[1], s);
     if (st == FRAG_OK && !fwd && b.F1)
@@ -1275,7 +1289,7 @@ frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t non
         fw.unit_lo = sy0 * strips;
         fw.total_units = (sy1 - sy0) * strips;
         if (!fwd && c.nblocks)
-            st = ctr_launch(*d, keys, nullptr, 0, &c, s);
+            st = ctr_launch(*d, keys, nullptr, &c, s);
         if (st == FRAG_OK)
             st = fuse_launch(*d, fwd, false, fw, slots, s);
         if (st == FRAG_OK && fwd) {
@@ -1287,7 +1301,7 @@ frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t non
                 c.out = d_priv;
                 c.first_block = blk0;
                 c.nblocks = bhi - blk0;
-                st = ctr_launch(*d, keys, nullptr, 0, &c, s);
+                st = ctr_launch(*d, keys, nullptr, &c, s);
             }
         }
         if (st != FRAG_OK)
@@ -1348,6 +1362,8 @@ struct DagWave {
     std::vector<uint32_t> first, levels; // per buffer: first job, number of jobs
     std::vector<DagUnit> units;
     std::vector<frag::CtrChunk> chunks; // private fragments of the separate CTR launch
+    std::vector<uint64_t> turn_start;   // their first warp turns (one more entry)
+    uint64_t turn_blocks = 0;
     std::vector<frag::FuseBuf> fbufs;   // buffers of the fused launch (levels 1..3)
     uint64_t fuse_units = 0;
     std::vector<frag::FuseBuf> fbufs2;  // buffers of the second fused pass (levels 4 to 6)
@@ -1357,7 +1373,7 @@ struct DagWave {
     std::vector<frag::FuseBuf> pbufs;   // buffers of the packed block launch
     uint64_t packed_units = 0;
     uint32_t counters = 0;
-    size_t jobs_off = 0, units_off = 0, done_off = 0, queue_off = 0, chunks_off = 0, fbufs_off = 0,
+    size_t jobs_off = 0, units_off = 0, done_off = 0, queue_off = 0, chunks_off = 0, turns_off = 0, fbufs_off = 0,
            bbufs_off = 0, fbufs2_off = 0, pbufs_off = 0;
 };
 
@@ -1455,25 +1471,28 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
     uint64_t u64 = 0;
     for (const Buf &b : bp.bufs)
         u64 += l1_units_at_64(b);
-    // CTR chunks (a warp's turn): kCtrChunkList blocks, one a lane, doubled
-    // (up to 128x) while the batch keeps more than 4 chunks per resident
-    // warp of the CTR launch, so a batch of large private fragments builds
-    // and uploads fewer descriptors with the same parallelism and a batch of
-    // small ones still spreads over every SM
+    // CTR warp turns: kCtrTurn blocks (one a lane a step), doubled up to
+    // 128x while the batch keeps more than 4 turns a resident warp of the CTR
+    // launch, so a batch of small fragments still spreads over every SM;
+    // the launch reads one descriptor per fragment and finds a turn's
+    // fragment by binary search, so the host's work grows with the buffers,
+    // not with the blocks
     uint64_t ctr_blocks = 0;
     for (const Buf &b : bp.bufs)
         if (ctr_pass(b))
             ctr_blocks += ctr_fragment(bp.fwd, b).nblocks;
-    uint64_t chunk = frag::kCtrChunkList;
+    uint64_t turn = frag::kCtrTurn;
     const uint64_t per_warp = 4 * std::max<uint64_t>(1, bp.sms) * (frag::kCtrThreads / 32);
-    while (chunk < 128 * frag::kCtrChunkList && ctr_blocks / (2 * chunk) >= per_warp)
-        chunk *= 2;
+    while (turn < 128 * frag::kCtrTurn && ctr_blocks / (2 * turn) >= per_warp)
+        turn *= 2;
     for (auto &wv : bp.waves) {
         wv.jobs.clear();
         wv.first.clear();
         wv.levels.clear();
         wv.units.clear();
         wv.chunks.clear();
+        wv.turn_start.assign(1, 0);
+        wv.turn_blocks = turn;
         wv.fbufs.clear();
         wv.fuse_units = 0;
         wv.bbufs.clear();
@@ -1504,15 +1523,10 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
             wv.fbufs.push_back(fuse_buf(bp.fwd, b, 1));
         if (b.F2)
             wv.fbufs2.push_back(fuse_buf(bp.fwd, b, 2));
-        if (ctr_pass(b)) {
-            // the private fragment in chunks of `chunk` blocks
+        if (ctr_pass(b)) { // the private fragment, whole, and its turns
             const frag::CtrChunk whole = ctr_fragment(bp.fwd, b);
-            for (uint64_t f = 0; f < whole.nblocks; f += chunk) {
-                frag::CtrChunk c = whole;
-                c.first_block = f;
-                c.nblocks = std::min<uint64_t>(chunk, whole.nblocks - f);
-                wv.chunks.push_back(c);
-            }
+            wv.chunks.push_back(whole);
+            wv.turn_start.push_back(wv.turn_start.back() + (whole.nblocks + turn - 1) / turn);
         }
     }
     for (auto &wv : bp.waves) {
@@ -1538,6 +1552,8 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
         off += 256;
         wv.chunks_off = off;
         off += align256(wv.chunks.size() * sizeof(frag::CtrChunk));
+        wv.turns_off = off;
+        off += align256(wv.turn_start.size() * sizeof(uint64_t));
         wv.fbufs_off = off;
         off += align256(wv.fbufs.size() * sizeof(frag::FuseBuf));
         wv.bbufs_off = off;
@@ -1559,9 +1575,12 @@ frag_status upload_batch(const BatchPlan &bp, uint8_t *mem, cudaStream_t s, bool
     for (const auto &wv : bp.waves) {
         std::memcpy(host.data() + (wv.jobs_off - base), wv.jobs.data(), wv.jobs.size() * sizeof(LevelJob));
         std::memcpy(host.data() + (wv.units_off - base), wv.units.data(), wv.units.size() * sizeof(DagUnit));
-        if (!wv.chunks.empty())
+        if (!wv.chunks.empty()) {
             std::memcpy(host.data() + (wv.chunks_off - base), wv.chunks.data(),
                         wv.chunks.size() * sizeof(frag::CtrChunk));
+            std::memcpy(host.data() + (wv.turns_off - base), wv.turn_start.data(),
+                        wv.turn_start.size() * sizeof(uint64_t));
+        }
         if (!wv.fbufs.empty())
             std::memcpy(host.data() + (wv.fbufs_off - base), wv.fbufs.data(),
                         wv.fbufs.size() * sizeof(frag::FuseBuf));
@@ -1671,7 +1690,12 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
 {
     LaunchTimer tm{timed, s};
     for (const auto &wv : bp.waves) {
-        const frag::CtrChunk *chunks = (const frag::CtrChunk *)(mem + wv.chunks_off);
+        CtrList clist;
+        clist.frags = (const frag::CtrChunk *)(mem + wv.chunks_off);
+        clist.turn_start = (const uint64_t *)(mem + wv.turns_off);
+        clist.nfrags = wv.chunks.size();
+        clist.nturns = wv.turn_start.empty() ? 0 : wv.turn_start.back();
+        clist.turn_blocks = wv.turn_blocks;
         frag_status st = FRAG_OK;
         if (bp.fwd && (st = launch_wave_fused(bp, wv, mem, d, s, tm, keys)) != FRAG_OK)
             return st;
@@ -1683,7 +1707,7 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
             return st;
         if (!bp.fwd && !wv.chunks.empty()) { // decipher before the transform reads LL_L
             tm.begin();
-            st = ctr_launch(d, keys, chunks, wv.chunks.size(), nullptr, s);
+            st = ctr_launch(d, keys, &clist, nullptr, s);
             tm.end(FRAG_KERNEL_CIPHER);
             if (st != FRAG_OK)
                 return st;
@@ -1717,7 +1741,7 @@ frag_status launch_batch(const BatchPlan &bp, uint8_t *mem, DeviceState &d, cons
         }
         if (bp.fwd && !wv.chunks.empty()) { // encipher after the transform wrote LL_L
             tm.begin();
-            st = ctr_launch(d, keys, chunks, wv.chunks.size(), nullptr, s);
+            st = ctr_launch(d, keys, &clist, nullptr, s);
             tm.end(FRAG_KERNEL_CIPHER);
             if (st != FRAG_OK)
                 return st;
@@ -2211,7 +2235,7 @@ frag_status frag_aes128_ctr(frag_key key, uint64_t nonce, const void *d_in, void
     c.nonce = nonce;
     c.bytes = nbytes;
     c.nblocks = (nbytes + 15) / 16;
-    return ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, 0, &c, (cudaStream_t)stream);
+    return ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, &c, (cudaStream_t)stream);
 }
 
 frag_status frag_recover(frag_plan plan, frag_key key, uint64_t nonce, const void *d_private,

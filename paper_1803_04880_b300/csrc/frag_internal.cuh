@@ -171,18 +171,24 @@ struct CtrChunk {
     uint64_t nblocks; // this chunk's blocks (a lone fragment: from first_block on)
 };
 
+// A launch over one fragment (`single`, blocks first_block .. + nblocks) or
+// a list of fragments (one descriptor each, all of its blocks).  Work goes
+// by warp turns of `turn_blocks` blocks (a multiple of 32, one block a lane
+// a step); a list's turns are numbered fragment by fragment, turn_start[f]
+// the first of fragment f (nfrags + 1 entries), so no turn spans two.
 struct CtrWork {
-    const CtrChunk *chunks; // device array (nullptr: one fragment, `single`)
-    uint64_t nchunks;
+    const CtrChunk *frags;      // device array (nullptr: one fragment, `single`)
+    const uint64_t *turn_start; // device array, with frags
+    uint64_t nfrags, nturns;
     CtrChunk single;
-    uint64_t single_chunk;      // blocks per warp turn over `single` (a multiple of 32)
+    uint64_t turn_blocks;
     const uint32_t *aes_tables; // table 0 is the first 256 words
     AesKeys keys;
 };
 
 cudaError_t launch_ctr(const CtrWork &w, uint32_t grid, cudaStream_t stream);
 cudaError_t ctr_occupancy(int *blocks_per_sm);
-constexpr uint32_t kCtrChunkList = 32;  // blocks per chunk of a chunk list at least (a warp turn)
+constexpr uint32_t kCtrTurn = 32;       // blocks of a warp turn at least (one a lane)
 constexpr int kCtrThreads = 1024;       // one CTA an SM (the two-table AES in shared memory)
 
 // Programmatic dependent launch: a kernel launched with

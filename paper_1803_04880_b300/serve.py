@@ -1,73 +1,133 @@
 """Serving loop for protect / recover requests on one GPU, with continuous
-batching.
+batching: a Python face on the library's server (``frag_server_*`` in
+include/frag.h), whose scheduler runs as a C++ thread inside the library.
 
 Requests arrive at any time (``submit_protect`` / ``submit_recover``, from any
-thread).  A scheduler thread admits waiting requests in arrival order while
-the device memory they need (their outputs plus the library's level scratch)
-fits the budget, launches every admitted group as one batched call per kind
-(``frag_protect_batch`` / ``frag_recover_batch``: one dependency-ordered
-launch for all of the group's buffers) on one of its streams, and retires
-groups whose completion event has fired.  Requests that arrive while earlier
-groups are still on the GPU are admitted as soon as a stream and memory are
-free, so their work overlaps on the device (up to ``max_groups`` groups in
-flight).  Plans, per (width, levels), and the key schedule stay resident.
+thread); a submit records the caller's current stream (the work that fills
+the input comes first) and queues the request -- one ctypes call.  The
+library's scheduler admits waiting requests in arrival order while the device
+memory they need (their outputs plus the level scratch) fits the budget and a
+group stream is free, allocates their outputs, launches every admitted group
+as one batched call per kind, and learns of a group's end from a host
+function the group's stream runs -- no polling.  Requests that arrive while
+earlier groups are on the GPU are admitted as soon as a stream and memory are
+free, so their work overlaps on the device.  Plans, per (width, levels), and
+the key schedule stay resident.
 
 Every result is the same as that of a lone call: the transform is exact
 integer arithmetic and each buffer's work is independent of the others in a
-launch.  The latency of a request runs from ``submit_*`` to the scheduler
-seeing its group's completion event.
+launch.  The latency of a request runs from its submit to the end of its
+group on the device (the library's steady clock).
 """
 from __future__ import annotations
 
-import collections
 import contextlib
-import threading
-import time
-from typing import List, Optional
+import ctypes
+from typing import Optional
 
 import torch
 
-from . import Key, Plan, protect_batch, recover_batch, sync_status
+from . import FRAG_ETIMEOUT, FRAG_OK, FragError, Key, Plan, _stream, check, frag_request_info, last_error, lib
+
+
+class _DevBytes:
+    """A device byte range as __cuda_array_interface__ (no ownership)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "|u1", "data": (ptr, False),
+                                         "version": 2}
+
+
+class _Handle:
+    """Owns the library's server; destroyed when the Server and every request
+    that still holds outputs are gone."""
+
+    def __init__(self, key: Key, budget: int, max_groups: int, max_items: int):
+        self.key = key  # the key must outlive the server
+        self.ptr = ctypes.c_void_p()
+        check(lib().frag_server_create(ctypes.byref(self.ptr), key.handle, budget, max_groups, max_items))
+
+    def __del__(self):
+        if self.ptr:
+            lib().frag_server_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
 
 
 class Request:
-    """One protect or recover request and, once ``done``, its outputs."""
+    """One protect or recover request.  Once done: ``private`` / ``public``
+    (protect) or ``out`` (recover) are uint8 CUDA tensors over the memory the
+    server allocated, valid until ``release()`` (or until the request and
+    every such tensor are garbage)."""
 
-    __slots__ = ("kind", "nonce", "nbytes", "plan", "data", "private", "public", "out",
-                 "need", "t_submit", "t_launch", "t_done", "error", "_event", "_ready")
-
-    def __init__(self, kind: str, plan: Plan, nonce: int, nbytes: int):
+    def __init__(self, handle: _Handle, kind: str, plan: Plan, nonce: int, nbytes: int):
+        self._h = handle
         self.kind = kind
         self.plan = plan
         self.nonce = nonce
         self.nbytes = nbytes
-        self.data = self.private = self.public = self.out = None
-        self.need = 0
-        self.t_submit = time.perf_counter()
-        self.t_launch = self.t_done = None
+        self.id = None
+        self.data = None           # protect: the input (kept alive)
+        self.private = self.public = None
+        self.out = None
         self.error: Optional[BaseException] = None
-        self._event = threading.Event()
-        # the caller's stream position at submit: the inputs are ready there
-        self._ready = torch.cuda.Event()
-        self._ready.record()
+        self.t_submit = self.t_launch = self.t_done = None
+        self._done = False
+        self._released = False
+
+    def _take(self, info: frag_request_info, status: int) -> None:
+        self._done = True
+        self.t_submit, self.t_launch, self.t_done = info.t_submit, info.t_launch, info.t_done
+        if status != FRAG_OK:
+            self.error = FragError(status, last_error())
+            return
+        if self.kind == "protect":
+            self.private = self._view(info.d_private, info.private_bytes)
+            self.public = self._view(info.d_public, info.public_bytes)
+        else:
+            self.out = self._view(info.d_out, info.nbytes)
+
+    def _view(self, ptr: Optional[int], n: int) -> torch.Tensor:
+        t = torch.as_tensor(_DevBytes(ptr or 0, n), device="cuda") if n else \
+            torch.empty(0, dtype=torch.uint8, device="cuda")
+        t._frag_request = self  # the tensor keeps the request (and so its memory) alive
+        return t
+
+    def wait(self, timeout: Optional[float] = None) -> bool:
+        """True once the request is done (its outputs are ready on the GPU);
+        False if timeout seconds pass first."""
+        if self._done:
+            return True
+        info = frag_request_info()
+        st = lib().frag_server_wait(self._h.ptr, self.id, -1.0 if timeout is None else float(timeout),
+                                    ctypes.byref(info))
+        if st == FRAG_ETIMEOUT and not info.done:
+            return False
+        self._take(info, st)
+        return True
 
     @property
     def done(self) -> bool:
-        return self._event.is_set()
-
-    def wait(self, timeout: Optional[float] = None) -> bool:
-        return self._event.wait(timeout)
+        return self.wait(0.0)
 
     @property
     def latency_s(self) -> Optional[float]:
         return None if self.t_done is None else self.t_done - self.t_submit
 
+    def release(self) -> None:
+        """Give the request's outputs back to the library's pool (after the
+        work queued on the current stream)."""
+        if self._released or self.id is None or not self._done:
+            return
+        self._released = True
+        self.private = self.public = self.out = None
+        if self._h.ptr:
+            lib().frag_server_release(self._h.ptr, self.id, _stream(None))
 
-class _Group:
-    __slots__ = ("requests", "stream", "event", "need")
-
-    def __init__(self, requests, stream, event, need):
-        self.requests, self.stream, self.event, self.need = requests, stream, event, need
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
 
 
 class Server:
@@ -87,22 +147,12 @@ class Server:
         self.key = Key(key)
         self._plans = {}
         self.default_plan = self.plan(width, levels)
-        free, _ = torch.cuda.mem_get_info(self.device)
-        self.budget = memory_budget if memory_budget is not None else max(0, free - reserve)
-        self.max_groups = max_groups
-        self.max_items = max_items
-        self._streams = [torch.cuda.Stream(device=self.device) for _ in range(max_groups)]
-        self._pending = collections.deque()
-        self._inflight: List[_Group] = []
-        self._used = 0
-        self._cv = threading.Condition()
-        self._stop = False
-        self._hold = 0
-        self.launches = 0
-        self._thread = threading.Thread(target=self._loop, name="frag-serve", daemon=True)
-        self._thread.start()
-
-    # -- client side --------------------------------------------------------------
+        if memory_budget is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            memory_budget = max(1, free - reserve)
+        self.budget = memory_budget
+        self._h = _Handle(self.key, memory_budget, max_groups, max_items)
+        self._closed = False
 
     def plan(self, width: int, levels: int) -> Plan:
         key = (width, levels)
@@ -110,157 +160,61 @@ class Server:
             self._plans[key] = Plan(width, levels)
         return self._plans[key]
 
-    def _need(self, plan: Plan, kind: str, n: int) -> int:
-        _, pb, ub = plan.sizes(n)
-        # outputs, plus the level scratch the library allocates (at most about
-        # two thirds of the padded matrix, as packed pairs) and descriptors
-        scratch = (pb + ub) // 3 + (1 << 16)
-        return (pb + ub if kind == "protect" else n) + scratch
-
     def submit_protect(self, data: torch.Tensor, nonce: int, plan: Optional[Plan] = None) -> Request:
         """Protect the bytes of a uint8 CUDA tensor (kept alive until done).
         Work the caller queued on its current stream before the call (that
         fills `data`) comes first."""
         plan = plan or self.default_plan
-        r = Request("protect", plan, nonce, data.numel())
+        r = Request(self._h, "protect", plan, nonce, data.numel())
         r.data = data
-        r.need = self._need(plan, "protect", r.nbytes)
-        self._enqueue(r)
+        rid = ctypes.c_uint64()
+        check(lib().frag_server_submit_protect(self._h.ptr, plan.handle, nonce, data.data_ptr(), data.numel(),
+                                               _stream(None), ctypes.byref(rid)))
+        r.id = rid.value
         return r
 
     def submit_recover(self, private: torch.Tensor, public: torch.Tensor, nbytes: int, nonce: int,
                        plan: Optional[Plan] = None) -> Request:
         plan = plan or self.default_plan
-        r = Request("recover", plan, nonce, nbytes)
-        r.private, r.public = private, public
-        r.need = self._need(plan, "recover", nbytes)
-        self._enqueue(r)
+        r = Request(self._h, "recover", plan, nonce, nbytes)
+        r.private, r.public = private, public  # inputs, kept alive until done
+        rid = ctypes.c_uint64()
+        check(lib().frag_server_submit_recover(self._h.ptr, plan.handle, nonce, private.data_ptr(),
+                                               public.data_ptr(), nbytes, _stream(None), ctypes.byref(rid)))
+        r.id = rid.value
         return r
-
-    def _enqueue(self, r: Request) -> None:
-        with self._cv:
-            if self._stop:
-                raise RuntimeError("server is closed")
-            self._pending.append(r)
-            if not self._hold:  # a held scheduler has nothing to do yet
-                self._cv.notify()
 
     @contextlib.contextmanager
     def held(self):
         """Admit nothing while the block runs: the requests submitted inside
         it wait and are admitted together when it ends (in arrival order,
-        within the memory budget), so their grouping does not depend on how
-        the scheduler thread interleaves with the submitting one."""
-        with self._cv:
-            self._hold += 1
+        within the memory budget)."""
+        check(lib().frag_server_hold(self._h.ptr, 1))
         try:
             yield self
         finally:
-            with self._cv:
-                self._hold -= 1
-                self._cv.notify()
+            check(lib().frag_server_hold(self._h.ptr, 0))
+
+    @property
+    def launches(self) -> int:
+        n = ctypes.c_uint64()
+        check(lib().frag_server_stats(self._h.ptr, ctypes.byref(n), None, None, None))
+        return n.value
+
+    def check(self) -> None:
+        """Raise if a kernel of the server's launches reported an error (the
+        device error word is read once every group in flight has finished)."""
+        check(lib().frag_server_check(self._h.ptr))
 
     def close(self) -> None:
-        """Finish every submitted request, then stop the scheduler."""
-        with self._cv:
-            self._stop = True
-            self._cv.notify()
-        self._thread.join()
+        """Finish every submitted request, then stop the scheduler (results
+        stay valid until released)."""
+        if not self._closed:
+            self._closed = True
+            check(lib().frag_server_stop(self._h.ptr))
 
     def __enter__(self):
         return self
 
     def __exit__(self, *exc):
         self.close()
-
-    # -- scheduler -----------------------------------------------------------------
-
-    def _admit(self) -> List[Request]:
-        """Requests to launch now, in arrival order, within the memory budget."""
-        take = []
-        used = self._used
-        while self._pending and len(take) < self.max_items:
-            r = self._pending[0]
-            if used + r.need > self.budget and (take or self._inflight):
-                break  # wait for memory (a request alone always goes, so nothing starves)
-            take.append(self._pending.popleft())
-            used += r.need
-        return take
-
-    def _launch(self, reqs: List[Request]) -> None:
-        stream = self._streams[len(self._inflight) % self.max_groups]
-        busy = {id(g.stream) for g in self._inflight}
-        for s in self._streams:
-            if id(s) not in busy:
-                stream = s
-                break
-        need = sum(r.need for r in reqs)
-        now = time.perf_counter()
-        try:
-            with torch.cuda.stream(stream):
-                pitems, ritems = [], []
-                for r in reqs:
-                    stream.wait_event(r._ready)
-                    r.t_launch = now
-                    if r.kind == "protect":
-                        _, pb, ub = r.plan.sizes(r.nbytes)
-                        r.private = torch.empty(pb, dtype=torch.uint8, device=self.device)
-                        r.public = torch.empty(ub, dtype=torch.uint8, device=self.device)
-                        pitems.append((r.plan, r.nonce, r.nbytes, r.data, r.private, r.public))
-                    else:
-                        r.out = torch.empty(r.nbytes, dtype=torch.uint8, device=self.device)
-                        ritems.append((r.plan, r.nonce, r.nbytes, r.private, r.public, r.out))
-                if pitems:
-                    protect_batch(pitems, self.key, stream)
-                    self.launches += 1
-                if ritems:
-                    recover_batch(ritems, self.key, stream)
-                    self.launches += 1
-                ev = torch.cuda.Event()
-                ev.record(stream)
-        except BaseException as e:  # report on every request of the group
-            for r in reqs:
-                r.error = e
-                r.t_done = time.perf_counter()
-                r._event.set()
-            return
-        self._inflight.append(_Group(reqs, stream, ev, need))
-        self._used += need
-
-    def _retire(self) -> bool:
-        progressed = False
-        for g in list(self._inflight):
-            if g.event.query():
-                now = time.perf_counter()
-                for r in g.requests:
-                    r.t_done = now
-                    r._event.set()
-                self._inflight.remove(g)
-                self._used -= g.need
-                progressed = True
-        return progressed
-
-    def check(self) -> None:
-        """Raise if a kernel of the server's launches reported an error (the
-        device error word is read once every group in flight has finished)."""
-        for s in self._streams:
-            s.synchronize()
-        sync_status(self._streams[0])
-
-    def _loop(self) -> None:
-        torch.cuda.set_device(self.device)
-        while True:
-            with self._cv:
-                if self._stop and not self._pending and not self._inflight:
-                    return
-                free_slot = len(self._inflight) < self.max_groups
-                reqs = self._admit() if free_slot and not self._hold else []
-            if reqs:
-                self._launch(reqs)
-                continue
-            if self._retire():
-                continue
-            with self._cv:
-                # nothing to launch now: poll the groups' events, or sleep
-                # until a submit when the GPU holds nothing
-                self._cv.wait(timeout=20e-6 if self._inflight else 0.01)
