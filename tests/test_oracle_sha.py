@@ -67,6 +67,14 @@ def _case(width=72, rows=40, seed=3):
 
 
 def test_keyed_framing_restated_with_hashlib():
+    """Sec. 5.2.1 fixes which fragment feeds which hash: the first public
+    fragment is protected with SHA-256 of the private fragment and the key,
+    the second with SHA-512 of the first *protected* public fragment and the
+    key.  Those choices are pinned here (and the two slips that would keep
+    every round trip working -- hashing B instead of B', or reading the
+    digest's bits in the other order -- are shown to fail); the byte layout
+    of the hash inputs (key, nonce, block index, record) is this
+    implementation's reading and stays unpinned by the thesis."""
     x, W = _case()
     a, pub = oracle.protect_keyed(x, W, KEY, NONCE)
     a0, pub0 = oracle.protect_packed(x, W, KEY, NONCE)
@@ -83,6 +91,13 @@ def test_keyed_framing_restated_with_hashlib():
         h2 = int.from_bytes(hashlib.sha512(prefix + b_prot.to_bytes(16, "little")).digest(),
                             "little") & ((1 << 480) - 1)
         assert keyed[idx][2] == c ^ h2
+        # SHA-512 over the plain B (not B') would give other bits
+        h2_plain = int.from_bytes(hashlib.sha512(prefix + b.to_bytes(16, "little")).digest(),
+                                  "little") & ((1 << 480) - 1)
+        assert keyed[idx][2] != c ^ h2_plain
+        # the digest read big-endian (its bits in the other order) would too
+        h1_rev = int.from_bytes(hashlib.sha256(prefix + a_rec).digest(), "big") & ((1 << 124) - 1)
+        assert keyed[idx][1] != b ^ h1_rev
 
 
 @pytest.mark.parametrize("width,n", [(8, 64), (16, 8 * 16 * 3 - 1), (72, 72 * 24), (256, 256 * 16 + 77)])
