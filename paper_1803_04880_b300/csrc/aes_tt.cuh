@@ -131,12 +131,22 @@ __device__ __forceinline__ void sts32(uint32_t a, uint32_t v)
     asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
-// every thread of the block writes its share of the 16,384 words
+// every thread of a block of THREADS threads writes its share of the 16,384
+// words; all of a thread's loads are issued before its stores, so the
+// build costs one round trip to L2, not one per word
+template <int THREADS>
 __device__ __forceinline__ void build_dual(uint32_t tab, const uint32_t *t0g)
 {
-    for (uint32_t i = threadIdx.x; i < kDualBytes / 4; i += blockDim.x) {
-        const uint32_t v = __ldg(t0g + (i >> 6));
-        sts32(tab + 4 * i, ((i >> 5) & 1) ? ror16(v) : v);
+    constexpr int kPer = (int)(kDualBytes / 4) / THREADS;
+    static_assert(kPer * THREADS == (int)(kDualBytes / 4), "the block's threads divide the table");
+    uint32_t v[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k)
+        v[k] = __ldg(t0g + ((threadIdx.x + (uint32_t)(k * THREADS)) >> 6));
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const uint32_t i = threadIdx.x + (uint32_t)(k * THREADS);
+        sts32(tab + 4 * i, ((i >> 5) & 1) ? ror16(v[k]) : v[k]);
     }
 }
 

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kCtrThreads, 1) ctr_kernel(CtrWork w)
     grid_release();
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t tab = aes::dual_table_at((uint32_t)__cvta_generic_to_shared(smem));
-    aes::build_dual(tab, w.aes_tables);
+    aes::build_dual<kCtrThreads>(tab, w.aes_tables);
     __syncthreads();
     const aes::Lut L = aes::make_lut(tab, lane);
     grid_wait(); // the fragment is complete from here on
