@@ -392,10 +392,8 @@ __device__ __forceinline__ void block_rows(const FuseBuf &f, uint64_t bi, uint32
     }
 }
 
-template <bool PACKED, bool KEYED>
 __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged,
-                                          const uint2 (&v)[8], uint32_t (&rb)[4], int *err,
-                                          const uint32_t (&key)[4], pkb::Stage *stg = nullptr, int lane = 0)
+                                          const uint2 (&v)[8])
 {
     const uint32_t W = f.W, L = f.F;
     uint32_t x1[8][4]; // row-lifted rows, 4 words each
@@ -407,13 +405,11 @@ __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_
     // level-1 tiles: LL_1 = s1[][0..1], HL_1 = s1[][2..3], LH_1 = d1[][0..1], HH_1 = d1[][2..3]
     const uint32_t W1 = W >> 1;
     const bool vec = staged;
-    if (!PACKED) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            st_tile(tile_row(f.band[0][0], W1, 4, bi, bj, r), 4, to_i16x2(s1[r][2]), to_i16x2(s1[r][3]), vec);
-            st_tile(tile_row(f.band[0][1], W1, 4, bi, bj, r), 4, to_i16x2(d1[r][0]), to_i16x2(d1[r][1]), vec);
-            st_tile(tile_row(f.band[0][2], W1, 4, bi, bj, r), 4, to_i16x2(d1[r][2]), to_i16x2(d1[r][3]), vec);
-        }
+    for (int r = 0; r < 4; ++r) {
+        st_tile(tile_row(f.band[0][0], W1, 4, bi, bj, r), 4, to_i16x2(s1[r][2]), to_i16x2(s1[r][3]), vec);
+        st_tile(tile_row(f.band[0][1], W1, 4, bi, bj, r), 4, to_i16x2(d1[r][0]), to_i16x2(d1[r][1]), vec);
+        st_tile(tile_row(f.band[0][2], W1, 4, bi, bj, r), 4, to_i16x2(d1[r][2]), to_i16x2(d1[r][3]), vec);
     }
     if (L == 1) {
 #pragma unroll
@@ -428,54 +424,6 @@ __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_
         lift4(s1[r][0], s1[r][1], x2[r][0], x2[r][1]);
     uint32_t s2[2][2], d2[2][2];
     col_lift<4, 2>(x2, s2, d2);
-    if (PACKED) {
-        // A: LL_2 - 128 (10 bits); B: HL_2, LH_2 (10), HH_2 (11); C: the
-        // level-1 details (10), each pair of coefficients one field from its
-        // biased word; B goes back to the warp (put_b), A and C to the warp's
-        // staging area (copy_out)
-        uint32_t bad = 0u, ra[2] = {0u, 0u}, rc[15];
-#pragma unroll
-        for (int i = 0; i < 15; ++i)
-            rc[i] = 0u;
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const uint32_t a = s2[r][0] - 0x00800080u; // LL_2 - 128
-            bad |= pkb::range_bits<10>(a) | pkb::range_bits<10>(s2[r][1]) | pkb::range_bits<10>(d2[r][0]) |
-                   pkb::range_bits<11>(d2[r][1]);
-            pkb::ins(ra, 20 * r, pkb::field2<10>(a), 20);
-            pkb::ins(rb, 20 * r, pkb::field2<10>(s2[r][1]), 20);      // HL_2
-            pkb::ins(rb, 40 + 20 * r, pkb::field2<10>(d2[r][0]), 20); // LH_2
-            pkb::ins(rb, 80 + 22 * r, pkb::field2<11>(d2[r][1]), 22); // HH_2
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            bad |= pkb::range_bits<10>(s1[r][2]) | pkb::range_bits<10>(s1[r][3]) | pkb::range_bits<10>(d1[r][0]) |
-                   pkb::range_bits<10>(d1[r][1]) | pkb::range_bits<10>(d1[r][2]) | pkb::range_bits<10>(d1[r][3]);
-            pkb::ins(rc, 40 * r, pkb::field2<10>(s1[r][2]), 20); // HL_1
-            pkb::ins(rc, 40 * r + 20, pkb::field2<10>(s1[r][3]), 20);
-            pkb::ins(rc, 160 + 40 * r, pkb::field2<10>(d1[r][0]), 20); // LH_1
-            pkb::ins(rc, 180 + 40 * r, pkb::field2<10>(d1[r][1]), 20);
-            pkb::ins(rc, 320 + 40 * r, pkb::field2<10>(d1[r][2]), 20); // HH_1
-            pkb::ins(rc, 340 + 40 * r, pkb::field2<10>(d1[r][3]), 20);
-        }
-        if (bad)
-            atomicCAS(err, 0, pkb::kErrWidth);
-        const uint64_t idx = bi * (uint64_t)(W >> 3) + bj;
-        if (KEYED && f.keyed) { // B' = B ^ H1(A), then C' = C ^ H2(B')
-            sha::mask_b(key, f.nonce, idx, ra, rb);
-            sha::mask_c(key, f.nonce, idx, rb, rc);
-        }
-        uint8_t *sa = stg->a + 5 * lane;
-        sa[0] = (uint8_t)ra[0];
-        sa[1] = (uint8_t)(ra[0] >> 8);
-        sa[2] = (uint8_t)(ra[0] >> 16);
-        sa[3] = (uint8_t)(ra[0] >> 24);
-        sa[4] = (uint8_t)ra[1];
-#pragma unroll
-        for (int i = 0; i < 15; ++i)
-            stg->c[15 * lane + i] = rc[i];
-        return;
-    }
     const uint32_t W2 = W >> 2;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -503,53 +451,12 @@ __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_
     st_tile(tile_row(f.ll, W3, 1, bi, bj, 0), 1, ll_final(s3[0][0]), 0, vec);
 }
 
-template <bool PACKED, bool KEYED>
 __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged,
-                                          bool vec, uint32_t s8, uint32_t s4, const uint32_t (&rb_in)[4],
-                                          const uint32_t (&key)[4], const pkb::StageIn *stg = nullptr,
-                                          int lane = 0)
+                                          bool vec, uint32_t s8, uint32_t s4)
 {
     const uint32_t W = f.W, L = f.F;
     const uint32_t W1 = W >> 1, W2 = W >> 2, W3 = W >> 3;
     uint32_t s1[4][4], d1[4][4];
-    if (PACKED) {
-        // the block's A (deciphered) and C records from the warp's staging
-        // area, and its B record from the warp
-        const uint64_t idx = bi * (uint64_t)W3 + bj;
-        const uint8_t *sa = stg->a + 5 * lane;
-        const uint32_t ra[2] = {(uint32_t)sa[0] | ((uint32_t)sa[1] << 8) | ((uint32_t)sa[2] << 16) |
-                                    ((uint32_t)sa[3] << 24),
-                                (uint32_t)sa[4]};
-        uint32_t rc[15];
-#pragma unroll
-        for (int i = 0; i < 15; ++i)
-            rc[i] = stg->c[15 * lane + i];
-        uint32_t rb[4] = {rb_in[0], rb_in[1], rb_in[2], rb_in[3]};
-        if (KEYED && f.keyed) { // C = C' ^ H2(B') first, then B = B' ^ H1(A)
-            sha::mask_c(key, f.nonce, idx, rb, rc);
-            sha::mask_b(key, f.nonce, idx, ra, rb);
-        }
-        uint32_t s2[2][2], d2[2][2];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            s2[r][0] = pkb::unfield2<10>(pkb::ext(ra, 20 * r, 20)) + 0x00800080u;
-            s2[r][1] = pkb::unfield2<10>(pkb::ext(rb, 20 * r, 20));
-            d2[r][0] = pkb::unfield2<10>(pkb::ext(rb, 40 + 20 * r, 20));
-            d2[r][1] = pkb::unfield2<11>(pkb::ext(rb, 80 + 22 * r, 22));
-        }
-        uint32_t x2[4][2];
-        col_unlift<4, 2>(s2, d2, x2);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            unlift4(x2[r][0], x2[r][1], s1[r][0], s1[r][1]);
-            s1[r][2] = pkb::unfield2<10>(pkb::ext(rc, 40 * r, 20));
-            s1[r][3] = pkb::unfield2<10>(pkb::ext(rc, 40 * r + 20, 20));
-            d1[r][0] = pkb::unfield2<10>(pkb::ext(rc, 160 + 40 * r, 20));
-            d1[r][1] = pkb::unfield2<10>(pkb::ext(rc, 180 + 40 * r, 20));
-            d1[r][2] = pkb::unfield2<10>(pkb::ext(rc, 320 + 40 * r, 20));
-            d1[r][3] = pkb::unfield2<10>(pkb::ext(rc, 340 + 40 * r, 20));
-        }
-    } else {
     // LL_1: from the input (one level) or from the levels above
     if (L >= 2) {
         uint32_t s2[2][2], d2[2][2];
@@ -638,7 +545,6 @@ __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_
         d1[r][2] = from_i16x2(v[2][0]);
         d1[r][3] = from_i16x2(v[2][1]);
     }
-    } // not packed
     uint32_t x1[8][4];
     col_unlift<8, 4>(s1, d1, x1);
     const uint64_t base = bi * 8 * W + (uint64_t)bj * 8;
@@ -656,39 +562,383 @@ __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_
     }
 }
 
-// the packed record areas of a unit (A, B and C of its 32 blocks), and
-// whether the warp can prefetch them whole
-struct Areas {
-    const uint8_t *a, *b, *c;
-    uint32_t nvalid;
-    bool full;
+// ---------------------------------------------------------------------------
+// the packed forward (Sec. 5.2.3's records of two-level 8 x 8 blocks)
+//
+// A unit is a warp's 32 neighbouring blocks of a block row, one a lane.  Its
+// descriptor fields are decoded once into registers (a lone buffer's straight
+// from the kernel parameter), the next unit's rows are fetched into registers
+// while the current one is transformed, and a unit whose 8 rows are whole
+// data takes its loads without per-row tests.
+// ---------------------------------------------------------------------------
+struct PkUnit {
+    const uint8_t *src;  // forward: the block's first byte (bi 8 W + bj 8 of the buffer)
+    uint8_t *out;        // inverse: the same byte of the recovered buffer
+    uint8_t *pa, *pb, *pc; // the unit's A, B and C record areas
+    uint64_t n_left;     // data bytes from the block's first byte on
+    uint64_t idx;        // the block's index (keyed hash input)
+    uint64_t nonce;
+    uint32_t W;
+    uint32_t nvalid;     // blocks of the unit (0: no unit)
+    bool on;             // the lane has a block
+    bool whole;          // every row of the unit is data, 8-byte aligned
+    bool keyed;
 };
-__device__ __forceinline__ Areas areas_of(const Slot &sl)
+
+__device__ __forceinline__ uint64_t ldg64(const void *p)
 {
-    Areas r{nullptr, nullptr, nullptr, 0u, false};
-    if (!sl.b)
-        return r;
-    const uint32_t nbx = sl.b->W >> 3, s = sl.bj >> 5;
-    const uint64_t idx0 = sl.bi * (uint64_t)nbx + 32ull * s;
-    r.nvalid = min(32u, nbx - 32 * s);
-    r.a = sl.b->pk[0] + 5 * idx0;
-    r.b = sl.b->pk[1] + sl.bi * pkb::b_row_bytes(nbx) + 496ull * s;
-    r.c = sl.b->pk[2] + 60 * idx0;
-    r.full = pkb::full_aligned(r.nvalid, r.a, r.b, r.c);
-    return r;
+    return __ldg(reinterpret_cast<const unsigned long long *>(p));
 }
 
-// the inverse reads four times as many tiles per block as the forward;
-// it runs best with direct loads and many warps, the forward with the ring
-// PACKED: every buffer of the launch is packed (the warp stores or loads its
-// blocks' B records between blocks, which the staged loop below does not
-// allow for); the inverse, and any packed launch, take direct loads
+template <bool FWD>
+__device__ __forceinline__ PkUnit pk_unit(const FuseWork &w, uint64_t u, int lane)
+{
+    PkUnit p;
+    p.nvalid = 0;
+    p.on = p.whole = p.keyed = false;
+    p.src = nullptr;
+    p.out = p.pa = p.pb = p.pc = nullptr;
+    p.n_left = p.idx = p.nonce = 0;
+    p.W = 8;
+    if (u >= w.total_units)
+        return p;
+    const FuseBuf *bp = nullptr; // null: the launch's lone buffer (w.single)
+    uint64_t local = u;
+    if (w.nbufs != 1) {
+        uint32_t lo = 0, hi = w.nbufs;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(&w.bufs[mid].unit0) <= u)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        bp = w.bufs + lo;
+        local = u - __ldg(&bp->unit0);
+    }
+    const uint8_t *src;
+    uint8_t *k0, *k1, *k2;
+    uint64_t n, nonce;
+    uint32_t W, strips, full_rows, vec, keyed;
+    if (bp) {
+        src = reinterpret_cast<const uint8_t *>(ldg64(FWD ? (const void *)&bp->src : (const void *)&bp->out));
+        k0 = reinterpret_cast<uint8_t *>(ldg64(&bp->pk[0]));
+        k1 = reinterpret_cast<uint8_t *>(ldg64(&bp->pk[1]));
+        k2 = reinterpret_cast<uint8_t *>(ldg64(&bp->pk[2]));
+        n = ldg64(&bp->n);
+        nonce = ldg64(&bp->nonce);
+        W = __ldg(&bp->W);
+        strips = __ldg(&bp->strips);
+        full_rows = __ldg(&bp->full_rows);
+        vec = __ldg(&bp->vec);
+        keyed = __ldg(&bp->keyed);
+    } else {
+        src = FWD ? w.single.src : w.single.out;
+        k0 = w.single.pk[0];
+        k1 = w.single.pk[1];
+        k2 = w.single.pk[2];
+        n = w.single.n;
+        nonce = w.single.nonce;
+        W = w.single.W;
+        strips = w.single.strips;
+        full_rows = w.single.full_rows;
+        vec = w.single.vec;
+        keyed = w.single.keyed;
+    }
+    uint64_t bi;
+    uint32_t s;
+    if (local < (1ull << 32)) {
+        const uint32_t l32 = (uint32_t)local, q = l32 / strips;
+        bi = q;
+        s = l32 - q * strips;
+    } else {
+        bi = local / strips;
+        s = (uint32_t)(local % strips);
+    }
+    const uint32_t nbx = W >> 3, bj = 32 * s + (uint32_t)lane;
+    p.W = W;
+    p.nvalid = min(32u, nbx - 32 * s);
+    p.on = bj < nbx;
+    const uint64_t idx0 = bi * (uint64_t)nbx + 32ull * s;
+    p.idx = idx0 + (uint64_t)lane;
+    const uint64_t off = bi * 8 * (uint64_t)W + 8ull * bj;
+    p.n_left = off < n ? n - off : 0;
+    p.src = src + off;
+    p.out = const_cast<uint8_t *>(src) + off;
+    p.pa = k0 + 5 * idx0;
+    p.pb = k1 + bi * pkb::b_row_bytes(nbx) + 496ull * s;
+    p.pc = k2 + 60 * idx0;
+    p.whole = vec != 0 && bi * 8 + 8 <= (uint64_t)full_rows;
+    p.keyed = keyed != 0;
+    p.nonce = nonce;
+    return p;
+}
+
+// the lane's 8 rows of 8 bytes (bytes past the data read as zero)
+__device__ __forceinline__ void pk_rows(const PkUnit &p, uint2 (&v)[8])
+{
+    if (p.whole) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            v[r] = __ldg(reinterpret_cast<const uint2 *>(p.src + (uint64_t)r * p.W));
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        v[r] = make_uint2(0u, 0u);
+        if (!p.on)
+            continue;
+        const uint64_t o = (uint64_t)r * p.W;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (o + i < p.n_left) {
+                const uint32_t b = (uint32_t)__ldg(p.src + o + i) << (8 * (i & 3));
+                if (i < 4)
+                    v[r].x |= b;
+                else
+                    v[r].y |= b;
+            }
+    }
+}
+
+// The block's two levels and its three records in registers.  Only the
+// level-2 values are range-checked: every level-1 detail of bytes is within
+// +-510 (row predict d in [-255, 255], row update s in [-127, 383]; the
+// column steps then give HH = d - floor((d + d') / 2), HL = d +
+// floor((HH + HH' + 2) / 4) and LH = s - floor((s + s') / 2), each in
+// [-510, 510]), so it always fits its 10 bits.
+template <bool KEYED>
+__device__ __forceinline__ void pk_block(const uint2 (&v)[8], bool keyed, const uint32_t (&key)[4],
+                                         uint64_t nonce, uint64_t idx, uint32_t (&ra)[2], uint32_t (&rb)[4],
+                                         uint32_t (&rc)[15], uint32_t &bad)
+{
+    uint32_t x1[8][4];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+        lift8(v[r].x, v[r].y, x1[r]);
+    uint32_t s1[4][4], d1[4][4];
+    col_lift<8, 4>(x1, s1, d1);
+    uint32_t x2[4][2];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        lift4(s1[r][0], s1[r][1], x2[r][0], x2[r][1]);
+    uint32_t s2[2][2], d2[2][2];
+    col_lift<4, 2>(x2, s2, d2);
+    ra[0] = ra[1] = 0u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        rb[i] = 0u;
+#pragma unroll
+    for (int i = 0; i < 15; ++i)
+        rc[i] = 0u;
+    bad = 0u;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const uint32_t a = s2[r][0] - 0x00800080u; // LL_2 - 128
+        bad |= pkb::range_bits<10>(a) | pkb::range_bits<10>(s2[r][1]) | pkb::range_bits<10>(d2[r][0]) |
+               pkb::range_bits<11>(d2[r][1]);
+        pkb::ins(ra, 20 * r, pkb::field2<10>(a), 20);
+        pkb::ins(rb, 20 * r, pkb::field2<10>(s2[r][1]), 20);      // HL_2
+        pkb::ins(rb, 40 + 20 * r, pkb::field2<10>(d2[r][0]), 20); // LH_2
+        pkb::ins(rb, 80 + 22 * r, pkb::field2<11>(d2[r][1]), 22); // HH_2
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        pkb::ins(rc, 40 * r, pkb::field2<10>(s1[r][2]), 20); // HL_1
+        pkb::ins(rc, 40 * r + 20, pkb::field2<10>(s1[r][3]), 20);
+        pkb::ins(rc, 160 + 40 * r, pkb::field2<10>(d1[r][0]), 20); // LH_1
+        pkb::ins(rc, 180 + 40 * r, pkb::field2<10>(d1[r][1]), 20);
+        pkb::ins(rc, 320 + 40 * r, pkb::field2<10>(d1[r][2]), 20); // HH_1
+        pkb::ins(rc, 340 + 40 * r, pkb::field2<10>(d1[r][3]), 20);
+    }
+    if (KEYED && keyed) { // B' = B ^ H1(A), then C' = C ^ H2(B')
+        sha::mask_b(key, nonce, idx, ra, rb);
+        sha::mask_c(key, nonce, idx, rb, rc);
+    }
+}
+
+// Every unit of a packed launch, forward: the lane transforms its block
+// while the next unit's rows load, writes its A and C records into the
+// warp's staging area (C at word 15 lane: conflict-free) and its B record
+// into the warp's shuffle-built chunks, and the warp moves the unit's
+// records with 16-byte stores.
+template <bool KEYED>
+__device__ __forceinline__ void packed_fwd(const FuseWork &w, const uint32_t (&key)[4])
+{
+    __shared__ uint32_t sb[kWarps][pkb::kPackBWords]; // B records of an unaligned unit
+    __shared__ pkb::Stage stg_all[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    pkb::Stage &stg = stg_all[warp];
+    const uint64_t G = (uint64_t)gridDim.x * kWarps;
+    uint64_t u = (uint64_t)blockIdx.x * kWarps + warp;
+    // one unit, whose rows are in v (the next unit's are loading)
+    auto unit = [&](const PkUnit &cur, const uint2 (&v)[8]) {
+        uint32_t ra[2], rb[4], rc[15], bad;
+        pk_block<KEYED>(v, cur.keyed, key, cur.nonce, cur.idx, ra, rb, rc, bad);
+        if (bad && cur.on)
+            atomicCAS(w.err, 0, pkb::kErrWidth);
+        if (!cur.on) { // the B chunks take a lane without a block as zeros
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                rb[i] = 0u;
+        }
+        uint8_t *sa = stg.a + 5 * lane;
+        sa[0] = (uint8_t)ra[0];
+        sa[1] = (uint8_t)(ra[0] >> 8);
+        sa[2] = (uint8_t)(ra[0] >> 16);
+        sa[3] = (uint8_t)(ra[0] >> 24);
+        sa[4] = (uint8_t)ra[1];
+#pragma unroll
+        for (int i = 0; i < 15; ++i)
+            stg.c[15 * lane + i] = rc[i];
+        pkb::put_b(sb[warp], cur.pb, (124 * cur.nvalid + 7) / 8, cur.on, lane, rb);
+        __syncwarp();
+        if (pkb::full_aligned(cur.nvalid, cur.pa, cur.pb, cur.pc)) {
+            pkb::copy_out_full(cur.pa, cur.pc, stg, lane);
+        } else {
+            pkb::copy_out(cur.pa, stg.a, 5 * cur.nvalid, lane);
+            pkb::copy_out(cur.pc, reinterpret_cast<const uint8_t *>(stg.c), 60 * cur.nvalid, lane);
+        }
+        __syncwarp(); // every lane is done with the staging area before it is refilled
+    };
+    PkUnit cur = pk_unit<true>(w, u, lane);
+    uint2 rows[8];
+    pk_rows(cur, rows);
+    for (; u < w.total_units; u += G) {
+        uint2 v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            v[r] = rows[r];
+        const PkUnit nx = pk_unit<true>(w, u + G, lane);
+        pk_rows(nx, rows);
+        unit(cur, v);
+        cur = nx;
+    }
+}
+
+// The block's records (A deciphered and C from the warp's staging area, B
+// from the warp) back to its 8 rows of bytes: both levels undone in the
+// registers, the rows stored straight from them.
+template <bool KEYED>
+__device__ __forceinline__ void pk_inv_block(const PkUnit &p, const pkb::StageIn &st, const uint32_t (&rb_in)[4],
+                                             const uint32_t (&key)[4], int lane)
+{
+    const uint8_t *sa = st.a + 5 * lane;
+    const uint32_t ra[2] = {(uint32_t)sa[0] | ((uint32_t)sa[1] << 8) | ((uint32_t)sa[2] << 16) |
+                                ((uint32_t)sa[3] << 24),
+                            (uint32_t)sa[4]};
+    uint32_t rc[15];
+#pragma unroll
+    for (int i = 0; i < 15; ++i)
+        rc[i] = st.c[15 * lane + i];
+    uint32_t rb[4] = {rb_in[0], rb_in[1], rb_in[2], rb_in[3]};
+    if (KEYED && p.keyed) { // C = C' ^ H2(B') first, then B = B' ^ H1(A)
+        sha::mask_c(key, p.nonce, p.idx, rb, rc);
+        sha::mask_b(key, p.nonce, p.idx, ra, rb);
+    }
+    uint32_t s1[4][4], d1[4][4];
+    uint32_t s2[2][2], d2[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        s2[r][0] = pkb::unfield2<10>(pkb::ext(ra, 20 * r, 20)) + 0x00800080u;
+        s2[r][1] = pkb::unfield2<10>(pkb::ext(rb, 20 * r, 20));
+        d2[r][0] = pkb::unfield2<10>(pkb::ext(rb, 40 + 20 * r, 20));
+        d2[r][1] = pkb::unfield2<11>(pkb::ext(rb, 80 + 22 * r, 22));
+    }
+    uint32_t x2[4][2];
+    col_unlift<4, 2>(s2, d2, x2);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        unlift4(x2[r][0], x2[r][1], s1[r][0], s1[r][1]);
+        s1[r][2] = pkb::unfield2<10>(pkb::ext(rc, 40 * r, 20));
+        s1[r][3] = pkb::unfield2<10>(pkb::ext(rc, 40 * r + 20, 20));
+        d1[r][0] = pkb::unfield2<10>(pkb::ext(rc, 160 + 40 * r, 20));
+        d1[r][1] = pkb::unfield2<10>(pkb::ext(rc, 180 + 40 * r, 20));
+        d1[r][2] = pkb::unfield2<10>(pkb::ext(rc, 320 + 40 * r, 20));
+        d1[r][3] = pkb::unfield2<10>(pkb::ext(rc, 340 + 40 * r, 20));
+    }
+    uint32_t x1[8][4];
+    col_unlift<8, 4>(s1, d1, x1);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const uint2 v = unlift8(x1[r]);
+        const uint64_t o = (uint64_t)r * p.W;
+        if (p.whole) {
+            __stcs(reinterpret_cast<uint2 *>(p.out + o), v);
+        } else {
+            for (int i = 0; i < 8 && o + i < p.n_left; ++i)
+                p.out[o + i] = (uint8_t)((i < 4 ? v.x : v.y) >> (8 * (i & 3)));
+        }
+    }
+}
+
+// Every unit of a packed launch, inverse: the warp fetches the next unit's
+// A, B and C records into the other of its two staging areas with cp.async
+// (a full warp whose three areas are 16-byte aligned; other units load
+// synchronously) while the current unit is transformed.
+template <bool KEYED>
+__device__ __forceinline__ void packed_inv(const FuseWork &w, const uint32_t (&key)[4])
+{
+    __shared__ uint32_t sb[kWarps][pkb::kPackBWords];
+    __shared__ pkb::StageIn stg_in[kWarps][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t G = (uint64_t)gridDim.x * kWarps;
+    uint64_t u = (uint64_t)blockIdx.x * kWarps + warp;
+    // one unit, whose records (when `full`) are landing in `st`; the next
+    // unit's group was committed after this one's
+    auto unit = [&](const PkUnit &cur, bool full, pkb::StageIn &st) {
+        cp_wait<1>(); // this unit's group has landed
+        __syncwarp();
+        uint32_t rb[4] = {0u, 0u, 0u, 0u};
+        if (full) {
+            pkb::b_from_stage(st, cur.on, lane, rb);
+        } else {
+            pkb::get_b(sb[warp], cur.pb, (124 * cur.nvalid + 7) / 8, cur.on, lane, rb);
+            pkb::copy_in(st.a, cur.pa, 5 * cur.nvalid, lane);
+            pkb::copy_in(reinterpret_cast<uint8_t *>(st.c), cur.pc, 60 * cur.nvalid, lane);
+            __syncwarp();
+        }
+        if (cur.on)
+            pk_inv_block<KEYED>(cur, st, rb, key, lane);
+        __syncwarp(); // every lane is done with this area before it is refilled
+    };
+    PkUnit cur = pk_unit<false>(w, u, lane);
+    bool cur_full = pkb::full_aligned(cur.nvalid, cur.pa, cur.pb, cur.pc);
+    if (cur_full)
+        pkb::prefetch_full(stg_in[warp][0], cur.pa, cur.pb, cur.pc, lane);
+    cp_commit();
+    for (uint32_t i = 0; u < w.total_units; u += G, ++i) {
+        const PkUnit nx = pk_unit<false>(w, u + G, lane);
+        const bool nx_full = pkb::full_aligned(nx.nvalid, nx.pa, nx.pb, nx.pc);
+        if (nx_full)
+            pkb::prefetch_full(stg_in[warp][(i + 1) & 1], nx.pa, nx.pb, nx.pc, lane);
+        cp_commit();
+        unit(cur, cur_full, stg_in[warp][i & 1]);
+        cur = nx;
+        cur_full = nx_full;
+    }
+    cp_wait<0>();
+}
+
+// The unpacked inverse reads four times as many tiles per block as the
+// forward; it runs best with direct loads and many warps, the unpacked
+// forward with the ring.  Packed launches run their own loops (packed_fwd,
+// packed_inv): every buffer of such a launch is packed.
 #ifndef BLOCK_PACKED_FWD_MINB
 #define BLOCK_PACKED_FWD_MINB 5
 #endif
-// the packed forward: five 4-warp blocks an SM (registers capped at 102)
+#ifndef BLOCK_PACKED_INV_MINB
+#define BLOCK_PACKED_INV_MINB 6
+#endif
+template <bool FWD, bool PACKED>
+__host__ __device__ constexpr int block_min_ctas(bool keyed)
+{
+    return (!PACKED || keyed) ? 1 : FWD ? BLOCK_PACKED_FWD_MINB : BLOCK_PACKED_INV_MINB;
+}
+// the packed forward: five 4-warp blocks an SM (registers capped at 102);
+// the packed inverse: six (capped at 85)
 template <bool FWD, bool PACKED, bool KEYED>
-__global__ void __launch_bounds__(kThreads, (FWD && PACKED && !KEYED) ? BLOCK_PACKED_FWD_MINB : 1)
+__global__ void __launch_bounds__(kThreads, block_min_ctas<FWD, PACKED>(KEYED))
     block_kernel(FuseWork w)
 {
     __shared__ FuseBuf s_single;
@@ -702,101 +952,23 @@ __global__ void __launch_bounds__(kThreads, (FWD && PACKED && !KEYED) ? BLOCK_PA
             key[i] = __ldg(w.key_words + i);
     }
     if (PACKED && !FWD) {
-        // the packed inverse: a warp's records (A deciphered, B, C) come into
-        // one of two staging areas with cp.async while the unit before is
-        // transformed (full warps whose three areas are 16-byte aligned);
-        // other units load them synchronously
-        __shared__ uint32_t sb[kWarps][pkb::kPackBWords];
-        __shared__ pkb::StageIn stg_in[kWarps][2];
         grid_release();
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const uint64_t G = (uint64_t)gridDim.x * kWarps;
-        const uint64_t u0 = (uint64_t)blockIdx.x * kWarps + warp;
-        {
-            const Slot s0 = slot_of(w, &s_single, u0, lane);
-            const Areas a0 = areas_of(s0);
-            if (a0.full)
-                pkb::prefetch_full(stg_in[warp][0], a0.a, a0.b, a0.c, lane);
-            cp_commit();
-        }
-        uint32_t i = 0;
-        for (uint64_t u = u0; u < w.total_units; u += G, ++i) {
-            const Slot sl = slot_of(w, &s_single, u, lane);
-            const Areas ar = areas_of(sl);
-            {
-                const Slot nx = slot_of(w, &s_single, u + G, lane);
-                const Areas an = areas_of(nx);
-                if (an.full)
-                    pkb::prefetch_full(stg_in[warp][(i + 1) & 1], an.a, an.b, an.c, lane);
-                cp_commit();
-            }
-            cp_wait<1>(); // this unit's group has landed
-            __syncwarp();
-            pkb::StageIn &cur = stg_in[warp][i & 1];
-            uint32_t rb[4] = {0u, 0u, 0u, 0u};
-            if (ar.full) {
-                pkb::b_from_stage(cur, sl.on, lane, rb);
-            } else {
-                pkb::get_b(sb[warp], ar.b, (124 * ar.nvalid + 7) / 8, sl.on, lane, rb);
-                pkb::copy_in(cur.a, ar.a, 5 * ar.nvalid, lane);
-                pkb::copy_in(reinterpret_cast<uint8_t *>(cur.c), ar.c, 60 * ar.nvalid, lane);
-                __syncwarp();
-            }
-            if (sl.on)
-                inv_block<true, KEYED>(*sl.b, sl.bi, sl.bj, false, sl.vec, 0, 0, rb, key, &cur, lane);
-            __syncwarp(); // every lane is done with this area before it is refilled
-        }
-        cp_wait<0>();
+        packed_inv<KEYED>(w, key);
         return;
     }
-    if (!FWD || PACKED) {
-        __shared__ uint32_t sb[kWarps][pkb::kPackBWords]; // a warp's B records
-        __shared__ pkb::Stage stg_all[PACKED ? kWarps : 1]; // a warp's A and C records
+    if (FWD && PACKED) {
+        grid_release();
+        packed_fwd<KEYED>(w, key);
+        return;
+    }
+    if (!FWD) { // the unpacked inverse: direct loads
         grid_release();
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const uint64_t G = (uint64_t)gridDim.x * kWarps;
-        // forward: the rows of the unit after the current one, fetched while
-        // the current one is transformed
-        uint2 rows[8];
-        if (FWD) {
-            const Slot s0 = slot_of(w, &s_single, (uint64_t)blockIdx.x * kWarps + warp, lane);
-            if (s0.on)
-                block_rows(*s0.b, s0.bi, s0.bj, false, s0.vec, 0, rows);
-        }
         for (uint64_t u = (uint64_t)blockIdx.x * kWarps + warp; u < w.total_units; u += G) {
             const Slot sl = slot_of(w, &s_single, u, lane);
-            uint32_t rb[4] = {0u, 0u, 0u, 0u};
-            const uint32_t nbx = sl.b->W >> 3, s = sl.bj >> 5, nvalid = min(32u, nbx - 32 * s);
-            uint8_t *bbase = PACKED ? sl.b->pk[1] + sl.bi * pkb::b_row_bytes(nbx) + 496ull * s : nullptr;
-            const uint32_t bcount = (124 * nvalid + 7) / 8;
-            pkb::Stage *stg = &stg_all[PACKED ? warp : 0];
-            const uint64_t idx0 = PACKED ? sl.bi * (uint64_t)nbx + 32ull * s : 0;
-            if (FWD) {
-                // this block's rows came with the previous unit; fetch the next unit's
-                uint2 v[8];
-#pragma unroll
-                for (int r = 0; r < 8; ++r)
-                    v[r] = rows[r];
-                const Slot nx = slot_of(w, &s_single, u + G, lane);
-                if (nx.on)
-                    block_rows(*nx.b, nx.bi, nx.bj, false, nx.vec, 0, rows);
-                if (sl.on)
-                    fwd_block<PACKED, KEYED>(*sl.b, sl.bi, sl.bj, false, v, rb, w.err, key, stg, lane);
-            } else if (sl.on) {
-                inv_block<false, KEYED>(*sl.b, sl.bi, sl.bj, false, sl.vec, 0, 0, rb, key);
-            }
-            if (PACKED && FWD) {
-                pkb::put_b(sb[warp], bbase, bcount, sl.on, lane, rb);
-                __syncwarp();
-                uint8_t *pa = sl.b->pk[0] + 5 * idx0, *pc = sl.b->pk[2] + 60 * idx0;
-                if (pkb::full_aligned(nvalid, pa, bbase, pc)) {
-                    pkb::copy_out_full(pa, pc, *stg, lane);
-                } else {
-                    pkb::copy_out(pa, stg->a, 5 * nvalid, lane);
-                    pkb::copy_out(pc, reinterpret_cast<const uint8_t *>(stg->c), 60 * nvalid, lane);
-                }
-                __syncwarp();
-            }
+            if (sl.on)
+                inv_block(*sl.b, sl.bi, sl.bj, false, sl.vec, 0, 0);
         }
         return;
     }
@@ -829,15 +1001,13 @@ __global__ void __launch_bounds__(kThreads, (FWD && PACKED && !KEYED) ? BLOCK_PA
         else
             inv_issue(ahead, ring8 + ahead_off, ring4 + ahead_off);
         cp_wait<kDepth - 1>();
-        uint32_t rb[4] = {0u, 0u, 0u, 0u};
         if (cur.on) {
             if (FWD) {
                 uint2 v[8];
                 block_rows(*cur.b, cur.bi, cur.bj, cur.vec, false, ring8 + cur_off, v);
-                fwd_block<false, false>(*cur.b, cur.bi, cur.bj, cur.vec, v, rb, w.err, key);
+                fwd_block(*cur.b, cur.bi, cur.bj, cur.vec, v);
             } else
-                inv_block<false, false>(*cur.b, cur.bi, cur.bj, cur.vec, cur.vec, ring8 + cur_off, ring4 + cur_off,
-                                        rb, key);
+                inv_block(*cur.b, cur.bi, cur.bj, cur.vec, cur.vec, ring8 + cur_off, ring4 + cur_off);
         }
     };
     for (uint64_t i = 0; u0 + i * G < w.total_units; i += 3) {

@@ -82,26 +82,32 @@ __device__ __forceinline__ U128 u128(const uint32_t (&r)[4])
     return {r[0] | ((uint64_t)r[1] << 32), r[2] | ((uint64_t)r[3] << 32)};
 }
 
-__device__ __forceinline__ U128 shr128(U128 x, uint32_t s) // 0 <= s <= 128
+// 64-bit shifts whose amount may exceed 63: PTX clamps the amount to 64,
+// so the result is then 0 (C++ shifts would be undefined there)
+__device__ __forceinline__ uint64_t shr64z(uint64_t x, uint32_t s)
 {
-    if (s >= 128)
-        return {0ull, 0ull};
-    if (s >= 64)
-        return {x.hi >> (s - 64), 0ull};
-    if (s == 0)
-        return x;
-    return {(x.lo >> s) | (x.hi << (64 - s)), x.hi >> s};
+    uint64_t r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+    return r;
+}
+__device__ __forceinline__ uint64_t shl64z(uint64_t x, uint32_t s)
+{
+    uint64_t r;
+    asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+    return r;
 }
 
-__device__ __forceinline__ U128 shl128(U128 x, uint32_t s) // 0 <= s <= 128
+// 128-bit shifts by 0 <= s <= 128, without branches: of the three terms of
+// the word that straddles, the ones whose amount is out of range (64 - s or
+// s - 64 wraps to a huge unsigned value) are 0
+__device__ __forceinline__ U128 shr128(U128 x, uint32_t s)
 {
-    if (s >= 128)
-        return {0ull, 0ull};
-    if (s >= 64)
-        return {0ull, x.lo << (s - 64)};
-    if (s == 0)
-        return x;
-    return {x.lo << s, (x.hi << s) | (x.lo >> (64 - s))};
+    return {shr64z(x.lo, s) | shl64z(x.hi, 64u - s) | shr64z(x.hi, s - 64u), shr64z(x.hi, s)};
+}
+
+__device__ __forceinline__ U128 shl128(U128 x, uint32_t s)
+{
+    return {shl64z(x.lo, s), shl64z(x.hi, s) | shr64z(x.lo, 64u - s) | shl64z(x.lo, s - 64u)};
 }
 
 __device__ __forceinline__ void store_b_vec(uint8_t *base, uint32_t count, int lane, const uint32_t (&rb)[4])
@@ -117,7 +123,7 @@ __device__ __forceinline__ void store_b_vec(uint8_t *base, uint32_t count, int l
     const uint32_t off = 16u * (uint32_t)lane;
     if (off + 16 <= count) {
         __stcs(reinterpret_cast<uint4 *>(base + off), make_uint4(c[0], c[1], c[2], c[3]));
-    } else {
+    } else if (off < count) {
 #pragma unroll
         for (uint32_t k = 0; k < 16; ++k)
             if (off + k < count)
@@ -136,7 +142,7 @@ __device__ __forceinline__ void load_b_vec(const uint8_t *base, uint32_t count, 
         w[1] = v.y;
         w[2] = v.z;
         w[3] = v.w;
-    } else {
+    } else if (off < count) {
 #pragma unroll
         for (uint32_t k = 0; k < 16; ++k)
             if (off + k < count)
