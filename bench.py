@@ -1244,6 +1244,40 @@ def run_aesfull(args, rank, world, local_rank):
                 "hbm_frac": round(2 * n / (t_launch / 1e3) / 1e9 / peak_hbm, 4),
                 "hbm_peak": peak_hbm, "hbm_peak_kind": peak_kind}
 
+    # the table form against the bitsliced form (frag_aes128_ctr_bitsliced),
+    # at the comparator's size and at the private fragments of the same
+    # buffer at one level (LL_1 as int16: 128 MiB) and two (LL_2: 32 MiB);
+    # each launch timed alone, L2 flushed before it, the median of 20
+    forms = None
+    if not args.no_sub:
+        forms = {}
+        with torch.cuda.stream(s):
+            fr.aes_ctr_bitsliced(key, 0, src, out, stream=s)
+        torch.cuda.synchronize()
+        assert torch.equal(ct, out), "the two AES forms differ"
+        for label, m in (("comparator_256MiB", n), ("fragment_L1_128MiB", n // 2),
+                         ("fragment_L2_32MiB", n // 8)):
+            row = {}
+            for fname, f in (("table", fr.aes_ctr), ("bitsliced", fr.aes_ctr_bitsliced)):
+                evs = []
+                with torch.cuda.stream(s):
+                    for i in range(max(3, Wm) + 20):
+                        flush_l2(i)
+                        e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                        e[0].record(s)
+                        f(key, 0, src[:m], out[:m], stream=s)
+                        e[1].record(s)
+                        if i >= max(3, Wm):
+                            evs.append(e)
+                torch.cuda.synchronize()
+                t = sorted(a.elapsed_time(b) for a, b in evs)[len(evs) // 2]
+                row[fname] = {"us_per_launch": round(t * 1e3, 1), "us_per_MiB": round(t * 1e3 / (m / 2**20), 4),
+                              "GBps": round(m / (t / 1e3) / 1e9, 1)}
+            row["bitsliced_over_table"] = round(row["bitsliced"]["us_per_launch"] /
+                                                row["table"]["us_per_launch"], 3)
+            forms[label] = row
+        fr.sync_status(s)
+
     # e2e: pinned host buffers, copies inside the timed region
     e2e = None
     if args.e2e_steps > 0:
@@ -1300,6 +1334,7 @@ def run_aesfull(args, rank, world, local_rank):
                 "gpu_launches": 2 * K,
                 "encrypt_gbps": round(n / (statistics.mean(te) / 1e3) / 1e9, 2),
                 "decrypt_gbps": round(n / (statistics.mean(td) / 1e3) / 1e9, 2),
+                "aes_forms": forms,
                 "p50_ms": round(q[len(q) // 2], 5), "p99_ms": round(q[min(len(q) - 1, int(0.99 * len(q)))], 5),
                 "wall_s_timed_region": round(wall, 3)}
         print(json.dumps(line), flush=True)

@@ -244,6 +244,15 @@ frag_status frag_recover(frag_plan plan, frag_key key, uint64_t nonce, const voi
 frag_status frag_aes128_ctr(frag_key key, uint64_t nonce, const void *d_in, void *d_out,
                             uint64_t nbytes, frag_stream stream);
 
+/* The same full-buffer AES-128-CTR computed bitsliced instead of with
+ * tables (FIPS-197's rounds as AND/XOR circuits over bit planes of 32 blocks
+ * a thread; the S-box as Boyar and Peralta's 128-gate circuit): the
+ * measured alternative to the table form, which the library's fragment
+ * cipher uses.  Same arguments, result, alignment and error behaviour as
+ * frag_aes128_ctr; its output is byte-identical. */
+frag_status frag_aes128_ctr_bitsliced(frag_key key, uint64_t nonce, const void *d_in, void *d_out,
+                                      uint64_t nbytes, frag_stream stream);
+
 /* Host-buffer forms of the two calls: copy the host input into stream-ordered
  * device memory (the library's pool), run the same kernels, copy the results
  * back, and return once they are in host memory.  Pinned (cudaHostAlloc) host

@@ -28,7 +28,8 @@ EXPORTS = [
     "frag_plan_set_block", "frag_plan_get_block", "frag_plan_set_packed", "frag_plan_get_packed",
     "frag_plan_fragment_sizes", "frag_plan_set_protect_public", "frag_plan_get_protect_public",
     "frag_key_create", "frag_key_destroy",
-    "frag_protect", "frag_recover", "frag_aes128_ctr", "frag_protect_host", "frag_recover_host",
+    "frag_protect", "frag_recover", "frag_aes128_ctr", "frag_aes128_ctr_bitsliced", "frag_protect_host",
+    "frag_recover_host",
     "frag_protect_batch", "frag_recover_batch", "frag_batch_create_protect",
     "frag_batch_create_recover", "frag_batch_run", "frag_batch_destroy", "frag_batch_info",
     "frag_batch_set_timing", "frag_batch_launch_times",
@@ -108,6 +109,7 @@ def lib():
         "frag_protect": ([vp, vp, u64, vp, u64, vp, vp, vp], ctypes.c_int),
         "frag_recover": ([vp, vp, u64, vp, vp, u64, vp, vp], ctypes.c_int),
         "frag_aes128_ctr": ([vp, u64, vp, vp, u64, vp], ctypes.c_int),
+        "frag_aes128_ctr_bitsliced": ([vp, u64, vp, vp, u64, vp], ctypes.c_int),
         "frag_protect_host": ([vp, vp, u64, vp, u64, vp, vp, vp], ctypes.c_int),
         "frag_recover_host": ([vp, vp, u64, vp, vp, u64, vp, vp], ctypes.c_int),
         "frag_protect_batch": ([ctypes.POINTER(frag_item), u32, vp, vp], ctypes.c_int),
@@ -322,6 +324,16 @@ def aes_ctr(key: Key, nonce: int, data, out=None, stream=None):
         out = _empty(data.numel(), data.device)
     check(lib().frag_aes128_ctr(key.handle, nonce, _ptr(data), _ptr(out), data.numel(),
                                 _stream(stream)))
+    return out
+
+
+def aes_ctr_bitsliced(key: Key, nonce: int, data, out=None, stream=None):
+    """aes_ctr computed by the bitsliced kernel (the measured alternative to
+    the table form); byte-identical output."""
+    if out is None:
+        out = _empty(data.numel(), data.device)
+    check(lib().frag_aes128_ctr_bitsliced(key.handle, nonce, _ptr(data), _ptr(out), data.numel(),
+                                          _stream(stream)))
     return out
 
 

@@ -122,3 +122,110 @@ cudaError_t ctr_occupancy(int *blocks_per_sm)
 }
 
 } // namespace frag
+
+// ---------------------------------------------------------------------------
+// bitsliced AES-128-CTR (aes_bs.cuh): the measured alternative to the table
+// form.  A warp takes a chunk of 1,024 counter blocks; lane l computes blocks
+// base + 32 j + l (j = 0..31) as one bitsliced state, so its counter planes
+// need no transpose (bits 0..4 of the block index are the lane's, bits 5..9
+// the fixed patterns of j, the rest the chunk's), and after the last round
+// four 32 x 32 transposes give each block's 16 keystream bytes, which the
+// warp XORs into the data 512 contiguous bytes at a time.
+// ---------------------------------------------------------------------------
+#include "aes_bs.cuh"
+
+namespace frag {
+
+constexpr int kBsThreads = 128;
+
+__global__ void __launch_bounds__(kBsThreads, 2) ctr_bs_kernel(const __grid_constant__ BsCtrWork w)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (kBsThreads / 32);
+    const bool vec = (((uintptr_t)w.in | (uintptr_t)w.out) & 15u) == 0;
+    const uint32_t jpat[5] = {0xaaaaaaaau, 0xccccccccu, 0xf0f0f0f0u, 0xff00ff00u, 0xffff0000u};
+    for (uint64_t ch = (uint64_t)blockIdx.x * (kBsThreads / 32) + (threadIdx.x >> 5); ch < w.nchunks;
+         ch += warps) {
+        const uint64_t base = ch * (uint64_t)bs::kChunkBlocks;
+        // the counter blocks nonce || (base + 32 j + lane), big-endian, with
+        // round key 0
+        uint32_t x[128];
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                uint32_t v;
+                if (p < 8) {
+                    v = 0u - (uint32_t)((w.nonce >> (8 * (7 - p) + b)) & 1u);
+                } else {
+                    const int q = 8 * (15 - p) + b; // bit q of the block index
+                    if (q < 5)
+                        v = 0u - ((lane >> q) & 1u);
+                    else if (q < 10)
+                        v = jpat[q - 5];
+                    else
+                        v = 0u - (uint32_t)((base >> q) & 1u);
+                }
+                x[8 * p + b] = v ^ w.w[0][8 * p + b];
+            }
+        }
+#pragma unroll 1
+        for (int r = 1; r < 10; ++r) {
+            uint32_t y[128], z[128];
+            bs::sub_shift(x, y);
+            bs::mix(y, z);
+#pragma unroll
+            for (int k = 0; k < 128; ++k)
+                x[k] = z[k] ^ w.w[r][k];
+        }
+        {
+            uint32_t y[128];
+            bs::sub_shift(x, y);
+#pragma unroll
+            for (int k = 0; k < 128; ++k)
+                x[k] = y[k] ^ w.w[10][k];
+        }
+        // keystream word g of block j = bytes 4 g .. 4 g + 3 little-endian
+        uint32_t T[4][32];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+                T[g][k] = x[8 * (4 * g + k / 8) + k % 8];
+            bs::transpose32(T[g]);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const uint64_t o = 16 * (base + 32 * (uint64_t)j + lane);
+            if (o >= w.bytes)
+                continue;
+            if (vec && o + 16 <= w.bytes) {
+                const uint4 t = __ldcs(reinterpret_cast<const uint4 *>(w.in + o));
+                __stcs(reinterpret_cast<uint4 *>(w.out + o),
+                       make_uint4(t.x ^ T[0][j], t.y ^ T[1][j], t.z ^ T[2][j], t.w ^ T[3][j]));
+            } else {
+                for (int k = 0; k < 16 && o + k < w.bytes; ++k)
+                    w.out[o + k] = (uint8_t)(w.in[o + k] ^ (uint8_t)(T[k >> 2][j] >> (8 * (k & 3))));
+            }
+        }
+    }
+}
+
+cudaError_t launch_ctr_bs(const BsCtrWork &w, cudaStream_t stream)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)ctr_bs_kernel, kBsThreads, 0);
+    if (e != cudaSuccess)
+        return e;
+    const uint64_t need = (w.nchunks + kBsThreads / 32 - 1) / (kBsThreads / 32);
+    const uint64_t most = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
+    const uint32_t grid = (uint32_t)(need < most ? need : most);
+    ctr_bs_kernel<<<grid, kBsThreads, 0, stream>>>(w);
+    return cudaGetLastError();
+}
+
+} // namespace frag

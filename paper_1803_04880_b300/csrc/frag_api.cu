@@ -5,6 +5,7 @@
 // the AES tables and a device error word.  All work is enqueued on the
 // caller's stream; nothing here falls back to the CPU.
 #include "aes_tt.cuh"
+#include "aes_bs.cuh"
 #include "frag.h"
 #include "frag_internal.cuh"
 
@@ -2236,6 +2237,42 @@ frag_status frag_aes128_ctr(frag_key key, uint64_t nonce, const void *d_in, void
     c.bytes = nbytes;
     c.nblocks = (nbytes + 15) / 16;
     return ctr_launch(*d, frag::aes::keys_from_words(key->rk), nullptr, &c, (cudaStream_t)stream);
+}
+
+frag_status frag_aes128_ctr_bitsliced(frag_key key, uint64_t nonce, const void *d_in, void *d_out,
+                                      uint64_t nbytes, frag_stream stream)
+{
+    if (key == nullptr)
+        return fail(FRAG_EINVAL, "key is NULL");
+    if (nbytes == 0)
+        return FRAG_OK;
+    if (d_in == nullptr || d_out == nullptr)
+        return fail(FRAG_EINVAL, "NULL buffer");
+    DeviceState *d = nullptr;
+    int dev = 0;
+    frag_status st = device_state(&d, &dev);
+    if (st != FRAG_OK)
+        return st;
+    // the key schedule sliced into bit planes: word b of byte p of round r is
+    // all-ones when bit b of that byte is set; 0x63 (the S-box's affine
+    // constant, which the circuit leaves out) folded into rounds 1..10
+    static_assert(sizeof(frag::BsCtrWork) < 32000, "the sliced key schedule travels in the kernel parameter");
+    frag::BsCtrWork w;
+    std::memset(&w, 0, sizeof(w));
+    w.in = (const uint8_t *)d_in;
+    w.out = (uint8_t *)d_out;
+    w.bytes = nbytes;
+    w.nonce = nonce;
+    const uint64_t nblocks = (nbytes + 15) / 16;
+    w.nchunks = (nblocks + frag::bs::kChunkBlocks - 1) / frag::bs::kChunkBlocks;
+    for (int r = 0; r < 11; ++r)
+        for (int p = 0; p < 16; ++p) {
+            const uint32_t byte = ((key->rk[4 * r + p / 4] >> (24 - 8 * (p % 4))) & 0xffu) ^ (r ? 0x63u : 0u);
+            for (int b = 0; b < 8; ++b)
+                w.w[r][8 * p + b] = ((byte >> b) & 1u) ? 0xffffffffu : 0u;
+        }
+    const cudaError_t e = frag::launch_ctr_bs(w, (cudaStream_t)stream);
+    return e == cudaSuccess ? FRAG_OK : cuda_fail(e, "bitsliced CTR launch");
 }
 
 frag_status frag_recover(frag_plan plan, frag_key key, uint64_t nonce, const void *d_private,

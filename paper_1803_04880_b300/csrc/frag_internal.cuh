@@ -188,6 +188,20 @@ struct CtrWork {
 
 cudaError_t launch_ctr(const CtrWork &w, uint32_t grid, cudaStream_t stream);
 cudaError_t ctr_occupancy(int *blocks_per_sm);
+
+// The bitsliced AES-128-CTR of a whole buffer (aes_bs.cuh): the comparator
+// form measured against the table form above.  Warp chunks of 1,024 counter
+// blocks; the sliced key schedule (11 x 128 words, 0x63 folded into rounds
+// 1..10) travels in the kernel parameter.
+struct BsCtrWork {
+    const uint8_t *in;
+    uint8_t *out;
+    uint64_t bytes;
+    uint64_t nonce;
+    uint64_t nchunks; // chunks of 1,024 blocks
+    uint32_t w[11][128];
+};
+cudaError_t launch_ctr_bs(const BsCtrWork &w, cudaStream_t stream);
 constexpr uint32_t kCtrTurn = 32;       // blocks of a warp turn at least (one a lane)
 constexpr int kCtrThreads = 1024;       // one CTA an SM (the two-table AES in shared memory)
 
