@@ -210,22 +210,12 @@ __device__ __forceinline__ void ld_tile(const uint8_t *p, uint32_t b, uint32_t &
 }
 
 // ---------------------------------------------------------------------------
-// one block, forward and inverse
-// ---------------------------------------------------------------------------
-// ---------------------------------------------------------------------------
-// staged loads: each warp copies the rows of its next blocks into a ring of
-// shared-memory stages with cp.async (each lane its own bytes, so no
-// barrier), two blocks ahead of the one it computes
+// staged loads (the unpacked forward): each warp copies the rows of its next
+// blocks into a ring of shared-memory stages with cp.async (each lane its own
+// bytes, so no barrier), two blocks ahead of the one it computes
 // ---------------------------------------------------------------------------
 constexpr int kDepth = 3;
 constexpr int kFwdStage = 8 * 256; // 8 rows x 32 lanes x 8 bytes
-// inverse stage: level-1 bands (HL, LH, HH) x 4 rows, 8 bytes a lane, then
-// LL_1 rows (one level) or the level-2 bands x 2 rows (4 bytes a lane)
-// followed by LL_2 rows (two levels) or the four level-3 words (three)
-constexpr int kInvX = 12 * 256;
-constexpr int kInvL2Ll = kInvX + 6 * 128;
-constexpr int kInvL3 = kInvX + 6 * 128;
-constexpr int kInvStage = kInvL3 + 4 * 128;
 
 extern __shared__ __align__(16) uint8_t g_block_smem[];
 
@@ -233,10 +223,6 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)
 __device__ __forceinline__ void cp8(uint32_t dst, const void *src, uint32_t bytes)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp4(uint32_t dst, const void *src, uint32_t bytes)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -250,7 +236,6 @@ __device__ __forceinline__ const uint8_t *ring_ptr(uint32_t a)
     return g_block_smem + (a - smem_addr(g_block_smem));
 }
 __device__ __forceinline__ uint2 lds8(uint32_t a) { return *reinterpret_cast<const uint2 *>(ring_ptr(a)); }
-__device__ __forceinline__ uint32_t lds4(uint32_t a) { return *reinterpret_cast<const uint32_t *>(ring_ptr(a)); }
 
 // the block a lane works on, or none
 struct Slot {
@@ -325,44 +310,6 @@ __device__ __forceinline__ void fwd_issue(const Slot &sl, uint32_t st)
     cp_commit();
 }
 
-__device__ __forceinline__ void inv_issue(const Slot &sl, uint32_t s8, uint32_t s4)
-{
-    if (sl.on && sl.vec) {
-        const FuseBuf &f = *sl.b;
-        const uint32_t W = f.W, L = f.F;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                cp8(s8 + 256 * (3 * r + k), tile_row(f.band[0][k], W >> 1, 4, sl.bi, sl.bj, r), 8);
-            if (L == 1)
-                cp8(s8 + kInvX + 256 * r, tile_row(f.ll, W >> 1, 4, sl.bi, sl.bj, r), 8);
-        }
-        if (L >= 2) {
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    cp4(s4 + kInvX + 128 * (3 * r + k), tile_row(f.band[1][k], W >> 2, 2, sl.bi, sl.bj, r), 4);
-                if (L == 2)
-                    cp4(s4 + kInvL2Ll + 128 * r, tile_row(f.ll, W >> 2, 2, sl.bi, sl.bj, r), 4);
-            }
-        }
-        if (L == 3) {
-            // one int16 per band: the aligned word that holds it (the bases
-            // are 4-byte aligned, so the word stays inside the band)
-            const uint64_t e = sl.bi * (W >> 3) + sl.bj;
-            const uint64_t off = 2ull * (e & ~1ull);
-            const uint32_t bytes = (e & 1ull) ? 4u : 2u;
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                cp4(s4 + kInvL3 + 128 * k, f.band[2][k] + off, bytes);
-            cp4(s4 + kInvL3 + 384, f.ll + off, bytes);
-        }
-    }
-    cp_commit();
-}
-
 // ---------------------------------------------------------------------------
 // one block, forward and inverse (rows from the stage, or straight from
 // global memory with byte accesses when the buffer is not aligned)
@@ -392,8 +339,11 @@ __device__ __forceinline__ void block_rows(const FuseBuf &f, uint64_t bi, uint32
     }
 }
 
-__device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged,
-                                          const uint2 (&v)[8])
+// VEC: the buffer's tiles are aligned to their vector widths (a compile-time
+// choice, so the unaligned byte path is not issued under predicates beside
+// the vector stores)
+template <bool VEC>
+__device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_t bj, const uint2 (&v)[8])
 {
     const uint32_t W = f.W, L = f.F;
     uint32_t x1[8][4]; // row-lifted rows, 4 words each
@@ -404,7 +354,7 @@ __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_
     col_lift<8, 4>(x1, s1, d1);
     // level-1 tiles: LL_1 = s1[][0..1], HL_1 = s1[][2..3], LH_1 = d1[][0..1], HH_1 = d1[][2..3]
     const uint32_t W1 = W >> 1;
-    const bool vec = staged;
+    constexpr bool vec = VEC;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         st_tile(tile_row(f.band[0][0], W1, 4, bi, bj, r), 4, to_i16x2(s1[r][2]), to_i16x2(s1[r][3]), vec);
@@ -451,9 +401,10 @@ __device__ __forceinline__ void fwd_block(const FuseBuf &f, uint64_t bi, uint32_
     st_tile(tile_row(f.ll, W3, 1, bi, bj, 0), 1, ll_final(s3[0][0]), 0, vec);
 }
 
-__device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_t bj, bool staged,
-                                          bool vec, uint32_t s8, uint32_t s4)
+template <bool VEC>
+__device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_t bj)
 {
+    constexpr bool vec = VEC;
     const uint32_t W = f.W, L = f.F;
     const uint32_t W1 = W >> 1, W2 = W >> 2, W3 = W >> 3;
     uint32_t s1[4][4], d1[4][4];
@@ -462,18 +413,10 @@ __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_
         uint32_t s2[2][2], d2[2][2];
         if (L == 3) {
             uint32_t a, b, c, e, z;
-            if (staged) {
-                const uint32_t sh = 16u * (uint32_t)((bi * (uint64_t)W3 + bj) & 1ull);
-                b = (lds4(s4 + kInvL3) >> sh) & 0xffffu;
-                c = (lds4(s4 + kInvL3 + 128) >> sh) & 0xffffu;
-                e = (lds4(s4 + kInvL3 + 256) >> sh) & 0xffffu;
-                a = (lds4(s4 + kInvL3 + 384) >> sh) & 0xffffu;
-            } else {
-                ld_tile(tile_row(f.ll, W3, 1, bi, bj, 0), 1, a, z, vec);
-                ld_tile(tile_row(f.band[2][0], W3, 1, bi, bj, 0), 1, b, z, vec);
-                ld_tile(tile_row(f.band[2][1], W3, 1, bi, bj, 0), 1, c, z, vec);
-                ld_tile(tile_row(f.band[2][2], W3, 1, bi, bj, 0), 1, e, z, vec);
-            }
+            ld_tile(tile_row(f.ll, W3, 1, bi, bj, 0), 1, a, z, vec);
+            ld_tile(tile_row(f.band[2][0], W3, 1, bi, bj, 0), 1, b, z, vec);
+            ld_tile(tile_row(f.band[2][1], W3, 1, bi, bj, 0), 1, c, z, vec);
+            ld_tile(tile_row(f.band[2][2], W3, 1, bi, bj, 0), 1, e, z, vec);
             uint32_t s3[1][1], d3[1][1], x3[2][1];
             s3[0][0] = from_i16x2(a | (b << 16)) + 0x80u;
             d3[0][0] = from_i16x2(c | (e << 16));
@@ -484,10 +427,7 @@ __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 uint32_t w, z;
-                if (staged)
-                    w = lds4(s4 + kInvL2Ll + 128 * r);
-                else
-                    ld_tile(tile_row(f.ll, W2, 2, bi, bj, r), 2, w, z, vec);
+                ld_tile(tile_row(f.ll, W2, 2, bi, bj, r), 2, w, z, vec);
                 s2[r][0] = from_i16x2(w) + 0x00800080u;
             }
         }
@@ -495,12 +435,8 @@ __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_
         for (int r = 0; r < 2; ++r) {
             uint32_t w[3], z;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (staged)
-                    w[k] = lds4(s4 + kInvX + 128 * (3 * r + k));
-                else
-                    ld_tile(tile_row(f.band[1][k], W2, 2, bi, bj, r), 2, w[k], z, vec);
-            }
+            for (int k = 0; k < 3; ++k)
+                ld_tile(tile_row(f.band[1][k], W2, 2, bi, bj, r), 2, w[k], z, vec);
             s2[r][1] = from_i16x2(w[0]);
             d2[r][0] = from_i16x2(w[1]);
             d2[r][1] = from_i16x2(w[2]);
@@ -514,13 +450,7 @@ __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             uint32_t a, b;
-            if (staged) {
-                const uint2 v = lds8(s8 + kInvX + 256 * r);
-                a = v.x;
-                b = v.y;
-            } else {
-                ld_tile(tile_row(f.ll, W1, 4, bi, bj, r), 4, a, b, vec);
-            }
+            ld_tile(tile_row(f.ll, W1, 4, bi, bj, r), 4, a, b, vec);
             s1[r][0] = from_i16x2(a) + 0x00800080u;
             s1[r][1] = from_i16x2(b) + 0x00800080u;
         }
@@ -529,15 +459,8 @@ __device__ __forceinline__ void inv_block(const FuseBuf &f, uint64_t bi, uint32_
     for (int r = 0; r < 4; ++r) {
         uint32_t v[3][2];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if (staged) {
-                const uint2 t = lds8(s8 + 256 * (3 * r + k));
-                v[k][0] = t.x;
-                v[k][1] = t.y;
-            } else {
-                ld_tile(tile_row(f.band[0][k], W1, 4, bi, bj, r), 4, v[k][0], v[k][1], vec);
-            }
-        }
+        for (int k = 0; k < 3; ++k)
+            ld_tile(tile_row(f.band[0][k], W1, 4, bi, bj, r), 4, v[k][0], v[k][1], vec);
         s1[r][2] = from_i16x2(v[0][0]);
         s1[r][3] = from_i16x2(v[0][1]);
         d1[r][0] = from_i16x2(v[1][0]);
@@ -930,13 +853,21 @@ __device__ __forceinline__ void packed_inv(const FuseWork &w, const uint32_t (&k
 #ifndef BLOCK_PACKED_INV_MINB
 #define BLOCK_PACKED_INV_MINB 6
 #endif
+#ifndef BLOCK_FWD_MINB
+#define BLOCK_FWD_MINB 6
+#endif
+#ifndef BLOCK_INV_MINB
+#define BLOCK_INV_MINB 8
+#endif
 template <bool FWD, bool PACKED>
 __host__ __device__ constexpr int block_min_ctas(bool keyed)
 {
-    return (!PACKED || keyed) ? 1 : FWD ? BLOCK_PACKED_FWD_MINB : BLOCK_PACKED_INV_MINB;
+    return keyed ? 1 : PACKED ? (FWD ? BLOCK_PACKED_FWD_MINB : BLOCK_PACKED_INV_MINB)
+                              : (FWD ? BLOCK_FWD_MINB : BLOCK_INV_MINB);
 }
 // the packed forward: five 4-warp blocks an SM (registers capped at 102);
-// the packed inverse: six (capped at 85)
+// the packed inverse: six (capped at 85); the unpacked forward six, its
+// inverse (direct loads, latency-bound) eight (capped at 64)
 template <bool FWD, bool PACKED, bool KEYED>
 __global__ void __launch_bounds__(kThreads, block_min_ctas<FWD, PACKED>(KEYED))
     block_kernel(FuseWork w)
@@ -967,57 +898,55 @@ __global__ void __launch_bounds__(kThreads, block_min_ctas<FWD, PACKED>(KEYED))
         const uint64_t G = (uint64_t)gridDim.x * kWarps;
         for (uint64_t u = (uint64_t)blockIdx.x * kWarps + warp; u < w.total_units; u += G) {
             const Slot sl = slot_of(w, &s_single, u, lane);
-            if (sl.on)
-                inv_block(*sl.b, sl.bi, sl.bj, false, sl.vec, 0, 0);
+            if (sl.on) {
+                if (sl.vec)
+                    inv_block<true>(*sl.b, sl.bi, sl.bj);
+                else
+                    inv_block<false>(*sl.b, sl.bi, sl.bj);
+            }
         }
         return;
     }
-    // the next kernel (the CTR pass after a protect) may start its
-    // data-independent part now; it waits for this grid before reading
+    // the unpacked forward: the rows of each unit staged with cp.async two
+    // units ahead.  The next kernel (the CTR pass after a protect) may start
+    // its data-independent part now; it waits for this grid before reading
     grid_release();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t stage = FWD ? kFwdStage : kInvStage;
+    const uint32_t stage = kFwdStage;
     const uint32_t ring = smem_addr(g_block_smem) + (uint32_t)warp * kDepth * stage;
-    const uint32_t ring8 = ring + 8u * lane, ring4 = ring + 4u * lane;
+    const uint32_t ring8 = ring + 8u * lane;
     const uint64_t G = (uint64_t)gridDim.x * kWarps;
     const uint64_t u0 = (uint64_t)blockIdx.x * kWarps + warp;
     static_assert(kDepth == 3, "the unit loop below is unrolled for three stages");
     // the blocks of the units in flight, in stages 0, 1, 2 (static indices
     // keep them in registers)
     Slot q0 = slot_of(w, &s_single, u0, lane), q1 = slot_of(w, &s_single, u0 + G, lane), q2;
-    if (FWD) {
-        fwd_issue(q0, ring8);
-        fwd_issue(q1, ring8 + stage);
-    } else {
-        inv_issue(q0, ring8, ring4);
-        inv_issue(q1, ring8 + stage, ring4 + stage);
-    }
+    fwd_issue(q0, ring8);
+    fwd_issue(q1, ring8 + stage);
     // unit i computes from stage i % 3 after issuing unit i + 2 into stage
     // (i + 2) % 3, the one unit i - 1 freed
-    auto step = [&](uint64_t i, Slot &cur, Slot &ahead, uint32_t cur_off, uint32_t ahead_off) {
+    auto step = [&](uint64_t i, Slot &cur, Slot &ahead, int cur_k, int ahead_k) {
         ahead = slot_of(w, &s_single, u0 + (i + 2) * G, lane);
-        if (FWD)
-            fwd_issue(ahead, ring8 + ahead_off);
-        else
-            inv_issue(ahead, ring8 + ahead_off, ring4 + ahead_off);
+        fwd_issue(ahead, ring8 + (uint32_t)ahead_k * stage);
         cp_wait<kDepth - 1>();
         if (cur.on) {
-            if (FWD) {
-                uint2 v[8];
-                block_rows(*cur.b, cur.bi, cur.bj, cur.vec, false, ring8 + cur_off, v);
-                fwd_block(*cur.b, cur.bi, cur.bj, cur.vec, v);
-            } else
-                inv_block(*cur.b, cur.bi, cur.bj, cur.vec, cur.vec, ring8 + cur_off, ring4 + cur_off);
+            const FuseBuf &f = *cur.b;
+            uint2 v[8];
+            block_rows(f, cur.bi, cur.bj, cur.vec, false, ring8 + (uint32_t)cur_k * stage, v);
+            if (cur.vec)
+                fwd_block<true>(f, cur.bi, cur.bj, v);
+            else
+                fwd_block<false>(f, cur.bi, cur.bj, v);
         }
     };
     for (uint64_t i = 0; u0 + i * G < w.total_units; i += 3) {
-        step(i, q0, q2, 0, 2 * stage);
+        step(i, q0, q2, 0, 2);
         if (u0 + (i + 1) * G >= w.total_units)
             break;
-        step(i + 1, q1, q0, stage, 0);
+        step(i + 1, q1, q0, 1, 0);
         if (u0 + (i + 2) * G >= w.total_units)
             break;
-        step(i + 2, q2, q1, 2 * stage, stage);
+        step(i + 2, q2, q1, 2, 1);
     }
     cp_wait<0>();
 }
