@@ -36,8 +36,10 @@ __global__ void __launch_bounds__(kCtrThreads, 1) ctr_kernel(CtrWork w)
     const aes::Lut L = aes::make_lut(tab, lane);
     grid_wait(); // the fragment is complete from here on
     const uint64_t nturns = w.frags ? w.nturns : (w.single.nblocks + w.turn_blocks - 1) / w.turn_blocks;
+    // turn c of the launch goes to warp c / grid of CTA c % grid, so a launch
+    // of few turns still spreads them over every CTA (every SM)
     const uint64_t warps = (uint64_t)gridDim.x * (kCtrThreads / 32);
-    for (uint64_t c = (uint64_t)blockIdx.x * (kCtrThreads / 32) + (threadIdx.x >> 5); c < nturns; c += warps) {
+    for (uint64_t c = (uint64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; c < nturns; c += warps) {
         CtrChunk ch;
         uint64_t first;
         if (w.frags) { // the fragment whose turns hold c

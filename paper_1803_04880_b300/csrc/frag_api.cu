@@ -648,8 +648,9 @@ frag_status ctr_launch(DeviceState &d, const frag::AesKeys &keys, const CtrList 
     }
     if (work == 0)
         return FRAG_OK;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(slots, (work + frag::kCtrThreads / 32 - 1) /
-                                                                    (frag::kCtrThreads / 32));
+    // every SM takes a share of the turns (the kernel interleaves them over
+    // its CTAs), even when the turns would fill fewer full CTAs
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(slots, work);
     cudaError_t e = frag::launch_ctr(w, grid, s);
     if (e != cudaSuccess)
         return cuda_fail(e, "cipher launch");
