@@ -249,8 +249,12 @@ ALU_LANES_PER_SM_CLOCK = 64
 # the files that define the dominant kernel (the fused-level kernel; the
 # keyed packed block kernel on c2keyed)
 KERNEL_SOURCES = ("fused_kernels.cu", "swar.cuh", "frag_internal.cuh")
-KEYED_SOURCES = ("block_kernels.cu", "sha2.cuh", "sha2_constants.cuh", "pack_bits.cuh", "swar.cuh",
+BLOCK_SOURCES = ("block_kernels.cu", "sha2.cuh", "sha2_constants.cuh", "pack_bits.cuh", "swar.cuh",
                  "frag_internal.cuh")
+CTR_SOURCES = ("cipher_kernels.cu", "aes_tt.cuh", "frag_internal.cuh")
+# the sources a dominant kernel of each kind is built from
+KIND_SOURCES = {"fused": KERNEL_SOURCES, "fused_low": KERNEL_SOURCES, "blocks": BLOCK_SOURCES,
+                "cipher": CTR_SOURCES, "levels": ("stream_kernels.cu", "swar.cuh", "frag_internal.cuh")}
 
 
 def _kernel_hash(sources=KERNEL_SOURCES):
@@ -261,14 +265,15 @@ def _kernel_hash(sources=KERNEL_SOURCES):
     return h.hexdigest()[:16]
 
 
-def _traffic(workload, kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it is current."""
+def _traffic(workload, direction, kind):
+    """DRAM bytes per launch of the dominant kernel (its kind: fused, blocks,
+    cipher) from the committed ncu summary, if the entry is of that kernel and
+    its sources are unchanged since the capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        e = t[workload][kernel]
-        sources = KEYED_SOURCES if workload == "c2keyed" else KERNEL_SOURCES
-        if e["kernel_hash"] == _kernel_hash(sources):
+        e = t[workload][direction]
+        if e.get("kind") == kind and e["kernel_hash"] == _kernel_hash(KIND_SOURCES[kind]):
             return e["dram_bytes_per_launch"]
     except Exception:
         pass
@@ -574,7 +579,7 @@ def _measure(args, name, dev, s, world, dist, local_rank, K, Wm, e2e_steps, pf_r
         label = names["cipher"] % (dom_dir, "")
     else:
         label = names[dom_kind] % ("true" if dom_dir == "protect" else "false", dom_dir)
-    traffic = _traffic(name, dom_dir)
+    traffic = _traffic(name, dom_dir, dom_kind)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "traffic_source": TRAFFIC_SOURCE if traffic is not None else
