@@ -355,8 +355,7 @@ frag_status frag_batch_launch_times(frag_batch batch, double *ms, uint32_t *laun
  *   - at most FRAG_NOALLOC_MAX_ITEMS items per call; more is FRAG_EINVAL with
  *     a message saying so;
  *   - the first call on a device sets that device up synchronously (it looks
- *     up the array's device address and copies the AES tables into it), so
- *     make that first call before any stream capture;
+ *     up the array's device address and copies the AES tables into it);
  *   - every call shares the one array and the array keeps the last call's
  *     contents; the call clears what must start at zero (the queue head) on
  *     the stream.  Calls whose work overlaps on the GPU (other streams, or no

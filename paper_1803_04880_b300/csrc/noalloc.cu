@@ -66,8 +66,7 @@ uint32_t h_rk[44];
 
 // Once per device, with that device current: look up the scratch's device
 // address, copy the AES tables into it and zero the queue head and error
-// word.  This is synchronous, so the first call on a device must not be made
-// while its stream is being captured.
+// word (synchronously).
 frag_status setup_device(int dev, DeviceSetup **out)
 {
     DeviceSetup &d = g_setup[dev];
