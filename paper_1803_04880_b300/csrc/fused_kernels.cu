@@ -510,11 +510,12 @@ struct FwdState {
 // One iteration (rows 8t-1 .. 8t+6 in stage st).  CHECK: the iteration may
 // meet the top (a level's row 0) or the bottom (a level's last row) of the
 // matrix; no other iteration does, and none stores a row outside it.
-template <bool CHECK, bool PK, bool CIPH>
+template <bool CHECK, bool PK, bool CIPH, int FL>
 __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t, uint32_t st,
                                          bool store, FwdState &S, const Ks &K)
 {
-    const int W = (int)b.W, H = (int)b.H, F = (int)b.F;
+    const int W = (int)b.W, H = (int)b.H;
+    const int F = FL ? FL : (int)b.F;
     const int W1 = W >> 1, H1 = H >> 1, W2 = W >> 2, H2 = H >> 2, W3 = W >> 3, H3 = H >> 3;
     const bool fin = b.ll_final != 0;
     const bool ciph = CIPH && b.cipher != 0; // LL_F is the private fragment, enciphered here
@@ -671,11 +672,11 @@ __device__ __forceinline__ void fwd_iter(const FuseBuf &b, const Lane &ln, int t
 // The row-H halves of the level-1 column lifting, the level-2 H column and
 // the level-3 column are read again only through state the last warm-up
 // iteration rebuilds from the rows it holds, and no band is written.
-template <bool PK>
+template <bool PK, int FL>
 __device__ __forceinline__ void fwd_warm(const FuseBuf &b, const Lane &ln, uint32_t st, bool first, bool last,
                                          FwdState &S)
 {
-    const int F = (int)b.F;
+    const int F = FL ? FL : (int)b.F;
     auto lift = [&](int r, uint32_t(&P)[4]) {
         if (PK) {
             lift8p(*reinterpret_cast<const uint4 *>(ring_ptr(st + 512 * r)), ln.sR, ln.sL, P);
@@ -746,17 +747,18 @@ __device__ __forceinline__ void fwd_warm(const FuseBuf &b, const Lane &ln, uint3
     S.e3 = we;
 }
 
-template <bool PK, bool CIPH>
+template <bool PK, bool CIPH, int FL>
 __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t sy, uint32_t ring_lane,
                                          int lane, uint32_t ks_ring, const uint32_t *tel, const AesKeys &keys)
 {
     const Lane ln = make_lane(b, sx, lane);
     const int t_begin = (int)(sy * b.seg_iters);
     const int t_end = min(t_begin + (int)b.seg_iters, (int)b.iters);
-    const int t_first = max(t_begin - (int)b.F, 0);
+    const int F = FL ? FL : (int)b.F;
+    const int t_first = max(t_begin - F, 0);
     const int t_fast_end = (int)b.iters - 2; // iterations t >= 2 and below this skip the checks
     // LL rows a stored iteration t writes: R t - 1 .. R t + R - 2
-    const int R = 8 >> b.F;
+    const int R = 8 >> F;
     Ks K = {};
     if (CIPH && b.cipher)
         K = ks_init(b, sx, lane, ks_ring, R * t_begin - 1);
@@ -784,11 +786,11 @@ __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t
         const bool store = ln.own && t >= t_begin;
         if (t >= 2 && t < t_fast_end) {
             if (t < t_begin)
-                fwd_warm<PK>(b, ln, st, t == t_first && t_first == t_begin - (int)b.F, t == t_begin - 1, S);
+                fwd_warm<PK, FL>(b, ln, st, t == t_first && t_first == t_begin - F, t == t_begin - 1, S);
             else
-                fwd_iter<false, PK, CIPH>(b, ln, t, st, store, S, K);
+                fwd_iter<false, PK, CIPH, FL>(b, ln, t, st, store, S, K);
         } else {
-            fwd_iter<true, PK, CIPH>(b, ln, t, st, store, S, K);
+            fwd_iter<true, PK, CIPH, FL>(b, ln, t, st, store, S, K);
         }
     }
     cp_wait<0>();
@@ -802,11 +804,12 @@ __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t
 __device__ __forceinline__ uint32_t in16(uint32_t w) { return from_i16x2(w); }
 
 // the coefficient rows iteration t consumes, into its stage
+template <int FL>
 __device__ __forceinline__ void inv_issue(const FuseBuf &b, const Lane &ln, int t, int t_end,
                                           uint32_t ring8, uint32_t ring4)
 {
     if (t < t_end && ln.loads) {
-        const int F = (int)b.F;
+        const int F = FL ? FL : (int)b.F;
         const uint32_t so = (uint32_t)(t % kInvDepth) * kInvStage;
         const uint32_t W1 = b.W >> 1, H1 = b.H >> 1, W2 = b.W >> 2, H2 = b.H >> 2;
         const uint32_t c1 = (uint32_t)ln.c0 >> 1, c2 = (uint32_t)ln.c0 >> 2;
@@ -918,11 +921,12 @@ struct InvState {
     uint32_t x3, d3;
 };
 
-template <bool CHECK, bool PK, bool CIPH>
+template <bool CHECK, bool PK, bool CIPH, int FL>
 __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t, uint32_t s8,
                                          uint32_t s4, bool store, bool whole, InvState &S, const Ks &K)
 {
-    const int W = (int)b.W, H = (int)b.H, F = (int)b.F;
+    const int W = (int)b.W, H = (int)b.H;
+    const int F = FL ? FL : (int)b.F;
     const int W3 = W >> 3, H1 = H >> 1, H2 = H >> 2, H3 = H >> 3;
     const uint32_t llb = b.ll_final ? 0x00800080u : 0u; // LL_L - 128 -> LL_L
     const bool ciph = CIPH && b.cipher != 0; // LL_F is the private fragment, deciphered here
@@ -1043,11 +1047,11 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
 // coefficient row in the iteration, whose d[q-1] is the row before it,
 // loaded in the same iteration (level 3: the d preloaded at the unit's
 // start); level 2 hands down its row-inversed even row, LL_1 row 4t.
-template <bool CIPH>
+template <bool CIPH, int FL>
 __device__ __forceinline__ void inv_warm(const FuseBuf &b, const Lane &ln, int t, uint32_t s8, uint32_t s4,
                                          InvState &S, const Ks &K)
 {
-    const int F = (int)b.F;
+    const int F = FL ? FL : (int)b.F;
     const uint32_t llb = b.ll_final ? 0x00800080u : 0u;
     const bool ciph = CIPH && b.cipher != 0;
     uint32_t y3[2] = {0u, 0u};
@@ -1124,13 +1128,13 @@ __device__ __forceinline__ void inv_warm(const FuseBuf &b, const Lane &ln, int t
     }
 }
 
-template <bool PK, bool CIPH>
+template <bool PK, bool CIPH, int FL>
 __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t sy, uint32_t ring_lane8,
                                          uint32_t ring_lane4, int lane, uint32_t ks_ring, const uint32_t *tel,
                                          const AesKeys &keys)
 {
     const Lane ln = make_lane(b, sx, lane);
-    const int F = (int)b.F;
+    const int F = FL ? FL : (int)b.F;
     const int t_begin = (int)(sy * b.seg_iters);
     const int t_end = min(t_begin + (int)b.seg_iters, (int)b.iters);
     // one iteration rebuilds the column state of every level above the
@@ -1149,7 +1153,7 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
 
 #pragma unroll
     for (int k = 0; k < kInvDepth - 1; ++k)
-        inv_issue(b, ln, t_first + k, t_end, ring_lane8, ring_lane4);
+        inv_issue<FL>(b, ln, t_first + k, t_end, ring_lane8, ring_lane4);
 
     InvState S; // zeros, in each word's form
 #pragma unroll
@@ -1167,7 +1171,7 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
     }
 
     for (int t = t_first; t < t_end; ++t) {
-        inv_issue(b, ln, t + kInvDepth - 1, t_end, ring_lane8, ring_lane4);
+        inv_issue<FL>(b, ln, t + kInvDepth - 1, t_end, ring_lane8, ring_lane4);
         if (CIPH && b.cipher)
             ks_fill(K, (uint32_t)((uint64_t)(R * t + 1) - K.r_first) * K.nb, tel, keys, b.nonce, lane);
         cp_wait<kInvDepth - 1>();
@@ -1176,11 +1180,11 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
         const bool whole = 8 * t < (int)b.full_rows; // rows 8t-7 .. 8t hold only data
         if (t >= 1 && t < t_fast_end) {
             if (t < t_begin)
-                inv_warm<CIPH>(b, ln, t, ring_lane8 + so, ring_lane4 + so, S, K);
+                inv_warm<CIPH, FL>(b, ln, t, ring_lane8 + so, ring_lane4 + so, S, K);
             else
-                inv_iter<false, PK, CIPH>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S, K);
+                inv_iter<false, PK, CIPH, FL>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S, K);
         } else {
-            inv_iter<true, PK, CIPH>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S, K);
+            inv_iter<true, PK, CIPH, FL>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S, K);
         }
     }
     cp_wait<0>();
@@ -1241,10 +1245,23 @@ __global__ void __launch_bounds__(32 * cta_warps<FWD, PK, CIPH>(), 16 / cta_warp
         const FuseBuf *bp = unit_buf(w, u, local);
         const FuseBuf b = *bp;
         const uint32_t sy = (uint32_t)(local / b.strips), sx = (uint32_t)(local % b.strips);
-        if (FWD)
-            fwd_unit<PK, CIPH>(b, sx, sy, ring + (PK ? 16u : 8u) * lane, lane, ks_ring, tel, w.keys);
-        else
-            inv_unit<PK, CIPH>(b, sx, sy, ring + 8u * lane, ring + 4u * lane, lane, ks_ring, tel, w.keys);
+        // the inverse takes the levels a buffer fuses (1..3) as a template
+        // argument, chosen once per unit: as a runtime value its tests and
+        // the shuffles under them cost branches and reconvergence points in
+        // every iteration.  The forward reads them from the descriptor
+        // (FL = 0 reads b.F): specialised, it needed more registers and ran
+        // slower
+        if (FWD) {
+            fwd_unit<PK, CIPH, 0>(b, sx, sy, ring + (PK ? 16u : 8u) * lane, lane, ks_ring, tel, w.keys);
+        } else {
+            const uint32_t r8 = ring + 8u * lane, r4 = ring + 4u * lane;
+            if (b.F == 1)
+                inv_unit<PK, CIPH, 1>(b, sx, sy, r8, r4, lane, ks_ring, tel, w.keys);
+            else if (b.F == 2)
+                inv_unit<PK, CIPH, 2>(b, sx, sy, r8, r4, lane, ks_ring, tel, w.keys);
+            else
+                inv_unit<PK, CIPH, 3>(b, sx, sy, r8, r4, lane, ks_ring, tel, w.keys);
+        }
     }
 }
 
