@@ -1027,7 +1027,7 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
         }
         const uint2 vo = unlift8(xo, ln.sR, ln.sL);
         const uint2 ve = unlift8(xe, ln.sR, ln.sL);
-        if (!CHECK && whole) { // both rows are whole rows of data
+        if (!CHECK) { // both rows are whole rows of data (the caller sends others to CHECK)
             uint8_t *p = b.out + (uint64_t)r * b.W + (uint64_t)ln.c0;
             pst8b(store, p, vo);
             pst8b(store, p + b.W, ve);
@@ -1178,7 +1178,9 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
         const uint32_t so = (uint32_t)(t % kInvDepth) * kInvStage;
         const bool store = ln.own && t >= t_begin;
         const bool whole = 8 * t < (int)b.full_rows; // rows 8t-7 .. 8t hold only data
-        if (t >= 1 && t < t_fast_end) {
+        // the unchecked iteration stores whole rows only; an iteration over
+        // the last, partial row of the data takes the checked one
+        if (t >= 1 && t < t_fast_end && (PK || whole || t < t_begin)) {
             if (t < t_begin)
                 inv_warm<CIPH, FL>(b, ln, t, ring_lane8 + so, ring_lane4 + so, S, K);
             else
