@@ -249,27 +249,47 @@ struct Slot {
 // single: the launch's lone descriptor, copied to shared memory by the block
 // (a pointer to the kernel parameter itself would make the compiler copy the
 // whole parameter block into local memory)
+// A warp's units only grow, so it keeps the buffer its last unit fell in
+// and that buffer's unit range: the next unit is usually found with one
+// comparison instead of a binary search of dependent loads.
+struct BufCursor {
+    uint32_t lo = 0;
+    uint64_t u_lo = 1, u_hi = 0; // empty: the first lookup searches
+};
+
+__device__ __forceinline__ uint32_t find_buf(const FuseWork &w, uint64_t u, BufCursor &c)
+{
+    if (u < c.u_lo || u >= c.u_hi) {
+        uint32_t lo = 0, hi = w.nbufs;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(&w.bufs[mid].unit0) <= u)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        c.lo = lo;
+        c.u_lo = __ldg(&w.bufs[lo].unit0);
+        c.u_hi = lo + 1 < w.nbufs ? __ldg(&w.bufs[lo + 1].unit0) : w.total_units;
+    }
+    return c.lo;
+}
+
 __device__ __forceinline__ const FuseBuf *unit_buf(const FuseWork &w, const FuseBuf *single, uint64_t u,
-                                                  uint64_t &local)
+                                                  uint64_t &local, BufCursor &c)
 {
     if (w.nbufs == 1) {
         local = u;
         return single;
     }
-    uint32_t lo = 0, hi = w.nbufs;
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(&w.bufs[mid].unit0) <= u)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    local = u - __ldg(&w.bufs[lo].unit0);
+    const uint32_t lo = find_buf(w, u, c);
+    local = u - c.u_lo;
     return &w.bufs[lo];
 }
 
 // one unit = one block row of 32 blocks (a warp), lane = block column
-__device__ __forceinline__ Slot slot_of(const FuseWork &w, const FuseBuf *single, uint64_t u, int lane)
+__device__ __forceinline__ Slot slot_of(const FuseWork &w, const FuseBuf *single, uint64_t u, int lane,
+                                       BufCursor &c)
 {
     Slot sl;
     sl.on = false;
@@ -280,7 +300,7 @@ __device__ __forceinline__ Slot slot_of(const FuseWork &w, const FuseBuf *single
     if (u >= w.total_units)
         return sl;
     uint64_t local;
-    sl.b = unit_buf(w, single, u, local);
+    sl.b = unit_buf(w, single, u, local, c);
     const uint32_t strips = sl.b->strips;
     if (local < (1ull << 32)) { // 32-bit division: a unit is one warp's 32 blocks, so it counts
         const uint32_t l32 = (uint32_t)local, q = l32 / strips;
@@ -514,7 +534,7 @@ __device__ __forceinline__ uint64_t ldg64(const void *p)
 }
 
 template <bool FWD>
-__device__ __forceinline__ PkUnit pk_unit(const FuseWork &w, uint64_t u, int lane)
+__device__ __forceinline__ PkUnit pk_unit(const FuseWork &w, uint64_t u, int lane, BufCursor &c)
 {
     PkUnit p;
     p.nvalid = 0;
@@ -528,16 +548,8 @@ __device__ __forceinline__ PkUnit pk_unit(const FuseWork &w, uint64_t u, int lan
     const FuseBuf *bp = nullptr; // null: the launch's lone buffer (w.single)
     uint64_t local = u;
     if (w.nbufs != 1) {
-        uint32_t lo = 0, hi = w.nbufs;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (__ldg(&w.bufs[mid].unit0) <= u)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        bp = w.bufs + lo;
-        local = u - __ldg(&bp->unit0);
+        bp = w.bufs + find_buf(w, u, c);
+        local = u - c.u_lo;
     }
     const uint8_t *src;
     uint8_t *k0, *k1, *k2;
@@ -724,7 +736,8 @@ __device__ __forceinline__ void packed_fwd(const FuseWork &w, const uint32_t (&k
         }
         __syncwarp(); // every lane is done with the staging area before it is refilled
     };
-    PkUnit cur = pk_unit<true>(w, u, lane);
+    BufCursor bc;
+    PkUnit cur = pk_unit<true>(w, u, lane, bc);
     uint2 rows[8];
     pk_rows(cur, rows);
     for (; u < w.total_units; u += G) {
@@ -732,7 +745,7 @@ __device__ __forceinline__ void packed_fwd(const FuseWork &w, const uint32_t (&k
 #pragma unroll
         for (int r = 0; r < 8; ++r)
             v[r] = rows[r];
-        const PkUnit nx = pk_unit<true>(w, u + G, lane);
+        const PkUnit nx = pk_unit<true>(w, u + G, lane, bc);
         pk_rows(nx, rows);
         unit(cur, v);
         cur = nx;
@@ -825,13 +838,14 @@ __device__ __forceinline__ void packed_inv(const FuseWork &w, const uint32_t (&k
             pk_inv_block<KEYED>(cur, st, rb, key, lane);
         __syncwarp(); // every lane is done with this area before it is refilled
     };
-    PkUnit cur = pk_unit<false>(w, u, lane);
+    BufCursor bc;
+    PkUnit cur = pk_unit<false>(w, u, lane, bc);
     bool cur_full = pkb::full_aligned(cur.nvalid, cur.pa, cur.pb, cur.pc);
     if (cur_full)
         pkb::prefetch_full(stg_in[warp][0], cur.pa, cur.pb, cur.pc, lane);
     cp_commit();
     for (uint32_t i = 0; u < w.total_units; u += G, ++i) {
-        const PkUnit nx = pk_unit<false>(w, u + G, lane);
+        const PkUnit nx = pk_unit<false>(w, u + G, lane, bc);
         const bool nx_full = pkb::full_aligned(nx.nvalid, nx.pa, nx.pb, nx.pc);
         if (nx_full)
             pkb::prefetch_full(stg_in[warp][(i + 1) & 1], nx.pa, nx.pb, nx.pc, lane);
@@ -896,8 +910,9 @@ __global__ void __launch_bounds__(kThreads, block_min_ctas<FWD, PACKED>(KEYED))
         grid_release();
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const uint64_t G = (uint64_t)gridDim.x * kWarps;
+        BufCursor bc;
         for (uint64_t u = (uint64_t)blockIdx.x * kWarps + warp; u < w.total_units; u += G) {
-            const Slot sl = slot_of(w, &s_single, u, lane);
+            const Slot sl = slot_of(w, &s_single, u, lane, bc);
             if (sl.on) {
                 if (sl.vec)
                     inv_block<true>(*sl.b, sl.bi, sl.bj);
@@ -920,13 +935,14 @@ __global__ void __launch_bounds__(kThreads, block_min_ctas<FWD, PACKED>(KEYED))
     static_assert(kDepth == 3, "the unit loop below is unrolled for three stages");
     // the blocks of the units in flight, in stages 0, 1, 2 (static indices
     // keep them in registers)
-    Slot q0 = slot_of(w, &s_single, u0, lane), q1 = slot_of(w, &s_single, u0 + G, lane), q2;
+    BufCursor bc;
+    Slot q0 = slot_of(w, &s_single, u0, lane, bc), q1 = slot_of(w, &s_single, u0 + G, lane, bc), q2;
     fwd_issue(q0, ring8);
     fwd_issue(q1, ring8 + stage);
     // unit i computes from stage i % 3 after issuing unit i + 2 into stage
     // (i + 2) % 3, the one unit i - 1 freed
     auto step = [&](uint64_t i, Slot &cur, Slot &ahead, int cur_k, int ahead_k) {
-        ahead = slot_of(w, &s_single, u0 + (i + 2) * G, lane);
+        ahead = slot_of(w, &s_single, u0 + (i + 2) * G, lane, bc);
         fwd_issue(ahead, ring8 + (uint32_t)ahead_k * stage);
         cp_wait<kDepth - 1>();
         if (cur.on) {
