@@ -745,7 +745,8 @@ __device__ __forceinline__ void packed_fwd(const FuseWork &w, const uint32_t (&k
 #pragma unroll
         for (int r = 0; r < 8; ++r)
             v[r] = rows[r];
-        const PkUnit nx = pk_unit<true>(w, u + G, lane, bc);
+        BufCursor fresh; // keyed launches keep no cursor across units (registers)
+        const PkUnit nx = pk_unit<true>(w, u + G, lane, KEYED ? fresh : bc);
         pk_rows(nx, rows);
         unit(cur, v);
         cur = nx;
@@ -845,7 +846,8 @@ __device__ __forceinline__ void packed_inv(const FuseWork &w, const uint32_t (&k
         pkb::prefetch_full(stg_in[warp][0], cur.pa, cur.pb, cur.pc, lane);
     cp_commit();
     for (uint32_t i = 0; u < w.total_units; u += G, ++i) {
-        const PkUnit nx = pk_unit<false>(w, u + G, lane, bc);
+        BufCursor fresh; // keyed launches keep no cursor across units (registers)
+        const PkUnit nx = pk_unit<false>(w, u + G, lane, KEYED ? fresh : bc);
         const bool nx_full = pkb::full_aligned(nx.nvalid, nx.pa, nx.pb, nx.pc);
         if (nx_full)
             pkb::prefetch_full(stg_in[warp][(i + 1) & 1], nx.pa, nx.pb, nx.pc, lane);
