@@ -106,3 +106,35 @@ def test_batch_mixes_block_and_whole_plans(fr, key):
         assert np.array_equal(rit[5].cpu().numpy(), data)
     b = fr.Batch(items, True)
     assert b.launches == 3  # fused, block, CTR
+
+
+def test_block_batch_with_more_units_than_warps(fr, key):
+    """Block-mode buffers at 1..3 levels whose units (32 blocks each)
+    outnumber the launch's warps, so warps take several units across buffer
+    boundaries (the per-warp buffer cursor advances and is reused), one of
+    them at an odd address (the byte-wise path): every fragment and every
+    recovered byte as the oracle's."""
+    specs = [(4096, 1024, 2, 0), (2048, 2048, 3, 0), (1024, 512, 1, 1), (4096, 512, 2, 0)]
+    items, ritems, refs = [], [], []
+    for i, (W, rows, L, off) in enumerate(specs):
+        n = W * rows - 7 * i
+        plan = fr.Plan(W, L)
+        plan.set_block(8)
+        data = wl.random_bytes(n, seed=400 + i)
+        refs.append((data, oracle.protect(data, W, L, KEY, 50 + i, block=8)))
+        _, pb, ub = plan.sizes(n)
+        d = torch.zeros(n + off, dtype=torch.uint8, device="cuda")
+        d[off:] = torch.from_numpy(data).cuda()
+        p = torch.empty(pb, dtype=torch.uint8, device="cuda")
+        u = torch.empty(ub, dtype=torch.uint8, device="cuda")
+        o = torch.empty(n, dtype=torch.uint8, device="cuda")
+        items.append((plan, 50 + i, n, d[off:], p, u))
+        ritems.append((plan, 50 + i, n, p, u, o))
+    assert sum(W // 8 // 32 * rows // 8 for W, rows, _, _ in specs) > 148 * 8 * 4
+    fr.protect_batch(items, key)
+    fr.recover_batch(ritems, key)
+    fr.sync_status()
+    for (data, (pr, ur)), it, rit in zip(refs, items, ritems):
+        assert np.array_equal(it[4].cpu().numpy(), pr)
+        assert np.array_equal(it[5].cpu().numpy(), ur)
+        assert np.array_equal(rit[5].cpu().numpy(), data)

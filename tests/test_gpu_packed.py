@@ -123,3 +123,35 @@ def test_batch_mixes_packed_block_and_whole_matrix(fr, key):
         assert np.array_equal(p.cpu().numpy(), p_ref)
         assert np.array_equal(u.cpu().numpy(), u_ref)
         assert np.array_equal(o.cpu().numpy(), data)
+
+
+def test_batch_with_more_units_than_warps(fr, key):
+    """Packed buffers whose units (32 blocks each) outnumber the launch's
+    warps, so warps take several units across buffer boundaries (the loops'
+    per-warp buffer cursor advances and is reused): every fragment and every
+    recovered byte as the oracle's."""
+    specs = [(4096, 4096 * 1024), (2048, 2048 * 2048 - 5), (1024, 1024 * 512 + 3), (4096, 4096 * 512)]
+    ents, rents, refs = [], [], []
+    for i, (W, n) in enumerate(specs):
+        data = wl.random_bytes(n, seed=300 + i)
+        plan = fr.Plan(W, 2)
+        plan.set_block(8)
+        plan.set_packed(True)
+        ref = oracle.protect_packed(data, W, KEY, 40 + i)
+        _, pb, ub = plan.sizes(n)
+        d = torch.from_numpy(data).cuda()
+        p = torch.empty(pb, dtype=torch.uint8, device="cuda")
+        u = torch.empty(ub, dtype=torch.uint8, device="cuda")
+        o = torch.empty(n, dtype=torch.uint8, device="cuda")
+        ents.append((plan, 40 + i, n, d, p, u))
+        rents.append((plan, 40 + i, n, p, u, o))
+        refs.append((data, ref, p, u, o))
+    units = sum((W // 8 + 31) // 32 * ((n + W - 1) // W + 7) // 8 for W, n in specs)
+    assert units > 148 * 6 * 4  # more than the warps of any packed launch
+    fr.protect_batch(ents, key)
+    fr.recover_batch(rents, key)
+    fr.sync_status()
+    for data, (p_ref, u_ref), p, u, o in refs:
+        assert np.array_equal(p.cpu().numpy(), p_ref)
+        assert np.array_equal(u.cpu().numpy(), u_ref)
+        assert np.array_equal(o.cpu().numpy(), data)
