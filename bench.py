@@ -858,6 +858,7 @@ def run_c4(args, rank, world, local_rank):
     torch.cuda.synchronize()
     fr.sync_status(s)
     per_file_ms = e0.elapsed_time(e1)
+    noalloc = _noalloc_leg(fr, pentries, privs, pubs, key, wl.KEY, s)
     launches, held = bp.info()
     if rank == 0:
         value = world * n_total / (batched_ms / 1e3) / 1e9
@@ -877,9 +878,59 @@ def run_c4(args, rank, world, local_rank):
                 "per_file": {"ms_per_step": round(per_file_ms, 3),
                              "value": round(n_total / (per_file_ms / 1e3) / 1e9, 2),
                              "batched_over_per_file": round(per_file_ms / batched_ms, 3)},
+                "noalloc": noalloc,
                 "gpu_launches": K * (launches + br.info()[0]),
                 "checked_sample_items": len(sample), "batch_device_bytes": held}
         print(json.dumps(line), flush=True)
+
+
+def _noalloc_leg(fr, pentries, privs, pubs, key, raw_key, s, reps=5):
+    """Protect of the batch's first FRAG_NOALLOC_MAX_ITEMS buffers through
+    the allocation-free call (the shared-memory tile kernel) against a batch
+    object's protect of the same buffers (the fused path), both event-timed
+    on the launch stream; the call's fragments must equal the batch's, which
+    privs / pubs hold after the batched round trips."""
+    import torch
+
+    sub = pentries[:1024]
+    nbytes = sum(e[2] for e in sub)
+    p2 = [torch.empty_like(privs[i]) for i in range(len(sub))]
+    u2 = [torch.empty_like(pubs[i]) for i in range(len(sub))]
+    arr = (fr.frag_item * len(sub))()
+    for i, (plan, nonce, n, d, _, _) in enumerate(sub):
+        arr[i] = fr.frag_item(plan.handle, nonce, n, d.data_ptr(), p2[i].data_ptr(), u2[i].data_ptr())
+
+    def call():
+        st = fr.lib().frag_protect_batch_noalloc(arr, len(sub), bytes(raw_key), s.cuda_stream)
+        assert st == fr.FRAG_OK, fr.last_error()
+
+    call()
+    torch.cuda.synchronize()
+    assert fr.lib().frag_noalloc_sync_status(s.cuda_stream) == fr.FRAG_OK, fr.last_error()
+    same = all(torch.equal(p2[i], privs[i]) and torch.equal(u2[i], pubs[i]) for i in range(len(sub)))
+    assert same, "allocation-free fragments differ from the batch's"
+    bsub = fr.Batch(sub, protect=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = {}
+    for name, fn in (("noalloc", call), ("batch", lambda: bsub.run(key, s))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(reps):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / reps
+    assert fr.lib().frag_noalloc_sync_status(s.cuda_stream) == fr.FRAG_OK, fr.last_error()
+    fr.sync_status(s)
+    del p2, u2
+    return {"what": "protect only, the first %d buffers (%.2f GB), allocation-free call "
+                    "(shared-memory tile kernel) vs a batch object (fused path); fragments equal"
+                    % (len(sub), nbytes / 1e9),
+            "ms": round(times["noalloc"], 3), "value": round(nbytes / (times["noalloc"] / 1e3) / 1e9, 2),
+            "batch_ms": round(times["batch"], 3),
+            "batch_value": round(nbytes / (times["batch"] / 1e3) / 1e9, 2)}
 
 
 # -- C5: served stream of requests -------------------------------------------------

@@ -344,13 +344,20 @@ frag_status frag_batch_launch_times(frag_batch batch, double *ms, uint32_t *laun
  * a plug-in whose host process owns every byte of device memory through its
  * own pool, or a latency-critical path that cannot accept the implicit
  * synchronisation of a driver allocation.  This call gives fragments
- * byte-identical to frag_protect_batch (it runs the tile kernel that keeps
- * every level of a tile in shared memory, so it needs no level scratch; up to
- * 5 levels), but keeps its work
- * queue, job descriptors, round keys, AES tables and error word in one static
- * device array of about 110 KiB that every GPU loading this library holds
- * until the process exits; it calls no cudaMalloc, cudaFree or other
+ * byte-identical to frag_protect_batch.  Items whose levels all fit the first
+ * fused pass (1..3 levels under FRAG_PATH_AUTO's width and alignment
+ * conditions, whatever the plan's path) go through the same two launches as
+ * that call (the fused pass, then the CTR pass over their private
+ * fragments); the others (4 or 5 levels, or buffers that pass does not take)
+ * through the tile kernel that keeps every level of a tile in shared memory,
+ * so that no item needs level scratch.  Up to 5 levels.  The call keeps its
+ * descriptors, work queue, round keys, AES tables and error word in one
+ * static device array of about 375 KiB that every GPU loading this library
+ * holds until the process exits; it calls no cudaMalloc, cudaFree or other
  * allocating routine, and takes the raw 16-byte key instead of a frag_key.
+ * The fused launches take the library's adaptive units and the full device
+ * (frag_plan_set_schedule is not used); the tile kernel takes the tile size
+ * of frag_plan_set_tiling for 4 and 5 levels.
  * Limits and rules:
  *   - at most FRAG_NOALLOC_MAX_ITEMS items per call; more is FRAG_EINVAL with
  *     a message saying so;

@@ -1885,6 +1885,47 @@ frag_status plan_job(frag_plan plan, uint64_t nonce, uint64_t n, Job &j)
 }
 frag_status report(frag_status st, const char *msg) { return fail(st, "%s", msg); }
 frag_status report_cuda(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+
+// A protect item of the allocation-free call whose levels all run in the
+// first fused pass (1..3 levels, under FRAG_PATH_AUTO's width and alignment
+// conditions, whatever the plan's path): its fused descriptor (schedule
+// fields 0) and the CTR chunk of its private fragment, the ones a batch
+// builds for it; *cells = H * W, the batch's ordering key.  False: the
+// item is not one (the tile kernel takes it).
+bool noalloc_fused_item(frag_plan plan, const frag_item &it, FuseBuf &f, CtrChunk &c,
+                        uint64_t *cells)
+{
+    if (plan->block || plan->packed || plan->levels > kFuseMaxLevels || it.nbytes == 0)
+        return false;
+    const uint64_t H = rows_for(it.nbytes, plan->width, plan->levels);
+    if (H > 0xFFFFFFFFull)
+        return false;
+    Buf b;
+    std::memset(&b, 0, sizeof(b));
+    b.W = plan->width;
+    b.L = plan->levels;
+    b.H = (uint32_t)H;
+    b.n = it.nbytes;
+    b.nonce = it.nonce;
+    b.in = (const uint8_t *)it.d_in;
+    b.priv = (uint8_t *)it.d_private;
+    b.pub = (uint8_t *)it.d_public;
+    fused_split(true, b, FRAG_PATH_AUTO);
+    if (b.F1 != b.L || b.F2 != 0 || !ctr_pass(b))
+        return false;
+    f = fuse_buf(true, b, 1);
+    c = ctr_fragment(true, b);
+    *cells = H * (uint64_t)b.W;
+    return true;
+}
+
+// a batch's schedule of one fused protect launch over f[0..n) for `slots`
+// resident warps (plan_rows: the level-0 rows of a unit, 0 = adaptive);
+// returns the launch's units
+uint64_t noalloc_fuse_schedule(FuseBuf *f, size_t n, uint64_t slots, uint32_t plan_rows)
+{
+    return fuse_schedule(f, n, std::max<uint64_t>(1, slots), plan_rows, true);
+}
 } // namespace frag
 
 // ===========================================================================

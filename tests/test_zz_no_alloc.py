@@ -105,3 +105,54 @@ def test_rejects_more_than_five_levels(fr):
     st = _noalloc(fr, [(plan, 0, t.numel(), t, p, u)])
     assert st == fr.FRAG_EUNSUPPORTED
     assert "at most 5 levels" in fr.last_error()
+
+
+# (bytes, width, levels, nonce, input offset, private-fragment offset): the
+# fused pass takes the first three (1..3 levels, aligned, width a multiple of
+# 8); the tile kernel the rest -- an input one byte off alignment, a width of
+# 4, a private fragment 4 bytes off 8-byte alignment at one level, 4 and 5
+# levels
+ROUTES = [(50_000, 64, 1, 910, 0, 0), (70_001, 128, 2, 911, 0, 0), (90_000, 256, 3, 912, 0, 0),
+          (50_000, 64, 2, 913, 1, 0), (6_000, 4, 2, 914, 0, 0), (30_000, 64, 1, 915, 0, 4),
+          (100_000, 256, 4, 916, 0, 0), (120_000, 512, 5, 917, 0, 0)]
+
+
+def _route_entries(fr, rows):
+    out = []
+    for (n, W, L, nonce, ioff, poff) in rows:
+        plan = fr.Plan(W, L)
+        _, pb, ub = plan.sizes(n)
+        base = torch.from_numpy(wl.random_bytes(n + ioff, seed=nonce)).cuda()
+        t = base[ioff:]
+        ref = (plan, nonce, n, t, torch.full((pb,), 0x5A, dtype=torch.uint8, device="cuda"),
+               torch.full((ub,), 0x5A, dtype=torch.uint8, device="cuda"))
+        pg = torch.full((pb + poff,), 0x5A, dtype=torch.uint8, device="cuda")[poff:]
+        got = (plan, nonce, n, t, pg, torch.full((ub,), 0x5A, dtype=torch.uint8, device="cuda"))
+        out.append((ref, got))
+    return out
+
+
+def test_fused_and_tile_routes_alike(fr):
+    """The call sends items whose levels all fit the fused pass through it
+    and the CTR pass, and the rest through the tile kernel; in one call,
+    each route alone and a call of one fused item, every fragment equals
+    frag_protect_batch's (which the parity tests hold to the oracle)."""
+    key = fr.Key(wl.KEY)
+    entries = _route_entries(fr, ROUTES)
+    fr.protect_batch([r for r, _ in entries], key)
+    torch.cuda.synchronize()
+    fr.sync_status()
+    for name, idx in (("mixed", range(8)), ("fused only", range(3)), ("tile only", range(3, 8)),
+                      ("one fused item", [1])):
+        got = [entries[i][1] for i in idx]
+        for (_, _, _, _, p, u) in got:
+            p.fill_(0x5A)
+            u.fill_(0x5A)
+        assert _noalloc(fr, got) == fr.FRAG_OK, fr.last_error()
+        assert fr.lib().frag_noalloc_sync_status(
+            torch.cuda.current_stream().cuda_stream) == fr.FRAG_OK, fr.last_error()
+        for i in idx:
+            (plan, _, n, _, p0, u0), (_, _, _, _, p1, u1) = entries[i]
+            what = "(n=%d, W=%d, L=%d, row %d) in the %s call" % (n, plan.width, plan.levels, i, name)
+            assert torch.equal(p0, p1), "private fragment differs " + what
+            assert torch.equal(u0, u1), "public fragment differs " + what
