@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define FRAG_ABI_VERSION 1
+#define FRAG_ABI_VERSION 2
 
 typedef enum {
     FRAG_OK = 0,
@@ -92,15 +92,6 @@ frag_status frag_plan_destroy(frag_plan plan);
  * FRAG_EINVAL if H would not fit in 32 bits. */
 frag_status frag_plan_sizes(frag_plan plan, uint64_t nbytes, uint32_t *height,
                             uint64_t *private_bytes, uint64_t *public_bytes);
-
-/* Launch tuning of the shared-memory tile kernel that frag_protect_batch_noalloc
- * runs (0 keeps the default).  tile_w / tile_h: owned tile size in pixels,
- * multiples of 16 and of 2^L, at most 256; ctas_per_sm: resident CTAs per SM
- * of the persistent grid (0 = as many as fit). */
-frag_status frag_plan_set_tiling(frag_plan plan, uint32_t tile_w, uint32_t tile_h,
-                                 uint32_t ctas_per_sm);
-frag_status frag_plan_get_tiling(frag_plan plan, uint32_t *tile_w, uint32_t *tile_h,
-                                 uint32_t *ctas_per_sm);
 
 /* Schedule of the streaming kernel that every other protect / recover call
  * runs (the autotuner in the Python package sets it; 0 keeps the library's
@@ -355,9 +346,8 @@ frag_status frag_batch_launch_times(frag_batch batch, double *ms, uint32_t *laun
  * static device array of about 375 KiB that every GPU loading this library
  * holds until the process exits; it calls no cudaMalloc, cudaFree or other
  * allocating routine, and takes the raw 16-byte key instead of a frag_key.
- * The fused launches take the library's adaptive units and the full device
- * (frag_plan_set_schedule is not used); the tile kernel takes the tile size
- * of frag_plan_set_tiling for 4 and 5 levels.
+ * The launches take the library's adaptive units and the full device
+ * (frag_plan_set_schedule is not used).
  * Limits and rules:
  *   - at most FRAG_NOALLOC_MAX_ITEMS items per call; more is FRAG_EINVAL with
  *     a message saying so;

@@ -23,8 +23,7 @@ STATUS_NAMES = {0: "FRAG_OK", 1: "FRAG_EINVAL", 2: "FRAG_EUNSUPPORTED", 3: "FRAG
 # every symbol include/frag.h declares
 EXPORTS = [
     "frag_abi_version", "frag_plan_create", "frag_plan_destroy", "frag_plan_sizes",
-    "frag_plan_set_tiling", "frag_plan_get_tiling", "frag_plan_set_schedule",
-    "frag_plan_get_schedule", "frag_plan_set_path", "frag_plan_get_path",
+    "frag_plan_set_schedule", "frag_plan_get_schedule", "frag_plan_set_path", "frag_plan_get_path",
     "frag_plan_set_block", "frag_plan_get_block", "frag_plan_set_packed", "frag_plan_get_packed",
     "frag_plan_fragment_sizes", "frag_plan_set_protect_public", "frag_plan_get_protect_public",
     "frag_key_create", "frag_key_destroy",
@@ -90,9 +89,6 @@ def lib():
         "frag_plan_destroy": ([vp], ctypes.c_int),
         "frag_plan_sizes": ([vp, u64, ctypes.POINTER(u32), ctypes.POINTER(u64),
                              ctypes.POINTER(u64)], ctypes.c_int),
-        "frag_plan_set_tiling": ([vp, u32, u32, u32], ctypes.c_int),
-        "frag_plan_get_tiling": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u32),
-                                  ctypes.POINTER(u32)], ctypes.c_int),
         "frag_plan_set_schedule": ([vp, u32, u32], ctypes.c_int),
         "frag_plan_get_schedule": ([vp, ctypes.POINTER(u32), ctypes.POINTER(u32)], ctypes.c_int),
         "frag_plan_set_path": ([vp, ctypes.c_int], ctypes.c_int),
@@ -191,9 +187,6 @@ class Plan:
                                     ctypes.byref(ub)))
         return H.value, pb.value, ub.value
 
-    def set_tiling(self, tile_w: int = 0, tile_h: int = 0, ctas_per_sm: int = 0) -> None:
-        check(lib().frag_plan_set_tiling(self._h, tile_w, tile_h, ctas_per_sm))
-
     def set_schedule(self, seg_rows: int = 0, ctas: int = 0) -> None:
         """Rows per work unit and grid cap of the streaming kernel (0 = auto)."""
         check(lib().frag_plan_set_schedule(self._h, seg_rows, ctas))
@@ -253,12 +246,6 @@ class Plan:
         v = (ctypes.c_uint64 * 3)()
         check(lib().frag_plan_fragment_sizes(self._h, nbytes, v))
         return v[0], v[1], v[2]
-
-    def tiling(self) -> Tuple[int, int, int]:
-        a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
-        check(lib().frag_plan_get_tiling(self._h, ctypes.byref(a), ctypes.byref(b),
-                                         ctypes.byref(c)))
-        return a.value, b.value, c.value
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

@@ -20,14 +20,10 @@
 #include <vector>
 
 using frag::Job;
-using frag::Work;
 
 struct frag_plan_s {
     uint32_t width;
     uint32_t levels;
-    uint32_t tile_w;      // tile path (allocation-free call)
-    uint32_t tile_h;
-    uint32_t ctas_per_sm;
     uint32_t seg_rows;    // streaming path: level-0 rows per unit (0: adaptive)
     uint32_t max_ctas;    // streaming path: grid cap (0: all resident CTAs)
     uint32_t path;        // frag_path: which kernels run the levels
@@ -46,8 +42,6 @@ struct frag_key_s {
 namespace {
 
 constexpr uint32_t kMaxLevels = 8;
-constexpr uint32_t kMaxTileLevels = 5; // the tile kernel: one tile window in shared memory
-constexpr uint32_t kDefaultTile = 64;
 
 thread_local char g_err[512] = "";
 
@@ -222,33 +216,6 @@ frag_status key_on_device(frag_key key, int dev, const uint32_t **out)
     return FRAG_OK;
 }
 
-// occupancy-sized persistent grid for a launch that needs `smem` bytes
-frag_status launch_shape(DeviceState &d, bool fwd, size_t smem, uint32_t ctas_per_sm,
-                         uint64_t total_tiles, uint32_t *grid)
-{
-    int occ = 0;
-    {
-        std::lock_guard<std::mutex> lock(g_mu);
-        auto it = d.occ[fwd].find(smem);
-        if (it != d.occ[fwd].end())
-            occ = it->second;
-    }
-    if (occ == 0) {
-        cudaError_t e = frag::tile_occupancy(fwd, smem, &occ);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "occupancy query");
-        if (occ <= 0)
-            return fail(FRAG_EUNSUPPORTED, "tile window of %zu bytes does not fit on an SM", smem);
-        std::lock_guard<std::mutex> lock(g_mu);
-        d.occ[fwd][smem] = occ;
-    }
-    if (ctas_per_sm != 0 && (int)ctas_per_sm < occ)
-        occ = (int)ctas_per_sm;
-    const uint64_t slots = (uint64_t)d.sms * (uint64_t)occ;
-    *grid = (uint32_t)std::min<uint64_t>(slots, total_tiles);
-    return FRAG_OK;
-}
-
 frag_status check_plan(frag_plan plan)
 {
     if (plan == nullptr)
@@ -264,13 +231,14 @@ uint64_t rows_for(uint64_t n, uint32_t W, uint32_t L, uint32_t block = 0)
     return (rows + step - 1) / step * step;
 }
 
+// a tile-kernel job for the allocation-free call (its buffers set by the caller)
 frag_status fill_job(frag_plan plan, uint64_t nonce, uint64_t n, Job &j)
 {
     if (plan->block)
         return fail(FRAG_EUNSUPPORTED, "the allocation-free call does not take block plans");
-    if (plan->levels > kMaxTileLevels)
+    if (plan->levels > frag::kTileMaxLevels)
         return fail(FRAG_EUNSUPPORTED, "the allocation-free call takes at most %u levels, got %u",
-                    kMaxTileLevels, plan->levels);
+                    frag::kTileMaxLevels, plan->levels);
     const uint64_t H = rows_for(n, plan->width, plan->levels);
     if (H > 0xFFFFFFFFull || H * (uint64_t)plan->width / plan->width != H)
         return fail(FRAG_EINVAL, "buffer of %llu bytes is too tall for width %u",
@@ -281,28 +249,10 @@ frag_status fill_job(frag_plan plan, uint64_t nonce, uint64_t n, Job &j)
     j.W = plan->width;
     j.H = (uint32_t)H;
     j.L = plan->levels;
-    if (plan->levels <= frag::kFastMaxLevels) {
-        j.path = 1;
-        j.tile_w = frag::kFastTile;
-        j.tile_h = frag::kFastTile;
-    } else {
-        j.path = 0;
-        j.tile_w = plan->tile_w;
-        j.tile_h = plan->tile_h;
-    }
-    j.tiles_x = (j.W + j.tile_w - 1) / j.tile_w;
-    j.tiles_y = (j.H + j.tile_h - 1) / j.tile_h;
+    j.tile = frag::tile_side(j.L);
+    j.tiles_x = (j.W + j.tile - 1) / j.tile;
+    j.tiles_y = (j.H + j.tile - 1) / j.tile;
     return FRAG_OK;
-}
-
-size_t job_smem(const Job &j, bool fwd) { return frag::job_smem_bytes(j, fwd); }
-
-void base_work(Work &w, DeviceState &d, const uint32_t *rk)
-{
-    std::memset(&w, 0, sizeof(w));
-    w.aes_tables = d.tables;
-    w.round_keys = rk;
-    w.err = d.err;
 }
 
 // ---------------------------------------------------------------------------
@@ -1959,9 +1909,6 @@ frag_status frag_plan_create(frag_plan *out, uint32_t width, uint32_t levels, fr
         return fail(FRAG_ENOMEM, "out of host memory");
     p->width = width;
     p->levels = levels;
-    p->tile_w = std::max(kDefaultTile, 1u << levels);
-    p->tile_h = std::max(kDefaultTile, 1u << levels);
-    p->ctas_per_sm = 0;
     *out = p;
     return FRAG_OK;
 }
@@ -2020,44 +1967,6 @@ frag_status frag_plan_fragment_sizes(frag_plan plan, uint64_t nbytes, uint64_t s
     sizes[0] = pb;
     sizes[1] = first;
     sizes[2] = ub - first;
-    return FRAG_OK;
-}
-
-frag_status frag_plan_set_tiling(frag_plan plan, uint32_t tile_w, uint32_t tile_h,
-                                 uint32_t ctas_per_sm)
-{
-    frag_status st = check_plan(plan);
-    if (st != FRAG_OK)
-        return st;
-    const uint32_t step = std::max(16u, 1u << plan->levels);
-    tile_w = tile_w ? tile_w : std::max(kDefaultTile, 1u << plan->levels);
-    tile_h = tile_h ? tile_h : std::max(kDefaultTile, 1u << plan->levels);
-    if (tile_w % step || tile_h % step || tile_w > 256 || tile_h > 256)
-        return fail(FRAG_EINVAL, "tile %ux%u must be multiples of %u, at most 256", tile_w, tile_h,
-                    step);
-    const size_t smem = std::max(frag::tile_smem_bytes(tile_w, tile_h, plan->levels, true),
-                                 frag::tile_smem_bytes(tile_w, tile_h, plan->levels, false));
-    if (smem > 227 * 1024)
-        return fail(FRAG_EINVAL, "tile %ux%u needs %zu bytes of shared memory", tile_w, tile_h,
-                    smem);
-    plan->tile_w = tile_w;
-    plan->tile_h = tile_h;
-    plan->ctas_per_sm = ctas_per_sm;
-    return FRAG_OK;
-}
-
-frag_status frag_plan_get_tiling(frag_plan plan, uint32_t *tile_w, uint32_t *tile_h,
-                                 uint32_t *ctas_per_sm)
-{
-    frag_status st = check_plan(plan);
-    if (st != FRAG_OK)
-        return st;
-    if (tile_w)
-        *tile_w = plan->tile_w;
-    if (tile_h)
-        *tile_h = plan->tile_h;
-    if (ctas_per_sm)
-        *ctas_per_sm = plan->ctas_per_sm;
     return FRAG_OK;
 }
 

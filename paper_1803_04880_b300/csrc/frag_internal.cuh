@@ -11,25 +11,20 @@
 
 namespace frag {
 
-// One buffer of a launch.  For protect, `in` is read and priv/pub are
-// written; for recover, priv_in/pub_in are read and `out` is written.
+// One buffer of a tile-kernel launch (the allocation-free protect): `in` is
+// read, priv / pub are written.
 struct Job {
     const uint8_t *in;
-    const uint8_t *priv_in;
-    const uint8_t *pub_in;
-    uint8_t *out;
     uint8_t *priv;
     uint8_t *pub;
     uint64_t n;       // bytes of the original buffer
     uint64_t nonce;   // AES-CTR nonce (high 64 bits of the counter block)
     uint32_t W;       // matrix width
     uint32_t H;       // padded rows (multiple of 2^L)
-    uint32_t L;       // levels
-    uint32_t tile_w;  // owned tile width  (multiple of 2^L)
-    uint32_t tile_h;  // owned tile height (multiple of 2^L)
+    uint32_t L;       // levels (1..kTileMaxLevels)
+    uint32_t tile;    // owned tile side: tile_side(L)
     uint32_t tiles_x;
     uint32_t tiles_y;
-    uint32_t path;    // 0: generic tile body, 1: row/column-pass body (L <= 3)
 };
 
 // Job kinds of the dependency-ordered launch.
@@ -96,14 +91,13 @@ struct DagWork {
     uint32_t spin_limit;
 };
 
-// Launch-wide description of where jobs and tiles come from.
+// A tile-kernel launch: its jobs, their tiles and the work queue.
 struct Work {
-    Job single;                 // used when jobs == nullptr
-    const Job *jobs;            // device array of jobs (batched launch)
+    const Job *jobs;            // device array of jobs
     const uint64_t *tile_start; // exclusive prefix of tiles per job (njobs + 1 entries)
     uint32_t njobs;
     uint64_t total_tiles;
-    unsigned long long *queue;  // device work-queue head (nullptr: static striding)
+    unsigned long long *queue;  // device work-queue head (zero at launch)
     const uint32_t *aes_tables; // 4 x 256 T-table words + 256 S-box words, device
     const uint32_t *round_keys; // 44 big-endian round-key words, device
     int *err;                   // device error word
@@ -122,16 +116,6 @@ __host__ __device__ inline uint64_t band_offset(uint32_t H, uint32_t W, uint32_t
         off += 6ull * (uint64_t)(H >> k) * (uint64_t)(W >> k);
     return off + 2ull * b * (uint64_t)(H >> l) * (uint64_t)(W >> l);
 }
-
-// Halo of the tile window in level-0 pixels.  Forward: the level-L output at
-// index k depends on level-0 samples 2^L k - 2(2^L - 1) .. 2^L k + 2^L - 1
-// (each level needs two samples left and one right of its pair), so 2^(L+1)
-// to the left and 2^L to the right cover it.  Inverse: level-0 sample x needs
-// level-l coefficients from about x/2^l - 2 to x/2^l + 1 plus the detail
-// half-step, so 2^(L+1) on both sides.
-__host__ __device__ inline uint32_t halo_lo(uint32_t L) { return 2u << L; }
-__host__ __device__ inline uint32_t halo_hi_fwd(uint32_t L) { return 1u << L; }
-__host__ __device__ inline uint32_t halo_hi_inv(uint32_t L) { return 2u << L; }
 
 // host helpers (frag_api.cu)
 const uint32_t *host_aes_words();                             // kAesWords words
@@ -280,13 +264,12 @@ cudaError_t launch_blocks(bool fwd, bool packed, bool keyed, const FuseWork &w, 
                           cudaStream_t stream);
 cudaError_t block_occupancy(bool fwd, bool packed, bool keyed, int *blocks_per_sm);
 
-// kernels (tile_kernels.cu)
-constexpr uint32_t kFastTile = 256;   // owned tile side of the row/column-pass body
-constexpr uint32_t kFastMaxLevels = 3;
-size_t tile_smem_bytes(uint32_t tile_w, uint32_t tile_h, uint32_t L, bool fwd);
-size_t fast_smem_bytes(bool fwd);
-size_t job_smem_bytes(const Job &j, bool fwd); // dynamic shared memory one job's tiles need
-cudaError_t launch_tiles(bool fwd, const Work &w, uint32_t grid, size_t smem, cudaStream_t stream);
-cudaError_t tile_occupancy(bool fwd, size_t smem, int *blocks_per_sm);
+// the tile kernel (tile_kernels.cu, fast_tiles.cuh): 1 to 5 levels, one
+// square tile of a buffer and its halo in shared memory per CTA
+constexpr uint32_t kTileMaxLevels = 5;
+__host__ __device__ constexpr uint32_t tile_side(uint32_t L) { return L <= 3 ? 256 : (L == 4 ? 240 : 160); }
+size_t tile_smem_bytes(uint32_t L); // dynamic shared memory of an L-level job's tiles
+cudaError_t launch_tiles(const Work &w, uint32_t grid, size_t smem, cudaStream_t stream);
+cudaError_t tile_occupancy(size_t smem, int *blocks_per_sm);
 
 } // namespace frag

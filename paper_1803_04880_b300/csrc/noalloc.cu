@@ -184,9 +184,9 @@ extern "C" frag_status frag_protect_batch_noalloc(const frag_item *items, uint32
         j.in = (const uint8_t *)items[i].d_in;
         j.priv = (uint8_t *)items[i].d_private;
         j.pub = (uint8_t *)items[i].d_public;
-        h_cost[nj] = (uint64_t)j.tiles_x * j.tiles_y * (uint64_t)j.tile_w * j.tile_h;
+        h_cost[nj] = (uint64_t)j.tiles_x * j.tiles_y * (uint64_t)j.tile * j.tile;
         h_order[nj] = nj;
-        smem = std::max(smem, frag::job_smem_bytes(j, true));
+        smem = std::max(smem, frag::tile_smem_bytes(j.L));
         ++nj;
     }
     if (nj + nf == 0)
@@ -305,13 +305,13 @@ extern "C" frag_status frag_protect_batch_noalloc(const frag_item *items, uint32
     w.round_keys = (const uint32_t *)(base + kOffKeys);
 
     int occ = 0;
-    if ((e = frag::tile_occupancy(true, smem, &occ)) != cudaSuccess)
+    if ((e = frag::tile_occupancy(smem, &occ)) != cudaSuccess)
         return frag::report_cuda(e, "frag_protect_batch_noalloc: occupancy query");
     if (occ <= 0)
         return frag::report(FRAG_EUNSUPPORTED, "frag_protect_batch_noalloc: tile too large");
     const uint32_t grid =
         (uint32_t)std::min<uint64_t>((uint64_t)d->sms * (uint64_t)occ, w.total_tiles);
-    if ((e = frag::launch_tiles(true, w, grid, smem, s)) != cudaSuccess)
+    if ((e = frag::launch_tiles(w, grid, smem, s)) != cudaSuccess)
         return frag::report_cuda(e, "frag_protect_batch_noalloc: launch");
     return FRAG_OK;
 }

@@ -33,7 +33,7 @@ def test_exports_every_declared_symbol(L):
 
 
 def test_abi_version(L):
-    assert L.frag_abi_version() == 1
+    assert L.frag_abi_version() == 2
 
 
 @pytest.mark.parametrize("w,l,status", [(0, 1, fr.FRAG_EINVAL), (12, 3, fr.FRAG_EINVAL),
@@ -65,16 +65,6 @@ def test_sizes_match_oracle(L, n, w, l):
     p = fr.Plan(w, l)
     H, pb, ub = p.sizes(n)
     assert (H, pb, ub) == oracle.sizes(n, w, l)
-
-
-def test_tiling_validation(L):
-    p = fr.Plan(256, 3)
-    assert p.tiling()[:2] == (64, 64)
-    p.set_tiling(128, 32, 2)
-    assert p.tiling() == (128, 32, 2)
-    for bad in ((40, 64), (64, 300), (8, 64)):
-        with pytest.raises(fr.FragError):
-            p.set_tiling(*bad)
 
 
 def test_null_arguments_are_rejected(L):

@@ -31,11 +31,9 @@ def key(fr):
     return fr.Key(KEY)
 
 
-def gpu_round_trip(fr, key, data, W, L, nonce, tiling=None, offset=0, path=0):
+def gpu_round_trip(fr, key, data, W, L, nonce, offset=0, path=0):
     plan = fr.Plan(W, L)
     plan.set_path(path)
-    if tiling:
-        plan.set_tiling(*tiling)
     n = data.size
     _, pb, ub = plan.sizes(n)
     # offset > 0 places every buffer at an odd address
@@ -52,10 +50,10 @@ def gpu_round_trip(fr, key, data, W, L, nonce, tiling=None, offset=0, path=0):
     return priv[offset:].cpu().numpy(), pub[offset:].cpu().numpy(), o[offset:offset + n]
 
 
-def check_against_oracle(fr, key, data, W, L, nonce=0, tiling=None, offset=0, path=0):
+def check_against_oracle(fr, key, data, W, L, nonce=0, offset=0, path=0):
     data = np.ascontiguousarray(data).reshape(-1)
     p_ref, u_ref = oracle.protect(data, W, L, KEY, nonce)
-    p, u, r = gpu_round_trip(fr, key, data, W, L, nonce, tiling, offset, path)
+    p, u, r = gpu_round_trip(fr, key, data, W, L, nonce, offset, path)
     assert np.array_equal(p, p_ref), "private fragment differs"
     if not np.array_equal(u, u_ref):
         bad = np.flatnonzero(u != u_ref)
@@ -68,21 +66,19 @@ def test_c1_full(fr, key):
 
 
 SWEEP = [
-    # (n, W, L, tiling)
-    (1, 2, 1, None), (2, 2, 1, None), (5, 4, 2, None), (64, 8, 2, None), (1000, 64, 3, None),
-    (4096, 64, 1, None), (4097, 64, 1, None), (5000, 16, 4, None), (12345, 128, 2, None),
-    (65536 + 17, 256, 3, None), (77777, 256, 5, None), (100000, 1024, 4, None),
-    (200000, 96, 2, None), (300000, 160, 5, None), (131072, 512, 3, (32, 16, 0)),
-    (131072, 512, 3, (128, 32, 1)), (250000, 1000, 3, (16, 16, 0)), (262144, 256, 4, (256, 16, 0)),
-    (99999, 32, 5, (32, 32, 0)), (1 << 20, 2048, 2, (64, 128, 0)),
+    # (n, W, L)
+    (1, 2, 1), (2, 2, 1), (5, 4, 2), (64, 8, 2), (1000, 64, 3),
+    (4096, 64, 1), (4097, 64, 1), (5000, 16, 4), (12345, 128, 2), (65536 + 17, 256, 3),
+    (77777, 256, 5), (100000, 1024, 4), (200000, 96, 2), (300000, 160, 5), (131072, 512, 3),
+    (250000, 1000, 3), (262144, 256, 4), (99999, 32, 5), (1 << 20, 2048, 2),
     # around the 224-pixel tile of the register-streaming path
-    (224 * 230, 224, 3, None), (448 * 449 + 3, 448, 2, None), (240 * 500, 240, 3, None),
-    (672 * 225 + 100, 672, 1, None), (16 * 1000, 16, 3, None), (8 * 7, 8, 3, None),
-    (232 * 232, 232, 3, None), (456 * 456 - 1, 456, 3, None), (904 * 220, 904, 2, None),
+    (224 * 230, 224, 3), (448 * 449 + 3, 448, 2), (240 * 500, 240, 3), (672 * 225 + 100, 672, 1),
+    (16 * 1000, 16, 3), (8 * 7, 8, 3), (232 * 232, 232, 3), (456 * 456 - 1, 456, 3),
+    (904 * 220, 904, 2),
     # six to eight levels (W a multiple of 2^L, ragged heights and tails)
-    (64 * 130 + 5, 64, 6, None), (128 * 200 - 1, 128, 7, None), (256 * 300 + 13, 256, 8, None),
-    (1024 * 1024 + 777, 1024, 6, None), (512 * 600, 512, 7, None), (2048 * 300 + 1, 2048, 8, None),
-    (768 * 256, 768, 8, None), (320 * 999, 320, 6, None),
+    (64 * 130 + 5, 64, 6), (128 * 200 - 1, 128, 7), (256 * 300 + 13, 256, 8),
+    (1024 * 1024 + 777, 1024, 6), (512 * 600, 512, 7), (2048 * 300 + 1, 2048, 8),
+    (768 * 256, 768, 8), (320 * 999, 320, 6),
 ]
 
 
@@ -91,10 +87,10 @@ SWEEP = [
 # kernel; 2: the fused levels with the private fragment enciphered inside the
 # fused pass that reaches level L
 @pytest.mark.parametrize("path", [0, 1, 2])
-@pytest.mark.parametrize("n,W,L,tiling", SWEEP)
-def test_sweep_random(fr, key, n, W, L, tiling, path):
+@pytest.mark.parametrize("n,W,L", SWEEP)
+def test_sweep_random(fr, key, n, W, L, path):
     data = wl.random_bytes(n, seed=n + W + L)
-    check_against_oracle(fr, key, data, W, L, nonce=n % 7, tiling=tiling, path=path)
+    check_against_oracle(fr, key, data, W, L, nonce=n % 7, path=path)
 
 
 # the fused kernel's segment height: from one 8-row iteration per unit (the

@@ -114,7 +114,13 @@ def test_rejects_more_than_five_levels(fr):
 # levels
 ROUTES = [(50_000, 64, 1, 910, 0, 0), (70_001, 128, 2, 911, 0, 0), (90_000, 256, 3, 912, 0, 0),
           (50_000, 64, 2, 913, 1, 0), (6_000, 4, 2, 914, 0, 0), (30_000, 64, 1, 915, 0, 4),
-          (100_000, 256, 4, 916, 0, 0), (120_000, 512, 5, 917, 0, 0)]
+          (100_000, 256, 4, 916, 0, 0), (120_000, 512, 5, 917, 0, 0),
+          # 4 levels: 240-pixel tiles, 5 levels: 160-pixel tiles -- several
+          # tile columns and rows with ragged last ones, narrow widths, an
+          # unaligned input, a last row cut short
+          (1024 * 700 + 5, 1024, 4, 918, 0, 0), (2048 * 400 + 77, 2048, 5, 919, 0, 0),
+          (16 * 3000, 16, 4, 920, 0, 0), (32 * 5000 - 3, 32, 5, 921, 0, 0),
+          (480 * 481, 480, 4, 922, 3, 0), (320 * 330 + 1, 320, 5, 923, 0, 0)]
 
 
 def _route_entries(fr, rows):
@@ -142,8 +148,9 @@ def test_fused_and_tile_routes_alike(fr):
     fr.protect_batch([r for r, _ in entries], key)
     torch.cuda.synchronize()
     fr.sync_status()
-    for name, idx in (("mixed", range(8)), ("fused only", range(3)), ("tile only", range(3, 8)),
-                      ("one fused item", [1])):
+    for name, idx in (("mixed", range(len(ROUTES))), ("fused only", range(3)),
+                      ("tile only", range(3, len(ROUTES))), ("one fused item", [1]),
+                      ("one tile item", [9])):
         got = [entries[i][1] for i in idx]
         for (_, _, _, _, p, u) in got:
             p.fill_(0x5A)
