@@ -886,10 +886,11 @@ def run_c4(args, rank, world, local_rank):
 
 def _noalloc_leg(fr, pentries, privs, pubs, key, raw_key, s, reps=5):
     """Protect of the batch's first FRAG_NOALLOC_MAX_ITEMS buffers through
-    the allocation-free call (the shared-memory tile kernel) against a batch
-    object's protect of the same buffers (the fused path), both event-timed
-    on the launch stream; the call's fragments must equal the batch's, which
-    privs / pubs hold after the batched round trips."""
+    the allocation-free call (the fused and CTR launches for buffers of 1..3
+    levels, the shared-memory tile kernel for 4 levels) against a batch
+    object's protect of the same buffers, both event-timed on the launch
+    stream; the call's fragments must equal the batch's, which privs / pubs
+    hold after the batched round trips."""
     import torch
 
     sub = pentries[:1024]
@@ -926,8 +927,8 @@ def _noalloc_leg(fr, pentries, privs, pubs, key, raw_key, s, reps=5):
     fr.sync_status(s)
     del p2, u2
     return {"what": "protect only, the first %d buffers (%.2f GB), allocation-free call "
-                    "(shared-memory tile kernel) vs a batch object (fused path); fragments equal"
-                    % (len(sub), nbytes / 1e9),
+                    "(fused + CTR launches at 1..3 levels, tile kernel at 4) vs a batch "
+                    "object; fragments equal" % (len(sub), nbytes / 1e9),
             "ms": round(times["noalloc"], 3), "value": round(nbytes / (times["noalloc"] / 1e3) / 1e9, 2),
             "batch_ms": round(times["batch"], 3),
             "batch_value": round(nbytes / (times["batch"] / 1e3) / 1e9, 2)}
