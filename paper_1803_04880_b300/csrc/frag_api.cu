@@ -1316,8 +1316,10 @@ struct DagWave {
     std::vector<frag::CtrChunk> chunks; // private fragments of the separate CTR launch
     std::vector<uint64_t> turn_start;   // their first warp turns (one more entry)
     uint64_t turn_blocks = 0;
-    std::vector<frag::FuseBuf> fbufs;   // buffers of the fused launch (levels 1..3)
+    std::vector<frag::FuseBuf> fbufs;   // buffers of the first fused pass (levels 1..3)
     uint64_t fuse_units = 0;
+    std::vector<uint32_t> fgroups;      // fbufs[fgroups[g] .. fgroups[g + 1]): one launch each
+    std::vector<uint64_t> fgroup_units; // the units of each of those launches
     std::vector<frag::FuseBuf> fbufs2;  // buffers of the second fused pass (levels 4 to 6)
     uint64_t fuse_units2 = 0;
     std::vector<frag::FuseBuf> bbufs;   // buffers of the block launch
@@ -1415,6 +1417,53 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
     return FRAG_OK;
 }
 
+// The launches of a first fused pass over f[0..n): one per level count
+// (true) when every count present has at least a round of full units for
+// the `slots` resident warps, else one launch (C4's protect: one launch whose
+// warps mixed units of 1, 2 and 3 levels took 51.5 ms, one launch per count
+// 43.8 ms in all).
+bool fuse_split_by_levels(const frag::FuseBuf *f, size_t n, uint64_t slots)
+{
+    uint64_t work[frag::kFuseMaxLevels + 1] = {0};
+    for (size_t i = 0; i < n; ++i)
+        work[f[i].F] += (uint64_t)f[i].strips * f[i].iters;
+    int kinds = 0;
+    bool split = true;
+    for (uint32_t F = 1; F <= frag::kFuseMaxLevels; ++F)
+        if (work[F]) {
+            ++kinds;
+            split = split && work[F] >= slots * kFuseBatchSegIters;
+        }
+    return kinds > 1 && split;
+}
+
+// a wave's first-pass launches (fgroups, fgroup_units) by that rule: a
+// count's buffers keep their order (largest first), and each launch's units
+// are scheduled on their own
+void fuse_groups(DagWave &wv, uint64_t slots, uint32_t plan_rows)
+{
+    std::vector<frag::FuseBuf> &f = wv.fbufs;
+    wv.fgroups.assign(1, 0);
+    wv.fgroup_units.clear();
+    wv.fuse_units = 0;
+    if (f.empty())
+        return;
+    if (fuse_split_by_levels(f.data(), f.size(), slots)) {
+        std::stable_sort(f.begin(), f.end(),
+                         [](const frag::FuseBuf &a, const frag::FuseBuf &b) { return a.F > b.F; });
+        for (size_t i = 1; i < f.size(); ++i)
+            if (f[i].F != f[i - 1].F)
+                wv.fgroups.push_back((uint32_t)i);
+    }
+    wv.fgroups.push_back((uint32_t)f.size());
+    for (size_t g = 0; g + 1 < wv.fgroups.size(); ++g) {
+        const uint64_t u = fuse_schedule(f.data() + wv.fgroups[g], wv.fgroups[g + 1] - wv.fgroups[g],
+                                         slots, plan_rows, true);
+        wv.fgroup_units.push_back(u);
+        wv.fuse_units += u;
+    }
+}
+
 // jobs and units of every wave, with scratch pointers from `scratch_base`;
 // then the layout of the descriptors after the scratch
 void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
@@ -1483,9 +1532,7 @@ void fill_batch(BatchPlan &bp, uint8_t *scratch_base)
     }
     for (auto &wv : bp.waves) {
         wave_units(wv.jobs, wv.first, wv.levels, wv.units);
-        wv.fuse_units = fuse_schedule(wv.fbufs.data(), wv.fbufs.size(),
-                                      std::max<uint64_t>(1, bp.fuse_slots),
-                                      bp.fuse_rows, true);
+        fuse_groups(wv, std::max<uint64_t>(1, bp.fuse_slots), bp.fuse_rows);
         wv.block_units = block_units(wv.bbufs.data(), wv.bbufs.size());
         wv.packed_units = block_units(wv.pbufs.data(), wv.pbufs.size());
         wv.fuse_units2 = fuse_schedule(wv.fbufs2.data(), wv.fbufs2.size(),
@@ -1586,29 +1633,37 @@ struct LaunchTimer {
     }
 };
 
-// the fused launch of a wave (its buffers' descriptors at fbufs_off)
+// the fused launches of a wave: the first pass, one launch per group of
+// fgroups (descriptors at fbufs_off), or the second pass, one launch
+// (descriptors at fbufs2_off)
 frag_status launch_wave_fused(const BatchPlan &bp, const DagWave &wv, uint8_t *mem, DeviceState &d,
                               cudaStream_t s, LaunchTimer &tm, const frag::AesKeys &keys, int pass = 1)
 {
     const std::vector<frag::FuseBuf> &bufs = pass == 1 ? wv.fbufs : wv.fbufs2;
     if (bufs.empty())
         return FRAG_OK;
-    frag::FuseWork w;
-    std::memset(&w, 0, sizeof(w));
-    for (const auto &f : bufs)
-        w.cipher |= f.cipher;
-    if (w.cipher)
-        w.keys = keys;
-    w.nbufs = (uint32_t)bufs.size();
-    w.bufs = (const frag::FuseBuf *)(mem + (pass == 1 ? wv.fbufs_off : wv.fbufs2_off));
-    if (w.nbufs == 1)
-        w.single = bufs[0];
-    w.total_units = pass == 1 ? wv.fuse_units : wv.fuse_units2;
-    tm.begin();
-    frag_status st = fuse_launch(d, bp.fwd, pass == 2, w,
-                                 std::max<uint64_t>(1, pass == 1 ? bp.fuse_slots : bp.fuse_slots2), s);
-    tm.end(pass == 1 ? FRAG_KERNEL_FUSED : FRAG_KERNEL_FUSED_LOW);
-    return st;
+    const size_t groups = pass == 1 ? wv.fgroups.size() - 1 : 1;
+    for (size_t g = 0; g < groups; ++g) {
+        const size_t lo = pass == 1 ? wv.fgroups[g] : 0, hi = pass == 1 ? wv.fgroups[g + 1] : bufs.size();
+        frag::FuseWork w;
+        std::memset(&w, 0, sizeof(w));
+        for (size_t i = lo; i < hi; ++i)
+            w.cipher |= bufs[i].cipher;
+        if (w.cipher)
+            w.keys = keys;
+        w.nbufs = (uint32_t)(hi - lo);
+        w.bufs = (const frag::FuseBuf *)(mem + (pass == 1 ? wv.fbufs_off : wv.fbufs2_off)) + lo;
+        if (w.nbufs == 1)
+            w.single = bufs[lo];
+        w.total_units = pass == 1 ? wv.fgroup_units[g] : wv.fuse_units2;
+        tm.begin();
+        frag_status st = fuse_launch(d, bp.fwd, pass == 2, w,
+                                     std::max<uint64_t>(1, pass == 1 ? bp.fuse_slots : bp.fuse_slots2), s);
+        tm.end(pass == 1 ? FRAG_KERNEL_FUSED : FRAG_KERNEL_FUSED_LOW);
+        if (st != FRAG_OK)
+            return st;
+    }
+    return FRAG_OK;
 }
 
 // the block launch of a wave (its buffers' descriptors at bbufs_off)
@@ -1875,6 +1930,13 @@ bool noalloc_fused_item(frag_plan plan, const frag_item &it, FuseBuf &f, CtrChun
 uint64_t noalloc_fuse_schedule(FuseBuf *f, size_t n, uint64_t slots, uint32_t plan_rows)
 {
     return fuse_schedule(f, n, std::max<uint64_t>(1, slots), plan_rows, true);
+}
+
+// a batch's choice for the fused protect of f[0..n): one launch per level
+// count (true) or one launch
+bool noalloc_split_fused(const FuseBuf *f, size_t n, uint64_t slots)
+{
+    return fuse_split_by_levels(f, n, std::max<uint64_t>(1, slots));
 }
 } // namespace frag
 
@@ -2431,8 +2493,9 @@ frag_status frag_batch_info(frag_batch batch, uint32_t *launches, uint64_t *scra
         return fail(FRAG_EINVAL, "batch is NULL");
     uint32_t n = 0;
     for (const auto &wv : batch->bp.waves)
-        n += (wv.units.empty() ? 0 : 1) + (wv.chunks.empty() ? 0 : 1) + (wv.fbufs.empty() ? 0 : 1) +
-             (wv.bbufs.empty() ? 0 : 1) + (wv.fbufs2.empty() ? 0 : 1) + (wv.pbufs.empty() ? 0 : 1);
+        n += (wv.units.empty() ? 0 : 1) + (wv.chunks.empty() ? 0 : 1) +
+             (wv.fbufs.empty() ? 0 : (uint32_t)wv.fgroups.size() - 1) + (wv.bbufs.empty() ? 0 : 1) +
+             (wv.fbufs2.empty() ? 0 : 1) + (wv.pbufs.empty() ? 0 : 1);
     if (launches)
         *launches = n;
     if (scratch_bytes)

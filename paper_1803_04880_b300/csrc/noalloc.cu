@@ -31,6 +31,7 @@ frag_status report_cuda(cudaError_t e, const char *what);
 bool noalloc_fused_item(frag_plan plan, const frag_item &it, FuseBuf &f, CtrChunk &c,
                         uint64_t *cells);
 uint64_t noalloc_fuse_schedule(FuseBuf *f, size_t n, uint64_t slots, uint32_t plan_rows);
+bool noalloc_split_fused(const FuseBuf *f, size_t n, uint64_t slots);
 } // namespace frag
 
 namespace {
@@ -83,6 +84,8 @@ frag::CtrChunk h_chunk[kMaxItems], h_chunk_sorted[kMaxItems];
 uint64_t h_turns[kMaxItems + 1];
 uint64_t h_fcost[kMaxItems];
 uint32_t h_forder[kMaxItems];
+uint32_t h_group[frag::kFuseMaxLevels + 1];      // fused launches: h_fuse_sorted[h_group[g] ..
+uint64_t h_group_units[frag::kFuseMaxLevels];    //   h_group[g + 1]) and their units
 
 // Once per device, with that device current: look up the scratch's device
 // address, copy the AES tables into it and zero the queue head and error
@@ -198,7 +201,13 @@ extern "C" frag_status frag_protect_batch_noalloc(const frag_item *items, uint32
     std::sort(h_order, h_order + nj, [](uint32_t a, uint32_t b) {
         return h_cost[a] != h_cost[b] ? h_cost[a] > h_cost[b] : a < b;
     });
-    std::sort(h_forder, h_forder + nf, [](uint32_t a, uint32_t b) {
+    // the fused items in one launch, or (as a batch decides) one launch per
+    // level count, each count's items together
+    const uint64_t fslots = (uint64_t)d->sms * d->fuse_ctas * d->fuse_warps;
+    const bool split = nf > 1 && frag::noalloc_split_fused(h_fuse, nf, fslots);
+    std::sort(h_forder, h_forder + nf, [split](uint32_t a, uint32_t b) {
+        if (split && h_fuse[a].F != h_fuse[b].F)
+            return h_fuse[a].F > h_fuse[b].F;
         return h_fcost[a] != h_fcost[b] ? h_fcost[a] > h_fcost[b] : a < b;
     });
     h_start[0] = 0;
@@ -206,20 +215,26 @@ extern "C" frag_status frag_protect_batch_noalloc(const frag_item *items, uint32
         h_sorted[k] = h_jobs[h_order[k]];
         h_start[k + 1] = h_start[k] + (uint64_t)h_sorted[k].tiles_x * h_sorted[k].tiles_y;
     }
-    // the fused launch's units and the CTR launch's warp turns, as a batch
-    // schedules them: units for the resident warps of the fused launch;
+    // the fused launches' units and the CTR launch's warp turns, as a batch
+    // schedules them: units for the resident warps of each fused launch;
     // turns of kCtrTurn blocks, doubled (up to 128x) while the fragments keep
     // more than 4 turns a resident warp of the CTR launch
-    uint64_t fuse_units = 0, turn = frag::kCtrTurn;
+    uint64_t turn = frag::kCtrTurn;
+    uint32_t ngroups = 0;
     if (nf) {
         uint64_t ctr_blocks = 0;
+        h_group[0] = 0;
         for (uint32_t k = 0; k < nf; ++k) {
             h_fuse_sorted[k] = h_fuse[h_forder[k]];
             h_chunk_sorted[k] = h_chunk[h_forder[k]];
             ctr_blocks += h_chunk_sorted[k].nblocks;
+            if (k > 0 && h_fuse_sorted[k].F != h_fuse_sorted[k - 1].F && split)
+                h_group[++ngroups] = k;
         }
-        fuse_units = frag::noalloc_fuse_schedule(
-            h_fuse_sorted, nf, (uint64_t)d->sms * d->fuse_ctas * d->fuse_warps, 0);
+        h_group[++ngroups] = nf;
+        for (uint32_t g = 0; g < ngroups; ++g)
+            h_group_units[g] = frag::noalloc_fuse_schedule(h_fuse_sorted + h_group[g],
+                                                           h_group[g + 1] - h_group[g], fslots, 0);
         const uint64_t per_warp = 4ull * d->sms * (frag::kCtrThreads / 32);
         while (turn < 128 * frag::kCtrTurn && ctr_blocks / (2 * turn) >= per_warp)
             turn *= 2;
@@ -260,22 +275,26 @@ extern "C" frag_status frag_protect_batch_noalloc(const frag_item *items, uint32
     const uint32_t *tables = (const uint32_t *)(base + kOffTables);
 
     if (nf) {
-        // the fused pass over the bytes, then the CTR pass enciphering every
-        // private fragment in place
-        frag::FuseWork fw;
-        std::memset(&fw, 0, sizeof(fw));
-        fw.bufs = (const frag::FuseBuf *)(base + kOffFuse);
-        if (nf == 1)
-            fw.single = h_fuse_sorted[0];
-        fw.nbufs = nf;
-        fw.total_units = fuse_units;
-        fw.err = err;
-        fw.aes_t0 = tables;
-        const uint64_t need = (fuse_units + d->fuse_warps - 1) / d->fuse_warps;
-        const uint32_t fgrid = (uint32_t)std::max<uint64_t>(
-            1, std::min<uint64_t>((uint64_t)d->sms * d->fuse_ctas, need));
-        if (fuse_units && (e = frag::launch_fuse(true, false, fw, fgrid, s)) != cudaSuccess)
-            return frag::report_cuda(e, "frag_protect_batch_noalloc: fused launch");
+        // the fused pass over the bytes (a launch per group), then the CTR
+        // pass enciphering every private fragment in place
+        for (uint32_t g = 0; g < ngroups; ++g) {
+            const uint32_t lo = h_group[g], cnt = h_group[g + 1] - lo;
+            const uint64_t units = h_group_units[g];
+            frag::FuseWork fw;
+            std::memset(&fw, 0, sizeof(fw));
+            fw.bufs = (const frag::FuseBuf *)(base + kOffFuse) + lo;
+            if (cnt == 1)
+                fw.single = h_fuse_sorted[lo];
+            fw.nbufs = cnt;
+            fw.total_units = units;
+            fw.err = err;
+            fw.aes_t0 = tables;
+            const uint64_t need = (units + d->fuse_warps - 1) / d->fuse_warps;
+            const uint32_t fgrid = (uint32_t)std::max<uint64_t>(
+                1, std::min<uint64_t>((uint64_t)d->sms * d->fuse_ctas, need));
+            if (units && (e = frag::launch_fuse(true, false, fw, fgrid, s)) != cudaSuccess)
+                return frag::report_cuda(e, "frag_protect_batch_noalloc: fused launch");
+        }
         frag::CtrWork cw;
         std::memset(&cw, 0, sizeof(cw));
         cw.frags = (const frag::CtrChunk *)(base + kOffChunks);

@@ -74,3 +74,41 @@ def test_tuner_picks_a_candidate(fr, tmp_path):
     plan = fr.Plan(2048, 3)
     assert tune.apply(plan, 4 << 20, path=path)
     assert plan.schedule() == (res["seg_rows"], res["ctas"])
+
+
+def test_large_batch_one_fused_launch_per_level_count(fr):
+    """A batch whose level counts each fill at least a round of full fused
+    units on the device runs its first fused pass as one launch per count;
+    its fragments equal one protect call per buffer, and its recover gives
+    the bytes back."""
+    key = fr.Key(wl.KEY)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    W = 4096
+    strips = -(-W // 240)                      # warp strips of 240 owned columns (232 at three levels)
+    need = 1.25 * sms * 16 * 32 / strips       # fused iterations per level count, with a margin
+    rows = int(need * 8 / 5) + 1               # five buffers a count
+    entries, rentries, singles = [], [], []
+    for L in (1, 2, 3):
+        plan = fr.Plan(W, L)
+        for k in range(5):
+            n = W * (rows + 37 * k) + 1000 * k + 3
+            nonce = 100 * L + k
+            d = torch.from_numpy(wl.random_bytes(n, nonce)).cuda()
+            _, pb, ub = plan.sizes(n)
+            p = torch.empty(pb, dtype=torch.uint8, device="cuda")
+            u = torch.empty(ub, dtype=torch.uint8, device="cuda")
+            o = torch.empty(n, dtype=torch.uint8, device="cuda")
+            entries.append((plan, nonce, n, d, p, u))
+            rentries.append((plan, nonce, n, p, u, o))
+            singles.append(fr.protect(plan, key, nonce, d))
+    bp, br = fr.Batch(entries, protect=True), fr.Batch(rentries, protect=False)
+    # three fused launches (one per level count) and the CTR launch, each way
+    assert bp.info()[0] == 4 and br.info()[0] == 4
+    bp.run(key)
+    br.run(key)
+    fr.sync_status()
+    for (plan, nonce, n, d, p, u), (_, _, _, _, _, o), (p1, u1) in zip(entries, rentries, singles):
+        what = "(L=%d, n=%d)" % (plan.levels, n)
+        assert torch.equal(p, p1), "private fragment differs " + what
+        assert torch.equal(u, u1), "public fragment differs " + what
+        assert torch.equal(o, d), "recovered bytes differ " + what

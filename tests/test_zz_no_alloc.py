@@ -163,3 +163,35 @@ def test_fused_and_tile_routes_alike(fr):
             what = "(n=%d, W=%d, L=%d, row %d) in the %s call" % (n, plan.width, plan.levels, i, name)
             assert torch.equal(p0, p1), "private fragment differs " + what
             assert torch.equal(u0, u1), "public fragment differs " + what
+
+
+def test_large_call_one_fused_launch_per_level_count(fr):
+    """Fused items large enough that each level count fills a round of full
+    units on the device (the call then runs one fused launch per count, as a
+    batch does): fragments equal frag_protect_batch's."""
+    key = fr.Key(wl.KEY)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    W = 4096
+    need = 1.25 * sms * 16 * 32 / -(-W // 240)   # fused iterations per level count, with a margin
+    rows = int(need * 8 / 4) + 1                  # four buffers a count
+    ref, got = [], []
+    for L in (3, 1, 2):
+        plan = fr.Plan(W, L)
+        for k in range(4):
+            n = W * (rows + 53 * k) + 777 * k
+            nonce = 1000 + 10 * L + k
+            t = torch.from_numpy(wl.random_bytes(n, nonce)).cuda()
+            _, pb, ub = plan.sizes(n)
+            mk = lambda m: torch.full((m,), 0x5A, dtype=torch.uint8, device="cuda")
+            ref.append((plan, nonce, n, t, mk(pb), mk(ub)))
+            got.append((plan, nonce, n, t, mk(pb), mk(ub)))
+    fr.protect_batch(ref, key)
+    torch.cuda.synchronize()
+    fr.sync_status()
+    assert _noalloc(fr, got) == fr.FRAG_OK, fr.last_error()
+    assert fr.lib().frag_noalloc_sync_status(
+        torch.cuda.current_stream().cuda_stream) == fr.FRAG_OK, fr.last_error()
+    for (plan, _, n, _, p0, u0), (_, _, _, _, p1, u1) in zip(ref, got):
+        what = "(n=%d, L=%d)" % (n, plan.levels)
+        assert torch.equal(p0, p1), "private fragment differs " + what
+        assert torch.equal(u0, u1), "public fragment differs " + what
