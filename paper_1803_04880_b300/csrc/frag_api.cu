@@ -1418,10 +1418,14 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
 }
 
 // The launches of a first fused pass over f[0..n): one per level count
-// (true) when every count present has at least a round of full units for
-// the `slots` resident warps, else one launch (C4's protect: one launch whose
-// warps mixed units of 1, 2 and 3 levels took 51.5 ms, one launch per count
-// 43.8 ms in all).
+// (true) when every count present has at least kFuseSplitRounds rounds of
+// full units for the `slots` resident warps, else one launch.  Protect of
+// 1, 2 and 3 levels at width 4096, one launch per count against one mixed
+// launch, by rounds per count: 1.4 rounds 17 % slower (each launch ends in a
+// part-filled round), 2.9 even, 4.3 3 % slower, 8.7 4 % faster, 17 and 47
+// 7-8 % faster; C4 (10,000 buffers, about 118 rounds a count) 51.5 -> 45.4 ms.
+constexpr uint64_t kFuseSplitRounds = 8;
+
 bool fuse_split_by_levels(const frag::FuseBuf *f, size_t n, uint64_t slots)
 {
     uint64_t work[frag::kFuseMaxLevels + 1] = {0};
@@ -1432,7 +1436,7 @@ bool fuse_split_by_levels(const frag::FuseBuf *f, size_t n, uint64_t slots)
     for (uint32_t F = 1; F <= frag::kFuseMaxLevels; ++F)
         if (work[F]) {
             ++kinds;
-            split = split && work[F] >= slots * kFuseBatchSegIters;
+            split = split && work[F] >= kFuseSplitRounds * slots * kFuseBatchSegIters;
         }
     return kinds > 1 && split;
 }

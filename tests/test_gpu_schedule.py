@@ -77,15 +77,15 @@ def test_tuner_picks_a_candidate(fr, tmp_path):
 
 
 def test_large_batch_one_fused_launch_per_level_count(fr):
-    """A batch whose level counts each fill at least a round of full fused
-    units on the device runs its first fused pass as one launch per count;
-    its fragments equal one protect call per buffer, and its recover gives
-    the bytes back."""
+    """A batch whose level counts each fill at least eight rounds of full
+    fused units on the device runs its first fused pass as one launch per
+    count; its fragments equal one protect call per buffer, and its recover
+    gives the bytes back."""
     key = fr.Key(wl.KEY)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     W = 4096
     strips = -(-W // 240)                      # warp strips of 240 owned columns (232 at three levels)
-    need = 1.25 * sms * 16 * 32 / strips       # fused iterations per level count, with a margin
+    need = 8.8 * sms * 16 * 32 / strips        # fused iterations per level count, with a margin
     rows = int(need * 8 / 5) + 1               # five buffers a count
     entries, rentries, singles = [], [], []
     for L in (1, 2, 3):

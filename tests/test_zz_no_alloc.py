@@ -166,13 +166,13 @@ def test_fused_and_tile_routes_alike(fr):
 
 
 def test_large_call_one_fused_launch_per_level_count(fr):
-    """Fused items large enough that each level count fills a round of full
-    units on the device (the call then runs one fused launch per count, as a
-    batch does): fragments equal frag_protect_batch's."""
+    """Fused items large enough that each level count fills eight rounds of
+    full units on the device (the call then runs one fused launch per count,
+    as a batch does): fragments equal frag_protect_batch's."""
     key = fr.Key(wl.KEY)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     W = 4096
-    need = 1.25 * sms * 16 * 32 / -(-W // 240)   # fused iterations per level count, with a margin
+    need = 8.8 * sms * 16 * 32 / -(-W // 240)    # fused iterations per level count, with a margin
     rows = int(need * 8 / 4) + 1                  # four buffers a count
     ref, got = [], []
     for L in (3, 1, 2):
