@@ -1422,7 +1422,7 @@ frag_status plan_batch(bool fwd, const frag_item *pi, const frag_ritem *ri, uint
 // full units for the `slots` resident warps, else one launch.  Protect of
 // 1, 2 and 3 levels at width 4096, one launch per count against one mixed
 // launch, by rounds per count: 1.4 rounds 17 % slower (each launch ends in a
-// part-filled round), 2.9 even, 4.3 3 % slower, 8.7 4 % faster, 17 and 47
+// part-filled round), 2.9 even, 4.3 3 % slower, 8.7 4 % faster, 17 and 52
 // 7-8 % faster; C4 (10,000 buffers, about 118 rounds a count) 51.5 -> 45.4 ms.
 constexpr uint64_t kFuseSplitRounds = 8;
 
