@@ -283,11 +283,12 @@ def protect(plan: Plan, key: Key, nonce: int, data, nbytes: Optional[int] = None
             private=None, public=None, stream=None):
     """Device bytes -> (private, public) uint8 device tensors."""
     n = data.numel() * data.element_size() if nbytes is None else nbytes
-    _, pb, ub = plan.sizes(n)
-    if private is None:
-        private = _empty(pb, data.device)
-    if public is None:
-        public = _empty(ub, data.device)
+    if private is None or public is None:
+        _, pb, ub = plan.sizes(n)
+        if private is None:
+            private = _empty(pb, data.device)
+        if public is None:
+            public = _empty(ub, data.device)
     check(lib().frag_protect(plan.handle, key.handle, nonce, _ptr(data), n, _ptr(private),
                              _ptr(public), _stream(stream)))
     return private, public

@@ -974,8 +974,8 @@ size_t smem_bytes(bool fwd, bool packed) { return fwd && !packed ? (size_t)kWarp
 template <bool FWD, bool PACKED, bool KEYED>
 cudaError_t set_attr()
 {
-    return cudaFuncSetAttribute((const void *)block_kernel<FWD, PACKED, KEYED>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(FWD, PACKED));
+    static std::atomic<uint64_t> done{0};
+    return smem_attr_once((const void *)block_kernel<FWD, PACKED, KEYED>, (int)smem_bytes(FWD, PACKED), done);
 }
 
 template <bool FWD, bool PACKED, bool KEYED>

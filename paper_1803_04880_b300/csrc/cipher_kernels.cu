@@ -92,8 +92,8 @@ __global__ void __launch_bounds__(kCtrThreads, 1) ctr_kernel(CtrWork w)
 
 static cudaError_t ctr_attr()
 {
-    return cudaFuncSetAttribute((const void *)ctr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kCtrSmem);
+    static std::atomic<uint64_t> done{0};
+    return smem_attr_once((const void *)ctr_kernel, (int)kCtrSmem, done);
 }
 
 cudaError_t launch_ctr(const CtrWork &w, uint32_t grid, cudaStream_t stream)

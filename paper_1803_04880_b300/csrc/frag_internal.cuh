@@ -5,6 +5,7 @@
 // is written for the in-place tile layout the kernels use.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -115,6 +116,28 @@ __host__ __device__ inline uint64_t band_offset(uint32_t H, uint32_t W, uint32_t
     for (uint32_t k = L; k > l; --k)
         off += 6ull * (uint64_t)(H >> k) * (uint64_t)(W >> k);
     return off + 2ull * b * (uint64_t)(H >> l) * (uint64_t)(W >> l);
+}
+
+// cudaFuncSetAttribute(fn, MaxDynamicSharedMemorySize, bytes) on the current
+// device once per kernel and device: `done` is that kernel's mask of devices
+// already set (devices 0..63; any other is set on every call).  A launch of
+// a small buffer is host-bound (about 1 us a call of the attribute set out
+// of 15-20 us a call), so the launches skip the repeat.  The attribute lasts
+// as long as the device's context: the library is not for use across a
+// cudaDeviceReset (its device state, AES tables and pool are cached too).
+inline cudaError_t smem_attr_once(const void *fn, int bytes, std::atomic<uint64_t> &done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit))
+        return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit)
+        done.fetch_or(bit, std::memory_order_release);
+    return e;
 }
 
 // host helpers (frag_api.cu)

@@ -1279,8 +1279,8 @@ constexpr size_t smem_bytes()
 template <bool FWD, bool PK, bool CIPH>
 cudaError_t set_attr()
 {
-    return cudaFuncSetAttribute((const void *)fuse_kernel<FWD, PK, CIPH>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<FWD, PK, CIPH>());
+    static std::atomic<uint64_t> done{0};
+    return smem_attr_once((const void *)fuse_kernel<FWD, PK, CIPH>, (int)smem_bytes<FWD, PK, CIPH>(), done);
 }
 
 template <bool FWD, bool PK, bool CIPH>

@@ -1401,15 +1401,16 @@ __global__ void __launch_bounds__(kCtaThreads, FRAG_CTAS_PER_SM) dag_kernel(DagW
     }
 }
 
-static cudaError_t dag_attr(const void *fn)
+static cudaError_t dag_attr(bool fwd)
 {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    static std::atomic<uint64_t> done[2] = {{0}, {0}};
+    const void *fn = fwd ? (const void *)dag_kernel<true> : (const void *)dag_kernel<false>;
+    return smem_attr_once(fn, (int)kSmemBytes, done[fwd ? 1 : 0]);
 }
 
 cudaError_t launch_dag(bool fwd, const DagWork &w, uint32_t grid, cudaStream_t stream)
 {
-    const void *fn = fwd ? (const void *)dag_kernel<true> : (const void *)dag_kernel<false>;
-    cudaError_t e = dag_attr(fn);
+    cudaError_t e = dag_attr(fwd);
     if (e != cudaSuccess)
         return e;
     if (fwd)
@@ -1421,10 +1422,10 @@ cudaError_t launch_dag(bool fwd, const DagWork &w, uint32_t grid, cudaStream_t s
 
 cudaError_t dag_occupancy(bool fwd, int *blocks_per_sm)
 {
-    const void *fn = fwd ? (const void *)dag_kernel<true> : (const void *)dag_kernel<false>;
-    cudaError_t e = dag_attr(fn);
+    cudaError_t e = dag_attr(fwd);
     if (e != cudaSuccess)
         return e;
+    const void *fn = fwd ? (const void *)dag_kernel<true> : (const void *)dag_kernel<false>;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kCtaThreads, kSmemBytes);
 }
 
