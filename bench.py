@@ -49,9 +49,11 @@ def _args():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3l2",
-                    choices=["c1", "c2", "c2blocks", "c2packed", "c2keyed", "c3l2", "c3l4", "c4", "c5", "aesfull"])
+                    choices=["c1", "c2", "c2blocks", "c2packed", "c2keyed", "c3l2", "c3l4", "c4", "c5", "aesfull",
+                             "noalloc"])
     ap.add_argument("--items", type=int, default=10000, help="c4: number of buffers")
     ap.add_argument("--requests", type=int, default=240, help="c5: requests per load level")
+    ap.add_argument("--levels", default="1,2,3,4,5", help="noalloc: level counts, comma-separated")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="default workload: skip the sub-records")
@@ -1397,6 +1399,84 @@ def run_aesfull(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+# -- the allocation-free protect, per level count ------------------------------------
+
+def run_noalloc(args, rank, world, local_rank):
+    """The allocation-free batched protect (frag_protect_batch_noalloc) of the
+    256 MiB mixed buffer at width 8192, once per level count of --levels:
+    K event-timed calls after W untimed ones on the launch stream, against a
+    batch object's protect of the same buffer timed the same way; the
+    fragments must be equal.  Buffers of 1..3 levels go through the fused and
+    CTR launches, of 4 and 5 levels through the shared-memory tile kernel.
+    The buffer and its fragments exceed L2.  value = input bytes of every
+    level count's calls / their summed time (protect only)."""
+    import torch
+    import paper_1803_04880_b300 as fr
+    from paper_1803_04880_b300 import workloads as wl
+
+    fr.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    d = torch.from_numpy(wl.c3()).to(dev)
+    n = d.numel()
+    key = fr.Key(wl.KEY)
+    s = torch.cuda.Stream(device=dev)
+    K, Wm = max(1, min(args.steps, 50)), max(1, min(args.warmup, 10))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(Wm):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(K):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    levels, total_ms = {}, 0.0
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    for L in [int(x) for x in args.levels.split(",") if x]:
+        plan = fr.Plan(8192, L)
+        _, pb, ub = plan.sizes(n)
+        p = torch.empty(pb, dtype=torch.uint8, device=dev)
+        u = torch.empty(ub, dtype=torch.uint8, device=dev)
+        arr = (fr.frag_item * 1)()
+        arr[0] = fr.frag_item(plan.handle, 0, n, d.data_ptr(), p.data_ptr(), u.data_ptr())
+
+        def call():
+            st = fr.lib().frag_protect_batch_noalloc(arr, 1, bytes(wl.KEY), s.cuda_stream)
+            assert st == fr.FRAG_OK, fr.last_error()
+        ms = timed(call)
+        assert fr.lib().frag_noalloc_sync_status(s.cuda_stream) == fr.FRAG_OK, fr.last_error()
+        p2, u2 = torch.empty_like(p), torch.empty_like(u)
+        b = fr.Batch([(plan, 0, n, d, p2, u2)], protect=True)
+        bms = timed(lambda: b.run(key, s))
+        fr.sync_status(s)
+        assert torch.equal(p, p2) and torch.equal(u, u2), "allocation-free fragments differ at %d levels" % L
+        levels[str(L)] = {"ms": round(ms, 4), "value": round(n / ms / 1e6, 2),
+                          "batch_ms": round(bms, 4), "batch_value": round(n / bms / 1e6, 2),
+                          "kernels": "tile" if L > 3 else "fused + CTR"}
+        total_ms += ms
+        del p, u, p2, u2, b
+    clocks = sampler.stop()
+    if rank == 0:
+        value = world * n * len(levels) / (total_ms / 1e3) / 1e9
+        line = {"metric": "allocation-free protect GB/s on one B300", "value": round(value, 2),
+                "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+                "ms_per_step": round(total_ms, 4), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": "256 MiB mixed buffer (uniform|text|int32 walk), width 8192, "
+                                       "protect through frag_protect_batch_noalloc, levels " + args.levels,
+                           "l2": "inputs larger than L2",
+                           "path": "one call per step and level count; the batch object's protect of "
+                                   "the same buffer beside it"},
+                "levels": levels, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1419,6 +1499,8 @@ def main():
             run_c5(args, rank, world, local_rank)
         elif args.workload == "aesfull":
             run_aesfull(args, rank, world, local_rank)
+        elif args.workload == "noalloc":
+            run_noalloc(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:
