@@ -9,6 +9,8 @@
 #include "frag.h"
 #include "frag_internal.cuh"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <array>
 #include <cstdarg>
@@ -655,6 +657,51 @@ void fused_split(bool fwd, Buf &b, uint32_t path)
     }
 }
 
+// cuTensorMapEncodeTiled from the driver (looked up once; nullptr if the
+// driver has none)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// The TMA maps of the three level-1 bands an inverse first pass over f reads
+// (2D uint16: W/2 values a row, H/2 rows; boxes of 4 rows x 136 values, zeros
+// outside) into w, with w.l1_tma = 1; left off (per-lane copies) unless the
+// pass fuses one or two levels, the row pitch and the band bases are 16-byte
+// aligned and a band is at least a box wide and tall.  The 256 MiB buffer at
+// width 8192: 2 levels 157.5 -> 150.0 us a recover with the boxes, 3 levels
+// 164.8 -> 167.2 us (so three-level passes keep the per-lane copies)
+void set_l1_maps(frag::FuseWork &w, const frag::FuseBuf &f)
+{
+    w.l1_tma = 0;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    const uint64_t W1 = f.W >> 1, H1 = f.H >> 1;
+    if (enc == nullptr || f.F < 1 || f.F > 2 || (f.W % 16) != 0 || W1 < 136 || H1 < 4)
+        return;
+    for (int k = 0; k < 3; ++k)
+        if (!aligned(f.band[0][k], 16))
+            return;
+    const cuuint64_t dims[2] = {W1, H1};
+    const cuuint64_t strides[1] = {2 * W1};
+    const cuuint32_t box[2] = {136, 4};
+    const cuuint32_t estr[2] = {1, 1};
+    for (int k = 0; k < 3; ++k)
+        if (enc(&w.l1_map[k], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, f.band[0][k], dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return;
+    w.l1_tma = 1;
+}
+
 // descriptor of buffer b for a fused pass (schedule fields left 0): pass 1
 // works on the bytes, pass 2 on the packed LL_{F1} scratch (levels
 // F1+1 .. F1+F2)
@@ -1007,6 +1054,9 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
             fw[p].cipher = 1;
             fw[p].keys = frag::aes::keys_from_words(key->rk);
         }
+        fw[p].err = d->err;
+        if (!fwd && p == 0)
+            set_l1_maps(fw[p], fw[p].single);
     }
     const bool sep = ctr_pass(b);
     const frag::CtrChunk frag_chunk = ctr_fragment(fwd, b);
@@ -1657,8 +1707,12 @@ frag_status launch_wave_fused(const BatchPlan &bp, const DagWave &wv, uint8_t *m
             w.keys = keys;
         w.nbufs = (uint32_t)(hi - lo);
         w.bufs = (const frag::FuseBuf *)(mem + (pass == 1 ? wv.fbufs_off : wv.fbufs2_off)) + lo;
-        if (w.nbufs == 1)
+        w.err = d.err;
+        if (w.nbufs == 1) {
             w.single = bufs[lo];
+            if (!bp.fwd && pass == 1)
+                set_l1_maps(w, w.single);
+        }
         w.total_units = pass == 1 ? wv.fgroup_units[g] : wv.fuse_units2;
         tm.begin();
         frag_status st = fuse_launch(d, bp.fwd, pass == 2, w,
@@ -2542,6 +2596,8 @@ frag_status frag_sync_status(frag_stream stream)
         return fail(FRAG_ETIMEOUT, "a bounded wait for a shared-memory stage ran out");
     if (word == 5)
         return fail(FRAG_EDEVICE, "a coefficient did not fit its width in the packed fragments");
+    if (word == 7)
+        return fail(FRAG_ETIMEOUT, "a bounded wait for a TMA box load ran out");
     return fail(FRAG_EDEVICE, "kernel reported inconsistent work descriptor (code %d)", word);
 }
 

@@ -8,6 +8,7 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h> // CUtensorMap (the type only; the library calls the runtime API)
 #include <cuda_runtime.h>
 
 namespace frag {
@@ -262,10 +263,16 @@ struct FuseWork {
     uint32_t cipher;     // some buffer of the launch has `cipher` set
     uint64_t unit_lo;    // the launch runs units unit_lo .. unit_lo + total_units - 1
     uint64_t total_units;
-    int *err;            // device error word (block mode, packed: 5 = a value outside its width)
+    int *err;            // device error word (block mode, packed: 5 = a value outside its width;
+                         // the inverse's TMA loads: 7 = a box that did not arrive in time)
     const uint32_t *key_words; // device: the 4 big-endian AES key words (keyed packed launches)
     const uint32_t *aes_t0;    // device: AES table 0 (256 words), when `cipher`
     AesKeys keys;              // round keys, when `cipher`
+    // the inverse's first pass over a lone buffer (nbufs == 1): TMA maps of
+    // the buffer's three level-1 bands (uint16, rows of W/2, boxes of 4 rows x
+    // 136 values) when l1_tma != 0, else per-lane copies
+    uint32_t l1_tma;
+    CUtensorMap l1_map[3];
 };
 
 // packed: the samples are 16-bit values (v + 0x4000) instead of bytes --

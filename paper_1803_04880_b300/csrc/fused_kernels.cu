@@ -90,14 +90,27 @@ template <bool PK>
 __host__ __device__ constexpr int fwd_stage() { return PK ? kFwdStagePk : kFwdStage; }
 template <bool PK>
 __host__ __device__ constexpr int fwd_depth() { return PK ? kFwdDepthPk : kFwdDepth; }
-// inverse stage: level-1 rows j = 0..3, bands HL/LH/HH, 8 bytes a lane, then
-// region X: level-1 LL rows (one level), or level-2 rows k = 0..1 of the three
-// bands (4 bytes a lane) followed by LL_2 rows (two levels) or the four
-// level-3 words (three levels)
-constexpr int kInvX = 12 * 256;
-constexpr int kInvL2Ll = kInvX + 6 * 128;
-constexpr int kInvL3 = kInvX + 6 * 128;
-constexpr int kInvStage = kInvL3 + 4 * 128;
+// inverse stage: the level-1 bands HL/LH/HH, rows j = 0..3, 8 bytes a lane --
+// with box loads each band a box of 4 rows of 272 bytes (136 int16 from the
+// 16-byte-aligned column just left of the strip's first lane; lane l's 8
+// bytes at 8 + 8 l) on a 128-byte boundary, the layout a TMA box load writes
+// -- then region X: level-1 LL rows (one level), or level-2 rows k = 0..1
+// of the three bands (4 bytes a lane) followed by LL_2 rows (two levels) or
+// the four level-3 words (three levels)
+constexpr int kL1Row = 272;
+constexpr int kL1Box = 9 * 128; // 4 rows of 272 bytes, rounded up to 128
+// BOX: the layout the level-1 box loads need (a launch that uses them);
+// otherwise rows of 256 bytes, lane l's 8 bytes at 8 l, row slot 3 j + k
+template <bool BOX>
+__host__ __device__ constexpr int l1_at(int j, int k) { return BOX ? 8 + kL1Box * k + kL1Row * j : 256 * (3 * j + k); }
+template <bool BOX>
+__host__ __device__ constexpr int inv_x() { return BOX ? 3 * kL1Box : 12 * 256; }
+template <bool BOX>
+__host__ __device__ constexpr int inv_l2ll() { return inv_x<BOX>() + 6 * 128; }
+template <bool BOX>
+__host__ __device__ constexpr int inv_l3() { return inv_x<BOX>() + 6 * 128; }
+template <bool BOX>
+__host__ __device__ constexpr int inv_stage() { return inv_l3<BOX>() + 4 * 128; }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -120,6 +133,44 @@ __device__ __forceinline__ void cp16(uint32_t dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+
+// TMA box loads of the inverse's level-1 bands: one mbarrier a stage and warp
+// (arrival count 1: the issuing lane's expect_tx), completed by the bytes of
+// the stage's three boxes
+constexpr uint32_t kL1TmaBytes = 3 * 4 * kL1Row;
+constexpr uint32_t kTmaSpinLimit = 1u << 22; // polls of a stage's barrier before giving up
+constexpr int kErrTmaWait = 7;               // device error word: a box load that did not arrive
+__device__ __forceinline__ void mbar_init(uint32_t a)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect(uint32_t a, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(a), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// generic-proxy reads of the stage before the async proxy overwrites it
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// box (x, y) of a 2D map into shared memory at dst (128-byte aligned); x a
+// multiple of 8 values (16 bytes)
+__device__ __forceinline__ void tma2d(uint32_t dst, const CUtensorMap *m, int x, int y, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(bar)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait()
@@ -130,7 +181,7 @@ __device__ __forceinline__ void cp_wait()
 // may schedule them freely; they stay after cp.async.wait_group, whose asm
 // clobbers memory.  `a` is a shared-window address like the cp.async
 // destinations.
-extern __shared__ __align__(16) uint8_t g_fuse_smem[];
+extern __shared__ __align__(128) uint8_t g_fuse_smem[];
 __device__ __forceinline__ const uint8_t *ring_ptr(uint32_t a)
 {
     return g_fuse_smem + (a - (uint32_t)__cvta_generic_to_shared(g_fuse_smem));
@@ -803,41 +854,77 @@ __device__ __forceinline__ void fwd_unit(const FuseBuf &b, uint32_t sx, uint32_t
 // int16 word(s) of the input -> biased values
 __device__ __forceinline__ uint32_t in16(uint32_t w) { return from_i16x2(w); }
 
-// the coefficient rows iteration t consumes, into its stage
+// every row iteration t reads inside its level: no per-row tests
 template <int FL>
-__device__ __forceinline__ void inv_issue(const FuseBuf &b, const Lane &ln, int t, int t_end,
-                                          uint32_t ring8, uint32_t ring4)
+__device__ __forceinline__ bool inv_inside(const FuseBuf &b, int t)
 {
+    const int F = FL ? FL : (int)b.F;
+    return t >= 1 && 4 * t < (int)(b.H >> 1) && (F < 2 || 2 * t < (int)(b.H >> 2)) &&
+           (F < 3 || t < (int)(b.H >> 3));
+}
+
+// The level-1 box loads of a lone buffer's first inverse pass: in an
+// iteration whose rows are all inside, lane 0 loads the three level-1 bands'
+// rows as three TMA boxes into the stage (the bytes the per-lane copies would
+// write, and the lanes outside the matrix read zeros) and the lanes wait on
+// the stage's barrier instead of copying them.
+struct Tma {
+    const CUtensorMap *map; // the three level-1 band maps (nullptr: per-lane copies)
+    uint32_t ring;          // the warp's stage ring (128-byte aligned)
+    uint32_t bar;           // the warp's barriers, one a stage
+    int x0;                 // box origin: the level-1 column 4 left of lane 0's first
+    bool leader;            // lane 0
+};
+
+// the coefficient rows iteration t consumes, into its stage
+template <int FL, bool BOX>
+__device__ __forceinline__ void inv_issue(const FuseBuf &b, const Lane &ln, int t, int t_end,
+                                          uint32_t ring8, uint32_t ring4, const Tma &tm)
+{
+    const bool inside = inv_inside<FL>(b, t);
+    const bool box = BOX && tm.map != nullptr && t < t_end && inside;
+    if (box) {
+        // every lane has read the stage's last contents (iteration t - 2)
+        __syncwarp();
+        if (tm.leader) {
+            const uint32_t st = (uint32_t)(t % kInvDepth);
+            const uint32_t bar = tm.bar + 8u * st;
+            fence_proxy_async();
+            mbar_expect(bar, kL1TmaBytes);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                tma2d(tm.ring + st * inv_stage<BOX>() + kL1Box * k, tm.map + k, tm.x0, 4 * t - 3, bar);
+        }
+    }
     if (t < t_end && ln.loads) {
         const int F = FL ? FL : (int)b.F;
-        const uint32_t so = (uint32_t)(t % kInvDepth) * kInvStage;
+        const uint32_t so = (uint32_t)(t % kInvDepth) * inv_stage<BOX>();
         const uint32_t W1 = b.W >> 1, H1 = b.H >> 1, W2 = b.W >> 2, H2 = b.H >> 2;
         const uint32_t c1 = (uint32_t)ln.c0 >> 1, c2 = (uint32_t)ln.c0 >> 2;
-        // every row of the iteration inside its level: no per-row tests
-        const bool inside = t >= 1 && 4 * t < (int)H1 && (F < 2 || 2 * t < (int)H2) &&
-                            (F < 3 || t < (int)(b.H >> 3));
         if (inside) {
             const uint64_t o1 = 2ull * ((uint64_t)(4 * t - 3) * W1 + c1);
+            if (!box) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    cp8(ring8 + so + 256 * (3 * j + k), b.band[0][k] + o1 + 2ull * j * W1, 8);
+                    for (int k = 0; k < 3; ++k)
+                        cp8(ring8 + so + l1_at<BOX>(j, k), b.band[0][k] + o1 + 2ull * j * W1, 8);
+            }
             if (F == 1) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    cp8(ring8 + so + kInvX + 256 * j, b.ll + o1 + 2ull * j * W1, 8);
+                    cp8(ring8 + so + inv_x<BOX>() + 256 * j, b.ll + o1 + 2ull * j * W1, 8);
             } else {
                 const uint64_t o2 = 2ull * ((uint64_t)(2 * t - 1) * W2 + c2);
 #pragma unroll
                 for (int k = 0; k < 2; ++k)
 #pragma unroll
                     for (int m = 0; m < 3; ++m)
-                        cp4(ring4 + so + kInvX + 128 * (3 * k + m), b.band[1][m] + o2 + 2ull * k * W2, 4);
+                        cp4(ring4 + so + inv_x<BOX>() + 128 * (3 * k + m), b.band[1][m] + o2 + 2ull * k * W2, 4);
                 if (F == 2) {
 #pragma unroll
                     for (int k = 0; k < 2; ++k)
-                        cp4(ring4 + so + kInvL2Ll + 128 * k, b.ll + o2 + 2ull * k * W2, 4);
+                        cp4(ring4 + so + inv_l2ll<BOX>() + 128 * k, b.ll + o2 + 2ull * k * W2, 4);
                 }
             }
         } else {
@@ -849,9 +936,9 @@ __device__ __forceinline__ void inv_issue(const FuseBuf &b, const Lane &ln, int 
                     const uint64_t o = off + 2ull * j * W1;
 #pragma unroll
                     for (int k = 0; k < 3; ++k)
-                        cp8(ring8 + so + 256 * (3 * j + k), b.band[0][k] + o, 8);
+                        cp8(ring8 + so + l1_at<BOX>(j, k), b.band[0][k] + o, 8);
                     if (F == 1)
-                        cp8(ring8 + so + kInvX + 256 * j, b.ll + o, 8);
+                        cp8(ring8 + so + inv_x<BOX>() + 256 * j, b.ll + o, 8);
                 }
             }
             if (F >= 2) {
@@ -863,9 +950,9 @@ __device__ __forceinline__ void inv_issue(const FuseBuf &b, const Lane &ln, int 
                         const uint64_t o = off2 + 2ull * k * W2;
 #pragma unroll
                         for (int m = 0; m < 3; ++m)
-                            cp4(ring4 + so + kInvX + 128 * (3 * k + m), b.band[1][m] + o, 4);
+                            cp4(ring4 + so + inv_x<BOX>() + 128 * (3 * k + m), b.band[1][m] + o, 4);
                         if (F == 2)
-                            cp4(ring4 + so + kInvL2Ll + 128 * k, b.ll + o, 4);
+                            cp4(ring4 + so + inv_l2ll<BOX>() + 128 * k, b.ll + o, 4);
                     }
                 }
             }
@@ -878,8 +965,8 @@ __device__ __forceinline__ void inv_issue(const FuseBuf &b, const Lane &ln, int 
             const uint32_t bytes = (e & 1ull) ? 4u : 2u;
 #pragma unroll
             for (int m = 0; m < 3; ++m)
-                cp4(ring4 + so + kInvL3 + 128 * m, b.band[2][m] + off, bytes);
-            cp4(ring4 + so + kInvL3 + 128 * 3, b.ll + off, bytes);
+                cp4(ring4 + so + inv_l3<BOX>() + 128 * m, b.band[2][m] + off, bytes);
+            cp4(ring4 + so + inv_l3<BOX>() + 128 * 3, b.ll + off, bytes);
         }
     }
     cp_commit();
@@ -921,7 +1008,7 @@ struct InvState {
     uint32_t x3, d3;
 };
 
-template <bool CHECK, bool PK, bool CIPH, int FL>
+template <bool CHECK, bool PK, bool CIPH, int FL, bool BOX>
 __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t, uint32_t s8,
                                          uint32_t s4, bool store, bool whole, InvState &S, const Ks &K)
 {
@@ -936,10 +1023,10 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
     if (F == 3) {
         const uint64_t e3 = (uint64_t)t * (uint64_t)W3 + (uint64_t)(ln.c0 >> 3);
         const uint32_t sh = 16u * (uint32_t)(e3 & 1ull);
-        const uint32_t hl = (lds4(s4 + kInvL3) >> sh) & 0xffffu;
-        const uint32_t lh = (lds4(s4 + kInvL3 + 128) >> sh) & 0xffffu;
-        const uint32_t hh = (lds4(s4 + kInvL3 + 256) >> sh) & 0xffffu;
-        uint32_t ll = (lds4(s4 + kInvL3 + 384) >> sh) & 0xffffu;
+        const uint32_t hl = (lds4(s4 + inv_l3<BOX>()) >> sh) & 0xffffu;
+        const uint32_t lh = (lds4(s4 + inv_l3<BOX>() + 128) >> sh) & 0xffffu;
+        const uint32_t hh = (lds4(s4 + inv_l3<BOX>() + 256) >> sh) & 0xffffu;
+        uint32_t ll = (lds4(s4 + inv_l3<BOX>() + 384) >> sh) & 0xffffu;
         if (ciph)
             ll ^= lds2(ks_at(K, (uint64_t)t, e3));
         const uint32_t s = b.ll_final ? in16(ll | (hl << 16)) + 0x80u
@@ -957,20 +1044,20 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int q2 = 2 * t - 1 + k;
-            const uint32_t hl = q_i16(lds4(s4 + kInvX + 128 * (3 * k))); // store-ready
-            const uint32_t lh = q_i16(lds4(s4 + kInvX + 128 * (3 * k + 1)));
-            const uint32_t hh = q_i16(lds4(s4 + kInvX + 128 * (3 * k + 2)));
+            const uint32_t hl = q_i16(lds4(s4 + inv_x<BOX>() + 128 * (3 * k))); // store-ready
+            const uint32_t lh = q_i16(lds4(s4 + inv_x<BOX>() + 128 * (3 * k + 1)));
+            const uint32_t hh = q_i16(lds4(s4 + inv_x<BOX>() + 128 * (3 * k + 2)));
             uint32_t ll;
             if (F == 3) {
                 ll = z[k];
             } else if (b.ll_final) {
-                uint32_t c = lds4(s4 + kInvL2Ll + 128 * k);
+                uint32_t c = lds4(s4 + inv_l2ll<BOX>() + 128 * k);
                 if (ciph)
                     c ^= lds4(ks_at(K, (uint64_t)q2,
                                     (uint64_t)q2 * (uint64_t)(W >> 2) + (uint64_t)(ln.c0 >> 2)));
                 ll = in16(c) + llb;
             } else {
-                ll = lds4(s4 + kInvL2Ll + 128 * k);
+                ll = lds4(s4 + inv_l2ll<BOX>() + 128 * k);
             }
             uint32_t oL, eL, oH, eH;
             col_inv<CHECK, false, true>(ll, lh, q2 == 0, q2 == H2, S.x2[0], S.d2[0], oL, eL);
@@ -984,12 +1071,12 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int q = 4 * t - 3 + j;
-        const uint2 hl = lds8(s8 + 256 * (3 * j));
-        const uint2 lh = lds8(s8 + 256 * (3 * j + 1));
-        const uint2 hh = lds8(s8 + 256 * (3 * j + 2));
+        const uint2 hl = lds8(s8 + l1_at<BOX>(j, 0));
+        const uint2 lh = lds8(s8 + l1_at<BOX>(j, 1));
+        const uint2 hh = lds8(s8 + l1_at<BOX>(j, 2));
         uint32_t s[4], d[4];
         if (F == 1) {
-            uint2 ll = lds8(s8 + kInvX + 256 * j);
+            uint2 ll = lds8(s8 + inv_x<BOX>() + 256 * j);
             if (ciph) {
                 const uint2 k = lds8(ks_at(K, (uint64_t)q, (uint64_t)q * (uint64_t)(W >> 1) + (uint64_t)(ln.c0 >> 1)));
                 ll.x ^= k.x;
@@ -1047,7 +1134,7 @@ __device__ __forceinline__ void inv_iter(const FuseBuf &b, const Lane &ln, int t
 // coefficient row in the iteration, whose d[q-1] is the row before it,
 // loaded in the same iteration (level 3: the d preloaded at the unit's
 // start); level 2 hands down its row-inversed even row, LL_1 row 4t.
-template <bool CIPH, int FL>
+template <bool CIPH, int FL, bool BOX>
 __device__ __forceinline__ void inv_warm(const FuseBuf &b, const Lane &ln, int t, uint32_t s8, uint32_t s4,
                                          InvState &S, const Ks &K)
 {
@@ -1059,10 +1146,10 @@ __device__ __forceinline__ void inv_warm(const FuseBuf &b, const Lane &ln, int t
     if (F == 3) { // level-3 row t
         const uint64_t e3 = (uint64_t)t * (uint64_t)(b.W >> 3) + (uint64_t)(ln.c0 >> 3);
         const uint32_t sh = 16u * (uint32_t)(e3 & 1ull);
-        const uint32_t hl = (lds4(s4 + kInvL3) >> sh) & 0xffffu;
-        const uint32_t lh = (lds4(s4 + kInvL3 + 128) >> sh) & 0xffffu;
-        const uint32_t hh = (lds4(s4 + kInvL3 + 256) >> sh) & 0xffffu;
-        uint32_t ll = (lds4(s4 + kInvL3 + 384) >> sh) & 0xffffu;
+        const uint32_t hl = (lds4(s4 + inv_l3<BOX>()) >> sh) & 0xffffu;
+        const uint32_t lh = (lds4(s4 + inv_l3<BOX>() + 128) >> sh) & 0xffffu;
+        const uint32_t hh = (lds4(s4 + inv_l3<BOX>() + 256) >> sh) & 0xffffu;
+        uint32_t ll = (lds4(s4 + inv_l3<BOX>() + 384) >> sh) & 0xffffu;
         if (ciph)
             ll ^= lds2(ks_at(K, (uint64_t)t, e3));
         const uint32_t s = b.ll_final ? in16(ll | (hl << 16)) + 0x80u
@@ -1073,22 +1160,22 @@ __device__ __forceinline__ void inv_warm(const FuseBuf &b, const Lane &ln, int t
         z1 = unlift2(S.x3, ln.first, ln.last);
     }
     if (F >= 2) { // level-2 row 2t; d[-1] from row 2t-1
-        const uint32_t lh0 = q_i16(lds4(s4 + kInvX + 128 * 1));
-        const uint32_t hh0 = q_i16(lds4(s4 + kInvX + 128 * 2));
-        const uint32_t hl1 = q_i16(lds4(s4 + kInvX + 128 * 3));
-        const uint32_t lh1 = q_i16(lds4(s4 + kInvX + 128 * 4));
-        const uint32_t hh1 = q_i16(lds4(s4 + kInvX + 128 * 5));
+        const uint32_t lh0 = q_i16(lds4(s4 + inv_x<BOX>() + 128 * 1));
+        const uint32_t hh0 = q_i16(lds4(s4 + inv_x<BOX>() + 128 * 2));
+        const uint32_t hl1 = q_i16(lds4(s4 + inv_x<BOX>() + 128 * 3));
+        const uint32_t lh1 = q_i16(lds4(s4 + inv_x<BOX>() + 128 * 4));
+        const uint32_t hh1 = q_i16(lds4(s4 + inv_x<BOX>() + 128 * 5));
         uint32_t ll;
         if (F == 3) {
             ll = z1;
         } else if (b.ll_final) {
-            uint32_t c = lds4(s4 + kInvL2Ll + 128);
+            uint32_t c = lds4(s4 + inv_l2ll<BOX>() + 128);
             if (ciph)
                 c ^= lds4(ks_at(K, (uint64_t)(2 * t),
                                 (uint64_t)(2 * t) * (uint64_t)(b.W >> 2) + (uint64_t)(ln.c0 >> 2)));
             ll = in16(c) + llb;
         } else {
-            ll = lds4(s4 + kInvL2Ll + 128);
+            ll = lds4(s4 + inv_l2ll<BOX>() + 128);
         }
         const uint32_t eL = ll - pq4q(lh0, lh1) + 0x20002000u;
         const uint32_t eH = hl1 - pq4q(hh0, hh1) - 0x20002000u;
@@ -1099,11 +1186,11 @@ __device__ __forceinline__ void inv_warm(const FuseBuf &b, const Lane &ln, int t
         unlift4(eL, eH, ln.sR, ln.sL, y3[0], y3[1]);
     }
     // level-1 row 4t (pair j = 3); d[-1] from row 4t-1 (j = 2)
-    const uint2 lh2 = lds8(s8 + 256 * 7), hh2 = lds8(s8 + 256 * 8);
-    const uint2 hl3 = lds8(s8 + 256 * 9), lh3 = lds8(s8 + 256 * 10), hh3 = lds8(s8 + 256 * 11);
+    const uint2 lh2 = lds8(s8 + l1_at<BOX>(2, 1)), hh2 = lds8(s8 + l1_at<BOX>(2, 2));
+    const uint2 hl3 = lds8(s8 + l1_at<BOX>(3, 0)), lh3 = lds8(s8 + l1_at<BOX>(3, 1)), hh3 = lds8(s8 + l1_at<BOX>(3, 2));
     uint32_t s[4];
     if (F == 1) {
-        uint2 ll = lds8(s8 + kInvX + 256 * 3);
+        uint2 ll = lds8(s8 + inv_x<BOX>() + 256 * 3);
         if (ciph) {
             const uint2 k = lds8(ks_at(K, (uint64_t)(4 * t),
                                        (uint64_t)(4 * t) * (uint64_t)(b.W >> 1) + (uint64_t)(ln.c0 >> 1)));
@@ -1128,10 +1215,13 @@ __device__ __forceinline__ void inv_warm(const FuseBuf &b, const Lane &ln, int t
     }
 }
 
-template <bool PK, bool CIPH, int FL>
-__device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t sy, uint32_t ring_lane8,
+// tm: the level-1 box loads (tm.map nullptr: none); tph: the phase bit of
+// each stage barrier (kept across the warp's units).  False: a box load did
+// not arrive within the spin limit (error word set); the warp stops.
+template <bool PK, bool CIPH, int FL, bool BOX>
+__device__ __forceinline__ bool inv_unit(const FuseBuf &b, uint32_t sx, uint32_t sy, uint32_t ring_lane8,
                                          uint32_t ring_lane4, int lane, uint32_t ks_ring, const uint32_t *tel,
-                                         const AesKeys &keys)
+                                         const AesKeys &keys, const Tma &tm, uint32_t &tph, int *err)
 {
     const Lane ln = make_lane(b, sx, lane);
     const int F = FL ? FL : (int)b.F;
@@ -1153,7 +1243,7 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
 
 #pragma unroll
     for (int k = 0; k < kInvDepth - 1; ++k)
-        inv_issue<FL>(b, ln, t_first + k, t_end, ring_lane8, ring_lane4);
+        inv_issue<FL, BOX>(b, ln, t_first + k, t_end, ring_lane8, ring_lane4, tm);
 
     InvState S; // zeros, in each word's form
 #pragma unroll
@@ -1171,25 +1261,40 @@ __device__ __forceinline__ void inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
     }
 
     for (int t = t_first; t < t_end; ++t) {
-        inv_issue<FL>(b, ln, t + kInvDepth - 1, t_end, ring_lane8, ring_lane4);
+        inv_issue<FL, BOX>(b, ln, t + kInvDepth - 1, t_end, ring_lane8, ring_lane4, tm);
         if (CIPH && b.cipher)
             ks_fill(K, (uint32_t)((uint64_t)(R * t + 1) - K.r_first) * K.nb, tel, keys, b.nonce, lane);
         cp_wait<kInvDepth - 1>();
-        const uint32_t so = (uint32_t)(t % kInvDepth) * kInvStage;
+        if (BOX && tm.map != nullptr && inv_inside<FL>(b, t)) {
+            const uint32_t st = (uint32_t)(t % kInvDepth);
+            const uint32_t bar = tm.bar + 8u * st, par = (tph >> st) & 1u;
+            // the lanes poll together, so they agree on the outcome
+            uint32_t polls = 0;
+            while (!__all_sync(0xffffffffu, mbar_try(bar, par)))
+                if (++polls == kTmaSpinLimit) {
+                    if (err != nullptr && tm.leader)
+                        atomicCAS(err, 0, kErrTmaWait);
+                    cp_wait<0>();
+                    return false;
+                }
+            tph ^= 1u << st;
+        }
+        const uint32_t so = (uint32_t)(t % kInvDepth) * inv_stage<BOX>();
         const bool store = ln.own && t >= t_begin;
         const bool whole = 8 * t < (int)b.full_rows; // rows 8t-7 .. 8t hold only data
         // the unchecked iteration stores whole rows only; an iteration over
         // the last, partial row of the data takes the checked one
         if (t >= 1 && t < t_fast_end && (PK || whole || t < t_begin)) {
             if (t < t_begin)
-                inv_warm<CIPH, FL>(b, ln, t, ring_lane8 + so, ring_lane4 + so, S, K);
+                inv_warm<CIPH, FL, BOX>(b, ln, t, ring_lane8 + so, ring_lane4 + so, S, K);
             else
-                inv_iter<false, PK, CIPH, FL>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S, K);
+                inv_iter<false, PK, CIPH, FL, BOX>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S, K);
         } else {
-            inv_iter<true, PK, CIPH, FL>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S, K);
+            inv_iter<true, PK, CIPH, FL, BOX>(b, ln, t, ring_lane8 + so, ring_lane4 + so, store, whole, S, K);
         }
     }
     cp_wait<0>();
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -1214,32 +1319,75 @@ __device__ __forceinline__ const FuseBuf *unit_buf(const FuseWork &w, uint64_t u
 }
 
 // shared memory of a block: every warp's stage ring, then (launches that
-// encipher) the lane-replicated AES table and every warp's keystream ring
-template <bool FWD, bool PK>
+// encipher) the lane-replicated AES table and every warp's keystream ring,
+// then (launches with level-1 box loads, BOX) two stage barriers a warp
+template <bool FWD, bool PK, bool BOX = false>
 __host__ __device__ constexpr uint32_t stage_ring_bytes()
 {
-    return FWD ? fwd_depth<PK>() * fwd_stage<PK>() : kInvDepth * kInvStage;
+    return FWD ? fwd_depth<PK>() * fwd_stage<PK>() : kInvDepth * inv_stage<BOX>();
+}
+
+// CIPH: the launch enciphers some buffer's LL (table and keystream rings);
+// the others leave that shared memory to L1
+template <bool FWD, bool PK, bool CIPH>
+__host__ __device__ constexpr size_t bar_offset(bool box)
+{
+    return (size_t)cta_warps<FWD, PK, CIPH>() * (box ? stage_ring_bytes<FWD, PK, true>() : stage_ring_bytes<FWD, PK>()) +
+           (CIPH ? (size_t)kTableBytes + (size_t)cta_warps<FWD, PK, CIPH>() * kKsBytes : 0);
+}
+template <bool FWD, bool PK, bool CIPH>
+__host__ __device__ constexpr size_t smem_bytes(bool box)
+{
+    return bar_offset<FWD, PK, CIPH>(box) + (box ? (size_t)16 * cta_warps<FWD, PK, CIPH>() : 0);
+}
+// the most a launch of the kernel takes (the attribute and the occupancy)
+template <bool FWD, bool PK, bool CIPH>
+__host__ __device__ constexpr size_t smem_max()
+{
+    return smem_bytes<FWD, PK, CIPH>(!FWD && !PK);
 }
 
 template <bool FWD, bool PK, bool CIPH>
 __global__ void __launch_bounds__(32 * cta_warps<FWD, PK, CIPH>(), 16 / cta_warps<FWD, PK, CIPH>())
-    fuse_kernel(FuseWork w)
+    fuse_kernel(const __grid_constant__ FuseWork w)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     // the next kernel (the CTR pass after a protect) may start its
     // data-independent part now; it waits for this grid before reading
     grid_release();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int kWarps = cta_warps<FWD, PK, CIPH>();
-    constexpr uint32_t kStages = (uint32_t)kWarps * stage_ring_bytes<FWD, PK>();
+    // the launch's level-1 box loads (a lone buffer's first inverse pass)
+    // take the larger box-layout rings
+    const bool box = !FWD && !PK && w.l1_tma != 0;
+    const uint32_t rstride = box ? stage_ring_bytes<FWD, PK, true>() : stage_ring_bytes<FWD, PK>();
+    const uint32_t kStages = (uint32_t)kWarps * rstride;
     uint32_t *te = reinterpret_cast<uint32_t *>(smem + kStages);
     if (CIPH) { // some buffer of the launch enciphers its LL here
         aes::build_table(te, w.aes_t0);
         __syncthreads();
     }
-    const uint32_t ring = smem_addr(smem) + (uint32_t)warp * stage_ring_bytes<FWD, PK>();
+    const uint32_t ring = smem_addr(smem) + (uint32_t)warp * rstride;
     const uint32_t ks_ring = smem_addr(smem) + kStages + (uint32_t)kTableBytes + (uint32_t)warp * kKsBytes;
     const uint32_t *tel = te + lane;
+    // the level-1 box loads of a lone buffer's first inverse pass: the warp's
+    // two stage barriers after the rings (the boxes need a 128-byte aligned
+    // ring; otherwise the lanes copy their own bytes)
+    Tma tm = {};
+    uint32_t tph = 0;
+    if (box) {
+        tm.bar = smem_addr(smem) + (uint32_t)bar_offset<FWD, PK, CIPH>(true) + 16u * (uint32_t)warp;
+        tm.ring = ring;
+        tm.leader = lane == 0;
+        if (lane == 0) {
+            mbar_init(tm.bar);
+            mbar_init(tm.bar + 8);
+            mbar_init_fence();
+        }
+        __syncwarp();
+        if ((ring & 127u) == 0)
+            tm.map = w.l1_map;
+    }
     const uint64_t G = (uint64_t)gridDim.x * kWarps;
     const uint64_t u_end = w.unit_lo + w.total_units;
     for (uint64_t u = w.unit_lo + (uint64_t)blockIdx.x * kWarps + warp; u < u_end; u += G) {
@@ -1257,30 +1405,42 @@ __global__ void __launch_bounds__(32 * cta_warps<FWD, PK, CIPH>(), 16 / cta_warp
             fwd_unit<PK, CIPH, 0>(b, sx, sy, ring + (PK ? 16u : 8u) * lane, lane, ks_ring, tel, w.keys);
         } else {
             const uint32_t r8 = ring + 8u * lane, r4 = ring + 4u * lane;
-            if (b.F == 1)
-                inv_unit<PK, CIPH, 1>(b, sx, sy, r8, r4, lane, ks_ring, tel, w.keys);
-            else if (b.F == 2)
-                inv_unit<PK, CIPH, 2>(b, sx, sy, r8, r4, lane, ks_ring, tel, w.keys);
-            else
-                inv_unit<PK, CIPH, 3>(b, sx, sy, r8, r4, lane, ks_ring, tel, w.keys);
+            // the box starts 4 level-1 columns left of lane 0's first (the
+            // strip's halo lane), on a 16-byte boundary with one lane of halo
+            Tma tu = tm;
+            if (tu.map != nullptr) {
+                const int c00 = (int)sx * 8 * (31 - (int)b.halo) - 8 * (int)b.halo;
+                tu.x0 = (c00 >> 1) - 4;
+                if ((tu.x0 & 7) != 0)
+                    tu.map = nullptr;
+            }
+            bool ok = true;
+            if (tu.map == nullptr) {
+                if (b.F == 1)
+                    inv_unit<PK, CIPH, 1, false>(b, sx, sy, r8, r4, lane, ks_ring, tel, w.keys, tu, tph, w.err);
+                else if (b.F == 2)
+                    inv_unit<PK, CIPH, 2, false>(b, sx, sy, r8, r4, lane, ks_ring, tel, w.keys, tu, tph, w.err);
+                else
+                    inv_unit<PK, CIPH, 3, false>(b, sx, sy, r8, r4, lane, ks_ring, tel, w.keys, tu, tph, w.err);
+            } else if (!PK) {
+                if (b.F == 1)
+                    ok = inv_unit<PK, CIPH, 1, true>(b, sx, sy, r8, r4, lane, ks_ring, tel, w.keys, tu, tph, w.err);
+                else if (b.F == 2)
+                    ok = inv_unit<PK, CIPH, 2, true>(b, sx, sy, r8, r4, lane, ks_ring, tel, w.keys, tu, tph, w.err);
+                else
+                    ok = inv_unit<PK, CIPH, 3, true>(b, sx, sy, r8, r4, lane, ks_ring, tel, w.keys, tu, tph, w.err);
+            }
+            if (!ok)
+                return;
         }
     }
-}
-
-// CIPH: the launch enciphers some buffer's LL (table and keystream rings);
-// the others leave that shared memory to L1
-template <bool FWD, bool PK, bool CIPH>
-constexpr size_t smem_bytes()
-{
-    constexpr int warps = cta_warps<FWD, PK, CIPH>();
-    return (size_t)warps * stage_ring_bytes<FWD, PK>() + (CIPH ? (size_t)kTableBytes + (size_t)warps * kKsBytes : 0);
 }
 
 template <bool FWD, bool PK, bool CIPH>
 cudaError_t set_attr()
 {
     static std::atomic<uint64_t> done{0};
-    return smem_attr_once((const void *)fuse_kernel<FWD, PK, CIPH>, (int)smem_bytes<FWD, PK, CIPH>(), done);
+    return smem_attr_once((const void *)fuse_kernel<FWD, PK, CIPH>, (int)smem_max<FWD, PK, CIPH>(), done);
 }
 
 template <bool FWD, bool PK, bool CIPH>
@@ -1291,7 +1451,7 @@ cudaError_t launch(const FuseWork &w, uint32_t grid, cudaStream_t stream)
         return e;
     // an ordinary launch (its loads go through L1, so it starts only once
     // the kernel before it has finished)
-    fuse_kernel<FWD, PK, CIPH><<<grid, 32 * cta_warps<FWD, PK, CIPH>(), smem_bytes<FWD, PK, CIPH>(), stream>>>(w);
+    fuse_kernel<FWD, PK, CIPH><<<grid, 32 * cta_warps<FWD, PK, CIPH>(), smem_bytes<FWD, PK, CIPH>(!FWD && !PK && w.l1_tma != 0), stream>>>(w);
     return cudaGetLastError();
 }
 
@@ -1311,7 +1471,7 @@ cudaError_t shape(int *ctas_per_sm, int *warps_per_cta)
     *warps_per_cta = cta_warps<FWD, PK, CIPH>();
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, (const void *)fuse_kernel<FWD, PK, CIPH>,
                                                          32 * cta_warps<FWD, PK, CIPH>(),
-                                                         smem_bytes<FWD, PK, CIPH>());
+                                                         smem_max<FWD, PK, CIPH>());
 }
 
 } // namespace fuse
