@@ -1360,6 +1360,15 @@ __global__ void __launch_bounds__(32 * cta_warps<FWD, PK, CIPH>(), 16 / cta_warp
     // the launch's level-1 box loads (a lone buffer's first inverse pass)
     // take the larger box-layout rings
     const bool box = !FWD && !PK && w.l1_tma != 0;
+    // a launch whose shared memory is smaller than this layout records an
+    // inconsistent descriptor (code 2) and does nothing
+    uint32_t dyn_smem;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
+    if (dyn_smem < (uint32_t)smem_bytes<FWD, PK, CIPH>(box)) {
+        if (threadIdx.x == 0 && w.err != nullptr)
+            atomicCAS(w.err, 0, 2);
+        return;
+    }
     const uint32_t rstride = box ? stage_ring_bytes<FWD, PK, true>() : stage_ring_bytes<FWD, PK>();
     const uint32_t kStages = (uint32_t)kWarps * rstride;
     uint32_t *te = reinterpret_cast<uint32_t *>(smem + kStages);
