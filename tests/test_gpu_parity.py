@@ -466,3 +466,22 @@ def test_batch_of_large_private_fragments(fr, key):
     plan, nonce, t = singles[-1]
     p_ref, u_ref = oracle.protect(t.cpu().numpy(), 256, 1, KEY, nonce)
     assert np.array_equal(entries[-1][4].cpu().numpy(), p_ref)
+
+
+# The recover of a lone buffer of 1-2 levels whose width is a multiple of 16
+# and at least 272 loads its level-1 bands as TMA boxes (4 rows x 136 int16,
+# starting 4 columns left of a strip's first lane): the narrowest such width
+# (two boxes' worth), a last strip much shorter than the others, two or three
+# level-1 row pairs, rows cut short by the end of the data, and two shapes
+# whose band bases miss the 16-byte boundary (272 x 12 and 2064 x 20 rows at
+# two levels), which fall back to per-lane copies.
+BOX_CASES = [(272 * 8, 272, 1), (288 * 40 + 17, 288, 1), (1040 * 40, 1040, 2), (1040 * 37, 1040, 2),
+             (4112 * 64 - 3, 4112, 2), (496 * 24, 496, 2), (2048 * 8, 2048, 1), (272 * 9 + 5, 272, 2),
+             (2064 * 16 + 1, 2064, 2)]
+
+
+@pytest.mark.parametrize("path", [0, 2])
+@pytest.mark.parametrize("n,W,L", BOX_CASES)
+def test_level1_box_loads(fr, key, n, W, L, path):
+    data = wl.random_bytes(n, seed=3 * n + W)
+    check_against_oracle(fr, key, data, W, L, nonce=n % 5, path=path)
