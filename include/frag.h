@@ -459,6 +459,14 @@ frag_status frag_sync_status(frag_stream stream);
  * FRAG_ETIMEOUT.  FRAG_EINVAL if polls is 0. */
 frag_status frag_check_wait_timeout(uint32_t polls, frag_stream stream);
 
+/* The same for the wait of the fused kernel's TMA box loads: enqueues on
+ * `stream` one wait, with that wait's code, on a shared-memory stage barrier
+ * armed for 16 bytes that no copy delivers, bounded at `polls` polls of the
+ * barrier; the next frag_sync_status on the stream then returns
+ * FRAG_ETIMEOUT ("a bounded wait for a TMA box load ran out").  FRAG_EINVAL
+ * if polls is 0. */
+frag_status frag_check_box_wait_timeout(uint32_t polls, frag_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

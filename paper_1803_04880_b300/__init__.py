@@ -32,7 +32,7 @@ EXPORTS = [
     "frag_protect_batch", "frag_recover_batch", "frag_batch_create_protect",
     "frag_batch_create_recover", "frag_batch_run", "frag_batch_destroy", "frag_batch_info",
     "frag_batch_set_timing", "frag_batch_launch_times",
-    "frag_get_error", "frag_check_wait_timeout",
+    "frag_get_error", "frag_check_wait_timeout", "frag_check_box_wait_timeout",
     "frag_sync_status", "frag_protect_batch_noalloc", "frag_noalloc_sync_status",
     "frag_server_create", "frag_server_stop", "frag_server_destroy", "frag_server_submit_protect",
     "frag_server_submit_recover", "frag_server_wait", "frag_server_release", "frag_server_hold",
@@ -123,6 +123,7 @@ def lib():
         "frag_get_error": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
         "frag_sync_status": ([vp], ctypes.c_int),
         "frag_check_wait_timeout": ([u32, vp], ctypes.c_int),
+        "frag_check_box_wait_timeout": ([u32, vp], ctypes.c_int),
         "frag_protect_batch_noalloc": ([ctypes.POINTER(frag_item), u32, ctypes.c_char_p, vp],
                                        ctypes.c_int),
         "frag_noalloc_sync_status": ([vp], ctypes.c_int),
@@ -432,3 +433,9 @@ def sync_status(stream=None) -> None:
 def check_wait_timeout(polls: int = 2000, stream=None) -> None:
     """Enqueue one bounded wait that is bound to run out (see frag.h)."""
     check(lib().frag_check_wait_timeout(polls, _stream(stream)))
+
+
+def check_box_wait_timeout(polls: int = 2000, stream=None) -> None:
+    """Enqueue the box loads' bounded wait on a barrier nothing completes
+    (see frag.h)."""
+    check(lib().frag_check_box_wait_timeout(polls, _stream(stream)))

@@ -2622,4 +2622,18 @@ frag_status frag_check_wait_timeout(uint32_t polls, frag_stream stream)
     return st;
 }
 
+frag_status frag_check_box_wait_timeout(uint32_t polls, frag_stream stream)
+{
+    if (polls == 0)
+        return fail(FRAG_EINVAL, "polls must be positive");
+    DeviceState *d = nullptr;
+    frag_status st = device_state(&d, nullptr);
+    if (st != FRAG_OK)
+        return st;
+    cudaError_t e = frag::launch_box_stall_probe(polls, d->err, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "box wait probe launch");
+    return FRAG_OK;
+}
+
 } // extern "C"

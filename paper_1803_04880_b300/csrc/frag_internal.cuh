@@ -150,6 +150,9 @@ cudaError_t launch_dag(bool fwd, const DagWork &w, uint32_t grid, cudaStream_t s
 cudaError_t dag_occupancy(bool fwd, int *blocks_per_sm);
 cudaError_t launch_stall_probe(const unsigned *ctr, uint32_t spin_limit, int *err,
                                cudaStream_t stream);
+// fused kernels (fused_kernels.cu): the box loads' bounded wait on a barrier
+// nothing completes
+cudaError_t launch_box_stall_probe(uint32_t limit, int *err, cudaStream_t stream);
 constexpr int kStripCols = 240;          // level-(l-1) columns owned by one warp strip
 constexpr uint32_t kTileStrips = 4;      // warp strips (consumer warps) of one tile unit
 constexpr uint32_t kCipherBlocks = 512;  // AES blocks of one cipher unit

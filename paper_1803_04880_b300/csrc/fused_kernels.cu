@@ -160,6 +160,17 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity)
                  : "memory");
     return ok != 0;
 }
+// the lanes of a warp poll a stage barrier together until its phase `par`
+// completes, at most `limit` polls (so they agree on the outcome); false: it
+// did not complete
+__device__ __forceinline__ bool box_wait(uint32_t bar, uint32_t par, uint32_t limit)
+{
+    uint32_t polls = 0;
+    while (!__all_sync(0xffffffffu, mbar_try(bar, par)))
+        if (++polls == limit)
+            return false;
+    return true;
+}
 // generic-proxy reads of the stage before the async proxy overwrites it
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 // box (x, y) of a 2D map into shared memory at dst (128-byte aligned); x a
@@ -1268,15 +1279,12 @@ __device__ __forceinline__ bool inv_unit(const FuseBuf &b, uint32_t sx, uint32_t
         if (BOX && tm.map != nullptr && inv_inside<FL>(b, t)) {
             const uint32_t st = (uint32_t)(t % kInvDepth);
             const uint32_t bar = tm.bar + 8u * st, par = (tph >> st) & 1u;
-            // the lanes poll together, so they agree on the outcome
-            uint32_t polls = 0;
-            while (!__all_sync(0xffffffffu, mbar_try(bar, par)))
-                if (++polls == kTmaSpinLimit) {
-                    if (err != nullptr && tm.leader)
-                        atomicCAS(err, 0, kErrTmaWait);
-                    cp_wait<0>();
-                    return false;
-                }
+            if (!box_wait(bar, par, kTmaSpinLimit)) {
+                if (err != nullptr && tm.leader)
+                    atomicCAS(err, 0, kErrTmaWait);
+                cp_wait<0>();
+                return false;
+            }
             tph ^= 1u << st;
         }
         const uint32_t so = (uint32_t)(t % kInvDepth) * inv_stage<BOX>();
@@ -1489,6 +1497,29 @@ cudaError_t launch_fuse(bool fwd, bool packed, const FuseWork &w, uint32_t grid,
     if (fwd)
         return packed ? fuse::launch<true, true>(w, grid, stream) : fuse::launch<true, false>(w, grid, stream);
     return packed ? fuse::launch<false, true>(w, grid, stream) : fuse::launch<false, false>(w, grid, stream);
+}
+
+// A stage barrier armed for 16 bytes that no copy delivers, waited on with
+// the box loads' bounded wait: lets a test check that such a wait that runs
+// out sets the error word (7) and returns.
+__global__ void box_stall_probe_kernel(uint32_t limit, int *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t a = fuse::smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        fuse::mbar_init(a);
+        fuse::mbar_init_fence();
+        fuse::mbar_expect(a, 16);
+    }
+    __syncwarp();
+    if (!fuse::box_wait(a, 0, limit) && threadIdx.x == 0)
+        atomicCAS(err, 0, fuse::kErrTmaWait);
+}
+
+cudaError_t launch_box_stall_probe(uint32_t limit, int *err, cudaStream_t stream)
+{
+    box_stall_probe_kernel<<<1, 32, 0, stream>>>(limit, err);
+    return cudaGetLastError();
 }
 
 cudaError_t fuse_shape(bool fwd, bool packed, bool cipher, int *ctas_per_sm, int *warps_per_cta)

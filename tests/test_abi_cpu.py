@@ -74,6 +74,7 @@ def test_null_arguments_are_rejected(L):
     assert L.frag_get_error(None, 0) == fr.FRAG_EINVAL
     assert L.frag_batch_info(None, None, None) == fr.FRAG_EINVAL
     assert L.frag_check_wait_timeout(0, None) == fr.FRAG_EINVAL
+    assert L.frag_check_box_wait_timeout(0, None) == fr.FRAG_EINVAL
     assert L.frag_batch_set_timing(None, 1) == fr.FRAG_EINVAL
     assert L.frag_batch_launch_times(None, None, None) == fr.FRAG_EINVAL
     assert L.frag_plan_set_path(None, 0) == fr.FRAG_EINVAL

@@ -49,3 +49,28 @@ def test_timeout_on_a_side_stream_is_reported_there(fr):
         fr.sync_status(s)
     assert ei.value.status == fr.FRAG_ETIMEOUT
     fr.sync_status()
+
+
+def test_box_load_wait_reports_timeout_and_context_survives(fr):
+    """The fused kernel's wait for a TMA box load, on a barrier armed for
+    bytes no copy delivers: it runs out, reports FRAG_ETIMEOUT with its own
+    message, and a recover that loads its level-1 bands as boxes (one
+    buffer, 2 levels, width 1024) still matches the oracle afterwards."""
+    fr.sync_status()
+    fr.check_box_wait_timeout(polls=1000)
+    with pytest.raises(fr.FragError) as ei:
+        fr.sync_status()
+    assert ei.value.status == fr.FRAG_ETIMEOUT
+    assert "TMA box" in str(ei.value)
+    fr.sync_status()
+    data = wl.random_bytes(1024 * 64, 9)
+    key = fr.Key(wl.KEY)
+    plan = fr.Plan(1024, 2)
+    d = torch.from_numpy(data).cuda()
+    priv, pub = fr.protect(plan, key, 2, d)
+    out = fr.recover(plan, key, 2, priv, pub, data.size)
+    fr.sync_status()
+    p_ref, u_ref = oracle.protect(data, 1024, 2, wl.KEY, 2)
+    assert np.array_equal(priv.cpu().numpy(), p_ref)
+    assert np.array_equal(pub.cpu().numpy(), u_ref)
+    assert np.array_equal(out.cpu().numpy(), data)
