@@ -183,3 +183,24 @@ def test_block_records_match_the_whole_buffer():
         bi, bj = divmod(idx, W // 8)
         got = oracle.keyed_block_records(img[8 * bi:8 * bi + 8, 8 * bj:8 * bj + 8], KEY, 77, idx)
         assert got == want
+
+
+def test_sha512_takes_the_protected_first_fragment():
+    """Sec. 5.2.1: SHA-256 keys the first public fragment from the private
+    one, and SHA-512 keys the second from the first *protected* public
+    fragment.  A block and the same block plus a constant have the same
+    detail bands (the 5/3 high-pass of a constant is exactly zero, floors
+    included) and LL_2 differing by the constant: the same unprotected B and
+    C, a different A.  So their B' differ, and their C' must differ too;
+    hashing the unprotected B into SHA-512 would give both the same C'."""
+    rng = np.random.default_rng(17)
+    x = rng.integers(0, 200, size=(8, 8), dtype=np.uint8)
+    y = (x.astype(np.int32) + 40).astype(np.uint8)
+    _, pub_x = oracle.protect_packed(x.reshape(-1), 8, KEY, NONCE)
+    _, pub_y = oracle.protect_packed(y.reshape(-1), 8, KEY, NONCE)
+    assert np.array_equal(pub_x, pub_y)  # same B and C before the keyed protection
+    a0, b0, c0 = oracle.keyed_block_records(x, KEY, NONCE, 0)
+    a1, b1, c1 = oracle.keyed_block_records(y, KEY, NONCE, 0)
+    assert a0 != a1
+    assert b0 != b1
+    assert c0 != c1
