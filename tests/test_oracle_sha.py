@@ -204,3 +204,24 @@ def test_sha512_takes_the_protected_first_fragment():
     assert a0 != a1
     assert b0 != b1
     assert c0 != c1
+
+
+def test_sha256_takes_only_the_private_fragment():
+    """Sec. 5.2.1: the first public fragment is keyed by SHA-256 of the
+    private fragment (with the key).  Two blocks with the same A and B whose
+    C differs in one coefficient (the second made by the exact inverse from
+    the first's fragments with that coefficient changed by one) get the same
+    B' -- its mask depends on A alone -- and different C'."""
+    rng = np.random.default_rng(23)
+    x = rng.integers(40, 200, size=64, dtype=np.uint8)
+    a, pub = oracle.protect_packed(x, 8, KEY, NONCE)
+    pub2 = pub.copy()
+    pub2[16] ^= np.uint8(1)  # the lowest bit of C's first 10-bit field
+    y = oracle.recover_packed(a, pub2, 64, 8, KEY, NONCE)
+    a_y, pub_y = oracle.protect_packed(y, 8, KEY, NONCE)
+    assert np.array_equal(a_y, a) and np.array_equal(pub_y, pub2)  # same A and B, C one field apart
+    a0, b0, c0 = oracle.keyed_block_records(x.reshape(8, 8), KEY, NONCE, 0)
+    a1, b1, c1 = oracle.keyed_block_records(y.reshape(8, 8), KEY, NONCE, 0)
+    assert a0 == a1
+    assert b0 == b1
+    assert c0 != c1
