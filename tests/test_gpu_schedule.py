@@ -79,7 +79,8 @@ def test_tuner_picks_a_candidate(fr, tmp_path):
 def test_large_batch_one_fused_launch_per_level_count(fr):
     """A batch whose level counts each fill at least eight rounds of full
     fused units on the device runs its first fused pass as one launch per
-    count; its fragments equal one protect call per buffer, and its recover
+    count (4-level buffers join the 3-level launch and add the second fused
+    pass); its fragments equal one protect call per buffer, and its recover
     gives the bytes back."""
     key = fr.Key(wl.KEY)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -88,9 +89,9 @@ def test_large_batch_one_fused_launch_per_level_count(fr):
     need = 8.8 * sms * 16 * 32 / strips        # fused iterations per level count, with a margin
     rows = int(need * 8 / 5) + 1               # five buffers a count
     entries, rentries, singles = [], [], []
-    for L in (1, 2, 3):
+    for L in (1, 2, 3, 4):
         plan = fr.Plan(W, L)
-        for k in range(5):
+        for k in range(5 if L < 4 else 2):
             n = W * (rows + 37 * k) + 1000 * k + 3
             nonce = 100 * L + k
             d = torch.from_numpy(wl.random_bytes(n, nonce)).cuda()
@@ -102,8 +103,9 @@ def test_large_batch_one_fused_launch_per_level_count(fr):
             rentries.append((plan, nonce, n, p, u, o))
             singles.append(fr.protect(plan, key, nonce, d))
     bp, br = fr.Batch(entries, protect=True), fr.Batch(rentries, protect=False)
-    # three fused launches (one per level count) and the CTR launch, each way
-    assert bp.info()[0] == 4 and br.info()[0] == 4
+    # three first-pass launches (one per level count), the second pass (the
+    # 4-level buffers' levels 4) and the CTR launch, each way
+    assert bp.info()[0] == 5 and br.info()[0] == 5
     bp.run(key)
     br.run(key)
     fr.sync_status()
