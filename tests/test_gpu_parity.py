@@ -431,6 +431,38 @@ def test_batch_object_in_cuda_graph(fr, key):
     fr.sync_status()
 
 
+def test_lone_buffer_batch_with_box_loads_in_cuda_graph(fr, key):
+    """A one-buffer batch whose recover loads its level-1 bands as TMA boxes
+    (width 1024, 2 levels; the maps travel in the captured launch's
+    parameters), captured once and replayed: every replay recovers the
+    bytes, and the fragments are the oracle's."""
+    n, W, L, nonce = 1024 * 300 + 77, 1024, 2, 6
+    d = wl.random_bytes(n, 41)
+    plan = fr.Plan(W, L)
+    _, pb, ub = plan.sizes(n)
+    t = torch.from_numpy(d).cuda()
+    p = torch.empty(pb, dtype=torch.uint8, device="cuda")
+    u = torch.empty(ub, dtype=torch.uint8, device="cuda")
+    o = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    bp = fr.Batch([(plan, nonce, n, t, p, u)], protect=True)
+    br = fr.Batch([(plan, nonce, n, p, u, o)], protect=False)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        bp.run(key)
+        br.run(key)
+    p_ref, u_ref = oracle.protect(d, W, L, KEY, nonce)
+    for _ in range(3):
+        o.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(o.cpu().numpy(), d)
+    assert np.array_equal(p.cpu().numpy(), p_ref)
+    assert np.array_equal(u.cpu().numpy(), u_ref)
+    fr.sync_status()
+
+
 def test_batch_of_large_private_fragments(fr, key):
     """A batch whose private fragments total about 16 M AES blocks (the CTR
     pass then takes chunks of several times 256 blocks): every fragment
