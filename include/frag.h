@@ -248,11 +248,14 @@ frag_status frag_aes128_ctr_bitsliced(frag_key key, uint64_t nonce, const void *
  * device memory (the library's pool), run the same kernels, copy the results
  * back, and return once they are in host memory.  Pinned (cudaHostAlloc) host
  * buffers give full copy bandwidth.  A buffer of 16 MiB or more whose levels
- * all run in the first fused pass (1..3 levels, FRAG_PATH_AUTO) moves in
- * eight row bands on two library streams beside the caller's: band k + 1
- * is copied in while band k is transformed and band k - 1 copied out, so
- * the two copy directions and the kernels overlap (with pinned buffers).
- * The bytes written do not depend on the form. */
+ * all run in the fused passes (1..6 levels, FRAG_PATH_AUTO) moves in row
+ * bands of about 32 MiB (8 to 64 of them) on two library streams beside the
+ * caller's: band k + 1 is copied in while band k is transformed and band
+ * k - 1 copied out, so the two copy directions and the kernels overlap
+ * (with pinned buffers).  At 4..6 levels the bands cover levels 1..3; the
+ * levels above and the private fragment move whole, after the bands
+ * (protect) or before them (recover).  The bytes written do not depend on
+ * the form. */
 frag_status frag_protect_host(frag_plan plan, frag_key key, uint64_t nonce, const void *h_in,
                               uint64_t nbytes, void *h_private, void *h_public,
                               frag_stream stream);

@@ -1122,8 +1122,28 @@ frag_status run_single(bool fwd, frag_plan plan, frag_key key, Buf b, cudaStream
 // no block may be done twice); recover deciphers, band by band, every block
 // the band's rows touch into the plaintext scratch the inverse reads.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kHostBands = 8;
+// bands of about FRAG_HOST_BAND_MB MiB, 8 to 64 of them: the first band's
+// copy in and the last band's copy out overlap nothing, so finer bands
+// shorten the pipeline's head and tail, but every copy also costs a few us
+// of its own (pinned, one B300, protect + recover of 256 MiB at 2 levels:
+// 8 / 16 / 32 / 64 bands 11.24 / 10.96 / 10.50 / 9.83 GB/s; of 1 GiB: 8 /
+// 16 / 32 bands 11.69 / 11.82 / 11.86 GB/s).  FRAG_HOST_COPY2D moves a
+// level's three band pieces in one strided copy instead of three
+// (256 MiB: 11.40 against 11.20 GB/s; 1 GiB: 11.86 against 11.51)
+#ifndef FRAG_HOST_BAND_MB
+#define FRAG_HOST_BAND_MB 32
+#endif
+#ifndef FRAG_HOST_COPY2D
+#define FRAG_HOST_COPY2D 1
+#endif
+constexpr uint64_t kHostBandBytes = (uint64_t)FRAG_HOST_BAND_MB << 20;
+constexpr uint32_t kHostBandsMin = 8, kHostBandsMax = 64;
 constexpr uint64_t kHostBandMin = 16ull << 20; // smaller buffers run in one piece
+
+uint32_t host_bands(uint64_t n)
+{
+    return (uint32_t)std::min<uint64_t>(kHostBandsMax, std::max<uint64_t>(kHostBandsMin, (n + kHostBandBytes - 1) / kHostBandBytes));
+}
 
 struct Pipe {
     cudaStream_t in = nullptr, out = nullptr;
@@ -1165,7 +1185,7 @@ frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t non
                             bool *done)
 {
     *done = false;
-    if (n < kHostBandMin || plan->block || plan->packed || plan->levels > frag::kFuseMaxLevels ||
+    if (n < kHostBandMin || plan->block || plan->packed || plan->levels > 2 * frag::kFuseMaxLevels ||
         plan->path != FRAG_PATH_AUTO)
         return FRAG_OK;
     DeviceState *d = nullptr;
@@ -1180,6 +1200,8 @@ frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t non
     const uint64_t pb = ll_bytes(H, W, L), ub = 2ull * H * W - pb;
     const uint64_t a_n = align256(n), a_pb = align256(pb), a_ub = align256(ub);
     const uint64_t ll_scr = fwd ? 0 : a_pb;
+    // 4..6 levels: LL_3 between the banded first pass and the second pass
+    const uint64_t a_s3 = L > frag::kFuseMaxLevels ? align256(ll_bytes(H, W, frag::kFuseMaxLevels)) : 0;
     Buf b;
     std::memset(&b, 0, sizeof(b));
     b.W = W;
@@ -1188,7 +1210,7 @@ frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t non
     b.n = n;
     b.nonce = nonce;
     uint8_t *mem = nullptr;
-    cudaError_t e = pool_malloc((void **)&mem, a_n + a_pb + a_ub + ll_scr, s);
+    cudaError_t e = pool_malloc((void **)&mem, a_n + a_pb + a_ub + ll_scr + a_s3, s);
     if (e != cudaSuccess)
         return cuda_fail(e, "pool_malloc(host-form buffers)");
     uint8_t *d_data = mem, *d_priv = mem + a_n, *d_pub = d_priv + a_pb;
@@ -1202,19 +1224,33 @@ frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t non
         b.pub_in = d_pub;
         b.scr[L] = d_pub + a_ub;
     }
+    if (a_s3)
+        b.scr[frag::kFuseMaxLevels] = d_pub + a_ub + ll_scr;
     fused_split(fwd, b, plan->path);
     const uint32_t *rk = nullptr;
-    frag::FuseWork fw;
+    // fw: the first fused pass, run band by band; fw2: the second (levels
+    // 4..L over LL_3), one launch after the bands (protect) or before them
+    // (recover)
+    frag::FuseWork fw, fw2;
     std::memset(&fw, 0, sizeof(fw));
-    uint64_t slots = 0;
-    bool ok = b.F1 == L && b.F2 == 0 && !b.kc;
-    if (ok && (st = key_on_device(key, dev, &rk)) == FRAG_OK &&
+    std::memset(&fw2, 0, sizeof(fw2));
+    uint64_t slots = 0, slots2 = 0;
+    const bool two = b.F2 != 0;
+    bool ok = b.F1 + b.F2 == L && (!two || b.F1 == frag::kFuseMaxLevels) && !b.kc;
+    if (ok && two && (st = fuse_slots(*d, fwd, true, plan->max_ctas, &slots2)) == FRAG_OK) {
+        fw2.single = fuse_buf(fwd, b, 2);
+        fw2.nbufs = 1;
+        fw2.total_units = fuse_schedule(&fw2.single, 1, slots2, plan->seg_rows);
+        fw2.err = d->err;
+    }
+    if (ok && st == FRAG_OK && (st = key_on_device(key, dev, &rk)) == FRAG_OK &&
         (st = fuse_slots(*d, fwd, false, plan->max_ctas, &slots)) == FRAG_OK) {
         fw.single = fuse_buf(fwd, b, 1);
         fw.nbufs = 1;
-        // units for kHostBands times the resident warps, so that every
+        fw.err = d->err;
+        // units for the band count times the resident warps, so that every
         // band's launch still fills the device
-        fuse_schedule(&fw.single, 1, slots * kHostBands, plan->seg_rows);
+        fuse_schedule(&fw.single, 1, slots * host_bands(n), plan->seg_rows);
         ok = fw.single.segs >= 2;
     }
     if (st != FRAG_OK || !ok) {
@@ -1224,13 +1260,13 @@ frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t non
     *done = true;
     const frag::AesKeys keys = frag::aes::keys_from_words(key->rk);
     const uint32_t segs = fw.single.segs, strips = fw.single.strips, seg = fw.single.seg_iters;
-    const uint32_t iters = fw.single.iters, K = std::min(kHostBands, segs);
+    const uint32_t iters = fw.single.iters, K = std::min(host_bands(n), segs);
     Pipe p;
-    if ((e = p.make(2 * K + 1)) != cudaSuccess) {
+    if ((e = p.make(2 * K + 2)) != cudaSuccess) {
         cudaFreeAsync(mem, s);
         return cuda_fail(e, "host-form streams");
     }
-    const uint32_t WL = W >> L;
+    const uint32_t WL = W >> L, F1 = b.F1;
     uint64_t row0 = 0;                     // level-0 rows moved so far
     uint64_t lrow[frag::kFuseMaxLevels + 1] = {0, 0, 0, 0}; // level-l rows moved so far
     uint64_t blk0 = 0;                     // AES blocks handled so far
@@ -1241,12 +1277,47 @@ frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t non
     auto band_rows = [&](uint32_t l, uint64_t r0, uint64_t r1, bool in, cudaStream_t cs) {
         const uint64_t rowb = 2ull * (W >> l);
         cudaError_t r = cudaSuccess;
+#if FRAG_HOST_COPY2D
+        // the three bands of a level lie one after another, so one strided
+        // copy moves their rows [r0, r1)
+        const uint64_t pitch = frag::band_offset(b.H, W, L, l, 1) - frag::band_offset(b.H, W, L, l, 0);
+        if (pitch < (1ull << 31)) {
+            const uint64_t off = frag::band_offset(b.H, W, L, l, 0) + rowb * r0, len = rowb * (r1 - r0);
+            return in ? cudaMemcpy2DAsync(d_pub + off, pitch, h_b + off, pitch, len, 3, h2d, cs)
+                      : cudaMemcpy2DAsync(h_d + off, pitch, d_pub + off, pitch, len, 3, d2h, cs);
+        }
+#endif
         for (uint32_t k = 0; k < 3 && r == cudaSuccess; ++k) {
             const uint64_t off = frag::band_offset(b.H, W, L, l, k) + rowb * r0, len = rowb * (r1 - r0);
             r = in ? copy_async(d_pub + off, h_b + off, len, h2d, cs) : copy_async(h_d + off, d_pub + off, len, d2h, cs);
         }
         return r;
     };
+    auto whole_chunk = [&](const uint8_t *in, uint8_t *out) {
+        frag::CtrChunk c;
+        std::memset(&c, 0, sizeof(c));
+        c.nonce = nonce;
+        c.bytes = pb;
+        c.in = in;
+        c.out = out;
+        c.nblocks = nblk;
+        return c;
+    };
+    if (two && !fwd) {
+        // the private fragment and the levels above 3 are small: in at once,
+        // then the deciphering and the second pass make LL_3 before the
+        // first band's kernels
+        e = copy_async(d_priv, h_a, pb, h2d, p.in);
+        for (uint32_t l = F1 + 1; l <= L && e == cudaSuccess; ++l)
+            e = band_rows(l, 0, H >> l, true, p.in);
+        if (e == cudaSuccess && (e = cudaEventRecord(p.ev[2 * K + 1], p.in)) == cudaSuccess)
+            e = cudaStreamWaitEvent(s, p.ev[2 * K + 1], 0);
+        if (e == cudaSuccess) {
+            const frag::CtrChunk c = whole_chunk(d_priv, b.scr[L]);
+            if ((st = ctr_launch(*d, keys, nullptr, &c, s)) == FRAG_OK)
+                st = fuse_launch(*d, false, true, fw2, slots2, s);
+        }
+    }
     for (uint32_t k = 0; k < K && e == cudaSuccess && st == FRAG_OK; ++k) {
         const bool last = k + 1 == K;
         const uint64_t sy0 = (uint64_t)k * segs / K, sy1 = (uint64_t)(k + 1) * segs / K;
@@ -1265,13 +1336,13 @@ frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t non
         } else {
             // in: coefficient rows the band's iterations read, and the
             // private blocks that cover its LL_L rows
-            for (uint32_t l = 1; l <= L && e == cudaSuccess; ++l) {
+            for (uint32_t l = 1; l <= F1 && e == cudaSuccess; ++l) {
                 const uint64_t Hl = H >> l, r1 = last ? Hl : std::min<uint64_t>(Hl, (8u >> l) * t1 + 1);
                 if (r1 > lrow[l])
                     e = band_rows(l, lrow[l], r1, true, p.in);
                 lrow[l] = std::max(lrow[l], r1);
             }
-            const uint64_t bhi = last ? nblk : std::min<uint64_t>(nblk, (2ull * WL * lrow[L] + 15) / 16);
+            const uint64_t bhi = two ? 0 : last ? nblk : std::min<uint64_t>(nblk, (2ull * WL * lrow[L] + 15) / 16);
             if (e == cudaSuccess && bhi > blk0)
                 e = copy_async(d_priv + 16 * blk0, h_a + 16 * blk0, std::min(pb, 16 * bhi) - 16 * blk0, h2d, p.in);
             if (bhi > blk0) {
@@ -1294,7 +1365,7 @@ frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t non
             st = ctr_launch(*d, keys, nullptr, &c, s);
         if (st == FRAG_OK)
             st = fuse_launch(*d, fwd, false, fw, slots, s);
-        if (st == FRAG_OK && fwd) {
+        if (st == FRAG_OK && fwd && !two) {
             // encipher the blocks whose bytes are all written now
             const uint64_t Hl = H >> L, r1 = last ? Hl : std::min<uint64_t>(Hl, (8u >> L) * t1 - 1);
             const uint64_t bhi = last ? nblk : std::min<uint64_t>(nblk, 2ull * WL * r1 / 16);
@@ -1314,14 +1385,14 @@ frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t non
             break;
         if (fwd) {
             // out: the detail rows and the enciphered blocks the band finished
-            for (uint32_t l = 1; l <= L && e == cudaSuccess; ++l) {
+            for (uint32_t l = 1; l <= F1 && e == cudaSuccess; ++l) {
                 const uint64_t Hl = H >> l, r1 = last ? Hl : std::min<uint64_t>(Hl, (8u >> l) * t1 - 1);
                 if (r1 > lrow[l])
                     e = band_rows(l, lrow[l], r1, false, p.out);
                 lrow[l] = std::max(lrow[l], r1);
             }
             const uint64_t Hl = H >> L, r1 = last ? Hl : std::min<uint64_t>(Hl, (8u >> L) * t1 - 1);
-            const uint64_t bhi = last ? nblk : std::min<uint64_t>(nblk, 2ull * WL * r1 / 16);
+            const uint64_t bhi = two ? 0 : last ? nblk : std::min<uint64_t>(nblk, 2ull * WL * r1 / 16);
             if (e == cudaSuccess && bhi > blk0)
                 e = copy_async(h_c + 16 * blk0, d_priv + 16 * blk0, std::min(pb, 16 * bhi) - 16 * blk0, d2h, p.out);
             blk0 = std::max(blk0, bhi);
@@ -1331,6 +1402,20 @@ frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t non
             const uint64_t lo = std::min(n, row0 * W), hi = std::min(n, r1 * W);
             e = copy_async(h_c + lo, d_data + lo, hi - lo, d2h, p.out);
             row0 = std::max(row0, r1);
+        }
+    }
+    if (two && fwd && e == cudaSuccess && st == FRAG_OK) {
+        // after the last band: the second pass over LL_3, the private
+        // fragment enciphered whole, and the small rest copied out
+        const frag::CtrChunk c = whole_chunk(d_priv, d_priv);
+        if ((st = fuse_launch(*d, true, true, fw2, slots2, s)) == FRAG_OK &&
+            (st = ctr_launch(*d, keys, nullptr, &c, s)) == FRAG_OK &&
+            (e = cudaEventRecord(p.ev[2 * K + 1], s)) == cudaSuccess &&
+            (e = cudaStreamWaitEvent(p.out, p.ev[2 * K + 1], 0)) == cudaSuccess) {
+            for (uint32_t l = F1 + 1; l <= L && e == cudaSuccess; ++l)
+                e = band_rows(l, 0, H >> l, false, p.out);
+            if (e == cudaSuccess)
+                e = copy_async(h_c, d_priv, pb, d2h, p.out);
         }
     }
     if (e == cudaSuccess && st == FRAG_OK && (e = cudaEventRecord(p.ev[2 * K], p.out)) == cudaSuccess)

@@ -303,11 +303,15 @@ def test_host_buffer_forms(fr, key):
 
 
 # buffers of 16 MiB and more take the banded host form: copies in, kernels
-# and copies out of row bands overlap on three streams
+# and copies out of row bands overlap on three streams (bands of about 32
+# MiB, at least 8: the 300 MiB case runs 10); at 4..6 levels the bands run
+# the first fused pass and the second pass runs whole
 @pytest.mark.parametrize("pinned", [True, False])
 @pytest.mark.parametrize("n,W,L", [((16 << 20) + 12345, 4096, 3), ((20 << 20) - 7, 8192, 2),
                                    ((17 << 20) + 1, 2048, 1), (24 << 20, 1024, 3),
-                                   ((18 << 20) + 999, 4000, 2)])
+                                   ((18 << 20) + 999, 4000, 2), ((300 << 20) + 77, 8192, 2),
+                                   ((20 << 20) + 3, 4096, 4), ((40 << 20) - 5, 8192, 5),
+                                   ((24 << 20) + 11, 2048, 6)])
 def test_host_forms_in_bands(fr, key, n, W, L, pinned):
     """The banded host forms give the device calls' fragments byte for byte
     and recover every byte (and, on one case, the oracle's fragments)."""
