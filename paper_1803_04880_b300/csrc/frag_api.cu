@@ -613,6 +613,10 @@ frag_status ctr_launch(DeviceState &d, const frag::AesKeys &keys, const CtrList 
 // Fused path: levels 1..F of a buffer in one pass down its rows
 // ---------------------------------------------------------------------------
 constexpr uint32_t kFuseMinSegIters = 8; // iterations per unit at least (adaptive choice)
+#ifndef FRAG_FUSE_TINY_SEG
+#define FRAG_FUSE_TINY_SEG 1
+#endif
+constexpr uint32_t kFuseTinySegIters = FRAG_FUSE_TINY_SEG;
 
 // levels a fused pass over levels lo+1 .. lo+F can take (0: none): its
 // input width (W >> lo) a multiple of 8 and every band and the LL output it
@@ -750,7 +754,8 @@ frag::FuseBuf fuse_buf(bool fwd, const Buf &b, int pass = 1)
 // protect, units of 32 iterations 60.5 ms, of 16 or 8 iterations 62.5 ms)
 constexpr uint32_t kFuseBatchSegIters = 32;
 
-uint64_t fuse_schedule(frag::FuseBuf *f, size_t nbufs, uint64_t warps, uint32_t plan_rows, bool batch = false)
+uint64_t fuse_schedule(frag::FuseBuf *f, size_t nbufs, uint64_t warps, uint32_t plan_rows, bool batch = false,
+                       bool tiny = true)
 {
     uint32_t seg = 0;
     if (plan_rows) {
@@ -762,7 +767,13 @@ uint64_t fuse_schedule(frag::FuseBuf *f, size_t nbufs, uint64_t warps, uint32_t 
         uint64_t per = (work + warps - 1) / std::max<uint64_t>(1, warps);
         if (batch && nbufs > 1) // one buffer's units are all alike
             per = std::min<uint64_t>(per, kFuseBatchSegIters);
-        seg = (uint32_t)std::min<uint64_t>(1u << 20, std::max<uint64_t>(kFuseMinSegIters, per));
+        // a launch too small to give each resident warp one iteration is
+        // latency-bound: shorter units shorten its longest chain (the
+        // 256 x 256 buffer at one level: units of 8 / 4 / 2 / 1 iterations,
+        // protect p50 17.5 / 15.5 / 12.9 / 11.2 us); `tiny` false keeps the
+        // longer units (a band of the host forms, which overlaps copies)
+        const uint32_t lo = tiny && work <= warps ? kFuseTinySegIters : kFuseMinSegIters;
+        seg = (uint32_t)std::min<uint64_t>(1u << 20, std::max<uint64_t>(lo, per));
     }
     uint64_t units = 0;
     for (size_t i = 0; i < nbufs; ++i) {
@@ -1250,7 +1261,7 @@ frag_status run_host_banded(bool fwd, frag_plan plan, frag_key key, uint64_t non
         fw.err = d->err;
         // units for the band count times the resident warps, so that every
         // band's launch still fills the device
-        fuse_schedule(&fw.single, 1, slots * host_bands(n), plan->seg_rows);
+        fuse_schedule(&fw.single, 1, slots * host_bands(n), plan->seg_rows, false, false);
         ok = fw.single.segs >= 2;
     }
     if (st != FRAG_OK || !ok) {
