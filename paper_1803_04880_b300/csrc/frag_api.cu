@@ -835,8 +835,14 @@ frag_status fuse_launch(DeviceState &d, bool fwd, bool packed, frag::FuseWork &w
     frag_status st = fuse_shape(d, fwd, packed, w.cipher != 0, &ctas, &wpc);
     if (st != FRAG_OK)
         return st;
-    const uint64_t need = (w.total_units + wpc - 1) / wpc;
     const uint64_t cap = std::min<uint64_t>((uint64_t)d.sms * ctas, (slots + wpc - 1) / wpc);
+    // at most half as many units as the launch's warps: one CTA a unit
+    // first, spread over the SMs (8 / 16 MiB at 3 levels, protect 30.7 /
+    // 31.6 -> 21.5 / 24.6 us); a fuller launch keeps a CTA's warps on
+    // neighbouring strips of the same rows (spread, 32 / 48 / 64 MiB lost
+    // 1 us a protect, the 256 MiB buffer's went from 154.8 to 171.7 us)
+    w.spread = 2 * w.total_units <= cap * (uint64_t)wpc;
+    const uint64_t need = w.spread ? w.total_units : (w.total_units + wpc - 1) / wpc;
     const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min(cap, need));
     cudaError_t e = frag::launch_fuse(fwd, packed, w, grid, s);
     if (e != cudaSuccess)

@@ -275,6 +275,12 @@ struct FuseWork {
     // the buffer's three level-1 bands (uint16, rows of W/2, boxes of 4 rows x
     // 136 values) when l1_tma != 0, else per-lane copies
     uint32_t l1_tma;
+    // units to warps: 0 = unit u to warp u % W of CTA u / W (W warps a CTA:
+    // a CTA's warps take neighbouring strips of the same rows, which a full
+    // launch reads faster); 1 = unit u to CTA u % grid (a launch with fewer
+    // units than warps then spreads them over every SM instead of filling a
+    // few)
+    uint32_t spread;
     CUtensorMap l1_map[3];
 };
 

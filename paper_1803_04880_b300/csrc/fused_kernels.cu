@@ -1407,7 +1407,8 @@ __global__ void __launch_bounds__(32 * cta_warps<FWD, PK, CIPH>(), 16 / cta_warp
     }
     const uint64_t G = (uint64_t)gridDim.x * kWarps;
     const uint64_t u_end = w.unit_lo + w.total_units;
-    for (uint64_t u = w.unit_lo + (uint64_t)blockIdx.x * kWarps + warp; u < u_end; u += G) {
+    const uint64_t u0 = w.spread ? (uint64_t)warp * gridDim.x + blockIdx.x : (uint64_t)blockIdx.x * kWarps + warp;
+    for (uint64_t u = w.unit_lo + u0; u < u_end; u += G) {
         uint64_t local;
         const FuseBuf *bp = unit_buf(w, u, local);
         const FuseBuf b = *bp;

@@ -289,9 +289,12 @@ extern "C" frag_status frag_protect_batch_noalloc(const frag_item *items, uint32
             fw.total_units = units;
             fw.err = err;
             fw.aes_t0 = tables;
-            const uint64_t need = (units + d->fuse_warps - 1) / d->fuse_warps;
-            const uint32_t fgrid = (uint32_t)std::max<uint64_t>(
-                1, std::min<uint64_t>((uint64_t)d->sms * d->fuse_ctas, need));
+            // at most half as many units as warps: spread over the SMs, as
+            // the other calls do
+            const uint64_t cap = (uint64_t)d->sms * d->fuse_ctas;
+            fw.spread = 2 * units <= cap * d->fuse_warps;
+            const uint64_t need = fw.spread ? units : (units + d->fuse_warps - 1) / d->fuse_warps;
+            const uint32_t fgrid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(cap, need));
             if (units && (e = frag::launch_fuse(true, false, fw, fgrid, s)) != cudaSuccess)
                 return frag::report_cuda(e, "frag_protect_batch_noalloc: fused launch");
         }
